@@ -1,0 +1,128 @@
+"""Pointwise KL proximal maps of sigma*f (oracle, FP64).
+
+Prox^{KL}_{sigma f}(s) = argmin_{p >= 0} KL(p|s) + sigma f(p)
+(Eq. def-kl-prox-operator), separable over cells for every f used here.
+
+Per cell, with l = log s - sigma w (linear shift rule, Eq. prox-calculus-shift):
+  * no entropy term         psi = e^l
+  * m = 1 (entropy)         psi = exp(l / (1 + sigma alpha))          (Eq. prox-entropy)
+  * m > 1 (power)           log psi + beta psi^{m-1} = l,
+                            beta = sigma alpha m/(m-1)                (Eq. prox-psi, power form)
+  * congestion              p = min(psi, kappa)                       (Prop. 4.1; a 1-D
+                            strictly convex problem on [0, kappa] is solved by clamping)
+  * obstacle mask           p = 0.
+For m > 1 the root has the closed form
+  psi^{m-1} = W0((m-1) beta e^{(m-1) l}) / ((m-1) beta)
+with W0 the principal Lambert W branch (SciPy); ``root_bisect`` finds the same
+root by bisection and the tests pin the two against each other and against a
+direct numerical minimisation of the 1-D objective.
+
+``ratio`` returns a = Prox(s)/s, continuously extended at s = 0 (reading of
+the 0/0 case): e^{-sigma w} for the congestion/potential and power cases,
+0 for the m = 1 entropy and for masked cells.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import lambertw
+
+from .energy import Energy
+
+
+def root_lambertw(l: np.ndarray, beta: np.ndarray, m: float) -> np.ndarray:
+    """psi > 0 solving log psi + beta psi^{m-1} = l, m > 1 (closed form)."""
+    l = np.asarray(l, np.float64)
+    beta = np.broadcast_to(np.asarray(beta, np.float64), l.shape)
+    k = (m - 1.0) * beta
+    out = np.empty_like(l)
+    zero = np.isneginf(l)
+    out[zero] = 0.0
+    nz = ~zero
+    ln_arg = np.log(k[nz]) + (m - 1.0) * l[nz]
+    W = np.empty_like(ln_arg)
+    small = ln_arg < 700.0
+    W[small] = lambertw(np.exp(ln_arg[small])).real
+    W[~small] = _lambertw_large(ln_arg[~small])
+    out[nz] = (W / k[nz]) ** (1.0 / (m - 1.0))
+    return out
+
+
+def _lambertw_large(ln_x: np.ndarray) -> np.ndarray:
+    """W0(e^{ln_x}) for huge arguments by Newton on w + log w = ln_x."""
+    w = np.maximum(ln_x - np.log(np.maximum(ln_x, 1.0)), 1.0)
+    for _ in range(50):
+        w = w - (w + np.log(w) - ln_x) / (1.0 + 1.0 / w)
+    return w
+
+
+def root_bisect(l: np.ndarray, beta: np.ndarray, m: float, iters: int = 200) -> np.ndarray:
+    """Same root as ``root_lambertw`` by bisection on y = log psi.
+
+    g(y) = y + beta e^{(m-1) y} - l is increasing; g(l) >= 0 and
+    g(l - beta e^{(m-1) l}) <= 0 bracket the root."""
+    l = np.asarray(l, np.float64)
+    beta = np.broadcast_to(np.asarray(beta, np.float64), l.shape)
+    hi = l.copy()
+    lo = l - beta * np.exp((m - 1.0) * l)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        g = mid + beta * np.exp((m - 1.0) * mid) - l
+        pos = g > 0
+        hi = np.where(pos, mid, hi)
+        lo = np.where(pos, lo, mid)
+        if np.all(hi - lo <= 1e-16 * np.maximum(1.0, np.abs(hi))):
+            break
+    return np.exp(0.5 * (lo + hi))
+
+
+def prox(s: np.ndarray, sigma: float, energy: Energy, method: str = "lambertw") -> np.ndarray:
+    """Prox^{KL}_{sigma f}(s) cell by cell."""
+    s = np.asarray(s, np.float64)
+    N = s.size
+    w, kappa, alpha, mask = energy.arrays(N)
+    with np.errstate(divide="ignore"):
+        l = np.log(s) - sigma * w
+    if energy.m == 0:
+        psi = np.exp(l)
+    elif energy.m == 1:
+        psi = np.exp(l / (1.0 + sigma * alpha))
+    else:
+        m = float(energy.m)
+        beta = sigma * alpha * m / (m - 1.0)
+        psi = (root_lambertw(l, beta, m) if method == "lambertw"
+               else root_bisect(l, beta, m))
+    p = np.minimum(psi, kappa)
+    p[mask] = 0.0
+    return p
+
+
+def ratio(s: np.ndarray, sigma: float, energy: Energy, method: str = "lambertw") -> np.ndarray:
+    """a = Prox_{sigma f}(s) / s, extended continuously at s = 0."""
+    s = np.asarray(s, np.float64)
+    N = s.size
+    w, kappa, alpha, mask = energy.arrays(N)
+    p = prox(s, sigma, energy, method)
+    a = np.empty(N)
+    pos = s > 0
+    a[pos] = p[pos] / s[pos]
+    z = ~pos
+    if energy.m == 1:
+        a[z] = 0.0
+    else:
+        a[z] = np.exp(-sigma * w[z])
+    a[mask] = 0.0
+    return a
+
+
+def objective_1d(p: float, s: float, sigma: float, w: float, kappa: float,
+                 m: float, alpha: float) -> float:
+    """KL(p|s) + sigma f(p) for one cell (used to pin the maps by brute force)."""
+    if p < 0 or p > kappa:
+        return np.inf
+    kl = (p * np.log(p / s) if p > 0 else 0.0) - p + s
+    f = w * p
+    if m == 1:
+        f += alpha * ((p * np.log(p) if p > 0 else 0.0) - p)
+    elif m > 1:
+        f += alpha * p ** m / (m - 1.0)
+    return kl + sigma * f

@@ -1,0 +1,244 @@
+"""Seeded synthetic inputs for the entropic JKO workloads.
+
+This module only *describes problems*: grid geometry, initial densities,
+potentials, weight fields and obstacle masks.  It contains none of the
+method's arithmetic (no Gibbs kernel, no proximal map, no scaling loop), so
+both the FP64 CPU oracle (``oracle/``) and the CUDA path can be fed from it
+without sharing any computation.
+
+Workload recipes (Peyre 2015, Sec. 4.2 crowd motion and Sec. 4.4 non-linear
+diffusion give the shapes; the paper prints no data, so everything here is
+synthetic):
+
+* crowd motion  -- f = iota_{[0,kappa]} + <w,p> (Eq. dfn-congestion),
+  w(x) = |x - x0|^2, q = normalised uniform disk, kappa = factor * max q.
+* porous medium -- f = sum alpha_i p_i^m/(m-1) with m = 2, alpha a smooth
+  field built from 8 random Gaussians and rescaled to [0.5, 2], an obstacle
+  mask made of 3 axis-aligned rectangles covering 15% of the cells, and q a
+  mixture of 4 Gaussian bumps, zeroed on the mask and renormalised.
+
+All arrays are float64, row-major ``[ny, nx]`` images flattened to length
+N = nx*ny (index y*nx + x), on the domain [0, lx] x [0, ly] sampled at cell
+centres ((i + 1/2) h).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "Problem",
+    "cell_centres",
+    "crowd_problem",
+    "porous_problem",
+    "seed_for",
+    "CONFIGS",
+    "config_problem",
+    "batched_problems",
+    "differentiation_problem",
+]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One entropic JKO flow: grid, step parameters, energy terms and q0."""
+
+    nx: int
+    ny: int
+    gamma: float
+    tau: float
+    q0: np.ndarray                       # (N,) float64, sums to 1
+    lx: float = 1.0
+    ly: float = 1.0
+    w: Optional[np.ndarray] = None       # (N,) potential, None = 0
+    kappa: float = float("inf")          # congestion bound, inf = none
+    m: float = 0.0                       # 0: no entropy term; 1: entropy; >1 power
+    alpha: Optional[np.ndarray] = None   # (N,) weights of the entropy term
+    mask: Optional[np.ndarray] = None    # (N,) uint8, 1 = obstacle cell
+    n_steps: int = 1
+    max_iter: int = 200
+    tol: float = 1e-9
+    name: str = ""
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny
+
+
+def seed_for(config: int, flow: int = 0) -> int:
+    """Seed convention: 1000 * config index + flow index."""
+    return 1000 * config + flow
+
+
+def cell_centres(n: int, length: float = 1.0) -> np.ndarray:
+    """Cell-centre coordinates (i + 1/2) * length / n, i = 0..n-1."""
+    return (np.arange(n, dtype=np.float64) + 0.5) * (length / n)
+
+
+def _mesh(nx: int, ny: int, lx: float, ly: float):
+    xs = cell_centres(nx, lx)
+    ys = cell_centres(ny, ly)
+    X, Y = np.meshgrid(xs, ys, indexing="xy")  # shape (ny, nx)
+    return X, Y
+
+
+def _disk(nx, ny, centre, radius, lx=1.0, ly=1.0):
+    X, Y = _mesh(nx, ny, lx, ly)
+    inside = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2 <= radius ** 2
+    q = inside.astype(np.float64)
+    if q.sum() == 0.0:  # very coarse grid: take the nearest cell
+        d = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2
+        q.flat[np.argmin(d)] = 1.0
+    return (q / q.sum()).ravel()
+
+
+def crowd_problem(n: int, gamma: float, tau: float = 0.02,
+                  kappa_factor: float = 1.5,
+                  target=(0.9, 0.5), disk_centre=(0.25, 0.5),
+                  disk_radius: float = 0.2, n_steps: int = 20,
+                  max_iter: int = 200, tol: float = 1e-9,
+                  ny: Optional[int] = None, name: str = "crowd") -> Problem:
+    """Crowd motion: congestion kappa = factor * max q0 and w = |x - target|^2."""
+    nx = n
+    ny = n if ny is None else ny
+    q0 = _disk(nx, ny, disk_centre, disk_radius)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    w = ((X - target[0]) ** 2 + (Y - target[1]) ** 2).ravel()
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w,
+                   kappa=float(kappa_factor * q0.max()), n_steps=n_steps,
+                   max_iter=max_iter, tol=tol, name=name)
+
+
+def _smooth_field(rng, X, Y, n_bumps=8):
+    acc = np.zeros_like(X)
+    for _ in range(n_bumps):
+        amp = rng.uniform(0.5, 1.0)
+        c = rng.uniform(0.0, 1.0, size=2)
+        s = rng.uniform(0.05, 0.2)
+        acc += amp * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2) / (2 * s * s))
+    lo, hi = acc.min(), acc.max()
+    return (acc - lo) / (hi - lo) if hi > lo else np.zeros_like(acc)
+
+
+def _rect_mask(rng, X, Y, cover=0.15, n_rect=3, slack=0.005):
+    centres = rng.uniform(0.1, 0.9, size=(n_rect, 2))
+    aspect = rng.uniform(0.5, 2.0, size=n_rect)
+
+    def union(t):
+        m = np.zeros(X.shape, dtype=bool)
+        for k in range(n_rect):
+            hx = t * np.sqrt(aspect[k])
+            hy = t / np.sqrt(aspect[k])
+            m |= (np.abs(X - centres[k, 0]) <= hx) & (np.abs(Y - centres[k, 1]) <= hy)
+        return m
+
+    lo, hi = 0.0, 1.0
+    best = union(0.5 * (lo + hi))
+    for _ in range(60):  # coverage is monotone in the half-width scale t
+        t = 0.5 * (lo + hi)
+        best = union(t)
+        frac = best.mean()
+        if abs(frac - cover) <= slack:
+            break
+        if frac < cover:
+            lo = t
+        else:
+            hi = t
+    return best
+
+
+def _gaussian_mixture(rng, X, Y, n_bumps=4, sig=(0.03, 0.08), box=(0.15, 0.85)):
+    q = np.zeros_like(X)
+    for _ in range(n_bumps):
+        wgt = rng.uniform(0.5, 1.0)
+        c = rng.uniform(box[0], box[1], size=2)
+        s = rng.uniform(sig[0], sig[1])
+        q += wgt * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2) / (2 * s * s))
+    return q
+
+
+def porous_problem(n: int, seed: int, gamma: float = 5e-4, tau: float = 5e-3,
+                   m: float = 2.0, with_mask: bool = True, n_steps: int = 50,
+                   max_iter: int = 500, tol: float = 1e-6,
+                   ny: Optional[int] = None, name: str = "porous") -> Problem:
+    """Porous-medium flow with smooth weights alpha in [0.5, 2] and obstacles."""
+    nx = n
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    alpha = 0.5 + 1.5 * _smooth_field(rng, X, Y)
+    mask = _rect_mask(rng, X, Y) if with_mask else np.zeros(X.shape, dtype=bool)
+    q = _gaussian_mixture(rng, X, Y)
+    q[mask] = 0.0
+    if q.sum() <= 0.0:
+        q = np.where(mask, 0.0, 1.0)
+    q = q / q.sum()
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q.ravel(),
+                   m=m, alpha=alpha.ravel(), mask=mask.ravel().astype(np.uint8),
+                   n_steps=n_steps, max_iter=max_iter, tol=tol, name=name)
+
+
+# Named workloads.  Sizes are parameters so that tests can run the same recipe
+# at sizes a CPU finishes in seconds.
+CONFIGS = {
+    0: dict(kind="crowd", n=64, gamma=2e-3, tau=0.02, kappa_factor=1.5,
+            n_steps=20, max_iter=200, tol=1e-9),
+    1: dict(kind="porous", n=512, gamma=5e-4, tau=5e-3, m=2.0,
+            n_steps=50, max_iter=500, tol=1e-6),
+    2: dict(kind="crowd", n=1024, gamma=2e-4, tau=0.02, kappa_factor=1.2,
+            n_steps=30, max_iter=200, tol=1e-6),
+    4: dict(kind="crowd", n=256, gamma=1e-3, tau=0.02, kappa_factor=1.5,
+            n_steps=10, max_iter=200, tol=1e-6),
+}
+
+
+def config_problem(config: int, n: Optional[int] = None, **overrides) -> Problem:
+    """Problem of a named workload, optionally at another grid size n."""
+    spec = dict(CONFIGS[config])
+    kind = spec.pop("kind")
+    if n is not None:
+        spec["n"] = n
+    spec.update(overrides)
+    if kind == "crowd":
+        return crowd_problem(name=f"crowd-cfg{config}-{spec['n']}", **spec)
+    return porous_problem(seed=seed_for(config), name=f"porous-cfg{config}-{spec['n']}",
+                          **spec)
+
+
+def batched_problems(n_flows: int = 256, sizes=(64, 128, 256, 512),
+                     config: int = 3) -> list:
+    """Independent crowd (even index) and porous (odd index) flows of uneven sizes."""
+    out = []
+    for f in range(n_flows):
+        rng = np.random.default_rng(seed_for(config, f))
+        n = int(rng.choice(sizes))
+        gamma = float(rng.uniform(5e-4, 4e-3))
+        if f % 2 == 0:
+            kf = float(rng.uniform(1.1, 3.0))
+            x0 = (float(rng.uniform(0.6, 0.95)), float(rng.uniform(0.2, 0.8)))
+            p = crowd_problem(n, gamma=gamma, tau=0.02, kappa_factor=kf,
+                              target=x0, n_steps=10, max_iter=200, tol=1e-6,
+                              name=f"batch{f}-crowd-{n}")
+            X, Y = _mesh(n, n, 1.0, 1.0)
+            p.w = p.w + 0.2 * _smooth_field(rng, X, Y).ravel()
+            X2 = _gaussian_mixture(rng, X, Y)
+            p.q0 = (X2 / X2.sum()).ravel()
+            p.kappa = float(kf * p.q0.max())
+        else:
+            p = porous_problem(n, seed=seed_for(config, f), gamma=gamma, tau=5e-3,
+                               n_steps=10, max_iter=200, tol=1e-6,
+                               name=f"batch{f}-porous-{n}")
+        out.append(p)
+    return out
+
+
+def differentiation_problem(n: int = 256, seed: int = 4000):
+    """Potential-recovery workload: (problem with w0, hidden potential w*)."""
+    p = crowd_problem(n, gamma=1e-3, tau=0.02, kappa_factor=1.5, n_steps=10,
+                      max_iter=200, tol=1e-6, name=f"diff-{n}")
+    rng = np.random.default_rng(seed)
+    X, Y = _mesh(n, n, 1.0, 1.0)
+    w_star = p.w + 0.3 * _smooth_field(rng, X, Y).ravel()
+    return p, w_star
