@@ -1,0 +1,163 @@
+/*
+ * jko.h -- C ABI of the GB300 entropic JKO library (libjko.so).
+ *
+ * Computes discrete entropic Wasserstein gradient flows on a uniform 2-D grid
+ * (Peyre 2015, "Entropic Wasserstein Gradient Flows"):
+ *
+ *   one step   p = Prox^{W_gamma}_{tau f}(q) = argmin_{p in Sigma_N} W_gamma(p,q) + tau f(p)
+ *              (Eq. def-jko-operator), solved by the KL-proximal scaling
+ *              iteration of Prop. 3.3, which with u, v identically 1 reads
+ *                  b = q / xi^T a ;  s = xi b ;  p = Prox^{KL}_{sigma f}(s) ;  a = p / s
+ *              with sigma = tau/gamma (Eq. defn-KL-prbm) and the Gibbs kernel
+ *              xi = exp(-|x_i - x_j|^2 / gamma) applied as the separable product
+ *              K_y X K_x^T (Sec. 4.1);
+ *   the flow   p_{t+1} = Prox^{W_gamma}_{tau f}(p_t) (Eq. smooth-jko).
+ *
+ * Energy f (all terms optional, Sec. 4.2 and Sec. 4.4):
+ *   f(p) = iota_{[0,kappa]}(p) + <w,p> + sum_i alpha_i e(p_i) + iota{p_i = 0 on mask}
+ *   e(s) = s (log s - 1)            when m == 1   (Eq. defn-gen-entropies, m = 1)
+ *   e(s) = s^m / (m - 1)            when m >  1   (power form; the paper's e_m equals it
+ *                                                  plus the potential -m alpha/(m-1))
+ *   no entropy term                 when m == 0.
+ * Its pointwise KL proximal map is Prop. 4.1 (congestion + potential),
+ * Eq. prox-entropy (m = 1) and the root of Eq. prox-psi (m > 1), clamped at
+ * kappa, zero on the mask.
+ *
+ * Stopping rule (pseudo-code of Sec. 3.4): after each (odd, even) pair of
+ * half-steps, stop when ||b (.) xi^T a - q||_1 <= tol; at most max_iter pairs.
+ * Each step starts cold (a = b = 1).
+ *
+ * Memory and threading conventions (all entry points):
+ *   - Images are row-major [ny][nx] (index y*nx + x), cell centres (i+1/2)h
+ *     with h = lx/nx, ly/ny.
+ *   - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *     pointers are host memory owned by the caller.  Device images are double
+ *     for JKO_FP64 and float for every other precision.
+ *   - The handle owns every internal buffer; energy fields passed to
+ *     jko_create are copied, so the caller may free them afterwards.
+ *   - Work is enqueued on the handle's stream; jko_step / jko_flow return when
+ *     their results are complete on that stream.
+ *   - A handle may be used by one host thread at a time.  Distinct handles are
+ *     independent.
+ *   - Every entry point returns a jko_status; on an error the handle keeps a
+ *     message readable with jko_last_error.  JKO_ERR_INVALID_ARG leaves all
+ *     outputs untouched.  JKO_NOT_CONVERGED still writes the result.
+ */
+#ifndef JKO_H_
+#define JKO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum jko_status {
+  JKO_OK = 0,
+  JKO_ERR_INVALID_ARG = 1,  /* bad sizes, parameters or input data */
+  JKO_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  JKO_ERR_OOM = 3,          /* device or pinned allocation failed */
+  JKO_ERR_NUMERIC = 4,      /* a NaN or Inf appeared in the iterates */
+  JKO_NOT_CONVERGED = 5,    /* max_iter pairs reached; result still written */
+  JKO_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  JKO_ERR_UNSUPPORTED = 7   /* configuration not supported by this build */
+} jko_status;
+
+/* Arithmetic of the Gibbs-kernel applications (the hot path). */
+typedef enum jko_precision {
+  JKO_FP64 = 0,    /* CUDA cores, double throughout */
+  JKO_FP32 = 1,    /* CUDA cores, float throughout */
+  JKO_TF32 = 2,    /* tensor cores (tcgen05 kind::tf32), fp32 accumulation */
+  JKO_BF16 = 3,    /* tensor cores (tcgen05 kind::f16, bf16 operands), fp32 accumulation */
+  JKO_BF16X3 = 4   /* tensor cores, three bf16 products hi*hi + hi*lo + lo*hi */
+} jko_precision;
+
+/* Uniform grid on [0,lx] x [0,ly] (Sec. 2, numerical grids of Sec. 4). */
+typedef struct jko_grid {
+  int nx, ny;      /* cells along x (contiguous) and y; each >= 1 */
+  double lx, ly;   /* domain lengths; > 0 */
+} jko_grid;
+
+typedef struct jko_params {
+  double gamma;     /* entropic regularisation gamma > 0 (Sec. 2.1) */
+  double tau;       /* JKO step size tau > 0 (Eq. def-jko-operator) */
+  double tol;       /* L1 marginal residual tolerance >= 0 (Sec. 3.4) */
+  int max_iter;     /* maximum (odd, even) pairs per step, >= 1 */
+  int check_every;  /* iterations between host polls of the stop flag (0 = default 16) */
+  int precision;    /* a jko_precision value */
+  int renormalize;  /* 1: divide each output p by its FP64 sum; 0: leave as computed */
+} jko_params;
+
+/* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */
+typedef struct jko_energy {
+  const double* w;            /* potential w (Eq. dfn-congestion); NULL = 0 */
+  double kappa;               /* scalar congestion bound (> 0); +INFINITY = none */
+  const double* kappa_field;  /* per-cell bound (Sec. 4.2 remark); overrides kappa */
+  double m;                   /* 0: no entropy term, 1: entropy, > 1: power m */
+  const double* alpha;        /* per-cell weights of the entropy term (> 0); NULL = 1 */
+  const uint8_t* mask;        /* 1 = obstacle cell (f = +inf), 0 = free; NULL = none */
+} jko_energy;
+
+/* Per-step report. */
+typedef struct jko_step_info {
+  int iters;                 /* (odd, even) pairs performed */
+  int status;                /* JKO_OK, JKO_NOT_CONVERGED or JKO_ERR_NUMERIC */
+  double residual_l1;        /* ||b (.) xi^T a - q||_1 of the returned iterate */
+  double mass;               /* sum of p before any renormalisation (FP64) */
+  double max_p_over_kappa;   /* max_i p_i / kappa_i (0 without congestion) */
+  float ms;                  /* device time of the step in milliseconds */
+} jko_step_info;
+
+typedef struct jko_handle jko_handle;
+
+/* Creates a solver for one grid, one set of step parameters and one energy.
+ * Builds the 1-D Gibbs factors K_x, K_y (Sec. 4.1) and the per-cell energy
+ * constants, allocates the working buffers and captures the iteration graph.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns JKO_ERR_INVALID_ARG on bad sizes or parameters (gamma, tau <= 0,
+ * negative tol, max_iter < 1, kappa <= 0, alpha <= 0, m in (0, 1)),
+ * JKO_ERR_UNSUPPORTED when the precision is not available for this grid,
+ * JKO_ERR_OOM / JKO_ERR_CUDA on allocation or runtime failures.  *out is
+ * NULL on failure. */
+jko_status jko_create(const jko_grid* grid, const jko_params* params,
+                      const jko_energy* energy, void* stream, jko_handle** out);
+
+/* One JKO step p_out = Prox^{W_gamma}_{tau f}(q) (Eq. def-jko-operator).
+ * q_dev, p_out_dev: device images of N elements (double for JKO_FP64, float
+ * otherwise); they may alias.  q must be finite, >= 0, sum to 1 within 1e-3,
+ * vanish on masked cells and satisfy q <= kappa (1 + 1e-3) (Sec. 4.2 asks
+ * kappa >= max p_0), else JKO_ERR_INVALID_ARG.  info may be NULL. */
+jko_status jko_step(jko_handle* h, const void* q_dev, void* p_out_dev, jko_step_info* info);
+
+/* n_steps steps of the flow from p0 (Eq. smooth-jko).  traj_dev (may be NULL)
+ * receives p_1 .. p_n as n_steps consecutive images; p_final_dev (may be NULL)
+ * receives p_n.  infos (may be NULL) receives n_steps reports.  Only p0 is
+ * validated.  Returns the worst status over the steps. */
+jko_status jko_flow(jko_handle* h, const void* p0_dev, int n_steps, void* traj_dev,
+                    void* p_final_dev, jko_step_info* infos);
+
+/* jko_flow on HOST buffers: copies p0 to the device, runs the flow, copies the
+ * requested outputs back; returns once they are in host memory. */
+jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* traj_host,
+                         void* p_final_host, jko_step_info* infos);
+
+/* Re-targets the handle to another stream (a cudaStream_t). */
+jko_status jko_set_stream(jko_handle* h, void* stream);
+
+/* Frees every resource of the handle (NULL is accepted). */
+jko_status jko_destroy(jko_handle* h);
+
+/* Message of the last error on h (never NULL; "" when none). */
+const char* jko_last_error(const jko_handle* h);
+
+/* Static name of a status code. */
+const char* jko_status_string(int status);
+
+/* Library description: precisions compiled in, device, version. */
+const char* jko_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JKO_H_ */

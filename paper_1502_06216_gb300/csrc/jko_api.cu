@@ -1,0 +1,585 @@
+// jko_api.cu -- the C ABI of libjko (include/jko.h): handle set-up, the JKO
+// step driver and the flow.
+//
+// One step (Eq. def-jko-operator) is the scaling loop of Prop. 3.3 in its
+// 2-vector form.  Per (odd, even) pair the device runs four kernels:
+//   pass y of xi a ; pass x of xi a fused with  b = q / xi a  and the residual
+//   of the previous pair (stopping rule of Sec. 3.4) ;
+//   pass y of xi b ; pass x of xi b fused with  p = Prox(s), a = p / s.
+// A chunk of `check_every` pairs is captured once as a CUDA graph.  The host
+// launches chunks and polls a 16-byte slice of the device control block, with
+// one chunk always in flight; kernels launched after the stop return at once.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "jko.h"
+#include "jko_kernels.h"
+#include "tc_gemm.h"
+
+using jko::Ctrl;
+using jko::PassArgs;
+using jko::ProxArgs;
+
+struct jko_handle {
+  jko_grid grid{};
+  jko_params prm{};
+  int N = 0;
+  int prec = JKO_FP32;
+  int ek = jko::EK_CROWD;
+  bool fp64 = false;
+  size_t es = 4;  // element size of device images
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used for graph capture
+
+  // working images (es bytes per element)
+  void *a = nullptr, *b = nullptr, *t1 = nullptr, *p = nullptr, *q = nullptr;
+  void *stage_in = nullptr, *stage_out = nullptr;  // for the host-buffer entry point
+  // Gibbs factors (SIMT taps, centred and zero padded)
+  void *taps_x = nullptr, *taps_y = nullptr;
+  int rx = 0, ry = 0;
+  // per-cell energy constants
+  void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
+  uint8_t* mask = nullptr;
+  double kappa_s = INFINITY;
+  int has_kappa = 0;
+  double m = 0.0;
+
+  Ctrl* ctrl = nullptr;        // device control block
+  Ctrl* ctrl_init = nullptr;   // pinned initial value
+  Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
+  cudaEvent_t ev_poll[2] = {nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  cudaGraphExec_t chunk = nullptr;
+  int chunk_iters = 16;
+  int last_iters = 0;
+
+  jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
+
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+jko_status set_err(jko_handle* h, jko_status st, const std::string& msg) {
+  if (h) h->err = msg; else g_create_err = msg;
+  return st;
+}
+
+jko_status cuda_err(jko_handle* h, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+  return set_err(h, e == cudaErrorMemoryAllocation ? JKO_ERR_OOM : JKO_ERR_CUDA, msg);
+}
+
+#define CK(h, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_err(h, e_, #call); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// 1-D Gibbs factor along one axis (Sec. 4.1): k(d) = exp(-(d h)^2 / gamma),
+// d = 0..n-1.  r = largest d whose tap is non-zero in the working precision, so
+// dropping |d| > r changes nothing in that precision.  Returns the centred,
+// zero-padded tap vector of length 2r + 1 + pad as doubles.
+std::vector<double> gibbs_taps(int n, double length, double gamma, bool fp64, int pad, int* r_out) {
+  const double h = length / n;
+  std::vector<double> k(n);
+  int r = 0;
+  for (int d = 0; d < n; ++d) {
+    k[d] = std::exp(-(d * h) * (d * h) / gamma);
+    const bool nz = fp64 ? (k[d] != 0.0) : ((float)k[d] != 0.0f);
+    if (nz) r = d;
+  }
+  std::vector<double> t(2 * r + 1 + pad, 0.0);
+  for (int i = 0; i <= 2 * r; ++i) t[i] = k[std::abs(i - r)];
+  *r_out = r;
+  return t;
+}
+
+template <typename T>
+cudaError_t upload(void** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * tmp.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+ProxArgs<T> prox_args(const jko_handle* h) {
+  ProxArgs<T> P;
+  P.E = (const T*)h->E;
+  P.sw = (const T*)h->sw;
+  P.c = (const T*)h->c;
+  P.kappa = (const T*)h->kap;
+  P.kappa_s = (T)h->kappa_s;
+  P.mask = h->mask;
+  P.m1 = (T)(h->m - 1.0);
+  P.newton = 40;
+  P.has_kappa = h->has_kappa;
+  return P;
+}
+
+// One (odd, even) pair of the SIMT form on stream st.
+template <typename T>
+cudaError_t enqueue_pair_simt(jko_handle* h, cudaStream_t st) {
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  ProxArgs<T> P = prox_args<T>(h);
+  PassArgs<T> A{};
+  A.ctrl = h->ctrl;
+  cudaError_t e;
+  for (int half = 0; half < 2; ++half) {
+    // pass along y: in [ny][nx] -> t1 [nx][ny]
+    A.in = (const T*)(half == 0 ? h->a : h->b);
+    A.out = (T*)h->t1;
+    A.p = nullptr;
+    A.q = nullptr;
+    A.taps = (const T*)h->taps_y;
+    A.n_i = ny; A.n_j = nx; A.r = h->ry;
+    e = jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
+    if (e != cudaSuccess) return e;
+    // pass along x with the epilogue: in [nx][ny] -> [ny][nx]
+    A.in = (const T*)h->t1;
+    A.out = (T*)(half == 0 ? h->b : h->a);
+    A.p = (T*)h->p;
+    A.q = (const T*)h->q;
+    A.taps = (const T*)h->taps_x;
+    A.n_i = nx; A.n_j = ny; A.r = h->rx;
+    e = jko::simt_pass<T>(half == 0 ? jko::EPI_B : jko::EPI_A, h->ek, A, P, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
+  if (h->tc) return jko::tc_enqueue_pair(h->tc, st);
+  return h->fp64 ? enqueue_pair_simt<double>(h, st) : enqueue_pair_simt<float>(h, st);
+}
+
+jko_status capture_chunk(jko_handle* h) {
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i) e = enqueue_pair(h, h->cap);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_err(h, e, "capture of the iteration chunk"); }
+  CK(h, e2);
+  e = cudaGraphInstantiate(&h->chunk, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, e);
+  return JKO_OK;
+}
+
+void free_handle(jko_handle* h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  if (h->tc) jko::tc_destroy(h->tc);
+  if (h->chunk) cudaGraphExecDestroy(h->chunk);
+  void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
+                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl};
+  for (void* b : bufs) if (b) cudaFree(b);
+  if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
+  if (h->poll) cudaFreeHost(h->poll);
+  for (auto& e : h->ev_poll) if (e) cudaEventDestroy(e);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_energy* en) {
+  if (!g || !p || !en) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL grid, params or energy");
+  if (g->nx < 1 || g->ny < 1) return set_err(nullptr, JKO_ERR_INVALID_ARG, "nx, ny must be >= 1");
+  if ((long long)g->nx * g->ny > (1LL << 30))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "grid larger than 2^30 cells");
+  if (!(g->lx > 0) || !(g->ly > 0) || !std::isfinite(g->lx) || !std::isfinite(g->ly))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "lx, ly must be finite and > 0");
+  if (!(p->gamma > 0) || !std::isfinite(p->gamma))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "gamma must be finite and > 0");
+  if (!(p->tau > 0) || !std::isfinite(p->tau))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "tau must be finite and > 0");
+  if (!(p->tol >= 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "tol must be >= 0");
+  if (p->max_iter < 1) return set_err(nullptr, JKO_ERR_INVALID_ARG, "max_iter must be >= 1");
+  if (p->check_every < 0) return set_err(nullptr, JKO_ERR_INVALID_ARG, "check_every must be >= 0");
+  if (p->precision < JKO_FP64 || p->precision > JKO_BF16X3)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
+  if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
+  if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
+  const long long N = (long long)g->nx * g->ny;
+  for (long long i = 0; i < N; ++i) {
+    if (en->w && !std::isfinite(en->w[i]))
+      return set_err(nullptr, JKO_ERR_INVALID_ARG, "w must be finite");
+    if (en->kappa_field && !(en->kappa_field[i] > 0))
+      return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa_field must be > 0");
+    if (en->alpha && (!(en->alpha[i] > 0) || !std::isfinite(en->alpha[i])))
+      return set_err(nullptr, JKO_ERR_INVALID_ARG, "alpha must be finite and > 0");
+    if (en->mask && en->mask[i] > 1)
+      return set_err(nullptr, JKO_ERR_INVALID_ARG, "mask entries must be 0 or 1");
+  }
+  return JKO_OK;
+}
+
+template <typename T>
+jko_status build_energy(jko_handle* h, const jko_energy* en) {
+  const int N = h->N;
+  const double sigma = h->prm.tau / h->prm.gamma;
+  h->m = en->m;
+  h->ek = en->m == 0.0 ? jko::EK_CROWD : (en->m == 1.0 ? jko::EK_ENTROPY : jko::EK_POWER);
+  std::vector<double> v(N);
+  if (h->ek == jko::EK_CROWD) {
+    for (int i = 0; i < N; ++i) v[i] = std::exp(-sigma * (en->w ? en->w[i] : 0.0));
+    CK(h, upload<T>(&h->E, v));
+  } else {
+    if (en->w) {
+      for (int i = 0; i < N; ++i) v[i] = sigma * en->w[i];
+      CK(h, upload<T>(&h->sw, v));
+    }
+    const double m = en->m;
+    for (int i = 0; i < N; ++i) {
+      const double al = en->alpha ? en->alpha[i] : 1.0;
+      v[i] = (h->ek == jko::EK_ENTROPY) ? sigma * al : sigma * al * m / (m - 1.0);
+    }
+    CK(h, upload<T>(&h->c, v));
+  }
+  h->kappa_s = en->kappa;
+  h->has_kappa = std::isfinite(en->kappa) ? 1 : 0;
+  if (en->kappa_field) {
+    bool any = false;
+    for (int i = 0; i < N; ++i) { v[i] = en->kappa_field[i]; any |= std::isfinite(v[i]); }
+    CK(h, upload<T>(&h->kap, v));
+    h->has_kappa = any ? 1 : 0;
+  }
+  if (en->mask) {
+    CK(h, cudaMalloc((void**)&h->mask, N));
+    CK(h, cudaMemcpy(h->mask, en->mask, N, cudaMemcpyHostToDevice));
+  }
+  return JKO_OK;
+}
+
+template <typename T>
+jko_status setup_simt(jko_handle* h) {
+  const int pad = jko::simt_tap_padding();
+  auto tx = gibbs_taps(h->grid.nx, h->grid.lx, h->prm.gamma, h->fp64, pad, &h->rx);
+  auto ty = gibbs_taps(h->grid.ny, h->grid.ly, h->prm.gamma, h->fp64, pad, &h->ry);
+  CK(h, upload<T>(&h->taps_x, tx));
+  CK(h, upload<T>(&h->taps_y, ty));
+  const size_t smem = sizeof(T) * (size_t)(2 * std::max(h->rx, h->ry) + 1 + pad);
+  if (smem > 200 * 1024)
+    return set_err(h, JKO_ERR_UNSUPPORTED, "kernel radius too large for the shared-memory taps");
+  return JKO_OK;
+}
+
+// ---- one step on device buffers of element type T ----
+template <typename T>
+jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info, bool validate) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  ProxArgs<T> P = prox_args<T>(h);
+  CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  if (validate) {
+    CK(h, jko::launch_validate<T>(q_in, N, P, h->ctrl, st));
+    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const Ctrl& c = h->poll[0];
+    char buf[256];
+    if (c.q_bad) { snprintf(buf, sizeof buf, "q has %llu non-finite entries", c.q_bad); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_neg) { snprintf(buf, sizeof buf, "q has %llu negative entries", c.q_neg); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (std::fabs(c.q_sum - 1.0) > 1e-3) { snprintf(buf, sizeof buf, "q sums to %.9g, not 1", c.q_sum); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_masked) { snprintf(buf, sizeof buf, "q has mass on %llu masked cells", c.q_masked); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_over) { snprintf(buf, sizeof buf, "q exceeds kappa on %llu cells", c.q_over); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  }
+  CK(h, cudaEventRecord(h->ev0, st));
+  if ((const void*)q_in != h->q)
+    CK(h, cudaMemcpyAsync(h->q, q_in, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  if (h->tc) {
+    jko_status s2 = jko::tc_begin_step(h->tc, st) == cudaSuccess ? JKO_OK : JKO_ERR_CUDA;
+    if (s2 != JKO_OK) return set_err(h, s2, "tensor-core step set-up failed");
+  } else {
+    CK(h, jko::launch_fill<T>((T*)h->a, T(1), N, st));   // cold start a = 1 (Sec. 3.4)
+  }
+
+  // chunks: launch the expected number at once, then poll with one in flight
+  const int C = h->chunk_iters;
+  const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
+  int launched = 0, polled = 0;
+  auto launch = [&]() -> cudaError_t {
+    cudaError_t e = cudaGraphLaunch(h->chunk, st);
+    if (e != cudaSuccess) return e;
+    const int slot = launched & 1;
+    e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, 16, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(h->ev_poll[slot], st);
+    ++launched;
+    return e;
+  };
+  int ahead = h->last_iters / C;  // chunks surely needed, from the previous step
+  if (ahead < 1) ahead = 1;
+  if (ahead > max_chunks) ahead = max_chunks;
+  for (int i = 0; i < ahead; ++i) CK(h, launch());
+  bool stopped = false;
+  while (!stopped) {
+    // keep one chunk in flight while waiting for the oldest poll we need
+    if (launched - polled < 2 && launched < max_chunks) CK(h, launch());
+    // wait for the newest-but-one launched chunk's poll (or the newest if only one)
+    const int target = launched - 1 - ((launched - polled) >= 2 ? 1 : 0);
+    const int slot = target & 1;
+    CK(h, cudaEventSynchronize(h->ev_poll[slot]));
+    polled = target + 1;
+    stopped = h->poll[slot].done != jko::RUNNING;
+    if (!stopped && launched >= max_chunks && polled >= launched)
+      return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
+  }
+
+  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, N, P, h->ctrl, st));
+  if (p_out) CK(h, jko::launch_finalize_write<T>((const T*)h->p, p_out, N, h->prm.renormalize, h->ctrl, st));
+  CK(h, cudaEventRecord(h->ev1, st));
+  CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  const Ctrl& c = h->poll[0];
+  jko_status st_out = JKO_OK;
+  if (c.done == jko::NONFINITE || c.nonfinite) st_out = JKO_ERR_NUMERIC;
+  else if (c.done == jko::MAX_ITER) st_out = JKO_NOT_CONVERGED;
+  h->last_iters = c.it;
+  if (info) {
+    info->iters = c.it;
+    info->status = st_out;
+    info->residual_l1 = c.res_last;
+    info->mass = c.mass;
+    unsigned long long bits = c.maxpk_bits;
+    double mx;
+    std::memcpy(&mx, &bits, sizeof mx);
+    info->max_p_over_kappa = h->has_kappa ? mx : 0.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    info->ms = ms;
+  }
+  if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");
+  else if (st_out == JKO_NOT_CONVERGED) set_err(h, st_out, "max_iter reached before tol");
+  return st_out;
+}
+
+int worse(int a, int b) {
+  auto rank = [](int s) { return s == JKO_OK ? 0 : (s == JKO_NOT_CONVERGED ? 1 : 2); };
+  return rank(b) > rank(a) ? b : a;
+}
+
+template <typename T>
+jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_final,
+                     jko_step_info* infos) {
+  const long long N = h->N;
+  const T* q = p0;
+  int worst = JKO_OK;
+  for (int t = 0; t < n_steps; ++t) {
+    T* out = traj ? traj + (size_t)t * N : (T*)h->stage_out;
+    if (!traj && !h->stage_out) {
+      CK(h, cudaMalloc(&h->stage_out, N * sizeof(T)));
+      out = (T*)h->stage_out;
+    }
+    // never write the input of this step in place when q lives in stage_out
+    if (!traj && (const void*)q == (const void*)out) {
+      if (!h->stage_in) CK(h, cudaMalloc(&h->stage_in, N * sizeof(T)));
+      out = (T*)h->stage_in;
+    }
+    jko_step_info info{};
+    jko_status s = step_impl<T>(h, q, out, &info, t == 0);
+    if (s == JKO_ERR_INVALID_ARG || s == JKO_ERR_CUDA || s == JKO_ERR_OOM || s == JKO_ERR_TIMEOUT)
+      return s;
+    if (infos) infos[t] = info;
+    worst = worse(worst, s);
+    q = out;
+  }
+  if (p_final && n_steps > 0)
+    CK(h, cudaMemcpyAsync(p_final, q, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+  if (p_final && n_steps == 0)
+    CK(h, cudaMemcpyAsync(p_final, p0, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return (jko_status)worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_energy* energy,
+                      void* stream, jko_handle** out) {
+  if (!out) return set_err(nullptr, JKO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  jko_status s = validate_create(grid, params, energy);
+  if (s != JKO_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+    return set_err(nullptr, JKO_ERR_CUDA, "no CUDA device available");
+
+  jko_handle* h = new jko_handle();
+  h->grid = *grid;
+  h->prm = *params;
+  h->N = grid->nx * grid->ny;
+  h->prec = params->precision;
+  h->fp64 = params->precision == JKO_FP64;
+  h->es = h->fp64 ? 8 : 4;
+  h->stream = (cudaStream_t)stream;
+  h->chunk_iters = params->check_every > 0 ? params->check_every : 16;
+  cudaGetDevice(&h->device);
+
+  auto fail = [&](jko_status st) {
+    g_create_err = h->err;
+    free_handle(h);
+    return st;
+  };
+  cudaError_t e;
+  const size_t bytes = h->es * (size_t)h->N;
+  void** imgs[] = {&h->a, &h->b, &h->t1, &h->p, &h->q};
+  for (void** pp : imgs) {
+    e = cudaMalloc(pp, bytes);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(image)"));
+    e = cudaMemset(*pp, 0, bytes);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
+  }
+  e = cudaMalloc((void**)&h->ctrl, sizeof(Ctrl));
+  if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(ctrl)"));
+  e = cudaMallocHost((void**)&h->ctrl_init, sizeof(Ctrl));
+  if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMallocHost"));
+  e = cudaMallocHost((void**)&h->poll, 2 * sizeof(Ctrl));
+  if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMallocHost"));
+  std::memset(h->ctrl_init, 0, sizeof(Ctrl));
+  std::memset(h->poll, 0, 2 * sizeof(Ctrl));
+  h->ctrl_init->tol = params->tol;
+  h->ctrl_init->max_iter = params->max_iter;
+  for (auto& ev : h->ev_poll) {
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaEventCreate"));
+  }
+  if ((e = cudaEventCreate(&h->ev0)) != cudaSuccess || (e = cudaEventCreate(&h->ev1)) != cudaSuccess)
+    return fail(cuda_err(h, e, "cudaEventCreate"));
+  e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaStreamCreate"));
+
+  s = h->fp64 ? build_energy<double>(h, energy) : build_energy<float>(h, energy);
+  if (s != JKO_OK) return fail(s);
+  if (h->prec == JKO_FP64 || h->prec == JKO_FP32) {
+    s = h->fp64 ? setup_simt<double>(h) : setup_simt<float>(h);
+  } else {
+    jko::TcConfig cfg{};
+    cfg.nx = grid->nx; cfg.ny = grid->ny; cfg.lx = grid->lx; cfg.ly = grid->ly;
+    cfg.gamma = params->gamma; cfg.precision = h->prec; cfg.ek = h->ek;
+    cfg.a = (float*)h->a; cfg.b = (float*)h->b; cfg.p = (float*)h->p; cfg.q = (const float*)h->q;
+    cfg.ctrl = h->ctrl;
+    cfg.prox = prox_args<float>(h);
+    std::string msg;
+    int rc = jko::tc_create(cfg, &h->tc, &msg);
+    if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, msg);
+    else if (rc != 0) s = set_err(h, JKO_ERR_CUDA, msg);
+  }
+  if (s != JKO_OK) return fail(s);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_err(h, e, "set-up"));
+  s = capture_chunk(h);
+  if (s != JKO_OK) return fail(s);
+  *out = h;
+  return JKO_OK;
+}
+
+jko_status jko_step(jko_handle* h, const void* q_dev, void* p_out_dev, jko_step_info* info) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  if (!q_dev || !p_out_dev) return set_err(h, JKO_ERR_INVALID_ARG, "NULL q or p_out");
+  DeviceGuard dg(h->device);
+  h->err.clear();
+  return h->fp64 ? step_impl<double>(h, (const double*)q_dev, (double*)p_out_dev, info, true)
+                 : step_impl<float>(h, (const float*)q_dev, (float*)p_out_dev, info, true);
+}
+
+jko_status jko_flow(jko_handle* h, const void* p0_dev, int n_steps, void* traj_dev,
+                    void* p_final_dev, jko_step_info* infos) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  if (!p0_dev || n_steps < 0) return set_err(h, JKO_ERR_INVALID_ARG, "NULL p0 or n_steps < 0");
+  DeviceGuard dg(h->device);
+  h->err.clear();
+  return h->fp64 ? flow_impl<double>(h, (const double*)p0_dev, n_steps, (double*)traj_dev,
+                                     (double*)p_final_dev, infos)
+                 : flow_impl<float>(h, (const float*)p0_dev, n_steps, (float*)traj_dev,
+                                    (float*)p_final_dev, infos);
+}
+
+jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* traj_host,
+                         void* p_final_host, jko_step_info* infos) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  if (!p0_host || n_steps < 0) return set_err(h, JKO_ERR_INVALID_ARG, "NULL p0 or n_steps < 0");
+  DeviceGuard dg(h->device);
+  h->err.clear();
+  const size_t bytes = h->es * (size_t)h->N;
+  if (!h->stage_in) CK(h, cudaMalloc(&h->stage_in, bytes));
+  if (!h->stage_out) CK(h, cudaMalloc(&h->stage_out, bytes));
+  cudaStream_t st = h->stream;
+  CK(h, cudaMemcpyAsync(h->stage_in, p0_host, bytes, cudaMemcpyHostToDevice, st));
+  void* cur = h->stage_in;
+  void* nxt = h->stage_out;
+  int worst = JKO_OK;
+  for (int t = 0; t < n_steps; ++t) {
+    jko_step_info info{};
+    jko_status s = h->fp64 ? step_impl<double>(h, (const double*)cur, (double*)nxt, &info, t == 0)
+                           : step_impl<float>(h, (const float*)cur, (float*)nxt, &info, t == 0);
+    if (s == JKO_ERR_INVALID_ARG || s == JKO_ERR_CUDA || s == JKO_ERR_OOM || s == JKO_ERR_TIMEOUT)
+      return s;
+    if (infos) infos[t] = info;
+    worst = worse(worst, s);
+    if (traj_host)
+      CK(h, cudaMemcpyAsync((char*)traj_host + (size_t)t * bytes, nxt, bytes,
+                            cudaMemcpyDeviceToHost, st));
+    std::swap(cur, nxt);
+  }
+  if (p_final_host) CK(h, cudaMemcpyAsync(p_final_host, cur, bytes, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  return (jko_status)worst;
+}
+
+jko_status jko_set_stream(jko_handle* h, void* stream) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  h->stream = (cudaStream_t)stream;
+  return JKO_OK;
+}
+
+jko_status jko_destroy(jko_handle* h) {
+  free_handle(h);
+  return JKO_OK;
+}
+
+const char* jko_last_error(const jko_handle* h) {
+  return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+const char* jko_status_string(int s) {
+  switch (s) {
+    case JKO_OK: return "JKO_OK";
+    case JKO_ERR_INVALID_ARG: return "JKO_ERR_INVALID_ARG";
+    case JKO_ERR_CUDA: return "JKO_ERR_CUDA";
+    case JKO_ERR_OOM: return "JKO_ERR_OOM";
+    case JKO_ERR_NUMERIC: return "JKO_ERR_NUMERIC";
+    case JKO_NOT_CONVERGED: return "JKO_NOT_CONVERGED";
+    case JKO_ERR_TIMEOUT: return "JKO_ERR_TIMEOUT";
+    case JKO_ERR_UNSUPPORTED: return "JKO_ERR_UNSUPPORTED";
+    default: return "unknown jko_status";
+  }
+}
+
+const char* jko_build_info(void) {
+  return "libjko: sm_103a; precisions FP64 FP32 (CUDA cores), TF32 BF16 BF16X3 (tcgen05)";
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// jko_internal.cuh -- device-side shared pieces of the JKO path: the control
+// block that carries the stopping decision between kernels, reductions, and
+// the pointwise KL proximal maps evaluated in ratio form a = Prox(s)/s.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jko {
+
+// Stop states written into Ctrl::done.
+enum : int { RUNNING = 0, CONVERGED = 1, MAX_ITER = 2, NONFINITE = 3 };
+
+// Control block in device memory, one per handle.  Kernels of the scaling loop
+// read `done` when they start and return at once when it is set, so a fixed
+// chunk of launched iterations becomes a no-op after the stop.  Decisions are
+// taken by the last block of a kernel to finish (atomic arrival counter), so no
+// kernel ever waits on another block.
+struct Ctrl {
+  int it;                 // (odd, even) pairs completed in this step
+  int done;               // RUNNING / CONVERGED / MAX_ITER / NONFINITE
+  int nonfinite;          // set when an epilogue meets NaN or Inf
+  int max_iter;           // copy of the step budget
+  unsigned int arrive_b;  // arrival counter of the b-update kernel
+  unsigned int arrive_a;  // arrival counter of the prox / a-update kernel
+  unsigned int arrive_f;  // arrival counter of the finalisation kernel
+  unsigned int arrive_v;  // arrival counter of the validation kernel
+  double tol;             // L1 residual tolerance
+  double res_acc;         // residual accumulator of the running pass
+  double res_last;        // residual of the last completed pair
+  double mass;            // sum p (finalisation)
+  unsigned long long maxpk_bits;  // max p/kappa as ordered bits (p >= 0)
+  // validation of the step input q
+  double q_sum;
+  unsigned long long q_neg;       // count of q < 0
+  unsigned long long q_bad;       // count of non-finite q
+  unsigned long long q_over;      // count of q > kappa (1 + 1e-3)
+  unsigned long long q_masked;    // count of q != 0 on the mask
+};
+
+// Energy kinds of the proximal epilogue (compile-time).
+enum : int { EK_CROWD = 0, EK_ENTROPY = 1, EK_POWER = 2 };
+
+// Per-cell energy constants, precomputed at create time in working precision T.
+template <typename T>
+struct ProxArgs {
+  const T* E;          // e^{-sigma w} (crowd) ; unused otherwise
+  const T* sw;         // sigma * w (entropy, power), may be NULL (= 0)
+  const T* c;          // entropy: sigma*alpha ; power: beta = sigma*alpha*m/(m-1)
+  const T* kappa;      // per-cell kappa, or NULL
+  T kappa_s;           // scalar kappa (+inf = none), used when kappa == NULL
+  const uint8_t* mask; // 1 = obstacle, or NULL
+  T m1;                // m - 1 (power)
+  int newton;          // Newton steps (power)
+  int has_kappa;       // 1 if any congestion bound is finite
+};
+
+template <typename T> __device__ __forceinline__ T dev_exp(T x);
+template <> __device__ __forceinline__ float dev_exp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dev_exp<double>(double x) { return exp(x); }
+template <typename T> __device__ __forceinline__ T dev_log(T x);
+template <> __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double dev_log<double>(double x) { return log(x); }
+
+template <typename T> __device__ __forceinline__ bool dev_finite(T x) { return isfinite(x); }
+
+// Newton stopping threshold on the step |dy| relative to 1 + |y|.
+template <typename T> struct NewtonEps;
+template <> struct NewtonEps<float> { static constexpr float v = 1e-7f; };
+template <> struct NewtonEps<double> { static constexpr double v = 1e-15; };
+
+// a = Prox_{sigma f}(s) / s for one cell, extended continuously at s = 0
+// (Prop. 4.1, Eq. prox-entropy, Eq. prox-psi with the shift rule
+// Eq. prox-calculus-shift; clamp at kappa; 0 on the mask).
+template <typename T, int EK>
+__device__ __forceinline__ T prox_ratio(const ProxArgs<T>& P, int idx, T s) {
+  if (P.mask != nullptr && P.mask[idx]) return T(0);
+  T a;
+  if (EK == EK_CROWD) {
+    a = P.E[idx];
+  } else if (EK == EK_ENTROPY) {
+    // psi = (s e^{-sigma w})^{1/(1+sigma alpha)} ; a = psi / s
+    if (!(s > T(0))) return T(0);
+    const T c = P.c[idx];
+    const T sw = P.sw ? P.sw[idx] : T(0);
+    a = dev_exp<T>(-(c * dev_log<T>(s) + sw) / (T(1) + c));
+  } else {
+    // y = log psi solves y + beta e^{(m-1) y} = l, l = log s - sigma w.
+    // g is increasing and convex, so Newton from y0 = l (g(l) >= 0) decreases
+    // monotonically to the root without overshoot.
+    const T sw = P.sw ? P.sw[idx] : T(0);
+    if (!(s > T(0))) {
+      a = dev_exp<T>(-sw);  // limit of psi/s as s -> 0
+    } else {
+      const T ls = dev_log<T>(s);
+      const T l = ls - sw;
+      const T beta = P.c[idx];
+      T y = l;
+      for (int k = 0; k < P.newton; ++k) {
+        const T e = beta * dev_exp<T>(P.m1 * y);
+        const T dy = (y + e - l) / (T(1) + P.m1 * e);
+        y -= dy;
+        if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
+      }
+      a = dev_exp<T>(y - ls);
+    }
+  }
+  if (P.has_kappa && s > T(0)) {
+    const T kap = P.kappa ? P.kappa[idx] : P.kappa_s;
+    const T lim = kap / s;
+    a = a < lim ? a : lim;
+  }
+  return a;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_or(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum over a 1-, 2- or 3-D block (linear thread order, whole warps);
+// every thread gets the total.  `scratch` has >= 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, wid = tid >> 5;
+  const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (wid == 0) {
+    t = lane < nw ? scratch[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) scratch[32] = t;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+}  // namespace jko

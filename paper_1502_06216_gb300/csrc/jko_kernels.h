@@ -1,0 +1,52 @@
+// jko_kernels.h -- host-side launch interface of the JKO kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jko_internal.cuh"
+
+namespace jko {
+
+// Epilogue kinds of a filter pass.
+enum : int { EPI_STORE = 0, EPI_B = 1, EPI_A = 2 };
+
+// One separable filter pass: out[j][i'] = sum_i k(|i'-i|) in[i][j] followed by
+// the epilogue.  in is [n_i][n_j]; out (and p, q) are [n_j][n_i].
+template <typename T>
+struct PassArgs {
+  const T* in;
+  T* out;        // EPI_STORE: filtered image; EPI_B: b (read old, write new); EPI_A: a
+  T* p;          // EPI_A: p = a s
+  const T* q;    // EPI_B: target marginal q
+  const T* taps; // k(d) for d = -r..r, then simt_tap_padding() zeros
+  int n_i, n_j, r;
+  Ctrl* ctrl;
+};
+
+int simt_tap_padding();
+
+template <typename T>
+cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,
+                      cudaStream_t st);
+
+// Step prologue / epilogue kernels (jko_step_kernels.cu).
+template <typename T>
+cudaError_t launch_fill(T* x, T v, long long n, cudaStream_t st);
+
+// Counts invalid entries of q into ctrl (q_sum, q_neg, q_bad, q_over, q_masked).
+template <typename T>
+cudaError_t launch_validate(const T* q, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
+                            cudaStream_t st);
+
+// ctrl->mass = sum p, ctrl->maxpk_bits = max p/kappa, flags non-finite p.
+template <typename T>
+cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
+                                   cudaStream_t st);
+
+// out = renorm ? p / ctrl->mass : p   (out may alias p)
+template <typename T>
+cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
+                                  cudaStream_t st);
+
+}  // namespace jko

@@ -1,0 +1,145 @@
+// jko_step_kernels.cu -- per-step prologue and epilogue kernels: fill, input
+// validation, and the FP64 mass / congestion statistics with the optional
+// mass renormalisation of the step output.
+#include "jko_kernels.h"
+
+namespace jko {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T>
+__global__ void fill_kernel(T* x, T v, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T kappa_at(const ProxArgs<T>& P, long long i) {
+  return P.kappa ? P.kappa[i] : P.kappa_s;
+}
+
+template <typename T>
+__global__ void validate_kernel(const T* q, long long n, ProxArgs<T> P, Ctrl* ctrl) {
+  __shared__ double s_red[33];
+  double sum = 0.0;
+  unsigned long long neg = 0, bad = 0, over = 0, msk = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = q[i];
+    if (!isfinite(v)) { ++bad; continue; }
+    sum += (double)v;
+    if (v < T(0)) ++neg;
+    if (P.has_kappa && (double)v > (double)kappa_at(P, i) * (1.0 + 1e-3)) ++over;
+    if (P.mask && P.mask[i] && v != T(0)) ++msk;
+  }
+  sum = block_sum(sum, s_red);
+  neg = warp_sum_u64(neg);
+  bad = warp_sum_u64(bad);
+  over = warp_sum_u64(over);
+  msk = warp_sum_u64(msk);
+  if ((threadIdx.x & 31) == 0) {
+    if (neg) atomicAdd(&ctrl->q_neg, neg);
+    if (bad) atomicAdd(&ctrl->q_bad, bad);
+    if (over) atomicAdd(&ctrl->q_over, over);
+    if (msk) atomicAdd(&ctrl->q_masked, msk);
+  }
+  if (threadIdx.x == 0) atomicAdd(&ctrl->q_sum, sum);
+}
+
+template <typename T>
+__global__ void finalize_reduce_kernel(const T* p, long long n, ProxArgs<T> P, Ctrl* ctrl) {
+  __shared__ double s_red[33];
+  double sum = 0.0;
+  double mx = 0.0;
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = p[i];
+    bad |= !isfinite(v);
+    sum += (double)v;
+    if (P.has_kappa) {
+      const double r = (double)v / (double)kappa_at(P, i);
+      mx = r > mx ? r : mx;
+    }
+  }
+  sum = block_sum(sum, s_red);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  bad = warp_or(bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (mx > 0.0) atomicMax(&ctrl->maxpk_bits, (unsigned long long)__double_as_longlong(mx));
+    if (bad) atomicOr(&ctrl->nonfinite, 1);
+  }
+  if (threadIdx.x == 0) atomicAdd(&ctrl->mass, sum);
+}
+
+template <typename T>
+__global__ void finalize_write_kernel(const T* p, T* out, long long n, int renorm,
+                                      const Ctrl* ctrl) {
+  const double mass = ctrl->mass;
+  const bool scale = renorm && mass > 0.0 && isfinite(mass);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v = p[i];
+    out[i] = scale ? (T)((double)v / mass) : v;
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + NT - 1) / NT;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fill(T* x, T v, long long n, cudaStream_t st) {
+  fill_kernel<T><<<grid_for(n), NT, 0, st>>>(x, v, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_validate(const T* q, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
+                            cudaStream_t st) {
+  validate_kernel<T><<<grid_for(n), NT, 0, st>>>(q, n, P, ctrl);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
+                                   cudaStream_t st) {
+  finalize_reduce_kernel<T><<<grid_for(n), NT, 0, st>>>(p, n, P, ctrl);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
+                                  cudaStream_t st) {
+  finalize_write_kernel<T><<<grid_for(n), NT, 0, st>>>(p, out, n, renorm, ctrl);
+  return cudaGetLastError();
+}
+
+#define JKO_INST(T)                                                                     \
+  template cudaError_t launch_fill<T>(T*, T, long long, cudaStream_t);                  \
+  template cudaError_t launch_validate<T>(const T*, long long, const ProxArgs<T>&, Ctrl*, \
+                                          cudaStream_t);                                \
+  template cudaError_t launch_finalize_reduce<T>(const T*, long long, const ProxArgs<T>&, \
+                                                 Ctrl*, cudaStream_t);                  \
+  template cudaError_t launch_finalize_write<T>(const T*, T*, long long, int, const Ctrl*, \
+                                                cudaStream_t);
+JKO_INST(float)
+JKO_INST(double)
+#undef JKO_INST
+
+}  // namespace jko

@@ -1,0 +1,199 @@
+// simt_filter.cu -- plain CUDA-core (FP32 / FP64) form of the Gibbs-kernel
+// application and the fused scaling / proximal epilogues.
+//
+// xi = e^{-|x-y|^2/gamma} on a uniform grid is separable (Sec. 4.1):
+// xi X = K_y X K_x^T.  One "pass" filters an image along its strided axis and
+// writes the result transposed:
+//     out[j][i'] = sum_i k(|i' - i|) in[i][j],   in: [n_i][n_j], out: [n_j][n_i]
+// Two passes (y then x) give xi X back in the original [ny][nx] layout.  The
+// second pass of each half-iteration carries the elementwise work:
+//   EPI_B  b-update + residual (Eq. update-formula-1 and the stopping rule of
+//          Sec. 3.4):  r += |b_old Y - q| ;  b = q / Y  (0 where q = 0)
+//   EPI_A  KL prox + a-update (Eq. update-formula-2, Eq. defn-pell):
+//          a = Prox_{sigma f}(s)/s ;  p = a s
+//
+// Thread layout: a warp spans 32 consecutive j (coalesced loads of in[i][j]);
+// each thread computes RB consecutive outputs i' with a register window that
+// slides along i, so each input load feeds RB multiply-adds.  The taps are
+// the 2r+1 values k(d), d = -r..r, held in shared memory (broadcast reads).
+#include "jko_internal.cuh"
+#include "jko_kernels.h"
+
+namespace jko {
+
+namespace {
+
+constexpr int RB = 16;   // outputs per thread along the filtered axis
+constexpr int BJ = 32;   // threads along the contiguous axis
+constexpr int BI = 4;    // thread rows per block
+
+template <typename T, int EPI, int EK>
+__global__ void __launch_bounds__(BJ * BI)
+filter_pass(PassArgs<T> A, ProxArgs<T> P) {
+  Ctrl* ctrl = A.ctrl;
+  if (ctrl->done) return;  // uniform over the grid: set only between launches
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_k = reinterpret_cast<T*>(smem_raw);
+  __shared__ double s_red[33];
+  const int tid = threadIdx.y * BJ + threadIdx.x;
+  const int ntap = 2 * A.r + 1 + RB;  // taps are zero-padded by RB entries
+  for (int t = tid; t < ntap; t += BJ * BI) s_k[t] = A.taps[t];
+  __syncthreads();
+
+  const int j = blockIdx.x * BJ + threadIdx.x;
+  const int i0 = (blockIdx.y * BI + threadIdx.y) * RB;
+  const bool active = (j < A.n_j) && (i0 < A.n_i);
+
+  T acc[RB];
+#pragma unroll
+  for (int o = 0; o < RB; ++o) acc[o] = T(0);
+
+  if (active) {
+    // acc[o] = sum_{t=0}^{2r} k[t] in[i0 + o + t - r][j]; rows outside [0, n_i) are 0.
+    const int r = A.r;
+    const int n_i = A.n_i;
+    int t_lo = r - i0 - (RB - 1);
+    if (t_lo < 0) t_lo = 0;
+    int t_hi = n_i - 1 - i0 + r;
+    if (t_hi > 2 * r) t_hi = 2 * r;
+    const T* col = A.in + j;
+    const size_t ld = (size_t)A.n_j;
+    T win[2 * RB];
+    int base = i0 - r + t_lo;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int ii = base + u;
+      win[u] = (ii >= 0 && ii < n_i) ? __ldg(col + (size_t)ii * ld) : T(0);
+    }
+    for (int t0 = t_lo; t0 <= t_hi; t0 += RB) {
+      base = i0 - r + t0;
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int ii = base + RB + u;
+        win[RB + u] = (ii >= 0 && ii < n_i) ? __ldg(col + (size_t)ii * ld) : T(0);
+      }
+#pragma unroll
+      for (int dd = 0; dd < RB; ++dd) {
+        const T k = s_k[t0 + dd];
+#pragma unroll
+        for (int o = 0; o < RB; ++o) acc[o] = fma(k, win[o + dd], acc[o]);
+      }
+#pragma unroll
+      for (int u = 0; u < RB; ++u) win[u] = win[RB + u];
+    }
+  }
+
+  // ---- epilogue: out is [n_j][n_i], this thread owns out[j][i0 .. i0+RB) ----
+  double res = 0.0;
+  int bad = 0;
+  if (active) {
+    const size_t rowoff = (size_t)j * A.n_i;
+    const int nout = (A.n_i - i0) < RB ? (A.n_i - i0) : RB;
+    if (EPI == EPI_STORE) {
+#pragma unroll
+      for (int o = 0; o < RB; ++o)
+        if (o < nout) A.out[rowoff + i0 + o] = acc[o];
+    } else if (EPI == EPI_B) {
+      const bool have_prev = ctrl->it > 0;
+#pragma unroll
+      for (int o = 0; o < RB; ++o) {
+        if (o < nout) {
+          const size_t idx = rowoff + i0 + o;
+          const T Y = acc[o];
+          const T qv = A.q[idx];
+          if (have_prev) res += fabs((double)A.out[idx] * (double)Y - (double)qv);
+          const T bn = (qv == T(0)) ? T(0) : qv / Y;
+          bad |= !dev_finite(bn);
+          A.out[idx] = bn;
+        }
+      }
+    } else {  // EPI_A
+#pragma unroll
+      for (int o = 0; o < RB; ++o) {
+        if (o < nout) {
+          const size_t idx = rowoff + i0 + o;
+          const T s = acc[o];
+          const T a = prox_ratio<T, EK>(P, (int)idx, s);
+          bad |= !dev_finite(a);
+          A.out[idx] = a;
+          A.p[idx] = a * s;
+        }
+      }
+    }
+  }
+  if (EPI == EPI_STORE) return;
+
+  // ---- reductions and the last-block decision ----
+  bad = warp_or(bad);
+  if (EPI == EPI_B) res = block_sum(res, s_red);
+  __shared__ int s_bad;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    if (EPI == EPI_B && res != 0.0) atomicAdd(&ctrl->res_acc, res);
+    if (s_bad) atomicOr(&ctrl->nonfinite, 1);
+    __threadfence();
+    unsigned* counter = (EPI == EPI_B) ? &ctrl->arrive_b : &ctrl->arrive_a;
+    const unsigned prev = atomicAdd(counter, 1u);
+    if (prev == nblocks - 1) {  // last block of this launch
+      __threadfence();
+      const int nonf = atomicOr(&ctrl->nonfinite, 0);
+      const int it = ctrl->it;
+      if (EPI == EPI_B) {
+        const double total = atomicAdd(&ctrl->res_acc, 0.0);
+        if (it > 0) ctrl->res_last = total;
+        if (nonf || (it > 0 && !isfinite(total))) ctrl->done = NONFINITE;
+        else if (it > 0 && total <= ctrl->tol) ctrl->done = CONVERGED;
+        else if (it >= ctrl->max_iter) ctrl->done = MAX_ITER;
+        ctrl->res_acc = 0.0;
+      } else {
+        ctrl->it = it + 1;
+        if (nonf) ctrl->done = NONFINITE;
+      }
+      *counter = 0u;
+      __threadfence();
+    }
+  }
+}
+
+template <typename T, int EPI, int EK>
+cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
+  const size_t smem = sizeof(T) * (size_t)(2 * A.r + 1 + RB);
+  auto kern = filter_pass<T, EPI, EK>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 block(BJ, BI);
+  dim3 grid((A.n_j + BJ - 1) / BJ, (A.n_i + BI * RB - 1) / (BI * RB));
+  kern<<<grid, block, smem, st>>>(A, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int simt_tap_padding() { return RB; }
+
+template <typename T>
+cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,
+                      cudaStream_t st) {
+  if (epi == EPI_STORE) return launch_one<T, EPI_STORE, EK_CROWD>(A, P, st);
+  if (epi == EPI_B) return launch_one<T, EPI_B, EK_CROWD>(A, P, st);
+  switch (ek) {
+    case EK_CROWD: return launch_one<T, EPI_A, EK_CROWD>(A, P, st);
+    case EK_ENTROPY: return launch_one<T, EPI_A, EK_ENTROPY>(A, P, st);
+    default: return launch_one<T, EPI_A, EK_POWER>(A, P, st);
+  }
+}
+
+template cudaError_t simt_pass<float>(int, int, const PassArgs<float>&, const ProxArgs<float>&,
+                                      cudaStream_t);
+template cudaError_t simt_pass<double>(int, int, const PassArgs<double>&,
+                                       const ProxArgs<double>&, cudaStream_t);
+
+}  // namespace jko

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libjko (include/jko.h), same names as the C ABI.
+
+Argument marshalling only: every step of the JKO path runs in the CUDA
+library.  PyTorch provides device memory and streams; energy fields are
+passed as host float64 arrays and copied by ``jko_create``.  If libjko.so has
+not been built the binding raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libjko.so")
+
+
+class Precision(enum.IntEnum):
+    FP64 = 0
+    FP32 = 1
+    TF32 = 2
+    BF16 = 3
+    BF16X3 = 4
+
+
+class Status(enum.IntEnum):
+    OK = 0
+    INVALID_ARG = 1
+    CUDA = 2
+    OOM = 3
+    NUMERIC = 4
+    NOT_CONVERGED = 5
+    TIMEOUT = 6
+    UNSUPPORTED = 7
+
+
+class JKOError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{Status(status).name}: {message}")
+        self.status = Status(status)
+        self.message = message
+
+
+class jko_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
+
+
+class jko_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("tau", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("precision", ctypes.c_int), ("renormalize", ctypes.c_int)]
+
+
+class jko_energy(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("kappa", ctypes.c_double),
+                ("kappa_field", ctypes.c_void_p), ("m", ctypes.c_double),
+                ("alpha", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+class jko_step_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
+                ("max_p_over_kappa", ctypes.c_double), ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = {
+    "jko_create": (ctypes.c_int, [ctypes.POINTER(jko_grid), ctypes.POINTER(jko_params),
+                                  ctypes.POINTER(jko_energy), ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "jko_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.POINTER(jko_step_info)]),
+    "jko_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.POINTER(jko_step_info)]),
+    "jko_flow_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(jko_step_info)]),
+    "jko_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "jko_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "jko_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "jko_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "jko_build_info": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libjko.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, handle=None) -> int:
+    if status in (Status.OK, Status.NOT_CONVERGED, Status.NUMERIC):
+        return status
+    msg = lib().jko_last_error(handle).decode(errors="replace")
+    raise JKOError(status, msg)
+
+
+def _host_f64(x, N) -> Optional[np.ndarray]:
+    if x is None:
+        return None
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), (N,)))
+    return a
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Handle:
+    """Owns a jko_handle*; keeps the parameters used to create it."""
+
+    def __init__(self, ptr: ctypes.c_void_p, nx: int, ny: int, precision: Precision):
+        self.ptr = ptr
+        self.nx, self.ny = nx, ny
+        self.N = nx * ny
+        self.precision = Precision(precision)
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == Precision.FP64 else torch.float32
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.precision == Precision.FP64 else np.float32
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                jko_destroy(self)
+        except Exception:
+            pass
+
+
+def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, ly: float = 1.0,
+               tol: float = 1e-6, max_iter: int = 200, check_every: int = 0,
+               precision: int = Precision.FP32, renormalize: bool = True,
+               w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
+               alpha=None, mask=None, stream=None) -> Handle:
+    """jko_create: grid, step parameters and energy (host arrays, copied)."""
+    N = nx * ny
+    g = jko_grid(nx, ny, lx, ly)
+    p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)))
+    keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N)]
+    mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
+    e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
+                   keep[1].ctypes.data if keep[1] is not None else None, float(m),
+                   keep[2].ctypes.data if keep[2] is not None else None,
+                   mk.ctypes.data if mk is not None else None)
+    out = ctypes.c_void_p()
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    _check(lib().jko_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), st,
+                            ctypes.byref(out)))
+    return Handle(out, nx, ny, precision)
+
+
+def _dev_image(h: Handle, t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != h.dtype or not t.is_contiguous() or t.numel() < h.N:
+        raise TypeError(f"{name} must be a contiguous {h.dtype} tensor of {h.N} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def jko_step(h: Handle, q, p_out=None):
+    """One JKO step on device tensors; returns (p_out, info dict)."""
+    import torch
+    if p_out is None:
+        p_out = torch.empty(h.N, dtype=h.dtype, device=q.device)
+    info = jko_step_info()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_step(h.ptr, _dev_image(h, q, "q"), _dev_image(h, p_out, "p_out"),
+                      ctypes.byref(info)), h.ptr)
+    return p_out, info.as_dict()
+
+
+def jko_flow(h: Handle, p0, n_steps: int, traj=None, p_final=None, want_traj: bool = True):
+    """n_steps of the flow on device tensors; returns (p_final, traj, infos)."""
+    import torch
+    if traj is None and want_traj and n_steps > 0:
+        traj = torch.empty((n_steps, h.N), dtype=h.dtype, device=p0.device)
+    if p_final is None:
+        p_final = torch.empty(h.N, dtype=h.dtype, device=p0.device)
+    infos = (jko_step_info * max(n_steps, 1))()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    tptr = _dev_image(h, traj.reshape(-1), "traj") if traj is not None else None
+    _check(L.jko_flow(h.ptr, _dev_image(h, p0, "p0"), n_steps, tptr,
+                      _dev_image(h, p_final, "p_final"), infos), h.ptr)
+    return p_final, traj, [infos[i].as_dict() for i in range(n_steps)]
+
+
+def jko_flow_host(h: Handle, p0_host, n_steps: int, traj_host=None, p_final_host=None):
+    """The flow on host buffers (numpy arrays or pinned CPU tensors)."""
+    def ptr(x):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            if x.dtype != h.np_dtype or not x.flags.c_contiguous:
+                raise TypeError(f"host buffer must be a contiguous {h.np_dtype} array")
+            return ctypes.c_void_p(x.ctypes.data)
+        return ctypes.c_void_p(x.data_ptr())
+    infos = (jko_step_info * max(n_steps, 1))()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_flow_host(h.ptr, ptr(p0_host), n_steps, ptr(traj_host), ptr(p_final_host),
+                           infos), h.ptr)
+    return [infos[i].as_dict() for i in range(n_steps)]
+
+
+def jko_destroy(h: Handle) -> None:
+    if h.ptr:
+        lib().jko_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+
+
+def jko_last_error(h: Optional[Handle] = None) -> str:
+    return lib().jko_last_error(h.ptr if h else None).decode(errors="replace")
+
+
+def jko_build_info() -> str:
+    return lib().jko_build_info().decode()
+
+
+def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
+                        max_iter: Optional[int] = None, check_every: int = 0,
+                        renormalize: bool = True, stream=None) -> Handle:
+    """jko_create from an ``inputs.Problem``."""
+    return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
+                      tol=pb.tol if tol is None else tol,
+                      max_iter=pb.max_iter if max_iter is None else max_iter,
+                      check_every=check_every, precision=precision, renormalize=renormalize,
+                      w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
+                      stream=stream)

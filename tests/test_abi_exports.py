@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/jko.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(jko_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libjko():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no CUDA toolkit to build libjko")
+    from paper_1502_06216_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_every_declared_symbol_is_exported(libjko):
+    names = declared_symbols()
+    assert {"jko_create", "jko_step", "jko_flow", "jko_destroy"} <= names
+    for n in sorted(names):
+        assert hasattr(libjko, n), n
+
+
+def test_binding_covers_header():
+    from paper_1502_06216_gb300 import jko
+    assert declared_symbols() <= set(jko.EXPORTS)
+
+
+def test_info_and_status_strings(libjko):
+    libjko.jko_status_string.restype = ctypes.c_char_p
+    libjko.jko_build_info.restype = ctypes.c_char_p
+    assert libjko.jko_status_string(0) == b"JKO_OK"
+    assert libjko.jko_status_string(5) == b"JKO_NOT_CONVERGED"
+    assert b"sm_103a" in libjko.jko_build_info()
+
+
+def test_create_rejects_bad_arguments_on_host(libjko):
+    """Argument checks happen before any device call."""
+    from paper_1502_06216_gb300 import jko
+    with pytest.raises(jko.JKOError) as e:
+        jko.jko_create(8, 8, gamma=-1.0, tau=0.1, stream=0)
+    assert e.value.status == jko.Status.INVALID_ARG
+    with pytest.raises(jko.JKOError):
+        jko.jko_create(0, 8, gamma=1e-2, tau=0.1, stream=0)
+    with pytest.raises(jko.JKOError):
+        jko.jko_create(8, 8, gamma=1e-2, tau=0.1, m=0.5, stream=0)
