@@ -1,0 +1,384 @@
+"""Benchmark of the entropic JKO hot path on one GB300 (or N independent replicas).
+
+Workload: crowd motion on a 1024 x 1024 grid of [0,1]^2, c = |x-y|^2,
+gamma = 2e-4, tau = 0.02, f = iota_{p <= kappa} + <w,p>, kappa = 1.2 max q0,
+w = |x - (0.9, 0.5)|^2, q0 = uniform disk of radius 0.2 at (0.25, 0.5); each
+JKO step runs the KL-proximal scaling loop for at most 200 pairs at L1
+tolerance 1e-6 (synthetic, seeded).  One bench "step" is one JKO step of that
+flow; the W warm-up steps advance the flow (congestion is active from step 5
+on), the K timed steps continue it.
+
+Metric: KL-prox iterations per second (one iteration = one (odd, even) pair:
+xi^T a, b-update, xi b, prox and a-update), whole job; JKO steps/s reported
+beside it.  Inputs (4 MB per image) are smaller than L2, so L2 is flushed by
+writing a 256 MB buffer between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision FP32|BF16|BF16X3|TF32|FP64] [--n 1024]
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on bounded samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "KL-prox iters/s at 1024^2 crowd motion (gamma=2e-4), JKO steps/s beside"
+UNIT = "iters/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def _peak_value(peaks, *keys):
+    for k in keys:
+        v = peaks.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("value", "gbs", "tflops"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n):
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.config_problem(2, n=n)
+    return pb
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on bounded samples of the same workload
+# ----------------------------------------------------------------------------------------
+
+def oracle_iteration_rate(pb, q, n_iter_max=None, budget_s=10.0):
+    """Times the oracle's scaling loop (2-vector form, FP64, separable xi) on a
+    bounded number of iterations of one step from q; returns (iters/s, iters, s)."""
+    from oracle import gibbs, jko as ojko
+    from oracle.energy import Energy
+    xi = gibbs.SeparableXi(pb.nx, pb.ny, pb.gamma, pb.lx, pb.ly)
+    en = Energy.from_problem(pb)
+    sigma = pb.tau / pb.gamma
+    t0 = time.perf_counter()
+    ojko.step(q, xi, sigma, en, tol=0.0, max_iter=1)
+    t1 = time.perf_counter()
+    per = max(t1 - t0, 1e-6)
+    k = max(1, int(budget_s / per))
+    if n_iter_max is not None:
+        k = min(k, n_iter_max)
+    t0 = time.perf_counter()
+    ojko.step(q, xi, sigma, en, tol=0.0, max_iter=k)
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    pb = workload(args.n)
+    q = pb.q0.copy()
+    # each bench step: a bounded sample of oracle iterations of one JKO step
+    per_step_budget = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_iteration_rate(pb, q, n_iter_max=2, budget_s=per_step_budget)
+    iters, secs = 0, 0.0
+    for _ in range(args.steps):
+        _, k, dt = oracle_iteration_rate(pb, q, budget_s=per_step_budget)
+        iters += k
+        secs += dt
+    value = iters / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"crowd motion {args.n}x{args.n}, gamma=2e-4, tau=0.02, "
+                               "kappa=1.2 max q0, <=200 pairs/step",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                         "sample": f"{iters} FP64 scaling-loop iterations over {args.steps} "
+                                   f"samples of one {args.n}^2 JKO step (NumPy/BLAS, separable xi)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1502_06216_gb300 import jko
+
+    prec = jko.Precision[args.precision]
+    pb = workload(args.n)
+    h = jko.create_from_problem(pb, precision=prec)
+    N = pb.N
+    dt = h.dtype
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up: advance the flow W steps from q0
+    q = torch.tensor(pb.q0, dtype=dt, device=dev)
+    p = torch.empty_like(q)
+    for _ in range(args.warmup):
+        jko.jko_step(h, q, p)
+        q, p = p, q
+    q_start = q.clone()
+
+    # timed region: K steps, per-step CUDA events on the launching stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    infos = []
+    barrier()
+    with ClockSampler(dev.index) as clk:
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))            # evict L2 between timed steps
+            ev[k][0].record(stream)
+            _, info = jko.jko_step(h, q, p)
+            ev[k][1].record(stream)
+            infos.append(info)
+            q, p = p, q
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    iters = sum(i["iters"] for i in infos)
+    launches = sum(i["kernels"] for i in infos)
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        it_t = torch.tensor([iters], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(it_t)
+        iters_all = float(it_t.item())
+    else:
+        iters_all = float(iters)
+    value = iters_all / total_s
+    steps_per_s = ws * args.steps / total_s
+
+    # per-kernel durations (CUDA events on the handle's stream) for the roofline
+    ms4, fl4 = jko.jko_profile_passes(h, reps=20)
+    kern = max(range(4), key=lambda k: ms4[k])
+
+    # e2e through the public API with host buffers: every step copies its input
+    # from pinned host memory and reads its result back
+    host_q = torch.empty(N, dtype=dt, pin_memory=True)
+    host_p = torch.empty(N, dtype=dt, pin_memory=True)
+    host_q.copy_(q_start.cpu())
+    barrier()
+    e2e_iters = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        inf = jko.jko_flow_host(h, host_q, 1, None, host_p)
+        e2e_iters += inf[0]["iters"]
+        host_q, host_p = host_p, host_q
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * e2e_iters / e2e_s
+
+    peaks, peak_src = load_peaks()
+    if prec in (jko.Precision.FP32, jko.Precision.FP64):
+        clock_mhz = clocks.get("sm_max_mhz") or 2070.0
+        if prec == jko.Precision.FP32:
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+            peak_note = (f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                         f"{clock_mhz:.0f} MHz")
+        else:
+            peak = FP64_TFLOPS_NOMINAL
+            peak_note = "FP64 nominal"
+        bound = "alu"
+    else:
+        bf16 = _peak_value(peaks, "bf16_tflops_sustained", "bf16_tflops") or 1700.0
+        ratio = {jko.Precision.BF16: 1.0, jko.Precision.BF16X3: 1.0, jko.Precision.TF32: 0.5}[prec]
+        peak = bf16 * ratio
+        peak_note = f"bf16 sustained ({peak_src}) x {ratio} for {prec.name}"
+        bound = "tensor"
+    achieved = fl4[kern] / (ms4[kern] / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": ["pass_y_xi_a", "pass_x_xi_a+b_update", "pass_y_xi_b",
+                           "pass_x_xi_b+prox"][kern],
+                "kernel_ms": ms4[kern], "flops_per_launch": fl4[kern],
+                "peak_source": peak_note, "passes_ms": ms4}
+
+    # cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, k_it, secs = oracle_iteration_rate(pb, q_start.double().cpu().numpy(),
+                                                 budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"{k_it} FP64 scaling-loop iterations of one {args.n}^2 JKO step "
+                         f"from the warmed-up state ({secs:.1f} s, NumPy/BLAS, separable xi)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"FP64": "f64", "FP32": "f32", "TF32": "tf32", "BF16": "bf16",
+                      "BF16X3": "bf16x3"}[prec.name],
+            "data": "synthetic",
+            "config": {"workload": f"crowd motion {args.n}x{args.n}, gamma=2e-4, tau=0.02, "
+                                   "kappa=1.2 max q0, w=|x-(0.9,0.5)|^2, <=200 pairs/step, tol 1e-6",
+                       "precision": prec.name, "parallelism": f"replicas{ws}",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "steps_timed": f"JKO steps {args.warmup + 1}..{args.warmup + args.steps}"},
+            "jko_steps_per_s": steps_per_s,
+            "iters_per_step": [i["iters"] for i in infos],
+            "wall_s": t_wall,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * h.np_dtype().itemsize,
+                    "d2h_bytes_per_step": N * h.np_dtype().itemsize},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    jko.jko_destroy(h)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default=os.environ.get("JKO_BENCH_PRECISION", "FP32"))
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -106,6 +106,7 @@ typedef struct jko_step_info {
   double mass;               /* sum of p before any renormalisation (FP64) */
   double max_p_over_kappa;   /* max_i p_i / kappa_i (0 without congestion) */
   float ms;                  /* device time of the step in milliseconds */
+  int kernels;               /* kernels this library enqueued for the step */
 } jko_step_info;
 
 typedef struct jko_handle jko_handle;
@@ -140,6 +141,16 @@ jko_status jko_flow(jko_handle* h, const void* p0_dev, int n_steps, void* traj_d
  * requested outputs back; returns once they are in host memory. */
 jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* traj_host,
                          void* p_final_host, jko_step_info* infos);
+
+/* Times the four kernel passes of one (odd, even) pair in isolation on the
+ * handle's stream: pass 0 / 2 apply the first 1-D factor of xi to a / b, pass
+ * 1 / 3 the second factor fused with the b-update and residual / the KL prox
+ * and a-update.  Each pass is launched `reps` times back to back after one
+ * warm-up launch; ms[k] receives the mean milliseconds per launch (CUDA
+ * events) and, if flops is not NULL, flops[k] the algorithmic floating-point
+ * operations of one launch.  Overwrites the handle's scaling iterates: call it
+ * between flows, not inside one. */
+jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops);
 
 /* Re-targets the handle to another stream (a cudaStream_t). */
 jko_status jko_set_stream(jko_handle* h, void* stream);

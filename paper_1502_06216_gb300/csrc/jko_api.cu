@@ -59,6 +59,7 @@ struct jko_handle {
   int last_iters = 0;
 
   jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
+  long long kernels = 0;       // kernels enqueued by the running step
 
   std::string err;
 };
@@ -135,40 +136,54 @@ ProxArgs<T> prox_args(const jko_handle* h) {
   return P;
 }
 
-// One (odd, even) pair of the SIMT form on stream st.
+// Pass `which` of one (odd, even) pair in the SIMT form, on stream st:
+//   0: pass along y of xi a          1: pass along x of xi a + b-update/residual
+//   2: pass along y of xi b          3: pass along x of xi b + prox/a-update
 template <typename T>
-cudaError_t enqueue_pair_simt(jko_handle* h, cudaStream_t st) {
+cudaError_t enqueue_pass_simt(jko_handle* h, int which, cudaStream_t st) {
   const int nx = h->grid.nx, ny = h->grid.ny;
   ProxArgs<T> P = prox_args<T>(h);
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
-  cudaError_t e;
-  for (int half = 0; half < 2; ++half) {
+  const int half = which >> 1;
+  if ((which & 1) == 0) {
     // pass along y: in [ny][nx] -> t1 [nx][ny]
     A.in = (const T*)(half == 0 ? h->a : h->b);
     A.out = (T*)h->t1;
-    A.p = nullptr;
-    A.q = nullptr;
     A.taps = (const T*)h->taps_y;
     A.n_i = ny; A.n_j = nx; A.r = h->ry;
-    e = jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
-    if (e != cudaSuccess) return e;
-    // pass along x with the epilogue: in [nx][ny] -> [ny][nx]
-    A.in = (const T*)h->t1;
-    A.out = (T*)(half == 0 ? h->b : h->a);
-    A.p = (T*)h->p;
-    A.q = (const T*)h->q;
-    A.taps = (const T*)h->taps_x;
-    A.n_i = nx; A.n_j = ny; A.r = h->rx;
-    e = jko::simt_pass<T>(half == 0 ? jko::EPI_B : jko::EPI_A, h->ek, A, P, st);
+    return jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
+  }
+  // pass along x with the epilogue: in [nx][ny] -> [ny][nx]
+  A.in = (const T*)h->t1;
+  A.out = (T*)(half == 0 ? h->b : h->a);
+  A.p = (T*)h->p;
+  A.q = (const T*)h->q;
+  A.taps = (const T*)h->taps_x;
+  A.n_i = nx; A.n_j = ny; A.r = h->rx;
+  return jko::simt_pass<T>(half == 0 ? jko::EPI_B : jko::EPI_A, h->ek, A, P, st);
+}
+
+cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
+  if (h->tc) return jko::tc_enqueue_pass(h->tc, which, st);
+  return h->fp64 ? enqueue_pass_simt<double>(h, which, st) : enqueue_pass_simt<float>(h, which, st);
+}
+
+cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = enqueue_pass(h, k, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
-  if (h->tc) return jko::tc_enqueue_pair(h->tc, st);
-  return h->fp64 ? enqueue_pair_simt<double>(h, st) : enqueue_pair_simt<float>(h, st);
+// Algorithmic flops of pass `which`: the band-limited separable filter does
+// 2 (2r+1) flops per output (taps beyond r are zero in the working precision);
+// the tensor-core form reports the multiply-adds of the tiles it executes.
+double pass_flops(const jko_handle* h, int which) {
+  if (h->tc) return jko::tc_pass_flops(h->tc, which);
+  const int r = (which & 1) ? h->rx : h->ry;
+  return 2.0 * (2.0 * r + 1.0) * (double)h->N;
 }
 
 jko_status capture_chunk(jko_handle* h) {
@@ -319,7 +334,9 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   const int C = h->chunk_iters;
   const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
   int launched = 0, polled = 0;
+  h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   auto launch = [&]() -> cudaError_t {
+    h->kernels += 4LL * C;
     cudaError_t e = cudaGraphLaunch(h->chunk, st);
     if (e != cudaSuccess) return e;
     const int slot = launched & 1;
@@ -369,6 +386,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
+    info->kernels = (int)h->kernels;
   }
   if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");
   else if (st_out == JKO_NOT_CONVERGED) set_err(h, st_out, "max_iter reached before tol");
@@ -547,6 +565,34 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
   if (p_final_host) CK(h, cudaMemcpyAsync(p_final_host, cur, bytes, cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
   return (jko_status)worst;
+}
+
+jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  if (reps < 1 || !ms) return set_err(h, JKO_ERR_INVALID_ARG, "reps < 1 or NULL ms");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = h->stream;
+  // A running control block that never stops: it = 1 (residuals computed),
+  // tol < 0 and an unreachable budget.
+  Ctrl c0;
+  std::memcpy(&c0, h->ctrl_init, sizeof(Ctrl));
+  c0.it = 1;
+  c0.tol = -1.0;
+  c0.max_iter = 0x7fffffff;
+  CK(h, cudaMemcpy(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  for (int k = 0; k < 4; ++k) {
+    CK(h, enqueue_pass(h, k, st));  // warm-up launch
+    CK(h, cudaEventRecord(h->ev0, st));
+    for (int r = 0; r < reps; ++r) CK(h, enqueue_pass(h, k, st));
+    CK(h, cudaEventRecord(h->ev1, st));
+    CK(h, cudaEventSynchronize(h->ev1));
+    float t = 0.f;
+    CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
+    ms[k] = t / reps;
+    if (flops) flops[k] = pass_flops(h, k);
+  }
+  CK(h, cudaMemcpy(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  return JKO_OK;
 }
 
 jko_status jko_set_stream(jko_handle* h, void* stream) {

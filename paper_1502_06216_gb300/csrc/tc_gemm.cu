@@ -11,7 +11,8 @@ int tc_create(const TcConfig&, TcPlan** out, std::string* msg) {
   return 1;
 }
 cudaError_t tc_begin_step(TcPlan*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_enqueue_pair(TcPlan*, cudaStream_t) { return cudaErrorNotSupported; }
+cudaError_t tc_enqueue_pass(TcPlan*, int, cudaStream_t) { return cudaErrorNotSupported; }
+double tc_pass_flops(const TcPlan*, int) { return 0.0; }
 void tc_destroy(TcPlan* p) { delete p; }
 
 }  // namespace jko

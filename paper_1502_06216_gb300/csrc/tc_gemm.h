@@ -29,8 +29,10 @@ struct TcPlan;
 int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);
 // Per-step reset of the scaling operands (a = 1).
 cudaError_t tc_begin_step(TcPlan* plan, cudaStream_t st);
-// One (odd, even) pair: four tensor-core passes with fused epilogues.
-cudaError_t tc_enqueue_pair(TcPlan* plan, cudaStream_t st);
+// Pass `which` (0..3) of one (odd, even) pair, same numbering as the SIMT form.
+cudaError_t tc_enqueue_pass(TcPlan* plan, int which, cudaStream_t st);
+// Multiply-add flops (x2) of the tiles pass `which` executes.
+double tc_pass_flops(const TcPlan* plan, int which);
 void tc_destroy(TcPlan* plan);
 
 }  // namespace jko

@@ -65,7 +65,8 @@ class jko_energy(ctypes.Structure):
 class jko_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
-                ("max_p_over_kappa", ctypes.c_double), ("ms", ctypes.c_float)]
+                ("max_p_over_kappa", ctypes.c_double), ("ms", ctypes.c_float),
+                ("kernels", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +83,9 @@ EXPORTS = {
     "jko_flow_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.POINTER(jko_step_info)]),
+    "jko_profile_passes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "jko_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "jko_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "jko_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -229,6 +233,16 @@ def jko_flow_host(h: Handle, p0_host, n_steps: int, traj_host=None, p_final_host
     _check(L.jko_flow_host(h.ptr, ptr(p0_host), n_steps, ptr(traj_host), ptr(p_final_host),
                            infos), h.ptr)
     return [infos[i].as_dict() for i in range(n_steps)]
+
+
+def jko_profile_passes(h: Handle, reps: int = 20):
+    """Mean ms per launch and algorithmic flops of the four passes of a pair."""
+    ms = (ctypes.c_float * 4)()
+    fl = (ctypes.c_double * 4)()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_profile_passes(h.ptr, reps, ms, fl), h.ptr)
+    return list(ms), list(fl)
 
 
 def jko_destroy(h: Handle) -> None:
