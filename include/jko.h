@@ -152,6 +152,37 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
  * between flows, not inside one. */
 jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops);
 
+/* One JKO step without any memory allocation (the paper has no counterpart;
+ * this is a deployment variant of jko_step).
+ *
+ * For callers that cannot allocate device memory when they need a step: code
+ * running inside a framework that owns all device memory through its own pool
+ * (a cudaMalloc there escapes the pool's accounting, and a cudaFree
+ * synchronises the whole device), or services that forbid allocation after
+ * start-up.  It computes what jko_create + jko_step + jko_destroy compute for
+ * JKO_FP32, with the same CUDA-core kernels, but every working buffer lives in
+ * one fixed file-scope device array of about 3 MB that each GPU loading the
+ * library holds until the process exits.  Nothing is allocated: no
+ * cudaMalloc/cudaFree, no pinned memory, no graphs or events.
+ *
+ * Arguments are those of jko_create and jko_step (energy fields are HOST
+ * arrays; q_dev / p_out_dev are float device images of N = nx*ny elements and
+ * may alias); work is enqueued on `stream` (a cudaStream_t) and the call
+ * returns when p_out is complete.  info->ms is always 0.
+ *
+ * Limits and errors: JKO_ERR_UNSUPPORTED when nx > 256 or ny > 256 (the fixed
+ * array holds at most 256 x 256 cells) or precision != JKO_FP32;
+ * JKO_ERR_INVALID_ARG for the argument and input checks of jko_create /
+ * jko_step (outputs untouched); no message is recorded for jko_last_error.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and re-initialise what they read, so consecutive calls are
+ * independent, but calls whose GPU work overlaps (other streams or threads)
+ * race on it. */
+jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* params,
+                            const jko_energy* energy, const void* q_dev, void* p_out_dev,
+                            void* stream, jko_step_info* info);
+
 /* Re-targets the handle to another stream (a cudaStream_t). */
 jko_status jko_set_stream(jko_handle* h, void* stream);
 

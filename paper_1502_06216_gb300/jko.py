@@ -86,6 +86,10 @@ EXPORTS = {
     "jko_profile_passes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_double)]),
+    "jko_step_noalloc": (ctypes.c_int, [ctypes.POINTER(jko_grid), ctypes.POINTER(jko_params),
+                                        ctypes.POINTER(jko_energy), ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(jko_step_info)]),
     "jko_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "jko_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "jko_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -243,6 +247,35 @@ def jko_profile_passes(h: Handle, reps: int = 20):
     _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
     _check(L.jko_profile_passes(h.ptr, reps, ms, fl), h.ptr)
     return list(ms), list(fl)
+
+
+def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
+                     max_iter: Optional[int] = None, renormalize: bool = True):
+    """jko_step_noalloc for an ``inputs.Problem``: one FP32 step whose working
+    buffers live in the library's fixed device array (nothing is allocated by
+    the library; q and p_out are caller-owned float32 CUDA tensors).  Returns
+    (status, info dict); raises on errors other than NOT_CONVERGED/NUMERIC."""
+    N = pb.nx * pb.ny
+    for t, name in ((q, "q"), (p_out, "p_out")):
+        if not t.is_cuda or str(t.dtype) != "torch.float32" or not t.is_contiguous() \
+                or t.numel() < N:
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor of {N} elements")
+    g = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
+    p = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
+                   pb.max_iter if max_iter is None else max_iter, 0, int(Precision.FP32),
+                   int(bool(renormalize)))
+    keep = [_host_f64(pb.w, N), None, _host_f64(pb.alpha, N)]
+    mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
+    e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(pb.kappa), None,
+                   float(pb.m), keep[2].ctypes.data if keep[2] is not None else None,
+                   mk.ctypes.data if mk is not None else None)
+    info = jko_step_info()
+    st = lib().jko_step_noalloc(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e),
+                                ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(p_out.data_ptr()),
+                                _current_stream(), ctypes.byref(info))
+    if st not in (Status.OK, Status.NOT_CONVERGED, Status.NUMERIC):
+        raise JKOError(st, "jko_step_noalloc failed (see the status code)")
+    return Status(st), info.as_dict()
 
 
 def jko_destroy(h: Handle) -> None:
