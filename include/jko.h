@@ -126,7 +126,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params,
 /* One JKO step p_out = Prox^{W_gamma}_{tau f}(q) (Eq. def-jko-operator).
  * q_dev, p_out_dev: device images of N elements (double for JKO_FP64, float
  * otherwise); they may alias.  q must be finite, >= 0, sum to 1 within 1e-3,
- * vanish on masked cells and satisfy q <= kappa (1 + 1e-3) (Sec. 4.2 asks
+ * vanish on masked cells and satisfy q <= kappa (1 + 1e-2) (Sec. 4.2 asks
  * kappa >= max p_0), else JKO_ERR_INVALID_ARG.  info may be NULL. */
 jko_status jko_step(jko_handle* h, const void* q_dev, void* p_out_dev, jko_step_info* info);
 
@@ -143,7 +143,7 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
                          void* p_final_host, jko_step_info* infos);
 
 /* Times the four kernel passes of one (odd, even) pair in isolation on the
- * handle's stream: pass 0 / 2 apply the first 1-D factor of xi to a / b, pass
+ * handle's stream (captured in a CUDA graph, as the scaling loop runs them): pass 0 / 2 apply the first 1-D factor of xi to a / b, pass
  * 1 / 3 the second factor fused with the b-update and residual / the KL prox
  * and a-update.  Each pass is launched `reps` times back to back after one
  * warm-up launch; ms[k] receives the mean milliseconds per launch (CUDA

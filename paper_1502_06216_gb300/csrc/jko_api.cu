@@ -371,7 +371,9 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   CK(h, cudaStreamSynchronize(st));
   const Ctrl& c = h->poll[0];
   jko_status st_out = JKO_OK;
-  if (c.done == jko::NONFINITE || c.nonfinite) st_out = JKO_ERR_NUMERIC;
+  // nonfinite bit 1: NaN/Inf met by an epilogue; bit 2: a bounded device wait gave up
+  if (c.nonfinite & 2) st_out = JKO_ERR_TIMEOUT;
+  else if (c.done == jko::NONFINITE || c.nonfinite) st_out = JKO_ERR_NUMERIC;
   else if (c.done == jko::MAX_ITER) st_out = JKO_NOT_CONVERGED;
   h->last_iters = c.it;
   if (info) {
@@ -388,7 +390,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     info->ms = ms;
     info->kernels = (int)h->kernels;
   }
-  if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");
+  if (st_out == JKO_ERR_TIMEOUT) set_err(h, st_out, "a bounded device-side wait gave up");
+  else if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");
   else if (st_out == JKO_NOT_CONVERGED) set_err(h, st_out, "max_iter reached before tol");
   return st_out;
 }
@@ -581,11 +584,26 @@ jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops)
   c0.max_iter = 0x7fffffff;
   CK(h, cudaMemcpy(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice));
   for (int k = 0; k < 4; ++k) {
-    CK(h, enqueue_pass(h, k, st));  // warm-up launch
-    CK(h, cudaEventRecord(h->ev0, st));
-    for (int r = 0; r < reps; ++r) CK(h, enqueue_pass(h, k, st));
-    CK(h, cudaEventRecord(h->ev1, st));
-    CK(h, cudaEventSynchronize(h->ev1));
+    // the reps launches are captured in a graph, as the scaling loop runs them,
+    // so that host launch latency does not enter the per-launch time
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_pass(h, k, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_err(h, e, "profile capture"); }
+    CK(h, e2);
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    e = cudaGraphLaunch(ge, st);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev0, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev1);
+    cudaGraphExecDestroy(ge);
+    CK(h, e);
     float t = 0.f;
     CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
     ms[k] = t / reps;

@@ -34,7 +34,7 @@ struct Ctrl {
   double q_sum;
   unsigned long long q_neg;       // count of q < 0
   unsigned long long q_bad;       // count of non-finite q
-  unsigned long long q_over;      // count of q > kappa (1 + 1e-3)
+  unsigned long long q_over;      // count of q > kappa (1 + 1e-2)
   unsigned long long q_masked;    // count of q != 0 on the mask
 };
 
@@ -64,6 +64,30 @@ template <> __device__ __forceinline__ double dev_log<double>(double x) { return
 
 template <typename T> __device__ __forceinline__ bool dev_finite(T x) { return isfinite(x); }
 
+// x / y for the scaling updates.  In FP32 it is x times the correctly rounded
+// reciprocal of y (within about one ulp of the quotient): the IEEE division's
+// slow path, taken for the extreme magnitudes the scalings reach, costs more
+// than the rest of the epilogue.  FP64 keeps the true division.
+template <typename T> __device__ __forceinline__ T ratio_div(T x, T y);
+template <> __device__ __forceinline__ float ratio_div<float>(float x, float y) {
+  return x * __frcp_rn(y);
+}
+template <> __device__ __forceinline__ double ratio_div<double>(double x, double y) {
+  return x / y;
+}
+
+// b = q / Y of the b-update (Eq. update-formula-1), 0 where q = 0 and also
+// where Y = xi^T a is below the smallest normal number of the working
+// precision: there a has underflowed over the whole kernel width, the cell's
+// mass is below what the scalings can represent, and q / Y would overflow.
+template <typename T> struct NormalMin;
+template <> struct NormalMin<float> { static constexpr float v = 1.17549435e-38f; };
+template <> struct NormalMin<double> { static constexpr double v = 2.2250738585072014e-308; };
+template <typename T>
+__device__ __forceinline__ T b_update(T q, T Y) {
+  return (q == T(0) || !(Y >= NormalMin<T>::v)) ? T(0) : ratio_div<T>(q, Y);
+}
+
 // Newton stopping threshold on the step |dy| relative to 1 + |y|.
 template <typename T> struct NewtonEps;
 template <> struct NewtonEps<float> { static constexpr float v = 1e-7f; };
@@ -72,12 +96,14 @@ template <> struct NewtonEps<double> { static constexpr double v = 1e-15; };
 // a = Prox_{sigma f}(s) / s for one cell, extended continuously at s = 0
 // (Prop. 4.1, Eq. prox-entropy, Eq. prox-psi with the shift rule
 // Eq. prox-calculus-shift; clamp at kappa; 0 on the mask).
+// `e` is e^{-sigma w} of the cell when the caller has already loaded it (crowd
+// kind only; pass P.E[idx] otherwise).
 template <typename T, int EK>
-__device__ __forceinline__ T prox_ratio(const ProxArgs<T>& P, int idx, T s) {
+__device__ __forceinline__ T prox_ratio_e(const ProxArgs<T>& P, int idx, T s, T e) {
   if (P.mask != nullptr && P.mask[idx]) return T(0);
   T a;
   if (EK == EK_CROWD) {
-    a = P.E[idx];
+    a = e;
   } else if (EK == EK_ENTROPY) {
     // psi = (s e^{-sigma w})^{1/(1+sigma alpha)} ; a = psi / s
     if (!(s > T(0))) return T(0);
@@ -105,13 +131,23 @@ __device__ __forceinline__ T prox_ratio(const ProxArgs<T>& P, int idx, T s) {
       a = dev_exp<T>(y - ls);
     }
   }
-  if (P.has_kappa && s > T(0)) {
+  // clamp p = a s at kappa: a = min(a, kappa / s), dividing only where the
+  // bound is active (a s > kappa > 0 implies s > 0)
+  if (P.has_kappa) {
     const T kap = P.kappa ? P.kappa[idx] : P.kappa_s;
-    const T lim = kap / s;
-    a = a < lim ? a : lim;
+    if (a * s > kap) a = ratio_div<T>(kap, s);
   }
   return a;
 }
+
+template <typename T, int EK>
+__device__ __forceinline__ T prox_ratio(const ProxArgs<T>& P, int idx, T s) {
+  return prox_ratio_e<T, EK>(P, idx, s, EK == EK_CROWD ? P.E[idx] : T(0));
+}
+
+// |b Y - q| with one rounding (fused multiply-add) in the working precision.
+template <typename T>
+__device__ __forceinline__ T abs_residual(T b, T Y, T q) { return fabs(fma(b, Y, -q)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -38,7 +38,7 @@ __global__ void validate_kernel(const T* q, long long n, ProxArgs<T> P, Ctrl* ct
     if (!isfinite(v)) { ++bad; continue; }
     sum += (double)v;
     if (v < T(0)) ++neg;
-    if (P.has_kappa && (double)v > (double)kappa_at(P, i) * (1.0 + 1e-3)) ++over;
+    if (P.has_kappa && (double)v > (double)kappa_at(P, i) * (1.0 + 1e-2)) ++over;
     if (P.mask && P.mask[i] && v != T(0)) ++msk;
   }
   sum = block_sum(sum, s_red);

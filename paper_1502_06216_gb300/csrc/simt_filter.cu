@@ -85,7 +85,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   }
 
   // ---- epilogue: out is [n_j][n_i], this thread owns out[j][i0 .. i0+RB) ----
-  double res = 0.0;
+  T res_t = T(0);  // this thread's residual terms, in the working precision
   int bad = 0;
   if (active) {
     const size_t rowoff = (size_t)j * A.n_i;
@@ -102,8 +102,8 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
           const size_t idx = rowoff + i0 + o;
           const T Y = acc[o];
           const T qv = A.q[idx];
-          if (have_prev) res += fabs((double)A.out[idx] * (double)Y - (double)qv);
-          const T bn = (qv == T(0)) ? T(0) : qv / Y;
+          if (have_prev) res_t += abs_residual<T>(A.out[idx], Y, qv);
+          const T bn = b_update<T>(qv, Y);
           bad |= !dev_finite(bn);
           A.out[idx] = bn;
         }
@@ -126,7 +126,8 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
 
   // ---- reductions and the last-block decision ----
   bad = warp_or(bad);
-  if (EPI == EPI_B) res = block_sum(res, s_red);
+  double res = 0.0;
+  if (EPI == EPI_B) res = block_sum((double)res_t, s_red);
   __shared__ int s_bad;
   if (tid == 0) s_bad = 0;
   __syncthreads();

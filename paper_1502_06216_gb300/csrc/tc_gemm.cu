@@ -1,18 +1,927 @@
-// tc_gemm.cu -- tensor-core form (placeholder until the tcgen05 kernels land).
+// tc_gemm.cu -- tensor-core form of the Gibbs-kernel application (tcgen05 +
+// TMA + TMEM, sm_103a) with the scaling and proximal updates fused into the
+// GEMM epilogues.
+//
+// xi X = K_y X K_x^T (Sec. 4.1) is two dense contractions.  Each pass computes
+//     D[m][n] = sum_k K[m][k] B[n][k]
+// with K a 1-D Gibbs factor (symmetric, n_k x n_k) and B an image stored with
+// its contracted axis contiguous, so both operands are K-major:
+//   pass 0 / 2:  K = K_x, B = a / b as [ny][nx]   ->  D = T^T  as [nx][ny]
+//   pass 1 / 3:  K = K_y, B = T^T as [nx][ny]     ->  D = xi a / xi b as [ny][nx]
+// Pass 1 carries  b = q / xi a  and the residual (Eq. update-formula-1, the
+// stopping rule of Sec. 3.4); pass 3 carries  p = Prox_{sigma f}(s),  a = p / s
+// (Eq. update-formula-2, Eq. defn-pell).
+//
+// One CTA computes a 128 x BN tile: warp 0 (one lane) streams K-blocks of the
+// kernel factor and of the image through a ring of shared-memory stages with
+// TMA (128-byte swizzle), warp 1 (one lane) issues tcgen05.mma into a TMEM
+// accumulator and commits each stage back to the producer, and all four warps
+// then drain TMEM (tcgen05.ld) through the epilogue.  Only the K-blocks that
+// meet the band |m - k| <= r are visited, r being the last offset at which the
+// factor is a normal number in the operand precision (entries beyond it are
+// stored as exact zeros), so the skipped tiles contribute exactly zero.
+//
+// Precision modes: BF16 (one bf16 x bf16 product), BF16X3 (hi*hi + hi*lo +
+// lo*hi with x = hi + lo split into two bf16), TF32 (kind::tf32, operands
+// rounded to tf32).  Accumulation is FP32 in TMEM throughout.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "jko.h"
+#include "jko_kernels.h"
 #include "tc_gemm.h"
 
 namespace jko {
 
-struct TcPlan {};
+namespace {
 
-int tc_create(const TcConfig&, TcPlan** out, std::string* msg) {
-  *out = nullptr;
-  *msg = "tensor-core precisions are not built yet";
-  return 1;
+constexpr int BM = 128;            // UMMA M (rows of the kernel factor per tile)
+constexpr int KB_BYTES = 128;      // K-block width in bytes (one 128-byte swizzle row)
+constexpr int MAX_STAGES = 4;
+constexpr uint32_t SMEM_BUDGET = 200 * 1024;  // operand stages per CTA
+constexpr int NT = 128;            // threads per CTA
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier polls
+
+enum : int { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_TF32 = 2 };
+
+// Bytes of one pipeline stage and the number of stages that fit the budget.
+__host__ __device__ constexpr uint32_t stage_bytes(int mode, int bn) {
+  return (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)(BM + bn) * (uint32_t)KB_BYTES;
 }
-cudaError_t tc_begin_step(TcPlan*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_enqueue_pass(TcPlan*, int, cudaStream_t) { return cudaErrorNotSupported; }
-double tc_pass_flops(const TcPlan*, int) { return 0.0; }
-void tc_destroy(TcPlan* p) { delete p; }
+__host__ __device__ constexpr int num_stages(int mode, int bn) {
+  return SMEM_BUDGET / stage_bytes(mode, bn) < (uint32_t)MAX_STAGES
+             ? (int)(SMEM_BUDGET / stage_bytes(mode, bn))
+             : MAX_STAGES;
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after kSpinLimit polls (the caller records a fault).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accum) {
+  if (MODE == MODE_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x,
+                                             int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          (uint64_t)map),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B bf16 (kind::f16) or tf32, both K-major.
+template <int MODE>
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | ((MODE == MODE_TF32 ? 2u : 1u) << 7) | ((MODE == MODE_TF32 ? 2u : 1u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MODE> struct OpT;
+template <> struct OpT<MODE_BF16> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
+template <> struct OpT<MODE_BF16X3> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
+template <> struct OpT<MODE_TF32> { using T = float; static constexpr int kElems = 32; };
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Operand value of one image element (hi [+ lo]) as float.
+template <int MODE, typename T>
+__device__ __forceinline__ float op_load(const T* hi, const T* lo, size_t i) {
+  if constexpr (MODE == MODE_TF32) return hi[i];
+  else if constexpr (MODE == MODE_BF16X3) return __bfloat162float(hi[i]) + __bfloat162float(lo[i]);
+  else return __bfloat162float(hi[i]);
+}
+template <int MODE, typename T>
+__device__ __forceinline__ void op_store(T* hi, T* lo, size_t i, float v) {
+  if constexpr (MODE == MODE_TF32) {
+    hi[i] = tf32_round(v);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    if constexpr (MODE == MODE_BF16X3) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// 16 consecutive fp32 of one row: vector loads when the row segment is
+// 16-byte aligned and complete, scalar loads of the first `cnt` otherwise.
+__device__ __forceinline__ void load_f32x16(const float* src, int cnt, bool vec, float (&o)[16]) {
+  if (vec && cnt == 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(src) + q);
+      o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = j < cnt ? src[j] : 0.0f;
+  }
+}
+__device__ __forceinline__ void store_f32x16(float* dst, int cnt, bool vec, const float (&v)[16]) {
+  if (vec && cnt == 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      reinterpret_cast<float4*>(dst)[q] =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < cnt) dst[j] = v[j];
+  }
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+  return __bfloat1622float2(h);
+}
+// 16 operand-typed values of one row (rows padded to 16 bytes): the value is
+// hi (+ lo).  Vector loads when the 16 lie inside the valid columns.
+template <int MODE, typename T>
+__device__ __forceinline__ void load_op16(const T* hi, const T* lo, size_t off, int cnt,
+                                          float (&o)[16]) {
+  if (cnt == 16) {
+    if constexpr (MODE == MODE_TF32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = reinterpret_cast<const float4*>(hi + off)[q];
+        o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint4 t = reinterpret_cast<const uint4*>(hi + off)[q];
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(w[k]);
+          o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
+        }
+      }
+      if constexpr (MODE == MODE_BF16X3) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint4 t = reinterpret_cast<const uint4*>(lo + off)[q];
+          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 f = unpack_bf16x2(w[k]);
+            o[8 * q + 2 * k] += f.x; o[8 * q + 2 * k + 1] += f.y;
+          }
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = j < cnt ? op_load<MODE>(hi, lo, off + j) : 0.0f;
+  }
+}
+// Writes 16 values of local row r, columns 16c .. 16c+15, into the staging
+// tile in the layout of a 128-byte-swizzled TMA box of 128 rows: column block
+// cb holds 128 bytes per row; the 16-byte chunk k of row r sits at k ^ (r & 7).
+template <int MODE>
+__device__ __forceinline__ void stage16(unsigned char* st_hi, unsigned char* st_lo, int r, int c,
+                                        const float (&o)[16]) {
+  constexpr uint32_t BLK = BM * 128;
+  if constexpr (MODE == MODE_TF32) {
+    const int cb = c >> 1, k0 = (c & 1) * 4;
+    unsigned char* row = st_hi + cb * BLK + r * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 u;
+      u.x = __float_as_uint(tf32_round(o[4 * q]));
+      u.y = __float_as_uint(tf32_round(o[4 * q + 1]));
+      u.z = __float_as_uint(tf32_round(o[4 * q + 2]));
+      u.w = __float_as_uint(tf32_round(o[4 * q + 3]));
+      *reinterpret_cast<uint4*>(row + (((k0 + q) ^ (r & 7)) << 4)) = u;
+    }
+  } else {
+    const int cb = c >> 2, k0 = (c & 3) * 2;
+    unsigned char* row_hi = st_hi + cb * BLK + r * 128;
+    unsigned char* row_lo = st_lo + cb * BLK + r * 128;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float h[8], l[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float v = o[8 * q + k];
+        h[k] = __bfloat162float(__float2bfloat16_rn(v));
+        l[k] = v - h[k];
+      }
+      uint4 u;
+      u.x = pack_bf16x2(h[0], h[1]); u.y = pack_bf16x2(h[2], h[3]);
+      u.z = pack_bf16x2(h[4], h[5]); u.w = pack_bf16x2(h[6], h[7]);
+      *reinterpret_cast<uint4*>(row_hi + (((k0 + q) ^ (r & 7)) << 4)) = u;
+      if constexpr (MODE == MODE_BF16X3) {
+        uint4 w;
+        w.x = pack_bf16x2(l[0], l[1]); w.y = pack_bf16x2(l[2], l[3]);
+        w.z = pack_bf16x2(l[4], l[5]); w.w = pack_bf16x2(l[6], l[7]);
+        *reinterpret_cast<uint4*>(row_lo + (((k0 + q) ^ (r & 7)) << 4)) = w;
+      }
+    }
+  }
+}
+
+struct TcPassArgs {
+  int M, N, Kdim;         // D is M x N, contraction length Kdim (= M)
+  int r;                  // band radius of the kernel factor
+  int pitch_out;          // row pitch (elements) of the operand-typed output image
+  void* out_hi;           // EPI_STORE: T^T ; EPI_B: b ; EPI_A: a   (operand type)
+  void* out_lo;           // BF16X3 low parts
+  float* p;               // EPI_A
+  const float* q;         // EPI_B
+  Ctrl* ctrl;
+  ProxArgs<float> P;
+};
+
+template <int MODE, int EPI, int EK, int BN>
+__global__ void __launch_bounds__(NT, 1)
+tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
+               const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
+               const __grid_constant__ CUtensorMap mapO_hi, const __grid_constant__ CUtensorMap mapO_lo,
+               TcPassArgs args) {
+  using T = typename OpT<MODE>::T;
+  constexpr int KE = OpT<MODE>::kElems;                  // elements per K-block
+  constexpr int UK = (MODE == MODE_TF32) ? 8 : 16;      // K per MMA
+  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;  // hi (+ lo) operand tiles
+  constexpr uint32_t A_BYTES = BM * KB_BYTES;
+  constexpr uint32_t B_BYTES = BN * KB_BYTES;
+  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  constexpr int STAGES = num_stages(MODE, BN);
+  static_assert(STAGE_BYTES == stage_bytes(MODE, BN), "stage size");
+  static_assert(STAGES >= 2, "at least two stages");
+  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t IDESC = make_idesc<MODE>(BM, BN);
+
+  Ctrl* ctrl = args.ctrl;
+  if (ctrl->done) return;  // uniform: set only between launches
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full_bar = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty_bar = full_bar + STAGES;
+  uint64_t* accum_bar = empty_bar + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 1);
+  __shared__ double s_red[33];
+  __shared__ int s_fault;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * BM;
+
+  // band of K-blocks that meet |m - k| <= r for m in [m0, m0 + BM)
+  int k_lo = m0 - args.r;
+  if (k_lo < 0) k_lo = 0;
+  int k_hi = m0 + BM - 1 + args.r;
+  if (k_hi > args.Kdim - 1) k_hi = args.Kdim - 1;
+  const int kb_lo = k_lo / KE;
+  const int nkb = k_hi / KE - kb_lo + 1;
+
+  if (threadIdx.x == 0) {
+    s_fault = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(accum_bar, 1);
+    fence_mbar_init();
+    tma_prefetch_desc(&mapA_hi);
+    tma_prefetch_desc(&mapB_hi);
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int s = i % STAGES;
+      if (i >= STAGES) ok = mbar_wait(&empty_bar[s], ((i / STAGES) - 1) & 1);
+      if (!ok) break;
+      unsigned char* st = smem + s * STAGE_BYTES;
+      mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+      const int kx = (kb_lo + i) * KE;
+      tma_load_2d(st, &mapA_hi, &full_bar[s], kx, m0);
+      tma_load_2d(st + A_BYTES, &mapB_hi, &full_bar[s], kx, n0);
+      if constexpr (NSPLIT == 2) {
+        tma_load_2d(st + A_BYTES + B_BYTES, &mapA_lo, &full_bar[s], kx, m0);
+        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapB_lo, &full_bar[s], kx, n0);
+      }
+    }
+    if (!ok) atomicOr(&s_fault, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    for (int i = 0; i < nkb && ok; ++i) {
+      const int s = i % STAGES;
+      ok = mbar_wait(&full_bar[s], (i / STAGES) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint64_t a_hi = sdesc_sw128(sa);
+      const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < KB_BYTES / 32; ++kk) {   // 32 bytes of K per MMA
+        const uint64_t adv = (uint64_t)(kk * 2);      // +32 bytes in 16-byte units
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
+        if constexpr (NSPLIT == 2) {
+          const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
+          const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
+          umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
+          umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
+        }
+      }
+      umma_commit(&empty_bar[s]);   // frees the stage once these MMAs have read it
+    }
+    umma_commit(accum_bar);          // accumulator complete
+    if (!ok) atomicOr(&s_fault, 1);
+  }
+  (void)UK;
+  __syncwarp();
+
+  // ---- epilogue: all four warps, warp w owns TMEM lanes 32w .. 32w+31 ----
+  bool have = mbar_wait(accum_bar, 0);
+  if (!have) atomicOr(&s_fault, 1);
+  __syncwarp();
+  tc_fence_after();
+
+  // The operand-typed output tile is staged in shared memory (the pipeline
+  // stages are free once the accumulator is complete) and written with TMA.
+  constexpr int CB = BN * (int)sizeof(T) / 128;       // 128-byte column blocks
+  constexpr uint32_t OUT_BLOCK = BM * 128;
+  static_assert((NSPLIT * CB) * OUT_BLOCK <= STAGES * STAGE_BYTES, "staging fits the stages");
+  unsigned char* st_hi = smem;
+  unsigned char* st_lo = smem + CB * OUT_BLOCK;
+  const int rl = warp * 32 + lane;
+  const int m = m0 + rl;
+  const bool row_ok = m < args.M;
+  const bool vec_in = (args.N & 3) == 0;
+  float res_f = 0.0f;  // this thread's residual terms (FP32, one rounding each)
+  int bad = 0;
+  const bool have_prev = (EPI == EPI_B) ? (ctrl->it > 0) : false;
+  const T* cur_hi = (const T*)args.out_hi;
+  const T* cur_lo = (const T*)args.out_lo;
+  if (have) {
+#pragma unroll 1
+    for (int c = 0; c < BN / 16; ++c) {
+      float v[16];
+      tmem_ld16(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+      const int nb = n0 + c * 16;
+      int cnt = args.N - nb;
+      cnt = !row_ok || cnt < 0 ? 0 : (cnt > 16 ? 16 : cnt);
+      float o[16];
+      if (EPI == EPI_STORE) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = v[j];
+      } else if (EPI == EPI_B) {
+        const size_t irow = (size_t)m * args.N + nb;   // q is [M][N] unpadded
+        float qv[16], bo[16];
+        load_f32x16(args.q + (cnt ? irow : 0), cnt, vec_in, qv);
+        if (have_prev) load_op16<MODE>(cur_hi, cur_lo, cnt ? (size_t)m * args.pitch_out + nb : 0, cnt, bo);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (j < cnt) {
+            if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
+            o[j] = b_update<float>(qv[j], v[j]);
+            bad |= !isfinite(o[j]);
+          } else {
+            o[j] = 0.0f;
+          }
+        }
+      } else {  // EPI_A
+        const size_t irow = (size_t)m * args.N + nb;
+        float ev[16], pv[16];
+        if (EK == EK_CROWD) load_f32x16(args.P.E + (cnt ? irow : 0), cnt, vec_in, ev);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (j < cnt) {
+            const float a = prox_ratio_e<float, EK>(args.P, (int)(irow + j), v[j],
+                                                     EK == EK_CROWD ? ev[j] : 0.0f);
+            bad |= !isfinite(a);
+            o[j] = a;
+            pv[j] = a * v[j];
+          } else {
+            o[j] = 0.0f;
+            pv[j] = 0.0f;
+          }
+        }
+        if (cnt) store_f32x16(args.p + irow, cnt, vec_in, pv);
+      }
+      stage16<MODE>(st_hi, st_lo, rl, c, o);
+    }
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && have) {
+    constexpr int KEo = 128 / (int)sizeof(T);  // columns per block
+#pragma unroll
+    for (int cb = 0; cb < CB; ++cb) {
+      tma_store_2d(&mapO_hi, st_hi + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+      if constexpr (NSPLIT == 2) tma_store_2d(&mapO_lo, st_lo + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+    }
+    bulk_commit();
+    bulk_wait_all();
+  }
+  if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+
+  if (EPI == EPI_STORE) {
+    if (threadIdx.x == 0 && s_fault) atomicOr(&ctrl->nonfinite, 2);
+    return;
+  }
+  // ---- residual / flags and the last-block decision ----
+  bad = warp_or(bad);
+  double res = 0.0;
+  if (EPI == EPI_B) res = block_sum((double)res_f, s_red);
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (lane == 0 && bad) atomicOr(&s_bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    if (EPI == EPI_B && res != 0.0) atomicAdd(&ctrl->res_acc, res);
+    if (s_bad) atomicOr(&ctrl->nonfinite, 1);
+    if (s_fault) atomicOr(&ctrl->nonfinite, 2);
+    __threadfence();
+    unsigned* counter = (EPI == EPI_B) ? &ctrl->arrive_b : &ctrl->arrive_a;
+    const unsigned prev = atomicAdd(counter, 1u);
+    if (prev == nblocks - 1) {
+      __threadfence();
+      const int nonf = atomicOr(&ctrl->nonfinite, 0);
+      const int it = ctrl->it;
+      if (EPI == EPI_B) {
+        const double total = atomicAdd(&ctrl->res_acc, 0.0);
+        if (it > 0) ctrl->res_last = total;
+        if (nonf || (it > 0 && !isfinite(total))) ctrl->done = NONFINITE;
+        else if (it > 0 && total <= ctrl->tol) ctrl->done = CONVERGED;
+        else if (it >= ctrl->max_iter) ctrl->done = MAX_ITER;
+        ctrl->res_acc = 0.0;
+      } else {
+        ctrl->it = it + 1;
+        if (nonf) ctrl->done = NONFINITE;
+      }
+      *counter = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// a = 1 in operand precision (cold start), padded columns included.
+template <typename T>
+__global__ void fill_op_kernel(T* hi, T* lo, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(T) == 4) {
+      hi[i] = v;
+    } else {
+      hi[i] = __float2bfloat16_rn(v);
+      if (lo) lo[i] = __float2bfloat16_rn(0.0f);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D tensor map of a row-major [rows][pitch] operand matrix whose first
+// `cols` columns are valid; box = box_rows x (128 bytes of K).
+bool make_map(CUtensorMap* map, void* base, int mode, int rows, int cols, int pitch, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const int es = mode == MODE_TF32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+  cuuint32_t box[2] = {(cuuint32_t)(KB_BYTES / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, mode == MODE_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct TcPlan {
+  TcConfig cfg;
+  int mode = MODE_BF16;
+  int bn_x = 64, bn_y = 64;   // BN of the pass over x (N = ny) and over y (N = nx)
+  int rx = 0, ry = 0;          // band radii
+  int px = 0, py = 0;          // pitches (elements) of images with x / y contiguous
+  void* kx[2] = {nullptr, nullptr};
+  void* ky[2] = {nullptr, nullptr};
+  void* img_a[2] = {nullptr, nullptr};   // [ny][px]
+  void* img_b[2] = {nullptr, nullptr};   // [ny][px]
+  void* img_t[2] = {nullptr, nullptr};   // [nx][py]
+  CUtensorMap mKx[2], mKy[2], mA[2], mB[2], mT[2];  // operand loads
+  CUtensorMap sA[2], sB[2], sT[2];                  // epilogue stores (box 128 rows)
+  double flops[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+template <int MODE, int EPI, int EK, int BN>
+size_t smem_bytes() {
+  constexpr int ST = num_stages(MODE, BN);
+  return (size_t)ST * stage_bytes(MODE, BN) + 1024 + (2 * ST + 1) * 8 + 16;
+}
+
+struct Maps {
+  const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo, *o_hi, *o_lo;
+};
+
+template <int MODE, int EPI, int EK, int BN>
+cudaError_t launch_pass(const Maps& M, const TcPassArgs& args, cudaStream_t st) {
+  dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM);
+  tc_pass_kernel<MODE, EPI, EK, BN><<<grid, NT, smem_bytes<MODE, EPI, EK, BN>(), st>>>(
+      *M.a_hi, *M.a_lo, *M.b_hi, *M.b_lo, *M.o_hi, *M.o_lo, args);
+  return cudaGetLastError();
+}
+
+template <int MODE, int EPI, int EK, int BN>
+cudaError_t set_attr() {
+  return cudaFuncSetAttribute(tc_pass_kernel<MODE, EPI, EK, BN>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes<MODE, EPI, EK, BN>());
+}
+
+template <int MODE, int BN>
+cudaError_t set_attrs_bn() {
+  cudaError_t e;
+  if ((e = set_attr<MODE, EPI_STORE, EK_CROWD, BN>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, EPI_B, EK_CROWD, BN>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, EPI_A, EK_CROWD, BN>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, EPI_A, EK_ENTROPY, BN>()) != cudaSuccess) return e;
+  return set_attr<MODE, EPI_A, EK_POWER, BN>();
+}
+
+template <int MODE>
+cudaError_t set_attrs() {
+  cudaError_t e = set_attrs_bn<MODE, 64>();
+  if (e != cudaSuccess) return e;
+  return set_attrs_bn<MODE, 128>();
+}
+
+template <int MODE, int BN>
+cudaError_t dispatch_epi(int epi, int ek, const Maps& M, const TcPassArgs& args, cudaStream_t st) {
+  if (epi == EPI_STORE) return launch_pass<MODE, EPI_STORE, EK_CROWD, BN>(M, args, st);
+  if (epi == EPI_B) return launch_pass<MODE, EPI_B, EK_CROWD, BN>(M, args, st);
+  if (ek == EK_CROWD) return launch_pass<MODE, EPI_A, EK_CROWD, BN>(M, args, st);
+  if (ek == EK_ENTROPY) return launch_pass<MODE, EPI_A, EK_ENTROPY, BN>(M, args, st);
+  return launch_pass<MODE, EPI_A, EK_POWER, BN>(M, args, st);
+}
+
+template <int MODE>
+cudaError_t dispatch_bn(int bn, int epi, int ek, const Maps& M, const TcPassArgs& args,
+                        cudaStream_t st) {
+  if (bn == 128) return dispatch_epi<MODE, 128>(epi, ek, M, args, st);
+  return dispatch_epi<MODE, 64>(epi, ek, M, args, st);
+}
+
+// Radius of the band: last offset whose factor entry is a normal number in the
+// operand precision (bf16 shares the fp32 exponent range; tf32 too).
+int band_radius(int n, double length, double gamma) {
+  const double h = length / n;
+  int r = 0;
+  for (int d = 0; d < n; ++d) {
+    const double v = std::exp(-(d * h) * (d * h) / gamma);
+    if (v >= 1.1754943508222875e-38) r = d;
+  }
+  return r;
+}
+
+// Host construction of one factor in operand precision: hi (+ lo) [n][pitch].
+template <typename T>
+void build_factor(std::vector<T>& hi, std::vector<T>& lo, int n, int pitch, double length,
+                  double gamma, int r, int mode) {
+  const double h = length / n;
+  hi.assign((size_t)n * pitch, T(0.0f));
+  lo.assign((size_t)n * pitch, T(0.0f));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const int d = i > j ? i - j : j - i;
+      if (d > r) continue;
+      const double v = std::exp(-(d * h) * (d * h) / gamma);
+      if constexpr (sizeof(T) == 4) {
+        // round to tf32 (10 mantissa bits, nearest-away as cvt.rna)
+        float f = (float)v;
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        u = (u + 0x1000u) & 0xFFFFE000u;
+        std::memcpy(&f, &u, 4);
+        hi[(size_t)i * pitch + j] = f;
+      } else {
+        const float f = (float)v;
+        const __nv_bfloat16 bh = __float2bfloat16_rn(f);
+        hi[(size_t)i * pitch + j] = bh;
+        lo[(size_t)i * pitch + j] = __float2bfloat16_rn(f - __bfloat162float(bh));
+      }
+    }
+  (void)mode;
+}
+
+template <typename T>
+cudaError_t alloc_img(void** p, size_t elems) {
+  cudaError_t e = cudaMalloc(p, elems * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemset(*p, 0, elems * sizeof(T));
+}
+
+template <typename T>
+int create_typed(TcPlan* P, std::string* msg) {
+  const TcConfig& c = P->cfg;
+  const int nx = c.nx, ny = c.ny;
+  const int align = 16 / (int)sizeof(T);
+  P->px = round_up(nx, align);
+  P->py = round_up(ny, align);
+  P->rx = band_radius(nx, c.lx, c.gamma);
+  P->ry = band_radius(ny, c.ly, c.gamma);
+  const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
+  std::vector<T> hi, lo;
+  cudaError_t e;
+  for (int axis = 0; axis < 2; ++axis) {
+    const int n = axis == 0 ? nx : ny;
+    const int pitch = axis == 0 ? P->px : P->py;
+    build_factor<T>(hi, lo, n, pitch, axis == 0 ? c.lx : c.ly, c.gamma,
+                    axis == 0 ? P->rx : P->ry, P->mode);
+    void** dst = axis == 0 ? P->kx : P->ky;
+    for (int s = 0; s < nsplit; ++s) {
+      const auto& src = s == 0 ? hi : lo;
+      if ((e = cudaMalloc(&dst[s], src.size() * sizeof(T))) != cudaSuccess) { *msg = "cudaMalloc factor"; return 2; }
+      if ((e = cudaMemcpy(dst[s], src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) { *msg = "upload factor"; return 2; }
+    }
+  }
+  for (int s = 0; s < nsplit; ++s) {
+    if (alloc_img<T>(&P->img_a[s], (size_t)ny * P->px) != cudaSuccess ||
+        alloc_img<T>(&P->img_b[s], (size_t)ny * P->px) != cudaSuccess ||
+        alloc_img<T>(&P->img_t[s], (size_t)nx * P->py) != cudaSuccess) {
+      *msg = "cudaMalloc operand images";
+      return 2;
+    }
+  }
+  // tile widths: BN = 128 when that still fills the GPU, else 64
+  auto pick = [](int M, int N) { return ((M + BM - 1) / BM) * ((N + 127) / 128) >= 152 ? 128 : 64; };
+  P->bn_x = pick(nx, ny);  // pass over x: M = nx, N = ny
+  P->bn_y = pick(ny, nx);  // pass over y: M = ny, N = nx
+  // tensor maps (hi and lo; lo maps alias hi when unused)
+  const int m = P->mode;
+  for (int s = 0; s < 2; ++s) {
+    const int si = s < nsplit ? s : 0;
+    bool ok = make_map(&P->mKx[s], P->kx[si], m, nx, nx, P->px, BM) &&
+              make_map(&P->mKy[s], P->ky[si], m, ny, ny, P->py, BM) &&
+              make_map(&P->mA[s], P->img_a[si], m, ny, nx, P->px, P->bn_x) &&
+              make_map(&P->mB[s], P->img_b[si], m, ny, nx, P->px, P->bn_x) &&
+              make_map(&P->mT[s], P->img_t[si], m, nx, ny, P->py, P->bn_y) &&
+              make_map(&P->sA[s], P->img_a[si], m, ny, nx, P->px, BM) &&
+              make_map(&P->sB[s], P->img_b[si], m, ny, nx, P->px, BM) &&
+              make_map(&P->sT[s], P->img_t[si], m, nx, ny, P->py, BM);
+    if (!ok) { *msg = "cuTensorMapEncodeTiled failed"; return 2; }
+  }
+  // executed flops per pass
+  const int KE = m == MODE_TF32 ? 32 : 64;
+  const double mult = m == MODE_BF16X3 ? 3.0 : 1.0;
+  for (int pass = 0; pass < 4; ++pass) {
+    const bool over_x = (pass & 1) == 0;
+    const int M = over_x ? nx : ny, N = over_x ? ny : nx, r = over_x ? P->rx : P->ry;
+    const int bn = over_x ? P->bn_x : P->bn_y;
+    double f = 0.0;
+    for (int mt = 0; mt * BM < M; ++mt) {
+      const int m0 = mt * BM;
+      const int klo = std::max(0, m0 - r), khi = std::min(M - 1, m0 + BM - 1 + r);
+      const int nk = (khi / KE - klo / KE + 1) * KE;
+      f += 2.0 * BM * nk * (double)(((N + bn - 1) / bn) * bn) * mult;
+    }
+    P->flops[pass] = f;
+  }
+  cudaError_t ea = m == MODE_TF32 ? set_attrs<MODE_TF32>()
+                                  : (m == MODE_BF16X3 ? set_attrs<MODE_BF16X3>() : set_attrs<MODE_BF16>());
+  if (ea != cudaSuccess) { *msg = "cudaFuncSetAttribute (shared memory)"; return 2; }
+  return 0;
+}
+
+}  // namespace
+
+int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg) {
+  *out = nullptr;
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) {
+    *msg = "tensor-core precisions need an sm_103 GPU (GB300)";
+    return 1;
+  }
+  if (!get_encode()) { *msg = "cuTensorMapEncodeTiled is unavailable"; return 1; }
+  TcPlan* P = new TcPlan();
+  P->cfg = cfg;
+  P->mode = cfg.precision == JKO_TF32 ? MODE_TF32 : (cfg.precision == JKO_BF16X3 ? MODE_BF16X3 : MODE_BF16);
+  const int rc = P->mode == MODE_TF32 ? create_typed<float>(P, msg) : create_typed<__nv_bfloat16>(P, msg);
+  if (rc != 0) { tc_destroy(P); return rc; }
+  *out = P;
+  return 0;
+}
+
+cudaError_t tc_begin_step(TcPlan* P, cudaStream_t st) {
+  const long long n = (long long)P->cfg.ny * P->px;
+  if (P->mode == MODE_TF32)
+    fill_op_kernel<float><<<152 * 4, 256, 0, st>>>((float*)P->img_a[0], nullptr, n, 1.0f);
+  else
+    fill_op_kernel<__nv_bfloat16><<<152 * 4, 256, 0, st>>>(
+        (__nv_bfloat16*)P->img_a[0], (__nv_bfloat16*)P->img_a[1], n, 1.0f);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
+  const TcConfig& c = P->cfg;
+  const bool over_x = (which & 1) == 0;
+  const int half = which >> 1;
+  TcPassArgs a{};
+  a.ctrl = c.ctrl;
+  a.P = c.prox;
+  a.q = c.q;
+  a.p = c.p;
+  Maps mp{};
+  int bn, epi;
+  if (over_x) {  // K_x . image^T -> T^T [nx][ny]
+    a.M = c.nx; a.N = c.ny; a.Kdim = c.nx; a.r = P->rx;
+    a.pitch_out = P->py;
+    a.out_hi = P->img_t[0]; a.out_lo = P->img_t[1];
+    mp.a_hi = &P->mKx[0]; mp.a_lo = &P->mKx[1];
+    mp.b_hi = half == 0 ? &P->mA[0] : &P->mB[0];
+    mp.b_lo = half == 0 ? &P->mA[1] : &P->mB[1];
+    mp.o_hi = &P->sT[0]; mp.o_lo = &P->sT[1];
+    bn = P->bn_x;
+    epi = EPI_STORE;
+  } else {       // K_y . T^T^T -> [ny][nx] with the epilogue
+    a.M = c.ny; a.N = c.nx; a.Kdim = c.ny; a.r = P->ry;
+    a.pitch_out = P->px;
+    a.out_hi = half == 0 ? P->img_b[0] : P->img_a[0];
+    a.out_lo = half == 0 ? P->img_b[1] : P->img_a[1];
+    mp.a_hi = &P->mKy[0]; mp.a_lo = &P->mKy[1];
+    mp.b_hi = &P->mT[0]; mp.b_lo = &P->mT[1];
+    mp.o_hi = half == 0 ? &P->sB[0] : &P->sA[0];
+    mp.o_lo = half == 0 ? &P->sB[1] : &P->sA[1];
+    bn = P->bn_y;
+    epi = half == 0 ? EPI_B : EPI_A;
+  }
+  switch (P->mode) {
+    case MODE_TF32: return dispatch_bn<MODE_TF32>(bn, epi, c.ek, mp, a, st);
+    case MODE_BF16X3: return dispatch_bn<MODE_BF16X3>(bn, epi, c.ek, mp, a, st);
+    default: return dispatch_bn<MODE_BF16>(bn, epi, c.ek, mp, a, st);
+  }
+}
+
+double tc_pass_flops(const TcPlan* P, int which) { return P->flops[which & 3]; }
+
+void tc_destroy(TcPlan* P) {
+  if (!P) return;
+  void* bufs[] = {P->kx[0], P->kx[1], P->ky[0], P->ky[1], P->img_a[0], P->img_a[1],
+                  P->img_b[0], P->img_b[1], P->img_t[0], P->img_t[1]};
+  for (void* b : bufs) if (b) cudaFree(b);
+  delete P;
+}
 
 }  // namespace jko
