@@ -49,6 +49,8 @@ struct jko_handle {
   double m = 0.0;
 
   Ctrl* ctrl = nullptr;        // device control block
+  double* part = nullptr;      // residual partials of the b-update pass (one per block)
+  int nparts_simt = 0;
   Ctrl* ctrl_init = nullptr;   // pinned initial value
   Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
   cudaEvent_t ev_poll[2] = {nullptr, nullptr};
@@ -145,6 +147,9 @@ cudaError_t enqueue_pass_simt(jko_handle* h, int which, cudaStream_t st) {
   ProxArgs<T> P = prox_args<T>(h);
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
+  A.part = h->part;
+  A.nparts = h->nparts_simt;
+  A.decide = which == 2 ? 1 : 0;  // the pass after the b-update takes the stop decision
   const int half = which >> 1;
   if ((which & 1) == 0) {
     // pass along y: in [ny][nx] -> t1 [nx][ny]
@@ -206,7 +211,7 @@ void free_handle(jko_handle* h) {
   if (h->tc) jko::tc_destroy(h->tc);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
-                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl};
+                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl, h->part};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -475,6 +480,14 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   }
   e = cudaMalloc((void**)&h->ctrl, sizeof(Ctrl));
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(ctrl)"));
+  h->nparts_simt = jko::simt_pass_blocks(grid->nx, grid->ny);  // the b-update pass runs along x
+  {
+    const int np = std::max(h->nparts_simt, jko::tc_partials(grid->nx, grid->ny));
+    e = cudaMalloc((void**)&h->part, sizeof(double) * np);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(partials)"));
+    e = cudaMemset(h->part, 0, sizeof(double) * np);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(partials)"));
+  }
   e = cudaMallocHost((void**)&h->ctrl_init, sizeof(Ctrl));
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMallocHost"));
   e = cudaMallocHost((void**)&h->poll, 2 * sizeof(Ctrl));
@@ -502,6 +515,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     cfg.gamma = params->gamma; cfg.precision = h->prec; cfg.ek = h->ek;
     cfg.a = (float*)h->a; cfg.b = (float*)h->b; cfg.p = (float*)h->p; cfg.q = (const float*)h->q;
     cfg.ctrl = h->ctrl;
+    cfg.part = h->part;
     cfg.prox = prox_args<float>(h);
     std::string msg;
     int rc = jko::tc_create(cfg, &h->tc, &msg);

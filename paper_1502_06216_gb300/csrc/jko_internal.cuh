@@ -38,6 +38,54 @@ struct Ctrl {
   unsigned long long q_masked;    // count of q != 0 on the mask
 };
 
+// ---- stop protocol of the scaling loop ----
+// The b-update pass writes one residual partial per block (plain stores, one
+// slot each).  The pass that follows it (along x of xi b) reduces the partials
+// in a fixed order at its start, so every block reaches the same decision:
+// converged (residual <= tol, Sec. 3.4), budget exhausted, or non-finite;
+// block 0 records it in Ctrl.  The prox pass advances the pair counter from
+// block 0.  Every other pass only checks the recorded state.  No block waits
+// for another and no address is contended, except the rare non-finite flag.
+// Must be called by all threads of the block; returns true when the kernel
+// has to return at once.
+__device__ __forceinline__ bool stop_gate(Ctrl* ctrl, const double* part, int nparts,
+                                          bool decide, int* s_it) {
+  __shared__ int s_state[2];
+  __shared__ double s_total;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const bool first = tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+  if (tid == 0) {
+    s_state[0] = *(volatile int*)&ctrl->done;
+    s_state[1] = *(volatile int*)&ctrl->nonfinite;
+    *s_it = ctrl->it;
+  }
+  if (decide && tid < 32) {
+    double v = 0.0;
+    for (int i = tid; i < nparts; i += 32) v += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tid == 0) s_total = v;
+  }
+  __syncthreads();
+  if (s_state[0] != RUNNING) return true;
+  if (s_state[1] != 0) {
+    if (first) ctrl->done = NONFINITE;
+    return true;
+  }
+  if (!decide) return false;
+  const double total = s_total;
+  const int it = *s_it;
+  int d = RUNNING;
+  if (it > 0 && !isfinite(total)) d = NONFINITE;
+  else if (it > 0 && total <= ctrl->tol) d = CONVERGED;
+  else if (it >= ctrl->max_iter) d = MAX_ITER;
+  if (first) {
+    if (it > 0) ctrl->res_last = total;
+    if (d != RUNNING) ctrl->done = d;
+  }
+  return d != RUNNING;
+}
+
 // Energy kinds of the proximal epilogue (compile-time).
 enum : int { EK_CROWD = 0, EK_ENTROPY = 1, EK_POWER = 2 };
 

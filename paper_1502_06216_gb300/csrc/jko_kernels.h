@@ -22,9 +22,15 @@ struct PassArgs {
   const T* taps; // k(d) for d = -r..r, then simt_tap_padding() zeros
   int n_i, n_j, r;
   Ctrl* ctrl;
+  double* part;  // residual partials: one per block of the b-update pass
+  int nparts;    // number of partials (read by the deciding pass)
+  int decide;    // 1: this pass takes the stop decision (stop_gate)
 };
 
 int simt_tap_padding();
+// Blocks of a filter pass over an [n_i][n_j] input (= residual partials of the
+// b-update pass).
+int simt_pass_blocks(int n_i, int n_j);
 
 template <typename T>
 cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,

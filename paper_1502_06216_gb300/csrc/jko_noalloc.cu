@@ -42,7 +42,9 @@ constexpr size_t kOffTapsY = kOffTapsX + kTapBytes;
 constexpr size_t kOffMask = kOffTapsY + kTapBytes;
 constexpr size_t kOffStage = kOffMask + kMaxCells;          // FP64 staging of host fields
 constexpr size_t kOffCtrl = kOffStage + kMaxCells * sizeof(double);
-constexpr size_t kJkoNoallocScratchBytes = kOffCtrl + 256;
+constexpr size_t kOffPart = kOffCtrl + 256;                  // residual partials
+constexpr int kMaxParts = 256;
+constexpr size_t kJkoNoallocScratchBytes = kOffPart + kMaxParts * sizeof(double);
 static_assert(sizeof(Ctrl) <= 256, "control block must fit its slot");
 static_assert((2 * (kMaxSide - 1) + 1 + kTapPad) * sizeof(float) <= kTapBytes, "tap slot");
 
@@ -161,6 +163,9 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
   float* taps_y = (float*)(base + kOffTapsY);
   uint8_t* mask = (uint8_t*)(base + kOffMask);
   Ctrl* ctrl = (Ctrl*)(base + kOffCtrl);
+  double* part = (double*)(base + kOffPart);
+  const int nparts = jko::simt_pass_blocks(nx, ny);  // blocks of the b-update pass
+  if (nparts > kMaxParts) return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: partials slot");
 
   // energy constants (same definitions as jko_create)
   const double sigma = prm->tau / prm->gamma;
@@ -236,11 +241,15 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
       for (int half = 0; half < 2; ++half) {
         PassArgs<float> A{};
         A.ctrl = ctrl;
+        A.part = part;
+        A.nparts = nparts;
+        A.decide = half == 1 ? 1 : 0;   // the pass after the b-update decides
         A.in = half == 0 ? img[S_A] : img[S_B];
         A.out = img[S_T1];
         A.taps = taps_y;
         A.n_i = ny; A.n_j = nx; A.r = ry;
         NA_CK(jko::simt_pass<float>(jko::EPI_STORE, ek, A, P, st));
+        A.decide = 0;
         A.in = img[S_T1];
         A.out = half == 0 ? img[S_B] : img[S_A];
         A.p = img[S_P];

@@ -31,7 +31,8 @@ template <typename T, int EPI, int EK>
 __global__ void __launch_bounds__(BJ * BI)
 filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   Ctrl* ctrl = A.ctrl;
-  if (ctrl->done) return;  // uniform over the grid: set only between launches
+  __shared__ int s_it;
+  if (stop_gate(ctrl, A.part, A.nparts, A.decide != 0, &s_it)) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_k = reinterpret_cast<T*>(smem_raw);
@@ -95,7 +96,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
       for (int o = 0; o < RB; ++o)
         if (o < nout) A.out[rowoff + i0 + o] = acc[o];
     } else if (EPI == EPI_B) {
-      const bool have_prev = ctrl->it > 0;
+      const bool have_prev = s_it > 0;
 #pragma unroll
       for (int o = 0; o < RB; ++o) {
         if (o < nout) {
@@ -124,41 +125,14 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   }
   if (EPI == EPI_STORE) return;
 
-  // ---- reductions and the last-block decision ----
+  // ---- residual partial / flags / pair counter (see stop_gate) ----
   bad = warp_or(bad);
-  double res = 0.0;
-  if (EPI == EPI_B) res = block_sum((double)res_t, s_red);
-  __shared__ int s_bad;
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&s_bad, 1);
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned nblocks = gridDim.x * gridDim.y;
-    if (EPI == EPI_B && res != 0.0) atomicAdd(&ctrl->res_acc, res);
-    if (s_bad) atomicOr(&ctrl->nonfinite, 1);
-    __threadfence();
-    unsigned* counter = (EPI == EPI_B) ? &ctrl->arrive_b : &ctrl->arrive_a;
-    const unsigned prev = atomicAdd(counter, 1u);
-    if (prev == nblocks - 1) {  // last block of this launch
-      __threadfence();
-      const int nonf = atomicOr(&ctrl->nonfinite, 0);
-      const int it = ctrl->it;
-      if (EPI == EPI_B) {
-        const double total = atomicAdd(&ctrl->res_acc, 0.0);
-        if (it > 0) ctrl->res_last = total;
-        if (nonf || (it > 0 && !isfinite(total))) ctrl->done = NONFINITE;
-        else if (it > 0 && total <= ctrl->tol) ctrl->done = CONVERGED;
-        else if (it >= ctrl->max_iter) ctrl->done = MAX_ITER;
-        ctrl->res_acc = 0.0;
-      } else {
-        ctrl->it = it + 1;
-        if (nonf) ctrl->done = NONFINITE;
-      }
-      *counter = 0u;
-      __threadfence();
-    }
+  if (EPI == EPI_B) {
+    const double res = block_sum((double)res_t, s_red);
+    if (tid == 0) A.part[blockIdx.y * gridDim.x + blockIdx.x] = res;
   }
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+  if (EPI == EPI_A && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) ctrl->it = s_it + 1;
 }
 
 template <typename T, int EPI, int EK>
@@ -179,6 +153,9 @@ cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t 
 }  // namespace
 
 int simt_tap_padding() { return RB; }
+int simt_pass_blocks(int n_i, int n_j) {
+  return ((n_j + BJ - 1) / BJ) * ((n_i + BI * RB - 1) / (BI * RB));
+}
 
 template <typename T>
 cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,

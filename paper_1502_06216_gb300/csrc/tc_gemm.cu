@@ -43,19 +43,34 @@ namespace {
 constexpr int BM = 128;            // UMMA M (rows of the kernel factor per tile)
 constexpr int KB_BYTES = 128;      // K-block width in bytes (one 128-byte swizzle row)
 constexpr int MAX_STAGES = 4;
-constexpr uint32_t SMEM_BUDGET = 200 * 1024;  // operand stages per CTA
-constexpr int NT = 128;            // threads per CTA
+constexpr uint32_t SMEM_BUDGET = 212 * 1024;  // operand stages + epilogue tiles per CTA
+constexpr int NT = 512;            // threads per CTA: 16 warps, 4 per TMEM lane quadrant
+constexpr int NWG = NT / 128;      // warps sharing one quadrant (column groups)
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier polls
 
 enum : int { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_TF32 = 2 };
 
-// Bytes of one pipeline stage and the number of stages that fit the budget.
+// Bytes of one pipeline stage.
 __host__ __device__ constexpr uint32_t stage_bytes(int mode, int bn) {
   return (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)(BM + bn) * (uint32_t)KB_BYTES;
 }
-__host__ __device__ constexpr int num_stages(int mode, int bn) {
-  return SMEM_BUDGET / stage_bytes(mode, bn) < (uint32_t)MAX_STAGES
-             ? (int)(SMEM_BUDGET / stage_bytes(mode, bn))
+// Epilogue tiles kept beside the stages: b-update pass -> q (fp32) and the old
+// b (operand type, hi [+ lo]); prox pass -> e^{-sigma w} (fp32) and the staged
+// p (fp32).  Epilogue numbering as in jko_kernels.h (0 store, 1 b, 2 a).
+__host__ __device__ constexpr uint32_t epi_bytes(int mode, int epi, int bn) {
+  return epi == 0 ? 0u
+         : epi == 1 ? (uint32_t)bn * BM * 4u +
+                          (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)bn * BM *
+                              (mode == MODE_TF32 ? 4u : 2u)
+                    : 2u * (uint32_t)bn * BM * 4u;
+}
+// Bytes the producer loads into the epilogue tiles (the p tile is only stored).
+__host__ __device__ constexpr uint32_t epi_load_bytes(int mode, int epi, int bn) {
+  return epi == 2 ? (uint32_t)bn * BM * 4u : epi_bytes(mode, epi, bn);
+}
+__host__ __device__ constexpr int num_stages(int mode, int epi, int bn) {
+  return (SMEM_BUDGET - epi_bytes(mode, epi, bn)) / stage_bytes(mode, bn) < (uint32_t)MAX_STAGES
+             ? (int)((SMEM_BUDGET - epi_bytes(mode, epi, bn)) / stage_bytes(mode, bn))
              : MAX_STAGES;
 }
 
@@ -173,6 +188,29 @@ __device__ __forceinline__ void bulk_wait_all() {
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Issue-only TMEM load of 16 columns (32-bit) of this warp's 32 lanes; the
+// values are valid after tmem_wait_ld() and reg_fence16().
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Ties the registers of an issued TMEM load to the point after the wait, so
+// that the compiler schedules no use of them before it.
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
 }
 
 // Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
@@ -344,6 +382,58 @@ __device__ __forceinline__ void stage16(unsigned char* st_hi, unsigned char* st_
   }
 }
 
+// 16 fp32 of row r, columns 16c .. 16c+15, of a 128-byte-swizzled fp32 tile
+// (column blocks of 32 floats x 128 rows, 16-byte chunk k of row r at k ^ (r & 7)).
+__device__ __forceinline__ void smem_ld_f32x16(const unsigned char* reg, int r, int c,
+                                               float (&o)[16]) {
+  const int cb = c >> 1, k0 = (c & 1) * 4;
+  const unsigned char* row = reg + cb * (BM * 128) + r * 128;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 t = *reinterpret_cast<const float4*>(row + (((k0 + q) ^ (r & 7)) << 4));
+    o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void smem_st_f32x16(unsigned char* reg, int r, int c,
+                                               const float (&v)[16]) {
+  const int cb = c >> 1, k0 = (c & 1) * 4;
+  unsigned char* row = reg + cb * (BM * 128) + r * 128;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<float4*>(row + (((k0 + q) ^ (r & 7)) << 4)) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+// 16 operand values (hi [+ lo]) of row r, columns 16c .., from swizzled tiles.
+template <int MODE>
+__device__ __forceinline__ void smem_ld_op16(const unsigned char* hi, const unsigned char* lo,
+                                             int r, int c, float (&o)[16]) {
+  if constexpr (MODE == MODE_TF32) {
+    smem_ld_f32x16(hi, r, c, o);
+  } else {
+    const int cb = c >> 2, k0 = (c & 3) * 2;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const size_t off = cb * (BM * 128) + r * 128 + (((k0 + q) ^ (r & 7)) << 4);
+      const uint4 t = *reinterpret_cast<const uint4*>(hi + off);
+      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = unpack_bf16x2(w[k]);
+        o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
+      }
+      if constexpr (MODE == MODE_BF16X3) {
+        const uint4 u = *reinterpret_cast<const uint4*>(lo + off);
+        const uint32_t z[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(z[k]);
+          o[8 * q + 2 * k] += f.x; o[8 * q + 2 * k + 1] += f.y;
+        }
+      }
+    }
+  }
+}
+
 struct TcPassArgs {
   int M, N, Kdim;         // D is M x N, contraction length Kdim (= M)
   int r;                  // band radius of the kernel factor
@@ -354,6 +444,10 @@ struct TcPassArgs {
   const float* q;         // EPI_B
   Ctrl* ctrl;
   ProxArgs<float> P;
+  int tma_epi;            // 1: epilogue tiles moved by TMA (fp32 fields with nx % 4 == 0)
+  double* part;           // residual partials, one per block of the b-update pass
+  int nparts;             // partials read by the deciding pass
+  int decide;             // 1: this pass takes the stop decision (stop_gate)
 };
 
 template <int MODE, int EPI, int EK, int BN>
@@ -361,6 +455,7 @@ __global__ void __launch_bounds__(NT, 1)
 tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
                const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
                const __grid_constant__ CUtensorMap mapO_hi, const __grid_constant__ CUtensorMap mapO_lo,
+               const __grid_constant__ CUtensorMap mapF, const __grid_constant__ CUtensorMap mapP,
                TcPassArgs args) {
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;                  // elements per K-block
@@ -369,21 +464,30 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   constexpr uint32_t A_BYTES = BM * KB_BYTES;
   constexpr uint32_t B_BYTES = BN * KB_BYTES;
   constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
-  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int STAGES = num_stages(MODE, EPI, BN);
+  constexpr uint32_t EPI_BYTES = epi_bytes(MODE, EPI, BN);
+  // the prox pass loads e^{-sigma w} only for the congestion/potential kind
+  constexpr uint32_t EPI_LOAD =
+      (EPI == EPI_A && EK != EK_CROWD) ? 0u : epi_load_bytes(MODE, EPI, BN);
+  constexpr uint32_t F32_TILE = (uint32_t)BN * BM * 4u;   // one fp32 epilogue tile
   static_assert(STAGE_BYTES == stage_bytes(MODE, BN), "stage size");
   static_assert(STAGES >= 2, "at least two stages");
   constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
   constexpr uint32_t IDESC = make_idesc<MODE>(BM, BN);
 
   Ctrl* ctrl = args.ctrl;
-  if (ctrl->done) return;  // uniform: set only between launches
+  __shared__ int s_it;
+  if (stop_gate(ctrl, args.part, args.nparts, args.decide != 0, &s_it)) return;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full_bar = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  unsigned char* epi_f = smem + STAGES * STAGE_BYTES;   // q (b pass) or e^{-sigma w} (prox)
+  unsigned char* epi_g = epi_f + F32_TILE;                // old b (b pass) or p (prox)
+  uint64_t* full_bar = (uint64_t*)(smem + STAGES * STAGE_BYTES + EPI_BYTES);
   uint64_t* empty_bar = full_bar + STAGES;
   uint64_t* accum_bar = empty_bar + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 1);
+  uint64_t* epi_bar = accum_bar + 1;
+  uint32_t* tmem_slot = (uint32_t*)(epi_bar + 1);
   __shared__ double s_red[33];
   __shared__ int s_fault;
 
@@ -406,6 +510,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(accum_bar, 1);
+    mbar_init(epi_bar, 1);
     fence_mbar_init();
     tma_prefetch_desc(&mapA_hi);
     tma_prefetch_desc(&mapB_hi);
@@ -419,9 +524,28 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  const bool tma_epi = EPI != EPI_STORE && args.tma_epi;
   bool ok = true;
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
+    // ---- TMA producer: epilogue tiles first (independent of the MMAs) ----
+    if (tma_epi) {
+      mbar_arrive_expect_tx(epi_bar, EPI_LOAD);
+      if (EPI == EPI_B || EK == EK_CROWD) {
+#pragma unroll
+        for (int cb = 0; cb < BN / 32; ++cb)
+          tma_load_2d(epi_f + cb * (BM * 128), &mapF, epi_bar, n0 + cb * 32, m0);
+      }
+      if constexpr (EPI == EPI_B) {
+        constexpr int CBO = BN * (int)sizeof(T) / 128;
+        constexpr int KEO = 128 / (int)sizeof(T);
+#pragma unroll
+        for (int cb = 0; cb < CBO; ++cb) {
+          tma_load_2d(epi_g + cb * (BM * 128), &mapO_hi, epi_bar, n0 + cb * KEO, m0);
+          if constexpr (NSPLIT == 2)
+            tma_load_2d(epi_g + (CBO + cb) * (BM * 128), &mapO_lo, epi_bar, n0 + cb * KEO, m0);
+        }
+      }
+    }
     for (int i = 0; i < nkb && ok; ++i) {
       const int s = i % STAGES;
       if (i >= STAGES) ok = mbar_wait(&empty_bar[s], ((i / STAGES) - 1) & 1);
@@ -469,6 +593,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
 
   // ---- epilogue: all four warps, warp w owns TMEM lanes 32w .. 32w+31 ----
   bool have = mbar_wait(accum_bar, 0);
+  if (have && tma_epi) have = mbar_wait(epi_bar, 0);
   if (!have) atomicOr(&s_fault, 1);
   __syncwarp();
   tc_fence_after();
@@ -480,20 +605,38 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   static_assert((NSPLIT * CB) * OUT_BLOCK <= STAGES * STAGE_BYTES, "staging fits the stages");
   unsigned char* st_hi = smem;
   unsigned char* st_lo = smem + CB * OUT_BLOCK;
-  const int rl = warp * 32 + lane;
+  // warp w reads TMEM lanes 32 (w % 4) .. +31 (its quadrant) and the column
+  // group w / 4 of the tile: chunks [g CPG, (g + 1) CPG) of 16 columns
+  const int quad = warp & 3;
+  const int grp = warp >> 2;
+  const int rl = quad * 32 + lane;
   const int m = m0 + rl;
   const bool row_ok = m < args.M;
   const bool vec_in = (args.N & 3) == 0;
   float res_f = 0.0f;  // this thread's residual terms (FP32, one rounding each)
   int bad = 0;
-  const bool have_prev = (EPI == EPI_B) ? (ctrl->it > 0) : false;
+  const bool have_prev = (EPI == EPI_B) ? (s_it > 0) : false;
   const T* cur_hi = (const T*)args.out_hi;
   const T* cur_lo = (const T*)args.out_lo;
   if (have) {
-#pragma unroll 1
-    for (int c = 0; c < BN / 16; ++c) {
+    // all TMEM loads of this thread's row first, one wait, then the chunks
+    // unrolled so that their shared-memory loads and arithmetic overlap
+    constexpr int NCH = BN / 16 / NWG;   // chunks per thread
+    static_assert(NCH >= 1 && NCH * 16 * NWG == BN, "column groups cover the tile");
+    uint32_t racc[NCH][16];
+#pragma unroll
+    for (int cc = 0; cc < NCH; ++cc)
+      tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)((grp * NCH + cc) * 16),
+                      racc[cc]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int cc = 0; cc < NCH; ++cc) reg_fence16(racc[cc]);
+#pragma unroll
+    for (int cc = 0; cc < NCH; ++cc) {
+      const int c = grp * NCH + cc;
       float v[16];
-      tmem_ld16(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[cc][j]);
       const int nb = n0 + c * 16;
       int cnt = args.N - nb;
       cnt = !row_ok || cnt < 0 ? 0 : (cnt > 16 ? 16 : cnt);
@@ -504,8 +647,15 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       } else if (EPI == EPI_B) {
         const size_t irow = (size_t)m * args.N + nb;   // q is [M][N] unpadded
         float qv[16], bo[16];
-        load_f32x16(args.q + (cnt ? irow : 0), cnt, vec_in, qv);
-        if (have_prev) load_op16<MODE>(cur_hi, cur_lo, cnt ? (size_t)m * args.pitch_out + nb : 0, cnt, bo);
+        if (tma_epi) {
+          smem_ld_f32x16(epi_f, rl, c, qv);
+          if (have_prev)
+            smem_ld_op16<MODE>(epi_g, epi_g + (BN * (int)sizeof(T) / 128) * (BM * 128), rl, c, bo);
+        } else {
+          load_f32x16(args.q + (cnt ? irow : 0), cnt, vec_in, qv);
+          if (have_prev)
+            load_op16<MODE>(cur_hi, cur_lo, cnt ? (size_t)m * args.pitch_out + nb : 0, cnt, bo);
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           if (j < cnt) {
@@ -519,7 +669,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       } else {  // EPI_A
         const size_t irow = (size_t)m * args.N + nb;
         float ev[16], pv[16];
-        if (EK == EK_CROWD) load_f32x16(args.P.E + (cnt ? irow : 0), cnt, vec_in, ev);
+        if (EK == EK_CROWD) {
+          if (tma_epi) smem_ld_f32x16(epi_f, rl, c, ev);
+          else load_f32x16(args.P.E + (cnt ? irow : 0), cnt, vec_in, ev);
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           if (j < cnt) {
@@ -533,7 +686,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
             pv[j] = 0.0f;
           }
         }
-        if (cnt) store_f32x16(args.p + irow, cnt, vec_in, pv);
+        if (tma_epi) smem_st_f32x16(epi_g, rl, c, pv);
+        else if (cnt) store_f32x16(args.p + irow, cnt, vec_in, pv);
       }
       stage16<MODE>(st_hi, st_lo, rl, c, o);
     }
@@ -548,6 +702,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       tma_store_2d(&mapO_hi, st_hi + cb * OUT_BLOCK, n0 + cb * KEo, m0);
       if constexpr (NSPLIT == 2) tma_store_2d(&mapO_lo, st_lo + cb * OUT_BLOCK, n0 + cb * KEo, m0);
     }
+    if (EPI == EPI_A && tma_epi) {
+#pragma unroll
+      for (int cb = 0; cb < BN / 32; ++cb)
+        tma_store_2d(&mapP, epi_g + cb * (BM * 128), n0 + cb * 32, m0);
+    }
     bulk_commit();
     bulk_wait_all();
   }
@@ -557,42 +716,15 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
     if (threadIdx.x == 0 && s_fault) atomicOr(&ctrl->nonfinite, 2);
     return;
   }
-  // ---- residual / flags and the last-block decision ----
+  // ---- residual partial / flags / pair counter (see stop_gate) ----
   bad = warp_or(bad);
-  double res = 0.0;
-  if (EPI == EPI_B) res = block_sum((double)res_f, s_red);
-  __shared__ int s_bad;
-  if (threadIdx.x == 0) s_bad = 0;
-  __syncthreads();
-  if (lane == 0 && bad) atomicOr(&s_bad, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned nblocks = gridDim.x * gridDim.y;
-    if (EPI == EPI_B && res != 0.0) atomicAdd(&ctrl->res_acc, res);
-    if (s_bad) atomicOr(&ctrl->nonfinite, 1);
-    if (s_fault) atomicOr(&ctrl->nonfinite, 2);
-    __threadfence();
-    unsigned* counter = (EPI == EPI_B) ? &ctrl->arrive_b : &ctrl->arrive_a;
-    const unsigned prev = atomicAdd(counter, 1u);
-    if (prev == nblocks - 1) {
-      __threadfence();
-      const int nonf = atomicOr(&ctrl->nonfinite, 0);
-      const int it = ctrl->it;
-      if (EPI == EPI_B) {
-        const double total = atomicAdd(&ctrl->res_acc, 0.0);
-        if (it > 0) ctrl->res_last = total;
-        if (nonf || (it > 0 && !isfinite(total))) ctrl->done = NONFINITE;
-        else if (it > 0 && total <= ctrl->tol) ctrl->done = CONVERGED;
-        else if (it >= ctrl->max_iter) ctrl->done = MAX_ITER;
-        ctrl->res_acc = 0.0;
-      } else {
-        ctrl->it = it + 1;
-        if (nonf) ctrl->done = NONFINITE;
-      }
-      *counter = 0u;
-      __threadfence();
-    }
+  if (EPI == EPI_B) {
+    const double res = block_sum((double)res_f, s_red);
+    if (threadIdx.x == 0) args.part[blockIdx.y * gridDim.x + blockIdx.x] = res;
   }
+  if (lane == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+  if (threadIdx.x == 0 && s_fault) atomicOr(&ctrl->nonfinite, 2);
+  if (EPI == EPI_A && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) ctrl->it = s_it + 1;
 }
 
 // a = 1 in operand precision (cold start), padded columns included.
@@ -658,6 +790,8 @@ struct TcPlan {
   void* img_t[2] = {nullptr, nullptr};   // [nx][py]
   CUtensorMap mKx[2], mKy[2], mA[2], mB[2], mT[2];  // operand loads
   CUtensorMap sA[2], sB[2], sT[2];                  // epilogue stores (box 128 rows)
+  CUtensorMap fQ, fE, fP;                           // fp32 fields q, e^{-sigma w}, p
+  int tma_epi = 0;
   double flops[4] = {0, 0, 0, 0};
 };
 
@@ -665,19 +799,20 @@ namespace {
 
 template <int MODE, int EPI, int EK, int BN>
 size_t smem_bytes() {
-  constexpr int ST = num_stages(MODE, BN);
-  return (size_t)ST * stage_bytes(MODE, BN) + 1024 + (2 * ST + 1) * 8 + 16;
+  constexpr int ST = num_stages(MODE, EPI, BN);
+  return (size_t)ST * stage_bytes(MODE, BN) + epi_bytes(MODE, EPI, BN) + 1024 + (2 * ST + 2) * 8 +
+         16;
 }
 
 struct Maps {
-  const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo, *o_hi, *o_lo;
+  const CUtensorMap *a_hi, *a_lo, *b_hi, *b_lo, *o_hi, *o_lo, *f, *pm;
 };
 
 template <int MODE, int EPI, int EK, int BN>
 cudaError_t launch_pass(const Maps& M, const TcPassArgs& args, cudaStream_t st) {
   dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM);
   tc_pass_kernel<MODE, EPI, EK, BN><<<grid, NT, smem_bytes<MODE, EPI, EK, BN>(), st>>>(
-      *M.a_hi, *M.a_lo, *M.b_hi, *M.b_lo, *M.o_hi, *M.o_lo, args);
+      *M.a_hi, *M.a_lo, *M.b_hi, *M.b_lo, *M.o_hi, *M.o_lo, *M.f, *M.pm, args);
   return cudaGetLastError();
 }
 
@@ -698,11 +833,17 @@ cudaError_t set_attrs_bn() {
   return set_attr<MODE, EPI_A, EK_POWER, BN>();
 }
 
+// 128-wide tiles exist for the forms whose epilogue tiles leave room for at
+// least two pipeline stages (not BF16X3).
+template <int MODE>
+constexpr bool has_bn128() { return MODE != MODE_BF16X3; }
+
 template <int MODE>
 cudaError_t set_attrs() {
   cudaError_t e = set_attrs_bn<MODE, 64>();
   if (e != cudaSuccess) return e;
-  return set_attrs_bn<MODE, 128>();
+  if constexpr (has_bn128<MODE>()) return set_attrs_bn<MODE, 128>();
+  return cudaSuccess;
 }
 
 template <int MODE, int BN>
@@ -717,7 +858,9 @@ cudaError_t dispatch_epi(int epi, int ek, const Maps& M, const TcPassArgs& args,
 template <int MODE>
 cudaError_t dispatch_bn(int bn, int epi, int ek, const Maps& M, const TcPassArgs& args,
                         cudaStream_t st) {
-  if (bn == 128) return dispatch_epi<MODE, 128>(epi, ek, M, args, st);
+  if constexpr (has_bn128<MODE>()) {
+    if (bn == 128) return dispatch_epi<MODE, 128>(epi, ek, M, args, st);
+  }
   return dispatch_epi<MODE, 64>(epi, ek, M, args, st);
 }
 
@@ -806,6 +949,7 @@ int create_typed(TcPlan* P, std::string* msg) {
   auto pick = [](int M, int N) { return ((M + BM - 1) / BM) * ((N + 127) / 128) >= 152 ? 128 : 64; };
   P->bn_x = pick(nx, ny);  // pass over x: M = nx, N = ny
   P->bn_y = pick(ny, nx);  // pass over y: M = ny, N = nx
+  if (P->mode == MODE_BF16X3) P->bn_x = P->bn_y = 64;
   // tensor maps (hi and lo; lo maps alias hi when unused)
   const int m = P->mode;
   for (int s = 0; s < 2; ++s) {
@@ -819,6 +963,16 @@ int create_typed(TcPlan* P, std::string* msg) {
               make_map(&P->sB[s], P->img_b[si], m, ny, nx, P->px, BM) &&
               make_map(&P->sT[s], P->img_t[si], m, nx, ny, P->py, BM);
     if (!ok) { *msg = "cuTensorMapEncodeTiled failed"; return 2; }
+  }
+  // fp32 fields [ny][nx] (q, e^{-sigma w}, p) as TMA tiles when rows are 16-byte multiples
+  P->tma_epi = (nx % 4 == 0) ? 1 : 0;
+  P->fQ = P->fE = P->fP = P->mKx[0];
+  if (P->tma_epi) {
+    bool ok = make_map(&P->fQ, (void*)c.q, MODE_TF32, ny, nx, nx, BM) &&
+              make_map(&P->fP, (void*)c.p, MODE_TF32, ny, nx, nx, BM);
+    if (ok && c.ek == EK_CROWD && c.prox.E)
+      ok = make_map(&P->fE, (void*)c.prox.E, MODE_TF32, ny, nx, nx, BM);
+    if (!ok) { *msg = "cuTensorMapEncodeTiled failed (fields)"; return 2; }
   }
   // executed flops per pass
   const int KE = m == MODE_TF32 ? 32 : 64;
@@ -883,6 +1037,8 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
   a.P = c.prox;
   a.q = c.q;
   a.p = c.p;
+  a.part = c.part;
+  a.nparts = ((c.nx + P->bn_y - 1) / P->bn_y) * ((c.ny + BM - 1) / BM);  // b-update grid
   Maps mp{};
   int bn, epi;
   if (over_x) {  // K_x . image^T -> T^T [nx][ny]
@@ -893,6 +1049,8 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
     mp.b_hi = half == 0 ? &P->mA[0] : &P->mB[0];
     mp.b_lo = half == 0 ? &P->mA[1] : &P->mB[1];
     mp.o_hi = &P->sT[0]; mp.o_lo = &P->sT[1];
+    mp.f = mp.pm = &P->mKx[0];   // unused by the plain pass
+    a.decide = half == 1 ? 1 : 0;  // the pass after the b-update decides
     bn = P->bn_x;
     epi = EPI_STORE;
   } else {       // K_y . T^T^T -> [ny][nx] with the epilogue
@@ -904,6 +1062,9 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
     mp.b_hi = &P->mT[0]; mp.b_lo = &P->mT[1];
     mp.o_hi = half == 0 ? &P->sB[0] : &P->sA[0];
     mp.o_lo = half == 0 ? &P->sB[1] : &P->sA[1];
+    mp.f = half == 0 ? &P->fQ : &P->fE;
+    mp.pm = &P->fP;
+    a.tma_epi = P->tma_epi;
     bn = P->bn_y;
     epi = half == 0 ? EPI_B : EPI_A;
   }
@@ -915,6 +1076,11 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
 }
 
 double tc_pass_flops(const TcPlan* P, int which) { return P->flops[which & 3]; }
+
+int tc_partials(int nx, int ny) {
+  // upper bound over the tile widths: 64-column tiles give the most blocks
+  return ((nx + 63) / 64) * ((ny + BM - 1) / BM);
+}
 
 void tc_destroy(TcPlan* P) {
   if (!P) return;

@@ -20,8 +20,12 @@ struct TcConfig {
   float* p;
   const float* q;
   Ctrl* ctrl;
+  double* part;   // residual partials (tc_partials(cfg) doubles)
   ProxArgs<float> prox;
 };
+
+// Number of residual partials (blocks of the b-update pass) for a grid.
+int tc_partials(int nx, int ny);
 
 struct TcPlan;
 
