@@ -42,7 +42,7 @@ namespace {
 
 constexpr int BM = 128;            // UMMA M (rows of the kernel factor per tile)
 constexpr int KB_BYTES = 128;      // K-block width in bytes (one 128-byte swizzle row)
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGES = 8;
 constexpr uint32_t SMEM_BUDGET = 212 * 1024;  // operand stages + epilogue tiles per CTA
 constexpr int NT = 512;            // threads per CTA: 16 warps, 4 per TMEM lane quadrant
 constexpr int NWG = NT / 128;      // warps sharing one quadrant (column groups)
@@ -116,6 +116,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
+// Programmatic dependent launch: the next kernel of the stream may start its
+// set-up once every CTA of this one has signalled; griddepcontrol.wait blocks
+// until the preceding kernel has completed and its writes are visible.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_u32(dst)),
@@ -477,7 +485,6 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
 
   Ctrl* ctrl = args.ctrl;
   __shared__ int s_it;
-  if (stop_gate(ctrl, args.part, args.nparts, args.decide != 0, &s_it)) return;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -523,6 +530,17 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+
+  // Everything above touches no data of the preceding kernel, so it overlaps
+  // that kernel's tail; from here on its results are read.
+  pdl_launch_dependents();
+  pdl_wait();
+  if (stop_gate(ctrl, args.part, args.nparts, args.decide != 0, &s_it)) {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+    return;
+  }
 
   const bool tma_epi = EPI != EPI_STORE && args.tma_epi;
   bool ok = true;
@@ -810,10 +828,18 @@ struct Maps {
 
 template <int MODE, int EPI, int EK, int BN>
 cudaError_t launch_pass(const Maps& M, const TcPassArgs& args, cudaStream_t st) {
-  dim3 grid((args.N + BN - 1) / BN, (args.M + BM - 1) / BM);
-  tc_pass_kernel<MODE, EPI, EK, BN><<<grid, NT, smem_bytes<MODE, EPI, EK, BN>(), st>>>(
-      *M.a_hi, *M.a_lo, *M.b_hi, *M.b_lo, *M.o_hi, *M.o_lo, *M.f, *M.pm, args);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((args.N + BN - 1) / BN, (args.M + BM - 1) / BM);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem_bytes<MODE, EPI, EK, BN>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_pass_kernel<MODE, EPI, EK, BN>, *M.a_hi, *M.a_lo, *M.b_hi,
+                            *M.b_lo, *M.o_hi, *M.o_lo, *M.f, *M.pm, args);
 }
 
 template <int MODE, int EPI, int EK, int BN>
