@@ -207,6 +207,32 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------------------
 
+def run_batched(args, jko, dev, barrier):
+    """256 independent crowd / porous flows of sizes {64,128,256,512}^2, 10 JKO
+    steps each, advanced together by one batch (graphs with a branch per flow)."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pbs = inputs.batched_problems(256)
+    out = {"workload": "256 flows (crowd even / porous odd), n in {64,128,256,512}, "
+                       "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6"}
+    for form in ("BF16X3", "FP32"):
+        b = jko.jko_batch_create(pbs, precision=jko.Precision[form])
+        p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
+        jko.jko_batch_flow(b, p0s, 1, want_final=False)        # warm-up
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, table = jko.jko_batch_flow(b, p0s, 10, want_final=False)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for row in table for i in row)
+        out[form] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
+                     "seconds": secs, "pairs": iters}
+        jko.jko_batch_destroy(b)
+    return out
+
+
 TC_FORMS = ("BF16", "BF16X3", "TF32")
 ALL_FORMS = TC_FORMS + ("FP32",)
 ERR_BAR = 1e-3
@@ -371,6 +397,8 @@ def run_ours(args):
                "sample": f"{k_it} FP64 scaling-loop iterations of one {args.n}^2 JKO step "
                          f"from the warmed-up state ({secs:.1f} s, NumPy/BLAS, separable xi)"}
 
+    batched = run_batched(args, jko, dev, barrier) if args.batched else None
+
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
                  "steps_timed": len(runs[f]["infos"]),
                  "rel_l1_vs_fp32_form": errs[f]} for f in forms_to_run}
@@ -401,6 +429,8 @@ def run_ours(args):
             "gpu_launches": R["launches"],
             "clocks": clocks,
         }
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
     for r in runs.values():
         jko.jko_destroy(r["h"])
@@ -421,6 +451,8 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the 256-flow batched workload (adds a 'batched' key)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

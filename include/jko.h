@@ -183,6 +183,35 @@ jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* params,
                             const jko_energy* energy, const void* q_dev, void* p_out_dev,
                             void* stream, jko_step_info* info);
 
+/* ---- batched flows (many independent problems advanced together) ---- */
+typedef struct jko_batch jko_batch;
+
+/* Creates n_flows independent flows, flow f with grids[f], params[f] and
+ * energies[f] (the same rules as jko_create; each flow may have its own grid
+ * size, gamma, tau, energy and precision; all share params[].check_every).
+ * Each JKO step of the batch runs as three CUDA graphs whose parallel
+ * branches are the flows, so small and large flows share the GPU; a flow that
+ * has met its stopping rule (Sec. 3.4) turns its remaining kernels into
+ * no-ops.  Errors as jko_create, with the failing flow named in
+ * jko_batch_last_error(NULL). */
+jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params* params,
+                            const jko_energy* energies, void* stream, jko_batch** out);
+
+/* n_steps steps of every flow (Eq. smooth-jko) from p0_dev[f] (device image of
+ * flow f, double for JKO_FP64 flows, float otherwise; validated as in
+ * jko_step).  p_final_dev[f] (array and entries may be NULL) receives the last
+ * iterate; infos (may be NULL) receives n_steps * n_flows reports, step-major
+ * (infos[t * n_flows + f]).  Returns the worst status over flows and steps. */
+jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
+                          void* const* p_final_dev, jko_step_info* infos);
+
+/* Frees the batch and its flows (NULL is accepted). */
+jko_status jko_batch_destroy(jko_batch* b);
+
+/* Message of the last error on b, or of the last failed jko_batch_create when
+ * b is NULL (never NULL; "" when none). */
+const char* jko_batch_last_error(const jko_batch* b);
+
 /* Re-targets the handle to another stream (a cudaStream_t). */
 jko_status jko_set_stream(jko_handle* h, void* stream);
 

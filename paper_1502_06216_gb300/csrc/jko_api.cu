@@ -661,3 +661,313 @@ const char* jko_build_info(void) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched flows: n independent flows (own grid, parameters, energy and
+// precision each) advanced together.  Each JKO step runs three CUDA graphs
+// whose branches are the flows (fork-join capture over worker streams): the
+// prologue (control reset, cold start a = 1), a chunk of `check_every` pairs,
+// and the finalisation (FP64 mass, renormalisation into the flow's input
+// buffer for the next step).  Flows that have stopped turn their kernels into
+// no-ops; one gather kernel and one small copy poll every flow at once.
+// ---------------------------------------------------------------------------
+struct jko_batch {
+  int n = 0;
+  std::vector<jko_handle*> h;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> cap;     // cap[0] is the capture root
+  std::vector<cudaEvent_t> ev;       // fork / join events
+  cudaGraphExec_t g_pro = nullptr, g_chunk = nullptr, g_fin = nullptr;
+  int C = 16;
+  int max_iter = 1;
+  Ctrl** ctrl_ptrs = nullptr;        // device: control block of each flow
+  Ctrl* ctrl_all = nullptr;          // device: gathered control blocks
+  Ctrl* host_all = nullptr;          // pinned copy
+  int* done_dev = nullptr;           // device: gathered stop states
+  int* done_host = nullptr;          // pinned, 2 slots of n
+  cudaEvent_t ev_poll[2] = {nullptr, nullptr};
+  int last_iters = 0;
+  std::string err;
+};
+
+namespace {
+
+jko_status batch_err(jko_batch* b, jko_status st, const std::string& msg) {
+  if (b) b->err = msg; else g_create_err = msg;
+  return st;
+}
+
+#define BCK(b, call)                                                        \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return batch_err(b, e_ == cudaErrorMemoryAllocation ? JKO_ERR_OOM : JKO_ERR_CUDA, \
+                       std::string(#call) + ": " + cudaGetErrorName(e_));   \
+  } while (0)
+
+void free_batch(jko_batch* b) {
+  if (!b) return;
+  for (auto* h : b->h) free_handle(h);
+  if (b->g_pro) cudaGraphExecDestroy(b->g_pro);
+  if (b->g_chunk) cudaGraphExecDestroy(b->g_chunk);
+  if (b->g_fin) cudaGraphExecDestroy(b->g_fin);
+  for (auto s : b->cap) if (s) cudaStreamDestroy(s);
+  for (auto e : b->ev) if (e) cudaEventDestroy(e);
+  for (auto e : b->ev_poll) if (e) cudaEventDestroy(e);
+  if (b->ctrl_ptrs) cudaFree(b->ctrl_ptrs);
+  if (b->ctrl_all) cudaFree(b->ctrl_all);
+  if (b->done_dev) cudaFree(b->done_dev);
+  if (b->host_all) cudaFreeHost(b->host_all);
+  if (b->done_host) cudaFreeHost(b->done_host);
+  delete b;
+}
+
+cudaError_t flow_prologue(jko_handle* h, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if (h->tc) return jko::tc_begin_step(h->tc, s);
+  if (h->fp64) return jko::launch_fill<double>((double*)h->a, 1.0, h->N, s);
+  return jko::launch_fill<float>((float*)h->a, 1.0f, h->N, s);
+}
+
+cudaError_t flow_chunk(jko_handle* h, int C, cudaStream_t s) {
+  for (int i = 0; i < C; ++i) {
+    cudaError_t e = enqueue_pair(h, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t flow_finalize_t(jko_handle* h, cudaStream_t s) {
+  ProxArgs<T> P = prox_args<T>(h);
+  cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->N, P, h->ctrl, s);
+  if (e != cudaSuccess) return e;
+  // the step output becomes the input of the next step
+  return jko::launch_finalize_write<T>((const T*)h->p, (T*)h->q, h->N, h->prm.renormalize,
+                                       h->ctrl, s);
+}
+
+cudaError_t flow_finalize(jko_handle* h, cudaStream_t s) {
+  return h->fp64 ? flow_finalize_t<double>(h, s) : flow_finalize_t<float>(h, s);
+}
+
+// Captures one graph whose branches run `per_flow` for every flow, joined on
+// the root stream, followed by `tail` on the root.
+template <class F, class G>
+jko_status capture_batch(jko_batch* b, F per_flow, G tail, cudaGraphExec_t* out) {
+  cudaStream_t root = b->cap[0];
+  const int nw = (int)b->cap.size() - 1;
+  cudaGraph_t g = nullptr;
+  BCK(b, cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b->ev[0], root);
+  std::vector<char> used(nw, 0);
+  for (int f = 0; f < b->n && e == cudaSuccess; ++f) {
+    const int k = f % nw;
+    cudaStream_t s = b->cap[1 + k];
+    if (!used[k]) { e = cudaStreamWaitEvent(s, b->ev[0], 0); used[k] = 1; }
+    if (e == cudaSuccess) e = per_flow(b->h[f], s);
+  }
+  for (int k = 0; k < nw && e == cudaSuccess; ++k) {
+    if (!used[k]) continue;
+    e = cudaEventRecord(b->ev[1 + k], b->cap[1 + k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(root, b->ev[1 + k], 0);
+  }
+  if (e == cudaSuccess) e = tail(root);
+  cudaError_t e2 = cudaStreamEndCapture(root, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return batch_err(b, JKO_ERR_CUDA, std::string("batch graph capture: ") +
+                                          cudaGetErrorName(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  BCK(b, e);
+  return JKO_OK;
+}
+
+template <typename T>
+jko_status check_input(jko_handle* h, const T* q, int flow, jko_batch* b) {
+  cudaStream_t st = h->stream;
+  ProxArgs<T> P = prox_args<T>(h);
+  BCK(b, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  BCK(b, jko::launch_validate<T>(q, h->N, P, h->ctrl, st));
+  BCK(b, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  BCK(b, cudaStreamSynchronize(st));
+  const Ctrl& c = h->poll[0];
+  if (c.q_bad || c.q_neg || std::fabs(c.q_sum - 1.0) > 1e-3 || c.q_masked || c.q_over) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "flow %d: p0 must be finite, >= 0, sum to 1, vanish on the mask "
+                              "and stay below kappa", flow);
+    return batch_err(b, JKO_ERR_INVALID_ARG, buf);
+  }
+  return JKO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params* params,
+                            const jko_energy* energies, void* stream, jko_batch** out) {
+  if (!out) return batch_err(nullptr, JKO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_flows < 1 || !grids || !params || !energies)
+    return batch_err(nullptr, JKO_ERR_INVALID_ARG, "n_flows < 1 or NULL arrays");
+  jko_batch* b = new jko_batch();
+  b->n = n_flows;
+  b->stream = (cudaStream_t)stream;
+  b->C = params[0].check_every > 0 ? params[0].check_every : 16;
+  auto fail = [&](jko_status st) {
+    g_create_err = b->err;
+    free_batch(b);
+    return st;
+  };
+  for (int f = 0; f < n_flows; ++f) {
+    if (params[f].check_every != params[0].check_every)
+      return fail(batch_err(b, JKO_ERR_INVALID_ARG, "all flows must share check_every"));
+    jko_handle* h = nullptr;
+    jko_status s = jko_create(&grids[f], &params[f], &energies[f], stream, &h);
+    if (s != JKO_OK) {
+      char buf[64];
+      snprintf(buf, sizeof buf, "flow %d: ", f);
+      return fail(batch_err(b, s, buf + g_create_err));
+    }
+    b->h.push_back(h);
+    b->max_iter = std::max(b->max_iter, params[f].max_iter);
+  }
+  const int nw = std::min(n_flows, 64);
+  b->cap.assign(nw + 1, nullptr);
+  b->ev.assign(nw + 1, nullptr);
+  for (auto& s : b->cap)
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(batch_err(b, JKO_ERR_CUDA, "cudaStreamCreate"));
+  for (auto& e : b->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(batch_err(b, JKO_ERR_CUDA, "cudaEventCreate"));
+  for (auto& e : b->ev_poll)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(batch_err(b, JKO_ERR_CUDA, "cudaEventCreate"));
+  std::vector<Ctrl*> ptrs(n_flows);
+  for (int f = 0; f < n_flows; ++f) ptrs[f] = b->h[f]->ctrl;
+  if (cudaMalloc((void**)&b->ctrl_ptrs, sizeof(Ctrl*) * n_flows) != cudaSuccess ||
+      cudaMalloc((void**)&b->ctrl_all, sizeof(Ctrl) * n_flows) != cudaSuccess ||
+      cudaMalloc((void**)&b->done_dev, sizeof(int) * n_flows) != cudaSuccess ||
+      cudaMallocHost((void**)&b->host_all, sizeof(Ctrl) * n_flows) != cudaSuccess ||
+      cudaMallocHost((void**)&b->done_host, 2 * sizeof(int) * n_flows) != cudaSuccess)
+    return fail(batch_err(b, JKO_ERR_OOM, "batch allocation"));
+  if (cudaMemcpy(b->ctrl_ptrs, ptrs.data(), sizeof(Ctrl*) * n_flows, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return fail(batch_err(b, JKO_ERR_CUDA, "upload of control pointers"));
+  const int C = b->C;
+  jko_status s = capture_batch(
+      b, [](jko_handle* h, cudaStream_t st) { return flow_prologue(h, st); },
+      [](cudaStream_t) { return cudaSuccess; }, &b->g_pro);
+  if (s != JKO_OK) return fail(s);
+  s = capture_batch(
+      b, [C](jko_handle* h, cudaStream_t st) { return flow_chunk(h, C, st); },
+      [b](cudaStream_t root) { return jko::launch_gather_done(b->ctrl_ptrs, b->done_dev, b->n, root); },
+      &b->g_chunk);
+  if (s != JKO_OK) return fail(s);
+  s = capture_batch(
+      b, [](jko_handle* h, cudaStream_t st) { return flow_finalize(h, st); },
+      [b](cudaStream_t root) { return jko::launch_gather_ctrl(b->ctrl_ptrs, b->ctrl_all, b->n, root); },
+      &b->g_fin);
+  if (s != JKO_OK) return fail(s);
+  *out = b;
+  return JKO_OK;
+}
+
+jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
+                          void* const* p_final_dev, jko_step_info* infos) {
+  if (!b) return batch_err(nullptr, JKO_ERR_INVALID_ARG, "NULL batch");
+  if (!p0_dev || n_steps < 0) return batch_err(b, JKO_ERR_INVALID_ARG, "NULL p0 or n_steps < 0");
+  b->err.clear();
+  cudaStream_t st = b->stream;
+  for (int f = 0; f < b->n; ++f) {
+    jko_handle* h = b->h[f];
+    h->stream = st;
+    if (!p0_dev[f]) return batch_err(b, JKO_ERR_INVALID_ARG, "NULL p0 entry");
+    jko_status s = h->fp64 ? check_input<double>(h, (const double*)p0_dev[f], f, b)
+                           : check_input<float>(h, (const float*)p0_dev[f], f, b);
+    if (s != JKO_OK) return s;
+  }
+  for (int f = 0; f < b->n; ++f)
+    BCK(b, cudaMemcpyAsync(b->h[f]->q, p0_dev[f], b->h[f]->es * (size_t)b->h[f]->N,
+                           cudaMemcpyDeviceToDevice, st));
+  const int n = b->n, C = b->C;
+  const int max_chunks = (b->max_iter + 1 + C - 1) / C + 2;
+  int worst = JKO_OK;
+  for (int t = 0; t < n_steps; ++t) {
+    BCK(b, cudaGraphLaunch(b->g_pro, st));
+    int launched = 0, polled = 0;
+    auto launch = [&]() -> cudaError_t {
+      cudaError_t e = cudaGraphLaunch(b->g_chunk, st);
+      if (e != cudaSuccess) return e;
+      const int slot = launched & 1;
+      e = cudaMemcpyAsync(b->done_host + slot * n, b->done_dev, sizeof(int) * n,
+                          cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_poll[slot], st);
+      ++launched;
+      return e;
+    };
+    int ahead = std::max(1, std::min(b->last_iters / C, max_chunks));
+    for (int i = 0; i < ahead; ++i) BCK(b, launch());
+    bool stopped = false;
+    while (!stopped) {
+      if (launched - polled < 2 && launched < max_chunks) BCK(b, launch());
+      const int target = launched - 1 - ((launched - polled) >= 2 ? 1 : 0);
+      const int slot = target & 1;
+      BCK(b, cudaEventSynchronize(b->ev_poll[slot]));
+      polled = target + 1;
+      stopped = true;
+      for (int f = 0; f < n && stopped; ++f) stopped = b->done_host[slot * n + f] != jko::RUNNING;
+      if (!stopped && launched >= max_chunks && polled >= launched)
+        return batch_err(b, JKO_ERR_TIMEOUT, "a flow did not report a stop within its budget");
+    }
+    BCK(b, cudaGraphLaunch(b->g_fin, st));
+    BCK(b, cudaMemcpyAsync(b->host_all, b->ctrl_all, sizeof(Ctrl) * n, cudaMemcpyDeviceToHost, st));
+    BCK(b, cudaStreamSynchronize(st));
+    int max_it = 0;
+    for (int f = 0; f < n; ++f) {
+      const Ctrl& c = b->host_all[f];
+      jko_status sf = JKO_OK;
+      if (c.nonfinite & 2) sf = JKO_ERR_TIMEOUT;
+      else if (c.done == jko::NONFINITE || c.nonfinite) sf = JKO_ERR_NUMERIC;
+      else if (c.done == jko::MAX_ITER) sf = JKO_NOT_CONVERGED;
+      worst = worse(worst, sf);
+      max_it = std::max(max_it, c.it);
+      if (infos) {
+        jko_step_info& in = infos[(size_t)t * n + f];
+        in.iters = c.it;
+        in.status = sf;
+        in.residual_l1 = c.res_last;
+        in.mass = c.mass;
+        double mx;
+        std::memcpy(&mx, &c.maxpk_bits, sizeof mx);
+        in.max_p_over_kappa = b->h[f]->has_kappa ? mx : 0.0;
+        in.ms = 0.f;
+        in.kernels = 0;
+      }
+    }
+    b->last_iters = max_it;
+  }
+  if (p_final_dev)
+    for (int f = 0; f < n; ++f)
+      if (p_final_dev[f])
+        BCK(b, cudaMemcpyAsync(p_final_dev[f], n_steps > 0 ? b->h[f]->q : p0_dev[f],
+                               b->h[f]->es * (size_t)b->h[f]->N, cudaMemcpyDeviceToDevice, st));
+  BCK(b, cudaStreamSynchronize(st));
+  return (jko_status)worst;
+}
+
+jko_status jko_batch_destroy(jko_batch* b) {
+  free_batch(b);
+  return JKO_OK;
+}
+
+const char* jko_batch_last_error(const jko_batch* b) {
+  return b ? b->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

@@ -55,4 +55,9 @@ template <typename T>
 cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
                                   cudaStream_t st);
 
+// Batched flows: copy the stop state of n control blocks into a contiguous
+// array (done flags only, or whole blocks).
+cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st);
+cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_t st);
+
 }  // namespace jko

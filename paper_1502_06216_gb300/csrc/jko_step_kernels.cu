@@ -130,6 +130,26 @@ cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, c
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void gather_done_kernel(Ctrl* const* ctrls, int* done, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    done[i] = ctrls[i]->done;
+}
+__global__ void gather_ctrl_kernel(Ctrl* const* ctrls, Ctrl* out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = *ctrls[i];
+}
+}  // namespace
+
+cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st) {
+  gather_done_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctrls, done, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_t st) {
+  gather_ctrl_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctrls, out, n);
+  return cudaGetLastError();
+}
+
 #define JKO_INST(T)                                                                     \
   template cudaError_t launch_fill<T>(T*, T, long long, cudaStream_t);                  \
   template cudaError_t launch_validate<T>(const T*, long long, const ProxArgs<T>&, Ctrl*, \

@@ -90,6 +90,14 @@ EXPORTS = {
                                         ctypes.POINTER(jko_energy), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(jko_step_info)]),
+    "jko_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(jko_grid),
+                                        ctypes.POINTER(jko_params), ctypes.POINTER(jko_energy),
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "jko_batch_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(jko_step_info)]),
+    "jko_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "jko_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "jko_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "jko_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "jko_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -302,3 +310,79 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       check_every=check_every, precision=precision, renormalize=renormalize,
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
                       stream=stream)
+
+
+class Batch:
+    """Owns a jko_batch*: independent flows advanced together."""
+
+    def __init__(self, ptr, shapes, precisions):
+        self.ptr = ptr
+        self.shapes = shapes              # (nx, ny) per flow
+        self.precisions = precisions
+
+    @property
+    def n(self):
+        return len(self.shapes)
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                jko_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def _energy_struct(pb, keep):
+    N = pb.nx * pb.ny
+    w, al = _host_f64(pb.w, N), _host_f64(pb.alpha, N)
+    mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
+    keep += [w, al, mk]
+    return jko_energy(w.ctypes.data if w is not None else None, float(pb.kappa), None, float(pb.m),
+                      al.ctypes.data if al is not None else None,
+                      mk.ctypes.data if mk is not None else None)
+
+
+def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
+                     check_every: int = 0, renormalize: bool = True, stream=None) -> Batch:
+    """jko_batch_create for a list of ``inputs.Problem``; ``precision`` may be
+    one value or one per flow."""
+    n = len(problems)
+    precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * n
+    G = (jko_grid * n)()
+    P = (jko_params * n)()
+    E = (jko_energy * n)()
+    keep = []
+    for f, pb in enumerate(problems):
+        G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
+        P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
+                          pb.max_iter if max_iter is None else max_iter, check_every,
+                          int(precs[f]), int(bool(renormalize)))
+        E[f] = _energy_struct(pb, keep)
+    out = ctypes.c_void_p()
+    st = _current_stream() if stream is None else ctypes.c_void_p(stream)
+    status = lib().jko_batch_create(n, G, P, E, st, ctypes.byref(out))
+    if status != Status.OK:
+        raise JKOError(status, lib().jko_batch_last_error(None).decode(errors="replace"))
+    return Batch(out, [(pb.nx, pb.ny) for pb in problems], [Precision(p) for p in precs])
+
+
+def jko_batch_flow(b: Batch, p0s, n_steps: int, want_final: bool = True):
+    """n_steps of every flow from the device tensors p0s; returns
+    (final images, infos[t][f])."""
+    import torch
+    n = b.n
+    P0 = (ctypes.c_void_p * n)(*[ctypes.c_void_p(t.data_ptr()) for t in p0s])
+    finals = [torch.empty_like(t) for t in p0s] if want_final else None
+    PF = (ctypes.c_void_p * n)(*[ctypes.c_void_p(t.data_ptr()) for t in finals]) if finals else None
+    infos = (jko_step_info * max(1, n * n_steps))()
+    status = lib().jko_batch_flow(b.ptr, P0, n_steps, PF, infos)
+    if status not in (Status.OK, Status.NOT_CONVERGED, Status.NUMERIC):
+        raise JKOError(status, lib().jko_batch_last_error(b.ptr).decode(errors="replace"))
+    table = [[infos[t * n + f].as_dict() for f in range(n)] for t in range(n_steps)]
+    return finals, table
+
+
+def jko_batch_destroy(b: Batch) -> None:
+    if b.ptr:
+        lib().jko_batch_destroy(b.ptr)
+        b.ptr = ctypes.c_void_p()
