@@ -183,6 +183,33 @@ jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* params,
                             const jko_energy* energy, const void* q_dev, void* p_out_dev,
                             void* stream, jko_step_info* info);
 
+/* ---- differentiation of the flow (CUDA-core handles: JKO_FP32, JKO_FP64) ---- */
+
+/* Replaces the potential w of the energy (HOST array of N doubles) without
+ * recreating the handle; the handle must have been created with a potential
+ * (or be of the congestion kind).  Used between gradient steps. */
+jko_status jko_set_potential(jko_handle* h, const double* w_host);
+
+/* jko_flow that also records, for every step t, its input q_t and the final
+ * scaling a_t (the tape of jko_flow_backward).  p_final_dev receives p_n;
+ * infos (may be NULL) n_steps reports.  JKO_ERR_UNSUPPORTED for tensor-core
+ * handles. */
+jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void* p_final_dev,
+                           jko_step_info* infos);
+
+/* Reverse-mode gradient of a scalar loss L(p_n) of the last recorded flow.
+ * grad_final_dev = dL/dp_n (device image); grad_p0_dev (may be NULL) receives
+ * dL/dp_0, grad_w_dev (may be NULL) dL/dw (device images, the handle's element
+ * type).  Each step is differentiated implicitly at its fixed point (a = r(s),
+ * s = xi(q / xi a); the paper has no adjoint, this follows from Prop. 3.3's
+ * fixed point by the implicit-function theorem), including the adjoint of the
+ * mass renormalisation; the adjoint linear system is solved by the fixed-point
+ * iteration of the transposed linearisation (tolerance params.tol relative,
+ * at most 10 max_iter sweeps).  adj_iters (may be NULL) receives the sweeps
+ * per step. */
+jko_status jko_flow_backward(jko_handle* h, const void* grad_final_dev, void* grad_p0_dev,
+                             void* grad_w_dev, int* adj_iters);
+
 /* ---- batched flows (many independent problems advanced together) ---- */
 typedef struct jko_batch jko_batch;
 

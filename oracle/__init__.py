@@ -20,6 +20,9 @@ Plain, slow and written to be checked against the paper by eye:
 * ``objective`` -- entropy E, W_gamma by a converged dense Sinkhorn, f, the step
                    objective.
 * ``logdomain`` -- the same scaling loop written with log-sum-exp (FP64).
+* ``adjoint``   -- gradients of a flow's terminal loss by FP64 reverse-mode
+                   autodiff (PyTorch CPU) through the unrolled loop; imported
+                   on demand (``from oracle import adjoint``).
 
 Parity status of every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force and invariants.

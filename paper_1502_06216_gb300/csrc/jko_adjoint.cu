@@ -1,0 +1,352 @@
+// jko_adjoint.cu -- reverse-mode differentiation of the JKO flow (CUDA cores).
+//
+// One step maps q to p through the fixed point of the scaling loop (Prop. 3.3,
+// 2-vector form): with Y = xi a, b = q / Y, s = xi b, the fixed point is
+// a = r(s, w), r = Prox_{sigma f}(s)/s, and the output is p = a (.) s
+// (then p / sum p when renormalising).  Implicit differentiation at the fixed
+// point, xi symmetric, D = b / Y, R_s = dr/ds, R_w = dr/dw:
+//   direct terms   abar = s (.) g - xi( D (.) xi(a (.) g) ),   qbar0 = xi(a (.) g) / Y
+//   adjoint solve  lambda = abar - xi( D (.) xi(R_s (.) lambda) )
+//                  (the transposed linearisation of the forward map a -> r(xi(q / xi a));
+//                  the same contraction, so a fixed-point iteration converges like
+//                  the forward loop)
+//   gradients      qbar = qbar0 + xi(R_s (.) lambda) / Y,   wbar += R_w (.) lambda.
+// Steps are walked backwards from a tape of each step's input q_t and final a_t
+// (jko_flow_record); Y, b, s are recomputed from them.  Every xi application
+// is the two CUDA-core filter passes of the forward.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "jko.h"
+#include "jko_handle.h"
+#include "jko_kernels.h"
+
+namespace {
+
+using jko::PassArgs;
+
+constexpr int NT = 256;
+
+int grid_for(long long n) {
+  long long g = (n + NT - 1) / NT;
+  if (g > 152 * 8) g = 152 * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+#define GS(i, n)                                                                  \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
+       i += (long long)gridDim.x * blockDim.x)
+
+// b = q / Y with the forward's guard, and 1/Y (0 where the forward set b = 0
+// because Y underflowed or where q = 0 but Y is fine: 1/Y there).
+template <typename T>
+__global__ void k_b_invY(const T* q, const T* Y, T* b, T* invY, long long n) {
+  GS(i, n) {
+    const T y = Y[i];
+    const bool ok = y >= jko::NormalMin<T>::v;
+    b[i] = jko::b_update<T>(q[i], y);
+    invY[i] = ok ? T(1) / y : T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_dot3(const T* x, const T* y, const T* z, double* out, long long n) {
+  __shared__ double s_red[33];
+  double v = 0.0;
+  GS(i, n) v += (double)x[i] * (double)y[i] * (double)z[i];
+  v = jko::block_sum(v, s_red);
+  if (threadIdx.x == 0) atomicAdd(out, v);
+}
+
+// gt = (g - <g, a s> / m) / m  (adjoint of p / m with m = sum p);  u = a gt
+template <typename T>
+__global__ void k_renorm(const T* g, const T* a, const double* dot, double m, int renorm, T* gt,
+                         T* u, long long n) {
+  const double c = renorm ? *dot / m : 0.0;
+  const double inv = renorm ? 1.0 / m : 1.0;
+  GS(i, n) {
+    const T v = (T)(((double)g[i] - c) * inv);
+    gt[i] = v;
+    u[i] = a[i] * v;
+  }
+}
+
+template <typename T>
+__global__ void k_mul(const T* x, const T* y, T* out, long long n) {
+  GS(i, n) out[i] = x[i] * y[i];
+}
+
+// out = s gt - w2 ; qbar0 = v invY
+template <typename T>
+__global__ void k_abar(const T* s, const T* gt, const T* w2, const T* v, const T* invY, T* abar,
+                       T* qbar0, long long n) {
+  GS(i, n) {
+    abar[i] = s[i] * gt[i] - w2[i];
+    qbar0[i] = v[i] * invY[i];
+  }
+}
+
+// u = R_s (.) lambda
+template <typename T, int EK>
+__global__ void k_rs(jko::ProxArgs<T> P, const T* s, const T* lam, T* u, long long n) {
+  GS(i, n) {
+    T rs, rw;
+    jko::ratio_grad<T, EK>(P, (int)i, s[i], rs, rw);
+    u[i] = rs * lam[i];
+  }
+}
+
+// lambda_new = abar - w2 ; diff += |lambda_new - lambda| ; norm += |abar|
+template <typename T>
+__global__ void k_lambda(const T* abar, const T* w2, T* lam, double* diff, double* norm,
+                         long long n) {
+  __shared__ double s_red[33];
+  double d = 0.0, a = 0.0;
+  GS(i, n) {
+    const T ln = abar[i] - w2[i];
+    d += fabs((double)ln - (double)lam[i]);
+    a += fabs((double)abar[i]);
+    lam[i] = ln;
+  }
+  d = jko::block_sum(d, s_red);
+  a = jko::block_sum(a, s_red);
+  if (threadIdx.x == 0) {
+    atomicAdd(diff, d);
+    atomicAdd(norm, a);
+  }
+}
+
+// g = qbar0 + v invY ;  wbar += R_w (.) lambda
+template <typename T, int EK>
+__global__ void k_final(jko::ProxArgs<T> P, const T* s, const T* lam, const T* qbar0, const T* v,
+                        const T* invY, T* g, T* wbar, long long n) {
+  GS(i, n) {
+    T rs, rw;
+    jko::ratio_grad<T, EK>(P, (int)i, s[i], rs, rw);
+    g[i] = qbar0[i] + v[i] * invY[i];
+    wbar[i] += rw * lam[i];
+  }
+}
+
+template <typename T>
+cudaError_t xi_apply(jko_handle* h, const T* in, T* out, cudaStream_t st) {
+  jko::ProxArgs<T> P = jko::prox_args<T>(h);
+  PassArgs<T> A{};
+  A.ctrl = h->ctrl;
+  A.part = h->part;
+  A.in = in;
+  A.out = (T*)h->t1;
+  A.taps = (const T*)h->taps_y;
+  A.n_i = h->grid.ny; A.n_j = h->grid.nx; A.r = h->ry;
+  cudaError_t e = jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
+  if (e != cudaSuccess) return e;
+  A.in = (const T*)h->t1;
+  A.out = out;
+  A.taps = (const T*)h->taps_x;
+  A.n_i = h->grid.nx; A.n_j = h->grid.ny; A.r = h->rx;
+  return jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
+}
+
+#define ACK(call)                                                                     \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return jko::handle_error(h, e_ == cudaErrorMemoryAllocation ? JKO_ERR_OOM : JKO_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorName(e_));     \
+  } while (0)
+
+template <typename T, int EK>
+jko_status backward_t(jko_handle* h, const T* grad_final, T* grad_p0, T* grad_w, int* adj_iters) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  if (!h->adj) {
+    ACK(cudaMalloc(&h->adj, sizeof(T) * N * 10));
+    ACK(cudaMalloc((void**)&h->adj_red, sizeof(double) * 4));
+  }
+  T* W = (T*)h->adj;
+  T *Y = W, *b = W + N, *s = W + 2 * N, *invY = W + 3 * N, *g = W + 4 * N, *gt = W + 5 * N,
+    *u = W + 6 * N, *v = W + 7 * N, *lam = W + 8 * N, *abar = W + 9 * N;
+  T* qbar0 = gt;  // written once gt has been consumed (k_abar)
+  jko::ProxArgs<T> P = jko::prox_args<T>(h);
+  // a clean control block: the filter passes only check that no stop is recorded
+  ACK(cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  ACK(cudaMemcpyAsync(g, grad_final, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  if (grad_w) ACK(cudaMemsetAsync(grad_w, 0, sizeof(T) * N, st));
+  T* wbar_dev = grad_w;
+  T* scratch_w = nullptr;
+  if (!wbar_dev) {  // gradient in w not requested: accumulate into u-sized scratch anyway
+    scratch_w = u;
+  }
+  const int budget = std::max(16, 10 * h->prm.max_iter);
+  const double tol = std::max(h->prm.tol, h->fp64 ? 1e-15 : 1e-7);
+  const int G = grid_for(N);
+  T* wtmp = v;  // second xi output shares v
+  for (int t = h->tape_steps - 1; t >= 0; --t) {
+    const T* q = (const T*)h->tape + (size_t)(2 * t) * N;
+    const T* a = q + N;
+    const double m = h->tape_mass[t];
+    // recompute the fixed-point quantities of step t
+    ACK(xi_apply<T>(h, a, Y, st));
+    k_b_invY<T><<<G, NT, 0, st>>>(q, Y, b, invY, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, b, s, st));
+    // adjoint of the renormalisation, then the direct terms
+    ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+    k_dot3<T><<<G, NT, 0, st>>>(g, a, s, h->adj_red, N);
+    ACK(cudaGetLastError());
+    k_renorm<T><<<G, NT, 0, st>>>(g, a, h->adj_red, m, h->prm.renormalize, gt, u, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u, v, st));                 // v = xi(a gt)
+    // D (.) v with D = b / Y = b invY
+    k_mul<T><<<G, NT, 0, st>>>(b, invY, u, N);      // u = D
+    k_mul<T><<<G, NT, 0, st>>>(u, v, lam, N);       // lam = D v (temporary)
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, lam, abar, st));            // abar = xi(D v) (temporary)
+    // D is needed in the solve: keep it in b (b itself is no longer needed)
+    ACK(cudaMemcpyAsync(b, u, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    T* D = b;
+    // qbar0 needs its own storage: use gt after abar is formed
+    k_abar<T><<<G, NT, 0, st>>>(s, gt, abar, v, invY, abar, gt, N);  // abar, qbar0 (in gt)
+    ACK(cudaGetLastError());
+    // adjoint fixed-point solve, lambda_0 = abar
+    ACK(cudaMemcpyAsync(lam, abar, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    int k = 0;
+    bool conv = false;
+    double host_red[4];
+    for (; k < budget && !conv; ++k) {
+      if ((k & 7) == 0) ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+      k_rs<T, EK><<<G, NT, 0, st>>>(P, s, lam, u, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u, v, st));
+      k_mul<T><<<G, NT, 0, st>>>(D, v, u, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u, wtmp, st));  // wtmp aliases v: v is consumed above
+      k_lambda<T><<<G, NT, 0, st>>>(abar, wtmp, lam, h->adj_red, h->adj_red + 1, N);
+      ACK(cudaGetLastError());
+      if ((k & 7) == 7) {
+        ACK(cudaMemcpyAsync(host_red, h->adj_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+        ACK(cudaStreamSynchronize(st));
+        // host_red holds the sums of 8 iterations; the last one dominates a
+        // contracting sequence, so the test is conservative
+        conv = host_red[0] <= tol * host_red[1];
+        if (!std::isfinite(host_red[0]))
+          return jko::handle_error(h, JKO_ERR_NUMERIC, "adjoint iterates are not finite");
+      }
+    }
+    if (adj_iters) adj_iters[t] = k;
+    // gradients of this step
+    k_rs<T, EK><<<G, NT, 0, st>>>(P, s, lam, u, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u, v, st));
+    k_final<T, EK><<<G, NT, 0, st>>>(P, s, lam, qbar0, v, invY, g,
+                                      wbar_dev ? wbar_dev : scratch_w, N);
+    ACK(cudaGetLastError());
+  }
+  if (grad_p0) ACK(cudaMemcpyAsync(grad_p0, g, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  ACK(cudaStreamSynchronize(st));
+  return JKO_OK;
+}
+
+template <typename T>
+jko_status backward_dispatch(jko_handle* h, const void* gf, void* gp, void* gw, int* it) {
+  switch (h->ek) {
+    case jko::EK_CROWD:
+      return backward_t<T, jko::EK_CROWD>(h, (const T*)gf, (T*)gp, (T*)gw, it);
+    case jko::EK_ENTROPY:
+      return backward_t<T, jko::EK_ENTROPY>(h, (const T*)gf, (T*)gp, (T*)gw, it);
+    default:
+      return backward_t<T, jko::EK_POWER>(h, (const T*)gf, (T*)gp, (T*)gw, it);
+  }
+}
+
+template <typename T>
+__global__ void k_set_potential(const double* w, T* E, T* sw, double sigma, long long n) {
+  GS(i, n) {
+    if (E) E[i] = (T)exp(-sigma * w[i]);
+    if (sw) sw[i] = (T)(sigma * w[i]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+jko_status jko_set_potential(jko_handle* h, const double* w_host) {
+  if (!h || !w_host) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
+  if (h->ek != jko::EK_CROWD && !h->sw)
+    return jko::handle_error(h, JKO_ERR_INVALID_ARG,
+                             "the handle was created without a potential (w = NULL)");
+  const long long N = h->N;
+  for (long long i = 0; i < N; ++i)
+    if (!std::isfinite(w_host[i])) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "w must be finite");
+  double* wd = nullptr;
+  ACK(cudaMalloc((void**)&wd, sizeof(double) * N));
+  cudaError_t e = cudaMemcpyAsync(wd, w_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
+  const double sigma = h->prm.tau / h->prm.gamma;
+  if (e == cudaSuccess) {
+    if (h->fp64)
+      k_set_potential<double><<<grid_for(N), NT, 0, h->stream>>>(wd, (double*)h->E, (double*)h->sw, sigma, N);
+    else
+      k_set_potential<float><<<grid_for(N), NT, 0, h->stream>>>(wd, (float*)h->E, (float*)h->sw, sigma, N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(wd);
+  ACK(e);
+  return JKO_OK;
+}
+
+jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void* p_final_dev,
+                           jko_step_info* infos) {
+  if (!h || !p0_dev || n_steps < 1) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "bad arguments");
+  if (h->tc) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "recording needs a JKO_FP32 or JKO_FP64 handle");
+  const size_t es = h->es, N = (size_t)h->N;
+  if (h->tape_cap < n_steps) {
+    if (h->tape) cudaFree(h->tape);
+    h->tape = nullptr;
+    h->tape_cap = 0;
+    ACK(cudaMalloc(&h->tape, es * N * 2 * n_steps));
+    h->tape_cap = n_steps;
+  }
+  h->tape_steps = 0;
+  h->tape_mass.assign(n_steps, 1.0);
+  cudaStream_t st = h->stream;
+  int worst = JKO_OK;
+  const void* q = p0_dev;
+  for (int t = 0; t < n_steps; ++t) {
+    char* slot = (char*)h->tape + es * N * 2 * t;
+    if (q != (const void*)slot)  // from step 1 on the previous step wrote its output here
+      ACK(cudaMemcpyAsync(slot, q, es * N, cudaMemcpyDeviceToDevice, st));
+    jko_step_info info{};
+    void* dst = (t + 1 < n_steps) ? (void*)((char*)h->tape + es * N * 2 * (t + 1)) : p_final_dev;
+    if (!dst) {
+      if (!h->stage_out) ACK(cudaMalloc(&h->stage_out, es * N));
+      dst = h->stage_out;
+    }
+    jko_status s = jko::step_internal(h, slot, dst, &info, t == 0);
+    if (s == JKO_ERR_INVALID_ARG || s == JKO_ERR_CUDA || s == JKO_ERR_OOM || s == JKO_ERR_TIMEOUT)
+      return s;
+    if (infos) infos[t] = info;
+    if (s == JKO_ERR_NUMERIC) worst = JKO_ERR_NUMERIC;
+    else if (s == JKO_NOT_CONVERGED && worst == JKO_OK) worst = JKO_NOT_CONVERGED;
+    ACK(cudaMemcpyAsync(slot + es * N, h->a, es * N, cudaMemcpyDeviceToDevice, st));
+    h->tape_mass[t] = info.mass;
+    h->tape_steps = t + 1;
+    q = dst;
+  }
+  ACK(cudaStreamSynchronize(st));
+  return (jko_status)worst;
+}
+
+jko_status jko_flow_backward(jko_handle* h, const void* grad_final_dev, void* grad_p0_dev,
+                             void* grad_w_dev, int* adj_iters) {
+  if (!h || !grad_final_dev) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "bad arguments");
+  if (h->tape_steps < 1) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "no recorded flow");
+  if (grad_w_dev && h->ek != jko::EK_CROWD && !h->sw)
+    return jko::handle_error(h, JKO_ERR_INVALID_ARG, "the energy has no potential to differentiate");
+  return h->fp64 ? backward_dispatch<double>(h, grad_final_dev, grad_p0_dev, grad_w_dev, adj_iters)
+                 : backward_dispatch<float>(h, grad_final_dev, grad_p0_dev, grad_w_dev, adj_iters);
+}
+
+}  // extern "C"

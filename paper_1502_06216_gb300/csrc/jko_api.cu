@@ -16,55 +16,13 @@
 #include <vector>
 
 #include "jko.h"
+#include "jko_handle.h"
 #include "jko_kernels.h"
 #include "tc_gemm.h"
 
 using jko::Ctrl;
 using jko::PassArgs;
 using jko::ProxArgs;
-
-struct jko_handle {
-  jko_grid grid{};
-  jko_params prm{};
-  int N = 0;
-  int prec = JKO_FP32;
-  int ek = jko::EK_CROWD;
-  bool fp64 = false;
-  size_t es = 4;  // element size of device images
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap = nullptr;  // private stream used for graph capture
-
-  // working images (es bytes per element)
-  void *a = nullptr, *b = nullptr, *t1 = nullptr, *p = nullptr, *q = nullptr;
-  void *stage_in = nullptr, *stage_out = nullptr;  // for the host-buffer entry point
-  // Gibbs factors (SIMT taps, centred and zero padded)
-  void *taps_x = nullptr, *taps_y = nullptr;
-  int rx = 0, ry = 0;
-  // per-cell energy constants
-  void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
-  uint8_t* mask = nullptr;
-  double kappa_s = INFINITY;
-  int has_kappa = 0;
-  double m = 0.0;
-
-  Ctrl* ctrl = nullptr;        // device control block
-  double* part = nullptr;      // residual partials of the b-update pass (one per block)
-  int nparts_simt = 0;
-  Ctrl* ctrl_init = nullptr;   // pinned initial value
-  Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
-  cudaEvent_t ev_poll[2] = {nullptr, nullptr};
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-
-  cudaGraphExec_t chunk = nullptr;
-  int chunk_iters = 16;
-  int last_iters = 0;
-
-  jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
-  long long kernels = 0;       // kernels enqueued by the running step
-
-  std::string err;
-};
 
 namespace {
 
@@ -123,20 +81,6 @@ cudaError_t upload(void** dst, const std::vector<double>& src) {
   return cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice);
 }
 
-template <typename T>
-ProxArgs<T> prox_args(const jko_handle* h) {
-  ProxArgs<T> P;
-  P.E = (const T*)h->E;
-  P.sw = (const T*)h->sw;
-  P.c = (const T*)h->c;
-  P.kappa = (const T*)h->kap;
-  P.kappa_s = (T)h->kappa_s;
-  P.mask = h->mask;
-  P.m1 = (T)(h->m - 1.0);
-  P.newton = 40;
-  P.has_kappa = h->has_kappa;
-  return P;
-}
 
 // Pass `which` of one (odd, even) pair in the SIMT form, on stream st:
 //   0: pass along y of xi a          1: pass along x of xi a + b-update/residual
@@ -144,7 +88,7 @@ ProxArgs<T> prox_args(const jko_handle* h) {
 template <typename T>
 cudaError_t enqueue_pass_simt(jko_handle* h, int which, cudaStream_t st) {
   const int nx = h->grid.nx, ny = h->grid.ny;
-  ProxArgs<T> P = prox_args<T>(h);
+  ProxArgs<T> P = jko::prox_args<T>(h);
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
   A.part = h->part;
@@ -211,7 +155,8 @@ void free_handle(jko_handle* h) {
   if (h->tc) jko::tc_destroy(h->tc);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
-                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl, h->part};
+                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl, h->part,
+                  h->tape, h->adj, h->adj_red};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -310,7 +255,7 @@ template <typename T>
 jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info, bool validate) {
   cudaStream_t st = h->stream;
   const long long N = h->N;
-  ProxArgs<T> P = prox_args<T>(h);
+  ProxArgs<T> P = jko::prox_args<T>(h);
   CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   if (validate) {
     CK(h, jko::launch_validate<T>(q_in, N, P, h->ctrl, st));
@@ -400,6 +345,20 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   else if (st_out == JKO_NOT_CONVERGED) set_err(h, st_out, "max_iter reached before tol");
   return st_out;
 }
+
+}  // namespace
+
+jko_status jko::step_internal(jko_handle* h, const void* q_in, void* p_out, jko_step_info* info,
+                              bool validate) {
+  return h->fp64 ? step_impl<double>(h, (const double*)q_in, (double*)p_out, info, validate)
+                 : step_impl<float>(h, (const float*)q_in, (float*)p_out, info, validate);
+}
+
+jko_status jko::handle_error(jko_handle* h, jko_status st, const std::string& msg) {
+  return set_err(h, st, msg);
+}
+
+namespace {
 
 int worse(int a, int b) {
   auto rank = [](int s) { return s == JKO_OK ? 0 : (s == JKO_NOT_CONVERGED ? 1 : 2); };
@@ -516,7 +475,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     cfg.a = (float*)h->a; cfg.b = (float*)h->b; cfg.p = (float*)h->p; cfg.q = (const float*)h->q;
     cfg.ctrl = h->ctrl;
     cfg.part = h->part;
-    cfg.prox = prox_args<float>(h);
+    cfg.prox = jko::prox_args<float>(h);
     std::string msg;
     int rc = jko::tc_create(cfg, &h->tc, &msg);
     if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, msg);
@@ -740,7 +699,7 @@ cudaError_t flow_chunk(jko_handle* h, int C, cudaStream_t s) {
 
 template <typename T>
 cudaError_t flow_finalize_t(jko_handle* h, cudaStream_t s) {
-  ProxArgs<T> P = prox_args<T>(h);
+  ProxArgs<T> P = jko::prox_args<T>(h);
   cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->N, P, h->ctrl, s);
   if (e != cudaSuccess) return e;
   // the step output becomes the input of the next step
@@ -789,7 +748,7 @@ jko_status capture_batch(jko_batch* b, F per_flow, G tail, cudaGraphExec_t* out)
 template <typename T>
 jko_status check_input(jko_handle* h, const T* q, int flow, jko_batch* b) {
   cudaStream_t st = h->stream;
-  ProxArgs<T> P = prox_args<T>(h);
+  ProxArgs<T> P = jko::prox_args<T>(h);
   BCK(b, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   BCK(b, jko::launch_validate<T>(q, h->N, P, h->ctrl, st));
   BCK(b, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));

@@ -1,0 +1,91 @@
+// jko_handle.h -- the solver handle behind the C ABI (internal to libjko).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "jko.h"
+#include "jko_internal.cuh"
+#include "tc_gemm.h"
+
+using jko::Ctrl;
+using jko::ProxArgs;
+
+struct jko_handle {
+  jko_grid grid{};
+  jko_params prm{};
+  int N = 0;
+  int prec = JKO_FP32;
+  int ek = jko::EK_CROWD;
+  bool fp64 = false;
+  size_t es = 4;  // element size of device images
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used for graph capture
+
+  // working images (es bytes per element)
+  void *a = nullptr, *b = nullptr, *t1 = nullptr, *p = nullptr, *q = nullptr;
+  void *stage_in = nullptr, *stage_out = nullptr;  // for the host-buffer entry point
+  // Gibbs factors (SIMT taps, centred and zero padded)
+  void *taps_x = nullptr, *taps_y = nullptr;
+  int rx = 0, ry = 0;
+  // per-cell energy constants
+  void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
+  uint8_t* mask = nullptr;
+  double kappa_s = INFINITY;
+  int has_kappa = 0;
+  double m = 0.0;
+
+  Ctrl* ctrl = nullptr;        // device control block
+  double* part = nullptr;      // residual partials of the b-update pass (one per block)
+  int nparts_simt = 0;
+  Ctrl* ctrl_init = nullptr;   // pinned initial value
+  Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
+  cudaEvent_t ev_poll[2] = {nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  cudaGraphExec_t chunk = nullptr;
+  int chunk_iters = 16;
+  int last_iters = 0;
+
+  jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
+  long long kernels = 0;       // kernels enqueued by the running step
+
+  // differentiation tape (jko_flow_record / jko_flow_backward)
+  int tape_steps = 0;           // steps recorded
+  int tape_cap = 0;             // steps the tape can hold
+  void* tape = nullptr;         // per step: q_t and the final a_t (2 N elements)
+  std::vector<double> tape_mass;  // sum of the unnormalised output per step
+  void* adj = nullptr;          // adjoint work images (8 N elements)
+  double* adj_red = nullptr;    // device reduction slots
+
+  std::string err;
+};
+
+
+namespace jko {
+template <typename T>
+inline ProxArgs<T> prox_args(const jko_handle* h) {
+  ProxArgs<T> P;
+  P.E = (const T*)h->E;
+  P.sw = (const T*)h->sw;
+  P.c = (const T*)h->c;
+  P.kappa = (const T*)h->kap;
+  P.kappa_s = (T)h->kappa_s;
+  P.mask = h->mask;
+  P.m1 = (T)(h->m - 1.0);
+  P.newton = 40;
+  P.has_kappa = h->has_kappa;
+  P.sigma = (T)(h->prm.tau / h->prm.gamma);
+  return P;
+}
+
+// One JKO step on device buffers (jko_api.cu); validate = check q first.
+jko_status step_internal(jko_handle* h, const void* q_in, void* p_out, jko_step_info* info,
+                         bool validate);
+// Records an error message on the handle and returns the status.
+jko_status handle_error(jko_handle* h, jko_status st, const std::string& msg);
+
+}  // namespace jko

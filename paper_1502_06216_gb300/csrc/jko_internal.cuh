@@ -101,6 +101,7 @@ struct ProxArgs {
   T m1;                // m - 1 (power)
   int newton;          // Newton steps (power)
   int has_kappa;       // 1 if any congestion bound is finite
+  T sigma;             // tau / gamma (derivatives with respect to w)
 };
 
 template <typename T> __device__ __forceinline__ T dev_exp(T x);
@@ -186,6 +187,61 @@ __device__ __forceinline__ T prox_ratio_e(const ProxArgs<T>& P, int idx, T s, T 
     if (a * s > kap) a = ratio_div<T>(kap, s);
   }
   return a;
+}
+
+// Derivatives of the ratio r(s, w) = Prox_{sigma f}(s)/s at one cell, for the
+// adjoint: (dr/ds, dr/dw).  Unclamped: crowd r = e^{-sigma w}; entropy from
+// Eq. prox-entropy; power from differentiating Eq. prox-psi (y = log psi):
+// dy/dl = 1/(1 + c), c = (m-1) beta psi^{m-1}.  Clamped at kappa (the forward's
+// test a s > kappa): r = kappa/s.  Masked cells: 0.
+template <typename T, int EK>
+__device__ __forceinline__ void ratio_grad(const ProxArgs<T>& P, int idx, T s, T& rs, T& rw) {
+  rs = T(0);
+  rw = T(0);
+  if (P.mask != nullptr && P.mask[idx]) return;
+  T a = T(0), ds = T(0), dw = T(0);
+  if (EK == EK_CROWD) {
+    a = P.E[idx];
+    dw = -P.sigma * a;
+  } else if (EK == EK_ENTROPY) {
+    if (!(s > T(0))) return;
+    const T c = P.c[idx];
+    const T sw = P.sw ? P.sw[idx] : T(0);
+    a = dev_exp<T>(-(c * dev_log<T>(s) + sw) / (T(1) + c));
+    ds = -a * c / ((T(1) + c) * s);
+    dw = -P.sigma * a / (T(1) + c);
+  } else {
+    const T sw = P.sw ? P.sw[idx] : T(0);
+    if (!(s > T(0))) {
+      a = dev_exp<T>(-sw);
+      dw = -P.sigma * a;
+    } else {
+      const T ls = dev_log<T>(s);
+      const T l = ls - sw;
+      const T beta = P.c[idx];
+      T y = l;
+      for (int k = 0; k < P.newton; ++k) {
+        const T e = beta * dev_exp<T>(P.m1 * y);
+        const T dy = (y + e - l) / (T(1) + P.m1 * e);
+        y -= dy;
+        if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
+      }
+      a = dev_exp<T>(y - ls);
+      const T c = P.m1 * beta * dev_exp<T>(P.m1 * y);
+      ds = -(a / s) * c / (T(1) + c);
+      dw = -P.sigma * a / (T(1) + c);
+    }
+  }
+  if (P.has_kappa) {
+    const T kap = P.kappa ? P.kappa[idx] : P.kappa_s;
+    if (a * s > kap) {
+      rs = -kap / (s * s);
+      rw = T(0);
+      return;
+    }
+  }
+  rs = ds;
+  rw = dw;
 }
 
 template <typename T, int EK>

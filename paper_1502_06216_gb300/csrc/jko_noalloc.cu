@@ -202,6 +202,7 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
   P.m1 = (float)(en->m - 1.0);
   P.newton = 40;
   P.has_kappa = has_kappa;
+  P.sigma = (float)sigma;
 
   // Gibbs taps (Sec. 4.1), radius = last tap non-zero in FP32
   const int rx = tap_radius(nx, grid->lx, prm->gamma);

@@ -90,6 +90,11 @@ EXPORTS = {
                                         ctypes.POINTER(jko_energy), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(jko_step_info)]),
+    "jko_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "jko_flow_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.POINTER(jko_step_info)]),
+    "jko_flow_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "jko_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(jko_grid),
                                         ctypes.POINTER(jko_params), ctypes.POINTER(jko_energy),
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -386,3 +391,75 @@ def jko_batch_destroy(b: Batch) -> None:
     if b.ptr:
         lib().jko_batch_destroy(b.ptr)
         b.ptr = ctypes.c_void_p()
+
+
+# ---- differentiation ---------------------------------------------------------------
+
+def jko_set_potential(h: Handle, w) -> None:
+    """Replaces the potential w (host float64 copy of any array-like)."""
+    wh = _host_f64(np.asarray(w, np.float64).reshape(-1), h.N)
+    _check(lib().jko_set_potential(h.ptr, ctypes.c_void_p(wh.ctypes.data)), h.ptr)
+
+
+def jko_flow_record(h: Handle, p0, n_steps: int):
+    """jko_flow that records the tape for jko_flow_backward; returns (p_n, infos)."""
+    import torch
+    p_final = torch.empty(h.N, dtype=h.dtype, device=p0.device)
+    infos = (jko_step_info * n_steps)()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_flow_record(h.ptr, _dev_image(h, p0, "p0"), n_steps,
+                             _dev_image(h, p_final, "p_final"), infos), h.ptr)
+    return p_final, [infos[i].as_dict() for i in range(n_steps)]
+
+
+def jko_flow_backward(h: Handle, grad_final, want_p0: bool = True, want_w: bool = True):
+    """dL/dp_0 and dL/dw of the last recorded flow, given dL/dp_n."""
+    import torch
+    gp = torch.empty(h.N, dtype=h.dtype, device=grad_final.device) if want_p0 else None
+    gw = torch.empty(h.N, dtype=h.dtype, device=grad_final.device) if want_w else None
+    n = 4096
+    iters = (ctypes.c_int * n)()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_flow_backward(h.ptr, _dev_image(h, grad_final.contiguous(), "grad"),
+                               _dev_image(h, gp, "grad_p0") if gp is not None else None,
+                               _dev_image(h, gw, "grad_w") if gw is not None else None,
+                               iters), h.ptr)
+    return gp, gw, list(iters)
+
+
+def _autograd_function():
+    import torch
+
+    class JKOFlow(torch.autograd.Function):
+        """p_n = flow(p_0, w) on a CUDA-core handle; backward through the
+        library's implicit adjoint.  One recorded flow per handle at a time."""
+
+        @staticmethod
+        def forward(ctx, p0, w, handle, n_steps):
+            jko_set_potential(handle, w.detach().double().cpu().numpy())
+            pT, _ = jko_flow_record(handle, p0.detach().to(handle.dtype).contiguous(), n_steps)
+            ctx.handle = handle
+            ctx.w_meta = (w.dtype, w.device)
+            ctx.p0_meta = (p0.dtype, p0.device)
+            return pT
+
+        @staticmethod
+        def backward(ctx, grad):
+            gp, gw, _ = jko_flow_backward(ctx.handle, grad.to(ctx.handle.dtype))
+            return (gp.to(dtype=ctx.p0_meta[0], device=ctx.p0_meta[1]),
+                    gw.to(dtype=ctx.w_meta[0], device=ctx.w_meta[1]), None, None)
+
+    return JKOFlow
+
+
+_JKOFlow = None
+
+
+def jko_flow_autograd(p0, w, handle: Handle, n_steps: int):
+    """Differentiable flow: returns p_n with gradients to p0 and w."""
+    global _JKOFlow
+    if _JKOFlow is None:
+        _JKOFlow = _autograd_function()
+    return _JKOFlow.apply(p0, w, handle, n_steps)

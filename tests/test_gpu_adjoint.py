@@ -1,0 +1,82 @@
+"""The implicit adjoint of the flow (jko_flow_backward) against the FP64
+oracle gradient (reverse-mode through the unrolled loop) and against central
+finite differences of the GPU's FP64 forward."""
+import numpy as np
+import pytest
+
+from paper_1502_06216_gb300 import inputs
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+torch_mod = pytest.importorskip("torch")
+
+
+def problem(n, gamma=1e-3, tau=0.02):
+    pb, w_star = inputs.differentiation_problem(n)
+    pb.gamma, pb.tau = gamma, tau
+    return pb, w_star
+
+
+def gpu_grad(pb, w, target, n_steps, prec, tol):
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    h = jko.create_from_problem(pb, precision=jko.Precision[prec], tol=tol, max_iter=20000)
+    dt = h.dtype
+    p0 = torch.tensor(pb.q0, dtype=dt, device="cuda", requires_grad=True)
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda", requires_grad=True)
+    pT = jko.jko_flow_autograd(p0, wt, h, n_steps)
+    L = ((pT.double() - torch.tensor(target, device="cuda")) ** 2).sum()
+    L.backward()
+    return float(L), p0.grad.double().cpu().numpy(), wt.grad.double().cpu().numpy(), h
+
+
+@pytest.mark.parametrize("n", [16, 32])
+def test_adjoint_matches_oracle_reverse_mode(n):
+    from oracle import adjoint
+    pb, w_star = problem(n, gamma=4e-3, tau=0.05)
+    target = adjoint.crowd_flow_loss_grad(pb.q0, w_star, np.zeros(pb.N), pb.nx, pb.ny, pb.gamma,
+                                          pb.tau, pb.kappa, 3)[3]
+    Lo, gpo, gwo, _ = adjoint.crowd_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma,
+                                                   pb.tau, pb.kappa, 3)
+    L, gp, gw, _ = gpu_grad(pb, pb.w, target, 3, "FP64", 1e-13)
+    ew = np.abs(gw - gwo).sum() / np.abs(gwo).sum()
+    sup = pb.q0 > 0
+    ep = np.abs(gp[sup] - gpo[sup]).sum() / np.abs(gpo[sup]).sum()
+    print(n, "loss", L, Lo, "rel L1 grad_w", ew, "grad_p0 (support)", ep)
+    assert abs(L - Lo) <= 1e-10 * abs(Lo)
+    assert ew <= 1e-6 and ep <= 1e-6
+
+
+def test_adjoint_matches_finite_differences_fp64_and_fp32():
+    """64^2 crowd flow, 4 steps: the FP64 and FP32 adjoints against central
+    differences of the FP64 forward (tol 1e-12) along 32 random directions,
+    relative error <= 1e-3 (the loss is only piecewise smooth where cells enter
+    or leave congestion, which bounds what finite differences can confirm; the
+    exact check is the oracle comparison above)."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pb, w_star = problem(64)
+    h64 = jko.create_from_problem(pb, precision=jko.Precision.FP64, tol=1e-12, max_iter=20000)
+    p0 = torch.tensor(pb.q0, dtype=torch.float64, device="cuda")
+    jko.jko_set_potential(h64, w_star)
+    target, _ = jko.jko_flow_record(h64, p0, 4)
+    target = target.cpu().numpy()
+
+    def loss(w):
+        jko.jko_set_potential(h64, w)
+        pT, _ = jko.jko_flow_record(h64, p0, 4)
+        return float(((pT.cpu().numpy() - target) ** 2).sum())
+
+    L64, _, gw64, _ = gpu_grad(pb, pb.w, target, 4, "FP64", 1e-12)
+    L32, _, gw32, _ = gpu_grad(pb, pb.w, target, 4, "FP32", 1e-7)
+    rng = np.random.default_rng(4000)
+    eps = 1e-6
+    worst64 = worst32 = 0.0
+    for _ in range(32):
+        d = rng.standard_normal(pb.N)
+        fd = (loss(pb.w + eps * d) - loss(pb.w - eps * d)) / (2 * eps)
+        worst64 = max(worst64, abs(gw64 @ d - fd) / abs(fd))
+        worst32 = max(worst32, abs(gw32 @ d - fd) / abs(fd))
+    print("FD rel err: FP64 adjoint", worst64, "FP32 adjoint", worst32)
+    assert worst64 <= 1e-3
+    assert worst32 <= 1e-3
