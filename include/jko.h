@@ -86,6 +86,8 @@ typedef struct jko_params {
   int check_every;  /* iterations between host polls of the stop flag (0 = default 16) */
   int precision;    /* a jko_precision value */
   int renormalize;  /* 1: divide each output p by its FP64 sum; 0: leave as computed */
+  int absorb;       /* tensor-core precisions: separable log-domain absorption of the
+                       potential (see jko_create); 0 = automatic, 1 = on, 2 = off */
 } jko_params;
 
 /* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */
@@ -115,6 +117,15 @@ typedef struct jko_handle jko_handle;
  * Builds the 1-D Gibbs factors K_x, K_y (Sec. 4.1) and the per-cell energy
  * constants, allocates the working buffers and captures the iteration graph.
  * stream: a cudaStream_t (NULL = legacy default stream).
+ * Log-domain absorption (tensor-core precisions): the scaling is carried as
+ * a = e^{beta(x,y)} a~ with the separable log-scale beta = beta_x(x) + beta_y(y)
+ * = -sigma times the additive separable fit of w, held in FP64 on the host and
+ * absorbed into the 1-D Gibbs factors, K~[i][j] = K[i][j] e^{beta(j) - beta(i)}
+ * for xi a and its transpose for xi b, and into the potential (sigma w + beta).
+ * The iterates a~, b~ then stay O(1) however small gamma is (for separable w
+ * entirely); p and the residual are unchanged and the step starts from a~ = 1.
+ * Automatic mode turns it on when sigma (max w - min w) > 120 (below that
+ * the plain form, whose scalings then stay in range, is the more accurate).
  * Returns JKO_ERR_INVALID_ARG on bad sizes or parameters (gamma, tau <= 0,
  * negative tol, max_iter < 1, kappa <= 0, alpha <= 0, m in (0, 1)),
  * JKO_ERR_UNSUPPORTED when the precision is not available for this grid,

@@ -51,11 +51,15 @@ def _safe_div(q: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 
 def step(q: np.ndarray, xi: Callable, sigma: float, energy: Energy,
-         tol: float = 1e-9, max_iter: int = 200, record: bool = False) -> StepResult:
-    """2-vector scaling loop for one JKO step (xi symmetric: xi^T = xi)."""
+         tol: float = 1e-9, max_iter: int = 200, record: bool = False,
+         a0: Optional[np.ndarray] = None) -> StepResult:
+    """2-vector scaling loop for one JKO step (xi symmetric: xi^T = xi).
+
+    ``a0`` replaces the cold start a = 1 (Sec. 3.4); the fixed point does not
+    depend on it, only the iterates of a step stopped by its budget do."""
     q = np.asarray(q, np.float64)
     N = q.size
-    a = np.ones(N)
+    a = np.ones(N) if a0 is None else np.asarray(a0, np.float64).copy()
     b = np.ones(N)
     p = np.zeros(N)
     res_hist = []
@@ -149,7 +153,7 @@ class FlowResult:
 
 def flow(p0: np.ndarray, xi: Callable, gamma: float, tau: float, energy: Energy,
          n_steps: int, tol: float = 1e-9, max_iter: int = 200,
-         renormalize: bool = True) -> FlowResult:
+         renormalize: bool = True, a0: Optional[np.ndarray] = None) -> FlowResult:
     """p_{t+1} = Prox^{W_gamma}_{tau f}(p_t) (Eq. smooth-jko), fixed gamma, tau.
 
     ``renormalize`` divides each p_{t+1} by its FP64 sum (the paper does not;
@@ -159,7 +163,7 @@ def flow(p0: np.ndarray, xi: Callable, gamma: float, tau: float, energy: Energy,
     iters, res, mass = [], [], []
     q = traj[0]
     for _ in range(n_steps):
-        r = step(q, xi, sigma, energy, tol=tol, max_iter=max_iter)
+        r = step(q, xi, sigma, energy, tol=tol, max_iter=max_iter, a0=a0)
         p = r.p
         mass.append(float(p.sum()))
         if renormalize:
@@ -171,13 +175,29 @@ def flow(p0: np.ndarray, xi: Callable, gamma: float, tau: float, energy: Energy,
     return FlowResult(np.stack(traj), iters, res, mass)
 
 
+def separable_logscale(w: np.ndarray, nx: int, ny: int, sigma: float) -> np.ndarray:
+    """beta(x, y) = -sigma (additive separable fit of w): row means + column
+    means - grand mean of the image w[y][x]."""
+    W = np.asarray(w, np.float64).reshape(ny, nx)
+    fit = W.mean(axis=0)[None, :] + W.mean(axis=1)[:, None] - W.mean()
+    return (-sigma * fit).ravel()
+
+
 def problem_flow(pb, n_steps: Optional[int] = None, renormalize: bool = True,
-                 tol: Optional[float] = None, max_iter: Optional[int] = None) -> FlowResult:
-    """Flow of an ``inputs.Problem``-like object (fields nx, ny, gamma, tau, q0, ...)."""
+                 tol: Optional[float] = None, max_iter: Optional[int] = None,
+                 absorbed_start: bool = False) -> FlowResult:
+    """Flow of an ``inputs.Problem``-like object (fields nx, ny, gamma, tau, q0, ...).
+
+    ``absorbed_start`` starts every step from a = e^{beta} with beta the
+    separable log-scale of the potential, the start of a solver that carries
+    the scaling as e^{beta} a~ from a~ = 1."""
     from .gibbs import SeparableXi
     xi = SeparableXi(pb.nx, pb.ny, pb.gamma, pb.lx, pb.ly)
+    a0 = None
+    if absorbed_start and pb.w is not None:
+        a0 = np.exp(separable_logscale(pb.w, pb.nx, pb.ny, pb.tau / pb.gamma))
     return flow(pb.q0, xi, pb.gamma, pb.tau, Energy.from_problem(pb),
                 pb.n_steps if n_steps is None else n_steps,
                 tol=pb.tol if tol is None else tol,
                 max_iter=pb.max_iter if max_iter is None else max_iter,
-                renormalize=renormalize)
+                renormalize=renormalize, a0=a0)

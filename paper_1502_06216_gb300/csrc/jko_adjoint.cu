@@ -274,6 +274,9 @@ extern "C" {
 
 jko_status jko_set_potential(jko_handle* h, const double* w_host) {
   if (!h || !w_host) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
+  if (h->tc && jko::tc_absorbed(h->tc))
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the potential is absorbed into the Gibbs factors of this handle");
   if (h->ek != jko::EK_CROWD && !h->sw)
     return jko::handle_error(h, JKO_ERR_INVALID_ARG,
                              "the handle was created without a potential (w = NULL)");

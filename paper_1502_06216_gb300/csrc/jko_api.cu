@@ -183,6 +183,8 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (p->check_every < 0) return set_err(nullptr, JKO_ERR_INVALID_ARG, "check_every must be >= 0");
   if (p->precision < JKO_FP64 || p->precision > JKO_BF16X3)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
+  if (p->absorb < 0 || p->absorb > 2)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "absorb must be 0 (automatic), 1 or 2");
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
@@ -476,6 +478,18 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     cfg.ctrl = h->ctrl;
     cfg.part = h->part;
     cfg.prox = jko::prox_args<float>(h);
+    // separable log-domain absorption of the potential: on, off, or automatic
+    // when the potential spans more than 120 e-folds (sigma (max w - min w)).
+    // Below that the plain form is the more accurate one (its scalings stay in
+    // range); beyond ~130 e-folds the plain form loses the far field.
+    cfg.w_host = energy->w;
+    cfg.sigma = params->tau / params->gamma;
+    cfg.absorb = 0;
+    if (energy->w && params->absorb != 2) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int i = 0; i < h->N; ++i) { lo = std::min(lo, energy->w[i]); hi = std::max(hi, energy->w[i]); }
+      cfg.absorb = params->absorb == 1 || cfg.sigma * (hi - lo) > 120.0 ? 1 : 0;
+    }
     std::string msg;
     int rc = jko::tc_create(cfg, &h->tc, &msg);
     if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, msg);

@@ -431,7 +431,6 @@ __device__ __forceinline__ void smem_ld_op16(const unsigned char* hi, const unsi
 
 struct TcPassArgs {
   int M, N, Kdim;         // D is M x N, contraction length Kdim (= M)
-  int r;                  // band radius of the kernel factor
   int pitch_out;          // row pitch (elements) of the operand-typed output image
   void* out_hi;           // EPI_STORE: T^T ; EPI_B: b ; EPI_A: a   (operand type)
   void* out_lo;           // BF16X3 low parts
@@ -440,6 +439,7 @@ struct TcPassArgs {
   Ctrl* ctrl;
   ProxArgs<float> P;
   int tma_epi;            // 1: epilogue tiles moved by TMA (fp32 fields with nx % 4 == 0)
+  const int2* kbt;        // per 128-row tile: first K-block and count (band of the factor)
   double* part;           // residual partials, one per block of the b-update pass
   int nparts;             // partials read by the deciding pass
   int decide;             // 1: this pass takes the stop decision (stop_gate)
@@ -489,13 +489,10 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   const int n0 = blockIdx.x * BN;
   const int m0 = blockIdx.y * BM;
 
-  // band of K-blocks that meet |m - k| <= r for m in [m0, m0 + BM)
-  int k_lo = m0 - args.r;
-  if (k_lo < 0) k_lo = 0;
-  int k_hi = m0 + BM - 1 + args.r;
-  if (k_hi > args.Kdim - 1) k_hi = args.Kdim - 1;
-  const int kb_lo = k_lo / KE;
-  const int nkb = k_hi / KE - kb_lo + 1;
+  // K-blocks holding the non-zero band of rows [m0, m0 + BM) of the factor
+  const int2 kb = args.kbt[blockIdx.y];
+  const int kb_lo = kb.x;
+  const int nkb = kb.y;
 
   if (threadIdx.x == 0) {
     s_fault = 0;
@@ -788,12 +785,18 @@ struct TcPlan {
   int bn_x = 64, bn_y = 64;   // BN of the pass over x (N = ny) and over y (N = nx)
   int rx = 0, ry = 0;          // band radii
   int px = 0, py = 0;          // pitches (elements) of images with x / y contiguous
-  void* kx[2] = {nullptr, nullptr};
-  void* ky[2] = {nullptr, nullptr};
+  // factors [axis 0 = x, 1 = y][side 0 = a (xi a), 1 = b (xi b)][hi, lo]; without
+  // absorption the b side aliases the a side (the factor is symmetric)
+  void* k[2][2][2] = {};
+  int2* kbt[2][2] = {};        // per-tile K-block ranges of each factor
+  float* E_abs = nullptr;      // absorbed e^{-(sigma w + beta)} (congestion kind)
+  float* sw_abs = nullptr;     // absorbed sigma w + beta (entropy kinds)
+  int absorbed = 0;
   void* img_a[2] = {nullptr, nullptr};   // [ny][px]
   void* img_b[2] = {nullptr, nullptr};   // [ny][px]
   void* img_t[2] = {nullptr, nullptr};   // [nx][py]
-  CUtensorMap mKx[2], mKy[2], mA[2], mB[2], mT[2];  // operand loads
+  CUtensorMap mK[2][2][2];                          // factor loads [axis][side][split]
+  CUtensorMap mA[2], mB[2], mT[2];                  // image operand loads
   CUtensorMap sA[2], sB[2], sT[2];                  // epilogue stores (box 128 rows)
   CUtensorMap fQ, fE, fP;                           // fp32 fields q, e^{-sigma w}, p
   int tma_epi = 0;
@@ -877,30 +880,54 @@ cudaError_t dispatch_bn(int bn, int epi, int ek, const Maps& M, const TcPassArgs
   return dispatch_epi<MODE, 64>(epi, ek, M, args, st);
 }
 
-// Radius of the band: last offset whose factor entry is a normal number in the
-// operand precision (bf16 shares the fp32 exponent range; tf32 too).
-int band_radius(int n, double length, double gamma) {
-  const double h = length / n;
-  int r = 0;
-  for (int d = 0; d < n; ++d) {
-    const double v = std::exp(-(d * h) * (d * h) / gamma);
-    if (v >= 1.1754943508222875e-38) r = d;
+// Smallest normal FP32 (and BF16) number: factor entries below it are stored
+// as exact zeros, so the K-blocks that hold none of the rest contribute nothing.
+constexpr double kNormalMin = 1.1754943508222875e-38;
+
+// Log-scale of one axis for the absorption: beta_axis(i) = -sigma (w_axis(i) -
+// mean(w)/2), w_axis = mean of w over the other axis, so beta_x(x) + beta_y(y)
+// = -sigma (additive separable fit of w).  Zero without absorption.
+void axis_logscale(const TcConfig& c, int axis, std::vector<double>& beta) {
+  const int nx = c.nx, ny = c.ny;
+  const int n = axis == 0 ? nx : ny;
+  beta.assign(n, 0.0);
+  if (!c.absorb || !c.w_host) return;
+  double tot = 0.0;
+  for (long long i = 0; i < (long long)nx * ny; ++i) tot += c.w_host[i];
+  const double mean = tot / ((double)nx * ny);
+  for (int i = 0; i < n; ++i) {
+    double acc = 0.0;
+    if (axis == 0) for (int y = 0; y < ny; ++y) acc += c.w_host[(size_t)y * nx + i];
+    else for (int x = 0; x < nx; ++x) acc += c.w_host[(size_t)i * nx + x];
+    const double wm = acc / (axis == 0 ? ny : nx);
+    beta[i] = -c.sigma * (wm - 0.5 * mean);
   }
-  return r;
 }
 
-// Host construction of one factor in operand precision: hi (+ lo) [n][pitch].
+// Factor of one axis and side in operand precision, hi (+ lo) [n][pitch]:
+//   a side  K~[i][j] = exp(-(i-j)^2 h^2 / gamma + beta(j) - beta(i))
+//   b side  the transpose.
+// Also the per-tile K-block ranges of its non-zero entries.  Returns false if
+// an entry would overflow FP32.
 template <typename T>
-void build_factor(std::vector<T>& hi, std::vector<T>& lo, int n, int pitch, double length,
-                  double gamma, int r, int mode) {
+bool build_factor(std::vector<T>& hi, std::vector<T>& lo, std::vector<int2>& kbt, int n,
+                  int pitch, double length, double gamma, const std::vector<double>& beta,
+                  bool transpose, int KE) {
   const double h = length / n;
   hi.assign((size_t)n * pitch, T(0.0f));
   lo.assign((size_t)n * pitch, T(0.0f));
+  const int tiles = (n + BM - 1) / BM;
+  std::vector<int> kmin(tiles, n), kmax(tiles, -1);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      const int d = i > j ? i - j : j - i;
-      if (d > r) continue;
-      const double v = std::exp(-(d * h) * (d * h) / gamma);
+      const double d = (i - j) * h;
+      const double ex = -(d * d) / gamma + (transpose ? beta[i] - beta[j] : beta[j] - beta[i]);
+      if (ex > 88.0) return false;
+      const double v = std::exp(ex);
+      if (v < kNormalMin) continue;
+      const int t = i / BM;
+      kmin[t] = std::min(kmin[t], j);
+      kmax[t] = std::max(kmax[t], j);
       if constexpr (sizeof(T) == 4) {
         // round to tf32 (10 mantissa bits, nearest-away as cvt.rna)
         float f = (float)v;
@@ -916,7 +943,10 @@ void build_factor(std::vector<T>& hi, std::vector<T>& lo, int n, int pitch, doub
         lo[(size_t)i * pitch + j] = __float2bfloat16_rn(f - __bfloat162float(bh));
       }
     }
-  (void)mode;
+  kbt.assign(tiles, make_int2(0, 0));
+  for (int t = 0; t < tiles; ++t)
+    if (kmax[t] >= 0) kbt[t] = make_int2(kmin[t] / KE, kmax[t] / KE - kmin[t] / KE + 1);
+  return true;
 }
 
 template <typename T>
@@ -926,34 +956,78 @@ cudaError_t alloc_img(void** p, size_t elems) {
   return cudaMemset(*p, 0, elems * sizeof(T));
 }
 
+// The absorbed energy: e^{-(sigma w + beta)} (congestion) or sigma w + beta.
+int absorbed_energy(TcPlan* P, const std::vector<double>& bx, const std::vector<double>& by,
+                    std::string* msg) {
+  TcConfig& c = P->cfg;
+  const int nx = c.nx, ny = c.ny;
+  std::vector<float> v((size_t)nx * ny);
+  const bool crowd = c.ek == EK_CROWD;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const double t = c.sigma * c.w_host[(size_t)y * nx + x] + bx[x] + by[y];
+      v[(size_t)y * nx + x] = crowd ? (float)std::exp(-t) : (float)t;
+    }
+  float** dst = crowd ? &P->E_abs : &P->sw_abs;
+  if (cudaMalloc((void**)dst, v.size() * sizeof(float)) != cudaSuccess ||
+      cudaMemcpy(*dst, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *msg = "upload of the absorbed energy";
+    return 2;
+  }
+  if (crowd) c.prox.E = P->E_abs;
+  else c.prox.sw = P->sw_abs;
+  return 0;
+}
+
 template <typename T>
 int create_typed(TcPlan* P, std::string* msg) {
-  const TcConfig& c = P->cfg;
+  TcConfig& c = P->cfg;
   const int nx = c.nx, ny = c.ny;
   const int align = 16 / (int)sizeof(T);
   P->px = round_up(nx, align);
   P->py = round_up(ny, align);
-  P->rx = band_radius(nx, c.lx, c.gamma);
-  P->ry = band_radius(ny, c.ly, c.gamma);
   const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
+  const int KE = P->mode == MODE_TF32 ? 32 : 64;
+  P->absorbed = c.absorb && c.w_host ? 1 : 0;
+  std::vector<double> beta[2];
+  axis_logscale(c, 0, beta[0]);
+  axis_logscale(c, 1, beta[1]);
   std::vector<T> hi, lo;
-  cudaError_t e;
+  std::vector<int2> kbt;
   for (int axis = 0; axis < 2; ++axis) {
     const int n = axis == 0 ? nx : ny;
     const int pitch = axis == 0 ? P->px : P->py;
-    build_factor<T>(hi, lo, n, pitch, axis == 0 ? c.lx : c.ly, c.gamma,
-                    axis == 0 ? P->rx : P->ry, P->mode);
-    void** dst = axis == 0 ? P->kx : P->ky;
-    for (int s = 0; s < nsplit; ++s) {
-      const auto& src = s == 0 ? hi : lo;
-      if ((e = cudaMalloc(&dst[s], src.size() * sizeof(T))) != cudaSuccess) { *msg = "cudaMalloc factor"; return 2; }
-      if ((e = cudaMemcpy(dst[s], src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice)) != cudaSuccess) { *msg = "upload factor"; return 2; }
+    for (int side = 0; side < (P->absorbed ? 2 : 1); ++side) {
+      if (!build_factor<T>(hi, lo, kbt, n, pitch, axis == 0 ? c.lx : c.ly, c.gamma, beta[axis],
+                           side == 1, KE)) {
+        *msg = "absorbed Gibbs factor overflows FP32 (potential too steep for gamma)";
+        return 1;
+      }
+      for (int sp = 0; sp < nsplit; ++sp) {
+        const auto& src = sp == 0 ? hi : lo;
+        if (cudaMalloc(&P->k[axis][side][sp], src.size() * sizeof(T)) != cudaSuccess ||
+            cudaMemcpy(P->k[axis][side][sp], src.data(), src.size() * sizeof(T),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+          *msg = "upload of a Gibbs factor";
+          return 2;
+        }
+      }
+      if (cudaMalloc((void**)&P->kbt[axis][side], kbt.size() * sizeof(int2)) != cudaSuccess ||
+          cudaMemcpy(P->kbt[axis][side], kbt.data(), kbt.size() * sizeof(int2),
+                     cudaMemcpyHostToDevice) != cudaSuccess) {
+        *msg = "upload of the band tables";
+        return 2;
+      }
     }
   }
-  for (int s = 0; s < nsplit; ++s) {
-    if (alloc_img<T>(&P->img_a[s], (size_t)ny * P->px) != cudaSuccess ||
-        alloc_img<T>(&P->img_b[s], (size_t)ny * P->px) != cudaSuccess ||
-        alloc_img<T>(&P->img_t[s], (size_t)nx * P->py) != cudaSuccess) {
+  if (P->absorbed) {
+    const int rc = absorbed_energy(P, beta[0], beta[1], msg);
+    if (rc) return rc;
+  }
+  for (int sp = 0; sp < nsplit; ++sp) {
+    if (alloc_img<T>(&P->img_a[sp], (size_t)ny * P->px) != cudaSuccess ||
+        alloc_img<T>(&P->img_b[sp], (size_t)ny * P->px) != cudaSuccess ||
+        alloc_img<T>(&P->img_t[sp], (size_t)nx * P->py) != cudaSuccess) {
       *msg = "cudaMalloc operand images";
       return 2;
     }
@@ -963,23 +1037,31 @@ int create_typed(TcPlan* P, std::string* msg) {
   P->bn_x = pick(nx, ny);  // pass over x: M = nx, N = ny
   P->bn_y = pick(ny, nx);  // pass over y: M = ny, N = nx
   if (P->mode == MODE_BF16X3) P->bn_x = P->bn_y = 64;
-  // tensor maps (hi and lo; lo maps alias hi when unused)
+  // tensor maps (hi and lo; lo maps alias hi when unused; b side aliases a side)
   const int m = P->mode;
-  for (int s = 0; s < 2; ++s) {
-    const int si = s < nsplit ? s : 0;
-    bool ok = make_map(&P->mKx[s], P->kx[si], m, nx, nx, P->px, BM) &&
-              make_map(&P->mKy[s], P->ky[si], m, ny, ny, P->py, BM) &&
-              make_map(&P->mA[s], P->img_a[si], m, ny, nx, P->px, P->bn_x) &&
-              make_map(&P->mB[s], P->img_b[si], m, ny, nx, P->px, P->bn_x) &&
-              make_map(&P->mT[s], P->img_t[si], m, nx, ny, P->py, P->bn_y) &&
-              make_map(&P->sA[s], P->img_a[si], m, ny, nx, P->px, BM) &&
-              make_map(&P->sB[s], P->img_b[si], m, ny, nx, P->px, BM) &&
-              make_map(&P->sT[s], P->img_t[si], m, nx, ny, P->py, BM);
+  for (int sp = 0; sp < 2; ++sp) {
+    const int si = sp < nsplit ? sp : 0;
+    bool ok = true;
+    for (int axis = 0; axis < 2 && ok; ++axis)
+      for (int side = 0; side < 2 && ok; ++side) {
+        const int sd = P->absorbed ? side : 0;
+        const int n = axis == 0 ? nx : ny;
+        ok = make_map(&P->mK[axis][side][sp], P->k[axis][sd][si], m, n, n,
+                      axis == 0 ? P->px : P->py, BM);
+      }
+    ok = ok && make_map(&P->mA[sp], P->img_a[si], m, ny, nx, P->px, P->bn_x) &&
+         make_map(&P->mB[sp], P->img_b[si], m, ny, nx, P->px, P->bn_x) &&
+         make_map(&P->mT[sp], P->img_t[si], m, nx, ny, P->py, P->bn_y) &&
+         make_map(&P->sA[sp], P->img_a[si], m, ny, nx, P->px, BM) &&
+         make_map(&P->sB[sp], P->img_b[si], m, ny, nx, P->px, BM) &&
+         make_map(&P->sT[sp], P->img_t[si], m, nx, ny, P->py, BM);
     if (!ok) { *msg = "cuTensorMapEncodeTiled failed"; return 2; }
   }
+  if (!P->absorbed)
+    for (int axis = 0; axis < 2; ++axis) P->kbt[axis][1] = P->kbt[axis][0];
   // fp32 fields [ny][nx] (q, e^{-sigma w}, p) as TMA tiles when rows are 16-byte multiples
   P->tma_epi = (nx % 4 == 0) ? 1 : 0;
-  P->fQ = P->fE = P->fP = P->mKx[0];
+  P->fQ = P->fE = P->fP = P->mK[0][0][0];
   if (P->tma_epi) {
     bool ok = make_map(&P->fQ, (void*)c.q, MODE_TF32, ny, nx, nx, BM) &&
               make_map(&P->fP, (void*)c.p, MODE_TF32, ny, nx, nx, BM);
@@ -987,20 +1069,17 @@ int create_typed(TcPlan* P, std::string* msg) {
       ok = make_map(&P->fE, (void*)c.prox.E, MODE_TF32, ny, nx, nx, BM);
     if (!ok) { *msg = "cuTensorMapEncodeTiled failed (fields)"; return 2; }
   }
-  // executed flops per pass
-  const int KE = m == MODE_TF32 ? 32 : 64;
+  // executed flops per pass, from the band tables
   const double mult = m == MODE_BF16X3 ? 3.0 : 1.0;
   for (int pass = 0; pass < 4; ++pass) {
-    const bool over_x = (pass & 1) == 0;
-    const int M = over_x ? nx : ny, N = over_x ? ny : nx, r = over_x ? P->rx : P->ry;
-    const int bn = over_x ? P->bn_x : P->bn_y;
+    const int axis = (pass & 1) == 0 ? 0 : 1;
+    const int side = P->absorbed ? (pass >> 1) : 0;
+    const int M = axis == 0 ? nx : ny, N = axis == 0 ? ny : nx;
+    const int bn = axis == 0 ? P->bn_x : P->bn_y;
+    std::vector<int2> tab((M + BM - 1) / BM);
+    cudaMemcpy(tab.data(), P->kbt[axis][side], tab.size() * sizeof(int2), cudaMemcpyDeviceToHost);
     double f = 0.0;
-    for (int mt = 0; mt * BM < M; ++mt) {
-      const int m0 = mt * BM;
-      const int klo = std::max(0, m0 - r), khi = std::min(M - 1, m0 + BM - 1 + r);
-      const int nk = (khi / KE - klo / KE + 1) * KE;
-      f += 2.0 * BM * nk * (double)(((N + bn - 1) / bn) * bn) * mult;
-    }
+    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)(((N + bn - 1) / bn) * bn) * mult;
     P->flops[pass] = f;
   }
   cudaError_t ea = m == MODE_TF32 ? set_attrs<MODE_TF32>()
@@ -1047,31 +1126,34 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
   const int half = which >> 1;
   TcPassArgs a{};
   a.ctrl = c.ctrl;
-  a.P = c.prox;
+  a.P = c.prox;   // absorbed energy images when the plan absorbs the potential
   a.q = c.q;
   a.p = c.p;
   a.part = c.part;
   a.nparts = ((c.nx + P->bn_y - 1) / P->bn_y) * ((c.ny + BM - 1) / BM);  // b-update grid
   Maps mp{};
   int bn, epi;
+  const int side = P->absorbed ? half : 0;  // xi a uses K~, xi b its transpose
   if (over_x) {  // K_x . image^T -> T^T [nx][ny]
-    a.M = c.nx; a.N = c.ny; a.Kdim = c.nx; a.r = P->rx;
+    a.M = c.nx; a.N = c.ny; a.Kdim = c.nx;
+    a.kbt = P->kbt[0][side];
     a.pitch_out = P->py;
     a.out_hi = P->img_t[0]; a.out_lo = P->img_t[1];
-    mp.a_hi = &P->mKx[0]; mp.a_lo = &P->mKx[1];
+    mp.a_hi = &P->mK[0][side][0]; mp.a_lo = &P->mK[0][side][1];
     mp.b_hi = half == 0 ? &P->mA[0] : &P->mB[0];
     mp.b_lo = half == 0 ? &P->mA[1] : &P->mB[1];
     mp.o_hi = &P->sT[0]; mp.o_lo = &P->sT[1];
-    mp.f = mp.pm = &P->mKx[0];   // unused by the plain pass
+    mp.f = mp.pm = &P->mK[0][0][0];   // unused by the plain pass
     a.decide = half == 1 ? 1 : 0;  // the pass after the b-update decides
     bn = P->bn_x;
     epi = EPI_STORE;
   } else {       // K_y . T^T^T -> [ny][nx] with the epilogue
-    a.M = c.ny; a.N = c.nx; a.Kdim = c.ny; a.r = P->ry;
+    a.M = c.ny; a.N = c.nx; a.Kdim = c.ny;
+    a.kbt = P->kbt[1][side];
     a.pitch_out = P->px;
     a.out_hi = half == 0 ? P->img_b[0] : P->img_a[0];
     a.out_lo = half == 0 ? P->img_b[1] : P->img_a[1];
-    mp.a_hi = &P->mKy[0]; mp.a_lo = &P->mKy[1];
+    mp.a_hi = &P->mK[1][side][0]; mp.a_lo = &P->mK[1][side][1];
     mp.b_hi = &P->mT[0]; mp.b_lo = &P->mT[1];
     mp.o_hi = half == 0 ? &P->sB[0] : &P->sA[0];
     mp.o_lo = half == 0 ? &P->sB[1] : &P->sA[1];
@@ -1090,6 +1172,8 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
 
 double tc_pass_flops(const TcPlan* P, int which) { return P->flops[which & 3]; }
 
+int tc_absorbed(const TcPlan* P) { return P ? P->absorbed : 0; }
+
 int tc_partials(int nx, int ny) {
   // upper bound over the tile widths: 64-column tiles give the most blocks
   return ((nx + 63) / 64) * ((ny + BM - 1) / BM);
@@ -1097,9 +1181,15 @@ int tc_partials(int nx, int ny) {
 
 void tc_destroy(TcPlan* P) {
   if (!P) return;
-  void* bufs[] = {P->kx[0], P->kx[1], P->ky[0], P->ky[1], P->img_a[0], P->img_a[1],
-                  P->img_b[0], P->img_b[1], P->img_t[0], P->img_t[1]};
+  void* bufs[] = {P->img_a[0], P->img_a[1], P->img_b[0], P->img_b[1], P->img_t[0],
+                  P->img_t[1], P->E_abs, P->sw_abs};
   for (void* b : bufs) if (b) cudaFree(b);
+  for (int axis = 0; axis < 2; ++axis)
+    for (int side = 0; side < 2; ++side) {
+      for (int sp = 0; sp < 2; ++sp)
+        if (P->k[axis][side][sp]) cudaFree(P->k[axis][side][sp]);
+      if (P->kbt[axis][side] && (side == 0 || P->absorbed)) cudaFree(P->kbt[axis][side]);
+    }
   delete P;
 }
 

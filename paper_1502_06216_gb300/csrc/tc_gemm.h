@@ -22,12 +22,21 @@ struct TcConfig {
   Ctrl* ctrl;
   double* part;   // residual partials (tc_partials(cfg) doubles)
   ProxArgs<float> prox;
+  // separable log-domain absorption of the potential
+  int absorb;             // 1: absorb (resolved by the caller)
+  const double* w_host;   // potential (host, N doubles) or NULL
+  double sigma;           // tau / gamma
 };
+
+
 
 // Number of residual partials (blocks of the b-update pass) for a grid.
 int tc_partials(int nx, int ny);
 
 struct TcPlan;
+
+// 1 when the plan carries an absorbed potential (it then owns its energy images).
+int tc_absorbed(const TcPlan* plan);
 
 // 0 = ok, 1 = unsupported configuration (message set), 2 = CUDA error.
 int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);

@@ -53,7 +53,8 @@ class jko_grid(ctypes.Structure):
 class jko_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("tau", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("precision", ctypes.c_int), ("renormalize", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("renormalize", ctypes.c_int),
+                ("absorb", ctypes.c_int)]
 
 
 class jko_energy(ctypes.Structure):
@@ -178,11 +179,12 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                tol: float = 1e-6, max_iter: int = 200, check_every: int = 0,
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
-               alpha=None, mask=None, stream=None) -> Handle:
+               alpha=None, mask=None, stream=None, absorb: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied)."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
-    p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)))
+    p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
+                   int(absorb))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
@@ -276,7 +278,7 @@ def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
     g = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
     p = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                    pb.max_iter if max_iter is None else max_iter, 0, int(Precision.FP32),
-                   int(bool(renormalize)))
+                   int(bool(renormalize)), 0)
     keep = [_host_f64(pb.w, N), None, _host_f64(pb.alpha, N)]
     mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(pb.kappa), None,
@@ -307,14 +309,14 @@ def jko_build_info() -> str:
 
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
                         max_iter: Optional[int] = None, check_every: int = 0,
-                        renormalize: bool = True, stream=None) -> Handle:
+                        renormalize: bool = True, stream=None, absorb: int = 0) -> Handle:
     """jko_create from an ``inputs.Problem``."""
     return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
                       tol=pb.tol if tol is None else tol,
                       max_iter=pb.max_iter if max_iter is None else max_iter,
                       check_every=check_every, precision=precision, renormalize=renormalize,
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
-                      stream=stream)
+                      stream=stream, absorb=absorb)
 
 
 class Batch:
@@ -361,7 +363,7 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
         G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
         P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                           pb.max_iter if max_iter is None else max_iter, check_every,
-                          int(precs[f]), int(bool(renormalize)))
+                          int(precs[f]), int(bool(renormalize)), 0)
         E[f] = _energy_struct(pb, keep)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)

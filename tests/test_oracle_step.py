@@ -138,3 +138,18 @@ def test_log_domain_where_potential_underflows():
     with np.errstate(all="ignore"):
         r = jko.step(pb.q0, gibbs.SeparableXi(n, n, g), tau / g, en, tol=1e-12, max_iter=5000)
     assert np.abs(r.p - p).sum() <= 1e-12
+
+
+def test_cold_start_does_not_change_the_fixed_point():
+    """The step's minimiser is unique (Eq. def-jko-operator), so a converged
+    step from a = e^{beta} equals the one from a = 1."""
+    pb = inputs.crowd_problem(12, gamma=5e-3, tau=0.2, kappa_factor=1.3, n_steps=2)
+    f1 = jko.problem_flow(pb, tol=1e-13, max_iter=100000)
+    f2 = jko.problem_flow(pb, tol=1e-13, max_iter=100000, absorbed_start=True)
+    assert np.abs(f1.traj - f2.traj).max() <= 1e-12
+
+
+def test_separable_fit_is_exact_for_separable_potentials():
+    pb = inputs.crowd_problem(9, gamma=1e-2, ny=7)           # w = |x - x0|^2 is separable
+    beta = jko.separable_logscale(pb.w, pb.nx, pb.ny, 3.0)
+    assert np.abs(beta + 3.0 * pb.w).max() <= 1e-13
