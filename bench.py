@@ -43,6 +43,33 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_TFLOPS_NOMINAL = 1.25
 
+# DRAM bytes (read + write) per launch of each tensor-core pass, BF16 form at
+# 1024^2, from one ncu capture (profiles/tc_pass_bf16_crowd1024_full.md).  They
+# hold for the kernel sources whose hash is given; any change to those sources
+# turns the roofline's traffic back to null until the counters are taken again.
+KERNEL_SOURCES = ("tc_gemm.cu", "tc_gemm.h", "jko_internal.cuh")
+PROFILED_TRAFFIC = {
+    "src_sha256": "70f92daf29d4afa904236a31111ba9b6707a65c42e516d403a1048e9eb72afd5",
+    "precision": "BF16", "n": 1024,
+    "bytes_per_launch": [3140096.0, 9449984.0, 3140096.0, 7355136.0],
+}
+
+
+def kernel_source_hash():
+    import hashlib
+    hsh = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1502_06216_gb300", "csrc", name), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()
+
+
+def profiled_traffic(precision_name, n, kern):
+    t = PROFILED_TRAFFIC
+    if precision_name != t["precision"] or n != t["n"] or kernel_source_hash() != t["src_sha256"]:
+        return None
+    return t["bytes_per_launch"][kern]
+
 
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -380,7 +407,9 @@ def run_ours(args):
     names = ["pass_x_xi_a", "pass_y_xi_a+b_update+residual", "pass_x_xi_b", "pass_y_xi_b+prox"]
     dense_flops = 8.0 * args.n ** 3
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": names[kern],
+                "frac": achieved / peak, "traffic": profiled_traffic(head, args.n, kern),
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "kernel": names[kern],
                 "kernel_ms": ms4[kern], "flops_per_launch": fl4[kern],
                 "flops_note": ("executed tensor-core flops of the band of K-tiles the pass visits"
                                if bound == "tensor" else
