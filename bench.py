@@ -260,6 +260,44 @@ def run_batched(args, jko, dev, barrier):
     return out
 
 
+def run_differentiation(args, jko, dev, barrier, adam_steps=200):
+    """Potential recovery at 256^2: Adam (lr 1e-2) on w so that the 10-step
+    crowd flow from the disk matches the flow of a hidden potential; every
+    Adam step is one recorded forward flow and one implicit adjoint."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb, w_star = inputs.differentiation_problem(256)
+    h = jko.create_from_problem(pb, precision=jko.Precision.FP32)
+    p0 = torch.tensor(pb.q0, dtype=torch.float32, device=dev)
+    jko.jko_set_potential_device(h, torch.tensor(w_star, device=dev))
+    target, _ = jko.jko_flow_record(h, p0, pb.n_steps)
+    target = target.clone()
+    w = torch.tensor(pb.w, dtype=torch.float32, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([w], lr=1e-2)
+
+    def adam_step():
+        opt.zero_grad()
+        loss = ((jko.jko_flow_autograd(p0, w, h, pb.n_steps) - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        return loss.detach()
+
+    first = float(adam_step())                          # warm-up (not timed)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = [adam_step() for _ in range(adam_steps)]
+    e1.record()
+    barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    jko.jko_destroy(h)
+    return {"workload": "potential recovery 256^2 crowd, gamma=1e-3, tau=0.02, 10 JKO steps "
+                        "(<=200 pairs, tol 1e-6), FP32 forward + implicit adjoint, Adam lr 1e-2",
+            "adam_steps": adam_steps, "seconds": secs, "adam_steps_per_s": adam_steps / secs,
+            "ms_per_adam_step": 1e3 * secs / adam_steps,
+            "loss_first": first, "loss_last": float(losses[-1])}
+
+
 TC_FORMS = ("BF16", "BF16X3", "TF32")
 ALL_FORMS = TC_FORMS + ("FP32",)
 ERR_BAR = 1e-3
@@ -427,6 +465,7 @@ def run_ours(args):
                          f"from the warmed-up state ({secs:.1f} s, NumPy/BLAS, separable xi)"}
 
     batched = run_batched(args, jko, dev, barrier) if args.batched else None
+    diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
                  "steps_timed": len(runs[f]["infos"]),
@@ -460,6 +499,8 @@ def run_ours(args):
         }
         if batched is not None:
             line["batched"] = batched
+        if diff is not None:
+            line["differentiation"] = diff
         print(json.dumps(line), flush=True)
     for r in runs.values():
         jko.jko_destroy(r["h"])
@@ -480,6 +521,9 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--diff", action="store_true",
+                    help="also time 200 Adam steps of potential recovery at 256^2 "
+                         "(forward flow + implicit adjoint)")
     ap.add_argument("--batched", action="store_true",
                     help="also time the 256-flow batched workload (adds a 'batched' key)")
     args = ap.parse_args()

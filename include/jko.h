@@ -201,6 +201,13 @@ jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* params,
  * (or be of the congestion kind).  Used between gradient steps. */
 jko_status jko_set_potential(jko_handle* h, const double* w_host);
 
+/* jko_set_potential from a DEVICE image w_dev of N entries in the handle's
+ * element type (double for JKO_FP64, float otherwise), stream-ordered on the
+ * handle's stream: no host synchronisation, no allocation, no finiteness
+ * check (a non-finite w makes the next step report JKO_ERR_NUMERIC).  The
+ * caller keeps w_dev alive until the work queued on the stream has run. */
+jko_status jko_set_potential_device(jko_handle* h, const void* w_dev);
+
 /* jko_flow that also records, for every step t, its input q_t and the final
  * scaling a_t (the tape of jko_flow_backward).  p_final_dev receives p_n;
  * infos (may be NULL) n_steps reports.  JKO_ERR_UNSUPPORTED for tensor-core

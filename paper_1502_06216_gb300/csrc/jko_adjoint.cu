@@ -260,12 +260,24 @@ jko_status backward_dispatch(jko_handle* h, const void* gf, void* gp, void* gw, 
   }
 }
 
-template <typename T>
-__global__ void k_set_potential(const double* w, T* E, T* sw, double sigma, long long n) {
+template <typename T, typename W>
+__global__ void k_set_potential(const W* w, T* E, T* sw, double sigma, long long n) {
   GS(i, n) {
-    if (E) E[i] = (T)exp(-sigma * w[i]);
-    if (sw) sw[i] = (T)(sigma * w[i]);
+    const double wi = (double)w[i];
+    if (E) E[i] = (T)exp(-sigma * wi);
+    if (sw) sw[i] = (T)(sigma * wi);
   }
+}
+
+jko_status check_set_potential(jko_handle* h, const void* w) {
+  if (!h || !w) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
+  if (h->tc && jko::tc_absorbed(h->tc))
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the potential is absorbed into the Gibbs factors of this handle");
+  if (h->ek != jko::EK_CROWD && !h->sw)
+    return jko::handle_error(h, JKO_ERR_INVALID_ARG,
+                             "the handle was created without a potential (w = NULL)");
+  return JKO_OK;
 }
 
 }  // namespace
@@ -273,13 +285,7 @@ __global__ void k_set_potential(const double* w, T* E, T* sw, double sigma, long
 extern "C" {
 
 jko_status jko_set_potential(jko_handle* h, const double* w_host) {
-  if (!h || !w_host) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
-  if (h->tc && jko::tc_absorbed(h->tc))
-    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "the potential is absorbed into the Gibbs factors of this handle");
-  if (h->ek != jko::EK_CROWD && !h->sw)
-    return jko::handle_error(h, JKO_ERR_INVALID_ARG,
-                             "the handle was created without a potential (w = NULL)");
+  if (jko_status st = check_set_potential(h, w_host)) return st;
   const long long N = h->N;
   for (long long i = 0; i < N; ++i)
     if (!std::isfinite(w_host[i])) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "w must be finite");
@@ -289,14 +295,28 @@ jko_status jko_set_potential(jko_handle* h, const double* w_host) {
   const double sigma = h->prm.tau / h->prm.gamma;
   if (e == cudaSuccess) {
     if (h->fp64)
-      k_set_potential<double><<<grid_for(N), NT, 0, h->stream>>>(wd, (double*)h->E, (double*)h->sw, sigma, N);
+      k_set_potential<double, double><<<grid_for(N), NT, 0, h->stream>>>(wd, (double*)h->E, (double*)h->sw, sigma, N);
     else
-      k_set_potential<float><<<grid_for(N), NT, 0, h->stream>>>(wd, (float*)h->E, (float*)h->sw, sigma, N);
+      k_set_potential<float, double><<<grid_for(N), NT, 0, h->stream>>>(wd, (float*)h->E, (float*)h->sw, sigma, N);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(wd);
   ACK(e);
+  return JKO_OK;
+}
+
+jko_status jko_set_potential_device(jko_handle* h, const void* w_dev) {
+  if (jko_status st = check_set_potential(h, w_dev)) return st;
+  const long long N = h->N;
+  const double sigma = h->prm.tau / h->prm.gamma;
+  if (h->fp64)
+    k_set_potential<double, double><<<grid_for(N), NT, 0, h->stream>>>(
+        (const double*)w_dev, (double*)h->E, (double*)h->sw, sigma, N);
+  else
+    k_set_potential<float, float><<<grid_for(N), NT, 0, h->stream>>>(
+        (const float*)w_dev, (float*)h->E, (float*)h->sw, sigma, N);
+  ACK(cudaGetLastError());
   return JKO_OK;
 }
 

@@ -316,7 +316,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
       return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
   }
 
-  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, N, P, h->ctrl, st));
+  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, N, P, h->ctrl, h->part, h->part_cap, st));
   if (p_out) CK(h, jko::launch_finalize_write<T>((const T*)h->p, p_out, N, h->prm.renormalize, h->ctrl, st));
   CK(h, cudaEventRecord(h->ev1, st));
   CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
@@ -445,6 +445,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   {
     const int np = std::max(h->nparts_simt, jko::tc_partials(grid->nx, grid->ny));
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
+    h->part_cap = np;
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(partials)"));
     e = cudaMemset(h->part, 0, sizeof(double) * np);
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(partials)"));
@@ -714,7 +715,8 @@ cudaError_t flow_chunk(jko_handle* h, int C, cudaStream_t s) {
 template <typename T>
 cudaError_t flow_finalize_t(jko_handle* h, cudaStream_t s) {
   ProxArgs<T> P = jko::prox_args<T>(h);
-  cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->N, P, h->ctrl, s);
+  cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->N, P, h->ctrl, h->part,
+                                                 h->part_cap, s);
   if (e != cudaSuccess) return e;
   // the step output becomes the input of the next step
   return jko::launch_finalize_write<T>((const T*)h->p, (T*)h->q, h->N, h->prm.renormalize,

@@ -45,10 +45,12 @@ template <typename T>
 cudaError_t launch_validate(const T* q, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
                             cudaStream_t st);
 
-// ctrl->mass = sum p, ctrl->maxpk_bits = max p/kappa, flags non-finite p.
+// ctrl->mass = sum p (FP64, fixed summation order: one partial per block in
+// part[0 .. min(blocks, part_cap)), added by the last block), ctrl->maxpk_bits
+// = max p/kappa, flags non-finite p.  part must not be in use by other work.
 template <typename T>
 cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
-                                   cudaStream_t st);
+                                   double* part, int part_cap, cudaStream_t st);
 
 // out = renorm ? p / ctrl->mass : p   (out may alias p)
 template <typename T>

@@ -267,7 +267,7 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
   }
   if (!stopped) return fail(JKO_ERR_TIMEOUT, "jko_step_noalloc: no stop within the budget");
 
-  NA_CK(jko::launch_finalize_reduce<float>(img[S_P], N, P, ctrl, st));
+  NA_CK(jko::launch_finalize_reduce<float>(img[S_P], N, P, ctrl, part, kMaxParts, st));
   NA_CK(jko::launch_finalize_write<float>(img[S_P], (float*)p_out_dev, N, prm->renormalize, ctrl, st));
   NA_CK(cudaMemcpyAsync(&host, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));

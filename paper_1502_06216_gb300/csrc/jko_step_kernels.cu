@@ -1,6 +1,8 @@
 // jko_step_kernels.cu -- per-step prologue and epilogue kernels: fill, input
 // validation, and the FP64 mass / congestion statistics with the optional
 // mass renormalisation of the step output.
+#include <algorithm>
+
 #include "jko_kernels.h"
 
 namespace jko {
@@ -56,8 +58,10 @@ __global__ void validate_kernel(const T* q, long long n, ProxArgs<T> P, Ctrl* ct
 }
 
 template <typename T>
-__global__ void finalize_reduce_kernel(const T* p, long long n, ProxArgs<T> P, Ctrl* ctrl) {
+__global__ void finalize_reduce_kernel(const T* p, long long n, ProxArgs<T> P, Ctrl* ctrl,
+                                       double* part) {
   __shared__ double s_red[33];
+  __shared__ int s_last;
   double sum = 0.0;
   double mx = 0.0;
   int bad = 0;
@@ -79,7 +83,23 @@ __global__ void finalize_reduce_kernel(const T* p, long long n, ProxArgs<T> P, C
     if (mx > 0.0) atomicMax(&ctrl->maxpk_bits, (unsigned long long)__double_as_longlong(mx));
     if (bad) atomicOr(&ctrl->nonfinite, 1);
   }
-  if (threadIdx.x == 0) atomicAdd(&ctrl->mass, sum);
+  // The mass is summed in a fixed order, so that repeated runs give the same
+  // bits: one partial per block, and the last block to arrive adds them up.
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sum;
+    __threadfence();
+    s_last = atomicAdd(&ctrl->arrive_f, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) tot += __ldcg(part + i);
+  tot = block_sum(tot, s_red);
+  if (threadIdx.x == 0) {
+    ctrl->mass = tot;
+    ctrl->arrive_f = 0;
+  }
 }
 
 template <typename T>
@@ -118,8 +138,10 @@ cudaError_t launch_validate(const T* q, long long n, const ProxArgs<T>& P, Ctrl*
 
 template <typename T>
 cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P, Ctrl* ctrl,
-                                   cudaStream_t st) {
-  finalize_reduce_kernel<T><<<grid_for(n), NT, 0, st>>>(p, n, P, ctrl);
+                                   double* part, int part_cap, cudaStream_t st) {
+  if (!part || part_cap < 1) return cudaErrorInvalidValue;
+  const int g = std::min(grid_for(n), part_cap);
+  finalize_reduce_kernel<T><<<g, NT, 0, st>>>(p, n, P, ctrl, part);
   return cudaGetLastError();
 }
 
@@ -155,7 +177,7 @@ cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_
   template cudaError_t launch_validate<T>(const T*, long long, const ProxArgs<T>&, Ctrl*, \
                                           cudaStream_t);                                \
   template cudaError_t launch_finalize_reduce<T>(const T*, long long, const ProxArgs<T>&, \
-                                                 Ctrl*, cudaStream_t);                  \
+                                                 Ctrl*, double*, int, cudaStream_t);    \
   template cudaError_t launch_finalize_write<T>(const T*, T*, long long, int, const Ctrl*, \
                                                 cudaStream_t);
 JKO_INST(float)

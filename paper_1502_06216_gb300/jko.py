@@ -92,6 +92,7 @@ EXPORTS = {
                                         ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(jko_step_info)]),
     "jko_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "jko_set_potential_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "jko_flow_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_void_p, ctypes.POINTER(jko_step_info)]),
     "jko_flow_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -403,6 +404,16 @@ def jko_set_potential(h: Handle, w) -> None:
     _check(lib().jko_set_potential(h.ptr, ctypes.c_void_p(wh.ctypes.data)), h.ptr)
 
 
+def jko_set_potential_device(h: Handle, w) -> None:
+    """Replaces the potential w from a device tensor (cast to the handle's
+    element type), stream-ordered on the current stream."""
+    wd = w.detach().to(h.dtype).contiguous()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_set_potential_device(h.ptr, _dev_image(h, wd, "w")), h.ptr)
+    return wd
+
+
 def jko_flow_record(h: Handle, p0, n_steps: int):
     """jko_flow that records the tape for jko_flow_backward; returns (p_n, infos)."""
     import torch
@@ -440,8 +451,13 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, p0, w, handle, n_steps):
-            jko_set_potential(handle, w.detach().double().cpu().numpy())
+            if w.is_cuda:
+                wd = jko_set_potential_device(handle, w)
+            else:
+                jko_set_potential(handle, w.detach().double().cpu().numpy())
             pT, _ = jko_flow_record(handle, p0.detach().to(handle.dtype).contiguous(), n_steps)
+            if w.is_cuda:
+                del wd      # flow_record synchronised: the potential kernel has run
             ctx.handle = handle
             ctx.w_meta = (w.dtype, w.device)
             ctx.p0_meta = (p0.dtype, p0.device)

@@ -80,3 +80,46 @@ def test_adjoint_matches_finite_differences_fp64_and_fp32():
     print("FD rel err: FP64 adjoint", worst64, "FP32 adjoint", worst32)
     assert worst64 <= 1e-3
     assert worst32 <= 1e-3
+
+
+def test_set_potential_device_matches_host():
+    """The device form of jko_set_potential gives the flow of the host form:
+    bitwise for FP64 handles, to FP32 rounding of w for FP32 handles."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pb, w_star = problem(64)
+    for prec, bar in (("FP64", 0.0), ("FP32", 1e-5)):
+        h = jko.create_from_problem(pb, precision=jko.Precision[prec], tol=1e-7, max_iter=2000)
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device="cuda")
+        jko.jko_set_potential(h, w_star)
+        ph, _ = jko.jko_flow_record(h, p0, 3)
+        jko.jko_set_potential_device(h, torch.tensor(w_star, device="cuda"))
+        pd, _ = jko.jko_flow_record(h, p0, 3)
+        err = float((ph.double() - pd.double()).abs().sum() / ph.double().abs().sum())
+        print(prec, "host vs device potential rel L1", err)
+        assert err <= bar
+        jko.jko_destroy(h)
+
+
+def test_potential_recovery_decreases_the_loss():
+    """A few Adam steps of the differentiation workload (at 64^2): the loss of
+    matching the flow of the hidden potential goes down."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pb, w_star = problem(64)
+    h = jko.create_from_problem(pb, precision=jko.Precision.FP32, tol=1e-6, max_iter=500)
+    p0 = torch.tensor(pb.q0, dtype=torch.float32, device="cuda")
+    jko.jko_set_potential_device(h, torch.tensor(w_star, device="cuda"))
+    target, _ = jko.jko_flow_record(h, p0, 10)
+    w = torch.tensor(pb.w, dtype=torch.float32, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([w], lr=1e-2)
+    losses = []
+    for _ in range(8):
+        opt.zero_grad()
+        loss = ((jko.jko_flow_autograd(p0, w, h, 10) - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    print("losses", losses)
+    assert losses[-1] < 0.5 * losses[0]
+    jko.jko_destroy(h)

@@ -99,3 +99,15 @@ def test_tc_and_simt_agree_on_bench_state():
     err = rel_l1(outs["BF16X3"].double().cpu().numpy(), outs["FP32"].double().cpu().numpy())
     print("BF16X3 vs FP32 after 50 pairs from step 5:", err)
     assert err <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["BF16", "FP32"])
+def test_flow_is_bitwise_reproducible(prec):
+    """Two runs of the same flow give the same bits: every reduction (residual
+    partials, mass) adds in a fixed order."""
+    pb = inputs.config_problem(2, n=256, n_steps=3)
+    t1, i1 = gpu_flow(pb, prec, 3)
+    t2, i2 = gpu_flow(pb, prec, 3)
+    assert np.array_equal(t1, t2)
+    assert [i["iters"] for i in i1] == [i["iters"] for i in i2]
+    assert [i["mass"] for i in i1] == [i["mass"] for i in i2]
