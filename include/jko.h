@@ -88,6 +88,10 @@ typedef struct jko_params {
   int renormalize;  /* 1: divide each output p by its FP64 sum; 0: leave as computed */
   int absorb;       /* tensor-core precisions: separable log-domain absorption of the
                        potential (see jko_create); 0 = automatic, 1 = on, 2 = off */
+  int loop;         /* tensor-core precisions: 0 = automatic (one persistent kernel per
+                       chunk of check_every pairs where the device and the grid allow
+                       it, else one kernel per pass), 1 = persistent kernel required
+                       (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one kernel per pass */
 } jko_params;
 
 /* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */
@@ -162,6 +166,14 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
  * operations of one launch.  Overwrites the handle's scaling iterates: call it
  * between flows, not inside one. */
 jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops);
+
+/* Times the persistent pair-loop kernel of a tensor-core handle: `reps`
+ * launches, each running `pairs` pairs with a stop rule that never fires.
+ * ms[0] receives the mean milliseconds per launch (CUDA events on the handle's
+ * stream) and flops[0] (may be NULL) the executed tensor-core flops of one
+ * launch.  JKO_ERR_UNSUPPORTED when the handle does not use that kernel.
+ * Overwrites the handle's scaling iterates, like jko_profile_passes. */
+jko_status jko_profile_loop(jko_handle* h, int pairs, int reps, float* ms, double* flops);
 
 /* One JKO step without any memory allocation (the paper has no counterpart;
  * this is a deployment variant of jko_step).

@@ -139,14 +139,34 @@ jko_status capture_chunk(jko_handle* h) {
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i) e = enqueue_pair(h, h->cap);
+  if (h->use_loop) e = jko::tc_enqueue_loop(h->tc, h->chunk_iters, h->cap);
+  else
+    for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i) e = enqueue_pair(h, h->cap);
   cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  if (h->use_loop && (e != cudaSuccess || e2 != cudaSuccess)) {
+    // a chunk is one launch: without a graph it is launched directly
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->chunk = nullptr;
+    return JKO_OK;
+  }
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_err(h, e, "capture of the iteration chunk"); }
   CK(h, e2);
   e = cudaGraphInstantiate(&h->chunk, g, 0);
   cudaGraphDestroy(g);
+  if (h->use_loop && e != cudaSuccess) {
+    cudaGetLastError();
+    h->chunk = nullptr;
+    return JKO_OK;
+  }
   CK(h, e);
   return JKO_OK;
+}
+
+// One chunk of check_every pairs on stream st.
+cudaError_t launch_chunk(jko_handle* h, cudaStream_t st) {
+  if (h->chunk) return cudaGraphLaunch(h->chunk, st);
+  return jko::tc_enqueue_loop(h->tc, h->chunk_iters, st);
 }
 
 void free_handle(jko_handle* h) {
@@ -183,6 +203,8 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (p->check_every < 0) return set_err(nullptr, JKO_ERR_INVALID_ARG, "check_every must be >= 0");
   if (p->precision < JKO_FP64 || p->precision > JKO_BF16X3)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
+  if (p->loop < 0 || p->loop > 2)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "loop must be 0 (automatic), 1 or 2");
   if (p->absorb < 0 || p->absorb > 2)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "absorb must be 0 (automatic), 1 or 2");
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
@@ -288,8 +310,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   int launched = 0, polled = 0;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   auto launch = [&]() -> cudaError_t {
-    h->kernels += 4LL * C;
-    cudaError_t e = cudaGraphLaunch(h->chunk, st);
+    h->kernels += h->use_loop ? 1LL : 4LL * C;
+    cudaError_t e = launch_chunk(h, st);
     if (e != cudaSuccess) return e;
     const int slot = launched & 1;
     e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, 16, cudaMemcpyDeviceToHost, st);
@@ -495,6 +517,13 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     int rc = jko::tc_create(cfg, &h->tc, &msg);
     if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, msg);
     else if (rc != 0) s = set_err(h, JKO_ERR_CUDA, msg);
+    if (s == JKO_OK) {
+      const int ok = jko::tc_loop_supported(h->tc);
+      if (params->loop == 1 && !ok)
+        s = set_err(h, JKO_ERR_UNSUPPORTED,
+                    "the persistent loop kernel cannot run here (nx % 4 != 0 or no cooperative launch)");
+      h->use_loop = params->loop != 2 && ok;
+    }
   }
   if (s != JKO_OK) return fail(s);
   e = cudaDeviceSynchronize();
@@ -598,6 +627,36 @@ jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops)
     if (flops) flops[k] = pass_flops(h, k);
   }
   CK(h, cudaMemcpy(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  return JKO_OK;
+}
+
+jko_status jko_profile_loop(jko_handle* h, int pairs, int reps, float* ms, double* flops) {
+  if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
+  if (pairs < 1 || reps < 1 || !ms) return set_err(h, JKO_ERR_INVALID_ARG, "pairs < 1, reps < 1 or NULL ms");
+  if (!h->use_loop) return set_err(h, JKO_ERR_UNSUPPORTED, "the handle does not use the loop kernel");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = h->stream;
+  // a running control block that never stops (as in jko_profile_passes)
+  Ctrl c0;
+  std::memcpy(&c0, h->ctrl_init, sizeof(Ctrl));
+  c0.it = 1;
+  c0.tol = -1.0;
+  c0.max_iter = 0x7fffffff;
+  CK(h, cudaMemcpy(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  cudaError_t e = jko::tc_enqueue_loop(h->tc, pairs, st);   // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = jko::tc_enqueue_loop(h->tc, pairs, st);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(h->ev1);
+  CK(h, e);
+  float t = 0.f;
+  CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
+  ms[0] = t / reps;
+  if (flops) flops[0] = jko::tc_loop_flops(h->tc, pairs);
+  CK(h, cudaMemcpy(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  const int nf = h->poll[0].nonfinite;
+  CK(h, cudaMemcpy(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  if (nf & 2) return set_err(h, JKO_ERR_TIMEOUT, "a bounded device wait gave up");
   return JKO_OK;
 }
 

@@ -21,8 +21,8 @@ struct Ctrl {
   int done;               // RUNNING / CONVERGED / MAX_ITER / NONFINITE
   int nonfinite;          // set when an epilogue meets NaN or Inf
   int max_iter;           // copy of the step budget
-  unsigned int arrive_b;  // arrival counter of the b-update kernel
-  unsigned int arrive_a;  // arrival counter of the prox / a-update kernel
+  unsigned int bar_base;  // grid barriers the persistent loop kernel completed this step
+  unsigned int bar_spare;
   unsigned int arrive_f;  // arrival counter of the finalisation kernel
   unsigned int arrive_v;  // arrival counter of the validation kernel
   double tol;             // L1 residual tolerance
@@ -36,6 +36,9 @@ struct Ctrl {
   unsigned long long q_bad;       // count of non-finite q
   unsigned long long q_over;      // count of q > kappa (1 + 1e-2)
   unsigned long long q_masked;    // count of q != 0 on the mask
+  // grid barrier of the persistent loop kernel (all 0 at the start of a step)
+  unsigned long long bar_cnt;     // arrivals, G per barrier
+  unsigned int bar_flag[4];       // [b % 3]: some CTA met NaN/Inf or gave up a wait before barrier b
 };
 
 // ---- stop protocol of the scaling loop ----
@@ -254,6 +257,11 @@ template <typename T>
 __device__ __forceinline__ T abs_residual(T b, T Y, T q) { return fabs(fma(b, Y, -q)); }
 
 __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

@@ -1,0 +1,528 @@
+// tc_common.cuh -- shared pieces of the tensor-core kernels (internal): tile
+// constants, tcgen05 / TMA / mbarrier PTX wrappers, the 128-byte-swizzled
+// shared-memory layouts of the epilogue tiles, tensor-map encoding, and the
+// per-handle plan of images, factors and maps.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "jko.h"
+#include "jko_kernels.h"
+#include "tc_gemm.h"
+
+namespace jko {
+
+namespace {
+
+
+constexpr int BM = 128;            // UMMA M (rows of the kernel factor per tile)
+constexpr int KB_BYTES = 128;      // K-block width in bytes (one 128-byte swizzle row)
+constexpr int MAX_STAGES = 8;
+constexpr uint32_t SMEM_BUDGET = 212 * 1024;  // operand stages + epilogue tiles per CTA
+constexpr int NT = 512;            // threads per CTA: 16 warps, 4 per TMEM lane quadrant
+constexpr int NWG = NT / 128;      // warps sharing one quadrant (column groups)
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier polls
+
+enum : int { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_TF32 = 2 };
+
+// Bytes of one pipeline stage.
+__host__ __device__ constexpr uint32_t stage_bytes(int mode, int bn) {
+  return (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)(BM + bn) * (uint32_t)KB_BYTES;
+}
+// Epilogue tiles kept beside the stages: b-update pass -> q (fp32) and the old
+// b (operand type, hi [+ lo]); prox pass -> e^{-sigma w} (fp32) and the staged
+// p (fp32).  Epilogue numbering as in jko_kernels.h (0 store, 1 b, 2 a).
+__host__ __device__ constexpr uint32_t epi_bytes(int mode, int epi, int bn) {
+  return epi == 0 ? 0u
+         : epi == 1 ? (uint32_t)bn * BM * 4u +
+                          (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)bn * BM *
+                              (mode == MODE_TF32 ? 4u : 2u)
+                    : 2u * (uint32_t)bn * BM * 4u;
+}
+// Bytes the producer loads into the epilogue tiles (the p tile is only stored).
+__host__ __device__ constexpr uint32_t epi_load_bytes(int mode, int epi, int bn) {
+  return epi == 2 ? (uint32_t)bn * BM * 4u : epi_bytes(mode, epi, bn);
+}
+__host__ __device__ constexpr int num_stages(int mode, int epi, int bn) {
+  return (SMEM_BUDGET - epi_bytes(mode, epi, bn)) / stage_bytes(mode, bn) < (uint32_t)MAX_STAGES
+             ? (int)((SMEM_BUDGET - epi_bytes(mode, epi, bn)) / stage_bytes(mode, bn))
+             : MAX_STAGES;
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after kSpinLimit polls (the caller records a fault).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+// Programmatic dependent launch: the next kernel of the stream may start its
+// set-up once every CTA of this one has signalled; griddepcontrol.wait blocks
+// until the preceding kernel has completed and its writes are visible.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accum) {
+  if (MODE == MODE_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x,
+                                             int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          (uint64_t)map),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Barrier among the first `n` threads (whole warps) of the block, id 1..15.
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Issue-only TMEM load of 16 columns (32-bit) of this warp's 32 lanes; the
+// values are valid after tmem_wait_ld() and reg_fence16().
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Ties the registers of an issued TMEM load to the point after the wait, so
+// that the compiler schedules no use of them before it.
+__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);      // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8-row groups
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B bf16 (kind::f16) or tf32, both K-major.
+template <int MODE>
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | ((MODE == MODE_TF32 ? 2u : 1u) << 7) | ((MODE == MODE_TF32 ? 2u : 1u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MODE> struct OpT;
+template <> struct OpT<MODE_BF16> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
+template <> struct OpT<MODE_BF16X3> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
+template <> struct OpT<MODE_TF32> { using T = float; static constexpr int kElems = 32; };
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Operand value of one image element (hi [+ lo]) as float.
+template <int MODE, typename T>
+__device__ __forceinline__ float op_load(const T* hi, const T* lo, size_t i) {
+  if constexpr (MODE == MODE_TF32) return hi[i];
+  else if constexpr (MODE == MODE_BF16X3) return __bfloat162float(hi[i]) + __bfloat162float(lo[i]);
+  else return __bfloat162float(hi[i]);
+}
+template <int MODE, typename T>
+__device__ __forceinline__ void op_store(T* hi, T* lo, size_t i, float v) {
+  if constexpr (MODE == MODE_TF32) {
+    hi[i] = tf32_round(v);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    if constexpr (MODE == MODE_BF16X3) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// 16 consecutive fp32 of one row: vector loads when the row segment is
+// 16-byte aligned and complete, scalar loads of the first `cnt` otherwise.
+__device__ __forceinline__ void load_f32x16(const float* src, int cnt, bool vec, float (&o)[16]) {
+  if (vec && cnt == 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(src) + q);
+      o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = j < cnt ? src[j] : 0.0f;
+  }
+}
+__device__ __forceinline__ void store_f32x16(float* dst, int cnt, bool vec, const float (&v)[16]) {
+  if (vec && cnt == 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      reinterpret_cast<float4*>(dst)[q] =
+          make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < cnt) dst[j] = v[j];
+  }
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+  return __bfloat1622float2(h);
+}
+// 16 operand-typed values of one row (rows padded to 16 bytes): the value is
+// hi (+ lo).  Vector loads when the 16 lie inside the valid columns.
+template <int MODE, typename T>
+__device__ __forceinline__ void load_op16(const T* hi, const T* lo, size_t off, int cnt,
+                                          float (&o)[16]) {
+  if (cnt == 16) {
+    if constexpr (MODE == MODE_TF32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = reinterpret_cast<const float4*>(hi + off)[q];
+        o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint4 t = reinterpret_cast<const uint4*>(hi + off)[q];
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(w[k]);
+          o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
+        }
+      }
+      if constexpr (MODE == MODE_BF16X3) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint4 t = reinterpret_cast<const uint4*>(lo + off)[q];
+          const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 f = unpack_bf16x2(w[k]);
+            o[8 * q + 2 * k] += f.x; o[8 * q + 2 * k + 1] += f.y;
+          }
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = j < cnt ? op_load<MODE>(hi, lo, off + j) : 0.0f;
+  }
+}
+// Writes 16 values of local row r, columns 16c .. 16c+15, into the staging
+// tile in the layout of a 128-byte-swizzled TMA box of 128 rows: column block
+// cb holds 128 bytes per row; the 16-byte chunk k of row r sits at k ^ (r & 7).
+template <int MODE>
+__device__ __forceinline__ void stage16(unsigned char* st_hi, unsigned char* st_lo, int r, int c,
+                                        const float (&o)[16]) {
+  constexpr uint32_t BLK = BM * 128;
+  if constexpr (MODE == MODE_TF32) {
+    const int cb = c >> 1, k0 = (c & 1) * 4;
+    unsigned char* row = st_hi + cb * BLK + r * 128;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 u;
+      u.x = __float_as_uint(tf32_round(o[4 * q]));
+      u.y = __float_as_uint(tf32_round(o[4 * q + 1]));
+      u.z = __float_as_uint(tf32_round(o[4 * q + 2]));
+      u.w = __float_as_uint(tf32_round(o[4 * q + 3]));
+      *reinterpret_cast<uint4*>(row + (((k0 + q) ^ (r & 7)) << 4)) = u;
+    }
+  } else {
+    const int cb = c >> 2, k0 = (c & 3) * 2;
+    unsigned char* row_hi = st_hi + cb * BLK + r * 128;
+    unsigned char* row_lo = st_lo + cb * BLK + r * 128;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float h[8], l[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float v = o[8 * q + k];
+        h[k] = __bfloat162float(__float2bfloat16_rn(v));
+        l[k] = v - h[k];
+      }
+      uint4 u;
+      u.x = pack_bf16x2(h[0], h[1]); u.y = pack_bf16x2(h[2], h[3]);
+      u.z = pack_bf16x2(h[4], h[5]); u.w = pack_bf16x2(h[6], h[7]);
+      *reinterpret_cast<uint4*>(row_hi + (((k0 + q) ^ (r & 7)) << 4)) = u;
+      if constexpr (MODE == MODE_BF16X3) {
+        uint4 w;
+        w.x = pack_bf16x2(l[0], l[1]); w.y = pack_bf16x2(l[2], l[3]);
+        w.z = pack_bf16x2(l[4], l[5]); w.w = pack_bf16x2(l[6], l[7]);
+        *reinterpret_cast<uint4*>(row_lo + (((k0 + q) ^ (r & 7)) << 4)) = w;
+      }
+    }
+  }
+}
+
+// 16 fp32 of row r, columns 16c .. 16c+15, of a 128-byte-swizzled fp32 tile
+// (column blocks of 32 floats x 128 rows, 16-byte chunk k of row r at k ^ (r & 7)).
+__device__ __forceinline__ void smem_ld_f32x16(const unsigned char* reg, int r, int c,
+                                               float (&o)[16]) {
+  const int cb = c >> 1, k0 = (c & 1) * 4;
+  const unsigned char* row = reg + cb * (BM * 128) + r * 128;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 t = *reinterpret_cast<const float4*>(row + (((k0 + q) ^ (r & 7)) << 4));
+    o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void smem_st_f32x16(unsigned char* reg, int r, int c,
+                                               const float (&v)[16]) {
+  const int cb = c >> 1, k0 = (c & 1) * 4;
+  unsigned char* row = reg + cb * (BM * 128) + r * 128;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<float4*>(row + (((k0 + q) ^ (r & 7)) << 4)) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+// 16 operand values (hi [+ lo]) of row r, columns 16c .., from swizzled tiles.
+template <int MODE>
+__device__ __forceinline__ void smem_ld_op16(const unsigned char* hi, const unsigned char* lo,
+                                             int r, int c, float (&o)[16]) {
+  if constexpr (MODE == MODE_TF32) {
+    smem_ld_f32x16(hi, r, c, o);
+  } else {
+    const int cb = c >> 2, k0 = (c & 3) * 2;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const size_t off = cb * (BM * 128) + r * 128 + (((k0 + q) ^ (r & 7)) << 4);
+      const uint4 t = *reinterpret_cast<const uint4*>(hi + off);
+      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = unpack_bf16x2(w[k]);
+        o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
+      }
+      if constexpr (MODE == MODE_BF16X3) {
+        const uint4 u = *reinterpret_cast<const uint4*>(lo + off);
+        const uint32_t z[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(z[k]);
+          o[8 * q + 2 * k] += f.x; o[8 * q + 2 * k + 1] += f.y;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D tensor map of a row-major [rows][pitch] operand matrix whose first
+// `cols` columns are valid; box = box_rows x (128 bytes of K).
+bool make_map(CUtensorMap* map, void* base, int mode, int rows, int cols, int pitch, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const int es = mode == MODE_TF32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+  cuuint32_t box[2] = {(cuuint32_t)(KB_BYTES / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, mode == MODE_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+namespace {
+// Sum of one float per thread over 16 warps (threads 0..511) in a fixed order:
+// each warp's butterfly, then warp 0 over the 16 warp sums.  `sync` is the
+// barrier of those 512 threads.  The result is valid in thread 0.
+template <typename Sync>
+__device__ __forceinline__ float tile_sum16(float v, float* scratch, Sync sync) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum_f(v);
+  if (lane == 0) scratch[warp] = v;
+  sync();
+  float t = 0.0f;
+  if (warp == 0) {
+    t = lane < 16 ? scratch[lane] : 0.0f;
+    t = warp_sum_f(t);
+  }
+  return t;
+}
+}  // namespace
+
+struct TcPlan {
+  TcConfig cfg;
+  int mode = MODE_BF16;
+  int bn_x = 64, bn_y = 64;   // BN of the pass over x (N = ny) and over y (N = nx)
+  int rx = 0, ry = 0;          // band radii
+  int px = 0, py = 0;          // pitches (elements) of images with x / y contiguous
+  // factors [axis 0 = x, 1 = y][side 0 = a (xi a), 1 = b (xi b)][hi, lo]; without
+  // absorption the b side aliases the a side (the factor is symmetric)
+  void* k[2][2][2] = {};
+  int2* kbt[2][2] = {};        // per-tile K-block ranges of each factor
+  float* E_abs = nullptr;      // absorbed e^{-(sigma w + beta)} (congestion kind)
+  float* sw_abs = nullptr;     // absorbed sigma w + beta (entropy kinds)
+  int absorbed = 0;
+  void* img_a[2] = {nullptr, nullptr};   // [ny][px]
+  void* img_b[2] = {nullptr, nullptr};   // [ny][px]
+  void* img_t[2] = {nullptr, nullptr};   // [nx][py]
+  CUtensorMap mK[2][2][2];                          // factor loads [axis][side][split]
+  CUtensorMap mA[2], mB[2], mT[2];                  // image operand loads
+  CUtensorMap sA[2], sB[2], sT[2];                  // epilogue stores (box 128 rows)
+  CUtensorMap fQ, fE, fP;                           // fp32 fields q, e^{-sigma w}, p
+  int tma_epi = 0;
+  double flops[4] = {0, 0, 0, 0};
+  // persistent pair-loop kernel (tc_loop.cu): image operand loads with 64-row
+  // boxes, support flag, grid size and executed flops of one pair
+  CUtensorMap lA[2], lB[2], lT[2];
+  int loop_ok = 0;
+  int loop_grid = 0;
+  double loop_flops_pair = 0.0;
+};
+
+}  // namespace jko

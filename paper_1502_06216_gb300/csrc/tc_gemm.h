@@ -48,4 +48,15 @@ cudaError_t tc_enqueue_pass(TcPlan* plan, int which, cudaStream_t st);
 double tc_pass_flops(const TcPlan* plan, int which);
 void tc_destroy(TcPlan* plan);
 
+// Persistent pair-loop kernel (tc_loop.cu).  Set-up after the plan's images
+// and maps exist: 0 = ok (tc_loop_supported tells whether it can run),
+// 2 = CUDA error.
+int tc_loop_setup(TcPlan* plan, std::string* msg);
+int tc_loop_supported(const TcPlan* plan);
+// One cooperative launch running up to `pairs` pairs of the scaling loop with
+// the stop protocol in the kernel (same Ctrl as the per-pass kernels).
+cudaError_t tc_enqueue_loop(TcPlan* plan, int pairs, cudaStream_t st);
+// Executed tensor-core flops of `pairs` pairs of the loop kernel.
+double tc_loop_flops(const TcPlan* plan, int pairs);
+
 }  // namespace jko

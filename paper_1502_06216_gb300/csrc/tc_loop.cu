@@ -1,0 +1,714 @@
+// tc_loop.cu -- the scaling loop as one persistent tensor-core kernel per chunk
+// of (odd, even) pairs.
+//
+// The four passes of a pair (see tc_gemm.cu: K_x and K_y contractions of a and
+// b with the b-update + residual and the prox + a-update epilogues) depend on
+// each other through whole images, so a pair needs a grid-wide barrier between
+// passes.  Launched one kernel per pass, every pass pays a launch, the CTA
+// set-up (barriers, TMEM allocation, descriptor fetch) and a cold operand
+// pipeline, and the next pass cannot start early: a CTA holds ~200 KB of
+// shared memory, so no CTA of the next kernel fits beside it on an SM.
+//
+// Here one cooperative launch with one CTA per SM runs up to `pairs` pairs:
+//   * warp 16 (one lane) is the TMA producer, warp 17 (one lane) issues
+//     tcgen05.mma, warps 0-15 drain TMEM through the epilogue;
+//   * a CTA takes the tiles blockIdx.x, blockIdx.x + G, ... of every pass;
+//   * between passes the epilogue warps meet every other CTA at a grid
+//     barrier: one release-add on a 64-bit arrival counter in Ctrl that never
+//     resets within a step (barrier b is complete at G b arrivals) and a
+//     bounded acquire poll; a CTA that met NaN/Inf or gave up a wait sets the
+//     flag slot of that barrier, and every CTA reads the slot after the
+//     barrier and acts on it at the next one, so all stop at the same pass;
+//   * before the barrier the producer has already loaded what does not depend
+//     on the previous pass: the Gibbs-factor K-blocks of its next tile (only
+//     the MMA reads them) and the epilogue tiles (q and e^{-sigma w} are fixed
+//     during the step; the old b is this CTA's own tile), so after it only the
+//     image K-blocks remain to be fetched;
+//   * the stop rule (Sec. 3.4) uses the per-tile residual partials of the
+//     b-update pass, added in a fixed order by every CTA while pass 2 (the
+//     x-contraction of xi b) runs, and takes effect at the barrier before the
+//     prox pass: when it fires, pass 2 has only rewritten the intermediate
+//     image, and p, a, b are those of the pair the residual belongs to.
+// The arithmetic of each tile is that of tc_pass_kernel with 64-wide tiles,
+// so the two forms give the same bits when the per-pass form also uses them.
+#include "tc_common.cuh"
+
+namespace jko {
+
+namespace {
+
+constexpr int LBN = 64;                      // output tile width of every pass
+constexpr int NEPI = 512;                    // epilogue threads: 16 warps, 4 per TMEM quadrant
+constexpr int NTL = NEPI + 64;               // + producer warp + MMA warp
+constexpr int WARP_PROD = 16;
+constexpr int WARP_MMA = 17;
+constexpr int EPI_BAR = 1;                   // named barrier of the epilogue warps
+constexpr uint32_t LOOP_SMEM_BUDGET = 224 * 1024;
+constexpr uint32_t kGridSpinLimit = 1u << 24;
+constexpr uint32_t kGoSpinLimit = 1u << 27;
+
+// output staging tile (operand type, hi [+ lo]) and epilogue region (two fp32
+// tiles: q | old b in the b-update pass, e^{-sigma w} | p in the prox pass)
+__host__ __device__ constexpr uint32_t loop_staging_bytes(int mode) {
+  return (mode == MODE_BF16 ? 1u : 2u) * (uint32_t)LBN * BM * 2u;
+}
+__host__ __device__ constexpr uint32_t loop_epi_bytes() { return 2u * LBN * BM * 4u; }
+__host__ __device__ constexpr int loop_stages(int mode) {
+  return (LOOP_SMEM_BUDGET - loop_epi_bytes() - loop_staging_bytes(mode)) / stage_bytes(mode, LBN) <
+                 (uint32_t)MAX_STAGES
+             ? (int)((LOOP_SMEM_BUDGET - loop_epi_bytes() - loop_staging_bytes(mode)) /
+                     stage_bytes(mode, LBN))
+             : MAX_STAGES;
+}
+__host__ __device__ constexpr size_t loop_smem_bytes(int mode) {
+  return (size_t)loop_stages(mode) * stage_bytes(mode, LBN) + loop_staging_bytes(mode) +
+         loop_epi_bytes() + 1024 + (size_t)(2 * loop_stages(mode) + 6) * 8 + 16;
+}
+
+struct LoopPass {
+  int M, N;          // output D is M x N (M along the contracted axis)
+  int tiles_n;       // tiles along N
+  int ntiles;        // tiles of the pass
+  const int2* kbt;   // per 128-row tile: first K-block and count of the factor band
+};
+
+struct LoopArgs {
+  LoopPass pass[4];
+  Ctrl* ctrl;
+  ProxArgs<float> P;
+  double* part;      // residual partial of each tile of the b-update pass
+  int nparts;
+  int pairs;         // pairs this launch may run
+};
+
+// Tensor maps of the four passes: factor (A), image (B) and output of each
+// pass (hi, lo), and the fp32 fields.
+struct LoopMaps {
+  CUtensorMap K[4][2];
+  CUtensorMap B[4][2];
+  CUtensorMap O[4][2];
+  CUtensorMap Q, E, P;
+};
+
+// Grid-wide barrier number b (1, 2, ... within the step) of the G
+// co-resident CTAs, called by one thread per CTA after the CTA's writes.
+// `flag`: this CTA met NaN/Inf or gave up a wait.  False if the poll gave up.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned G, unsigned b, bool flag) {
+  if (flag) atomicOr(&ctrl->bar_flag[b % 3], 1u);
+  red_release_add_u64(&ctrl->bar_cnt, 1ull);
+  const unsigned long long target = (unsigned long long)G * b;
+  for (uint32_t i = 0; i < kGridSpinLimit; ++i)
+    if (ld_acquire_gpu_u64(&ctrl->bar_cnt) >= target) return true;
+  return false;
+}
+
+// Bounded wait until the epilogue leader has published the barrier of pass q.
+__device__ __forceinline__ bool wait_go(const int* s_go, int q) {
+  for (uint32_t i = 0; i < kGoSpinLimit; ++i) {
+    if (*(const volatile int*)s_go >= q) {
+      __threadfence_block();
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int MODE, int EK>
+__global__ void __launch_bounds__(NTL, 1)
+tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ LoopArgs args) {
+  using T = typename OpT<MODE>::T;
+  constexpr int KE = OpT<MODE>::kElems;
+  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
+  constexpr uint32_t A_BYTES = BM * KB_BYTES;
+  constexpr uint32_t B_BYTES = LBN * KB_BYTES;
+  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  constexpr int STAGES = loop_stages(MODE);
+  static_assert(STAGE_BYTES == stage_bytes(MODE, LBN), "stage size");
+  static_assert(STAGES >= 2, "at least two stages");
+  constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
+  constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
+  constexpr uint32_t TMEM_COLS = LBN;
+  constexpr uint32_t IDESC = make_idesc<MODE>(BM, LBN);
+  constexpr int CB = LBN * (int)sizeof(T) / 128;   // 128-byte column blocks of an operand tile
+  constexpr uint32_t OUT_BLOCK = BM * 128;
+  static_assert((uint32_t)NSPLIT * CB * OUT_BLOCK <= STG_BYTES, "staging tile");
+  static_assert((uint32_t)NSPLIT * CB * OUT_BLOCK <= F32_TILE, "old b fits its tile");
+  constexpr uint32_t EPI_B_LOAD = F32_TILE + (uint32_t)NSPLIT * CB * OUT_BLOCK;
+  constexpr uint32_t EPI_A_LOAD = F32_TILE;
+  constexpr bool EPI3 = EK == EK_CROWD;   // the prox pass loads e^{-sigma w} tiles
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* st_hi = smem + STAGES * STAGE_BYTES;       // output staging
+  unsigned char* st_lo = st_hi + CB * OUT_BLOCK;
+  unsigned char* epi_f = st_hi + STG_BYTES;                  // q or e^{-sigma w}
+  unsigned char* epi_g = epi_f + F32_TILE;                   // old b or p
+  uint64_t* full_bar = (uint64_t*)(epi_g + F32_TILE);        // A + B arrivals of a stage
+  uint64_t* empty_bar = full_bar + STAGES;                   // stage consumed by the MMAs
+  uint64_t* accum_bar = empty_bar + STAGES;                  // accumulator of a tile complete
+  uint64_t* tmem_free_bar = accum_bar + 1;                   // accumulator drained (16 warps)
+  uint64_t* epi_full_bar = accum_bar + 2;                    // epilogue tiles loaded
+  uint64_t* epi_free_bar = accum_bar + 3;                    // epilogue region free again
+  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 4);
+
+  __shared__ int s_go;          // last pass whose barrier the epilogue has crossed
+  __shared__ int s_stop;        // 1: the loop ends at pass s_go
+  __shared__ int s_fault;       // 1: a bounded wait gave up; 4: NaN/Inf met
+  __shared__ int s_it0, s_maxit;
+  __shared__ unsigned s_base;   // barriers completed in this step before this launch
+  __shared__ double s_tol;
+  __shared__ float s_red[NEPI / 32];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  Ctrl* ctrl = args.ctrl;
+  const int nq = 4 * args.pairs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 2);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(accum_bar, 1);
+    mbar_init(tmem_free_bar, NEPI / 32);
+    mbar_init(epi_full_bar, 1);
+    mbar_init(epi_free_bar, 1);
+    fence_mbar_init();
+    const int done = *(volatile int*)&ctrl->done;
+    const int nonfinite = *(volatile int*)&ctrl->nonfinite;
+    s_stop = (done != RUNNING || nonfinite) ? 1 : 0;
+    if (done == RUNNING && nonfinite && blockIdx.x == 0) ctrl->done = NONFINITE;
+    s_it0 = ctrl->it;
+    s_maxit = ctrl->max_iter;
+    s_tol = ctrl->tol;
+    s_base = ctrl->bar_base;
+    s_go = 0;
+    s_fault = 0;
+  }
+  if (warp == WARP_MMA) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (warp == WARP_PROD && lane == 0) {
+    for (int p = 0; p < 4; ++p) {
+      tma_prefetch_desc(&maps.K[p][0]);
+      tma_prefetch_desc(&maps.B[p][0]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const bool stopped_at_start = s_stop != 0;
+  int pairs_done = 0;
+  unsigned nbar = 0;             // grid barriers crossed by this launch (epilogue thread 0)
+
+  if (stopped_at_start) {
+    // nothing to do: the step has already stopped
+  } else if (warp == WARP_PROD) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t kc = 0;   // K-blocks issued (position in the stage ring)
+      uint32_t ec = 0;   // epilogue-tile loads issued
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const int p = q & 3;
+        const LoopPass& PS = args.pass[p];
+        const bool epi_pass = p == 1 || (p == 3 && EPI3);
+        int pre = 0;              // K-blocks of the first tile whose A half is in flight
+        bool epi_pending = false; // epilogue tiles of the first tile issued before the barrier
+        for (int t = blockIdx.x; t < PS.ntiles && ok; t += G) {
+          const bool first = t == (int)blockIdx.x;
+          const int mt = t / PS.tiles_n;
+          const int m0 = mt * BM, n0 = (t - mt * PS.tiles_n) * LBN;
+          const int2 kb = PS.kbt[mt];
+          if (epi_pass) {
+            if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
+            if (!ok) break;
+            if (p == 1) {
+              mbar_arrive_expect_tx(epi_full_bar, EPI_B_LOAD);
+#pragma unroll
+              for (int cb = 0; cb < LBN / 32; ++cb)
+                tma_load_2d(epi_f + cb * (BM * 128), &maps.Q, epi_full_bar, n0 + cb * 32, m0);
+              constexpr int KEO = 128 / (int)sizeof(T);
+#pragma unroll
+              for (int cb = 0; cb < CB; ++cb) {
+                tma_load_2d(epi_g + cb * OUT_BLOCK, &maps.O[1][0], epi_full_bar, n0 + cb * KEO, m0);
+                if constexpr (NSPLIT == 2)
+                  tma_load_2d(epi_g + (CB + cb) * OUT_BLOCK, &maps.O[1][1], epi_full_bar,
+                              n0 + cb * KEO, m0);
+              }
+            } else {
+              mbar_arrive_expect_tx(epi_full_bar, EPI_A_LOAD);
+#pragma unroll
+              for (int cb = 0; cb < LBN / 32; ++cb)
+                tma_load_2d(epi_f + cb * (BM * 128), &maps.E, epi_full_bar, n0 + cb * 32, m0);
+            }
+            ++ec;
+            epi_pending = first;
+          }
+          if (first && q > 0) {
+            // factor halves of the first K-blocks: independent of the previous pass
+            pre = kb.y < STAGES ? kb.y : STAGES;
+            for (int i = 0; i < pre && ok; ++i) {
+              const uint32_t k = kc + i;
+              const int s = (int)(k % STAGES);
+              if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
+              if (!ok) break;
+              unsigned char* st = smem + s * STAGE_BYTES;
+              mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
+              const int kx = (kb.x + i) * KE;
+              tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
+              if constexpr (NSPLIT == 2)
+                tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
+            }
+            if (!ok) break;
+            ok = wait_go(&s_go, q);
+            if (!ok) break;
+            if (s_stop) {
+              // the loop ends here: let the loads in flight land, then leave
+              for (int i = 0; i < pre && ok; ++i) {
+                const uint32_t k = kc + i;
+                mbar_arrive(&full_bar[k % STAGES]);
+                ok = mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1);
+              }
+              if (ok && epi_pending) ok = mbar_wait(epi_full_bar, (ec - 1) & 1);
+              q = nq;
+              break;
+            }
+            fence_proxy_async_global();
+          }
+          for (int i = 0; i < kb.y && ok; ++i) {
+            const uint32_t k = kc + i;
+            const int s = (int)(k % STAGES);
+            unsigned char* st = smem + s * STAGE_BYTES;
+            const int kx = (kb.x + i) * KE;
+            if (!(first && i < pre)) {
+              if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
+              if (!ok) break;
+              mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
+              tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
+              if constexpr (NSPLIT == 2)
+                tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
+            }
+            mbar_arrive_expect_tx(&full_bar[s], NSPLIT * B_BYTES);
+            tma_load_2d(st + A_BYTES, &maps.B[p][0], &full_bar[s], kx, n0);
+            if constexpr (NSPLIT == 2)
+              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.B[p][1], &full_bar[s], kx, n0);
+          }
+          kc += kb.y;
+        }
+        if (ok && q > 0 && q < nq && (int)blockIdx.x >= PS.ntiles) {
+          // no tile in this pass: follow the barriers all the same
+          ok = wait_go(&s_go, q);
+          if (ok && s_stop) q = nq;
+        }
+      }
+      if (!ok) atomicOr(&s_fault, 1);
+    }
+  } else if (warp == WARP_MMA) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t kc = 0, tc = 0;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const int p = q & 3;
+        const LoopPass& PS = args.pass[p];
+        if (q > 0) {
+          ok = wait_go(&s_go, q);
+          if (!ok || s_stop) break;
+        }
+        for (int t = blockIdx.x; t < PS.ntiles && ok; t += G) {
+          const int nkb = PS.kbt[t / PS.tiles_n].y;
+          if (tc > 0) ok = mbar_wait(tmem_free_bar, (tc - 1) & 1);
+          if (!ok) break;
+          tc_fence_after();
+          for (int i = 0; i < nkb && ok; ++i) {
+            const uint32_t k = kc + i;
+            const int s = (int)(k % STAGES);
+            ok = mbar_wait(&full_bar[s], (k / STAGES) & 1);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint64_t a_hi = sdesc_sw128(sa);
+            const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < KB_BYTES / 32; ++kk) {
+              const uint64_t adv = (uint64_t)(kk * 2);
+              const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+              umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
+              if constexpr (NSPLIT == 2) {
+                const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
+                const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
+                umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
+                umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
+              }
+            }
+            umma_commit(&empty_bar[s]);
+          }
+          umma_commit(accum_bar);
+          kc += nkb;
+          ++tc;
+        }
+      }
+      if (!ok) atomicOr(&s_fault, 1);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int grp = warp >> 2;
+    const int rl = quad * 32 + lane;
+    const ProxArgs<float> P = args.P;
+    // congestion/potential cells with a scalar bound and no mask: the common
+    // case, evaluated without the per-cell field checks
+    const bool crowd_plain = EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr;
+    uint32_t tc = 0, ec = 0;
+    int bad = 0;
+    bool free_pending = false;   // epi_free owed once the last stores have read smem
+    int dec_stop = 0;            // stop rule of this pair, taken during pass 2
+    unsigned flag_prev = 0;      // flag slot of the previous barrier (thread 0)
+    for (int q = 0; q < nq; ++q) {
+      const int p = q & 3;
+      const int pair = q >> 2;
+      const LoopPass& PS = args.pass[p];
+      if (q > 0) {
+        // ---- grid barrier: the previous pass is complete everywhere ----
+        if (threadIdx.x == 0) {
+          bulk_wait_all();                 // this CTA's output tiles are in global memory
+          fence_proxy_async_global();
+          if (free_pending) mbar_arrive(epi_free_bar);
+          if (s_fault & 3) atomicOr(&ctrl->nonfinite, 2);
+        }
+        free_pending = false;
+        bad = warp_or(bad);
+        if (lane == 0 && bad) {
+          atomicOr(&ctrl->nonfinite, 1);
+          atomicOr(&s_fault, 4);
+        }
+        bad = 0;
+        named_bar_sync(EPI_BAR, NEPI);
+        if (threadIdx.x == 0) {
+          const unsigned b = s_base + (++nbar);
+          const bool ok = grid_barrier(ctrl, (unsigned)G, b, s_fault != 0);
+          // flags of the previous barrier: every CTA has read the same value
+          int stop = flag_prev != 0 || !ok;
+          if (!ok) {
+            atomicOr(&s_fault, 1);
+            atomicOr(&ctrl->nonfinite, 2);
+          }
+          if (stop && blockIdx.x == 0) ctrl->done = NONFINITE;
+          if (!stop && p == 3) stop = dec_stop;
+          s_stop = stop;
+          __threadfence_block();
+          *(volatile int*)&s_go = q;
+          // slot of this barrier, final now; the slot of barrier b + 2 (read
+          // after barrier b - 1 by every CTA) is cleared for its next use
+          flag_prev = *(volatile unsigned*)&ctrl->bar_flag[b % 3];
+          if (blockIdx.x == 0) ctrl->bar_flag[(b + 2) % 3] = 0u;
+        }
+        named_bar_sync(EPI_BAR, NEPI);
+        if (p == 0) pairs_done = pair;   // the pairs before this one are complete
+        if (s_stop) break;
+        if (p == 2 && warp == 0) {
+          // stop rule from the residual partials of the b-update pass, in a
+          // fixed order; it takes effect at the next barrier
+          double v = 0.0;
+          for (int i = lane; i < args.nparts; i += 32) v += __ldcg(args.part + i);
+          v = warp_sum(v);
+          const int it = s_it0 + pair;   // pairs completed before this one
+          int d = RUNNING;
+          if (it > 0 && !isfinite(v)) d = NONFINITE;
+          else if (it > 0 && v <= s_tol) d = CONVERGED;
+          else if (it >= s_maxit) d = MAX_ITER;
+          if (lane == 0 && blockIdx.x == 0) {
+            if (it > 0) ctrl->res_last = v;
+            if (d != RUNNING) ctrl->done = d;
+          }
+          dec_stop = d != RUNNING;
+        }
+      }
+      const bool have_prev = p == 1 && (s_it0 + pair) > 0;
+      const bool epi_pass = p == 1 || (p == 3 && EPI3);
+      bool first = true;
+      for (int t = blockIdx.x; t < PS.ntiles; t += G) {
+        const int mt = t / PS.tiles_n;
+        const int m0 = mt * BM, n0 = (t - mt * PS.tiles_n) * LBN;
+        if (!first) {
+          // the previous tile's stores must have read the staging and
+          // epilogue tiles; the producer waits for that before it refills them
+          if (threadIdx.x == 0) {
+            bulk_wait_read_all();
+            if (free_pending) mbar_arrive(epi_free_bar);
+          }
+          free_pending = false;
+          named_bar_sync(EPI_BAR, NEPI);
+        }
+        bool have = mbar_wait(accum_bar, tc & 1);
+        if (have && epi_pass) have = mbar_wait(epi_full_bar, ec & 1);
+        if (!have && lane == 0) atomicOr(&s_fault, 1);
+        __syncwarp();
+        tc_fence_after();
+        uint32_t racc[16];
+        tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(grp * 16), racc);
+        tmem_wait_ld();
+        reg_fence16(racc);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tmem_free_bar);
+        const int c = grp;                      // 16-column chunk of the tile
+        const int m = m0 + rl;
+        const int nb = n0 + c * 16;
+        int cnt = PS.N - nb;
+        cnt = (m >= PS.M || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
+        float v[16], o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[j]);
+        float res_f = 0.0f;
+        if (p == 0 || p == 2) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) o[j] = v[j];
+        } else if (p == 1) {
+          float qv[16], bo[16];
+          smem_ld_f32x16(epi_f, rl, c, qv);
+          if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (j < cnt) {
+              if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
+              o[j] = b_update<float>(qv[j], v[j]);
+              bad |= !isfinite(o[j]);
+            } else {
+              o[j] = 0.0f;
+            }
+          }
+        } else {
+          const int irow = m * PS.N + nb;
+          float ev[16], pv[16];
+          if (EK == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
+          if (crowd_plain) {
+            const bool hk = P.has_kappa != 0;
+            const float kap = P.kappa_s;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float a = ev[j];
+              if (hk && a * v[j] > kap) a = ratio_div<float>(kap, v[j]);
+              if (j >= cnt) a = 0.0f;
+              bad |= !isfinite(a);
+              o[j] = a;
+              pv[j] = a * v[j];
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (j < cnt) {
+                const float a = prox_ratio_e<float, EK>(P, irow + j, v[j],
+                                                         EK == EK_CROWD ? ev[j] : 0.0f);
+                bad |= !isfinite(a);
+                o[j] = a;
+                pv[j] = a * v[j];
+              } else {
+                o[j] = 0.0f;
+                pv[j] = 0.0f;
+              }
+            }
+          }
+          smem_st_f32x16(epi_g, rl, c, pv);
+        }
+        stage16<MODE>(st_hi, st_lo, rl, c, o);
+        fence_proxy_async_smem();
+        double res = 0.0;
+        if (p == 1)   // includes the barrier
+          res = (double)tile_sum16(res_f, s_red, [] { named_bar_sync(EPI_BAR, NEPI); });
+        else
+          named_bar_sync(EPI_BAR, NEPI);
+        if (threadIdx.x == 0) {
+          if (p == 1) args.part[t] = res;
+          constexpr int KEo = 128 / (int)sizeof(T);
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            tma_store_2d(&maps.O[p][0], st_hi + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+            if constexpr (NSPLIT == 2) tma_store_2d(&maps.O[p][1], st_lo + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+          }
+          if (p == 3) {
+#pragma unroll
+            for (int cb = 0; cb < LBN / 32; ++cb)
+              tma_store_2d(&maps.P, epi_g + cb * (BM * 128), n0 + cb * 32, m0);
+          }
+          bulk_commit();
+        }
+        free_pending = epi_pass;
+        first = false;
+        ++tc;
+        if (epi_pass) ++ec;
+      }
+      if (p == 3 && q == nq - 1) pairs_done = pair + 1;
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+    bad = warp_or(bad);
+    if (lane == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == WARP_MMA) tmem_dealloc(tmem_base, TMEM_COLS);
+  if (threadIdx.x == 0 && !stopped_at_start) {
+    if (s_fault & 3) atomicOr(&ctrl->nonfinite, 2);
+    if (blockIdx.x == 0) {
+      ctrl->it = s_it0 + pairs_done;
+      ctrl->bar_base = s_base + nbar;   // every CTA crossed the same barriers
+    }
+  }
+}
+
+template <int MODE, int EK>
+cudaError_t set_loop_attr() {
+  return cudaFuncSetAttribute(tc_loop_kernel<MODE, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)loop_smem_bytes(MODE));
+}
+
+template <int MODE, int EK>
+cudaError_t launch_loop(const LoopMaps& maps, const LoopArgs& args, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTL);
+  cfg.dynamicSmemBytes = loop_smem_bytes(MODE);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_loop_kernel<MODE, EK>, maps, args);
+}
+
+template <int MODE>
+cudaError_t dispatch_loop(int ek, const LoopMaps& maps, const LoopArgs& args, int grid,
+                          cudaStream_t st) {
+  if (ek == EK_CROWD) return launch_loop<MODE, EK_CROWD>(maps, args, grid, st);
+  if (ek == EK_ENTROPY) return launch_loop<MODE, EK_ENTROPY>(maps, args, grid, st);
+  return launch_loop<MODE, EK_POWER>(maps, args, grid, st);
+}
+
+template <int MODE, int EK>
+int blocks_per_sm() {
+  int nb = 0;
+  if (set_loop_attr<MODE, EK>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_loop_kernel<MODE, EK>, NTL,
+                                                    loop_smem_bytes(MODE)) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <int MODE>
+int loop_blocks_per_sm(int ek) {
+  if (ek == EK_CROWD) return blocks_per_sm<MODE, EK_CROWD>();
+  if (ek == EK_ENTROPY) return blocks_per_sm<MODE, EK_ENTROPY>();
+  return blocks_per_sm<MODE, EK_POWER>();
+}
+
+// Geometry of pass `which` (0..3) with 64-wide tiles.
+LoopPass loop_pass(const TcPlan* P, int which) {
+  const TcConfig& c = P->cfg;
+  const bool over_x = (which & 1) == 0;
+  const int side = P->absorbed ? (which >> 1) : 0;
+  LoopPass L;
+  L.M = over_x ? c.nx : c.ny;
+  L.N = over_x ? c.ny : c.nx;
+  L.tiles_n = (L.N + LBN - 1) / LBN;
+  L.ntiles = L.tiles_n * ((L.M + BM - 1) / BM);
+  L.kbt = P->kbt[over_x ? 0 : 1][side];
+  return L;
+}
+
+}  // namespace
+
+int tc_loop_setup(TcPlan* P, std::string* msg) {
+  P->loop_ok = 0;
+  if (!P->tma_epi) return 0;   // fp32 fields must be TMA tiles (nx % 4 == 0)
+  int dev = 0, sms = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || sms < 1) return 0;
+  const int ek = P->cfg.ek;
+  const int nb = P->mode == MODE_TF32 ? loop_blocks_per_sm<MODE_TF32>(ek)
+                 : P->mode == MODE_BF16X3 ? loop_blocks_per_sm<MODE_BF16X3>(ek)
+                                          : loop_blocks_per_sm<MODE_BF16>(ek);
+  cudaGetLastError();
+  if (nb < 1) return 0;
+  int maxt = 0;
+  for (int w = 0; w < 4; ++w) maxt = std::max(maxt, loop_pass(P, w).ntiles);
+  P->loop_grid = std::min(maxt, sms * nb);
+  // image operands with 64-row boxes
+  const TcConfig& c = P->cfg;
+  const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int si = sp < nsplit ? sp : 0;
+    if (!make_map(&P->lA[sp], P->img_a[si], P->mode, c.ny, c.nx, P->px, LBN) ||
+        !make_map(&P->lB[sp], P->img_b[si], P->mode, c.ny, c.nx, P->px, LBN) ||
+        !make_map(&P->lT[sp], P->img_t[si], P->mode, c.nx, c.ny, P->py, LBN)) {
+      *msg = "cuTensorMapEncodeTiled failed (loop maps)";
+      return 2;
+    }
+  }
+  // executed flops of one pair with 64-wide tiles
+  const int KE = P->mode == MODE_TF32 ? 32 : 64;
+  const double mult = P->mode == MODE_BF16X3 ? 3.0 : 1.0;
+  double f = 0.0;
+  for (int w = 0; w < 4; ++w) {
+    const LoopPass L = loop_pass(P, w);
+    std::vector<int2> tab((L.M + BM - 1) / BM);
+    if (cudaMemcpy(tab.data(), L.kbt, tab.size() * sizeof(int2), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      *msg = "reading the band tables";
+      return 2;
+    }
+    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)L.tiles_n * LBN * mult;
+  }
+  P->loop_flops_pair = f;
+  P->loop_ok = 1;
+  return 0;
+}
+
+int tc_loop_supported(const TcPlan* P) { return P && P->loop_ok; }
+
+double tc_loop_flops(const TcPlan* P, int pairs) { return P->loop_flops_pair * pairs; }
+
+cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
+  if (!P->loop_ok || pairs < 1) return cudaErrorInvalidValue;
+  const TcConfig& c = P->cfg;
+  LoopMaps maps;
+  LoopArgs args{};
+  for (int w = 0; w < 4; ++w) {
+    const bool over_x = (w & 1) == 0;
+    const int half = w >> 1;
+    const int side = P->absorbed ? half : 0;
+    args.pass[w] = loop_pass(P, w);
+    for (int sp = 0; sp < 2; ++sp) {
+      maps.K[w][sp] = P->mK[over_x ? 0 : 1][side][sp];
+      if (over_x) {
+        maps.B[w][sp] = half == 0 ? P->lA[sp] : P->lB[sp];
+        maps.O[w][sp] = P->sT[sp];
+      } else {
+        maps.B[w][sp] = P->lT[sp];
+        maps.O[w][sp] = half == 0 ? P->sB[sp] : P->sA[sp];
+      }
+    }
+  }
+  maps.Q = P->fQ;
+  maps.E = P->fE;
+  maps.P = P->fP;
+  args.ctrl = c.ctrl;
+  args.P = c.prox;
+  args.part = c.part;
+  args.nparts = args.pass[1].ntiles;
+  args.pairs = pairs;
+  switch (P->mode) {
+    case MODE_TF32: return dispatch_loop<MODE_TF32>(c.ek, maps, args, P->loop_grid, st);
+    case MODE_BF16X3: return dispatch_loop<MODE_BF16X3>(c.ek, maps, args, P->loop_grid, st);
+    default: return dispatch_loop<MODE_BF16>(c.ek, maps, args, P->loop_grid, st);
+  }
+}
+
+}  // namespace jko

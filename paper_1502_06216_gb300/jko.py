@@ -54,7 +54,8 @@ class jko_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("tau", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("precision", ctypes.c_int), ("renormalize", ctypes.c_int),
-                ("absorb", ctypes.c_int)]
+                ("absorb", ctypes.c_int),
+                ("loop", ctypes.c_int)]
 
 
 class jko_energy(ctypes.Structure):
@@ -87,6 +88,9 @@ EXPORTS = {
     "jko_profile_passes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_double)]),
+    "jko_profile_loop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "jko_step_noalloc": (ctypes.c_int, [ctypes.POINTER(jko_grid), ctypes.POINTER(jko_params),
                                         ctypes.POINTER(jko_energy), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p,
@@ -180,12 +184,12 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                tol: float = 1e-6, max_iter: int = 200, check_every: int = 0,
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
-               alpha=None, mask=None, stream=None, absorb: int = 0) -> Handle:
+               alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied)."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
-                   int(absorb))
+                   int(absorb), int(loop))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
@@ -265,6 +269,17 @@ def jko_profile_passes(h: Handle, reps: int = 20):
     return list(ms), list(fl)
 
 
+def jko_profile_loop(h: Handle, pairs: int = 16, reps: int = 10):
+    """Mean ms per launch and executed flops of the persistent pair-loop kernel
+    running `pairs` pairs."""
+    ms = (ctypes.c_float * 1)()
+    fl = (ctypes.c_double * 1)()
+    L = lib()
+    _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
+    _check(L.jko_profile_loop(h.ptr, pairs, reps, ms, fl), h.ptr)
+    return ms[0], fl[0]
+
+
 def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
                      max_iter: Optional[int] = None, renormalize: bool = True):
     """jko_step_noalloc for an ``inputs.Problem``: one FP32 step whose working
@@ -310,14 +325,15 @@ def jko_build_info() -> str:
 
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
                         max_iter: Optional[int] = None, check_every: int = 0,
-                        renormalize: bool = True, stream=None, absorb: int = 0) -> Handle:
+                        renormalize: bool = True, stream=None, absorb: int = 0,
+                        loop: int = 0) -> Handle:
     """jko_create from an ``inputs.Problem``."""
     return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
                       tol=pb.tol if tol is None else tol,
                       max_iter=pb.max_iter if max_iter is None else max_iter,
                       check_every=check_every, precision=precision, renormalize=renormalize,
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
-                      stream=stream, absorb=absorb)
+                      stream=stream, absorb=absorb, loop=loop)
 
 
 class Batch:
