@@ -43,16 +43,19 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_TFLOPS_NOMINAL = 1.25
 
-# DRAM bytes (read + write) per launch of each tensor-core pass, BF16 form at
-# 1024^2, from one ncu capture (profiles/tc_pass_bf16_crowd1024_full.md).  They
-# hold for the kernel sources whose hash is given; any change to those sources
-# turns the roofline's traffic back to null until the counters are taken again.
-KERNEL_SOURCES = ("tc_gemm.cu", "tc_gemm.h", "jko_internal.cuh")
+# DRAM bytes (read + write) per launch of the persistent loop kernel (200
+# pairs) and of each per-pass kernel, BF16 form at 1024^2, from one ncu
+# capture (profiles/tc_loop_bf16_crowd1024_full.md).  They hold for the kernel sources whose hash is given;
+# any change to those sources turns the roofline's traffic back to null until
+# the counters are taken again.
+KERNEL_SOURCES = ("tc_gemm.cu", "tc_gemm.h", "tc_loop.cu", "tc_common.cuh", "jko_internal.cuh")
 PROFILED_TRAFFIC = {
-    "src_sha256": "70f92daf29d4afa904236a31111ba9b6707a65c42e516d403a1048e9eb72afd5",
+    "src_sha256": "38a40491f1e161bb2184e3afbb84f3de84c3a6aa6391dbdbd14f9af88997b4f8",
     "precision": "BF16", "n": 1024,
-    "bytes_per_launch": [3140096.0, 9449984.0, 3140096.0, 7355136.0],
+    "loop": 14991616.0 + 698880.0,      # one 200-pair launch (one step)
+    "passes": [None, None, None, None],  # per-pass kernels: not captured for these sources
 }
+LOOP_PAIRS = 200  # pairs per launch of the loop kernel: one step of the workload (<= 200 pairs)
 
 
 def kernel_source_hash():
@@ -65,10 +68,11 @@ def kernel_source_hash():
 
 
 def profiled_traffic(precision_name, n, kern):
+    """kern: "loop" or a pass index 0..3."""
     t = PROFILED_TRAFFIC
     if precision_name != t["precision"] or n != t["n"] or kernel_source_hash() != t["src_sha256"]:
         return None
-    return t["bytes_per_launch"][kern]
+    return t["loop"] if kern == "loop" else t["passes"][kern]
 
 
 def load_peaks():
@@ -402,6 +406,12 @@ def run_ours(args):
     # per-kernel durations (CUDA events on the handle's stream) for the roofline
     ms4, fl4 = jko.jko_profile_passes(h, reps=50)
     kern = max(range(4), key=lambda k: ms4[k])
+    loop = None
+    if prec not in (jko.Precision.FP32, jko.Precision.FP64):
+        try:
+            loop = jko.jko_profile_loop(h, pairs=LOOP_PAIRS, reps=20)
+        except jko.JKOError:
+            loop = None     # this grid runs one kernel per pass
 
     # e2e through the public API with host buffers: every step copies its input
     # from pinned host memory and reads its result back
@@ -441,19 +451,31 @@ def run_ours(args):
         peak = bf16 * ratio
         peak_note = f"bf16 dense, sustained, of {src} x {ratio} for {prec.name}"
         bound = "tensor"
-    achieved = fl4[kern] / (ms4[kern] / 1e3) / 1e12
     names = ["pass_x_xi_a", "pass_y_xi_a+b_update+residual", "pass_x_xi_b", "pass_y_xi_b+prox"]
     dense_flops = 8.0 * args.n ** 3
+    if loop is not None:
+        # the kernel the step runs: one launch = LOOP_PAIRS pairs (four passes each)
+        k_ms, k_fl = loop
+        kname = f"tc_loop_kernel ({LOOP_PAIRS} pairs per launch)"
+        traffic = profiled_traffic(head, args.n, "loop")
+        pair_ms = k_ms / LOOP_PAIRS
+    else:
+        k_ms, k_fl = ms4[kern], fl4[kern]
+        kname = names[kern]
+        traffic = profiled_traffic(head, args.n, kern)
+        pair_ms = sum(ms4)
+    achieved = k_fl / (k_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(head, args.n, kern),
+                "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "kernel": names[kern],
-                "kernel_ms": ms4[kern], "flops_per_launch": fl4[kern],
-                "flops_note": ("executed tensor-core flops of the band of K-tiles the pass visits"
+                "kernel": kname, "kernel_ms": k_ms, "flops_per_launch": k_fl,
+                "flops_note": ("executed tensor-core flops of the band of K-tiles the passes visit"
                                if bound == "tensor" else
                                "2(2r+1) flops per output of the band-limited filter"),
-                "peak_source": peak_note, "passes_ms": ms4, "passes_flops": fl4,
-                "dense_equiv_tflops_per_pair": dense_flops / (sum(ms4) / 1e3) / 1e12}
+                "peak_source": peak_note,
+                "per_pass_kernels": {"passes_ms": ms4, "passes_flops": fl4},
+                "us_per_pair": pair_ms * 1e3,
+                "dense_equiv_tflops_per_pair": dense_flops / (pair_ms / 1e3) / 1e12}
 
     # cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

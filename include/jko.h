@@ -83,15 +83,18 @@ typedef struct jko_params {
   double tau;       /* JKO step size tau > 0 (Eq. def-jko-operator) */
   double tol;       /* L1 marginal residual tolerance >= 0 (Sec. 3.4) */
   int max_iter;     /* maximum (odd, even) pairs per step, >= 1 */
-  int check_every;  /* iterations between host polls of the stop flag (0 = default 16) */
+  int check_every;  /* iterations between host polls of the stop flag (0 = default 16);
+                       handles on the persistent loop kernel run a step's whole budget
+                       in one launch that stops itself, and ignore it */
   int precision;    /* a jko_precision value */
   int renormalize;  /* 1: divide each output p by its FP64 sum; 0: leave as computed */
   int absorb;       /* tensor-core precisions: separable log-domain absorption of the
                        potential (see jko_create); 0 = automatic, 1 = on, 2 = off */
   int loop;         /* tensor-core precisions: 0 = automatic (one persistent kernel per
-                       chunk of check_every pairs where the device and the grid allow
-                       it, else one kernel per pass), 1 = persistent kernel required
-                       (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one kernel per pass */
+                       step, with the stop rule taken in the kernel, where the device
+                       and the grid allow it, else one kernel per pass), 1 = persistent
+                       kernel required (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one
+                       kernel per pass */
 } jko_params;
 
 /* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */

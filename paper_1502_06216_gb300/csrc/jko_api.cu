@@ -528,6 +528,10 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   if (s != JKO_OK) return fail(s);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_err(h, e, "set-up"));
+  // the loop kernel takes the stop decision itself: one launch runs the whole
+  // pair budget (the decision at pair max_iter + 1 needs that many) and ends
+  // where the rule fires, so the host waits once instead of polling chunks
+  if (h->use_loop) h->chunk_iters = params->max_iter + 1;
   s = capture_chunk(h);
   if (s != JKO_OK) return fail(s);
   *out = h;

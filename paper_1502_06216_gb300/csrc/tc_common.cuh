@@ -522,6 +522,7 @@ struct TcPlan {
   CUtensorMap lA[2], lB[2], lT[2];
   int loop_ok = 0;
   int loop_grid = 0;
+  int loop_res = 0;            // the loop kernel keeps each CTA's factor band resident
   double loop_flops_pair = 0.0;
 };
 

@@ -47,22 +47,41 @@ constexpr uint32_t LOOP_SMEM_BUDGET = 224 * 1024;
 constexpr uint32_t kGridSpinLimit = 1u << 24;
 constexpr uint32_t kGoSpinLimit = 1u << 27;
 
-// output staging tile (operand type, hi [+ lo]) and epilogue region (two fp32
-// tiles: q | old b in the b-update pass, e^{-sigma w} | p in the prox pass)
+// Resident-factor mode (BF16, one tile per CTA, the same 1-D factor in every
+// pass): the CTA keeps its band of at most RES_KB factor K-blocks in shared
+// memory for the whole launch and streams only image K-blocks.
+constexpr int RES_KB = 8;
+constexpr int RES_STAGES = 4;
+
+// output staging tile (operand type, hi [+ lo]) and epilogue region: q | old b
+// in the b-update pass, e^{-sigma w} | p in the prox pass (two fp32 tiles); in
+// resident mode q | old b (operand type) and p is staged in the idle image
+// stages instead
 __host__ __device__ constexpr uint32_t loop_staging_bytes(int mode) {
   return (mode == MODE_BF16 ? 1u : 2u) * (uint32_t)LBN * BM * 2u;
 }
-__host__ __device__ constexpr uint32_t loop_epi_bytes() { return 2u * LBN * BM * 4u; }
-__host__ __device__ constexpr int loop_stages(int mode) {
-  return (LOOP_SMEM_BUDGET - loop_epi_bytes() - loop_staging_bytes(mode)) / stage_bytes(mode, LBN) <
-                 (uint32_t)MAX_STAGES
-             ? (int)((LOOP_SMEM_BUDGET - loop_epi_bytes() - loop_staging_bytes(mode)) /
+__host__ __device__ constexpr uint32_t loop_epi_bytes(bool res) {
+  return res ? (uint32_t)LBN * BM * 4u + (uint32_t)LBN * BM * 2u : 2u * LBN * BM * 4u;
+}
+__host__ __device__ constexpr uint32_t loop_res_bytes(bool res) {
+  return res ? (uint32_t)RES_KB * BM * KB_BYTES : 0u;
+}
+__host__ __device__ constexpr uint32_t loop_stage_bytes(int mode, bool res) {
+  return res ? (uint32_t)LBN * KB_BYTES : stage_bytes(mode, LBN);
+}
+__host__ __device__ constexpr int loop_stages(int mode, bool res) {
+  return res ? RES_STAGES
+         : (LOOP_SMEM_BUDGET - loop_epi_bytes(false) - loop_staging_bytes(mode)) /
+                       stage_bytes(mode, LBN) <
+                   (uint32_t)MAX_STAGES
+             ? (int)((LOOP_SMEM_BUDGET - loop_epi_bytes(false) - loop_staging_bytes(mode)) /
                      stage_bytes(mode, LBN))
              : MAX_STAGES;
 }
-__host__ __device__ constexpr size_t loop_smem_bytes(int mode) {
-  return (size_t)loop_stages(mode) * stage_bytes(mode, LBN) + loop_staging_bytes(mode) +
-         loop_epi_bytes() + 1024 + (size_t)(2 * loop_stages(mode) + 6) * 8 + 16;
+__host__ __device__ constexpr size_t loop_smem_bytes(int mode, bool res) {
+  return (size_t)loop_res_bytes(res) + (size_t)loop_stages(mode, res) * loop_stage_bytes(mode, res) +
+         loop_staging_bytes(mode) + loop_epi_bytes(res) + 1024 +
+         (size_t)(2 * loop_stages(mode, res) + 8) * 8 + 16;
 }
 
 struct LoopPass {
@@ -113,7 +132,7 @@ __device__ __forceinline__ bool wait_go(const int* s_go, int q) {
   return false;
 }
 
-template <int MODE, int EK>
+template <int MODE, int EK, bool RES>
 __global__ void __launch_bounds__(NTL, 1)
 tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ LoopArgs args) {
   using T = typename OpT<MODE>::T;
@@ -121,10 +140,12 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
   constexpr uint32_t A_BYTES = BM * KB_BYTES;
   constexpr uint32_t B_BYTES = LBN * KB_BYTES;
-  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
-  constexpr int STAGES = loop_stages(MODE);
-  static_assert(STAGE_BYTES == stage_bytes(MODE, LBN), "stage size");
+  constexpr uint32_t STAGE_BYTES = RES ? B_BYTES : NSPLIT * (A_BYTES + B_BYTES);
+  constexpr int STAGES = loop_stages(MODE, RES);
+  constexpr uint32_t B_OFF = RES ? 0u : A_BYTES;          // image half within a stage
+  static_assert(STAGE_BYTES == loop_stage_bytes(MODE, RES), "stage size");
   static_assert(STAGES >= 2, "at least two stages");
+  static_assert(!RES || MODE == MODE_BF16, "resident factors: BF16 only");
   constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
   constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
   constexpr uint32_t TMEM_COLS = LBN;
@@ -139,17 +160,22 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* st_hi = smem + STAGES * STAGE_BYTES;       // output staging
+  unsigned char* res_a = smem;                               // resident factor band
+  unsigned char* stages = smem + loop_res_bytes(RES);        // operand stages
+  unsigned char* st_hi = stages + STAGES * STAGE_BYTES;      // output staging
   unsigned char* st_lo = st_hi + CB * OUT_BLOCK;
   unsigned char* epi_f = st_hi + STG_BYTES;                  // q or e^{-sigma w}
-  unsigned char* epi_g = epi_f + F32_TILE;                   // old b or p
-  uint64_t* full_bar = (uint64_t*)(epi_g + F32_TILE);        // A + B arrivals of a stage
+  unsigned char* epi_g = epi_f + F32_TILE;                   // old b (or p)
+  unsigned char* p_st = RES ? stages : epi_g;                // staged p of the prox pass
+  static_assert(!RES || STAGES * STAGE_BYTES >= F32_TILE, "p fits the image stages");
+  uint64_t* full_bar = (uint64_t*)(epi_f + loop_epi_bytes(RES)); // A + B arrivals of a stage
   uint64_t* empty_bar = full_bar + STAGES;                   // stage consumed by the MMAs
   uint64_t* accum_bar = empty_bar + STAGES;                  // accumulator of a tile complete
   uint64_t* tmem_free_bar = accum_bar + 1;                   // accumulator drained (16 warps)
   uint64_t* epi_full_bar = accum_bar + 2;                    // epilogue tiles loaded
   uint64_t* epi_free_bar = accum_bar + 3;                    // epilogue region free again
-  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 4);
+  uint64_t* res_bar = accum_bar + 4;                         // resident band loaded
+  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 5);
 
   __shared__ int s_go;          // last pass whose barrier the epilogue has crossed
   __shared__ int s_stop;        // 1: the loop ends at pass s_go
@@ -166,13 +192,14 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full_bar[s], 2);
+      mbar_init(&full_bar[s], RES ? 1 : 2);
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(accum_bar, 1);
     mbar_init(tmem_free_bar, NEPI / 32);
     mbar_init(epi_full_bar, 1);
     mbar_init(epi_free_bar, 1);
+    mbar_init(res_bar, 1);
     fence_mbar_init();
     const int done = *(volatile int*)&ctrl->done;
     const int nonfinite = *(volatile int*)&ctrl->nonfinite;
@@ -211,6 +238,15 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
       uint32_t kc = 0;   // K-blocks issued (position in the stage ring)
       uint32_t ec = 0;   // epilogue-tile loads issued
       bool ok = true;
+      if constexpr (RES) {
+        // this CTA's factor band: the same m-tile and factor in every pass
+        const LoopPass& P0 = args.pass[0];
+        const int mt = (int)blockIdx.x / P0.tiles_n;
+        const int2 kb = P0.kbt[mt];
+        mbar_arrive_expect_tx(res_bar, (uint32_t)kb.y * A_BYTES);
+        for (int i = 0; i < kb.y; ++i)
+          tma_load_2d(res_a + i * A_BYTES, &maps.K[0][0], res_bar, (kb.x + i) * KE, mt * BM);
+      }
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
         const LoopPass& PS = args.pass[p];
@@ -249,13 +285,13 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           }
           if (first && q > 0) {
             // factor halves of the first K-blocks: independent of the previous pass
-            pre = kb.y < STAGES ? kb.y : STAGES;
+            pre = RES ? 0 : (kb.y < STAGES ? kb.y : STAGES);
             for (int i = 0; i < pre && ok; ++i) {
               const uint32_t k = kc + i;
               const int s = (int)(k % STAGES);
               if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
               if (!ok) break;
-              unsigned char* st = smem + s * STAGE_BYTES;
+              unsigned char* st = stages + s * STAGE_BYTES;
               mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
               const int kx = (kb.x + i) * KE;
               tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
@@ -273,6 +309,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
                 ok = mbar_wait(&full_bar[k % STAGES], (k / STAGES) & 1);
               }
               if (ok && epi_pending) ok = mbar_wait(epi_full_bar, (ec - 1) & 1);
+              if (ok && RES) ok = mbar_wait(res_bar, 0);
               q = nq;
               break;
             }
@@ -281,9 +318,12 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           for (int i = 0; i < kb.y && ok; ++i) {
             const uint32_t k = kc + i;
             const int s = (int)(k % STAGES);
-            unsigned char* st = smem + s * STAGE_BYTES;
+            unsigned char* st = stages + s * STAGE_BYTES;
             const int kx = (kb.x + i) * KE;
-            if (!(first && i < pre)) {
+            if (RES) {
+              if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
+              if (!ok) break;
+            } else if (!(first && i < pre)) {
               if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
               if (!ok) break;
               mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
@@ -292,7 +332,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
                 tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
             }
             mbar_arrive_expect_tx(&full_bar[s], NSPLIT * B_BYTES);
-            tma_load_2d(st + A_BYTES, &maps.B[p][0], &full_bar[s], kx, n0);
+            tma_load_2d(st + B_OFF, &maps.B[p][0], &full_bar[s], kx, n0);
             if constexpr (NSPLIT == 2)
               tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.B[p][1], &full_bar[s], kx, n0);
           }
@@ -311,6 +351,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
     if (lane == 0) {
       uint32_t kc = 0, tc = 0;
       bool ok = true;
+      if constexpr (RES) ok = mbar_wait(res_bar, 0);
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
         const LoopPass& PS = args.pass[p];
@@ -329,9 +370,9 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             ok = mbar_wait(&full_bar[s], (k / STAGES) & 1);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t a_hi = sdesc_sw128(sa);
-            const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+            const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+            const uint64_t a_hi = sdesc_sw128(RES ? smem_u32(res_a + i * A_BYTES) : sa);
+            const uint64_t b_hi = sdesc_sw128(sa + B_OFF);
 #pragma unroll
             for (int kk = 0; kk < KB_BYTES / 32; ++kk) {
               const uint64_t adv = (uint64_t)(kk * 2);
@@ -512,7 +553,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               }
             }
           }
-          smem_st_f32x16(epi_g, rl, c, pv);
+          smem_st_f32x16(p_st, rl, c, pv);
         }
         stage16<MODE>(st_hi, st_lo, rl, c, o);
         fence_proxy_async_smem();
@@ -532,7 +573,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           if (p == 3) {
 #pragma unroll
             for (int cb = 0; cb < LBN / 32; ++cb)
-              tma_store_2d(&maps.P, epi_g + cb * (BM * 128), n0 + cb * 32, m0);
+              tma_store_2d(&maps.P, p_st + cb * (BM * 128), n0 + cb * 32, m0);
           }
           bulk_commit();
         }
@@ -561,50 +602,51 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   }
 }
 
-template <int MODE, int EK>
+template <int MODE, int EK, bool RES>
 cudaError_t set_loop_attr() {
-  return cudaFuncSetAttribute(tc_loop_kernel<MODE, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)loop_smem_bytes(MODE));
+  return cudaFuncSetAttribute(tc_loop_kernel<MODE, EK, RES>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)loop_smem_bytes(MODE, RES));
 }
 
-template <int MODE, int EK>
+template <int MODE, int EK, bool RES>
 cudaError_t launch_loop(const LoopMaps& maps, const LoopArgs& args, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(NTL);
-  cfg.dynamicSmemBytes = loop_smem_bytes(MODE);
+  cfg.dynamicSmemBytes = loop_smem_bytes(MODE, RES);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc_loop_kernel<MODE, EK>, maps, args);
+  return cudaLaunchKernelEx(&cfg, tc_loop_kernel<MODE, EK, RES>, maps, args);
 }
 
-template <int MODE>
+template <int MODE, bool RES>
 cudaError_t dispatch_loop(int ek, const LoopMaps& maps, const LoopArgs& args, int grid,
                           cudaStream_t st) {
-  if (ek == EK_CROWD) return launch_loop<MODE, EK_CROWD>(maps, args, grid, st);
-  if (ek == EK_ENTROPY) return launch_loop<MODE, EK_ENTROPY>(maps, args, grid, st);
-  return launch_loop<MODE, EK_POWER>(maps, args, grid, st);
+  if (ek == EK_CROWD) return launch_loop<MODE, EK_CROWD, RES>(maps, args, grid, st);
+  if (ek == EK_ENTROPY) return launch_loop<MODE, EK_ENTROPY, RES>(maps, args, grid, st);
+  return launch_loop<MODE, EK_POWER, RES>(maps, args, grid, st);
 }
 
-template <int MODE, int EK>
+template <int MODE, int EK, bool RES>
 int blocks_per_sm() {
   int nb = 0;
-  if (set_loop_attr<MODE, EK>() != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_loop_kernel<MODE, EK>, NTL,
-                                                    loop_smem_bytes(MODE)) != cudaSuccess)
+  if (set_loop_attr<MODE, EK, RES>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_loop_kernel<MODE, EK, RES>, NTL,
+                                                    loop_smem_bytes(MODE, RES)) != cudaSuccess)
     return 0;
   return nb;
 }
 
-template <int MODE>
+template <int MODE, bool RES>
 int loop_blocks_per_sm(int ek) {
-  if (ek == EK_CROWD) return blocks_per_sm<MODE, EK_CROWD>();
-  if (ek == EK_ENTROPY) return blocks_per_sm<MODE, EK_ENTROPY>();
-  return blocks_per_sm<MODE, EK_POWER>();
+  if (ek == EK_CROWD) return blocks_per_sm<MODE, EK_CROWD, RES>();
+  if (ek == EK_ENTROPY) return blocks_per_sm<MODE, EK_ENTROPY, RES>();
+  return blocks_per_sm<MODE, EK_POWER, RES>();
 }
 
 // Geometry of pass `which` (0..3) with 64-wide tiles.
@@ -632,14 +674,31 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (!coop || sms < 1) return 0;
   const int ek = P->cfg.ek;
-  const int nb = P->mode == MODE_TF32 ? loop_blocks_per_sm<MODE_TF32>(ek)
-                 : P->mode == MODE_BF16X3 ? loop_blocks_per_sm<MODE_BF16X3>(ek)
-                                          : loop_blocks_per_sm<MODE_BF16>(ek);
+  const int nb = P->mode == MODE_TF32 ? loop_blocks_per_sm<MODE_TF32, false>(ek)
+                 : P->mode == MODE_BF16X3 ? loop_blocks_per_sm<MODE_BF16X3, false>(ek)
+                                          : loop_blocks_per_sm<MODE_BF16, false>(ek);
   cudaGetLastError();
   if (nb < 1) return 0;
   int maxt = 0;
   for (int w = 0; w < 4; ++w) maxt = std::max(maxt, loop_pass(P, w).ntiles);
   P->loop_grid = std::min(maxt, sms * nb);
+  // resident factors: BF16, the same factor and band table in every pass
+  // (square grid, equal lengths, no absorption), one tile per CTA and a band
+  // of at most RES_KB K-blocks per 128-row tile
+  P->loop_res = 0;
+  const TcConfig& cc = P->cfg;
+  if (P->mode == MODE_BF16 && !P->absorbed && cc.nx == cc.ny && cc.lx == cc.ly &&
+      maxt <= P->loop_grid && loop_blocks_per_sm<MODE_BF16, true>(ek) >= 1) {
+    const LoopPass L0 = loop_pass(P, 0), L1 = loop_pass(P, 1);
+    std::vector<int2> t0((L0.M + BM - 1) / BM), t1((L1.M + BM - 1) / BM);
+    bool same = t0.size() == t1.size() &&
+                cudaMemcpy(t0.data(), L0.kbt, t0.size() * sizeof(int2), cudaMemcpyDeviceToHost) == cudaSuccess &&
+                cudaMemcpy(t1.data(), L1.kbt, t1.size() * sizeof(int2), cudaMemcpyDeviceToHost) == cudaSuccess;
+    for (size_t i = 0; same && i < t0.size(); ++i)
+      same = t0[i].x == t1[i].x && t0[i].y == t1[i].y && t0[i].y <= RES_KB;
+    P->loop_res = same ? 1 : 0;
+  }
+  cudaGetLastError();
   // image operands with 64-row boxes
   const TcConfig& c = P->cfg;
   const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
@@ -705,9 +764,11 @@ cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
   args.nparts = args.pass[1].ntiles;
   args.pairs = pairs;
   switch (P->mode) {
-    case MODE_TF32: return dispatch_loop<MODE_TF32>(c.ek, maps, args, P->loop_grid, st);
-    case MODE_BF16X3: return dispatch_loop<MODE_BF16X3>(c.ek, maps, args, P->loop_grid, st);
-    default: return dispatch_loop<MODE_BF16>(c.ek, maps, args, P->loop_grid, st);
+    case MODE_TF32: return dispatch_loop<MODE_TF32, false>(c.ek, maps, args, P->loop_grid, st);
+    case MODE_BF16X3: return dispatch_loop<MODE_BF16X3, false>(c.ek, maps, args, P->loop_grid, st);
+    default:
+      return P->loop_res ? dispatch_loop<MODE_BF16, true>(c.ek, maps, args, P->loop_grid, st)
+                         : dispatch_loop<MODE_BF16, false>(c.ek, maps, args, P->loop_grid, st);
   }
 }
 
