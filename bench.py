@@ -246,8 +246,8 @@ def run_batched(args, jko, dev, barrier):
     pbs = inputs.batched_problems(256)
     out = {"workload": "256 flows (crowd even / porous odd), n in {64,128,256,512}, "
                        "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6"}
-    for form in ("BF16X3", "FP32"):
-        b = jko.jko_batch_create(pbs, precision=jko.Precision[form])
+    for form, loop in (("BF16X3", 0), ("BF16X3", 2), ("FP32", 0)):
+        b = jko.jko_batch_create(pbs, precision=jko.Precision[form], loop=loop)
         p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
         jko.jko_batch_flow(b, p0s, 1, want_final=False)        # warm-up
         barrier()
@@ -258,8 +258,9 @@ def run_batched(args, jko, dev, barrier):
         barrier()
         secs = e0.elapsed_time(e1) / 1e3
         iters = sum(i["iters"] for row in table for i in row)
-        out[form] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
-                     "seconds": secs, "pairs": iters}
+        key = form if loop == 0 else f"{form}_per_pass_kernels"
+        out[key] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
+                    "seconds": secs, "pairs": iters, "kernels": jko.jko_batch_info(b)}
         jko.jko_batch_destroy(b)
     return out
 

@@ -95,6 +95,13 @@ typedef struct jko_params {
                        and the grid allow it, else one kernel per pass), 1 = persistent
                        kernel required (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one
                        kernel per pass */
+  int tile;         /* tensor-core precisions: output tile width of the per-pass kernels,
+                       64 or 128 (128: not JKO_BF16X3), or 0 = automatic.  With loop = 0
+                       and tile = 0 on grids of 256^2 cells or more, jko_create times the
+                       loop kernel and the per-pass kernels at both widths on 16 pairs and
+                       keeps the fastest; the choice is cached per grid, lengths, gamma,
+                       precision and energy kind for the process, so handles created
+                       alike run the same kernels (jko_handle_info reports them) */
 } jko_params;
 
 /* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */
@@ -178,6 +185,13 @@ jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops)
  * Overwrites the handle's scaling iterates, like jko_profile_passes. */
 jko_status jko_profile_loop(jko_handle* h, int pairs, int reps, float* ms, double* flops);
 
+/* How a handle runs its scaling loop (diagnostics; the paper has no
+ * counterpart).  out[0] = 1 if it uses the persistent loop kernel, out[1] = 1
+ * if that kernel keeps the Gibbs-factor band resident in shared memory,
+ * out[2] = 1 if its launch (or chunk of per-pass launches) is replayed from a
+ * CUDA graph, out[3] = pairs per launch or chunk.  out: 4 ints (host). */
+jko_status jko_handle_info(const jko_handle* h, int* out);
+
 /* One JKO step without any memory allocation (the paper has no counterpart;
  * this is a deployment variant of jko_step).
  *
@@ -252,10 +266,20 @@ typedef struct jko_batch jko_batch;
  * Each JKO step of the batch runs as three CUDA graphs whose parallel
  * branches are the flows, so small and large flows share the GPU; a flow that
  * has met its stopping rule (Sec. 3.4) turns its remaining kernels into
- * no-ops.  Errors as jko_create, with the failing flow named in
+ * no-ops, and a flow on the persistent loop kernel is one launch per step in
+ * its branch.  When every flow is a tensor-core flow on automatic kernels
+ * (loop = tile = 0), the batch times the candidate kernel configurations on
+ * its own graph and keeps the fastest (jko_batch_info reports it).  Errors as jko_create, with the failing flow named in
  * jko_batch_last_error(NULL). */
 jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params* params,
                             const jko_energy* energies, void* stream, jko_batch** out);
+
+/* How a batch runs its flows (diagnostics).  out[0] = the configuration its
+ * autotuner chose (-1: not tuned; 0: each flow's own choice, 1: per-pass
+ * kernels with 64-wide tiles, 2: 128-wide tiles, 3: the loop kernel), out[1]
+ * = number of flows on the loop kernel, out[2] = 1 if the per-pass fallback
+ * was taken because loop launches could not be captured.  out: 3 ints. */
+jko_status jko_batch_info(const jko_batch* b, int* out);
 
 /* n_steps steps of every flow (Eq. smooth-jko) from p0_dev[f] (device image of
  * flow f, double for JKO_FP64 flows, float otherwise; validated as in

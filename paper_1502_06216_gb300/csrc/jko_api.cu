@@ -9,10 +9,14 @@
 // A chunk of `check_every` pairs is captured once as a CUDA graph.  The host
 // launches chunks and polls a 16-byte slice of the device control block, with
 // one chunk always in flight; kernels launched after the stop return at once.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "jko.h"
@@ -169,6 +173,105 @@ cudaError_t launch_chunk(jko_handle* h, cudaStream_t st) {
   return jko::tc_enqueue_loop(h->tc, h->chunk_iters, st);
 }
 
+// ---- tile-shape autotuner (tensor-core handles) ----
+// A candidate is how the scaling loop runs: the persistent loop kernel, or the
+// per-pass kernels with 64- or 128-wide output tiles.
+enum Cand : int { CAND_LOOP = 0, CAND_PP64 = 1, CAND_PP128 = 2 };
+
+bool apply_cand(jko_handle* h, int cand) {
+  if (cand == CAND_LOOP) {
+    if (!jko::tc_loop_supported(h->tc)) return false;
+    h->use_loop = 1;
+    return jko::tc_set_tile(h->tc, 64) == 0;
+  }
+  h->use_loop = 0;
+  return jko::tc_set_tile(h->tc, cand == CAND_PP128 ? 128 : 64) == 0;
+}
+
+// Puts a handle in a running state that never stops (it = 1, tol < 0, no
+// budget) with q = 1/N and a = 1, so that timed launches do full work.
+cudaError_t prime_for_timing(jko_handle* h, cudaStream_t st) {
+  Ctrl c0;
+  std::memcpy(&c0, h->ctrl_init, sizeof(Ctrl));
+  c0.it = 1;
+  c0.tol = -1.0;
+  c0.max_iter = 0x7fffffff;
+  cudaError_t e = cudaMemcpy(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = jko::launch_fill<float>((float*)h->q, 1.0f / (float)h->N, h->N, st);
+  if (e == cudaSuccess) e = jko::tc_begin_step(h->tc, st);
+  return e;
+}
+
+// Milliseconds of one replay of `g` (median of three after a warm-up), or a
+// negative value on error.
+float time_graph(cudaGraphExec_t g, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  float best[3] = {0, 0, 0};
+  if (cudaGraphLaunch(g, st) != cudaSuccess) return -1.f;
+  for (int r = 0; r < 3; ++r) {
+    if (cudaEventRecord(e0, st) != cudaSuccess || cudaGraphLaunch(g, st) != cudaSuccess ||
+        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&best[r], e0, e1) != cudaSuccess)
+      return -1.f;
+  }
+  std::sort(best, best + 3);
+  return best[1];
+}
+
+constexpr int kTunePairs = 16;
+
+// Times `pairs` pairs of candidate `cand` on handle h as a captured graph.
+float time_cand(jko_handle* h, int cand) {
+  if (!apply_cand(h, cand)) return -1.f;
+  if (prime_for_timing(h, h->cap) != cudaSuccess) return -1.f;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1.f;
+  cudaError_t e = cudaSuccess;
+  if (cand == CAND_LOOP) e = jko::tc_enqueue_loop(h->tc, kTunePairs, h->cap);
+  else
+    for (int i = 0; i < kTunePairs && e == cudaSuccess; ++i) e = enqueue_pair(h, h->cap);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  float ms = -1.f;
+  if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess)
+    ms = time_graph(ge, h->cap, h->ev0, h->ev1);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ms;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, double, double, double, int, int, int>, int> g_tune_cache;
+
+// Picks the fastest candidate for h (cached per device, grid, lengths, gamma,
+// precision, energy kind and absorption) and leaves it applied.
+jko_status autotune(jko_handle* h, const jko_grid* g, const jko_params* p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, g->nx, g->ny, g->lx, g->ly, p->gamma, h->prec, h->ek,
+                                   jko::tc_absorbed(h->tc));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply_cand(h, it->second);
+      return JKO_OK;
+    }
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  for (int cand = CAND_LOOP; cand <= CAND_PP128; ++cand) {
+    const float ms = time_cand(h, cand);
+    if (ms > 0.f && (best < 0 || ms < best_ms)) { best = cand; best_ms = ms; }
+  }
+  CK(h, cudaMemcpy(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  if (best < 0) return set_err(h, JKO_ERR_CUDA, "autotuner: no candidate ran");
+  apply_cand(h, best);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return JKO_OK;
+}
+
 void free_handle(jko_handle* h) {
   if (!h) return;
   DeviceGuard dg(h->device);
@@ -205,6 +308,8 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
   if (p->loop < 0 || p->loop > 2)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "loop must be 0 (automatic), 1 or 2");
+  if (p->tile != 0 && p->tile != 64 && p->tile != 128)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "tile must be 0 (automatic), 64 or 128");
   if (p->absorb < 0 || p->absorb > 2)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "absorb must be 0 (automatic), 1 or 2");
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
@@ -522,8 +627,16 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       if (params->loop == 1 && !ok)
         s = set_err(h, JKO_ERR_UNSUPPORTED,
                     "the persistent loop kernel cannot run here (nx % 4 != 0 or no cooperative launch)");
+      else if (params->tile != 0 && jko::tc_set_tile(h->tc, params->tile) != 0)
+        s = set_err(h, JKO_ERR_UNSUPPORTED, "tile width not available for this precision");
       h->use_loop = params->loop != 2 && ok;
     }
+  }
+  if (s == JKO_OK && h->tc && params->loop == 0 && params->tile == 0 &&
+      (long long)grid->nx * grid->ny >= 256LL * 256LL) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "set-up"));
+    s = autotune(h, grid, params);
   }
   if (s != JKO_OK) return fail(s);
   e = cudaDeviceSynchronize();
@@ -664,6 +777,15 @@ jko_status jko_profile_loop(jko_handle* h, int pairs, int reps, float* ms, doubl
   return JKO_OK;
 }
 
+jko_status jko_handle_info(const jko_handle* h, int* out) {
+  if (!h || !out) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle or out");
+  out[0] = h->use_loop;
+  out[1] = h->use_loop && h->tc ? jko::tc_loop_resident(h->tc) : 0;
+  out[2] = h->chunk != nullptr;
+  out[3] = h->chunk_iters;
+  return JKO_OK;
+}
+
 jko_status jko_set_stream(jko_handle* h, void* stream) {
   if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
   h->stream = (cudaStream_t)stream;
@@ -724,6 +846,8 @@ struct jko_batch {
   int* done_host = nullptr;          // pinned, 2 slots of n
   cudaEvent_t ev_poll[2] = {nullptr, nullptr};
   int last_iters = 0;
+  bool per_pass = false;             // run every flow on per-pass kernels
+  int tuned = -1;                    // candidate the batch autotuner chose
   std::string err;
 };
 
@@ -767,7 +891,11 @@ cudaError_t flow_prologue(jko_handle* h, cudaStream_t s) {
   return jko::launch_fill<float>((float*)h->a, 1.0f, h->N, s);
 }
 
-cudaError_t flow_chunk(jko_handle* h, int C, cudaStream_t s) {
+cudaError_t flow_chunk(jko_handle* h, int C, bool per_pass, cudaStream_t s, int loop_pairs = 0) {
+  // a flow on the loop kernel: one launch runs its whole pair budget and stops
+  // itself; later chunks of the step find it stopped and return at once
+  if (h->use_loop && !per_pass)
+    return jko::tc_enqueue_loop(h->tc, loop_pairs > 0 ? loop_pairs : h->chunk_iters, s);
   for (int i = 0; i < C; ++i) {
     cudaError_t e = enqueue_pair(h, s);
     if (e != cudaSuccess) return e;
@@ -788,6 +916,55 @@ cudaError_t flow_finalize_t(jko_handle* h, cudaStream_t s) {
 
 cudaError_t flow_finalize(jko_handle* h, cudaStream_t s) {
   return h->fp64 ? flow_finalize_t<double>(h, s) : flow_finalize_t<float>(h, s);
+}
+
+template <class F, class G>
+jko_status capture_batch(jko_batch* b, F per_flow, G tail, cudaGraphExec_t* out);
+
+// Batch autotuner: the configuration of every flow (loop kernel or per-pass
+// kernels with 64- or 128-wide tiles) that runs the whole batch fastest.
+// Candidates: each flow's own choice, all per-pass 64, all per-pass 128 (64
+// where the precision has no 128), all on the loop kernel where it can run.
+jko_status tune_batch(jko_batch* b) {
+  const int n = b->n;
+  std::vector<int> own(n);
+  for (int f = 0; f < n; ++f)
+    own[f] = b->h[f]->use_loop ? CAND_LOOP : (jko::tc_tile(b->h[f]->tc) == 128 ? CAND_PP128 : CAND_PP64);
+  auto cand_of = [&](int c, int f) {
+    jko_handle* h = b->h[f];
+    if (c == 0) return own[f];
+    if (c == 1) return (int)CAND_PP64;
+    if (c == 2) return h->prec == JKO_BF16X3 ? (int)CAND_PP64 : (int)CAND_PP128;
+    return jko::tc_loop_supported(h->tc) ? (int)CAND_LOOP : (int)CAND_PP64;
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = -1.f;
+  for (int c = 0; c < 4; ++c) {
+    bool ok = true;
+    for (int f = 0; f < n && ok; ++f) ok = apply_cand(b->h[f], cand_of(c, f));
+    for (int f = 0; f < n && ok; ++f) ok = prime_for_timing(b->h[f], b->stream) == cudaSuccess;
+    if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) { cudaGetLastError(); continue; }
+    cudaGraphExec_t ge = nullptr;
+    jko_status s = capture_batch(
+        b, [](jko_handle* h, cudaStream_t st) { return flow_chunk(h, kTunePairs, false, st, kTunePairs); },
+        [](cudaStream_t) { return cudaSuccess; }, &ge);
+    if (s != JKO_OK) { cudaGetLastError(); continue; }
+    const float ms = time_graph(ge, b->stream, e0, e1);
+    cudaGraphExecDestroy(ge);
+    if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) { best = c; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int f = 0; f < n; ++f) {
+    apply_cand(b->h[f], cand_of(best, f));
+    BCK(b, cudaMemcpy(b->h[f]->ctrl, b->h[f]->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  }
+  b->tuned = best;
+  b->err.clear();
+  return JKO_OK;
 }
 
 // Captures one graph whose branches run `per_flow` for every flow, joined on
@@ -898,21 +1075,56 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
       cudaSuccess)
     return fail(batch_err(b, JKO_ERR_CUDA, "upload of control pointers"));
   const int C = b->C;
+  // tile shapes for the batch as a whole: with every flow on automatic
+  // kernels, time the candidates on the batch graph and keep the fastest
+  bool tune = true;
+  for (int f = 0; f < n_flows; ++f)
+    tune = tune && params[f].loop == 0 && params[f].tile == 0 && b->h[f]->tc;
+  if (tune) {
+    jko_status st = tune_batch(b);
+    if (st != JKO_OK) return fail(st);
+  }
+  for (auto* h : b->h)
+    if (h->tc) h->chunk_iters = h->use_loop ? h->prm.max_iter + 1 : C;
   jko_status s = capture_batch(
       b, [](jko_handle* h, cudaStream_t st) { return flow_prologue(h, st); },
       [](cudaStream_t) { return cudaSuccess; }, &b->g_pro);
   if (s != JKO_OK) return fail(s);
-  s = capture_batch(
-      b, [C](jko_handle* h, cudaStream_t st) { return flow_chunk(h, C, st); },
-      [b](cudaStream_t root) { return jko::launch_gather_done(b->ctrl_ptrs, b->done_dev, b->n, root); },
-      &b->g_chunk);
+  auto capture_chunks = [&]() {
+    const bool pp = b->per_pass;
+    return capture_batch(
+        b, [C, pp](jko_handle* h, cudaStream_t st) { return flow_chunk(h, C, pp, st); },
+        [b](cudaStream_t root) { return jko::launch_gather_done(b->ctrl_ptrs, b->done_dev, b->n, root); },
+        &b->g_chunk);
+  };
+  s = capture_chunks();
+  if (s != JKO_OK) {
+    // cooperative launches that cannot be captured: per-pass kernels instead
+    cudaGetLastError();
+    b->per_pass = true;
+    s = capture_chunks();
+  }
   if (s != JKO_OK) return fail(s);
+  // every flow on the loop kernel: one chunk launch covers the whole budget
+  bool all_loop = !b->per_pass;
+  for (auto* h : b->h) all_loop = all_loop && h->use_loop;
+  if (all_loop) b->C = b->max_iter + 1;
   s = capture_batch(
       b, [](jko_handle* h, cudaStream_t st) { return flow_finalize(h, st); },
       [b](cudaStream_t root) { return jko::launch_gather_ctrl(b->ctrl_ptrs, b->ctrl_all, b->n, root); },
       &b->g_fin);
   if (s != JKO_OK) return fail(s);
   *out = b;
+  return JKO_OK;
+}
+
+jko_status jko_batch_info(const jko_batch* b, int* out) {
+  if (!b || !out) return batch_err(nullptr, JKO_ERR_INVALID_ARG, "NULL batch or out");
+  int nl = 0;
+  for (auto* h : b->h) nl += (h->use_loop && !b->per_pass) ? 1 : 0;
+  out[0] = b->tuned;
+  out[1] = nl;
+  out[2] = b->per_pass ? 1 : 0;
   return JKO_OK;
 }
 

@@ -517,9 +517,11 @@ struct TcPlan {
   CUtensorMap fQ, fE, fP;                           // fp32 fields q, e^{-sigma w}, p
   int tma_epi = 0;
   double flops[4] = {0, 0, 0, 0};
-  // persistent pair-loop kernel (tc_loop.cu): image operand loads with 64-row
-  // boxes, support flag, grid size and executed flops of one pair
+  // image operand loads with 64-row boxes (64-wide tiles: per-pass kernels and
+  // the persistent loop kernel); mA/mB/mT above have boxes of the wide tile
   CUtensorMap lA[2], lB[2], lT[2];
+  // persistent pair-loop kernel (tc_loop.cu): support flag, grid size and
+  // executed flops of one pair
   int loop_ok = 0;
   int loop_grid = 0;
   int loop_res = 0;            // the loop kernel keeps each CTA's factor band resident

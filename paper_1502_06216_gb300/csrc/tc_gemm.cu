@@ -523,6 +523,24 @@ int absorbed_energy(TcPlan* P, const std::vector<double>& bx, const std::vector<
   return 0;
 }
 
+// Executed flops of each pass for the current tile widths, from the band tables.
+void pass_flops_of(TcPlan* P) {
+  const TcConfig& c = P->cfg;
+  const int KE = P->mode == MODE_TF32 ? 32 : 64;
+  const double mult = P->mode == MODE_BF16X3 ? 3.0 : 1.0;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int axis = (pass & 1) == 0 ? 0 : 1;
+    const int side = P->absorbed ? (pass >> 1) : 0;
+    const int M = axis == 0 ? c.nx : c.ny, N = axis == 0 ? c.ny : c.nx;
+    const int bn = axis == 0 ? P->bn_x : P->bn_y;
+    std::vector<int2> tab((M + BM - 1) / BM);
+    cudaMemcpy(tab.data(), P->kbt[axis][side], tab.size() * sizeof(int2), cudaMemcpyDeviceToHost);
+    double f = 0.0;
+    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)(((N + bn - 1) / bn) * bn) * mult;
+    P->flops[pass] = f;
+  }
+}
+
 template <typename T>
 int create_typed(TcPlan* P, std::string* msg) {
   TcConfig& c = P->cfg;
@@ -593,9 +611,15 @@ int create_typed(TcPlan* P, std::string* msg) {
         ok = make_map(&P->mK[axis][side][sp], P->k[axis][sd][si], m, n, n,
                       axis == 0 ? P->px : P->py, BM);
       }
-    ok = ok && make_map(&P->mA[sp], P->img_a[si], m, ny, nx, P->px, P->bn_x) &&
-         make_map(&P->mB[sp], P->img_b[si], m, ny, nx, P->px, P->bn_x) &&
-         make_map(&P->mT[sp], P->img_t[si], m, nx, ny, P->py, P->bn_y) &&
+    // image operand loads: boxes of 64 rows (64-wide tiles) and, where the
+    // mode has them, 128 rows (128-wide tiles)
+    const int wide = m == MODE_BF16X3 ? 64 : 128;
+    ok = ok && make_map(&P->lA[sp], P->img_a[si], m, ny, nx, P->px, 64) &&
+         make_map(&P->lB[sp], P->img_b[si], m, ny, nx, P->px, 64) &&
+         make_map(&P->lT[sp], P->img_t[si], m, nx, ny, P->py, 64) &&
+         make_map(&P->mA[sp], P->img_a[si], m, ny, nx, P->px, wide) &&
+         make_map(&P->mB[sp], P->img_b[si], m, ny, nx, P->px, wide) &&
+         make_map(&P->mT[sp], P->img_t[si], m, nx, ny, P->py, wide) &&
          make_map(&P->sA[sp], P->img_a[si], m, ny, nx, P->px, BM) &&
          make_map(&P->sB[sp], P->img_b[si], m, ny, nx, P->px, BM) &&
          make_map(&P->sT[sp], P->img_t[si], m, nx, ny, P->py, BM);
@@ -613,19 +637,7 @@ int create_typed(TcPlan* P, std::string* msg) {
       ok = make_map(&P->fE, (void*)c.prox.E, MODE_TF32, ny, nx, nx, BM);
     if (!ok) { *msg = "cuTensorMapEncodeTiled failed (fields)"; return 2; }
   }
-  // executed flops per pass, from the band tables
-  const double mult = m == MODE_BF16X3 ? 3.0 : 1.0;
-  for (int pass = 0; pass < 4; ++pass) {
-    const int axis = (pass & 1) == 0 ? 0 : 1;
-    const int side = P->absorbed ? (pass >> 1) : 0;
-    const int M = axis == 0 ? nx : ny, N = axis == 0 ? ny : nx;
-    const int bn = axis == 0 ? P->bn_x : P->bn_y;
-    std::vector<int2> tab((M + BM - 1) / BM);
-    cudaMemcpy(tab.data(), P->kbt[axis][side], tab.size() * sizeof(int2), cudaMemcpyDeviceToHost);
-    double f = 0.0;
-    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)(((N + bn - 1) / bn) * bn) * mult;
-    P->flops[pass] = f;
-  }
+  pass_flops_of(P);
   cudaError_t ea = m == MODE_TF32 ? set_attrs<MODE_TF32>()
                                   : (m == MODE_BF16X3 ? set_attrs<MODE_BF16X3>() : set_attrs<MODE_BF16>());
   if (ea != cudaSuccess) { *msg = "cudaFuncSetAttribute (shared memory)"; return 2; }
@@ -684,8 +696,9 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
     a.pitch_out = P->py;
     a.out_hi = P->img_t[0]; a.out_lo = P->img_t[1];
     mp.a_hi = &P->mK[0][side][0]; mp.a_lo = &P->mK[0][side][1];
-    mp.b_hi = half == 0 ? &P->mA[0] : &P->mB[0];
-    mp.b_lo = half == 0 ? &P->mA[1] : &P->mB[1];
+    const bool w = P->bn_x != 64;   // image boxes of the tile width
+    mp.b_hi = half == 0 ? (w ? &P->mA[0] : &P->lA[0]) : (w ? &P->mB[0] : &P->lB[0]);
+    mp.b_lo = half == 0 ? (w ? &P->mA[1] : &P->lA[1]) : (w ? &P->mB[1] : &P->lB[1]);
     mp.o_hi = &P->sT[0]; mp.o_lo = &P->sT[1];
     mp.f = mp.pm = &P->mK[0][0][0];   // unused by the plain pass
     a.decide = half == 1 ? 1 : 0;  // the pass after the b-update decides
@@ -698,7 +711,9 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
     a.out_hi = half == 0 ? P->img_b[0] : P->img_a[0];
     a.out_lo = half == 0 ? P->img_b[1] : P->img_a[1];
     mp.a_hi = &P->mK[1][side][0]; mp.a_lo = &P->mK[1][side][1];
-    mp.b_hi = &P->mT[0]; mp.b_lo = &P->mT[1];
+    const bool w = P->bn_y != 64;
+    mp.b_hi = w ? &P->mT[0] : &P->lT[0];
+    mp.b_lo = w ? &P->mT[1] : &P->lT[1];
     mp.o_hi = half == 0 ? &P->sB[0] : &P->sA[0];
     mp.o_lo = half == 0 ? &P->sB[1] : &P->sA[1];
     mp.f = half == 0 ? &P->fQ : &P->fE;
@@ -715,6 +730,15 @@ cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
 }
 
 double tc_pass_flops(const TcPlan* P, int which) { return P->flops[which & 3]; }
+
+int tc_tile(const TcPlan* P) { return P->bn_x == P->bn_y ? P->bn_x : 0; }
+
+int tc_set_tile(TcPlan* P, int bn) {
+  if (bn != 64 && !(bn == 128 && P->mode != MODE_BF16X3)) return 1;
+  P->bn_x = P->bn_y = bn;
+  pass_flops_of(P);
+  return 0;
+}
 
 int tc_absorbed(const TcPlan* P) { return P ? P->absorbed : 0; }
 

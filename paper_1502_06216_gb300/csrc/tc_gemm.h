@@ -46,6 +46,10 @@ cudaError_t tc_begin_step(TcPlan* plan, cudaStream_t st);
 cudaError_t tc_enqueue_pass(TcPlan* plan, int which, cudaStream_t st);
 // Multiply-add flops (x2) of the tiles pass `which` executes.
 double tc_pass_flops(const TcPlan* plan, int which);
+// Output tile width of the per-pass kernels: 64, or 128 (not BF16X3).
+// tc_set_tile returns 1 for a width the precision does not have.
+int tc_tile(const TcPlan* plan);
+int tc_set_tile(TcPlan* plan, int bn);
 void tc_destroy(TcPlan* plan);
 
 // Persistent pair-loop kernel (tc_loop.cu).  Set-up after the plan's images
@@ -53,6 +57,7 @@ void tc_destroy(TcPlan* plan);
 // 2 = CUDA error.
 int tc_loop_setup(TcPlan* plan, std::string* msg);
 int tc_loop_supported(const TcPlan* plan);
+int tc_loop_resident(const TcPlan* plan);
 // One cooperative launch running up to `pairs` pairs of the scaling loop with
 // the stop protocol in the kernel (same Ctrl as the per-pass kernels).
 cudaError_t tc_enqueue_loop(TcPlan* plan, int pairs, cudaStream_t st);

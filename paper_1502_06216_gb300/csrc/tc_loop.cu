@@ -699,18 +699,7 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
     P->loop_res = same ? 1 : 0;
   }
   cudaGetLastError();
-  // image operands with 64-row boxes
-  const TcConfig& c = P->cfg;
-  const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
-  for (int sp = 0; sp < 2; ++sp) {
-    const int si = sp < nsplit ? sp : 0;
-    if (!make_map(&P->lA[sp], P->img_a[si], P->mode, c.ny, c.nx, P->px, LBN) ||
-        !make_map(&P->lB[sp], P->img_b[si], P->mode, c.ny, c.nx, P->px, LBN) ||
-        !make_map(&P->lT[sp], P->img_t[si], P->mode, c.nx, c.ny, P->py, LBN)) {
-      *msg = "cuTensorMapEncodeTiled failed (loop maps)";
-      return 2;
-    }
-  }
+  static_assert(LBN == 64, "the plan's 64-row image maps serve the loop kernel");
   // executed flops of one pair with 64-wide tiles
   const int KE = P->mode == MODE_TF32 ? 32 : 64;
   const double mult = P->mode == MODE_BF16X3 ? 3.0 : 1.0;
@@ -731,6 +720,8 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
 }
 
 int tc_loop_supported(const TcPlan* P) { return P && P->loop_ok; }
+
+int tc_loop_resident(const TcPlan* P) { return P && P->loop_ok && P->loop_res; }
 
 double tc_loop_flops(const TcPlan* P, int pairs) { return P->loop_flops_pair * pairs; }
 

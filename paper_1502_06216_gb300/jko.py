@@ -55,7 +55,8 @@ class jko_params(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("precision", ctypes.c_int), ("renormalize", ctypes.c_int),
                 ("absorb", ctypes.c_int),
-                ("loop", ctypes.c_int)]
+                ("loop", ctypes.c_int),
+                ("tile", ctypes.c_int)]
 
 
 class jko_energy(ctypes.Structure):
@@ -91,6 +92,8 @@ EXPORTS = {
     "jko_profile_loop": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "jko_handle_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "jko_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "jko_step_noalloc": (ctypes.c_int, [ctypes.POINTER(jko_grid), ctypes.POINTER(jko_params),
                                         ctypes.POINTER(jko_energy), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p,
@@ -184,12 +187,13 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                tol: float = 1e-6, max_iter: int = 200, check_every: int = 0,
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
-               alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0) -> Handle:
+               alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
+               tile: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied)."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
-                   int(absorb), int(loop))
+                   int(absorb), int(loop), int(tile))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
@@ -280,6 +284,24 @@ def jko_profile_loop(h: Handle, pairs: int = 16, reps: int = 10):
     return ms[0], fl[0]
 
 
+def jko_handle_info(h: Handle) -> dict:
+    """Which kernels a handle runs: persistent loop kernel, resident factor
+    band, graph replay, pairs per launch or chunk."""
+    out = (ctypes.c_int * 4)()
+    _check(lib().jko_handle_info(h.ptr, out), h.ptr)
+    return {"loop": bool(out[0]), "resident": bool(out[1]), "graph": bool(out[2]),
+            "pairs_per_launch": int(out[3])}
+
+
+def jko_batch_info(b) -> dict:
+    """The batch autotuner's choice: 'tuned' (-1 none, 0 each flow's own, 1
+    per-pass 64, 2 per-pass 128, 3 loop kernel), flows on the loop kernel,
+    and whether the per-pass fallback was taken."""
+    out = (ctypes.c_int * 3)()
+    _check(lib().jko_batch_info(b.ptr, out), None)
+    return {"tuned": int(out[0]), "loop_flows": int(out[1]), "per_pass_fallback": bool(out[2])}
+
+
 def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
                      max_iter: Optional[int] = None, renormalize: bool = True):
     """jko_step_noalloc for an ``inputs.Problem``: one FP32 step whose working
@@ -326,14 +348,14 @@ def jko_build_info() -> str:
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
                         max_iter: Optional[int] = None, check_every: int = 0,
                         renormalize: bool = True, stream=None, absorb: int = 0,
-                        loop: int = 0) -> Handle:
+                        loop: int = 0, tile: int = 0) -> Handle:
     """jko_create from an ``inputs.Problem``."""
     return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
                       tol=pb.tol if tol is None else tol,
                       max_iter=pb.max_iter if max_iter is None else max_iter,
                       check_every=check_every, precision=precision, renormalize=renormalize,
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
-                      stream=stream, absorb=absorb, loop=loop)
+                      stream=stream, absorb=absorb, loop=loop, tile=tile)
 
 
 class Batch:
@@ -367,7 +389,8 @@ def _energy_struct(pb, keep):
 
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
-                     check_every: int = 0, renormalize: bool = True, stream=None) -> Batch:
+                     check_every: int = 0, renormalize: bool = True, stream=None,
+                     loop: int = 0, tile: int = 0) -> Batch:
     """jko_batch_create for a list of ``inputs.Problem``; ``precision`` may be
     one value or one per flow."""
     n = len(problems)
@@ -380,7 +403,7 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
         G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
         P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                           pb.max_iter if max_iter is None else max_iter, check_every,
-                          int(precs[f]), int(bool(renormalize)), 0)
+                          int(precs[f]), int(bool(renormalize)), 0, int(loop), int(tile))
         E[f] = _energy_struct(pb, keep)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -60,3 +60,25 @@ def test_batch_recipe_flows_match_oracle():
         bar = 1e-5 if precs[f] == jko.Precision.FP32 else 1e-3
         print(f, pb.name, precs[f].name, "rel L1", err, "iters", [table[t][f]["iters"] for t in range(2)])
         assert err <= bar
+
+
+def test_batch_autotuner_all_tensor_core_flows():
+    """A batch of tensor-core flows on automatic kernels is tuned as a whole:
+    the chosen configuration is reported, and every flow still matches the
+    FP64 oracle within its form's bar (BF16x3 and TF32)."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pbs = [p for p in inputs.batched_problems(24) if p.nx <= 256][:8]
+    precs = [jko.Precision.BF16X3 if i % 2 == 0 else jko.Precision.TF32 for i in range(len(pbs))]
+    b = jko.jko_batch_create(pbs, precision=precs)
+    info = jko.jko_batch_info(b)
+    print("batch autotuner", info)
+    assert info["tuned"] in (0, 1, 2, 3)
+    p0s = [torch.tensor(pb.q0, dtype=torch.float32, device="cuda") for pb in pbs]
+    finals, table = jko.jko_batch_flow(b, p0s, 2)
+    for f, pb in enumerate(pbs):
+        ref = ojko.problem_flow(pb, n_steps=2)
+        err = rel_l1(finals[f].double().cpu().numpy(), ref.traj[2])
+        print(f, pb.name, precs[f].name, "rel L1", err)
+        assert err <= 1e-3
+    jko.jko_batch_destroy(b)

@@ -150,3 +150,27 @@ def test_profile_loop():
           fl / ms / 1e9, "TFLOP/s")
     assert 0 < ms < 50 and fl > 0
     jko.jko_destroy(h)
+
+
+def test_handle_info_and_autotuner():
+    """Explicit settings run the kernels they name; the automatic setting
+    (autotuned on this grid) runs one of the candidates and is cached: a second
+    handle of the same kind makes the same choice."""
+    need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pb = inputs.config_problem(2, n=1024)
+    def info(**kw):
+        h = jko.create_from_problem(pb, precision=jko.Precision.BF16, **kw)
+        i = jko.jko_handle_info(h)
+        jko.jko_destroy(h)
+        return i
+    loop = info(loop=1)
+    assert loop["loop"] and loop["resident"] and loop["pairs_per_launch"] == pb.max_iter + 1
+    pp = info(loop=2, tile=128)
+    assert not pp["loop"] and pp["pairs_per_launch"] == 16
+    a1, a2 = info(), info()
+    print("loop", loop, "per-pass", pp, "auto", a1)
+    assert a1 == a2
+    assert a1["graph"]
+    with pytest.raises(jko.JKOError):
+        jko.create_from_problem(pb, precision=jko.Precision.BF16X3, tile=128)
