@@ -17,6 +17,8 @@ Plain, slow and written to be checked against the paper by eye:
                    Dykstra on couplings (Eq. iter-dystra-1/2); the flow (Eq. smooth-jko).
 * ``dual``      -- an independent brute-force solve of the step by maximising its
                    Fenchel dual with L-BFGS-B (primal-dual route of Prop. 3.1).
+* ``mirror``    -- an independent brute-force solve of the step by entropic
+                   mirror descent on the full coupling (smooth energies).
 * ``objective`` -- entropy E, W_gamma by a converged dense Sinkhorn, f, the step
                    objective.
 * ``logdomain`` -- the same scaling loop written with log-sum-exp (FP64).
@@ -28,5 +30,5 @@ Parity status of every function is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force and invariants.
 """
 
-from . import gibbs, prox, jko, dual, objective, logdomain  # noqa: F401
+from . import gibbs, prox, jko, dual, mirror, objective, logdomain  # noqa: F401
 from .energy import Energy  # noqa: F401
