@@ -81,6 +81,20 @@ def test_full_size_1024_fixed_pairs(prec):
     assert err <= FLOW_BARS[prec]
 
 
+@pytest.mark.parametrize("prec", ["BF16X3", "TF32", "BF16"])
+def test_full_size_2048_fixed_pairs(prec):
+    """The second grid of the precision workload, 2048^2 (512 tiles per pass,
+    several per CTA): 4 pairs from q0 against the FP64 oracle, through the
+    kernels the automatic setting picks."""
+    pb = inputs.config_problem(2, n=2048)
+    ref = ojko.problem_flow(pb, n_steps=1, tol=0.0, max_iter=4)
+    traj, infos = gpu_flow(pb, prec, 1, tol=0.0, max_iter=4)
+    err = rel_l1(traj[0], ref.traj[1])
+    print(prec, "2048 rel L1 after 4 pairs", err)
+    assert infos[0]["iters"] == 4
+    assert err <= FLOW_BARS[prec]
+
+
 def test_tc_and_simt_agree_on_bench_state():
     """BF16x3 and FP32 CUDA-core forms from a congested state of the 1024^2 flow."""
     torch = need_gpu()
