@@ -163,6 +163,20 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(total_s, iters, ws, dev=None):
+    """Whole-job figures of N replicas: the slowest rank's timed seconds (max)
+    and the pairs all ranks ran (sum).  One rank: the inputs themselves."""
+    if ws <= 1:
+        return float(total_s), float(iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it_t = torch.tensor([float(iters)], device=dev, dtype=torch.float64)
+    dist.all_reduce(it_t)
+    return float(t.item()), float(it_t.item())
+
+
 def workload(n):
     from paper_1502_06216_gb300 import inputs
     pb = inputs.config_problem(2, n=n)
@@ -392,15 +406,7 @@ def run_ours(args):
     h = R["h"]
     prec = jko.Precision[head]
     total_s, iters, infos = R["total_s"], R["iters"], R["infos"]
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        it_t = torch.tensor([iters], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(it_t)
-        iters_all = float(it_t.item())
-    else:
-        iters_all = float(iters)
+    total_s, iters_all = aggregate_over_ranks(total_s, iters, ws, dev)
     value = iters_all / total_s
     steps_per_s = ws * args.steps / total_s
 
