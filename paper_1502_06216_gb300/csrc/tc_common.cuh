@@ -477,6 +477,16 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 }  // namespace
 
 namespace {
+// Band of one 128-row tile of a 1-D factor, as the kernels walk it: K-blocks
+// of KE columns starting at column x (a multiple of 128 bytes), y blocks, and
+// the first and last non-zero columns z, w.  Every K=UK sub-step of every
+// block is issued: skipping the sub-steps outside [z, w], which multiply
+// exact zeros, measured 7 % slower (25.4 against 23.8 us per pair at 1024^2).
+// Executed multiply-add flops (x2) of one tile of width bn over its band.
+inline double band_tile_flops(int4 kb, int KE, int bn, double mult) {
+  return 2.0 * 128.0 * (double)bn * KE * kb.y * mult;
+}
+
 // Sum of one float per thread over 16 warps (threads 0..511) in a fixed order:
 // each warp's butterfly, then warp 0 over the 16 warp sums.  `sync` is the
 // barrier of those 512 threads.  The result is valid in thread 0.
@@ -504,7 +514,7 @@ struct TcPlan {
   // factors [axis 0 = x, 1 = y][side 0 = a (xi a), 1 = b (xi b)][hi, lo]; without
   // absorption the b side aliases the a side (the factor is symmetric)
   void* k[2][2][2] = {};
-  int2* kbt[2][2] = {};        // per-tile K-block ranges of each factor
+  int4* kbt[2][2] = {};        // per-tile band of each factor (see band_tile)
   float* E_abs = nullptr;      // absorbed e^{-(sigma w + beta)} (congestion kind)
   float* sw_abs = nullptr;     // absorbed sigma w + beta (entropy kinds)
   int absorbed = 0;

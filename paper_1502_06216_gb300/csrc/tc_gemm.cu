@@ -40,7 +40,7 @@ struct TcPassArgs {
   Ctrl* ctrl;
   ProxArgs<float> P;
   int tma_epi;            // 1: epilogue tiles moved by TMA (fp32 fields with nx % 4 == 0)
-  const int2* kbt;        // per 128-row tile: first K-block and count (band of the factor)
+  const int4* kbt;        // per 128-row tile: band of the factor (band_tile)
   double* part;           // residual partials, one per block of the b-update pass
   int nparts;             // partials read by the deciding pass
   int decide;             // 1: this pass takes the stop decision (stop_gate)
@@ -90,8 +90,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   const int m0 = blockIdx.y * BM;
 
   // K-blocks holding the non-zero band of rows [m0, m0 + BM) of the factor
-  const int2 kb = args.kbt[blockIdx.y];
-  const int kb_lo = kb.x;
+  const int4 kb = args.kbt[blockIdx.y];
   const int nkb = kb.y;
 
   if (threadIdx.x == 0) {
@@ -154,7 +153,7 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       if (!ok) break;
       unsigned char* st = smem + s * STAGE_BYTES;
       mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
-      const int kx = (kb_lo + i) * KE;
+      const int kx = kb.x + i * KE;
       tma_load_2d(st, &mapA_hi, &full_bar[s], kx, m0);
       tma_load_2d(st + A_BYTES, &mapB_hi, &full_bar[s], kx, n0);
       if constexpr (NSPLIT == 2) {
@@ -454,7 +453,7 @@ void axis_logscale(const TcConfig& c, int axis, std::vector<double>& beta) {
 // Also the per-tile K-block ranges of its non-zero entries.  Returns false if
 // an entry would overflow FP32.
 template <typename T>
-bool build_factor(std::vector<T>& hi, std::vector<T>& lo, std::vector<int2>& kbt, int n,
+bool build_factor(std::vector<T>& hi, std::vector<T>& lo, std::vector<int4>& kbt, int n,
                   int pitch, double length, double gamma, const std::vector<double>& beta,
                   bool transpose, int KE) {
   const double h = length / n;
@@ -487,9 +486,17 @@ bool build_factor(std::vector<T>& hi, std::vector<T>& lo, std::vector<int2>& kbt
         lo[(size_t)i * pitch + j] = __float2bfloat16_rn(f - __bfloat162float(bh));
       }
     }
-  kbt.assign(tiles, make_int2(0, 0));
+  // K-blocks from the first non-zero column rounded down to a whole 128-byte
+  // block: a box row that straddles two 128-byte lines costs the TMA two L2
+  // requests (measured: 380 instead of 160 ns per 64-row box), which more
+  // than cancels the block saved.
+  constexpr int ALIGN = 128 / (int)sizeof(T);
+  kbt.assign(tiles, make_int4(0, 0, 0, -1));
   for (int t = 0; t < tiles; ++t)
-    if (kmax[t] >= 0) kbt[t] = make_int2(kmin[t] / KE, kmax[t] / KE - kmin[t] / KE + 1);
+    if (kmax[t] >= 0) {
+      const int k0 = kmin[t] / ALIGN * ALIGN;
+      kbt[t] = make_int4(k0, (kmax[t] - k0) / KE + 1, kmin[t], kmax[t]);
+    }
   return true;
 }
 
@@ -533,10 +540,10 @@ void pass_flops_of(TcPlan* P) {
     const int side = P->absorbed ? (pass >> 1) : 0;
     const int M = axis == 0 ? c.nx : c.ny, N = axis == 0 ? c.ny : c.nx;
     const int bn = axis == 0 ? P->bn_x : P->bn_y;
-    std::vector<int2> tab((M + BM - 1) / BM);
-    cudaMemcpy(tab.data(), P->kbt[axis][side], tab.size() * sizeof(int2), cudaMemcpyDeviceToHost);
+    std::vector<int4> tab((M + BM - 1) / BM);
+    cudaMemcpy(tab.data(), P->kbt[axis][side], tab.size() * sizeof(int4), cudaMemcpyDeviceToHost);
     double f = 0.0;
-    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)(((N + bn - 1) / bn) * bn) * mult;
+    for (const int4& t : tab) f += band_tile_flops(t, KE, bn, mult) * ((N + bn - 1) / bn);
     P->flops[pass] = f;
   }
 }
@@ -555,7 +562,7 @@ int create_typed(TcPlan* P, std::string* msg) {
   axis_logscale(c, 0, beta[0]);
   axis_logscale(c, 1, beta[1]);
   std::vector<T> hi, lo;
-  std::vector<int2> kbt;
+  std::vector<int4> kbt;
   for (int axis = 0; axis < 2; ++axis) {
     const int n = axis == 0 ? nx : ny;
     const int pitch = axis == 0 ? P->px : P->py;
@@ -574,8 +581,8 @@ int create_typed(TcPlan* P, std::string* msg) {
           return 2;
         }
       }
-      if (cudaMalloc((void**)&P->kbt[axis][side], kbt.size() * sizeof(int2)) != cudaSuccess ||
-          cudaMemcpy(P->kbt[axis][side], kbt.data(), kbt.size() * sizeof(int2),
+      if (cudaMalloc((void**)&P->kbt[axis][side], kbt.size() * sizeof(int4)) != cudaSuccess ||
+          cudaMemcpy(P->kbt[axis][side], kbt.data(), kbt.size() * sizeof(int4),
                      cudaMemcpyHostToDevice) != cudaSuccess) {
         *msg = "upload of the band tables";
         return 2;

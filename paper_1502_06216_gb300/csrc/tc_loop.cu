@@ -88,7 +88,7 @@ struct LoopPass {
   int M, N;          // output D is M x N (M along the contracted axis)
   int tiles_n;       // tiles along N
   int ntiles;        // tiles of the pass
-  const int2* kbt;   // per 128-row tile: first K-block and count of the factor band
+  const int4* kbt;   // per 128-row tile: band of the factor (band_tile)
 };
 
 struct LoopArgs {
@@ -242,10 +242,10 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         // this CTA's factor band: the same m-tile and factor in every pass
         const LoopPass& P0 = args.pass[0];
         const int mt = (int)blockIdx.x / P0.tiles_n;
-        const int2 kb = P0.kbt[mt];
+        const int4 kb = P0.kbt[mt];
         mbar_arrive_expect_tx(res_bar, (uint32_t)kb.y * A_BYTES);
         for (int i = 0; i < kb.y; ++i)
-          tma_load_2d(res_a + i * A_BYTES, &maps.K[0][0], res_bar, (kb.x + i) * KE, mt * BM);
+          tma_load_2d(res_a + i * A_BYTES, &maps.K[0][0], res_bar, kb.x + i * KE, mt * BM);
       }
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
@@ -257,7 +257,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           const bool first = t == (int)blockIdx.x;
           const int mt = t / PS.tiles_n;
           const int m0 = mt * BM, n0 = (t - mt * PS.tiles_n) * LBN;
-          const int2 kb = PS.kbt[mt];
+          const int4 kb = PS.kbt[mt];
           if (epi_pass) {
             if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
             if (!ok) break;
@@ -293,7 +293,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               if (!ok) break;
               unsigned char* st = stages + s * STAGE_BYTES;
               mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
-              const int kx = (kb.x + i) * KE;
+              const int kx = kb.x + i * KE;
               tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
               if constexpr (NSPLIT == 2)
                 tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
@@ -319,7 +319,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             const uint32_t k = kc + i;
             const int s = (int)(k % STAGES);
             unsigned char* st = stages + s * STAGE_BYTES;
-            const int kx = (kb.x + i) * KE;
+            const int kx = kb.x + i * KE;
             if (RES) {
               if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
               if (!ok) break;
@@ -690,12 +690,13 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
   if (P->mode == MODE_BF16 && !P->absorbed && cc.nx == cc.ny && cc.lx == cc.ly &&
       maxt <= P->loop_grid && loop_blocks_per_sm<MODE_BF16, true>(ek) >= 1) {
     const LoopPass L0 = loop_pass(P, 0), L1 = loop_pass(P, 1);
-    std::vector<int2> t0((L0.M + BM - 1) / BM), t1((L1.M + BM - 1) / BM);
+    std::vector<int4> t0((L0.M + BM - 1) / BM), t1((L1.M + BM - 1) / BM);
     bool same = t0.size() == t1.size() &&
-                cudaMemcpy(t0.data(), L0.kbt, t0.size() * sizeof(int2), cudaMemcpyDeviceToHost) == cudaSuccess &&
-                cudaMemcpy(t1.data(), L1.kbt, t1.size() * sizeof(int2), cudaMemcpyDeviceToHost) == cudaSuccess;
+                cudaMemcpy(t0.data(), L0.kbt, t0.size() * sizeof(int4), cudaMemcpyDeviceToHost) == cudaSuccess &&
+                cudaMemcpy(t1.data(), L1.kbt, t1.size() * sizeof(int4), cudaMemcpyDeviceToHost) == cudaSuccess;
     for (size_t i = 0; same && i < t0.size(); ++i)
-      same = t0[i].x == t1[i].x && t0[i].y == t1[i].y && t0[i].y <= RES_KB;
+      same = t0[i].x == t1[i].x && t0[i].y == t1[i].y && t0[i].z == t1[i].z &&
+             t0[i].w == t1[i].w && t0[i].y <= RES_KB;
     P->loop_res = same ? 1 : 0;
   }
   cudaGetLastError();
@@ -706,13 +707,13 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
   double f = 0.0;
   for (int w = 0; w < 4; ++w) {
     const LoopPass L = loop_pass(P, w);
-    std::vector<int2> tab((L.M + BM - 1) / BM);
-    if (cudaMemcpy(tab.data(), L.kbt, tab.size() * sizeof(int2), cudaMemcpyDeviceToHost) !=
+    std::vector<int4> tab((L.M + BM - 1) / BM);
+    if (cudaMemcpy(tab.data(), L.kbt, tab.size() * sizeof(int4), cudaMemcpyDeviceToHost) !=
         cudaSuccess) {
       *msg = "reading the band tables";
       return 2;
     }
-    for (const int2& t : tab) f += 2.0 * BM * (double)t.y * KE * (double)L.tiles_n * LBN * mult;
+    for (const int4& t : tab) f += band_tile_flops(t, KE, LBN, mult) * L.tiles_n;
   }
   P->loop_flops_pair = f;
   P->loop_ok = 1;
