@@ -254,12 +254,16 @@ def run_reference(args):
 
 def run_batched(args, jko, dev, barrier):
     """256 independent crowd / porous flows of sizes {64,128,256,512}^2, 10 JKO
-    steps each, advanced together by one batch (graphs with a branch per flow)."""
+    steps each, advanced together by one batch (graphs with a branch per flow).
+    With N ranks every rank takes every N-th flow (no data exchange); the
+    whole-job rate is all ranks' pairs over the slowest rank's time."""
     import torch
     from paper_1502_06216_gb300 import inputs
-    pbs = inputs.batched_problems(256)
+    ws, rank, _ = dist_env()
+    pbs = inputs.batched_problems(256)[rank::ws]
     out = {"workload": "256 flows (crowd even / porous odd), n in {64,128,256,512}, "
-                       "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6"}
+                       "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6",
+           "flows_per_rank": len(pbs), "scaling": "weak" if ws == 1 else "strong"}
     for form, loop in (("BF16X3", 0), ("BF16X3", 2), ("FP32", 0)):
         b = jko.jko_batch_create(pbs, precision=jko.Precision[form], loop=loop)
         p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
@@ -270,8 +274,8 @@ def run_batched(args, jko, dev, barrier):
         _, table = jko.jko_batch_flow(b, p0s, 10, want_final=False)
         e1.record()
         barrier()
-        secs = e0.elapsed_time(e1) / 1e3
-        iters = sum(i["iters"] for row in table for i in row)
+        secs, iters = aggregate_over_ranks(e0.elapsed_time(e1) / 1e3,
+                                           sum(i["iters"] for row in table for i in row), ws, dev)
         key = form if loop == 0 else f"{form}_per_pass_kernels"
         out[key] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
                     "seconds": secs, "pairs": iters, "kernels": jko.jko_batch_info(b)}

@@ -174,3 +174,41 @@ def test_handle_info_and_autotuner():
     assert a1["graph"]
     with pytest.raises(jko.JKOError):
         jko.create_from_problem(pb, precision=jko.Precision.BF16X3, tile=128)
+
+
+def _delta_problem():
+    pb = inputs.crowd_problem(64, gamma=2e-3, tau=0.02, n_steps=2, tol=1e-6, max_iter=300)
+    q = np.zeros(pb.N)
+    q[pb.N // 2 + 10] = 1.0
+    pb.q0 = q
+    pb.kappa = math.inf
+    return pb
+
+
+EDGE = {
+    "budget_one_pair": lambda: inputs.crowd_problem(96, gamma=4e-3, tau=0.02, n_steps=2,
+                                                    tol=1e-9, max_iter=1),
+    "converged_at_first_check": lambda: inputs.crowd_problem(96, gamma=4e-3, tau=0.02,
+                                                             n_steps=2, tol=10.0, max_iter=50),
+    "grid_8x8": lambda: inputs.crowd_problem(8, gamma=2e-2, tau=0.05, n_steps=3, tol=1e-6,
+                                             max_iter=300),
+    "point_mass": _delta_problem,
+}
+
+
+@pytest.mark.parametrize("prec", ["BF16", "TF32"])
+@pytest.mark.parametrize("case", list(EDGE))
+def test_loop_edge_cases_equal_per_pass(case, prec):
+    """Degenerate steps: the loop kernel's stop rule, pair count, status and
+    output equal the per-pass kernels' (64-wide tiles) bit for bit."""
+    pb = EDGE[case]()
+    t1, i1 = flow(pb, prec, pb.n_steps, loop=1)
+    t2, i2 = flow(pb, prec, pb.n_steps, loop=2, tile=64)
+    print(case, prec, [(i["iters"], int(i["status"])) for i in i1])
+    assert [(i["iters"], i["status"]) for i in i1] == [(i["iters"], i["status"]) for i in i2]
+    assert np.array_equal(t1, t2)
+    if case == "budget_one_pair":
+        assert all(i["iters"] == 1 for i in i1)
+    if case == "converged_at_first_check":
+        assert all(i["iters"] == 1 and i["status"] == 0 for i in i1)
+    assert np.all(np.isfinite(t1))
