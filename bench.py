@@ -264,7 +264,7 @@ def run_batched(args, jko, dev, barrier):
     out = {"workload": "256 flows (crowd even / porous odd), n in {64,128,256,512}, "
                        "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6",
            "flows_per_rank": len(pbs), "scaling": "weak" if ws == 1 else "strong"}
-    for form, loop in (("BF16X3", 0), ("BF16X3", 2), ("FP32", 0)):
+    for form, loop in (("BF16X3", 0), ("BF16X3", 3), ("BF16X3", 2), ("FP32", 0)):
         b = jko.jko_batch_create(pbs, precision=jko.Precision[form], loop=loop)
         p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
         jko.jko_batch_flow(b, p0s, 1, want_final=False)        # warm-up
@@ -276,7 +276,7 @@ def run_batched(args, jko, dev, barrier):
         barrier()
         secs, iters = aggregate_over_ranks(e0.elapsed_time(e1) / 1e3,
                                            sum(i["iters"] for row in table for i in row), ws, dev)
-        key = form if loop == 0 else f"{form}_per_pass_kernels"
+        key = form if loop == 0 else f"{form}_" + ("grouped" if loop == 3 else "per_pass_kernels")
         out[key] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
                     "seconds": secs, "pairs": iters, "kernels": jko.jko_batch_info(b)}
         jko.jko_batch_destroy(b)

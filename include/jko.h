@@ -94,7 +94,8 @@ typedef struct jko_params {
                        step, with the stop rule taken in the kernel, where the device
                        and the grid allow it, else one kernel per pass), 1 = persistent
                        kernel required (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one
-                       kernel per pass */
+                       kernel per pass, 3 = as 1, and in a batch the flow joins the
+                       grouped launch of its precision (jko_batch_create) */
   int tile;         /* tensor-core precisions: output tile width of the per-pass kernels,
                        64 or 128 (128: not JKO_BF16X3), or 0 = automatic.  With loop = 0
                        and tile = 0 on grids of 256^2 cells or more, jko_create times the
@@ -267,7 +268,12 @@ typedef struct jko_batch jko_batch;
  * branches are the flows, so small and large flows share the GPU; a flow that
  * has met its stopping rule (Sec. 3.4) turns its remaining kernels into
  * no-ops, and a flow on the persistent loop kernel is one launch per step in
- * its branch.  When every flow is a tensor-core flow on automatic kernels
+ * its branch.  Grouped launch: the flows with loop = 3 (or all loop-capable
+ * flows, when the autotuner picks it) that share a tensor-core precision run
+ * their steps in ONE cooperative launch of a persistent kernel that walks
+ * the tiles of all of them between grid barriers, each flow with its own
+ * stop rule; such a flow gives the same bits as the flow alone on the loop
+ * kernel.  When every flow is a tensor-core flow on automatic kernels
  * (loop = tile = 0), the batch times the candidate kernel configurations on
  * its own graph and keeps the fastest (jko_batch_info reports it).  Errors as jko_create, with the failing flow named in
  * jko_batch_last_error(NULL). */
@@ -276,9 +282,12 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
 
 /* How a batch runs its flows (diagnostics).  out[0] = the configuration its
  * autotuner chose (-1: not tuned; 0: each flow's own choice, 1: per-pass
- * kernels with 64-wide tiles, 2: 128-wide tiles, 3: the loop kernel), out[1]
- * = number of flows on the loop kernel, out[2] = 1 if the per-pass fallback
- * was taken because loop launches could not be captured.  out: 3 ints. */
+ * kernels with 64-wide tiles, 2: 128-wide tiles, 3: the loop kernel, 4: the
+ * loop-capable flows in grouped launches), out[1] = number of flows on a loop
+ * kernel launch of their own, out[2] = 1 if the per-pass fallback was taken
+ * because loop launches could not be captured, out[3] = number of flows in
+ * grouped launches, out[4] = number of grouped launches per chunk.  out: 5
+ * ints. */
 jko_status jko_batch_info(const jko_batch* b, int* out);
 
 /* n_steps steps of every flow (Eq. smooth-jko) from p0_dev[f] (device image of

@@ -306,8 +306,8 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (p->check_every < 0) return set_err(nullptr, JKO_ERR_INVALID_ARG, "check_every must be >= 0");
   if (p->precision < JKO_FP64 || p->precision > JKO_BF16X3)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
-  if (p->loop < 0 || p->loop > 2)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "loop must be 0 (automatic), 1 or 2");
+  if (p->loop < 0 || p->loop > 3)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "loop must be 0 (automatic), 1, 2 or 3");
   if (p->tile != 0 && p->tile != 64 && p->tile != 128)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "tile must be 0 (automatic), 64 or 128");
   if (p->absorb < 0 || p->absorb > 2)
@@ -624,7 +624,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     else if (rc != 0) s = set_err(h, JKO_ERR_CUDA, msg);
     if (s == JKO_OK) {
       const int ok = jko::tc_loop_supported(h->tc);
-      if (params->loop == 1 && !ok)
+      if ((params->loop == 1 || params->loop == 3) && !ok)
         s = set_err(h, JKO_ERR_UNSUPPORTED,
                     "the persistent loop kernel cannot run here (nx % 4 != 0 or no cooperative launch)");
       else if (params->tile != 0 && jko::tc_set_tile(h->tc, params->tile) != 0)
@@ -848,6 +848,9 @@ struct jko_batch {
   int last_iters = 0;
   bool per_pass = false;             // run every flow on per-pass kernels
   int tuned = -1;                    // candidate the batch autotuner chose
+  std::vector<jko::TcGroup*> groups; // grouped launches (one per precision)
+  std::vector<int> group_pairs;      // pairs one grouped launch may run
+  std::vector<char> in_group;        // flow f runs in a grouped launch
   std::string err;
 };
 
@@ -869,6 +872,7 @@ jko_status batch_err(jko_batch* b, jko_status st, const std::string& msg) {
 void free_batch(jko_batch* b) {
   if (!b) return;
   for (auto* h : b->h) free_handle(h);
+  for (auto* g : b->groups) jko::tc_group_destroy(g);
   if (b->g_pro) cudaGraphExecDestroy(b->g_pro);
   if (b->g_chunk) cudaGraphExecDestroy(b->g_chunk);
   if (b->g_fin) cudaGraphExecDestroy(b->g_fin);
@@ -918,13 +922,79 @@ cudaError_t flow_finalize(jko_handle* h, cudaStream_t s) {
   return h->fp64 ? flow_finalize_t<double>(h, s) : flow_finalize_t<float>(h, s);
 }
 
-template <class F, class G>
-jko_status capture_batch(jko_batch* b, F per_flow, G tail, cudaGraphExec_t* out);
+template <class H, class F, class G>
+jko_status capture_batch(jko_batch* b, H head, F per_flow, G tail, cudaGraphExec_t* out,
+                         bool skip_grouped = false);
+
+cudaError_t no_op(cudaStream_t) { return cudaSuccess; }
+
+void clear_groups(jko_batch* b) {
+  for (auto* g : b->groups) jko::tc_group_destroy(g);
+  b->groups.clear();
+  b->group_pairs.clear();
+  b->in_group.assign(b->n, 0);
+}
+
+// Puts the flows with sel[f] set that can run the loop kernel into grouped
+// launches, one per precision (and per 2048 flows); the others keep their own
+// branch.
+jko_status make_groups(jko_batch* b, const std::vector<char>& sel) {
+  clear_groups(b);
+  for (int prec : {JKO_TF32, JKO_BF16, JKO_BF16X3}) {
+    std::vector<jko::TcPlan*> plans;
+    std::vector<int> ids;
+    for (int f = 0; f < b->n; ++f) {
+      jko_handle* h = b->h[f];
+      if (sel[f] && h->tc && h->prec == prec && jko::tc_loop_supported(h->tc)) {
+        plans.push_back(h->tc);
+        ids.push_back(f);
+      }
+    }
+    for (size_t i0 = 0; i0 < plans.size(); i0 += 2048) {
+      const int n = (int)std::min<size_t>(2048, plans.size() - i0);
+      jko::TcGroup* g = nullptr;
+      std::string msg;
+      const int rc = jko::tc_group_create(plans.data() + i0, n, &g, &msg);
+      if (rc == 2) return batch_err(b, JKO_ERR_CUDA, msg);
+      if (rc != 0) continue;
+      int pairs = 1;
+      for (int k = 0; k < n; ++k) {
+        jko_handle* h = b->h[ids[i0 + k]];
+        apply_cand(h, CAND_LOOP);
+        h->chunk_iters = h->prm.max_iter + 1;
+        pairs = std::max(pairs, h->prm.max_iter + 1);
+        b->in_group[ids[i0 + k]] = 1;
+      }
+      b->groups.push_back(g);
+      b->group_pairs.push_back(pairs);
+    }
+  }
+  return JKO_OK;
+}
+
+// Launches every grouped launch of the batch for up to `pairs` pairs (0: the
+// flows' whole budgets) on stream st.
+cudaError_t launch_groups(jko_batch* b, cudaStream_t st, int pairs = 0) {
+  for (size_t i = 0; i < b->groups.size(); ++i) {
+    cudaError_t e = jko::tc_group_enqueue(b->groups[i], pairs > 0 ? pairs : b->group_pairs[i], st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t begin_groups(jko_batch* b, cudaStream_t st) {
+  for (auto* g : b->groups) {
+    cudaError_t e = jko::tc_group_begin_step(g, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 // Batch autotuner: the configuration of every flow (loop kernel or per-pass
 // kernels with 64- or 128-wide tiles) that runs the whole batch fastest.
 // Candidates: each flow's own choice, all per-pass 64, all per-pass 128 (64
-// where the precision has no 128), all on the loop kernel where it can run.
+// where the precision has no 128), all on the loop kernel where it can run,
+// and those flows in grouped launches (one cooperative launch per precision).
 jko_status tune_batch(jko_batch* b) {
   const int n = b->n;
   std::vector<int> own(n);
@@ -942,15 +1012,19 @@ jko_status tune_batch(jko_batch* b) {
   BCK(b, cudaEventCreate(&e1));
   int best = 0;
   float best_ms = -1.f;
-  for (int c = 0; c < 4; ++c) {
+  const std::vector<char> all(n, 1);
+  for (int c = 0; c < 5; ++c) {
     bool ok = true;
-    for (int f = 0; f < n && ok; ++f) ok = apply_cand(b->h[f], cand_of(c, f));
+    clear_groups(b);
+    for (int f = 0; f < n && ok; ++f) ok = apply_cand(b->h[f], cand_of(c == 4 ? 3 : c, f));
+    if (ok && c == 4) ok = make_groups(b, all) == JKO_OK && !b->groups.empty();
     for (int f = 0; f < n && ok; ++f) ok = prime_for_timing(b->h[f], b->stream) == cudaSuccess;
     if (!ok || cudaStreamSynchronize(b->stream) != cudaSuccess) { cudaGetLastError(); continue; }
     cudaGraphExec_t ge = nullptr;
     jko_status s = capture_batch(
-        b, [](jko_handle* h, cudaStream_t st) { return flow_chunk(h, kTunePairs, false, st, kTunePairs); },
-        [](cudaStream_t) { return cudaSuccess; }, &ge);
+        b, [b](cudaStream_t st) { return launch_groups(b, st, kTunePairs); },
+        [](jko_handle* h, cudaStream_t st) { return flow_chunk(h, kTunePairs, false, st, kTunePairs); },
+        no_op, &ge, true);
     if (s != JKO_OK) { cudaGetLastError(); continue; }
     const float ms = time_graph(ge, b->stream, e0, e1);
     cudaGraphExecDestroy(ge);
@@ -958,26 +1032,35 @@ jko_status tune_batch(jko_batch* b) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  clear_groups(b);
   for (int f = 0; f < n; ++f) {
-    apply_cand(b->h[f], cand_of(best, f));
+    apply_cand(b->h[f], cand_of(best == 4 ? 3 : best, f));
     BCK(b, cudaMemcpy(b->h[f]->ctrl, b->h[f]->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  }
+  if (best == 4) {
+    jko_status s = make_groups(b, all);
+    if (s != JKO_OK) return s;
   }
   b->tuned = best;
   b->err.clear();
   return JKO_OK;
 }
 
-// Captures one graph whose branches run `per_flow` for every flow, joined on
-// the root stream, followed by `tail` on the root.
-template <class F, class G>
-jko_status capture_batch(jko_batch* b, F per_flow, G tail, cudaGraphExec_t* out) {
+// Captures one graph: `head` on the root stream, then branches running
+// `per_flow` for every flow (but the grouped ones with skip_grouped), joined on
+// the root, then `tail` on the root.
+template <class H, class F, class G>
+jko_status capture_batch(jko_batch* b, H head, F per_flow, G tail, cudaGraphExec_t* out,
+                         bool skip_grouped) {
   cudaStream_t root = b->cap[0];
   const int nw = (int)b->cap.size() - 1;
   cudaGraph_t g = nullptr;
   BCK(b, cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaEventRecord(b->ev[0], root);
+  cudaError_t e = head(root);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], root);
   std::vector<char> used(nw, 0);
   for (int f = 0; f < b->n && e == cudaSuccess; ++f) {
+    if (skip_grouped && b->in_group[f]) continue;
     const int k = f % nw;
     cudaStream_t s = b->cap[1 + k];
     if (!used[k]) { e = cudaStreamWaitEvent(s, b->ev[0], 0); used[k] = 1; }
@@ -1080,22 +1163,33 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
   bool tune = true;
   for (int f = 0; f < n_flows; ++f)
     tune = tune && params[f].loop == 0 && params[f].tile == 0 && b->h[f]->tc;
+  b->in_group.assign(n_flows, 0);
   if (tune) {
     jko_status st = tune_batch(b);
     if (st != JKO_OK) return fail(st);
+  } else {
+    // flows asking for the grouped kernel (loop = 3)
+    std::vector<char> sel(n_flows, 0);
+    bool any = false;
+    for (int f = 0; f < n_flows; ++f) any |= (sel[f] = params[f].loop == 3 && b->h[f]->tc) != 0;
+    if (any) {
+      jko_status st = make_groups(b, sel);
+      if (st != JKO_OK) return fail(st);
+    }
   }
   for (auto* h : b->h)
     if (h->tc) h->chunk_iters = h->use_loop ? h->prm.max_iter + 1 : C;
   jko_status s = capture_batch(
-      b, [](jko_handle* h, cudaStream_t st) { return flow_prologue(h, st); },
-      [](cudaStream_t) { return cudaSuccess; }, &b->g_pro);
+      b, no_op, [](jko_handle* h, cudaStream_t st) { return flow_prologue(h, st); },
+      [b](cudaStream_t root) { return begin_groups(b, root); }, &b->g_pro);
   if (s != JKO_OK) return fail(s);
   auto capture_chunks = [&]() {
     const bool pp = b->per_pass;
     return capture_batch(
-        b, [C, pp](jko_handle* h, cudaStream_t st) { return flow_chunk(h, C, pp, st); },
+        b, [b, pp](cudaStream_t root) { return pp ? cudaSuccess : launch_groups(b, root); },
+        [C, pp](jko_handle* h, cudaStream_t st) { return flow_chunk(h, C, pp, st); },
         [b](cudaStream_t root) { return jko::launch_gather_done(b->ctrl_ptrs, b->done_dev, b->n, root); },
-        &b->g_chunk);
+        &b->g_chunk, !pp);
   };
   s = capture_chunks();
   if (s != JKO_OK) {
@@ -1110,7 +1204,7 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
   for (auto* h : b->h) all_loop = all_loop && h->use_loop;
   if (all_loop) b->C = b->max_iter + 1;
   s = capture_batch(
-      b, [](jko_handle* h, cudaStream_t st) { return flow_finalize(h, st); },
+      b, no_op, [](jko_handle* h, cudaStream_t st) { return flow_finalize(h, st); },
       [b](cudaStream_t root) { return jko::launch_gather_ctrl(b->ctrl_ptrs, b->ctrl_all, b->n, root); },
       &b->g_fin);
   if (s != JKO_OK) return fail(s);
@@ -1120,11 +1214,17 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
 
 jko_status jko_batch_info(const jko_batch* b, int* out) {
   if (!b || !out) return batch_err(nullptr, JKO_ERR_INVALID_ARG, "NULL batch or out");
-  int nl = 0;
-  for (auto* h : b->h) nl += (h->use_loop && !b->per_pass) ? 1 : 0;
+  int nl = 0, ng = 0;
+  for (int f = 0; f < b->n; ++f) {
+    const bool grouped = !b->per_pass && !b->in_group.empty() && b->in_group[f];
+    nl += (b->h[f]->use_loop && !b->per_pass && !grouped) ? 1 : 0;
+    ng += grouped ? 1 : 0;
+  }
   out[0] = b->tuned;
   out[1] = nl;
   out[2] = b->per_pass ? 1 : 0;
+  out[3] = ng;
+  out[4] = b->per_pass ? 0 : (int)b->groups.size();
   return JKO_OK;
 }
 

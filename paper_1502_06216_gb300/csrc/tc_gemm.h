@@ -63,5 +63,16 @@ int tc_loop_resident(const TcPlan* plan);
 cudaError_t tc_enqueue_loop(TcPlan* plan, int pairs, cudaStream_t st);
 // Executed tensor-core flops of `pairs` pairs of the loop kernel.
 double tc_loop_flops(const TcPlan* plan, int pairs);
+// Grouped persistent kernel (tc_loop.cu): one cooperative launch runs the
+// scaling loop of several flows of one precision, each with its own stop rule
+// in its own Ctrl.  Create: 0 = ok, 1 = not groupable (message set), 2 = CUDA
+// error.  begin_step resets the launch's grid-barrier words (once per step).
+struct TcGroup;
+int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg);
+cudaError_t tc_group_begin_step(TcGroup* g, cudaStream_t st);
+cudaError_t tc_group_enqueue(TcGroup* g, int pairs, cudaStream_t st);
+int tc_group_flows(const TcGroup* g);
+double tc_group_flops(const TcGroup* g, int pairs);
+void tc_group_destroy(TcGroup* g);
 
 }  // namespace jko

@@ -602,6 +602,490 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   }
 }
 
+// ------------------------------------------------------------ grouped batch
+// One cooperative launch runs the scaling loop of every flow of a batch that
+// shares the operand precision.  The tiles of all flows form one list per
+// pass, walked by the CTAs between the same grid barriers as above; each tile
+// names its flow, whose tensor maps and descriptor live in device memory.
+// Every flow keeps its own stop rule: during pass 2 the flow's designated CTA
+// (f mod G) adds its residual partials in the same order as the loop kernel,
+// records the decision in the flow's Ctrl and sets the flow's bit in a stop
+// word; after the barrier before the prox pass every CTA reads the words, so
+// all skip the flow's tiles from that pass on, exactly where the loop kernel
+// alone would stop.  The per-tile arithmetic is that of tc_loop_kernel, so a
+// flow of a grouped launch gives the bits of the same flow on the loop kernel.
+// NaN/Inf in a flow is recorded in its Ctrl and stops that flow at its next
+// decision; a wait that gives up stops the whole launch.
+constexpr int MAXF = 2048;                   // flows per grouped launch
+
+struct FlowDesc {
+  int M[4], N[4];           // output geometry of each pass
+  Ctrl* ctrl;               // it, done, max_iter, tol, res_last, nonfinite of the flow
+  double* part;             // residual partial of each b-update tile
+  int nparts;
+  int ek;
+  ProxArgs<float> P;
+};
+
+// Tile g of pass p: items[p][2g] = {flow, m0, n0, 2 t + e} (t: index of the
+// tile in the flow's pass, e: 1 if the tile loads epilogue tiles),
+// items[p][2g + 1] = the factor band of its 128-row block.
+struct BatchArgs {
+  const FlowDesc* flows;
+  const LoopMaps* maps;     // tensor maps of each flow
+  const int4* items[4];
+  int ntiles[4];
+  Ctrl* bctrl;              // grid-barrier words of the launch
+  unsigned* gstop;          // bit f: flow f stopped by a decision of this launch
+  int F;
+  int pairs;
+};
+
+__device__ __forceinline__ bool flow_stopped(const unsigned* mask, int f) {
+  return (*(const volatile unsigned*)&mask[f >> 5] >> (f & 31)) & 1u;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant__ BatchArgs args) {
+  using T = typename OpT<MODE>::T;
+  constexpr int KE = OpT<MODE>::kElems;
+  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
+  constexpr uint32_t A_BYTES = BM * KB_BYTES;
+  constexpr uint32_t B_BYTES = LBN * KB_BYTES;
+  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  constexpr int STAGES = loop_stages(MODE, false);
+  static_assert(STAGE_BYTES == loop_stage_bytes(MODE, false), "stage size");
+  static_assert(STAGES >= 2, "at least two stages");
+  constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
+  constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
+  constexpr uint32_t TMEM_COLS = LBN;
+  constexpr uint32_t IDESC = make_idesc<MODE>(BM, LBN);
+  constexpr int CB = LBN * (int)sizeof(T) / 128;
+  constexpr uint32_t OUT_BLOCK = BM * 128;
+  constexpr uint32_t EPI_B_LOAD = F32_TILE + (uint32_t)NSPLIT * CB * OUT_BLOCK;
+  constexpr uint32_t EPI_A_LOAD = F32_TILE;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* stages = smem;
+  unsigned char* st_hi = stages + STAGES * STAGE_BYTES;
+  unsigned char* st_lo = st_hi + CB * OUT_BLOCK;
+  unsigned char* epi_f = st_hi + STG_BYTES;
+  unsigned char* epi_g = epi_f + F32_TILE;
+  uint64_t* full_bar = (uint64_t*)(epi_f + loop_epi_bytes(false));
+  uint64_t* empty_bar = full_bar + STAGES;
+  uint64_t* accum_bar = empty_bar + STAGES;
+  uint64_t* tmem_free_bar = accum_bar + 1;
+  uint64_t* epi_full_bar = accum_bar + 2;
+  uint64_t* epi_free_bar = accum_bar + 3;
+  uint32_t* tmem_slot = (uint32_t*)(accum_bar + 5);
+
+  __shared__ int s_go, s_stop, s_fault, s_gfault;
+  __shared__ unsigned s_base;
+  __shared__ float s_red[NEPI / 32];
+  __shared__ unsigned s_fstop[MAXF / 32];   // flows whose tiles are skipped
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  const int F = args.F;
+  const int nwords = (F + 31) >> 5;
+  Ctrl* bctrl = args.bctrl;
+  const int nq = 4 * args.pairs;
+
+  for (int i = threadIdx.x; i < MAXF / 32; i += NTL) s_fstop[i] = 0u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(accum_bar, 1);
+    mbar_init(tmem_free_bar, NEPI / 32);
+    mbar_init(epi_full_bar, 1);
+    mbar_init(epi_free_bar, 1);
+    fence_mbar_init();
+    s_base = bctrl->bar_base;
+    s_go = 0;
+    s_fault = 0;
+    s_gfault = 0;
+  }
+  if (warp == WARP_MMA) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  // flows that stopped in an earlier launch of the step (their Ctrl changes
+  // only in pass 2, after two grid barriers, so every CTA reads the same)
+  for (int f = threadIdx.x; f < F; f += NTL) {
+    Ctrl* c = args.flows[f].ctrl;
+    const int done = *(volatile int*)&c->done;
+    const int nf = *(volatile int*)&c->nonfinite;
+    if (done != RUNNING || nf) atomicOr(&s_fstop[f >> 5], 1u << (f & 31));
+    if (done == RUNNING && nf && f % G == (int)blockIdx.x) c->done = NONFINITE;
+  }
+  // the stop words of this launch start empty (first read after barrier 3)
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nwords; i += NTL) args.gstop[i] = 0u;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) {
+    bool all = true;
+    for (int w = 0; w < nwords && all; ++w) {
+      const int nb = F - 32 * w;
+      all = s_fstop[w] == (nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u));
+    }
+    s_stop = all ? 1 : 0;
+  }
+  __syncthreads();
+  const uint32_t tmem_base = *tmem_slot;
+  const bool stopped_at_start = s_stop != 0;
+  int pairs_done = 0;
+  unsigned nbar = 0;
+
+  if (stopped_at_start) {
+    // every flow has already stopped
+  } else if (warp == WARP_PROD) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t kc = 0, ec = 0;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const int p = q & 3;
+        if (q > 0) {
+          ok = wait_go(&s_go, q);
+          if (!ok || s_stop) break;
+          fence_proxy_async_global();
+        }
+        for (int g = blockIdx.x; g < args.ntiles[p] && ok; g += G) {
+          const int4 it = __ldg(args.items[p] + 2 * g);
+          if (flow_stopped(s_fstop, it.x)) continue;
+          const int4 kb = __ldg(args.items[p] + 2 * g + 1);
+          const LoopMaps* mp = args.maps + it.x;
+          const int m0 = it.y, n0 = it.z;
+          if (it.w & 1) {
+            if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
+            if (!ok) break;
+            if (p == 1) {
+              mbar_arrive_expect_tx(epi_full_bar, EPI_B_LOAD);
+#pragma unroll
+              for (int cb = 0; cb < LBN / 32; ++cb)
+                tma_load_2d(epi_f + cb * (BM * 128), &mp->Q, epi_full_bar, n0 + cb * 32, m0);
+              constexpr int KEO = 128 / (int)sizeof(T);
+#pragma unroll
+              for (int cb = 0; cb < CB; ++cb) {
+                tma_load_2d(epi_g + cb * OUT_BLOCK, &mp->O[1][0], epi_full_bar, n0 + cb * KEO, m0);
+                if constexpr (NSPLIT == 2)
+                  tma_load_2d(epi_g + (CB + cb) * OUT_BLOCK, &mp->O[1][1], epi_full_bar,
+                              n0 + cb * KEO, m0);
+              }
+            } else {
+              mbar_arrive_expect_tx(epi_full_bar, EPI_A_LOAD);
+#pragma unroll
+              for (int cb = 0; cb < LBN / 32; ++cb)
+                tma_load_2d(epi_f + cb * (BM * 128), &mp->E, epi_full_bar, n0 + cb * 32, m0);
+            }
+            ++ec;
+          }
+          for (int i = 0; i < kb.y && ok; ++i) {
+            const uint32_t k = kc + i;
+            const int s = (int)(k % STAGES);
+            if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
+            if (!ok) break;
+            unsigned char* st = stages + s * STAGE_BYTES;
+            const int kx = kb.x + i * KE;
+            mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+            tma_load_2d(st, &mp->K[p][0], &full_bar[s], kx, m0);
+            tma_load_2d(st + A_BYTES, &mp->B[p][0], &full_bar[s], kx, n0);
+            if constexpr (NSPLIT == 2) {
+              tma_load_2d(st + A_BYTES + B_BYTES, &mp->K[p][1], &full_bar[s], kx, m0);
+              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mp->B[p][1], &full_bar[s], kx, n0);
+            }
+          }
+          kc += kb.y;
+        }
+      }
+      if (!ok) atomicOr(&s_fault, 1);
+    }
+  } else if (warp == WARP_MMA) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t kc = 0, tc = 0;
+      bool ok = true;
+      for (int q = 0; q < nq && ok; ++q) {
+        const int p = q & 3;
+        if (q > 0) {
+          ok = wait_go(&s_go, q);
+          if (!ok || s_stop) break;
+        }
+        for (int g = blockIdx.x; g < args.ntiles[p] && ok; g += G) {
+          if (flow_stopped(s_fstop, __ldg(&args.items[p][2 * g].x))) continue;
+          const int nkb = __ldg(&args.items[p][2 * g + 1].y);
+          if (tc > 0) ok = mbar_wait(tmem_free_bar, (tc - 1) & 1);
+          if (!ok) break;
+          tc_fence_after();
+          for (int i = 0; i < nkb && ok; ++i) {
+            const uint32_t k = kc + i;
+            const int s = (int)(k % STAGES);
+            ok = mbar_wait(&full_bar[s], (k / STAGES) & 1);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+            const uint64_t a_hi = sdesc_sw128(sa);
+            const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < KB_BYTES / 32; ++kk) {
+              const uint64_t adv = (uint64_t)(kk * 2);
+              const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+              umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
+              if constexpr (NSPLIT == 2) {
+                const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
+                const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
+                umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
+                umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
+              }
+            }
+            umma_commit(&empty_bar[s]);
+          }
+          umma_commit(accum_bar);
+          kc += nkb;
+          ++tc;
+        }
+      }
+      if (!ok) atomicOr(&s_fault, 1);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int grp = warp >> 2;
+    const int rl = quad * 32 + lane;
+    uint32_t tc = 0, ec = 0;
+    bool free_pending = false;
+    unsigned flag_prev = 0;      // flag slot of the previous barrier (warp 0)
+    for (int q = 0; q < nq; ++q) {
+      const int p = q & 3;
+      const int pair = q >> 2;
+      if (q > 0) {
+        // ---- grid barrier ----
+        if (threadIdx.x == 0) {
+          bulk_wait_all();
+          fence_proxy_async_global();
+          if (free_pending) mbar_arrive(epi_free_bar);
+          if (s_fault & 3) atomicOr(&bctrl->nonfinite, 2);
+        }
+        free_pending = false;
+        named_bar_sync(EPI_BAR, NEPI);
+        if (warp == 0) {
+          int stop = 0;
+          unsigned b = 0;
+          if (lane == 0) {
+            b = s_base + (++nbar);
+            const bool ok = grid_barrier(bctrl, (unsigned)G, b, (s_fault & 3) != 0);
+            stop = flag_prev != 0 || !ok;
+            if (!ok) {
+              atomicOr(&s_fault, 1);
+              atomicOr(&bctrl->nonfinite, 2);
+            }
+            if (stop) s_gfault = 1;
+          }
+          stop = __shfl_sync(0xffffffffu, stop, 0);
+          __syncwarp();
+          if (!stop && p == 3) {
+            // the decisions of pass 2 take effect now, in every CTA alike
+            bool all = true;
+            for (int w = lane; w < nwords; w += 32) {
+              const unsigned m = s_fstop[w] | __ldcg(args.gstop + w);
+              s_fstop[w] = m;
+              const int nb = F - 32 * w;
+              all = all && m == (nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u));
+            }
+            stop = __all_sync(0xffffffffu, all) ? 1 : 0;
+          }
+          if (lane == 0) {
+            s_stop = stop;
+            __threadfence_block();
+            *(volatile int*)&s_go = q;
+            flag_prev = *(volatile unsigned*)&bctrl->bar_flag[b % 3];
+            if (blockIdx.x == 0) bctrl->bar_flag[(b + 2) % 3] = 0u;
+          }
+        }
+        named_bar_sync(EPI_BAR, NEPI);
+        if (p == 0) pairs_done = pair;
+        if (s_stop) break;
+        if (p == 2) {
+          // stop rule of this CTA's flows (f = blockIdx.x + G k, warp by warp),
+          // the partials added in the loop kernel's order
+          for (int f = (int)blockIdx.x + warp * G; f < F; f += (NEPI / 32) * G) {
+            if (flow_stopped(s_fstop, f)) continue;
+            const FlowDesc& FD = args.flows[f];
+            const int np = FD.nparts;
+            double v = 0.0;
+            for (int i = lane; i < np; i += 32) v += __ldcg(FD.part + i);
+            v = warp_sum(v);
+            Ctrl* c = FD.ctrl;
+            const int it = *(const volatile int*)&c->it + pair;
+            int d = RUNNING;
+            if (*(const volatile int*)&c->nonfinite & 1) d = NONFINITE;
+            else if (it > 0 && !isfinite(v)) d = NONFINITE;
+            else if (it > 0 && v <= c->tol) d = CONVERGED;
+            else if (it >= c->max_iter) d = MAX_ITER;
+            if (lane == 0) {
+              if (it > 0) c->res_last = v;
+              if (d != RUNNING) {
+                c->done = d;
+                c->it = it;
+                atomicOr(args.gstop + (f >> 5), 1u << (f & 31));
+              }
+              __threadfence();
+            }
+          }
+        }
+      }
+      bool first = true;
+      for (int g = blockIdx.x; g < args.ntiles[p]; g += G) {
+        const int4 itm = __ldg(args.items[p] + 2 * g);
+        if (flow_stopped(s_fstop, itm.x)) continue;
+        const FlowDesc& FD = args.flows[itm.x];
+        const LoopMaps* mp = args.maps + itm.x;
+        const int t = itm.w >> 1;
+        const bool epi_pass = (itm.w & 1) != 0;
+        const int m0 = itm.y, n0 = itm.z;
+        const int PM = FD.M[p], PN = FD.N[p];
+        if (!first) {
+          if (threadIdx.x == 0) {
+            bulk_wait_read_all();
+            if (free_pending) mbar_arrive(epi_free_bar);
+          }
+          free_pending = false;
+          named_bar_sync(EPI_BAR, NEPI);
+        }
+        bool have = mbar_wait(accum_bar, tc & 1);
+        if (have && epi_pass) have = mbar_wait(epi_full_bar, ec & 1);
+        if (!have && lane == 0) atomicOr(&s_fault, 1);
+        __syncwarp();
+        tc_fence_after();
+        uint32_t racc[16];
+        tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(grp * 16), racc);
+        tmem_wait_ld();
+        reg_fence16(racc);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tmem_free_bar);
+        const int c = grp;
+        const int m = m0 + rl;
+        const int nb = n0 + c * 16;
+        int cnt = PN - nb;
+        cnt = (m >= PM || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
+        float v[16], o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[j]);
+        float res_f = 0.0f;
+        int bad = 0;
+        if (p == 0 || p == 2) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) o[j] = v[j];
+        } else if (p == 1) {
+          const bool have_prev = (*(const volatile int*)&FD.ctrl->it + pair) > 0;
+          float qv[16], bo[16];
+          smem_ld_f32x16(epi_f, rl, c, qv);
+          if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (j < cnt) {
+              if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
+              o[j] = b_update<float>(qv[j], v[j]);
+              bad |= !isfinite(o[j]);
+            } else {
+              o[j] = 0.0f;
+            }
+          }
+        } else {
+          const ProxArgs<float> P = FD.P;
+          const int ek = FD.ek;
+          const int irow = m * PN + nb;
+          float ev[16], pv[16];
+          if (ek == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
+          if (ek == EK_CROWD && P.mask == nullptr && P.kappa == nullptr) {
+            const bool hk = P.has_kappa != 0;
+            const float kap = P.kappa_s;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float a = ev[j];
+              if (hk && a * v[j] > kap) a = ratio_div<float>(kap, v[j]);
+              if (j >= cnt) a = 0.0f;
+              bad |= !isfinite(a);
+              o[j] = a;
+              pv[j] = a * v[j];
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float a = 0.0f;
+              if (j < cnt) {
+                a = ek == EK_CROWD    ? prox_ratio_e<float, EK_CROWD>(P, irow + j, v[j], ev[j])
+                    : ek == EK_ENTROPY ? prox_ratio_e<float, EK_ENTROPY>(P, irow + j, v[j], 0.0f)
+                                       : prox_ratio_e<float, EK_POWER>(P, irow + j, v[j], 0.0f);
+                bad |= !isfinite(a);
+              }
+              o[j] = a;
+              pv[j] = j < cnt ? a * v[j] : 0.0f;
+            }
+          }
+          smem_st_f32x16(epi_g, rl, c, pv);
+        }
+        bad = warp_or(bad);
+        if (lane == 0 && bad) atomicOr(&FD.ctrl->nonfinite, 1);
+        stage16<MODE>(st_hi, st_lo, rl, c, o);
+        fence_proxy_async_smem();
+        double res = 0.0;
+        if (p == 1)
+          res = (double)tile_sum16(res_f, s_red, [] { named_bar_sync(EPI_BAR, NEPI); });
+        else
+          named_bar_sync(EPI_BAR, NEPI);
+        if (threadIdx.x == 0) {
+          if (p == 1) FD.part[t] = res;
+          constexpr int KEo = 128 / (int)sizeof(T);
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            tma_store_2d(&mp->O[p][0], st_hi + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+            if constexpr (NSPLIT == 2) tma_store_2d(&mp->O[p][1], st_lo + cb * OUT_BLOCK, n0 + cb * KEo, m0);
+          }
+          if (p == 3) {
+#pragma unroll
+            for (int cb = 0; cb < LBN / 32; ++cb)
+              tma_store_2d(&mp->P, epi_g + cb * (BM * 128), n0 + cb * 32, m0);
+          }
+          bulk_commit();
+        }
+        free_pending = epi_pass;
+        first = false;
+        ++tc;
+        if (epi_pass) ++ec;
+      }
+      if (p == 3 && q == nq - 1) pairs_done = pair + 1;
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == WARP_MMA) tmem_dealloc(tmem_base, TMEM_COLS);
+  if (threadIdx.x == 0 && !stopped_at_start) {
+    if (s_fault & 3) atomicOr(&bctrl->nonfinite, 2);
+    // the designated CTA records the pairs of its flows still running
+    for (int f = blockIdx.x; f < F; f += G) {
+      Ctrl* c = args.flows[f].ctrl;
+      if (*(volatile int*)&c->done != RUNNING) continue;
+      c->it = *(volatile int*)&c->it + pairs_done;
+      if (s_gfault) {
+        atomicOr(&c->nonfinite, 2);
+        c->done = NONFINITE;
+      }
+    }
+    if (blockIdx.x == 0) bctrl->bar_base = s_base + nbar;
+  }
+}
+
 template <int MODE, int EK, bool RES>
 cudaError_t set_loop_attr() {
   return cudaFuncSetAttribute(tc_loop_kernel<MODE, EK, RES>,
@@ -726,30 +1210,35 @@ int tc_loop_resident(const TcPlan* P) { return P && P->loop_ok && P->loop_res; }
 
 double tc_loop_flops(const TcPlan* P, int pairs) { return P->loop_flops_pair * pairs; }
 
-cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
-  if (!P->loop_ok || pairs < 1) return cudaErrorInvalidValue;
-  const TcConfig& c = P->cfg;
-  LoopMaps maps;
-  LoopArgs args{};
+// Tensor maps of the four passes of plan P with 64-wide tiles.
+static void loop_maps_of(const TcPlan* P, LoopMaps* maps) {
   for (int w = 0; w < 4; ++w) {
     const bool over_x = (w & 1) == 0;
     const int half = w >> 1;
     const int side = P->absorbed ? half : 0;
-    args.pass[w] = loop_pass(P, w);
     for (int sp = 0; sp < 2; ++sp) {
-      maps.K[w][sp] = P->mK[over_x ? 0 : 1][side][sp];
+      maps->K[w][sp] = P->mK[over_x ? 0 : 1][side][sp];
       if (over_x) {
-        maps.B[w][sp] = half == 0 ? P->lA[sp] : P->lB[sp];
-        maps.O[w][sp] = P->sT[sp];
+        maps->B[w][sp] = half == 0 ? P->lA[sp] : P->lB[sp];
+        maps->O[w][sp] = P->sT[sp];
       } else {
-        maps.B[w][sp] = P->lT[sp];
-        maps.O[w][sp] = half == 0 ? P->sB[sp] : P->sA[sp];
+        maps->B[w][sp] = P->lT[sp];
+        maps->O[w][sp] = half == 0 ? P->sB[sp] : P->sA[sp];
       }
     }
   }
-  maps.Q = P->fQ;
-  maps.E = P->fE;
-  maps.P = P->fP;
+  maps->Q = P->fQ;
+  maps->E = P->fE;
+  maps->P = P->fP;
+}
+
+cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
+  if (!P->loop_ok || pairs < 1) return cudaErrorInvalidValue;
+  const TcConfig& c = P->cfg;
+  LoopMaps maps;
+  loop_maps_of(P, &maps);
+  LoopArgs args{};
+  for (int w = 0; w < 4; ++w) args.pass[w] = loop_pass(P, w);
   args.ctrl = c.ctrl;
   args.P = c.prox;
   args.part = c.part;
@@ -763,5 +1252,177 @@ cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
                          : dispatch_loop<MODE_BF16, false>(c.ek, maps, args, P->loop_grid, st);
   }
 }
+
+// ------------------------------------------------------------ grouped batch (host)
+namespace {
+
+template <int MODE>
+cudaError_t set_batch_attr() {
+  return cudaFuncSetAttribute(tc_batch_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)loop_smem_bytes(MODE, false));
+}
+
+template <int MODE>
+int batch_blocks_per_sm() {
+  int nb = 0;
+  if (set_batch_attr<MODE>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_batch_kernel<MODE>, NTL,
+                                                    loop_smem_bytes(MODE, false)) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <int MODE>
+cudaError_t launch_batch(const BatchArgs& args, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NTL);
+  cfg.dynamicSmemBytes = loop_smem_bytes(MODE, false);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc_batch_kernel<MODE>, args);
+}
+
+}  // namespace
+
+struct TcGroup {
+  int mode = 0, F = 0, grid = 0;
+  FlowDesc* flows = nullptr;
+  LoopMaps* maps = nullptr;
+  int4* items[4] = {nullptr, nullptr, nullptr, nullptr};
+  int ntiles[4] = {0, 0, 0, 0};
+  Ctrl* bctrl = nullptr;
+  unsigned* gstop = nullptr;
+  double flops_pair = 0.0;
+};
+
+void tc_group_destroy(TcGroup* g) {
+  if (!g) return;
+  cudaFree(g->flows);
+  cudaFree(g->maps);
+  for (auto* it : g->items) cudaFree(it);
+  cudaFree(g->bctrl);
+  cudaFree(g->gstop);
+  delete g;
+}
+
+int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg) {
+  *out = nullptr;
+  if (n < 1 || n > MAXF) {
+    *msg = "a grouped launch takes 1 to 2048 flows";
+    return 1;
+  }
+  const int mode = plans[0]->mode;
+  for (int f = 0; f < n; ++f)
+    if (!plans[f]->loop_ok || plans[f]->mode != mode) {
+      *msg = "every flow of a group needs the loop kernel and the group's precision";
+      return 1;
+    }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nb = mode == MODE_TF32 ? batch_blocks_per_sm<MODE_TF32>()
+                 : mode == MODE_BF16X3 ? batch_blocks_per_sm<MODE_BF16X3>()
+                                       : batch_blocks_per_sm<MODE_BF16>();
+  cudaGetLastError();
+  if (nb < 1 || sms < 1) {
+    *msg = "the grouped kernel does not fit an SM";
+    return 1;
+  }
+  TcGroup* g = new TcGroup();
+  g->mode = mode;
+  g->F = n;
+  std::vector<FlowDesc> fd(n);
+  std::vector<LoopMaps> mp(n);
+  std::vector<int4> items[4];
+  for (int f = 0; f < n; ++f) {
+    TcPlan* P = plans[f];
+    const TcConfig& c = P->cfg;
+    loop_maps_of(P, &mp[f]);
+    FlowDesc& d = fd[f];
+    for (int w = 0; w < 4; ++w) {
+      const LoopPass L = loop_pass(P, w);
+      d.M[w] = L.M;
+      d.N[w] = L.N;
+      std::vector<int4> tab((L.M + BM - 1) / BM);
+      if (cudaMemcpy(tab.data(), L.kbt, tab.size() * sizeof(int4), cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+        tc_group_destroy(g);
+        *msg = "reading the band tables";
+        return 2;
+      }
+      const int epi = (w == 1 || (w == 3 && c.ek == EK_CROWD)) ? 1 : 0;
+      for (int t = 0; t < L.ntiles; ++t) {
+        const int mt = t / L.tiles_n;
+        items[w].push_back(make_int4(f, mt * BM, (t - mt * L.tiles_n) * LBN, 2 * t + epi));
+        items[w].push_back(tab[mt]);
+      }
+    }
+    d.ctrl = c.ctrl;
+    d.part = c.part;
+    d.nparts = loop_pass(P, 1).ntiles;
+    d.ek = c.ek;
+    d.P = c.prox;
+    g->flops_pair += P->loop_flops_pair;
+  }
+  int maxt = 0;
+  for (int w = 0; w < 4; ++w) {
+    g->ntiles[w] = (int)items[w].size() / 2;
+    maxt = std::max(maxt, g->ntiles[w]);
+  }
+  g->grid = std::min(maxt, sms * nb);
+  cudaError_t e = cudaMalloc((void**)&g->flows, sizeof(FlowDesc) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->maps, sizeof(LoopMaps) * n);
+  for (int w = 0; w < 4 && e == cudaSuccess; ++w)
+    e = cudaMalloc((void**)&g->items[w], sizeof(int4) * items[w].size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->bctrl, sizeof(Ctrl));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->gstop, sizeof(unsigned) * (MAXF / 32));
+  if (e == cudaSuccess) e = cudaMemcpy(g->flows, fd.data(), sizeof(FlowDesc) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->maps, mp.data(), sizeof(LoopMaps) * n, cudaMemcpyHostToDevice);
+  for (int w = 0; w < 4 && e == cudaSuccess; ++w)
+    e = cudaMemcpy(g->items[w], items[w].data(), sizeof(int4) * items[w].size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(g->bctrl, 0, sizeof(Ctrl));
+  if (e == cudaSuccess) e = cudaMemset(g->gstop, 0, sizeof(unsigned) * (MAXF / 32));
+  if (e != cudaSuccess) {
+    tc_group_destroy(g);
+    *msg = std::string("grouped launch set-up: ") + cudaGetErrorName(e);
+    return 2;
+  }
+  *out = g;
+  return 0;
+}
+
+cudaError_t tc_group_begin_step(TcGroup* g, cudaStream_t st) {
+  return cudaMemsetAsync(g->bctrl, 0, sizeof(Ctrl), st);
+}
+
+cudaError_t tc_group_enqueue(TcGroup* g, int pairs, cudaStream_t st) {
+  if (!g || pairs < 1) return cudaErrorInvalidValue;
+  BatchArgs a{};
+  a.flows = g->flows;
+  a.maps = g->maps;
+  for (int w = 0; w < 4; ++w) {
+    a.items[w] = g->items[w];
+    a.ntiles[w] = g->ntiles[w];
+  }
+  a.bctrl = g->bctrl;
+  a.gstop = g->gstop;
+  a.F = g->F;
+  a.pairs = pairs;
+  switch (g->mode) {
+    case MODE_TF32: return launch_batch<MODE_TF32>(a, g->grid, st);
+    case MODE_BF16X3: return launch_batch<MODE_BF16X3>(a, g->grid, st);
+    default: return launch_batch<MODE_BF16>(a, g->grid, st);
+  }
+}
+
+int tc_group_flows(const TcGroup* g) { return g ? g->F : 0; }
+
+double tc_group_flops(const TcGroup* g, int pairs) { return g ? g->flops_pair * pairs : 0.0; }
+
 
 }  // namespace jko

@@ -295,11 +295,13 @@ def jko_handle_info(h: Handle) -> dict:
 
 def jko_batch_info(b) -> dict:
     """The batch autotuner's choice: 'tuned' (-1 none, 0 each flow's own, 1
-    per-pass 64, 2 per-pass 128, 3 loop kernel), flows on the loop kernel,
-    and whether the per-pass fallback was taken."""
-    out = (ctypes.c_int * 3)()
+    per-pass 64, 2 per-pass 128, 3 loop kernel, 4 grouped launches), flows on
+    a loop-kernel launch of their own, whether the per-pass fallback was
+    taken, flows in grouped launches and the number of grouped launches."""
+    out = (ctypes.c_int * 5)()
     _check(lib().jko_batch_info(b.ptr, out), None)
-    return {"tuned": int(out[0]), "loop_flows": int(out[1]), "per_pass_fallback": bool(out[2])}
+    return {"tuned": int(out[0]), "loop_flows": int(out[1]), "per_pass_fallback": bool(out[2]),
+            "grouped_flows": int(out[3]), "grouped_launches": int(out[4])}
 
 
 def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
@@ -391,10 +393,11 @@ def _energy_struct(pb, keep):
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
                      check_every: int = 0, renormalize: bool = True, stream=None,
                      loop: int = 0, tile: int = 0) -> Batch:
-    """jko_batch_create for a list of ``inputs.Problem``; ``precision`` may be
-    one value or one per flow."""
+    """jko_batch_create for a list of ``inputs.Problem``; ``precision`` and
+    ``loop`` may be one value or one per flow (loop = 3: grouped launch)."""
     n = len(problems)
     precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * n
+    loops = list(loop) if isinstance(loop, (list, tuple)) else [loop] * n
     G = (jko_grid * n)()
     P = (jko_params * n)()
     E = (jko_energy * n)()
@@ -403,7 +406,7 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
         G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
         P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                           pb.max_iter if max_iter is None else max_iter, check_every,
-                          int(precs[f]), int(bool(renormalize)), 0, int(loop), int(tile))
+                          int(precs[f]), int(bool(renormalize)), 0, int(loops[f]), int(tile))
         E[f] = _energy_struct(pb, keep)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -73,7 +73,7 @@ def test_batch_autotuner_all_tensor_core_flows():
     b = jko.jko_batch_create(pbs, precision=precs)
     info = jko.jko_batch_info(b)
     print("batch autotuner", info)
-    assert info["tuned"] in (0, 1, 2, 3)
+    assert info["tuned"] in (0, 1, 2, 3, 4)
     p0s = [torch.tensor(pb.q0, dtype=torch.float32, device="cuda") for pb in pbs]
     finals, table = jko.jko_batch_flow(b, p0s, 2)
     for f, pb in enumerate(pbs):
