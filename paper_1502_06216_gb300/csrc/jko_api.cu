@@ -936,16 +936,18 @@ void clear_groups(jko_batch* b) {
 }
 
 // Puts the flows with sel[f] set that can run the loop kernel into grouped
-// launches, one per precision (and per 2048 flows); the others keep their own
-// branch.
+// launches, one per precision and energy kind (and per 2048 flows); the
+// others keep their own branch.
 jko_status make_groups(jko_batch* b, const std::vector<char>& sel) {
   clear_groups(b);
-  for (int prec : {JKO_TF32, JKO_BF16, JKO_BF16X3}) {
+  for (int key = 0; key < 9; ++key) {
+    const int prec = key / 3 == 0 ? JKO_TF32 : key / 3 == 1 ? JKO_BF16 : JKO_BF16X3;
+    const int ek = key % 3;
     std::vector<jko::TcPlan*> plans;
     std::vector<int> ids;
     for (int f = 0; f < b->n; ++f) {
       jko_handle* h = b->h[f];
-      if (sel[f] && h->tc && h->prec == prec && jko::tc_loop_supported(h->tc)) {
+      if (sel[f] && h->tc && h->prec == prec && h->ek == ek && jko::tc_loop_supported(h->tc)) {
         plans.push_back(h->tc);
         ids.push_back(f);
       }

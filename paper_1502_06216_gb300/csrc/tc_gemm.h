@@ -64,8 +64,8 @@ cudaError_t tc_enqueue_loop(TcPlan* plan, int pairs, cudaStream_t st);
 // Executed tensor-core flops of `pairs` pairs of the loop kernel.
 double tc_loop_flops(const TcPlan* plan, int pairs);
 // Grouped persistent kernel (tc_loop.cu): one cooperative launch runs the
-// scaling loop of several flows of one precision, each with its own stop rule
-// in its own Ctrl.  Create: 0 = ok, 1 = not groupable (message set), 2 = CUDA
+// scaling loop of several flows of one precision and energy kind, each with
+// its own stop rule in its own Ctrl.  Create: 0 = ok, 1 = not groupable (message set), 2 = CUDA
 // error.  begin_step resets the launch's grid-barrier words (once per step).
 struct TcGroup;
 int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg);

@@ -604,7 +604,10 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
 
 // ------------------------------------------------------------ grouped batch
 // One cooperative launch runs the scaling loop of every flow of a batch that
-// shares the operand precision.  The tiles of all flows form one list per
+// shares the operand precision and the energy kind (the prox of the epilogue
+// is compiled for one kind: a run-time choice among the three inlines all of
+// them at the 96-register cap of 19 warps and made the element math of a tile
+// several times slower).  The tiles of all flows form one list per
 // pass, walked by the CTAs between the same grid barriers as above; each tile
 // names its flow, whose tensor maps and descriptor live in device memory.
 // Every flow keeps its own stop rule: during pass 2 the flow's designated CTA
@@ -627,9 +630,12 @@ struct FlowDesc {
   ProxArgs<float> P;
 };
 
-// Tile g of pass p: items[p][2g] = {flow, m0, n0, 2 t + e} (t: index of the
-// tile in the flow's pass, e: 1 if the tile loads epilogue tiles),
-// items[p][2g + 1] = the factor band of its 128-row block.
+// Tile g of pass p: items[p][2g] = {flow, m0, n0, 8 t + 2 ek + e} (t: index
+// of the tile in the flow's pass, ek: energy kind, e: 1 if the tile loads
+// epilogue tiles), items[p][2g + 1] = {first K element of the factor band of
+// its 128-row block, K-blocks of the band, M, N of the flow's pass}.  Every
+// role loads a tile's two int4 one tile ahead, so no per-tile global load
+// chain sits on the critical path.
 struct BatchArgs {
   const FlowDesc* flows;
   const LoopMaps* maps;     // tensor maps of each flow
@@ -645,8 +651,27 @@ __device__ __forceinline__ bool flow_stopped(const unsigned* mask, int f) {
   return (*(const volatile unsigned*)&mask[f >> 5] >> (f & 31)) & 1u;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant__ BatchArgs args) {
+struct TileItem {
+  int4 a, b;
+};
+
+__device__ __forceinline__ TileItem load_item(const int4* items, int g, int nt) {
+  TileItem r;
+  if (g < nt) {
+    r.a = __ldg(items + 2 * g);
+    r.b = __ldg(items + 2 * g + 1);
+  } else {
+    r.a = make_int4(0, 0, 0, 0);
+    r.b = make_int4(0, 0, 0, 0);
+  }
+  return r;
+}
+
+constexpr int NTB = NTL + 32;               // + warp 18, which loads the epilogue tiles
+constexpr int WARP_EPILD = 18;
+
+template <int MODE, int EK>
+__global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant__ BatchArgs args) {
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;
   constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
@@ -684,6 +709,7 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
   __shared__ unsigned s_base;
   __shared__ float s_red[NEPI / 32];
   __shared__ unsigned s_fstop[MAXF / 32];   // flows whose tiles are skipped
+  __shared__ unsigned s_itpos[MAXF / 32];   // flows with pairs done before this launch
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
@@ -692,7 +718,10 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
   Ctrl* bctrl = args.bctrl;
   const int nq = 4 * args.pairs;
 
-  for (int i = threadIdx.x; i < MAXF / 32; i += NTL) s_fstop[i] = 0u;
+  for (int i = threadIdx.x; i < MAXF / 32; i += NTB) {
+    s_fstop[i] = 0u;
+    s_itpos[i] = 0u;
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -715,16 +744,17 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
   __syncthreads();
   // flows that stopped in an earlier launch of the step (their Ctrl changes
   // only in pass 2, after two grid barriers, so every CTA reads the same)
-  for (int f = threadIdx.x; f < F; f += NTL) {
+  for (int f = threadIdx.x; f < F; f += NTB) {
     Ctrl* c = args.flows[f].ctrl;
     const int done = *(volatile int*)&c->done;
     const int nf = *(volatile int*)&c->nonfinite;
     if (done != RUNNING || nf) atomicOr(&s_fstop[f >> 5], 1u << (f & 31));
+    if (c->it > 0) atomicOr(&s_itpos[f >> 5], 1u << (f & 31));
     if (done == RUNNING && nf && f % G == (int)blockIdx.x) c->done = NONFINITE;
   }
   // the stop words of this launch start empty (first read after barrier 3)
   if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < nwords; i += NTL) args.gstop[i] = 0u;
+    for (int i = threadIdx.x; i < nwords; i += NTB) args.gstop[i] = 0u;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -744,25 +774,51 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
 
   if (stopped_at_start) {
     // every flow has already stopped
-  } else if (warp == WARP_PROD) {
-    // ------------------------------------------------------------ producer
+  } else if (warp == WARP_PROD || warp == WARP_EPILD) {
+    // ------------------------------------------------------------ producers
+    // warp 16 streams the operand K-blocks, warp 18 the epilogue tiles, each
+    // as soon as its own buffer is free, so the next tile's operands load
+    // while the epilogue still holds the current tile's q / old b /
+    // e^{-sigma w} (two lanes of one warp would wait on each other)
+    const bool kload = warp == WARP_PROD;
     if (lane == 0) {
       uint32_t kc = 0, ec = 0;
       bool ok = true;
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
+        const int nt = args.ntiles[p];
+        TileItem nx = load_item(args.items[p], blockIdx.x, nt);
         if (q > 0) {
           ok = wait_go(&s_go, q);
           if (!ok || s_stop) break;
           fence_proxy_async_global();
         }
-        for (int g = blockIdx.x; g < args.ntiles[p] && ok; g += G) {
-          const int4 it = __ldg(args.items[p] + 2 * g);
+        for (int g = blockIdx.x; g < nt && ok; g += G) {
+          const TileItem cur = nx;
+          nx = load_item(args.items[p], g + G, nt);
+          const int4 it = cur.a;
           if (flow_stopped(s_fstop, it.x)) continue;
-          const int4 kb = __ldg(args.items[p] + 2 * g + 1);
           const LoopMaps* mp = args.maps + it.x;
           const int m0 = it.y, n0 = it.z;
-          if (it.w & 1) {
+          if (kload) {
+            const int4 kb = cur.b;
+            for (int i = 0; i < kb.y && ok; ++i) {
+              const uint32_t k = kc + i;
+              const int s = (int)(k % STAGES);
+              if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
+              if (!ok) break;
+              unsigned char* st = stages + s * STAGE_BYTES;
+              const int kx = kb.x + i * KE;
+              mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
+              tma_load_2d(st, &mp->K[p][0], &full_bar[s], kx, m0);
+              tma_load_2d(st + A_BYTES, &mp->B[p][0], &full_bar[s], kx, n0);
+              if constexpr (NSPLIT == 2) {
+                tma_load_2d(st + A_BYTES + B_BYTES, &mp->K[p][1], &full_bar[s], kx, m0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mp->B[p][1], &full_bar[s], kx, n0);
+              }
+            }
+            kc += kb.y;
+          } else if (it.w & 1) {
             if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
             if (!ok) break;
             if (p == 1) {
@@ -786,22 +842,6 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
             }
             ++ec;
           }
-          for (int i = 0; i < kb.y && ok; ++i) {
-            const uint32_t k = kc + i;
-            const int s = (int)(k % STAGES);
-            if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
-            if (!ok) break;
-            unsigned char* st = stages + s * STAGE_BYTES;
-            const int kx = kb.x + i * KE;
-            mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
-            tma_load_2d(st, &mp->K[p][0], &full_bar[s], kx, m0);
-            tma_load_2d(st + A_BYTES, &mp->B[p][0], &full_bar[s], kx, n0);
-            if constexpr (NSPLIT == 2) {
-              tma_load_2d(st + A_BYTES + B_BYTES, &mp->K[p][1], &full_bar[s], kx, m0);
-              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mp->B[p][1], &full_bar[s], kx, n0);
-            }
-          }
-          kc += kb.y;
         }
       }
       if (!ok) atomicOr(&s_fault, 1);
@@ -813,13 +853,17 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
       bool ok = true;
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
+        const int nt = args.ntiles[p];
+        TileItem nx = load_item(args.items[p], blockIdx.x, nt);
         if (q > 0) {
           ok = wait_go(&s_go, q);
           if (!ok || s_stop) break;
         }
-        for (int g = blockIdx.x; g < args.ntiles[p] && ok; g += G) {
-          if (flow_stopped(s_fstop, __ldg(&args.items[p][2 * g].x))) continue;
-          const int nkb = __ldg(&args.items[p][2 * g + 1].y);
+        for (int g = blockIdx.x; g < nt && ok; g += G) {
+          const TileItem cur = nx;
+          nx = load_item(args.items[p], g + G, nt);
+          if (flow_stopped(s_fstop, cur.a.x)) continue;
+          const int nkb = cur.b.y;
           if (tc > 0) ok = mbar_wait(tmem_free_bar, (tc - 1) & 1);
           if (!ok) break;
           tc_fence_after();
@@ -864,6 +908,8 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
     for (int q = 0; q < nq; ++q) {
       const int p = q & 3;
       const int pair = q >> 2;
+      const int nt = args.ntiles[p];
+      TileItem nx = load_item(args.items[p], blockIdx.x, nt);
       if (q > 0) {
         // ---- grid barrier ----
         if (threadIdx.x == 0) {
@@ -941,15 +987,24 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
         }
       }
       bool first = true;
-      for (int g = blockIdx.x; g < args.ntiles[p]; g += G) {
-        const int4 itm = __ldg(args.items[p] + 2 * g);
+      for (int g = blockIdx.x; g < nt; g += G) {
+        const TileItem cur = nx;
+        nx = load_item(args.items[p], g + G, nt);
+        const int4 itm = cur.a;
         if (flow_stopped(s_fstop, itm.x)) continue;
         const FlowDesc& FD = args.flows[itm.x];
         const LoopMaps* mp = args.maps + itm.x;
-        const int t = itm.w >> 1;
+        const int t = itm.w >> 3;
         const bool epi_pass = (itm.w & 1) != 0;
         const int m0 = itm.y, n0 = itm.z;
-        const int PM = FD.M[p], PN = FD.N[p];
+        const int PM = cur.b.z, PN = cur.b.w;
+        const bool have_prev =
+            p == 1 && (pair > 0 || ((s_itpos[itm.x >> 5] >> (itm.x & 31)) & 1u) != 0);
+        // per-flow values, loaded while the tile's MMAs run
+        ProxArgs<float> P{};
+        double* part = nullptr;
+        if (p == 3) P = FD.P;
+        if (p == 1) part = FD.part;
         if (!first) {
           if (threadIdx.x == 0) {
             bulk_wait_read_all();
@@ -984,7 +1039,6 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
 #pragma unroll
           for (int j = 0; j < 16; ++j) o[j] = v[j];
         } else if (p == 1) {
-          const bool have_prev = (*(const volatile int*)&FD.ctrl->it + pair) > 0;
           float qv[16], bo[16];
           smem_ld_f32x16(epi_f, rl, c, qv);
           if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
@@ -999,12 +1053,10 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
             }
           }
         } else {
-          const ProxArgs<float> P = FD.P;
-          const int ek = FD.ek;
           const int irow = m * PN + nb;
           float ev[16], pv[16];
-          if (ek == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
-          if (ek == EK_CROWD && P.mask == nullptr && P.kappa == nullptr) {
+          if (EK == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
+          if (EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr) {
             const bool hk = P.has_kappa != 0;
             const float kap = P.kappa_s;
 #pragma unroll
@@ -1021,9 +1073,7 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
             for (int j = 0; j < 16; ++j) {
               float a = 0.0f;
               if (j < cnt) {
-                a = ek == EK_CROWD    ? prox_ratio_e<float, EK_CROWD>(P, irow + j, v[j], ev[j])
-                    : ek == EK_ENTROPY ? prox_ratio_e<float, EK_ENTROPY>(P, irow + j, v[j], 0.0f)
-                                       : prox_ratio_e<float, EK_POWER>(P, irow + j, v[j], 0.0f);
+                a = prox_ratio_e<float, EK>(P, irow + j, v[j], EK == EK_CROWD ? ev[j] : 0.0f);
                 bad |= !isfinite(a);
               }
               o[j] = a;
@@ -1042,7 +1092,7 @@ __global__ void __launch_bounds__(NTL, 1) tc_batch_kernel(const __grid_constant_
         else
           named_bar_sync(EPI_BAR, NEPI);
         if (threadIdx.x == 0) {
-          if (p == 1) FD.part[t] = res;
+          if (p == 1) part[t] = res;
           constexpr int KEo = 128 / (int)sizeof(T);
 #pragma unroll
           for (int cb = 0; cb < CB; ++cb) {
@@ -1256,27 +1306,27 @@ cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
 // ------------------------------------------------------------ grouped batch (host)
 namespace {
 
-template <int MODE>
+template <int MODE, int EK>
 cudaError_t set_batch_attr() {
-  return cudaFuncSetAttribute(tc_batch_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(tc_batch_kernel<MODE, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)loop_smem_bytes(MODE, false));
 }
 
-template <int MODE>
+template <int MODE, int EK>
 int batch_blocks_per_sm() {
   int nb = 0;
-  if (set_batch_attr<MODE>() != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_batch_kernel<MODE>, NTL,
+  if (set_batch_attr<MODE, EK>() != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_batch_kernel<MODE, EK>, NTB,
                                                     loop_smem_bytes(MODE, false)) != cudaSuccess)
     return 0;
   return nb;
 }
 
-template <int MODE>
+template <int MODE, int EK>
 cudaError_t launch_batch(const BatchArgs& args, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(NTL);
+  cfg.blockDim = dim3(NTB);
   cfg.dynamicSmemBytes = loop_smem_bytes(MODE, false);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1284,13 +1334,27 @@ cudaError_t launch_batch(const BatchArgs& args, int grid, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, tc_batch_kernel<MODE>, args);
+  return cudaLaunchKernelEx(&cfg, tc_batch_kernel<MODE, EK>, args);
+}
+
+template <int MODE>
+int batch_blocks_ek(int ek) {
+  return ek == EK_CROWD ? batch_blocks_per_sm<MODE, EK_CROWD>()
+         : ek == EK_ENTROPY ? batch_blocks_per_sm<MODE, EK_ENTROPY>()
+                            : batch_blocks_per_sm<MODE, EK_POWER>();
+}
+
+template <int MODE>
+cudaError_t launch_batch_ek(int ek, const BatchArgs& args, int grid, cudaStream_t st) {
+  return ek == EK_CROWD ? launch_batch<MODE, EK_CROWD>(args, grid, st)
+         : ek == EK_ENTROPY ? launch_batch<MODE, EK_ENTROPY>(args, grid, st)
+                            : launch_batch<MODE, EK_POWER>(args, grid, st);
 }
 
 }  // namespace
 
 struct TcGroup {
-  int mode = 0, F = 0, grid = 0;
+  int mode = 0, ek = 0, F = 0, grid = 0;
   FlowDesc* flows = nullptr;
   LoopMaps* maps = nullptr;
   int4* items[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -1316,18 +1380,18 @@ int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg
     *msg = "a grouped launch takes 1 to 2048 flows";
     return 1;
   }
-  const int mode = plans[0]->mode;
+  const int mode = plans[0]->mode, ek = plans[0]->cfg.ek;
   for (int f = 0; f < n; ++f)
-    if (!plans[f]->loop_ok || plans[f]->mode != mode) {
-      *msg = "every flow of a group needs the loop kernel and the group's precision";
+    if (!plans[f]->loop_ok || plans[f]->mode != mode || plans[f]->cfg.ek != ek) {
+      *msg = "every flow of a group needs the loop kernel, the group's precision and energy kind";
       return 1;
     }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nb = mode == MODE_TF32 ? batch_blocks_per_sm<MODE_TF32>()
-                 : mode == MODE_BF16X3 ? batch_blocks_per_sm<MODE_BF16X3>()
-                                       : batch_blocks_per_sm<MODE_BF16>();
+  const int nb = mode == MODE_TF32 ? batch_blocks_ek<MODE_TF32>(ek)
+                 : mode == MODE_BF16X3 ? batch_blocks_ek<MODE_BF16X3>(ek)
+                                       : batch_blocks_ek<MODE_BF16>(ek);
   cudaGetLastError();
   if (nb < 1 || sms < 1) {
     *msg = "the grouped kernel does not fit an SM";
@@ -1335,6 +1399,7 @@ int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg
   }
   TcGroup* g = new TcGroup();
   g->mode = mode;
+  g->ek = ek;
   g->F = n;
   std::vector<FlowDesc> fd(n);
   std::vector<LoopMaps> mp(n);
@@ -1358,8 +1423,8 @@ int tc_group_create(TcPlan* const* plans, int n, TcGroup** out, std::string* msg
       const int epi = (w == 1 || (w == 3 && c.ek == EK_CROWD)) ? 1 : 0;
       for (int t = 0; t < L.ntiles; ++t) {
         const int mt = t / L.tiles_n;
-        items[w].push_back(make_int4(f, mt * BM, (t - mt * L.tiles_n) * LBN, 2 * t + epi));
-        items[w].push_back(tab[mt]);
+        items[w].push_back(make_int4(f, mt * BM, (t - mt * L.tiles_n) * LBN, 8 * t + 2 * c.ek + epi));
+        items[w].push_back(make_int4(tab[mt].x, tab[mt].y, L.M, L.N));
       }
     }
     d.ctrl = c.ctrl;
@@ -1414,9 +1479,9 @@ cudaError_t tc_group_enqueue(TcGroup* g, int pairs, cudaStream_t st) {
   a.F = g->F;
   a.pairs = pairs;
   switch (g->mode) {
-    case MODE_TF32: return launch_batch<MODE_TF32>(a, g->grid, st);
-    case MODE_BF16X3: return launch_batch<MODE_BF16X3>(a, g->grid, st);
-    default: return launch_batch<MODE_BF16>(a, g->grid, st);
+    case MODE_TF32: return launch_batch_ek<MODE_TF32>(g->ek, a, g->grid, st);
+    case MODE_BF16X3: return launch_batch_ek<MODE_BF16X3>(g->ek, a, g->grid, st);
+    default: return launch_batch_ek<MODE_BF16>(g->ek, a, g->grid, st);
   }
 }
 

@@ -1,6 +1,6 @@
 """Grouped launch of a batch: one cooperative launch of the persistent kernel
-runs the scaling loop of every flow of a precision, each with its own stop
-rule (Sec. 3.4).  The per-tile arithmetic is the loop kernel's, so every flow
+runs the scaling loop of every flow of a precision and energy kind, each with
+its own stop rule (Sec. 3.4).  The per-tile arithmetic is the loop kernel's, so every flow
 must equal the same flow alone on the loop kernel bit for bit (images, pairs,
 residuals), and match the FP64 oracle within its form's bar."""
 import copy
@@ -23,6 +23,10 @@ def loop_mix():
             inputs.crowd_problem(96, gamma=4e-3, tau=0.02, kappa_factor=1.2, tol=1e-6, n_steps=3),
             inputs.crowd_problem(64, ny=100, gamma=1e-3, tau=0.05, tol=1e-6, n_steps=3),
             inputs.config_problem(2, n=256, n_steps=3)]
+
+
+def energy_kind(pb):
+    return 0 if pb.m == 0 else (1 if pb.m == 1 else 2)
 
 
 def alone(pb, prec, p0, n_steps):
@@ -56,7 +60,8 @@ def test_grouped_equals_loop_kernel_alone(precs):
     info = jko.jko_batch_info(b)
     print("batch", info)
     assert info["grouped_flows"] == len(pbs)
-    assert info["grouped_launches"] == len(set(precs))
+    # one launch per (precision, energy kind)
+    assert info["grouped_launches"] == len({(pr, energy_kind(pb)) for pr, pb in zip(precs, pbs)})
     p0s = [torch.tensor(pb.q0, dtype=torch.float32, device="cuda") for pb in pbs]
     finals, table = jko.jko_batch_flow(b, p0s, 3)
     torch.cuda.synchronize()
