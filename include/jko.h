@@ -298,6 +298,14 @@ jko_status jko_batch_info(const jko_batch* b, int* out);
 jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
                           void* const* p_final_dev, jko_step_info* infos);
 
+/* One JKO step (Eq. smooth-jko) of every flow: p_out_dev[f] = Prox step of
+ * q_dev[f] (device images as in jko_batch_flow, validated the same way;
+ * q_dev[f] and p_out_dev[f] may be the same buffer).  infos (may be NULL)
+ * receives n_flows reports.  Returns the worst status over flows; the flows'
+ * outputs are written for JKO_OK, JKO_NOT_CONVERGED and JKO_ERR_NUMERIC. */
+jko_status jko_batch_step(jko_batch* b, const void* const* q_dev, void* const* p_out_dev,
+                          jko_step_info* infos);
+
 /* Frees the batch and its flows (NULL is accepted). */
 jko_status jko_batch_destroy(jko_batch* b);
 

@@ -1313,6 +1313,15 @@ jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
   return (jko_status)worst;
 }
 
+jko_status jko_batch_step(jko_batch* b, const void* const* q_dev, void* const* p_out_dev,
+                          jko_step_info* infos) {
+  if (!b) return batch_err(nullptr, JKO_ERR_INVALID_ARG, "NULL batch");
+  if (!q_dev || !p_out_dev) return batch_err(b, JKO_ERR_INVALID_ARG, "NULL q or p_out array");
+  for (int f = 0; f < b->n; ++f)
+    if (!p_out_dev[f]) return batch_err(b, JKO_ERR_INVALID_ARG, "NULL p_out entry");
+  return jko_batch_flow(b, q_dev, 1, p_out_dev, infos);
+}
+
 jko_status jko_batch_destroy(jko_batch* b) {
   free_batch(b);
   return JKO_OK;

@@ -110,6 +110,9 @@ EXPORTS = {
     "jko_batch_flow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(jko_step_info)]),
+    "jko_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(jko_step_info)]),
     "jko_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "jko_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "jko_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -414,6 +417,21 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
     if status != Status.OK:
         raise JKOError(status, lib().jko_batch_last_error(None).decode(errors="replace"))
     return Batch(out, [(pb.nx, pb.ny) for pb in problems], [Precision(p) for p in precs])
+
+
+def jko_batch_step(b: Batch, qs, p_outs=None):
+    """One step of every flow from the device tensors qs into p_outs (new
+    tensors when None); returns (p_outs, infos[f])."""
+    import torch
+    n = b.n
+    outs = [torch.empty_like(t) for t in qs] if p_outs is None else list(p_outs)
+    Q = (ctypes.c_void_p * n)(*[ctypes.c_void_p(t.data_ptr()) for t in qs])
+    PO = (ctypes.c_void_p * n)(*[ctypes.c_void_p(t.data_ptr()) for t in outs])
+    infos = (jko_step_info * n)()
+    status = lib().jko_batch_step(b.ptr, Q, PO, infos)
+    if status not in (Status.OK, Status.NOT_CONVERGED, Status.NUMERIC):
+        raise JKOError(status, lib().jko_batch_last_error(b.ptr).decode(errors="replace"))
+    return outs, [infos[f].as_dict() for f in range(n)]
 
 
 def jko_batch_flow(b: Batch, p0s, n_steps: int, want_final: bool = True):

@@ -82,3 +82,27 @@ def test_batch_autotuner_all_tensor_core_flows():
         print(f, pb.name, precs[f].name, "rel L1", err)
         assert err <= 1e-3
     jko.jko_batch_destroy(b)
+
+
+def test_batch_step_equals_one_step_of_the_flow():
+    """jko_batch_step is one step of jko_batch_flow, also in place (q = p_out),
+    for grouped, loop-kernel and CUDA-core flows alike."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pbs = small_mix()
+    P = [jko.Precision.BF16X3, jko.Precision.TF32, jko.Precision.BF16, jko.Precision.FP32,
+         jko.Precision.BF16X3]
+    loops = [3, 3, 1, 0, 0]
+    b = jko.jko_batch_create(pbs, precision=P, loop=loops)
+    p0s = [torch.tensor(pb.q0, dtype=torch.float32, device="cuda") for pb in pbs]
+    finals, table = jko.jko_batch_flow(b, p0s, 1)
+    outs, infos = jko.jko_batch_step(b, p0s)
+    for f in range(len(pbs)):
+        assert torch.equal(outs[f], finals[f]), f
+        assert infos[f]["iters"] == table[0][f]["iters"]
+        assert infos[f]["residual_l1"] == table[0][f]["residual_l1"]
+    qs = [t.clone() for t in p0s]
+    outs2, _ = jko.jko_batch_step(b, qs, qs)
+    for f in range(len(pbs)):
+        assert torch.equal(qs[f], finals[f]), f
+    jko.jko_batch_destroy(b)
