@@ -11,7 +11,8 @@ Plain, slow and written to be checked against the paper by eye:
                    dense from 2-D coordinates and as 1-D factors.
 * ``prox``      -- pointwise KL proximal maps (Eq. def-kl-prox-operator):
                    congestion + potential (Prop. 4.1), entropy (Eq. prox-entropy),
-                   power entropies (Eq. prox-psi), obstacle mask.
+                   power entropies (Eq. prox-psi), the generalised entropies with
+                   per-cell exponents (Eq. defn-gen-entropies), obstacle mask.
 * ``jko``       -- one JKO step (Eq. def-jko-operator) by the 2-vector scaling
                    loop, the literal 4-vector Dykstra of Prop. 3.3, and the dense
                    Dykstra on couplings (Eq. iter-dystra-1/2); the flow (Eq. smooth-jko).

@@ -94,6 +94,8 @@ def solve_step(q: np.ndarray, c: np.ndarray, gamma: float, tau: float,
     opts = dict(gtol=gtol, ftol=0.0, maxiter=maxiter, maxcor=50, maxls=100)
     scale = 1.0 / gamma   # objective scaled to O(1) curvature
 
+    if energy.m_field is not None:
+        raise NotImplementedError("per-cell exponents: use prox / jko / mirror")
     if energy.m == 0:
         if not np.all(np.isfinite(kappa[active])):
             raise ValueError("congestion dual needs a finite kappa")

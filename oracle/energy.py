@@ -10,6 +10,14 @@ with the entropy term selected by ``m``:
            -m s/(m-1), i.e. by a potential, see ``paper_em_as_power``).
 Congestion is Eq. dfn-congestion (kappa may be a scalar or a field, Sec. 4.2);
 the mask is an obstacle set where f = +inf.
+
+``m_field`` (per-cell exponents m_i >= 1, overriding ``m``) selects the paper's
+generalised entropies with spatially varying exponents and weights b_i =
+``alpha`` (Eq. defn-gen-entropies):
+  e_{m}(s) = s (log s - 1)               if m = 1,
+  e_{m}(s) = s (s^{m-1} - m) / (m - 1)   if m > 1,
+written as it stands (no potential is split off: its -m/(m-1) slope has no
+finite limit as m -> 1, where e_m tends to the m = 1 entropy).
 """
 from __future__ import annotations
 
@@ -26,6 +34,7 @@ class Energy:
     m: float = 0.0
     alpha: Union[float, np.ndarray, None] = None
     mask: Optional[np.ndarray] = None
+    m_field: Optional[np.ndarray] = None
 
     def arrays(self, N: int):
         """(w, kappa, alpha, mask) as float64 / bool arrays of length N."""
@@ -39,9 +48,14 @@ class Energy:
                 else np.asarray(self.mask).astype(bool))
         return w, kappa, alpha, mask
 
+    def exponents(self, N: int) -> np.ndarray:
+        """Per-cell exponents m_i of the generalised entropies (``m_field``)."""
+        return np.broadcast_to(np.asarray(self.m_field, np.float64), (N,)).copy()
+
     @staticmethod
     def from_problem(pb) -> "Energy":
-        return Energy(w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask)
+        return Energy(w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
+                      m_field=getattr(pb, "m_field", None))
 
 
 def paper_em_as_power(m: float, alpha, w=None, N: Optional[int] = None) -> Energy:

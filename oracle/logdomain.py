@@ -41,6 +41,8 @@ def log_ratio(ls: np.ndarray, sigma: float, energy: Energy) -> np.ndarray:
     N = ls.size
     w, kappa, alpha, mask = energy.arrays(N)
     l = ls - sigma * w
+    if energy.m_field is not None:
+        raise NotImplementedError("per-cell exponents: use prox / jko / mirror")
     if energy.m == 0:
         lpsi = l
     elif energy.m == 1:

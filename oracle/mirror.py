@@ -17,8 +17,9 @@ by q_j) takes
 then rescales every column back to the sum q_j.  F is 1-strongly convex and
 (1 + L)-smooth relative to the entropy, L bounding sigma f'' against it, so
 eta = 1 / (1 + L) converges linearly.  Smooth energies only (potential,
-entropy m = 1, power m > 1, obstacle mask); the congestion constraint is not
-smooth and is pinned by the dual solver instead.
+entropy m = 1, power m > 1, the generalised entropies with per-cell exponents,
+obstacle mask); the congestion constraint is not smooth and is pinned by the
+dual solver instead.
 """
 from __future__ import annotations
 
@@ -31,6 +32,13 @@ def _fprime(p: np.ndarray, en: Energy, N: int) -> np.ndarray:
     """f'(p) of the smooth part of f: w + alpha e'(p)."""
     w, _, alpha, _ = en.arrays(N)
     g = w.copy()
+    if en.m_field is not None:
+        # e_m'(s) = m (s^{m-1} - 1)/(m - 1), log s at m = 1 (Eq. defn-gen-entropies)
+        m_i = en.exponents(N)
+        m1 = m_i - 1.0
+        lp = np.log(np.maximum(p, 1e-300))
+        g += alpha * np.where(m1 > 0, m_i * np.expm1(m1 * lp) / np.where(m1 > 0, m1, 1.0), lp)
+        return g
     if en.m == 1.0:
         g += alpha * np.log(np.maximum(p, 1e-300))          # e(s) = s (log s - 1)
     elif en.m > 1.0:
@@ -42,6 +50,9 @@ def _smoothness(p_max: float, en: Energy, N: int, sigma: float) -> float:
     """L with sigma (sum_j dpi_ij)^2 f''(p_i) <= L sum_j dpi_ij^2 / pi_ij
     (Cauchy-Schwarz: (sum dpi)^2 <= p_i sum dpi^2 / pi)."""
     _, _, alpha, _ = en.arrays(N)
+    if en.m_field is not None:
+        m_i = en.exponents(N)                                # f'' p = alpha m p^{m-1}
+        return sigma * float(np.max(alpha * m_i * p_max ** (m_i - 1.0)))
     if en.m == 1.0:
         return sigma * float(alpha.max())                    # f'' p = alpha
     if en.m > 1.0:

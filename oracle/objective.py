@@ -62,6 +62,16 @@ def f_value(p: np.ndarray, energy: Energy, atol: float = 0.0) -> float:
     if np.any(p < 0) or np.any(p > kappa * (1 + atol)) or np.any(p[mask] > 0):
         return float("inf")
     val = float(np.dot(w, p))
+    if energy.m_field is not None:
+        # the paper's e_{m_i} (Eq. defn-gen-entropies), per-cell exponents
+        m_i = energy.exponents(N)
+        m1 = m_i - 1.0
+        pos = p > 0
+        lp = np.log(p[pos])
+        one = m1[pos] == 0
+        e = np.where(one, p[pos] * (lp - 1.0),
+                     p[pos] * (np.exp(m1[pos] * lp) - m_i[pos]) / np.where(one, 1.0, m1[pos]))
+        return val + float(np.sum(alpha[pos] * e))
     m = energy.m
     if m == 1:
         pos = p > 0

@@ -16,6 +16,9 @@ synthetic):
   field built from 8 random Gaussians and rescaled to [0.5, 2], an obstacle
   mask made of 3 axis-aligned rectangles covering 15% of the cells, and q a
   mixture of 4 Gaussian bumps, zeroed on the mask and renormalised.
+* varying exponents -- the paper's e_{m_i} with m_i = 1 + t (1 on the boundary,
+  2 in the centre, t the normalised distance to the boundary) and weights 1,
+  or m_i = 1.4 with weights 1 + 19 t; q white noise (Sec. 4.4, Fig. fig-porous).
 
 All arrays are float64, row-major ``[ny, nx]`` images flattened to length
 N = nx*ny (index y*nx + x), on the domain [0, lx] x [0, ly] sampled at cell
@@ -38,6 +41,7 @@ __all__ = [
     "config_problem",
     "batched_problems",
     "differentiation_problem",
+    "varying_exponent_problem",
 ]
 
 
@@ -57,6 +61,8 @@ class Problem:
     m: float = 0.0                       # 0: no entropy term; 1: entropy; >1 power
     alpha: Optional[np.ndarray] = None   # (N,) weights of the entropy term
     mask: Optional[np.ndarray] = None    # (N,) uint8, 1 = obstacle cell
+    m_field: Optional[np.ndarray] = None  # (N,) per-cell exponents >= 1 (the paper's
+    #                                       e_{m_i} with weights alpha); overrides m
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -178,6 +184,33 @@ def porous_problem(n: int, seed: int, gamma: float = 5e-4, tau: float = 5e-3,
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q.ravel(),
                    m=m, alpha=alpha.ravel(), mask=mask.ravel().astype(np.uint8),
                    n_steps=n_steps, max_iter=max_iter, tol=tol, name=name)
+
+
+def varying_exponent_problem(n: int, seed: int, gamma: float = 1e-3, tau: float = 5e-3,
+                             vary: str = "m", n_steps: int = 20, max_iter: int = 300,
+                             tol: float = 1e-6, ny: Optional[int] = None,
+                             name: str = "genent") -> Problem:
+    """Non-linear diffusion on the generalised entropies with spatially varying
+    parameters (Sec. 4.4, the setting of its Fig. fig-porous): q0 white noise
+    (cells i.i.d. uniform on [0, 1], normalised to unit mass); the profile
+    t = distance to the domain boundary / its maximum (0 on the boundary, 1 in
+    the centre) sets either the exponents m_i = 1 + t with weights 1
+    (vary = "m") or the weights b_i = 1 + 19 t with m_i = 1.4 (vary = "b")."""
+    nx = n
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    d = np.minimum(np.minimum(X, 1.0 - X), np.minimum(Y, 1.0 - Y))
+    t = d / d.max()
+    q = rng.uniform(0.0, 1.0, X.shape)
+    q = q / q.sum()
+    if vary == "m":
+        m_field, alpha = 1.0 + t, np.ones(X.shape)
+    else:
+        m_field, alpha = np.full(X.shape, 1.4), 1.0 + 19.0 * t
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q.ravel(), alpha=alpha.ravel(),
+                   m_field=m_field.ravel(), n_steps=n_steps, max_iter=max_iter, tol=tol,
+                   name=name)
 
 
 # Named workloads.  Sizes are parameters so that tests can run the same recipe
