@@ -113,6 +113,10 @@ typedef struct jko_energy {
   double m;                   /* 0: no entropy term, 1: entropy, > 1: power m */
   const double* alpha;        /* per-cell weights of the entropy term (> 0); NULL = 1 */
   const uint8_t* mask;        /* 1 = obstacle cell (f = +inf), 0 = free; NULL = none */
+  const double* m_field;      /* per-cell exponents m_i >= 1 of the paper's generalised
+                                 entropies sum_i alpha_i e_{m_i}(p_i), e_1(s) = s (log s - 1),
+                                 e_m(s) = s (s^{m-1} - m)/(m-1) (Eq. defn-gen-entropies,
+                                 Sec. 4.4); overrides m; NULL = the scalar m above */
 } jko_energy;
 
 /* Per-step report. */

@@ -278,7 +278,7 @@ void free_handle(jko_handle* h) {
   if (h->tc) jko::tc_destroy(h->tc);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
-                  h->taps_y, h->E, h->sw, h->c, h->kap, h->mask, h->ctrl, h->part,
+                  h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->tape, h->adj, h->adj_red};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
@@ -315,6 +315,10 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
+  if (en->m_field)
+    for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
+      if (!(en->m_field[i] >= 1.0) || !std::isfinite(en->m_field[i]))
+        return set_err(nullptr, JKO_ERR_INVALID_ARG, "m_field entries must be finite and >= 1");
   const long long N = (long long)g->nx * g->ny;
   for (long long i = 0; i < N; ++i) {
     if (en->w && !std::isfinite(en->w[i]))
@@ -334,7 +338,8 @@ jko_status build_energy(jko_handle* h, const jko_energy* en) {
   const int N = h->N;
   const double sigma = h->prm.tau / h->prm.gamma;
   h->m = en->m;
-  h->ek = en->m == 0.0 ? jko::EK_CROWD : (en->m == 1.0 ? jko::EK_ENTROPY : jko::EK_POWER);
+  h->ek = en->m_field ? jko::EK_POWER
+          : en->m == 0.0 ? jko::EK_CROWD : (en->m == 1.0 ? jko::EK_ENTROPY : jko::EK_POWER);
   std::vector<double> v(N);
   if (h->ek == jko::EK_CROWD) {
     for (int i = 0; i < N; ++i) v[i] = std::exp(-sigma * (en->w ? en->w[i] : 0.0));
@@ -347,9 +352,15 @@ jko_status build_energy(jko_handle* h, const jko_energy* en) {
     const double m = en->m;
     for (int i = 0; i < N; ++i) {
       const double al = en->alpha ? en->alpha[i] : 1.0;
-      v[i] = (h->ek == jko::EK_ENTROPY) ? sigma * al : sigma * al * m / (m - 1.0);
+      // per-cell exponents: c = sigma alpha m_i of the paper's form of Eq. prox-psi
+      v[i] = en->m_field ? sigma * al * en->m_field[i]
+             : (h->ek == jko::EK_ENTROPY) ? sigma * al : sigma * al * m / (m - 1.0);
     }
     CK(h, upload<T>(&h->c, v));
+    if (en->m_field) {
+      for (int i = 0; i < N; ++i) v[i] = en->m_field[i] - 1.0;
+      CK(h, upload<T>(&h->m1f, v));
+    }
   }
   h->kappa_s = en->kappa;
   h->has_kappa = std::isfinite(en->kappa) ? 1 : 0;

@@ -33,6 +33,7 @@ struct jko_handle {
   int rx = 0, ry = 0;
   // per-cell energy constants
   void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
+  void* m1f = nullptr;          // per-cell m - 1 of the generalised entropies, or NULL
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;
   int has_kappa = 0;
@@ -75,6 +76,7 @@ inline ProxArgs<T> prox_args(const jko_handle* h) {
   P.sw = (const T*)h->sw;
   P.c = (const T*)h->c;
   P.kappa = (const T*)h->kap;
+  P.m1f = (const T*)h->m1f;
   P.kappa_s = (T)h->kappa_s;
   P.mask = h->mask;
   P.m1 = (T)(h->m - 1.0);

@@ -105,6 +105,9 @@ struct ProxArgs {
   int newton;          // Newton steps (power)
   int has_kappa;       // 1 if any congestion bound is finite
   T sigma;             // tau / gamma (derivatives with respect to w)
+  // generalised entropies with per-cell exponents (Eq. defn-gen-entropies,
+  // power kind): m_i - 1 per cell, with c = sigma alpha_i m_i; NULL = scalar m
+  const T* m1f = nullptr;
 };
 
 template <typename T> __device__ __forceinline__ T dev_exp(T x);
@@ -113,6 +116,9 @@ template <> __device__ __forceinline__ double dev_exp<double>(double x) { return
 template <typename T> __device__ __forceinline__ T dev_log(T x);
 template <> __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
 template <> __device__ __forceinline__ double dev_log<double>(double x) { return log(x); }
+template <typename T> __device__ __forceinline__ T dev_expm1(T x);
+template <> __device__ __forceinline__ float dev_expm1<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double dev_expm1<double>(double x) { return expm1(x); }
 
 template <typename T> __device__ __forceinline__ bool dev_finite(T x) { return isfinite(x); }
 
@@ -145,6 +151,55 @@ template <typename T> struct NewtonEps;
 template <> struct NewtonEps<float> { static constexpr float v = 1e-7f; };
 template <> struct NewtonEps<double> { static constexpr double v = 1e-15; };
 
+// y = log psi of the power kind for one cell with finite l = log s - sigma w,
+// and k = g'(y) - 1 for the derivative (dy/dl = 1 / (1 + k)).
+//  * scalar m (power form): y + beta e^{(m-1) y} = l, beta = sigma alpha m/(m-1);
+//    g is increasing and convex, so Newton from y0 = l (g(l) >= 0) decreases
+//    monotonically to the root without overshoot;
+//  * per-cell m (the paper's e_m, Eq. prox-psi as printed):
+//    y + c (e^{m1 y} - 1)/m1 = l, c = sigma alpha m, m1 = m - 1; at m1 = 0 it
+//    is Eq. prox-entropy, y = l/(1 + c).  From y0 = l/(1 + c), where
+//    g(y0) = c ((e^{m1 y0} - 1)/m1 - y0) >= 0, Newton again decreases
+//    monotonically (g increasing and convex); expm1 keeps small m1 exact.
+template <typename T>
+__device__ __forceinline__ T power_log_psi(const ProxArgs<T>& P, int idx, T l, T& k) {
+  const T c = P.c[idx];
+  if (P.m1f != nullptr) {
+    const T m1 = P.m1f[idx];
+    T y = l / (T(1) + c);
+    if (m1 > T(0)) {
+      for (int it = 0; it < P.newton; ++it) {
+        const T g = y + c * dev_expm1<T>(m1 * y) / m1 - l;
+        const T dy = g / (T(1) + c * dev_exp<T>(m1 * y));
+        y -= dy;
+        if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
+      }
+      k = c * dev_exp<T>(m1 * y);
+    } else {
+      k = c;
+    }
+    return y;
+  }
+  T y = l;
+  for (int it = 0; it < P.newton; ++it) {
+    const T e = c * dev_exp<T>(P.m1 * y);
+    const T dy = (y + e - l) / (T(1) + P.m1 * e);
+    y -= dy;
+    if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
+  }
+  k = P.m1 * c * dev_exp<T>(P.m1 * y);
+  return y;
+}
+
+// Limit of psi / s as s -> 0 for the power kind: e^{-sigma w} (scalar m);
+// e^{c/m1 - sigma w} for a per-cell m1 > 0, 0 at m1 = 0 (the entropy reading).
+template <typename T>
+__device__ __forceinline__ T power_ratio_at_zero(const ProxArgs<T>& P, int idx, T sw) {
+  if (P.m1f == nullptr) return dev_exp<T>(-sw);
+  const T m1 = P.m1f[idx];
+  return m1 > T(0) ? dev_exp<T>(P.c[idx] / m1 - sw) : T(0);
+}
+
 // a = Prox_{sigma f}(s) / s for one cell, extended continuously at s = 0
 // (Prop. 4.1, Eq. prox-entropy, Eq. prox-psi with the shift rule
 // Eq. prox-calculus-shift; clamp at kappa; 0 on the mask).
@@ -163,23 +218,14 @@ __device__ __forceinline__ T prox_ratio_e(const ProxArgs<T>& P, int idx, T s, T 
     const T sw = P.sw ? P.sw[idx] : T(0);
     a = dev_exp<T>(-(c * dev_log<T>(s) + sw) / (T(1) + c));
   } else {
-    // y = log psi solves y + beta e^{(m-1) y} = l, l = log s - sigma w.
-    // g is increasing and convex, so Newton from y0 = l (g(l) >= 0) decreases
-    // monotonically to the root without overshoot.
+    // power kind: y = log psi from power_log_psi, l = log s - sigma w
     const T sw = P.sw ? P.sw[idx] : T(0);
     if (!(s > T(0))) {
-      a = dev_exp<T>(-sw);  // limit of psi/s as s -> 0
+      a = power_ratio_at_zero<T>(P, idx, sw);
     } else {
       const T ls = dev_log<T>(s);
-      const T l = ls - sw;
-      const T beta = P.c[idx];
-      T y = l;
-      for (int k = 0; k < P.newton; ++k) {
-        const T e = beta * dev_exp<T>(P.m1 * y);
-        const T dy = (y + e - l) / (T(1) + P.m1 * e);
-        y -= dy;
-        if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
-      }
+      T k;
+      const T y = power_log_psi<T>(P, idx, ls - sw, k);
       a = dev_exp<T>(y - ls);
     }
   }
@@ -195,7 +241,8 @@ __device__ __forceinline__ T prox_ratio_e(const ProxArgs<T>& P, int idx, T s, T 
 // Derivatives of the ratio r(s, w) = Prox_{sigma f}(s)/s at one cell, for the
 // adjoint: (dr/ds, dr/dw).  Unclamped: crowd r = e^{-sigma w}; entropy from
 // Eq. prox-entropy; power from differentiating Eq. prox-psi (y = log psi):
-// dy/dl = 1/(1 + c), c = (m-1) beta psi^{m-1}.  Clamped at kappa (the forward's
+// dy/dl = 1/(1 + k), k = (m-1) beta psi^{m-1} (scalar m) or c psi^{m_i - 1}
+// (per-cell exponents), as power_log_psi returns it.  Clamped at kappa (the forward's
 // test a s > kappa): r = kappa/s.  Masked cells: 0.
 template <typename T, int EK>
 __device__ __forceinline__ void ratio_grad(const ProxArgs<T>& P, int idx, T s, T& rs, T& rw) {
@@ -216,23 +263,15 @@ __device__ __forceinline__ void ratio_grad(const ProxArgs<T>& P, int idx, T s, T
   } else {
     const T sw = P.sw ? P.sw[idx] : T(0);
     if (!(s > T(0))) {
-      a = dev_exp<T>(-sw);
+      a = power_ratio_at_zero<T>(P, idx, sw);
       dw = -P.sigma * a;
     } else {
       const T ls = dev_log<T>(s);
-      const T l = ls - sw;
-      const T beta = P.c[idx];
-      T y = l;
-      for (int k = 0; k < P.newton; ++k) {
-        const T e = beta * dev_exp<T>(P.m1 * y);
-        const T dy = (y + e - l) / (T(1) + P.m1 * e);
-        y -= dy;
-        if (!(dy > NewtonEps<T>::v * (T(1) + fabs(y)))) break;
-      }
+      T k;
+      const T y = power_log_psi<T>(P, idx, ls - sw, k);
       a = dev_exp<T>(y - ls);
-      const T c = P.m1 * beta * dev_exp<T>(P.m1 * y);
-      ds = -(a / s) * c / (T(1) + c);
-      dw = -P.sigma * a / (T(1) + c);
+      ds = -(a / s) * k / (T(1) + k);
+      dw = -P.sigma * a / (T(1) + k);
     }
   }
   if (P.has_kappa) {

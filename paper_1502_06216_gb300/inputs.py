@@ -186,7 +186,8 @@ def porous_problem(n: int, seed: int, gamma: float = 5e-4, tau: float = 5e-3,
                    n_steps=n_steps, max_iter=max_iter, tol=tol, name=name)
 
 
-def varying_exponent_problem(n: int, seed: int, gamma: float = 1e-3, tau: float = 5e-3,
+def varying_exponent_problem(n: int, seed: int, gamma: float = 1e-3,
+                             tau: Optional[float] = None,
                              vary: str = "m", n_steps: int = 20, max_iter: int = 300,
                              tol: float = 1e-6, ny: Optional[int] = None,
                              name: str = "genent") -> Problem:
@@ -195,7 +196,13 @@ def varying_exponent_problem(n: int, seed: int, gamma: float = 1e-3, tau: float 
     (cells i.i.d. uniform on [0, 1], normalised to unit mass); the profile
     t = distance to the domain boundary / its maximum (0 on the boundary, 1 in
     the centre) sets either the exponents m_i = 1 + t with weights 1
-    (vary = "m") or the weights b_i = 1 + 19 t with m_i = 1.4 (vary = "b")."""
+    (vary = "m") or the weights b_i = 1 + 19 t with m_i = 1.4 (vary = "b").
+    The paper prints no gamma or tau for this figure; the defaults take
+    sigma = tau / gamma = 5 for varying exponents and 0.5 for weights up to 20
+    (sigma b m / (m - 1) up to 350 at sigma = 5 drives the FP32 scalings out
+    of range, which the FP32 forms then report as JKO_ERR_NUMERIC)."""
+    if tau is None:
+        tau = 5e-3 if vary == "m" else 5e-4
     nx = n
     ny = n if ny is None else ny
     rng = np.random.default_rng(seed)
