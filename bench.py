@@ -285,15 +285,33 @@ def run_batched(args, jko, dev, barrier):
 
 def run_porous(args, jko, dev, barrier, peak_bf16, steps=5, warmup=2):
     """The non-linear-diffusion workload: porous medium m = 2 at 512^2 with
-    obstacles (gamma = 5e-4, tau = 5e-3, <= 500 pairs, tol 1e-6).  Per form:
-    pairs/s and JKO steps/s over `steps` steps after `warmup`, accuracy of one
-    step against the FP32 form from the same state, and the roofline of the
-    kernel that runs (loop kernel: executed tensor flops over 100 pairs)."""
-    import torch
+    obstacles (gamma = 5e-4, tau = 5e-3, <= 500 pairs, tol 1e-6)."""
     from paper_1502_06216_gb300 import inputs
     pb = inputs.config_problem(1)
-    out = {"workload": f"porous medium m=2, {pb.nx}x{pb.ny}, gamma={pb.gamma}, tau={pb.tau}, "
-                       f"15% obstacles, <={pb.max_iter} pairs/step, tol {pb.tol}"}
+    return run_diffusion(jko, dev, barrier, peak_bf16, pb,
+                         f"porous medium m=2, {pb.nx}x{pb.ny}, gamma={pb.gamma}, tau={pb.tau}, "
+                         f"15% obstacles, <={pb.max_iter} pairs/step, tol {pb.tol}", steps, warmup)
+
+
+def run_varying_exponents(args, jko, dev, barrier, peak_bf16, steps=5, warmup=2):
+    """Generalised entropies with per-cell exponents m_i = 1 + t in [1, 2]
+    (1 on the boundary, 2 in the centre), weights 1, white-noise q0 (Sec. 4.4,
+    Fig. fig-porous), 512^2, gamma = 1e-3, tau = 5e-3, <= 300 pairs, tol 1e-6."""
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.varying_exponent_problem(512, seed=inputs.seed_for(5), vary="m", tol=1e-6)
+    return run_diffusion(jko, dev, barrier, peak_bf16, pb,
+                         f"generalised entropies, per-cell exponents m in [1,2], {pb.nx}x{pb.ny}, "
+                         f"gamma={pb.gamma}, tau={pb.tau}, white-noise q0, <={pb.max_iter} "
+                         f"pairs/step, tol {pb.tol}", steps, warmup)
+
+
+def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
+    """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
+    accuracy of one step against the FP32 form from the same state, and the
+    roofline of the kernel that runs (loop kernel: executed tensor flops over
+    100 pairs)."""
+    import torch
+    out = {"workload": workload}
     outs, qs = {}, None
     for form in ALL_FORMS:
         h = jko.create_from_problem(pb, precision=jko.Precision[form])
@@ -571,6 +589,9 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
+    genent = None
+    if not args.no_porous and rank == 0 and ws == 1:
+        genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
     diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
@@ -607,6 +628,8 @@ def run_ours(args):
             line["batched"] = batched
         if porous is not None:
             line["porous"] = porous
+        if genent is not None:
+            line["varying_exponents"] = genent
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)
@@ -630,7 +653,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-porous", action="store_true",
-                    help="skip the non-linear-diffusion (porous 512^2) leg")
+                    help="skip the non-linear-diffusion legs (porous and varying exponents, 512^2)")
     ap.add_argument("--diff", action="store_true",
                     help="also time 200 Adam steps of potential recovery at 256^2 "
                          "(forward flow + implicit adjoint)")
