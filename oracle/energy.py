@@ -18,6 +18,9 @@ generalised entropies with spatially varying exponents and weights b_i =
   e_{m}(s) = s (s^{m-1} - m) / (m - 1)   if m > 1,
 written as it stands (no potential is split off: its -m/(m-1) slope has no
 finite limit as m -> 1, where e_m tends to the m = 1 entropy).
+
+``binary`` replaces the congestion box by the non-convex binary constraint
+f = iota_{{0, kappa}^N} + <w, p> (Eq. dfn-congestion-noncvx; no entropy term).
 """
 from __future__ import annotations
 
@@ -35,6 +38,8 @@ class Energy:
     alpha: Union[float, np.ndarray, None] = None
     mask: Optional[np.ndarray] = None
     m_field: Optional[np.ndarray] = None
+    binary: bool = False
+    binary_floor: float = 0.0   # test only: emptied cells keep floor * s (0 = the paper's rule)
 
     def arrays(self, N: int):
         """(w, kappa, alpha, mask) as float64 / bool arrays of length N."""
@@ -55,7 +60,8 @@ class Energy:
     @staticmethod
     def from_problem(pb) -> "Energy":
         return Energy(w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
-                      m_field=getattr(pb, "m_field", None))
+                      m_field=getattr(pb, "m_field", None),
+                      binary=bool(getattr(pb, "binary", False)))
 
 
 def paper_em_as_power(m: float, alpha, w=None, N: Optional[int] = None) -> Energy:

@@ -133,11 +133,15 @@ def step_dense(q: np.ndarray, xi_mat: np.ndarray, sigma: float, energy: Energy,
     for l in range(1, 2 * n_pairs + 1):
         x = pi * z_m2
         if l % 2 == 1:                               # Prox_{phi_1}: column rescale to q
-            new = x * (q / x.sum(axis=0))[None, :]
+            cs = x.sum(axis=0)                       # (an empty column stays empty)
+            new = x * np.where(cs > 0, q / np.where(cs > 0, cs, 1.0), 0.0)[None, :]
         else:                                        # Prox_{phi_2}: row rescale
             r = x.sum(axis=1)
-            new = x * (_prox.prox(r, sigma, energy) / r)[:, None]
-        z = z_m2 * pi / new
+            rs = np.where(r > 0, r, 1.0)
+            new = x * np.where(r > 0, _prox.prox(rs, sigma, energy) / rs, 0.0)[:, None]
+        # entries that are zero in xi stay zero; their correction is irrelevant
+        with np.errstate(divide="ignore", invalid="ignore"):
+            z = np.where(new > 0, z_m2 * pi / new, 1.0)
         z_m2, z_m1 = z_m1, z
         pi = new
     return pi.sum(axis=1), pi

@@ -31,6 +31,12 @@ For m1 > 0 the root is y = l + (c - W0(c e^{m1 l + c})) / m1 (``genent_lambertw`
 used where m1 >= 1e-3, the cancellation in c - W0 costing ~1e-16 c / m1);
 ``genent_bisect`` brackets the same root between min(l, 0) and l / (1 + c).
 At s = 0 the ratio's limit is e^{c/m1 - sigma w} for m1 > 0 and 0 for m1 = 0.
+
+Binary congestion (``Energy.binary``, Eq. dfn-congestion-noncvx): the KL prox
+of the indicator of {0, kappa} (the paper's threshold rule) at the shifted
+point psi = s e^{-sigma w}: p = kappa where psi > kappa / e, 0 where psi <
+kappa / e; at the tie psi = kappa / e, where both values are minimisers, the
+reading takes 0.  The ratio is kappa / s or 0 (0 at s = 0).
 """
 from __future__ import annotations
 
@@ -157,7 +163,10 @@ def prox(s: np.ndarray, sigma: float, energy: Energy, method: str = "lambertw") 
         beta = sigma * alpha * m / (m - 1.0)
         psi = (root_lambertw(l, beta, m) if method == "lambertw"
                else root_bisect(l, beta, m))
-    p = np.minimum(psi, kappa)
+    if energy.binary:
+        p = np.where(psi > kappa / np.e, kappa, energy.binary_floor * s)
+    else:
+        p = np.minimum(psi, kappa)
     p[mask] = 0.0
     return p
 
@@ -177,7 +186,7 @@ def ratio(s: np.ndarray, sigma: float, energy: Energy, method: str = "lambertw")
         m1, c = m_i[z] - 1.0, sigma * alpha[z] * m_i[z]
         with np.errstate(divide="ignore"):
             a[z] = np.where(m1 > 0, np.exp(c / np.where(m1 > 0, m1, 1.0) - sigma * w[z]), 0.0)
-    elif energy.m == 1:
+    elif energy.m == 1 or energy.binary:
         a[z] = 0.0
     else:
         a[z] = np.exp(-sigma * w[z])
@@ -215,3 +224,11 @@ def objective_1d_genent(p: float, s: float, sigma: float, w: float, kappa: float
         return np.inf
     kl = (p * np.log(p / s) if p > 0 else 0.0) - p + s
     return kl + sigma * (w * p + alpha * e_paper(p, m))
+
+
+def objective_binary(p: float, s: float, sigma: float, w: float, kappa: float) -> float:
+    """KL(p|s) + sigma (iota_{0,kappa}(p) + w p) for one cell (Eq. dfn-congestion-noncvx)."""
+    if p != 0.0 and p != kappa:
+        return np.inf
+    kl = (p * np.log(p / s) if p > 0 else 0.0) - p + s
+    return kl + sigma * w * p

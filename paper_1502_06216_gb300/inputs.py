@@ -19,6 +19,8 @@ synthetic):
 * varying exponents -- the paper's e_{m_i} with m_i = 1 + t (1 on the boundary,
   2 in the centre, t the normalised distance to the boundary) and weights 1,
   or m_i = 1.4 with weights 1 + 19 t; q white noise (Sec. 4.4, Fig. fig-porous).
+* binary congestion -- iota_{{0,kappa}} + <w,p> (Eq. dfn-congestion-noncvx),
+  kappa = max q0, the crowd disk and an optional two-room wall with a door.
 
 All arrays are float64, row-major ``[ny, nx]`` images flattened to length
 N = nx*ny (index y*nx + x), on the domain [0, lx] x [0, ly] sampled at cell
@@ -42,6 +44,7 @@ __all__ = [
     "batched_problems",
     "differentiation_problem",
     "varying_exponent_problem",
+    "binary_congestion_problem",
 ]
 
 
@@ -63,6 +66,7 @@ class Problem:
     mask: Optional[np.ndarray] = None    # (N,) uint8, 1 = obstacle cell
     m_field: Optional[np.ndarray] = None  # (N,) per-cell exponents >= 1 (the paper's
     #                                       e_{m_i} with weights alpha); overrides m
+    binary: bool = False                 # congestion iota_{{0,kappa}} instead of [0, kappa]
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -217,6 +221,32 @@ def varying_exponent_problem(n: int, seed: int, gamma: float = 1e-3,
         m_field, alpha = np.full(X.shape, 1.4), 1.0 + 19.0 * t
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q.ravel(), alpha=alpha.ravel(),
                    m_field=m_field.ravel(), n_steps=n_steps, max_iter=max_iter, tol=tol,
+                   name=name)
+
+
+def binary_congestion_problem(n: int, gamma: float = 1e-3, tau: float = 0.02,
+                              two_rooms: bool = True, n_steps: int = 20, max_iter: int = 300,
+                              tol: float = 1e-6, ny: Optional[int] = None,
+                              name: str = "binary") -> Problem:
+    """Crowd motion with the non-convex congestion iota_{{0,kappa}} + <w, p>
+    (Eq. dfn-congestion-noncvx) and kappa = max q0 (Sec. 4.5, Fig.
+    fig-nonconvex): q0 the uniform disk of radius 0.15 around c = (0.25, 0.5),
+    w = |x - t|^2 - |c - t|^2 with t = (0.85, 0.5) (zero at the disk centre: a
+    constant in w leaves the step's minimiser unchanged, as sum p = 1, but not
+    the non-convex iteration's first threshold decisions); with ``two_rooms`` a
+    wall at x in [0.48, 0.52] with a door at |y - 0.5| < 0.1 (obstacle cells)
+    separates the disk from the target."""
+    nx = n
+    ny = n if ny is None else ny
+    q0 = _disk(nx, ny, (0.25, 0.5), 0.15)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    w = ((X - 0.85) ** 2 + (Y - 0.5) ** 2 - 0.6 ** 2).ravel()
+    mask = None
+    if two_rooms:
+        wall = (np.abs(X - 0.5) < 0.02) & (np.abs(Y - 0.5) >= 0.1)
+        mask = wall.ravel().astype(np.uint8)
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w, kappa=float(q0.max()),
+                   mask=mask, binary=True, n_steps=n_steps, max_iter=max_iter, tol=tol,
                    name=name)
 
 
