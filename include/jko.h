@@ -117,6 +117,11 @@ typedef struct jko_energy {
                                  entropies sum_i alpha_i e_{m_i}(p_i), e_1(s) = s (log s - 1),
                                  e_m(s) = s (s^{m-1} - m)/(m-1) (Eq. defn-gen-entropies,
                                  Sec. 4.4); overrides m; NULL = the scalar m above */
+  int binary;                 /* 1: the congestion is the non-convex iota_{{0,kappa}} + <w,p>
+                                 (Eq. dfn-congestion-noncvx, Sec. 4.5): p_i in {0, kappa_i},
+                                 kappa_i where s_i e^{-sigma w_i} > kappa_i / e (0 at the tie);
+                                 needs m = 0, no m_field and a finite kappa; not for the
+                                 adjoint (the prox has no derivative) */
 } jko_energy;
 
 /* Per-step report. */

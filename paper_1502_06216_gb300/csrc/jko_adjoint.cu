@@ -324,6 +324,9 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
                            jko_step_info* infos) {
   if (!h || !p0_dev || n_steps < 1) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "bad arguments");
   if (h->tc) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "recording needs a JKO_FP32 or JKO_FP64 handle");
+  if (h->binary)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the binary congestion prox is discontinuous: no adjoint");
   const size_t es = h->es, N = (size_t)h->N;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);

@@ -315,6 +315,16 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
+  if (en->binary != 0 && en->binary != 1)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary must be 0 or 1");
+  if (en->binary && (en->m != 0.0 || en->m_field))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion takes no entropy term (m = 0)");
+  if (en->binary && !en->kappa_field && !std::isfinite(en->kappa))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion needs a finite kappa");
+  if (en->binary && en->kappa_field)
+    for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
+      if (!std::isfinite(en->kappa_field[i]))
+        return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion needs a finite kappa");
   if (en->m_field)
     for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
       if (!(en->m_field[i] >= 1.0) || !std::isfinite(en->m_field[i]))
@@ -364,6 +374,7 @@ jko_status build_energy(jko_handle* h, const jko_energy* en) {
   }
   h->kappa_s = en->kappa;
   h->has_kappa = std::isfinite(en->kappa) ? 1 : 0;
+  h->binary = en->binary;
   if (en->kappa_field) {
     bool any = false;
     for (int i = 0; i < N; ++i) { v[i] = en->kappa_field[i]; any |= std::isfinite(v[i]); }

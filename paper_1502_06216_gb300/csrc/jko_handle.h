@@ -34,6 +34,7 @@ struct jko_handle {
   // per-cell energy constants
   void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
   void* m1f = nullptr;          // per-cell m - 1 of the generalised entropies, or NULL
+  int binary = 0;               // congestion iota_{{0,kappa}} (Eq. dfn-congestion-noncvx)
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;
   int has_kappa = 0;
@@ -82,6 +83,7 @@ inline ProxArgs<T> prox_args(const jko_handle* h) {
   P.m1 = (T)(h->m - 1.0);
   P.newton = 40;
   P.has_kappa = h->has_kappa;
+  P.binary = h->binary;
   P.sigma = (T)(h->prm.tau / h->prm.gamma);
   return P;
 }

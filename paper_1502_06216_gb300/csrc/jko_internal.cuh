@@ -108,6 +108,8 @@ struct ProxArgs {
   // generalised entropies with per-cell exponents (Eq. defn-gen-entropies,
   // power kind): m_i - 1 per cell, with c = sigma alpha_i m_i; NULL = scalar m
   const T* m1f = nullptr;
+  // 1: the congestion is the non-convex iota_{{0,kappa}} (Eq. dfn-congestion-noncvx)
+  int binary = 0;
 };
 
 template <typename T> __device__ __forceinline__ T dev_exp(T x);
@@ -210,6 +212,12 @@ __device__ __forceinline__ T prox_ratio_e(const ProxArgs<T>& P, int idx, T s, T 
   if (P.mask != nullptr && P.mask[idx]) return T(0);
   T a;
   if (EK == EK_CROWD) {
+    if (P.binary) {
+      // Eq. dfn-congestion-noncvx with the shift rule: p = kappa where
+      // s e^{-sigma w} > kappa / e, else 0 (0 at the tie); a = p / s
+      const T kap = P.kappa ? P.kappa[idx] : P.kappa_s;
+      return (s * e > kap * T(0.36787944117144233)) ? ratio_div<T>(kap, s) : T(0);
+    }
     a = e;
   } else if (EK == EK_ENTROPY) {
     // psi = (s e^{-sigma w})^{1/(1+sigma alpha)} ; a = psi / s

@@ -402,7 +402,8 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
     const ProxArgs<float> P = args.P;
     // congestion/potential cells with a scalar bound and no mask: the common
     // case, evaluated without the per-cell field checks
-    const bool crowd_plain = EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr;
+    const bool crowd_plain =
+        EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr && P.binary == 0;
     uint32_t tc = 0, ec = 0;
     int bad = 0;
     bool free_pending = false;   // epi_free owed once the last stores have read smem
@@ -1056,7 +1057,7 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
           const int irow = m * PN + nb;
           float ev[16], pv[16];
           if (EK == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
-          if (EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr) {
+          if (EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr && P.binary == 0) {
             const bool hk = P.has_kappa != 0;
             const float kap = P.kappa_s;
 #pragma unroll

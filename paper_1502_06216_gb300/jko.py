@@ -63,7 +63,7 @@ class jko_energy(ctypes.Structure):
     _fields_ = [("w", ctypes.c_void_p), ("kappa", ctypes.c_double),
                 ("kappa_field", ctypes.c_void_p), ("m", ctypes.c_double),
                 ("alpha", ctypes.c_void_p), ("mask", ctypes.c_void_p),
-                ("m_field", ctypes.c_void_p)]
+                ("m_field", ctypes.c_void_p), ("binary", ctypes.c_int)]
 
 
 class jko_step_info(ctypes.Structure):
@@ -192,9 +192,10 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
-               tile: int = 0, m_field=None) -> Handle:
+               tile: int = 0, m_field=None, binary: bool = False) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
-    ``m_field``: per-cell exponents of the paper's generalised entropies."""
+    ``m_field``: per-cell exponents of the paper's generalised entropies;
+    ``binary``: the non-convex congestion iota_{{0,kappa}}."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
@@ -206,7 +207,7 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                    keep[1].ctypes.data if keep[1] is not None else None, float(m),
                    keep[2].ctypes.data if keep[2] is not None else None,
                    mk.ctypes.data if mk is not None else None,
-                   keep[3].ctypes.data if keep[3] is not None else None)
+                   keep[3].ctypes.data if keep[3] is not None else None, int(bool(binary)))
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
     _check(lib().jko_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), st,
@@ -332,7 +333,8 @@ def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(pb.kappa), None,
                    float(pb.m), keep[2].ctypes.data if keep[2] is not None else None,
                    mk.ctypes.data if mk is not None else None,
-                   keep[3].ctypes.data if keep[3] is not None else None)
+                   keep[3].ctypes.data if keep[3] is not None else None,
+                   int(bool(getattr(pb, "binary", False))))
     info = jko_step_info()
     st = lib().jko_step_noalloc(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e),
                                 ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(p_out.data_ptr()),
@@ -367,7 +369,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       check_every=check_every, precision=precision, renormalize=renormalize,
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
                       stream=stream, absorb=absorb, loop=loop, tile=tile,
-                      m_field=getattr(pb, "m_field", None))
+                      m_field=getattr(pb, "m_field", None),
+                      binary=bool(getattr(pb, "binary", False)))
 
 
 class Batch:
@@ -399,7 +402,8 @@ def _energy_struct(pb, keep):
     return jko_energy(w.ctypes.data if w is not None else None, float(pb.kappa), None, float(pb.m),
                       al.ctypes.data if al is not None else None,
                       mk.ctypes.data if mk is not None else None,
-                      mf.ctypes.data if mf is not None else None)
+                      mf.ctypes.data if mf is not None else None,
+                      int(bool(getattr(pb, "binary", False))))
 
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
