@@ -305,6 +305,66 @@ def run_varying_exponents(args, jko, dev, barrier, peak_bf16, steps=5, warmup=2)
                          f"pairs/step, tol {pb.tol}", steps, warmup)
 
 
+def form_roofline(jko, h, form, peak_bf16):
+    """Roofline of the kernel a handle runs: the loop kernel (executed tensor
+    flops over 100 pairs), else its slowest per-pass kernel."""
+    if form != "FP32":
+        ratio = 0.5 if form == "TF32" else 1.0
+        try:
+            ms, fl = jko.jko_profile_loop(h, pairs=100, reps=5)
+            kernel = "tc_loop_kernel (100 pairs)"
+        except jko.JKOError:
+            ms4, fl4 = jko.jko_profile_passes(h, reps=20)
+            k = max(range(4), key=lambda i: ms4[i])
+            ms, fl, kernel = ms4[k], fl4[k], f"tc_pass_kernel pass {k}"
+        ach = fl / (ms / 1e3) / 1e12
+        return {"kernel": kernel, "achieved": ach, "peak": peak_bf16 * ratio, "unit": "TFLOP/s",
+                "frac": ach / (peak_bf16 * ratio), "bound": "tensor"}
+    ms4, fl4 = jko.jko_profile_passes(h, reps=20)
+    k = max(range(4), key=lambda i: ms4[i])
+    ach = fl4[k] / (ms4[k] / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    return {"kernel": f"filter_pass pass {k}", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "bound": "alu"}
+
+
+def run_binary(args, jko, dev, barrier, peak_bf16, steps=5):
+    """Crowd motion with the non-convex binary congestion (Sec. 4.5): 512^2,
+    two rooms, kappa = max q0, gamma = 2.5e-4, tau = 5e-3, <= 300 pairs, tol
+    1e-6, no renormalisation.  Per form: pairs/s and JKO steps/s of one
+    `steps`-step flow (jko_flow) after a 1-step warm-up, its mass and the
+    cells whose value differs from the FP32 form's at the last step."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.binary_congestion_problem(512, gamma=2.5e-4, tau=5e-3, n_steps=steps)
+    out = {"workload": f"binary congestion (non-convex), two rooms, {pb.nx}x{pb.ny}, "
+                       f"gamma={pb.gamma}, tau={pb.tau}, kappa=max q0, <={pb.max_iter} "
+                       f"pairs/step, tol {pb.tol}, no renormalisation"}
+    finals = {}
+    for form in ALL_FORMS:
+        h = jko.create_from_problem(pb, precision=jko.Precision[form], renormalize=False)
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+        jko.jko_flow(h, p0, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pf, _, infos = jko.jko_flow(h, p0, steps)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for i in infos)
+        finals[form] = pf.double()
+        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                     "pairs_per_step": iters / steps, "mass_last_step": float(pf.double().sum()),
+                     "kernels": jko.jko_handle_info(h),
+                     "roofline": form_roofline(jko, h, form, peak_bf16)}
+        jko.jko_destroy(h)
+    for form in ALL_FORMS:
+        out[form]["cells_differing_from_fp32_form"] = int(
+            ((finals[form] - finals["FP32"]).abs() > 1e-3 * pb.kappa).sum())
+    return out
+
+
 def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
     """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
     accuracy of one step against the FP32 form from the same state, and the
@@ -336,29 +396,7 @@ def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
         outs[form], _ = jko.jko_step(h, qs.to(h.dtype))
         entry = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
                  "pairs_per_step": iters / steps, "kernels": jko.jko_handle_info(h)}
-        if form != "FP32":
-            try:
-                ms, fl = jko.jko_profile_loop(h, pairs=100, reps=5)
-                ach = fl / (ms / 1e3) / 1e12
-                ratio = 0.5 if form == "TF32" else 1.0
-                entry["roofline"] = {"kernel": "tc_loop_kernel (100 pairs)", "achieved": ach,
-                                     "peak": peak_bf16 * ratio, "unit": "TFLOP/s",
-                                     "frac": ach / (peak_bf16 * ratio), "bound": "tensor"}
-            except jko.JKOError:
-                ms4, fl4 = jko.jko_profile_passes(h, reps=20)
-                k = max(range(4), key=lambda i: ms4[i])
-                ratio = 0.5 if form == "TF32" else 1.0
-                ach = fl4[k] / (ms4[k] / 1e3) / 1e12
-                entry["roofline"] = {"kernel": f"tc_pass_kernel pass {k}", "achieved": ach,
-                                     "peak": peak_bf16 * ratio, "unit": "TFLOP/s",
-                                     "frac": ach / (peak_bf16 * ratio), "bound": "tensor"}
-        else:
-            ms4, fl4 = jko.jko_profile_passes(h, reps=20)
-            k = max(range(4), key=lambda i: ms4[i])
-            ach = fl4[k] / (ms4[k] / 1e3) / 1e12
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
-            entry["roofline"] = {"kernel": f"filter_pass pass {k}", "achieved": ach, "peak": peak,
-                                 "unit": "TFLOP/s", "frac": ach / peak, "bound": "alu"}
+        entry["roofline"] = form_roofline(jko, h, form, peak_bf16)
         out[form] = entry
         jko.jko_destroy(h)
     ref = outs["FP32"].double()
@@ -589,9 +627,10 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = None
+    genent = binary = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
+        binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
     diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
@@ -630,6 +669,8 @@ def run_ours(args):
             line["porous"] = porous
         if genent is not None:
             line["varying_exponents"] = genent
+        if binary is not None:
+            line["binary_congestion"] = binary
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)
@@ -653,7 +694,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-porous", action="store_true",
-                    help="skip the non-linear-diffusion legs (porous and varying exponents, 512^2)")
+                    help="skip the 512^2 legs beside the headline (porous, varying exponents, "
+                         "binary congestion)")
     ap.add_argument("--diff", action="store_true",
                     help="also time 200 Adam steps of potential recovery at 256^2 "
                          "(forward flow + implicit adjoint)")
