@@ -21,6 +21,8 @@ synthetic):
   or m_i = 1.4 with weights 1 + 19 t; q white noise (Sec. 4.4, Fig. fig-porous).
 * binary congestion -- iota_{{0,kappa}} + <w,p> (Eq. dfn-congestion-noncvx),
   kappa = max q0, the crowd disk and an optional two-room wall with a door.
+* Wasserstein attraction -- f = W_gamma(r, .) + iota_{[0,kappa]} (Sec. 5.2),
+  disks q0 and r, kappa = max q0, optional two-room wall.
 
 All arrays are float64, row-major ``[ny, nx]`` images flattened to length
 N = nx*ny (index y*nx + x), on the domain [0, lx] x [0, ly] sampled at cell
@@ -45,6 +47,7 @@ __all__ = [
     "differentiation_problem",
     "varying_exponent_problem",
     "binary_congestion_problem",
+    "attraction_problem",
 ]
 
 
@@ -67,6 +70,7 @@ class Problem:
     m_field: Optional[np.ndarray] = None  # (N,) per-cell exponents >= 1 (the paper's
     #                                       e_{m_i} with weights alpha); overrides m
     binary: bool = False                 # congestion iota_{{0,kappa}} instead of [0, kappa]
+    target: Optional[np.ndarray] = None  # (N,) target density r of the Wasserstein attraction
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -247,6 +251,28 @@ def binary_congestion_problem(n: int, gamma: float = 1e-3, tau: float = 0.02,
         mask = wall.ravel().astype(np.uint8)
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w, kappa=float(q0.max()),
                    mask=mask, binary=True, n_steps=n_steps, max_iter=max_iter, tol=tol,
+                   name=name)
+
+
+def attraction_problem(n: int, gamma: float = 1e-3, tau: float = 0.05, two_rooms: bool = False,
+                       n_steps: int = 20, max_iter: int = 300, tol: float = 1e-6,
+                       ny: Optional[int] = None, name: str = "attraction") -> Problem:
+    """Wasserstein attraction with congestion (Sec. 5.2, Fig. fig-wass-attrac):
+    f(p) = W_gamma(r, p) + iota_{[0,kappa]}(p), q0 the uniform disk of radius
+    0.15 at (0.25, 0.5), kappa = max q0, the target r the uniform disk of
+    radius 0.1 at (0.75, 0.5); with ``two_rooms`` the wall of
+    ``binary_congestion_problem`` (a door at |y - 0.5| < 0.1) separates them."""
+    nx = n
+    ny = n if ny is None else ny
+    q0 = _disk(nx, ny, (0.25, 0.5), 0.15)
+    r = _disk(nx, ny, (0.75, 0.5), 0.1)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    mask = None
+    if two_rooms:
+        wall = (np.abs(X - 0.5) < 0.02) & (np.abs(Y - 0.5) >= 0.1)
+        mask = wall.ravel().astype(np.uint8)
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, kappa=float(q0.max()),
+                   mask=mask, target=r, n_steps=n_steps, max_iter=max_iter, tol=tol,
                    name=name)
 
 
