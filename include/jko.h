@@ -122,6 +122,12 @@ typedef struct jko_energy {
                                  kappa_i where s_i e^{-sigma w_i} > kappa_i / e (0 at the tie);
                                  needs m = 0, no m_field and a finite kappa; not for the
                                  adjoint (the prox has no derivative) */
+  const double* target;       /* Wasserstein attraction with congestion (Sec. 5.2): f gains
+                                 W_gamma(r, p) toward this target density r (N entries, >= 0,
+                                 sum 1, 0 on the mask); the other terms form h of
+                                 Eq. prox-psi-attraction.  The step runs the generic diagonal
+                                 scaling with 2 couplings.  JKO_FP32 / JKO_FP64 only; not for
+                                 batches, the adjoint or jko_step_noalloc.  NULL = none */
 } jko_energy;
 
 /* Per-step report. */

@@ -327,6 +327,8 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   if (h->binary)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the binary congestion prox is discontinuous: no adjoint");
+  if (h->attract)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the Wasserstein attraction");
   const size_t es = h->es, N = (size_t)h->N;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);

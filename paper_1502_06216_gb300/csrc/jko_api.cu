@@ -117,12 +117,79 @@ cudaError_t enqueue_pass_simt(jko_handle* h, int which, cudaStream_t st) {
   return jko::simt_pass<T>(half == 0 ? jko::EPI_B : jko::EPI_A, h->ek, A, P, st);
 }
 
+// One filter pass of the CUDA-core form with explicit buffers: along y
+// ([ny][nx] -> [nx][ny]) or along x ([nx][ny] -> [ny][nx]).
+template <typename T>
+cudaError_t simt_pass_on(jko_handle* h, bool along_y, int epi, const void* in, void* out,
+                         const void* q, double* part, int decide, int nparts, cudaStream_t st) {
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  PassArgs<T> A{};
+  A.ctrl = h->ctrl;
+  A.part = part;
+  A.nparts = nparts;
+  A.decide = decide;
+  A.in = (const T*)in;
+  A.out = (T*)out;
+  A.q = (const T*)q;
+  A.p = (T*)h->p;
+  A.taps = (const T*)(along_y ? h->taps_y : h->taps_x);
+  A.n_i = along_y ? ny : nx;
+  A.n_j = along_y ? nx : ny;
+  A.r = along_y ? h->ry : h->rx;
+  return jko::simt_pass<T>(epi, h->ek, A, jko::prox_args<T>(h), st);
+}
+
+// One iteration of the Wasserstein attraction (Sec. 5.2, attraction.cu): the
+// b-updates of both couplings with their residual partials (the next pass
+// adds both sets for the stop rule), xi b_1 and xi b_2, then the joint prox.
+template <typename T>
+cudaError_t enqueue_pair_attraction(jko_handle* h, cudaStream_t st) {
+  const int nb = h->nparts_simt;
+  cudaError_t e;
+#define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a2, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b2, h->tgt, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 1, 2 * nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b2, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s2, nullptr, h->part, 0, nb, st));
+#undef JKO_TRY
+  return jko::launch_attraction_prox<T>(h->ek, (const T*)h->s1, (const T*)h->s2, (T*)h->a,
+                                        (T*)h->a2, (T*)h->p, h->N, h->prm.tau,
+                                        jko::prox_args<T>(h), h->ctrl, st);
+}
+
+// Start of an attraction step: b_1 = b_2 = 1, then the first joint prox from
+// s_1 = s_2 = xi 1 (the generic scaling's first half-step, Prop.
+// prop-implementation-generic, with a = b = 1).
+template <typename T>
+cudaError_t begin_attraction(jko_handle* h, cudaStream_t st) {
+  const long long N = h->N;
+  cudaError_t e = jko::launch_fill<T>((T*)h->b, T(1), N, st);
+  if (e == cudaSuccess) e = jko::launch_fill<T>((T*)h->b2, T(1), N, st);
+  if (e == cudaSuccess)
+    e = simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 0, 1, st);
+  if (e == cudaSuccess)
+    e = simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, 1, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->s2, h->s1, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = jko::launch_attraction_prox<T>(h->ek, (const T*)h->s1, (const T*)h->s2, (T*)h->a,
+                                       (T*)h->a2, (T*)h->p, N, h->prm.tau,
+                                       jko::prox_args<T>(h), h->ctrl, st);
+  return e;
+}
+
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
   if (h->tc) return jko::tc_enqueue_pass(h->tc, which, st);
   return h->fp64 ? enqueue_pass_simt<double>(h, which, st) : enqueue_pass_simt<float>(h, which, st);
 }
 
 cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
+  if (h->attract)
+    return h->fp64 ? enqueue_pair_attraction<double>(h, st) : enqueue_pair_attraction<float>(h, st);
   for (int k = 0; k < 4; ++k) {
     cudaError_t e = enqueue_pass(h, k, st);
     if (e != cudaSuccess) return e;
@@ -279,6 +346,7 @@ void free_handle(jko_handle* h) {
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
+                  h->a2, h->b2, h->tgt, h->s1, h->s2,
                   h->tape, h->adj, h->adj_red};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
@@ -315,6 +383,22 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
   if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
+  if (en->target) {
+    if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
+      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
+                     "the Wasserstein attraction runs on JKO_FP32 / JKO_FP64 only");
+    double tot = 0.0;
+    for (long long i = 0; i < (long long)g->nx * g->ny; ++i) {
+      const double v = en->target[i];
+      if (!(v >= 0) || !std::isfinite(v))
+        return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must be finite and >= 0");
+      if (en->mask && en->mask[i] && v != 0)
+        return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must vanish on the mask");
+      tot += v;
+    }
+    if (std::fabs(tot - 1.0) > 1e-3)
+      return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must sum to 1");
+  }
   if (en->binary != 0 && en->binary != 1)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary must be 0 or 1");
   if (en->binary && (en->m != 0.0 || en->m_field))
@@ -346,7 +430,8 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
 template <typename T>
 jko_status build_energy(jko_handle* h, const jko_energy* en) {
   const int N = h->N;
-  const double sigma = h->prm.tau / h->prm.gamma;
+  // the attraction's prox takes h with sigma / (1 + tau) (Eq. prox-psi-attraction)
+  const double sigma = h->prm.tau / h->prm.gamma / (en->target ? 1.0 + h->prm.tau : 1.0);
   h->m = en->m;
   h->ek = en->m_field ? jko::EK_POWER
           : en->m == 0.0 ? jko::EK_CROWD : (en->m == 1.0 ? jko::EK_ENTROPY : jko::EK_POWER);
@@ -427,6 +512,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   if (h->tc) {
     jko_status s2 = jko::tc_begin_step(h->tc, st) == cudaSuccess ? JKO_OK : JKO_ERR_CUDA;
     if (s2 != JKO_OK) return set_err(h, s2, "tensor-core step set-up failed");
+  } else if (h->attract) {
+    CK(h, begin_attraction<T>(h, st));
   } else {
     CK(h, jko::launch_fill<T>((T*)h->a, T(1), N, st));   // cold start a = 1 (Sec. 3.4)
   }
@@ -437,7 +524,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   int launched = 0, polled = 0;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   auto launch = [&]() -> cudaError_t {
-    h->kernels += h->use_loop ? 1LL : 4LL * C;
+    h->kernels += h->use_loop ? 1LL : (h->attract ? 9LL : 4LL) * C;
     cudaError_t e = launch_chunk(h, st);
     if (e != cudaSuccess) return e;
     const int slot = launched & 1;
@@ -591,8 +678,22 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   e = cudaMalloc((void**)&h->ctrl, sizeof(Ctrl));
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(ctrl)"));
   h->nparts_simt = jko::simt_pass_blocks(grid->nx, grid->ny);  // the b-update pass runs along x
+  h->attract = energy->target ? 1 : 0;
+  if (h->attract) {
+    void** more[] = {&h->a2, &h->b2, &h->s1, &h->s2};
+    for (void** pp : more) {
+      e = cudaMalloc(pp, bytes);
+      if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(image)"));
+      e = cudaMemset(*pp, 0, bytes);
+      if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
+    }
+    std::vector<double> r(energy->target, energy->target + h->N);
+    e = h->fp64 ? upload<double>(&h->tgt, r) : upload<float>(&h->tgt, r);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "upload of the target"));
+  }
   {
-    const int np = std::max(h->nparts_simt, jko::tc_partials(grid->nx, grid->ny));
+    const int np = std::max((h->attract ? 2 : 1) * h->nparts_simt,
+                            jko::tc_partials(grid->nx, grid->ny));
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
     h->part_cap = np;
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(partials)"));
@@ -1148,6 +1249,8 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
   for (int f = 0; f < n_flows; ++f) {
     if (params[f].check_every != params[0].check_every)
       return fail(batch_err(b, JKO_ERR_INVALID_ARG, "all flows must share check_every"));
+    if (energies[f].target)
+      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
     jko_handle* h = nullptr;
     jko_status s = jko_create(&grids[f], &params[f], &energies[f], stream, &h);
     if (s != JKO_OK) {

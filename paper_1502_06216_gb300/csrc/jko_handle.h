@@ -35,6 +35,10 @@ struct jko_handle {
   void *E = nullptr, *sw = nullptr, *c = nullptr, *kap = nullptr;
   void* m1f = nullptr;          // per-cell m - 1 of the generalised entropies, or NULL
   int binary = 0;               // congestion iota_{{0,kappa}} (Eq. dfn-congestion-noncvx)
+  // Wasserstein attraction (Sec. 5.2): second coupling's scalings, the target
+  // r and the two prox inputs xi b_m
+  int attract = 0;
+  void *a2 = nullptr, *b2 = nullptr, *tgt = nullptr, *s1 = nullptr, *s2 = nullptr;
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;
   int has_kappa = 0;

@@ -57,6 +57,13 @@ template <typename T>
 cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
                                   cudaStream_t st);
 
+// Wasserstein attraction (attraction.cu): p = Prox(s1^{1/(1+tau)} s2^{tau/(1+tau)}),
+// a_m = p / s_m, and the pair counter; returns at once once the step has stopped.
+template <typename T>
+cudaError_t launch_attraction_prox(int ek, const T* s1, const T* s2, T* a1, T* a2, T* p,
+                                   long long n, double tau, const ProxArgs<T>& P, Ctrl* ctrl,
+                                   cudaStream_t st);
+
 // Batched flows: copy the stop state of n control blocks into a contiguous
 // array (done flags only, or whole blocks).
 cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st);

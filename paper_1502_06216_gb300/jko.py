@@ -63,7 +63,8 @@ class jko_energy(ctypes.Structure):
     _fields_ = [("w", ctypes.c_void_p), ("kappa", ctypes.c_double),
                 ("kappa_field", ctypes.c_void_p), ("m", ctypes.c_double),
                 ("alpha", ctypes.c_void_p), ("mask", ctypes.c_void_p),
-                ("m_field", ctypes.c_void_p), ("binary", ctypes.c_int)]
+                ("m_field", ctypes.c_void_p), ("binary", ctypes.c_int),
+                ("target", ctypes.c_void_p)]
 
 
 class jko_step_info(ctypes.Structure):
@@ -192,22 +193,24 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
-               tile: int = 0, m_field=None, binary: bool = False) -> Handle:
+               tile: int = 0, m_field=None, binary: bool = False, target=None) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
-    ``binary``: the non-convex congestion iota_{{0,kappa}}."""
+    ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
+    density r of the Wasserstein attraction (Sec. 5.2)."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
                    int(absorb), int(loop), int(tile))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N),
-            _host_f64(m_field, N)]
+            _host_f64(m_field, N), _host_f64(target, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
                    keep[1].ctypes.data if keep[1] is not None else None, float(m),
                    keep[2].ctypes.data if keep[2] is not None else None,
                    mk.ctypes.data if mk is not None else None,
-                   keep[3].ctypes.data if keep[3] is not None else None, int(bool(binary)))
+                   keep[3].ctypes.data if keep[3] is not None else None, int(bool(binary)),
+                   keep[4].ctypes.data if keep[4] is not None else None)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
     _check(lib().jko_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), st,
@@ -328,13 +331,14 @@ def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
                    pb.max_iter if max_iter is None else max_iter, 0, int(Precision.FP32),
                    int(bool(renormalize)), 0)
     keep = [_host_f64(pb.w, N), None, _host_f64(pb.alpha, N),
-            _host_f64(getattr(pb, "m_field", None), N)]
+            _host_f64(getattr(pb, "m_field", None), N), _host_f64(getattr(pb, "target", None), N)]
     mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(pb.kappa), None,
                    float(pb.m), keep[2].ctypes.data if keep[2] is not None else None,
                    mk.ctypes.data if mk is not None else None,
                    keep[3].ctypes.data if keep[3] is not None else None,
-                   int(bool(getattr(pb, "binary", False))))
+                   int(bool(getattr(pb, "binary", False))),
+                   keep[4].ctypes.data if keep[4] is not None else None)
     info = jko_step_info()
     st = lib().jko_step_noalloc(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e),
                                 ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(p_out.data_ptr()),
@@ -370,7 +374,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       w=pb.w, kappa=pb.kappa, m=pb.m, alpha=pb.alpha, mask=pb.mask,
                       stream=stream, absorb=absorb, loop=loop, tile=tile,
                       m_field=getattr(pb, "m_field", None),
-                      binary=bool(getattr(pb, "binary", False)))
+                      binary=bool(getattr(pb, "binary", False)),
+                      target=getattr(pb, "target", None))
 
 
 class Batch:
@@ -398,12 +403,14 @@ def _energy_struct(pb, keep):
     w, al = _host_f64(pb.w, N), _host_f64(pb.alpha, N)
     mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
     mf = _host_f64(getattr(pb, "m_field", None), N)
-    keep += [w, al, mk, mf]
+    tg = _host_f64(getattr(pb, "target", None), N)
+    keep += [w, al, mk, mf, tg]
     return jko_energy(w.ctypes.data if w is not None else None, float(pb.kappa), None, float(pb.m),
                       al.ctypes.data if al is not None else None,
                       mk.ctypes.data if mk is not None else None,
                       mf.ctypes.data if mf is not None else None,
-                      int(bool(getattr(pb, "binary", False))))
+                      int(bool(getattr(pb, "binary", False))),
+                      tg.ctypes.data if tg is not None else None)
 
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
