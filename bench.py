@@ -365,6 +365,42 @@ def run_binary(args, jko, dev, barrier, peak_bf16, steps=5):
     return out
 
 
+def run_attraction(args, jko, dev, barrier, steps=5):
+    """Wasserstein attraction with congestion (Sec. 5.2, 2 couplings per step):
+    256^2, disk q0 toward a disk target r, kappa = max q0, gamma = 5e-3, tau =
+    0.3, <= 2000 pairs, tol 1e-6, on the FP32 CUDA-core form.  Pairs/s of one
+    `steps`-step flow after a 1-step warm-up, the roofline of its slowest
+    filter pass, and the last step against the FP64 form."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.attraction_problem(256, gamma=5e-3, tau=0.3, n_steps=steps, tol=1e-6,
+                                   max_iter=2000)
+    out = {"workload": f"Wasserstein attraction with congestion, {pb.nx}x{pb.ny}, gamma={pb.gamma}, "
+                       f"tau={pb.tau}, kappa=max q0, <={pb.max_iter} pairs/step, tol {pb.tol}"}
+    finals = {}
+    for form in ("FP32", "FP64"):
+        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+        jko.jko_flow(h, p0, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pf, _, infos = jko.jko_flow(h, p0, steps)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for i in infos)
+        finals[form] = pf.double()
+        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                     "pairs_per_step": iters / steps, "kernels_per_pair": 9}
+        if form == "FP32":
+            out[form]["roofline"] = form_roofline(jko, h, form, None)
+        jko.jko_destroy(h)
+    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
+                                               finals["FP64"].abs().sum())
+    return out
+
+
 def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
     """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
     accuracy of one step against the FP32 form from the same state, and the
@@ -627,10 +663,11 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = binary = None
+    genent = binary = attraction = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
         binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
+        attraction = run_attraction(args, jko, dev, barrier)
     diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
@@ -671,6 +708,8 @@ def run_ours(args):
             line["varying_exponents"] = genent
         if binary is not None:
             line["binary_congestion"] = binary
+        if attraction is not None:
+            line["wasserstein_attraction"] = attraction
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)
@@ -694,8 +733,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-porous", action="store_true",
-                    help="skip the 512^2 legs beside the headline (porous, varying exponents, "
-                         "binary congestion)")
+                    help="skip the legs beside the headline (porous, varying exponents, "
+                         "binary congestion, Wasserstein attraction)")
     ap.add_argument("--diff", action="store_true",
                     help="also time 200 Adam steps of potential recovery at 256^2 "
                          "(forward flow + implicit adjoint)")
