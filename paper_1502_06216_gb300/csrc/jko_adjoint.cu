@@ -135,6 +135,7 @@ cudaError_t xi_apply(jko_handle* h, const T* in, T* out, cudaStream_t st) {
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
   A.part = h->part;
+  A.latency = h->simt_latency;
   A.in = in;
   A.out = (T*)h->t1;
   A.taps = (const T*)h->taps_y;

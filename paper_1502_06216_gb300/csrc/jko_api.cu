@@ -98,6 +98,7 @@ cudaError_t enqueue_pass_simt(jko_handle* h, int which, cudaStream_t st) {
   A.part = h->part;
   A.nparts = h->nparts_simt;
   A.decide = which == 2 ? 1 : 0;  // the pass after the b-update takes the stop decision
+  A.latency = h->simt_latency;
   const int half = which >> 1;
   if ((which & 1) == 0) {
     // pass along y: in [ny][nx] -> t1 [nx][ny]
@@ -128,6 +129,7 @@ cudaError_t simt_pass_on(jko_handle* h, bool along_y, int epi, const void* in, v
   A.part = part;
   A.nparts = nparts;
   A.decide = decide;
+  A.latency = h->simt_latency;
   A.in = (const T*)in;
   A.out = (T*)out;
   A.q = (const T*)q;
@@ -1258,6 +1260,9 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
       snprintf(buf, sizeof buf, "flow %d: ", f);
       return fail(batch_err(b, s, buf + g_create_err));
     }
+    // other flows fill the GPU: the CUDA-core passes keep their throughput form
+    h->simt_latency = 0;
+    h->nparts_simt = jko::simt_pass_blocks(grids[f].nx, grids[f].ny, 0);
     b->h.push_back(h);
     b->max_iter = std::max(b->max_iter, params[f].max_iter);
   }

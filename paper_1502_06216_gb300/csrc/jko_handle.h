@@ -38,6 +38,7 @@ struct jko_handle {
   // Wasserstein attraction (Sec. 5.2): second coupling's scalings, the target
   // r and the two prox inputs xi b_m
   int attract = 0;
+  int simt_latency = 1;         // small CUDA-core passes in their latency form (0 in batches)
   void *a2 = nullptr, *b2 = nullptr, *tgt = nullptr, *s1 = nullptr, *s2 = nullptr;
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;

@@ -25,12 +25,15 @@ struct PassArgs {
   double* part;  // residual partials: one per block of the b-update pass
   int nparts;    // number of partials (read by the deciding pass)
   int decide;    // 1: this pass takes the stop decision (stop_gate)
+  int latency;   // 1: small images take the 4-output, shared-memory-staged variant
+                 // (a handle alone); 0: always 16 outputs per thread (flows of a
+                 // batch, where other flows fill the GPU)
 };
 
 int simt_tap_padding();
 // Blocks of a filter pass over an [n_i][n_j] input (= residual partials of the
 // b-update pass).
-int simt_pass_blocks(int n_i, int n_j);
+int simt_pass_blocks(int n_i, int n_j, int latency = 1);
 
 template <typename T>
 cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,

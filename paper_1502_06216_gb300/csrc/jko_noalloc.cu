@@ -251,6 +251,7 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
         A.part = part;
         A.nparts = nparts;
         A.decide = half == 1 ? 1 : 0;   // the pass after the b-update decides
+        A.latency = 1;                  // the form simt_pass_blocks counted (nparts)
         A.in = half == 0 ? img[S_A] : img[S_B];
         A.out = img[S_T1];
         A.taps = taps_y;

@@ -14,7 +14,9 @@
 //
 // Thread layout: a warp spans 32 consecutive j (coalesced loads of in[i][j]);
 // each thread computes RB consecutive outputs i' with a register window that
-// slides along i, so each input load feeds RB multiply-adds.  The taps are
+// slides along i, so each input load feeds RB multiply-adds.  RB = 16, or 4
+// where 16 would leave the grid under two blocks per SM (small images: more
+// threads, each tap sum in the same order, so the same bits).  The taps are
 // the 2r+1 values k(d), d = -r..r, held in shared memory (broadcast reads).
 #include "jko_internal.cuh"
 #include "jko_kernels.h"
@@ -23,11 +25,15 @@ namespace jko {
 
 namespace {
 
-constexpr int RB = 16;   // outputs per thread along the filtered axis
+constexpr int RB_MAX = 16;  // outputs per thread along the filtered axis (or 4)
 constexpr int BJ = 32;   // threads along the contiguous axis
 constexpr int BI = 4;    // thread rows per block
 
-template <typename T, int EPI, int EK>
+// TILE (small images): the block first stages its input rows [i_lo - r, i_lo + BI RB + r)
+// of its 32 columns in shared memory (coalesced, zeros outside the image), so
+// the tap loop reads shared memory instead of a chain of dependent global
+// loads; the same terms are added in the same order either way.
+template <typename T, int EPI, int EK, int RB, bool TILE>
 __global__ void __launch_bounds__(BJ * BI)
 filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   Ctrl* ctrl = A.ctrl;
@@ -50,7 +56,34 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
 #pragma unroll
   for (int o = 0; o < RB; ++o) acc[o] = T(0);
 
-  if (active) {
+  if constexpr (TILE) {
+    // rows [blk_lo - r, blk_lo + BI RB + r) of columns [blockIdx.x BJ, +BJ)
+    T* s_in = s_k + ntap;
+    const int r = A.r;
+    const int n_i = A.n_i;
+    const int blk_lo = blockIdx.y * BI * RB;
+    const int rows = BI * RB + 2 * r;
+    const int jc = blockIdx.x * BJ + threadIdx.x;
+    for (int rr = threadIdx.y; rr < rows; rr += BI) {
+      const int ii = blk_lo - r + rr;
+      s_in[rr * BJ + threadIdx.x] = (jc < A.n_j && ii >= 0 && ii < n_i)
+                                        ? __ldg(A.in + (size_t)ii * A.n_j + jc) : T(0);
+    }
+    __syncthreads();
+    if (active) {
+      // acc[o] = sum_t k[t] in[i0 + o + t - r]: row (i0 - blk_lo) + o + t of s_in
+      int t_lo = r - i0 - (RB - 1);
+      if (t_lo < 0) t_lo = 0;
+      int t_hi = n_i - 1 - i0 + r;
+      if (t_hi > 2 * r) t_hi = 2 * r;
+      const T* base = s_in + (i0 - blk_lo) * BJ + threadIdx.x;
+      for (int t = t_lo; t <= t_hi; ++t) {
+        const T k = s_k[t];
+#pragma unroll
+        for (int o = 0; o < RB; ++o) acc[o] = fma(k, base[(o + t) * BJ], acc[o]);
+      }
+    }
+  } else if (active) {
     // acc[o] = sum_{t=0}^{2r} k[t] in[i0 + o + t - r][j]; rows outside [0, n_i) are 0.
     const int r = A.r;
     const int n_i = A.n_i;
@@ -135,10 +168,23 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   if (EPI == EPI_A && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) ctrl->it = s_it + 1;
 }
 
-template <typename T, int EPI, int EK>
-cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
-  const size_t smem = sizeof(T) * (size_t)(2 * A.r + 1 + RB);
-  auto kern = filter_pass<T, EPI, EK>;
+// Outputs per thread for an [n_i][n_j] pass: 16 unless that leaves fewer than
+// two blocks per SM.
+int rb_for(int n_i, int n_j) {
+  const int blocks16 = ((n_j + BJ - 1) / BJ) * ((n_i + BI * 16 - 1) / (BI * 16));
+  return blocks16 < 2 * 152 ? 4 : 16;
+}
+
+// Shared memory of the tiled pass: taps + the staged rows.
+template <typename T, int RB>
+size_t tile_smem(int r) {
+  return sizeof(T) * ((size_t)(2 * r + 1 + RB) + (size_t)(BI * RB + 2 * r) * BJ);
+}
+
+template <typename T, int EPI, int EK, int RB, bool TILE>
+cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
+  const size_t smem = TILE ? tile_smem<T, RB>(A.r) : sizeof(T) * (size_t)(2 * A.r + 1 + RB);
+  auto kern = filter_pass<T, EPI, EK, RB, TILE>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -150,11 +196,27 @@ cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t 
   return cudaGetLastError();
 }
 
+// Small images (the 4-output variant) stage their rows in shared memory; on
+// large ones the untiled pass keeps more blocks resident and wins (1024^2
+// FP32: 5.5k against 3.8k pairs/s tiled, measured).  Flows of a batch keep the
+// 16-output form: there the other flows fill the GPU, and the extra blocks
+// and staged halos cost throughput (256-flow FP32 batch: 17.6k against 6.2k
+// flow-steps/s, measured).
+template <typename T, int EPI, int EK>
+cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
+  constexpr size_t kTileMax = 160 * 1024;
+  if (A.latency && rb_for(A.n_i, A.n_j) == 4)
+    return tile_smem<T, 4>(A.r) <= kTileMax ? launch_rb<T, EPI, EK, 4, true>(A, P, st)
+                                            : launch_rb<T, EPI, EK, 4, false>(A, P, st);
+  return launch_rb<T, EPI, EK, 16, false>(A, P, st);
+}
+
 }  // namespace
 
-int simt_tap_padding() { return RB; }
-int simt_pass_blocks(int n_i, int n_j) {
-  return ((n_j + BJ - 1) / BJ) * ((n_i + BI * RB - 1) / (BI * RB));
+int simt_tap_padding() { return RB_MAX; }
+int simt_pass_blocks(int n_i, int n_j, int latency) {
+  const int rb = latency ? rb_for(n_i, n_j) : 16;
+  return ((n_j + BJ - 1) / BJ) * ((n_i + BI * rb - 1) / (BI * rb));
 }
 
 template <typename T>
