@@ -57,12 +57,13 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   for (int o = 0; o < RB; ++o) acc[o] = T(0);
 
   if constexpr (TILE) {
-    // rows [blk_lo - r, blk_lo + BI RB + r) of columns [blockIdx.x BJ, +BJ)
+    // rows [blk_lo - r, blk_lo + BI RB + r + RB) of columns [blockIdx.x BJ, +BJ)
+    // (RB rows beyond the last used one: the window's last refill reads them)
     T* s_in = s_k + ntap;
     const int r = A.r;
     const int n_i = A.n_i;
     const int blk_lo = blockIdx.y * BI * RB;
-    const int rows = BI * RB + 2 * r;
+    const int rows = BI * RB + 2 * r + RB;
     const int jc = blockIdx.x * BJ + threadIdx.x;
     for (int rr = threadIdx.y; rr < rows; rr += BI) {
       const int ii = blk_lo - r + rr;
@@ -71,16 +72,27 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     }
     __syncthreads();
     if (active) {
-      // acc[o] = sum_t k[t] in[i0 + o + t - r]: row (i0 - blk_lo) + o + t of s_in
+      // the register window of the untiled pass, refilled from shared memory:
+      // input row ii sits at row ii - (blk_lo - r) of s_in
       int t_lo = r - i0 - (RB - 1);
       if (t_lo < 0) t_lo = 0;
       int t_hi = n_i - 1 - i0 + r;
       if (t_hi > 2 * r) t_hi = 2 * r;
-      const T* base = s_in + (i0 - blk_lo) * BJ + threadIdx.x;
-      for (int t = t_lo; t <= t_hi; ++t) {
-        const T k = s_k[t];
+      const T* col = s_in + (i0 - blk_lo) * BJ + threadIdx.x;   // row of t = 0
+      T win[2 * RB];
 #pragma unroll
-        for (int o = 0; o < RB; ++o) acc[o] = fma(k, base[(o + t) * BJ], acc[o]);
+      for (int u = 0; u < RB; ++u) win[u] = col[(t_lo + u) * BJ];
+      for (int t0 = t_lo; t0 <= t_hi; t0 += RB) {
+#pragma unroll
+        for (int u = 0; u < RB; ++u) win[RB + u] = col[(t0 + RB + u) * BJ];
+#pragma unroll
+        for (int dd = 0; dd < RB; ++dd) {
+          const T k = s_k[t0 + dd];
+#pragma unroll
+          for (int o = 0; o < RB; ++o) acc[o] = fma(k, win[o + dd], acc[o]);
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) win[u] = win[RB + u];
       }
     }
   } else if (active) {
@@ -178,14 +190,16 @@ int rb_for(int n_i, int n_j) {
 // Shared memory of the tiled pass: taps + the staged rows.
 template <typename T, int RB>
 size_t tile_smem(int r) {
-  return sizeof(T) * ((size_t)(2 * r + 1 + RB) + (size_t)(BI * RB + 2 * r) * BJ);
+  return sizeof(T) * ((size_t)(2 * r + 1 + RB) + (size_t)(BI * RB + 2 * r + RB) * BJ);
 }
 
 template <typename T, int EPI, int EK, int RB, bool TILE>
 cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
   const size_t smem = TILE ? tile_smem<T, RB>(A.r) : sizeof(T) * (size_t)(2 * A.r + 1 + RB);
   auto kern = filter_pass<T, EPI, EK, RB, TILE>;
-  if (smem > 48 * 1024) {
+  // opt in well below 48 KB: the kernel's static shared memory (stop gate,
+  // reductions) counts against the same default limit
+  if (smem > 32 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
