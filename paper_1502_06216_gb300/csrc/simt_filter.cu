@@ -212,7 +212,7 @@ cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t s
 
 // Small images (the 4-output variant) stage their rows in shared memory; on
 // large ones the untiled pass keeps more blocks resident and wins (1024^2
-// FP32: 5.5k against 3.8k pairs/s tiled, measured).  Flows of a batch keep the
+// FP32: 5.4k against 5.0k pairs/s tiled, measured).  Flows of a batch keep the
 // 16-output form: there the other flows fill the GPU, and the extra blocks
 // and staged halos cost throughput (256-flow FP32 batch: 17.6k against 6.2k
 // flow-steps/s, measured).
