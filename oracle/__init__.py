@@ -18,6 +18,10 @@ Plain, slow and written to be checked against the paper by eye:
                    Dykstra on couplings (Eq. iter-dystra-1/2); the flow (Eq. smooth-jko).
 * ``dual``      -- an independent brute-force solve of the step by maximising its
                    Fenchel dual with L-BFGS-B (primal-dual route of Prop. 3.1).
+* ``attraction`` -- Wasserstein attraction with congestion (Sec. 5.2): the
+                   generic diagonal scaling with 2 couplings, printed and reduced.
+* ``summation`` -- two densities coupled through the congestion of their sum
+                   (Sec. 5.3), the same scaling with 2 couplings.
 * ``mirror``    -- an independent brute-force solve of the step by entropic
                    mirror descent on the full coupling (smooth energies).
 * ``objective`` -- entropy E, W_gamma by a converged dense Sinkhorn, f, the step

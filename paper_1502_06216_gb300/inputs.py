@@ -23,6 +23,8 @@ synthetic):
   kappa = max q0, the crowd disk and an optional two-room wall with a door.
 * Wasserstein attraction -- f = W_gamma(r, .) + iota_{[0,kappa]} (Sec. 5.2),
   disks q0 and r, kappa = max q0, optional two-room wall.
+* two species -- h(p_1 + p_2) + <p_1, w_1> + <p_2, w_2> with h = iota_{[0,kappa]}
+  (Sec. 5.3, summation couplings): two rectangles heading for each other.
 
 All arrays are float64, row-major ``[ny, nx]`` images flattened to length
 N = nx*ny (index y*nx + x), on the domain [0, lx] x [0, ly] sampled at cell
@@ -48,6 +50,7 @@ __all__ = [
     "varying_exponent_problem",
     "binary_congestion_problem",
     "attraction_problem",
+    "two_species_problem",
 ]
 
 
@@ -71,6 +74,8 @@ class Problem:
     #                                       e_{m_i} with weights alpha); overrides m
     binary: bool = False                 # congestion iota_{{0,kappa}} instead of [0, kappa]
     target: Optional[np.ndarray] = None  # (N,) target density r of the Wasserstein attraction
+    species: int = 1                     # 2: q0 = [q_1, q_2] (2N), congestion on their sum
+    w2: Optional[np.ndarray] = None      # (N,) potential of the second species
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -274,6 +279,34 @@ def attraction_problem(n: int, gamma: float = 1e-3, tau: float = 0.05, two_rooms
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, kappa=float(q0.max()),
                    mask=mask, target=r, n_steps=n_steps, max_iter=max_iter, tol=tol,
                    name=name)
+
+
+def _rect(nx, ny, x0, x1, y0, y1):
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    return ((X >= x0) & (X <= x1) & (Y >= y0) & (Y <= y1)).astype(np.float64)
+
+
+def two_species_problem(n: int, gamma: float = 1e-3, tau: float = 0.02, kappa_factor: float = 1.0,
+                        n_steps: int = 20, max_iter: int = 300, tol: float = 1e-6,
+                        ny: Optional[int] = None, name: str = "two-species") -> Problem:
+    """Two crowds coupled through the congestion of their sum (Sec. 5.3,
+    summation couplings, Fig. of the two rectangles): species 1 uniform on
+    [0.1, 0.3] x [0.3, 0.7] heading for (0.85, 0.5), species 2 uniform on
+    [0.7, 0.9] x [0.3, 0.7] heading for (0.15, 0.5), each of mass 1/2,
+    w_m = |x - target_m|^2, kappa = factor * max(q_1 + q_2).  q0 = [q_1, q_2]."""
+    nx = n
+    ny = n if ny is None else ny
+    r1 = _rect(nx, ny, 0.1, 0.3, 0.3, 0.7)
+    r2 = _rect(nx, ny, 0.7, 0.9, 0.3, 0.7)
+    q1 = 0.5 * r1 / r1.sum()
+    q2 = 0.5 * r2 / r2.sum()
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    w1 = ((X - 0.85) ** 2 + (Y - 0.5) ** 2).ravel()
+    w2 = ((X - 0.15) ** 2 + (Y - 0.5) ** 2).ravel()
+    q0 = np.concatenate([q1.ravel(), q2.ravel()])
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w1, w2=w2,
+                   kappa=float(kappa_factor * (q1 + q2).max()), species=2, n_steps=n_steps,
+                   max_iter=max_iter, tol=tol, name=name)
 
 
 # Named workloads.  Sizes are parameters so that tests can run the same recipe
