@@ -401,6 +401,40 @@ def run_attraction(args, jko, dev, barrier, steps=5):
     return out
 
 
+def run_species(args, jko, dev, barrier, steps=5):
+    """Two crowds coupled through the congestion of their sum (Sec. 5.3,
+    summation couplings, 2 couplings per step): 256^2, two rectangles heading
+    for each other, kappa = max(q_1 + q_2), gamma = 2e-3, tau = 0.05, <= 2000
+    pairs, tol 1e-6, CUDA-core forms.  Pairs/s of one `steps`-step flow after a
+    1-step warm-up, and the last step of FP32 against FP64."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.two_species_problem(256, gamma=2e-3, tau=0.05, n_steps=steps, tol=1e-6,
+                                    max_iter=2000)
+    out = {"workload": f"two species, congestion on the sum, {pb.nx}x{pb.ny}, gamma={pb.gamma}, "
+                       f"tau={pb.tau}, kappa=max(q1+q2), <={pb.max_iter} pairs/step, tol {pb.tol}"}
+    finals = {}
+    for form in ("FP32", "FP64"):
+        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+        jko.jko_flow(h, p0, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pf, _, infos = jko.jko_flow(h, p0, steps)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for i in infos)
+        finals[form] = pf.double()
+        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                     "pairs_per_step": iters / steps, "kernels_per_pair": 9}
+        jko.jko_destroy(h)
+    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
+                                               finals["FP64"].abs().sum())
+    return out
+
+
 def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
     """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
     accuracy of one step against the FP32 form from the same state, and the
@@ -663,11 +697,12 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = binary = attraction = None
+    genent = binary = attraction = species = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
         binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
         attraction = run_attraction(args, jko, dev, barrier)
+        species = run_species(args, jko, dev, barrier)
     diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
@@ -710,6 +745,8 @@ def run_ours(args):
             line["binary_congestion"] = binary
         if attraction is not None:
             line["wasserstein_attraction"] = attraction
+        if species is not None:
+            line["two_species"] = species
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)
@@ -734,7 +771,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-porous", action="store_true",
                     help="skip the legs beside the headline (porous, varying exponents, "
-                         "binary congestion, Wasserstein attraction)")
+                         "binary congestion, Wasserstein attraction, two species)")
     ap.add_argument("--diff", action="store_true",
                     help="also time 200 Adam steps of potential recovery at 256^2 "
                          "(forward flow + implicit adjoint)")

@@ -128,6 +128,14 @@ typedef struct jko_energy {
                                  Eq. prox-psi-attraction.  The step runs the generic diagonal
                                  scaling with 2 couplings.  JKO_FP32 / JKO_FP64 only; not for
                                  batches, the adjoint or jko_step_noalloc.  NULL = none */
+  int species;                /* 2: two densities coupled through the congestion of their sum,
+                                 f = iota_{[0,kappa]}(p_1 + p_2) + <p_1, w> + <p_2, w2>
+                                 (Sec. 5.3, summation couplings): every state image (q, p,
+                                 trajectories) holds [p_1, p_2], 2 N entries, of total mass 1;
+                                 scalar kappa only (no kappa_field, mask, entropy, binary or
+                                 target); JKO_FP32 / JKO_FP64; not for batches, the adjoint or
+                                 jko_step_noalloc.  0 or 1: one density */
+  const double* w2;           /* potential of the second species (N entries); NULL = 0 */
 } jko_energy;
 
 /* Per-step report. */

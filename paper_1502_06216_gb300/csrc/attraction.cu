@@ -51,7 +51,54 @@ __global__ void __launch_bounds__(NT) attraction_prox_kernel(const T* s1, const 
   if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->it = s_it + 1;
 }
 
+// Two densities coupled through the congestion of their sum (Sec. 5.3): with
+// a~_m = s_m e^{-sigma w_m}, p_m = a~_m min(1, kappa / (a~_1 + a~_2)) and
+// a_m = p_m / s_m = e^{-sigma w_m} min(1, ...) (no division by s_m).
+template <typename T>
+__global__ void __launch_bounds__(NT) species_prox_kernel(const T* s1, const T* s2, const T* E1,
+                                                          const T* E2, T* a1, T* a2, T* p,
+                                                          long long n, T kappa, int has_kappa,
+                                                          Ctrl* ctrl) {
+  __shared__ int s_it;
+  if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T e1 = E1 ? E1[i] : T(1), e2 = E2 ? E2[i] : T(1);
+    const T t1 = s1[i] * e1, t2 = s2[i] * e2;
+    const T t = t1 + t2;
+    const T f = (has_kappa && t > kappa) ? kappa / t : T(1);
+    a1[i] = e1 * f;
+    a2[i] = e2 * f;
+    p[i] = t1 * f;
+    p[n + i] = t2 * f;
+    bad |= !dev_finite(t1 * f) || !dev_finite(t2 * f);
+  }
+  bad = warp_or(bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->it = s_it + 1;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,
+                                T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
+                                cudaStream_t st) {
+  long long g = (n + NT - 1) / NT;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  species_prox_kernel<T><<<(int)g, NT, 0, st>>>(s1, s2, E1, E2, a1, a2, p, n, (T)kappa,
+                                                has_kappa, ctrl);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_species_prox<float>(const float*, const float*, const float*,
+                                               const float*, float*, float*, float*, long long,
+                                               double, int, Ctrl*, cudaStream_t);
+template cudaError_t launch_species_prox<double>(const double*, const double*, const double*,
+                                                const double*, double*, double*, double*,
+                                                long long, double, int, Ctrl*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_attraction_prox(int ek, const T* s1, const T* s2, T* a1, T* a2, T* p,

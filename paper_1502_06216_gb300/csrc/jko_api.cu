@@ -184,12 +184,56 @@ cudaError_t begin_attraction(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
+// Two species (Sec. 5.3): b_1 = q_1 / xi a_1, b_2 = q_2 / xi a_2 with their
+// residual partials, xi b_1, xi b_2, then the joint prox on the sum.
+template <typename T>
+cudaError_t enqueue_pair_species(jko_handle* h, cudaStream_t st) {
+  const int nb = h->nparts_simt;
+  const T* q2 = (const T*)h->q + h->N;
+  cudaError_t e;
+#define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a2, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b2, q2, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 1, 2 * nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b2, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s2, nullptr, h->part, 0, nb, st));
+#undef JKO_TRY
+  return jko::launch_species_prox<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->E,
+                                     (const T*)h->E2, (T*)h->a, (T*)h->a2, (T*)h->p, h->N,
+                                     h->kappa_s, h->has_kappa, h->ctrl, st);
+}
+
+// Start of a two-species step: b_1 = b_2 = 1, the first joint prox from
+// s_1 = s_2 = xi 1.
+template <typename T>
+cudaError_t begin_species(jko_handle* h, cudaStream_t st) {
+  const long long N = h->N;
+  cudaError_t e = jko::launch_fill<T>((T*)h->b, T(1), N, st);
+  if (e == cudaSuccess) e = jko::launch_fill<T>((T*)h->b2, T(1), N, st);
+  if (e == cudaSuccess)
+    e = simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 0, 1, st);
+  if (e == cudaSuccess)
+    e = simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, 1, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->s2, h->s1, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = jko::launch_species_prox<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->E,
+                                    (const T*)h->E2, (T*)h->a, (T*)h->a2, (T*)h->p, N,
+                                    h->kappa_s, h->has_kappa, h->ctrl, st);
+  return e;
+}
+
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
   if (h->tc) return jko::tc_enqueue_pass(h->tc, which, st);
   return h->fp64 ? enqueue_pass_simt<double>(h, which, st) : enqueue_pass_simt<float>(h, which, st);
 }
 
 cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
+  if (h->species == 2)
+    return h->fp64 ? enqueue_pair_species<double>(h, st) : enqueue_pair_species<float>(h, st);
   if (h->attract)
     return h->fp64 ? enqueue_pair_attraction<double>(h, st) : enqueue_pair_attraction<float>(h, st);
   for (int k = 0; k < 4; ++k) {
@@ -348,7 +392,7 @@ void free_handle(jko_handle* h) {
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
-                  h->a2, h->b2, h->tgt, h->s1, h->s2,
+                  h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
                   h->tape, h->adj, h->adj_red};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
@@ -401,6 +445,18 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
     if (std::fabs(tot - 1.0) > 1e-3)
       return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must sum to 1");
   }
+  if (en->species < 0 || en->species > 2)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "species must be 0, 1 or 2");
+  if (en->species == 2) {
+    if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
+      return set_err(nullptr, JKO_ERR_UNSUPPORTED, "two species run on JKO_FP32 / JKO_FP64 only");
+    if (en->m != 0.0 || en->m_field || en->binary || en->target || en->kappa_field || en->mask)
+      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
+                     "two species take a scalar congestion bound and potentials only");
+    if (en->w2)
+      for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
+        if (!std::isfinite(en->w2[i])) return set_err(nullptr, JKO_ERR_INVALID_ARG, "w2 must be finite");
+  }
   if (en->binary != 0 && en->binary != 1)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary must be 0 or 1");
   if (en->binary && (en->m != 0.0 || en->m_field))
@@ -441,6 +497,10 @@ jko_status build_energy(jko_handle* h, const jko_energy* en) {
   if (h->ek == jko::EK_CROWD) {
     for (int i = 0; i < N; ++i) v[i] = std::exp(-sigma * (en->w ? en->w[i] : 0.0));
     CK(h, upload<T>(&h->E, v));
+    if (en->species == 2) {
+      for (int i = 0; i < N; ++i) v[i] = std::exp(-sigma * (en->w2 ? en->w2[i] : 0.0));
+      CK(h, upload<T>(&h->E2, v));
+    }
   } else {
     if (en->w) {
       for (int i = 0; i < N; ++i) v[i] = sigma * en->w[i];
@@ -497,6 +557,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   if (validate) {
     CK(h, jko::launch_validate<T>(q_in, N, P, h->ctrl, st));
+    if (h->species == 2) CK(h, jko::launch_validate<T>(q_in + N, N, P, h->ctrl, st));
     CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     const Ctrl& c = h->poll[0];
@@ -510,10 +571,12 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   }
   CK(h, cudaEventRecord(h->ev0, st));
   if ((const void*)q_in != h->q)
-    CK(h, cudaMemcpyAsync(h->q, q_in, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->q, q_in, h->ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (h->tc) {
     jko_status s2 = jko::tc_begin_step(h->tc, st) == cudaSuccess ? JKO_OK : JKO_ERR_CUDA;
     if (s2 != JKO_OK) return set_err(h, s2, "tensor-core step set-up failed");
+  } else if (h->species == 2) {
+    CK(h, begin_species<T>(h, st));
   } else if (h->attract) {
     CK(h, begin_attraction<T>(h, st));
   } else {
@@ -526,7 +589,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   int launched = 0, polled = 0;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   auto launch = [&]() -> cudaError_t {
-    h->kernels += h->use_loop ? 1LL : (h->attract ? 9LL : 4LL) * C;
+    h->kernels += h->use_loop ? 1LL : (h->attract || h->species == 2 ? 9LL : 4LL) * C;
     cudaError_t e = launch_chunk(h, st);
     if (e != cudaSuccess) return e;
     const int slot = launched & 1;
@@ -554,8 +617,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
       return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
   }
 
-  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, N, P, h->ctrl, h->part, h->part_cap, st));
-  if (p_out) CK(h, jko::launch_finalize_write<T>((const T*)h->p, p_out, N, h->prm.renormalize, h->ctrl, st));
+  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part, h->part_cap, st));
+  if (p_out) CK(h, jko::launch_finalize_write<T>((const T*)h->p, p_out, h->ns, h->prm.renormalize, h->ctrl, st));
   CK(h, cudaEventRecord(h->ev1, st));
   CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
@@ -608,7 +671,7 @@ int worse(int a, int b) {
 template <typename T>
 jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_final,
                      jko_step_info* infos) {
-  const long long N = h->N;
+  const long long N = h->ns;   // elements of a state image
   const T* q = p0;
   int worst = JKO_OK;
   for (int t = 0; t < n_steps; ++t) {
@@ -656,6 +719,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   h->grid = *grid;
   h->prm = *params;
   h->N = grid->nx * grid->ny;
+  h->species = energy->species == 2 ? 2 : 1;
+  h->ns = (long long)h->species * h->N;
   h->prec = params->precision;
   h->fp64 = params->precision == JKO_FP64;
   h->es = h->fp64 ? 8 : 4;
@@ -672,16 +737,18 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   const size_t bytes = h->es * (size_t)h->N;
   void** imgs[] = {&h->a, &h->b, &h->t1, &h->p, &h->q};
   for (void** pp : imgs) {
-    e = cudaMalloc(pp, bytes);
+    // p and q hold a state image: both species when there are two
+    const size_t nb = (pp == &h->p || pp == &h->q) ? h->es * (size_t)h->ns : bytes;
+    e = cudaMalloc(pp, nb);
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(image)"));
-    e = cudaMemset(*pp, 0, bytes);
+    e = cudaMemset(*pp, 0, nb);
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
   }
   e = cudaMalloc((void**)&h->ctrl, sizeof(Ctrl));
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(ctrl)"));
   h->nparts_simt = jko::simt_pass_blocks(grid->nx, grid->ny);  // the b-update pass runs along x
   h->attract = energy->target ? 1 : 0;
-  if (h->attract) {
+  if (h->attract || h->species == 2) {
     void** more[] = {&h->a2, &h->b2, &h->s1, &h->s2};
     for (void** pp : more) {
       e = cudaMalloc(pp, bytes);
@@ -689,12 +756,14 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       e = cudaMemset(*pp, 0, bytes);
       if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
     }
-    std::vector<double> r(energy->target, energy->target + h->N);
-    e = h->fp64 ? upload<double>(&h->tgt, r) : upload<float>(&h->tgt, r);
-    if (e != cudaSuccess) return fail(cuda_err(h, e, "upload of the target"));
+    if (h->attract) {
+      std::vector<double> r(energy->target, energy->target + h->N);
+      e = h->fp64 ? upload<double>(&h->tgt, r) : upload<float>(&h->tgt, r);
+      if (e != cudaSuccess) return fail(cuda_err(h, e, "upload of the target"));
+    }
   }
   {
-    const int np = std::max((h->attract ? 2 : 1) * h->nparts_simt,
+    const int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
                             jko::tc_partials(grid->nx, grid->ny));
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
     h->part_cap = np;
@@ -803,7 +872,7 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
   if (!p0_host || n_steps < 0) return set_err(h, JKO_ERR_INVALID_ARG, "NULL p0 or n_steps < 0");
   DeviceGuard dg(h->device);
   h->err.clear();
-  const size_t bytes = h->es * (size_t)h->N;
+  const size_t bytes = h->es * (size_t)h->ns;
   if (!h->stage_in) CK(h, cudaMalloc(&h->stage_in, bytes));
   if (!h->stage_out) CK(h, cudaMalloc(&h->stage_out, bytes));
   cudaStream_t st = h->stream;
@@ -1253,6 +1322,8 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
       return fail(batch_err(b, JKO_ERR_INVALID_ARG, "all flows must share check_every"));
     if (energies[f].target)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
+    if (energies[f].species == 2)
+      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "two species are not batched"));
     jko_handle* h = nullptr;
     jko_status s = jko_create(&grids[f], &params[f], &energies[f], stream, &h);
     if (s != JKO_OK) {

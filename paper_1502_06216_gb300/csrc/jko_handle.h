@@ -39,6 +39,9 @@ struct jko_handle {
   // r and the two prox inputs xi b_m
   int attract = 0;
   int simt_latency = 1;         // small CUDA-core passes in their latency form (0 in batches)
+  int species = 1;              // 2: two densities coupled through their sum (Sec. 5.3)
+  void* E2 = nullptr;           // e^{-sigma w2} of the second species
+  long long ns = 0;             // elements of a state image: N, or 2 N for two species
   void *a2 = nullptr, *b2 = nullptr, *tgt = nullptr, *s1 = nullptr, *s2 = nullptr;
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;

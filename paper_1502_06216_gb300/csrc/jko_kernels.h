@@ -67,6 +67,13 @@ cudaError_t launch_attraction_prox(int ek, const T* s1, const T* s2, T* a1, T* a
                                    long long n, double tau, const ProxArgs<T>& P, Ctrl* ctrl,
                                    cudaStream_t st);
 
+// Two species (attraction.cu): p = [p_1, p_2] = a~_m min(1, kappa/(a~_1 + a~_2)),
+// a~_m = s_m E_m (E_m = e^{-sigma w_m}, NULL = 1); a_m = E_m min(...).
+template <typename T>
+cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,
+                                T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
+                                cudaStream_t st);
+
 // Batched flows: copy the stop state of n control blocks into a contiguous
 // array (done flags only, or whole blocks).
 cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st);

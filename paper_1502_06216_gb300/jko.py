@@ -64,7 +64,8 @@ class jko_energy(ctypes.Structure):
                 ("kappa_field", ctypes.c_void_p), ("m", ctypes.c_double),
                 ("alpha", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("m_field", ctypes.c_void_p), ("binary", ctypes.c_int),
-                ("target", ctypes.c_void_p)]
+                ("target", ctypes.c_void_p), ("species", ctypes.c_int),
+                ("w2", ctypes.c_void_p)]
 
 
 class jko_step_info(ctypes.Structure):
@@ -165,10 +166,12 @@ def _current_stream():
 class Handle:
     """Owns a jko_handle*; keeps the parameters used to create it."""
 
-    def __init__(self, ptr: ctypes.c_void_p, nx: int, ny: int, precision: Precision):
+    def __init__(self, ptr: ctypes.c_void_p, nx: int, ny: int, precision: Precision,
+                 species: int = 1):
         self.ptr = ptr
         self.nx, self.ny = nx, ny
-        self.N = nx * ny
+        self.cells = nx * ny                             # elements of a field (w, kappa)
+        self.N = self.cells * (2 if species == 2 else 1)  # elements of a state image
         self.precision = Precision(precision)
 
     @property
@@ -193,37 +196,42 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                precision: int = Precision.FP32, renormalize: bool = True,
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
-               tile: int = 0, m_field=None, binary: bool = False, target=None) -> Handle:
+               tile: int = 0, m_field=None, binary: bool = False, target=None,
+               species: int = 1, w2=None) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
     ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
-    density r of the Wasserstein attraction (Sec. 5.2)."""
+    density r of the Wasserstein attraction (Sec. 5.2); ``species = 2`` with
+    ``w2``: two densities coupled through the congestion of their sum (Sec. 5.3),
+    whose state images hold [p_1, p_2]."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly)
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
                    int(absorb), int(loop), int(tile))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N),
-            _host_f64(m_field, N), _host_f64(target, N)]
+            _host_f64(m_field, N), _host_f64(target, N), _host_f64(w2, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
     e = jko_energy(keep[0].ctypes.data if keep[0] is not None else None, float(kappa),
                    keep[1].ctypes.data if keep[1] is not None else None, float(m),
                    keep[2].ctypes.data if keep[2] is not None else None,
                    mk.ctypes.data if mk is not None else None,
                    keep[3].ctypes.data if keep[3] is not None else None, int(bool(binary)),
-                   keep[4].ctypes.data if keep[4] is not None else None)
+                   keep[4].ctypes.data if keep[4] is not None else None, int(species),
+                   keep[5].ctypes.data if keep[5] is not None else None)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
     _check(lib().jko_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), st,
                             ctypes.byref(out)))
-    return Handle(out, nx, ny, precision)
+    return Handle(out, nx, ny, precision, species)
 
 
-def _dev_image(h: Handle, t, name):
+def _dev_image(h: Handle, t, name, n=None):
     import torch
+    n = h.N if n is None else n
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dtype != h.dtype or not t.is_contiguous() or t.numel() < h.N:
-        raise TypeError(f"{name} must be a contiguous {h.dtype} tensor of {h.N} elements")
+    if t.dtype != h.dtype or not t.is_contiguous() or t.numel() < n:
+        raise TypeError(f"{name} must be a contiguous {h.dtype} tensor of {n} elements")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -338,7 +346,8 @@ def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
                    mk.ctypes.data if mk is not None else None,
                    keep[3].ctypes.data if keep[3] is not None else None,
                    int(bool(getattr(pb, "binary", False))),
-                   keep[4].ctypes.data if keep[4] is not None else None)
+                   keep[4].ctypes.data if keep[4] is not None else None,
+                   int(getattr(pb, "species", 1)))
     info = jko_step_info()
     st = lib().jko_step_noalloc(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e),
                                 ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(p_out.data_ptr()),
@@ -375,7 +384,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       stream=stream, absorb=absorb, loop=loop, tile=tile,
                       m_field=getattr(pb, "m_field", None),
                       binary=bool(getattr(pb, "binary", False)),
-                      target=getattr(pb, "target", None))
+                      target=getattr(pb, "target", None),
+                      species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None))
 
 
 class Batch:
@@ -410,7 +420,8 @@ def _energy_struct(pb, keep):
                       mk.ctypes.data if mk is not None else None,
                       mf.ctypes.data if mf is not None else None,
                       int(bool(getattr(pb, "binary", False))),
-                      tg.ctypes.data if tg is not None else None)
+                      tg.ctypes.data if tg is not None else None,
+                      int(getattr(pb, "species", 1)))
 
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
@@ -480,7 +491,7 @@ def jko_batch_destroy(b: Batch) -> None:
 
 def jko_set_potential(h: Handle, w) -> None:
     """Replaces the potential w (host float64 copy of any array-like)."""
-    wh = _host_f64(np.asarray(w, np.float64).reshape(-1), h.N)
+    wh = _host_f64(np.asarray(w, np.float64).reshape(-1), h.cells)
     _check(lib().jko_set_potential(h.ptr, ctypes.c_void_p(wh.ctypes.data)), h.ptr)
 
 
@@ -490,7 +501,7 @@ def jko_set_potential_device(h: Handle, w) -> None:
     wd = w.detach().to(h.dtype).contiguous()
     L = lib()
     _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
-    _check(L.jko_set_potential_device(h.ptr, _dev_image(h, wd, "w")), h.ptr)
+    _check(L.jko_set_potential_device(h.ptr, _dev_image(h, wd, "w", h.cells)), h.ptr)
     return wd
 
 
@@ -510,7 +521,7 @@ def jko_flow_backward(h: Handle, grad_final, want_p0: bool = True, want_w: bool 
     """dL/dp_0 and dL/dw of the last recorded flow, given dL/dp_n."""
     import torch
     gp = torch.empty(h.N, dtype=h.dtype, device=grad_final.device) if want_p0 else None
-    gw = torch.empty(h.N, dtype=h.dtype, device=grad_final.device) if want_w else None
+    gw = torch.empty(h.cells, dtype=h.dtype, device=grad_final.device) if want_w else None
     n = 4096
     iters = (ctypes.c_int * n)()
     L = lib()
