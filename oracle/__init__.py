@@ -22,6 +22,8 @@ Plain, slow and written to be checked against the paper by eye:
                    generic diagonal scaling with 2 couplings, printed and reduced.
 * ``summation`` -- two densities coupled through the congestion of their sum
                    (Sec. 5.3), the same scaling with 2 couplings.
+* ``heat``      -- the heat-kernel Gibbs kernel (Id - (gamma/L) Delta_M)^{-L} on a
+                   domain with obstacles (Sec. 4.1, Eq. heat-kernel), sparse LU.
 * ``mirror``    -- an independent brute-force solve of the step by entropic
                    mirror descent on the full coupling (smooth energies).
 * ``objective`` -- entropy E, W_gamma by a converged dense Sinkhorn, f, the step

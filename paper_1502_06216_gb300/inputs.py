@@ -23,6 +23,8 @@ synthetic):
   kappa = max q0, the crowd disk and an optional two-room wall with a door.
 * Wasserstein attraction -- f = W_gamma(r, .) + iota_{[0,kappa]} (Sec. 5.2),
   disks q0 and r, kappa = max q0, optional two-room wall.
+* heat kernel -- crowd motion in two rooms with xi = (Id - (gamma/L) Delta)^{-L}
+  on the free cells (Sec. 4.1, Eq. heat-kernel), the exit at (1, 0.5).
 * two species -- h(p_1 + p_2) + <p_1, w_1> + <p_2, w_2> with h = iota_{[0,kappa]}
   (Sec. 5.3, summation couplings): two rectangles heading for each other.
 
@@ -51,6 +53,7 @@ __all__ = [
     "binary_congestion_problem",
     "attraction_problem",
     "two_species_problem",
+    "heat_crowd_problem",
 ]
 
 
@@ -76,6 +79,7 @@ class Problem:
     target: Optional[np.ndarray] = None  # (N,) target density r of the Wasserstein attraction
     species: int = 1                     # 2: q0 = [q_1, q_2] (2N), congestion on their sum
     w2: Optional[np.ndarray] = None      # (N,) potential of the second species
+    heat_L: int = 0                      # > 0: xi = (Id - (gamma/L) Delta)^{-L} on the free cells
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -307,6 +311,26 @@ def two_species_problem(n: int, gamma: float = 1e-3, tau: float = 0.02, kappa_fa
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w1, w2=w2,
                    kappa=float(kappa_factor * (q1 + q2).max()), species=2, n_steps=n_steps,
                    max_iter=max_iter, tol=tol, name=name)
+
+
+def heat_crowd_problem(n: int, gamma: float = 2e-3, tau: float = 0.02, L: int = 10,
+                       kappa_factor: float = 1.2, n_steps: int = 20, max_iter: int = 300,
+                       tol: float = 1e-6, ny: Optional[int] = None,
+                       name: str = "heat-crowd") -> Problem:
+    """Crowd motion in a non-convex domain with the heat-kernel Gibbs kernel
+    (Sec. 4.1, Eq. heat-kernel, L = 10; the setting of Fig. fig-examples): two
+    rooms separated by a wall at |x - 0.5| < 0.02 with a door at |y - 0.5| < 0.1
+    (obstacle cells), q0 the uniform disk of radius 0.15 at (0.25, 0.5), the
+    exit at (1, 0.5) with w = |x - (1, 0.5)|^2, kappa = factor * max q0."""
+    nx = n
+    ny = n if ny is None else ny
+    q0 = _disk(nx, ny, (0.25, 0.5), 0.15)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    wall = (np.abs(X - 0.5) < 0.02) & (np.abs(Y - 0.5) >= 0.1)
+    w = ((X - 1.0) ** 2 + (Y - 0.5) ** 2).ravel()
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w,
+                   kappa=float(kappa_factor * q0.max()), mask=wall.ravel().astype(np.uint8),
+                   heat_L=L, n_steps=n_steps, max_iter=max_iter, tol=tol, name=name)
 
 
 # Named workloads.  Sizes are parameters so that tests can run the same recipe
