@@ -76,6 +76,12 @@ typedef enum jko_precision {
 typedef struct jko_grid {
   int nx, ny;      /* cells along x (contiguous) and y; each >= 1 */
   double lx, ly;   /* domain lengths; > 0 */
+  /* Gibbs kernel: 0 = the separable Gaussian e^{-|x-y|^2/gamma} (Sec. 2.1);
+   * L in [1, 1000] = the heat kernel (Id - (gamma/L) Delta_M)^{-L} of the
+   * domain outside the obstacle mask (Sec. 4.1, Eq. heat-kernel), JKO_FP32 /
+   * JKO_FP64 single-density handles only (JKO_ERR_UNSUPPORTED otherwise; not
+   * batched, no adjoint, no fixed-scratch step). */
+  int heat_L;
 } jko_grid;
 
 typedef struct jko_params {

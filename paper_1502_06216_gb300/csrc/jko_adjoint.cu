@@ -272,9 +272,10 @@ __global__ void k_set_potential(const W* w, T* E, T* sw, double sigma, long long
 
 jko_status check_set_potential(jko_handle* h, const void* w) {
   if (!h || !w) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
-  if (h->attract || h->species == 2)
+  if (h->attract || h->species == 2 || h->heat_L)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "the potential of an attraction or two-species handle is fixed at creation");
+                             "the potential of an attraction, two-species or heat-kernel handle is "
+                             "fixed at creation");
   if (h->tc && jko::tc_absorbed(h->tc))
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the potential is absorbed into the Gibbs factors of this handle");
@@ -334,6 +335,7 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   if (h->attract)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the Wasserstein attraction");
   if (h->species == 2) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for two species");
+  if (h->heat_L) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the heat kernel");
   const size_t es = h->es, N = (size_t)h->N;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);

@@ -226,12 +226,42 @@ cudaError_t begin_species(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
+// One iteration with the heat-kernel Gibbs kernel (Sec. 4.1, heat.cu):
+// Y = xi~ a, b = q / Y with the residual partials, s = xi~ b (its first kernel
+// takes the stop decision), then a = Prox(s) / s.  xi~ is symmetric, so the
+// same operator serves xi and xi^T.
+template <typename T>
+cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  const uint8_t* mask = (const uint8_t*)h->mask;
+  const int nb = jko::heat_blocks(nx, ny);
+  cudaError_t e;
+#define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  JKO_TRY(jko::heat_apply<T>(h->heat, h->hb, (const T*)h->a, (T*)h->t1, nx, ny, mask, h->ctrl,
+                             h->part, nb, 0, st));
+  JKO_TRY(jko::heat_bupdate_launch<T>((const T*)h->t1, (T*)h->b, (const T*)h->q, nx, ny, h->ctrl,
+                                      h->part, st));
+  JKO_TRY(jko::heat_apply<T>(h->heat, h->hb, (const T*)h->b, (T*)h->t1, nx, ny, mask, h->ctrl,
+                             h->part, nb, 1, st));
+#undef JKO_TRY
+  return jko::heat_prox_launch<T>(h->ek, (const T*)h->t1, (T*)h->a, (T*)h->p, nx, ny,
+                                  jko::prox_args<T>(h), h->ctrl, st);
+}
+
+// kernels one pair launches
+long long pair_kernels(const jko_handle* h) {
+  if (h->heat_L) return 2LL * (h->heat.D + 1) + 2;
+  return h->attract || h->species == 2 ? 9 : 4;
+}
+
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
   if (h->tc) return jko::tc_enqueue_pass(h->tc, which, st);
   return h->fp64 ? enqueue_pass_simt<double>(h, which, st) : enqueue_pass_simt<float>(h, which, st);
 }
 
 cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
+  if (h->heat_L)
+    return h->fp64 ? enqueue_pair_heat<double>(h, st) : enqueue_pair_heat<float>(h, st);
   if (h->species == 2)
     return h->fp64 ? enqueue_pair_species<double>(h, st) : enqueue_pair_species<float>(h, st);
   if (h->attract)
@@ -393,7 +423,7 @@ void free_handle(jko_handle* h) {
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
-                  h->tape, h->adj, h->adj_red};
+                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1]};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -444,6 +474,15 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
     }
     if (std::fabs(tot - 1.0) > 1e-3)
       return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must sum to 1");
+  }
+  if (g->heat_L < 0 || g->heat_L > 1000)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "heat_L must be 0 (Gaussian) or in [1, 1000]");
+  if (g->heat_L > 0) {
+    if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
+      return set_err(nullptr, JKO_ERR_UNSUPPORTED, "the heat kernel runs on JKO_FP32 / JKO_FP64 only");
+    if (en->target || en->species == 2)
+      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
+                     "the heat kernel serves one density without attraction");
   }
   if (en->species < 0 || en->species > 2)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "species must be 0, 1 or 2");
@@ -589,7 +628,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   int launched = 0, polled = 0;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   auto launch = [&]() -> cudaError_t {
-    h->kernels += h->use_loop ? 1LL : (h->attract || h->species == 2 ? 9LL : 4LL) * C;
+    h->kernels += h->use_loop ? 1LL : pair_kernels(h) * C;
     cudaError_t e = launch_chunk(h, st);
     if (e != cudaSuccess) return e;
     const int slot = launched & 1;
@@ -725,7 +764,10 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   h->fp64 = params->precision == JKO_FP64;
   h->es = h->fp64 ? 8 : 4;
   h->stream = (cudaStream_t)stream;
-  h->chunk_iters = params->check_every > 0 ? params->check_every : 16;
+  h->heat_L = grid->heat_L;
+  // a heat-kernel pair is 2 (D + 1) + 2 launches: short chunks keep the
+  // graph small and the overshoot past the stop a pair or two
+  h->chunk_iters = params->check_every > 0 ? params->check_every : (h->heat_L ? 2 : 16);
   cudaGetDevice(&h->device);
 
   auto fail = [&](jko_status st) {
@@ -762,9 +804,26 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       if (e != cudaSuccess) return fail(cuda_err(h, e, "upload of the target"));
     }
   }
+  if (h->heat_L) {
+    h->heat = jko::heat_plan(grid->nx, grid->ny, grid->lx, grid->ly, params->gamma, h->heat_L,
+                             h->fp64);
+    if (h->heat.D < 0)
+      return fail(set_err(h, JKO_ERR_UNSUPPORTED,
+                          "the heat kernel's expansion needs a degree above 1500 "
+                          "(gamma / h^2 too large for this grid)"));
+    void** hbufs[] = {&h->hb.d[0], &h->hb.d[1]};
+    const size_t bytes64 = sizeof(double) * (size_t)h->N;   // FP64 Clenshaw iterates
+    for (void** pp : hbufs) {
+      e = cudaMalloc(pp, bytes64);
+      if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(heat scratch)"));
+      e = cudaMemset(*pp, 0, bytes64);
+      if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(heat scratch)"));
+    }
+  }
   {
-    const int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
-                            jko::tc_partials(grid->nx, grid->ny));
+    int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
+                      jko::tc_partials(grid->nx, grid->ny));
+    if (h->heat_L) np = std::max(np, jko::heat_blocks(grid->nx, grid->ny));
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
     h->part_cap = np;
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(partials)"));
@@ -791,7 +850,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   s = h->fp64 ? build_energy<double>(h, energy) : build_energy<float>(h, energy);
   if (s != JKO_OK) return fail(s);
   if (h->prec == JKO_FP64 || h->prec == JKO_FP32) {
-    s = h->fp64 ? setup_simt<double>(h) : setup_simt<float>(h);
+    // the heat kernel needs no Gaussian taps
+    if (!h->heat_L) s = h->fp64 ? setup_simt<double>(h) : setup_simt<float>(h);
   } else {
     jko::TcConfig cfg{};
     cfg.nx = grid->nx; cfg.ny = grid->ny; cfg.lx = grid->lx; cfg.ly = grid->ly;
@@ -1324,6 +1384,8 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
     if (energies[f].species == 2)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "two species are not batched"));
+    if (grids[f].heat_L)
+      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the heat kernel is not batched"));
     jko_handle* h = nullptr;
     jko_status s = jko_create(&grids[f], &params[f], &energies[f], stream, &h);
     if (s != JKO_OK) {

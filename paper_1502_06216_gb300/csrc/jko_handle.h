@@ -8,6 +8,7 @@
 
 #include "jko.h"
 #include "jko_internal.cuh"
+#include "jko_kernels.h"
 #include "tc_gemm.h"
 
 using jko::Ctrl;
@@ -42,6 +43,9 @@ struct jko_handle {
   int species = 1;              // 2: two densities coupled through their sum (Sec. 5.3)
   void* E2 = nullptr;           // e^{-sigma w2} of the second species
   long long ns = 0;             // elements of a state image: N, or 2 N for two species
+  int heat_L = 0;               // > 0: the heat-kernel Gibbs kernel (heat.cu)
+  jko::HeatPlan heat;
+  jko::HeatBuffers hb;
   void *a2 = nullptr, *b2 = nullptr, *tgt = nullptr, *s1 = nullptr, *s2 = nullptr;
   uint8_t* mask = nullptr;
   double kappa_s = INFINITY;

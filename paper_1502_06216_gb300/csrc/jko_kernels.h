@@ -1,5 +1,6 @@
 // jko_kernels.h -- host-side launch interface of the JKO kernels (internal).
 #pragma once
+#include <vector>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,6 +74,33 @@ template <typename T>
 cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,
                                 T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
                                 cudaStream_t st);
+
+// Heat-kernel Gibbs kernel (heat.cu): xi~ = (Id - (gamma/L) Delta_M)^{-L} as
+// the Chebyshev expansion of lambda^{-L} on the spectrum interval [1, lmax].
+constexpr int kMaxHeatDegree = 1500;
+struct HeatPlan {
+  int L = 0;
+  int D = 0;                    // degree of the expansion (-1: above kMaxHeatDegree)
+  double cx = 0, cy = 0;        // (gamma / L) / hx^2, (gamma / L) / hy^2
+  double theta = 0, delta = 0;  // centre and half-width of [1, lmax]
+  std::vector<double> coef;     // Chebyshev coefficients c_0 .. c_D
+};
+struct HeatBuffers {
+  void* d[2] = {nullptr, nullptr};   // the two Clenshaw iterates (FP64, N each)
+};
+HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bool fp64);
+int heat_blocks(int nx, int ny);   // blocks of heat_bupdate (= residual partials)
+// out_x = xi~ in (the first init takes the stop decision when decide = 1)
+template <typename T>
+cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T* out_x,
+                       int nx, int ny, const uint8_t* mask, Ctrl* ctrl, const double* part,
+                       int nparts, int decide, cudaStream_t st);
+template <typename T>
+cudaError_t heat_bupdate_launch(const T* Y, T* b, const T* q, int nx, int ny, Ctrl* ctrl,
+                                double* part, cudaStream_t st);
+template <typename T>
+cudaError_t heat_prox_launch(int ek, const T* s, T* a, T* p, int nx, int ny, const ProxArgs<T>& P,
+                             Ctrl* ctrl, cudaStream_t st);
 
 // Batched flows: copy the stop state of n control blocks into a contiguous
 // array (done flags only, or whole blocks).

@@ -148,6 +148,8 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the Wasserstein attraction is not available");
   if (en->species == 2)
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: two species are not available");
+  if (grid->heat_L != 0)
+    return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the heat kernel is not available");
   if (!(grid->lx > 0) || !(grid->ly > 0) || !(prm->gamma > 0) || !(prm->tau > 0) ||
       !(prm->tol >= 0) || prm->max_iter < 1 || prm->check_every < 0 || !(en->kappa > 0) ||
       !(en->m == 0.0 || en->m >= 1.0))

@@ -313,18 +313,20 @@ def two_species_problem(n: int, gamma: float = 1e-3, tau: float = 0.02, kappa_fa
                    max_iter=max_iter, tol=tol, name=name)
 
 
-def heat_crowd_problem(n: int, gamma: float = 2e-3, tau: float = 0.02, L: int = 10,
+def heat_crowd_problem(n: int, gamma: float = 5e-4, tau: float = 0.02, L: int = 10,
                        kappa_factor: float = 1.2, n_steps: int = 20, max_iter: int = 300,
                        tol: float = 1e-6, ny: Optional[int] = None,
+                       centre=(0.25, 0.5), radius: float = 0.15,
                        name: str = "heat-crowd") -> Problem:
     """Crowd motion in a non-convex domain with the heat-kernel Gibbs kernel
     (Sec. 4.1, Eq. heat-kernel, L = 10; the setting of Fig. fig-examples): two
     rooms separated by a wall at |x - 0.5| < 0.02 with a door at |y - 0.5| < 0.1
-    (obstacle cells), q0 the uniform disk of radius 0.15 at (0.25, 0.5), the
-    exit at (1, 0.5) with w = |x - (1, 0.5)|^2, kappa = factor * max q0."""
+    (obstacle cells), q0 the uniform disk of ``radius`` at ``centre`` (0.15 at
+    (0.25, 0.5) by default; a disk touching the wall congests from the first
+    step), the exit at (1, 0.5) with w = |x - (1, 0.5)|^2, kappa = factor * max q0."""
     nx = n
     ny = n if ny is None else ny
-    q0 = _disk(nx, ny, (0.25, 0.5), 0.15)
+    q0 = _disk(nx, ny, tuple(centre), radius)
     X, Y = _mesh(nx, ny, 1.0, 1.0)
     wall = (np.abs(X - 0.5) < 0.02) & (np.abs(Y - 0.5) >= 0.1)
     w = ((X - 1.0) ** 2 + (Y - 0.5) ** 2).ravel()

@@ -47,7 +47,7 @@ class JKOError(RuntimeError):
 
 class jko_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("lx", ctypes.c_double), ("ly", ctypes.c_double)]
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("heat_L", ctypes.c_int)]
 
 
 class jko_params(ctypes.Structure):
@@ -197,15 +197,16 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
                tile: int = 0, m_field=None, binary: bool = False, target=None,
-               species: int = 1, w2=None) -> Handle:
+               species: int = 1, w2=None, heat_L: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
     ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
     density r of the Wasserstein attraction (Sec. 5.2); ``species = 2`` with
     ``w2``: two densities coupled through the congestion of their sum (Sec. 5.3),
-    whose state images hold [p_1, p_2]."""
+    whose state images hold [p_1, p_2]; ``heat_L > 0``: the heat-kernel Gibbs
+    kernel (Id - (gamma/L) Delta)^{-L} of the domain outside ``mask`` (Sec. 4.1)."""
     N = nx * ny
-    g = jko_grid(nx, ny, lx, ly)
+    g = jko_grid(nx, ny, lx, ly, int(heat_L))
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
                    int(absorb), int(loop), int(tile))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N),
@@ -334,7 +335,7 @@ def jko_step_noalloc(pb, q, p_out, tol: Optional[float] = None,
         if not t.is_cuda or str(t.dtype) != "torch.float32" or not t.is_contiguous() \
                 or t.numel() < N:
             raise TypeError(f"{name} must be a contiguous float32 CUDA tensor of {N} elements")
-    g = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
+    g = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly, int(getattr(pb, "heat_L", 0)))
     p = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                    pb.max_iter if max_iter is None else max_iter, 0, int(Precision.FP32),
                    int(bool(renormalize)), 0)
@@ -385,7 +386,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       m_field=getattr(pb, "m_field", None),
                       binary=bool(getattr(pb, "binary", False)),
                       target=getattr(pb, "target", None),
-                      species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None))
+                      species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None),
+                      heat_L=int(getattr(pb, "heat_L", 0)))
 
 
 class Batch:
@@ -437,7 +439,7 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
     E = (jko_energy * n)()
     keep = []
     for f, pb in enumerate(problems):
-        G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly)
+        G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly, int(getattr(pb, "heat_L", 0)))
         P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                           pb.max_iter if max_iter is None else max_iter, check_every,
                           int(precs[f]), int(bool(renormalize)), 0, int(loops[f]), int(tile))

@@ -1,0 +1,123 @@
+"""The heat-kernel Gibbs kernel on a domain with obstacles (Sec. 4.1, Eq.
+heat-kernel) on the CUDA-core forms, against the FP64 oracle (oracle/heat.py:
+sparse LU solves); the crowd stays off the wall; and the rejections."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import heat as oheat
+from oracle import jko as ojko
+from oracle.energy import Energy
+from paper_1502_06216_gb300 import inputs
+from tests.gpu_util import need_gpu, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_flow(pb, prec, n_steps, **kw):
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    h = jko.create_from_problem(pb, precision=jko.Precision[prec], **kw)
+    p0 = torch.tensor(pb.q0, dtype=h.dtype, device="cuda")
+    _, traj, infos = jko.jko_flow(h, p0, n_steps)
+    torch.cuda.synchronize()
+    jko.jko_destroy(h)
+    return traj.double().cpu().numpy(), infos
+
+
+# FP64: the expansion of xi~ is exact to ~1e-15 of the largest entry of its
+# argument (pinned below on xi~ q); but the scalings span e^{sigma (max w -
+# min w)} ~ e^{48} here (sigma = 40), and p = a (xi~ b) weighs the kernel's
+# far tail, many orders below that, by the largest entries of a: there an
+# absolute error of 1e-15 is a large relative one, in either solver (the LU
+# oracle's triangular solves keep more of it).  Measured ~1.5e-8 in rel L1 of
+# p with equal pair counts.  FP32: the same plus single-precision rounding of
+# the scalings.
+@pytest.mark.parametrize("prec,nx,ny,bar", [("FP64", 48, 48, 5e-8), ("FP64", 40, 56, 5e-8),
+                                            ("FP32", 64, 64, 2e-4)])
+def test_heat_crowd_flow_matches_oracle(prec, nx, ny, bar):
+    tol = 1e-11 if prec == "FP64" else 1e-6
+    pb = inputs.heat_crowd_problem(nx, ny=ny, n_steps=3, tol=tol, max_iter=4000)
+    ref = oheat.problem_flow(pb)
+    traj, infos = gpu_flow(pb, prec, 3)
+    errs = [rel_l1(traj[t], ref.traj[t + 1]) for t in range(3)]
+    iters = [i["iters"] for i in infos]
+    print(prec, nx, ny, "rel L1", " ".join(f"{e:.2e}" for e in errs), "iters", iters, ref.iters)
+    assert max(errs) <= bar
+    if prec == "FP64":
+        assert all(abs(a - b) <= 1 for a, b in zip(iters, ref.iters))
+    wall = pb.mask.astype(bool)
+    assert np.all(traj[:, wall] == 0)
+    assert np.all(traj[-1] <= pb.kappa * (1 + 1e-4))
+
+
+def test_first_pair_applies_the_heat_kernel():
+    """One pair from a = 1: xi~ 1 = 1 on the domain, so b = q and the prox
+    returns p = e^{-sigma w} xi~ q where the bound is inactive: p / e^{-sigma w}
+    is the GPU's xi~ q, pinned to the LU oracle's."""
+    for nx, ny in ((44, 44), (40, 56)):
+        pb = inputs.heat_crowd_problem(nx, ny=ny, n_steps=1)
+        traj, infos = gpu_flow(pb, "FP64", 1, tol=0.0, max_iter=1, renormalize=False)
+        assert infos[0]["iters"] == 1
+        E = np.exp(-pb.tau / pb.gamma * pb.w)
+        s_ref = oheat.problem_xi(pb)(pb.q0)
+        assert np.all(s_ref * E < pb.kappa)
+        free = ~pb.mask.astype(bool)
+        s_gpu = np.where(free, traj[0] / E, 0.0)
+        err = rel_l1(s_gpu, s_ref)
+        print(nx, ny, "xi~ q rel L1", err)
+        assert err <= 1e-13
+
+
+def test_fixed_pairs_equal_the_oracle_iterates():
+    """Fixed pair counts.  The bar on p is looser than on xi~ q: p = a (xi~ b)
+    weighs the far field by up to e^{48} times more than the bulk, so the
+    absolute error of xi~ b in the kernel's tail (either solver's) shows."""
+    pb = inputs.heat_crowd_problem(44, n_steps=1)
+    xi = oheat.problem_xi(pb)
+    for k in (1, 2, 7):
+        r = ojko.step(pb.q0, xi, pb.tau / pb.gamma, Energy.from_problem(pb), tol=0.0, max_iter=k)
+        traj, infos = gpu_flow(pb, "FP64", 1, tol=0.0, max_iter=k, renormalize=False)
+        assert infos[0]["iters"] == k
+        err = rel_l1(traj[0], r.p)
+        print("pairs", k, "rel L1", err)
+        assert err <= 1e-7
+
+
+def test_the_wall_blocks_what_the_gaussian_crosses():
+    """A crowd in front of the wall, away from the door: the Gaussian of the
+    same spread (e^{-|x-y|^2 / (4 gamma)}, the variance of the heat kernel at
+    time gamma) ignores the obstacle and carries mass across it; the heat
+    kernel does not."""
+    pb = inputs.heat_crowd_problem(48, n_steps=1, centre=(0.38, 0.8), radius=0.08)
+    gauss = copy.deepcopy(pb)
+    gauss.heat_L = 0
+    gauss.gamma = 4.0 * pb.gamma
+    right = np.tile((np.arange(pb.nx) + 0.5) / pb.nx, pb.ny) > 0.52
+    th, _ = gpu_flow(pb, "FP64", 1)
+    tg, _ = gpu_flow(gauss, "FP64", 1)
+    print("mass right of the wall: heat", th[0][right].sum(), "gaussian", tg[0][right].sum())
+    assert tg[0][right].sum() > 1e-3
+    assert th[0][right].sum() < 0.05 * tg[0][right].sum()
+
+
+def test_rejections():
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    pb = inputs.heat_crowd_problem(32, n_steps=1)
+    for prec in ("BF16", "BF16X3"):
+        with pytest.raises(jko.JKOError):
+            jko.create_from_problem(pb, precision=jko.Precision[prec])
+    with pytest.raises(jko.JKOError):
+        jko.jko_batch_create([pb], precision=jko.Precision.FP32)
+    bad = copy.deepcopy(pb)
+    bad.heat_L = 1001
+    with pytest.raises(jko.JKOError):
+        jko.create_from_problem(bad, precision=jko.Precision.FP64)
+    h = jko.create_from_problem(pb, precision=jko.Precision.FP64)
+    with pytest.raises(jko.JKOError):
+        jko.jko_flow_record(h, torch.tensor(pb.q0, dtype=torch.float64, device="cuda"), 1)
+    with pytest.raises(jko.JKOError):
+        jko.jko_set_potential(h, np.zeros(pb.N))
+    jko.jko_destroy(h)
