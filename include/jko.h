@@ -204,7 +204,8 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
  * warm-up launch; ms[k] receives the mean milliseconds per launch (CUDA
  * events) and, if flops is not NULL, flops[k] the algorithmic floating-point
  * operations of one launch.  Overwrites the handle's scaling iterates: call it
- * between flows, not inside one. */
+ * between flows, not inside one.  Heat-kernel handles (jko_grid.heat_L > 0)
+ * have no separable passes: JKO_ERR_UNSUPPORTED. */
 jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops);
 
 /* Times the persistent pair-loop kernel of a tensor-core handle: `reps`

@@ -961,6 +961,8 @@ jko_status jko_flow_host(jko_handle* h, const void* p0_host, int n_steps, void* 
 jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops) {
   if (!h) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL handle");
   if (reps < 1 || !ms) return set_err(h, JKO_ERR_INVALID_ARG, "reps < 1 or NULL ms");
+  if (h->heat_L)
+    return set_err(h, JKO_ERR_UNSUPPORTED, "a heat-kernel handle has no separable passes to time");
   DeviceGuard dg(h->device);
   cudaStream_t st = h->stream;
   // A running control block that never stops: it = 1 (residuals computed),
