@@ -53,6 +53,7 @@ __all__ = [
     "binary_congestion_problem",
     "attraction_problem",
     "two_species_problem",
+    "pairwise_attraction_problem",
     "heat_crowd_problem",
 ]
 
@@ -80,6 +81,7 @@ class Problem:
     species: int = 1                     # 2: q0 = [q_1, q_2] (2N), congestion on their sum
     w2: Optional[np.ndarray] = None      # (N,) potential of the second species
     heat_L: int = 0                      # > 0: xi = (Id - (gamma/L) Delta)^{-L} on the free cells
+    pair_alpha: float = 0.0              # > 0 with species = 2: pairwise attraction alpha W(p_1, p_2)
     n_steps: int = 1
     max_iter: int = 200
     tol: float = 1e-9
@@ -311,6 +313,30 @@ def two_species_problem(n: int, gamma: float = 1e-3, tau: float = 0.02, kappa_fa
     return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w1, w2=w2,
                    kappa=float(kappa_factor * (q1 + q2).max()), species=2, n_steps=n_steps,
                    max_iter=max_iter, tol=tol, name=name)
+
+
+def pairwise_attraction_problem(n: int, gamma: float = 2e-3, tau: float = 0.05,
+                                alpha: float = 1.0, kappa_factor: float = 1.0,
+                                n_steps: int = 10, max_iter: int = 2000, tol: float = 1e-6,
+                                ny: Optional[int] = None,
+                                name: str = "pairwise-attraction") -> Problem:
+    """Two densities under the pairwise attraction alpha W(p_1, p_2) with
+    congestion (Sec. 5.3, Fig. fig-pairwise-attraction setting): q_1 the uniform
+    disk of radius 0.15 at (0.3, 0.35), q_2 at (0.7, 0.65), mass 1/2 each;
+    w_1 = |x - (0.35, 0.45)|^2 and w_2 = |x - (0.65, 0.55)|^2 draw each into
+    itself (so it congests at kappa) and toward the other; kappa = factor *
+    max q_1."""
+    nx = n
+    ny = n if ny is None else ny
+    d1 = _disk(nx, ny, (0.3, 0.35), 0.15)
+    d2 = _disk(nx, ny, (0.7, 0.65), 0.15)
+    X, Y = _mesh(nx, ny, 1.0, 1.0)
+    w1 = ((X - 0.35) ** 2 + (Y - 0.45) ** 2).ravel()
+    w2 = ((X - 0.65) ** 2 + (Y - 0.55) ** 2).ravel()
+    q0 = np.concatenate([0.5 * d1, 0.5 * d2])
+    return Problem(nx=nx, ny=ny, gamma=gamma, tau=tau, q0=q0, w=w1, w2=w2,
+                   kappa=float(kappa_factor * 0.5 * d1.max()), species=2, pair_alpha=alpha,
+                   n_steps=n_steps, max_iter=max_iter, tol=tol, name=name)
 
 
 def heat_crowd_problem(n: int, gamma: float = 5e-4, tau: float = 0.02, L: int = 10,
