@@ -435,6 +435,42 @@ def run_species(args, jko, dev, barrier, steps=5):
     return out
 
 
+def run_pairwise(args, jko, dev, barrier, steps=4):
+    """Two densities under the Wasserstein pairwise attraction with congestion
+    (Sec. 5.3, 3 couplings per step): 256^2, two disks drawn into themselves
+    and toward each other, alpha = 1, kappa = max q_1, gamma = 8e-3 (the kernel
+    between the densities stays in FP32 range), tau = 0.05, <= 2000 pairs, tol
+    1e-6, CUDA-core forms.  Pairs/s of one `steps`-step flow
+    after a 1-step warm-up, and the last step of FP32 against FP64."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.pairwise_attraction_problem(256, gamma=8e-3, n_steps=steps, tol=1e-6,
+                                            max_iter=2000)
+    out = {"workload": f"pairwise attraction of two densities, {pb.nx}x{pb.ny}, alpha="
+                       f"{pb.pair_alpha}, gamma={pb.gamma}, tau={pb.tau}, kappa=max q1, "
+                       f"<={pb.max_iter} pairs/step, tol {pb.tol}"}
+    finals = {}
+    for form in ("FP32", "FP64"):
+        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+        jko.jko_flow(h, p0, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pf, _, infos = jko.jko_flow(h, p0, steps)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for i in infos)
+        finals[form] = pf.double()
+        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                     "pairs_per_step": iters / steps, "kernels_per_pair": 14}
+        jko.jko_destroy(h)
+    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
+                                               finals["FP64"].abs().sum())
+    return out
+
+
 def run_heat(args, jko, dev, barrier, steps=4):
     """Crowd motion through a door with the heat-kernel Gibbs kernel (Sec. 4.1,
     Eq. heat-kernel, L = 10): 100^2, two rooms, q0 a disk, kappa = 1.2 max q0,
@@ -734,13 +770,14 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = binary = attraction = species = heat = None
+    genent = binary = attraction = species = heat = pairwise = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
         binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
         attraction = run_attraction(args, jko, dev, barrier)
         species = run_species(args, jko, dev, barrier)
         heat = run_heat(args, jko, dev, barrier)
+        pairwise = run_pairwise(args, jko, dev, barrier)
     diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
@@ -787,6 +824,8 @@ def run_ours(args):
             line["two_species"] = species
         if heat is not None:
             line["heat_kernel"] = heat
+        if pairwise is not None:
+            line["pairwise_attraction"] = pairwise
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)

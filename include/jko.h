@@ -142,6 +142,12 @@ typedef struct jko_energy {
                                  target); JKO_FP32 / JKO_FP64; not for batches, the adjoint or
                                  jko_step_noalloc.  0 or 1: one density */
   const double* w2;           /* potential of the second species (N entries); NULL = 0 */
+  double pair_alpha;          /* > 0 with species = 2: the Wasserstein pairwise attraction
+                                 f = pair_alpha W_gamma(p_1, p_2) + h_1(p_1) + h_2(p_2),
+                                 h_1 = iota_{[0,kappa]} + <w, .>, h_2 = iota_{[0,kappa]} +
+                                 <w2, .> (Sec. 5.3, multiple densities), in place of the
+                                 congestion of the sum; the step runs the generic diagonal
+                                 scaling with 3 couplings; finite; 0 = none */
 } jko_energy;
 
 /* Per-step report. */

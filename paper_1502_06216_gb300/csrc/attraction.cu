@@ -79,7 +79,127 @@ __global__ void __launch_bounds__(NT) species_prox_kernel(const T* s1, const T* 
   if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->it = s_it + 1;
 }
 
+// Pairwise attraction of two densities (Sec. 5.3, multiple densities): the
+// generic scaling with 3 couplings, pi_1 (rows p_1, columns q_1), pi_2 (rows
+// q_2, columns p_2), pi_3 (rows p_1, columns p_2), weights (1, 1, t), t = tau
+// alpha.  By the update rules of Prop. prop-implementation-generic the prox
+// inputs are xi b_m (rows) and xi^T a_m (columns) alone.
+
+// Weighted geometric mean x^{1/(1+t)} y^{t/(1+t)}, 0 where either vanishes.
+template <typename T>
+__device__ __forceinline__ T weighted_geomean(T x, T y, T t) {
+  return (x > T(0) && y > T(0)) ? dev_exp<T>((dev_log<T>(x) + t * dev_log<T>(y)) / (T(1) + t))
+                                : T(0);
+}
+
+// p / s with IEEE division, 0 where p = 0 (s may be subnormal in the far field)
+template <typename T>
+__device__ __forceinline__ T safe_ratio(T p, T s) {
+  return (p > T(0) && s > T(0)) ? p / s : T(0);
+}
+
+// Row half-step (psi_1): p_1 = min(e^{-sigma' w_1} g(s_1, s_3), kappa) is the
+// common row marginal of pi_1 and pi_3, pi_2 keeps the rows q_2.
+template <typename T>
+__global__ void __launch_bounds__(NT) pairwise_rows_kernel(const T* s1, const T* s2, const T* s3,
+                                                           const T* E1, const T* q2, T* a1, T* a2,
+                                                           T* a3, T* p1, long long n, T t, T kappa,
+                                                           int has_kappa, Ctrl* ctrl) {
+  __shared__ int s_it;
+  if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T x1 = s1[i], x3 = s3[i];
+    T pm = weighted_geomean<T>(x1, x3, t) * (E1 ? E1[i] : T(1));
+    if (has_kappa && pm > kappa) pm = kappa;
+    const T r1 = safe_ratio<T>(pm, x1), r3 = safe_ratio<T>(pm, x3);
+    const T r2 = b_update<T>(q2[i], s2[i]);
+    bad |= !dev_finite(r1) || !dev_finite(r2) || !dev_finite(r3) || !dev_finite(pm);
+    a1[i] = r1;
+    a2[i] = r2;
+    a3[i] = r3;
+    p1[i] = pm;
+  }
+  bad = warp_or(bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+}
+
+// Column half-step (psi_2): first the residual of the iterate the row
+// half-step left against psi_2's affine constraints, |b_1 y_1 - q_1| +
+// |b_2 y_2 - b_3 y_3| (one partial per block, summed by the next pair's first
+// kernel), and its column marginal p_2 = b_2 y_2; then the prox on the columns
+// of pi_2 and pi_3 and b_1 = q_1 / y_1; the pair counter.
+template <typename T>
+__global__ void __launch_bounds__(NT) pairwise_cols_kernel(const T* y1, const T* y2, const T* y3,
+                                                           const T* E2, const T* q1, T* b1, T* b2,
+                                                           T* b3, T* p2, double* part, long long n,
+                                                           T t, T kappa, int has_kappa,
+                                                           Ctrl* ctrl) {
+  __shared__ int s_it;
+  __shared__ double s_red[33];
+  if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
+  int bad = 0;
+  double res = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T v1 = y1[i], v2 = y2[i], v3 = y3[i];
+    const T qq = q1[i], c1 = b1[i], c2 = b2[i], c3 = b3[i];
+    res += (double)abs_residual<T>(c1, v1, qq) + (double)fabs(c2 * v2 - c3 * v3);
+    p2[i] = c2 * v2;
+    T pm = weighted_geomean<T>(v2, v3, t) * (E2 ? E2[i] : T(1));
+    if (has_kappa && pm > kappa) pm = kappa;
+    const T r1 = b_update<T>(qq, v1);
+    const T r2 = safe_ratio<T>(pm, v2), r3 = safe_ratio<T>(pm, v3);
+    bad |= !dev_finite(r1) || !dev_finite(r2) || !dev_finite(r3);
+    b1[i] = r1;
+    b2[i] = r2;
+    b3[i] = r3;
+  }
+  const double tot = block_sum(res, s_red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+  bad = warp_or(bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->it = s_it + 1;
+}
+
 }  // namespace
+
+int pairwise_blocks(long long n) {
+  long long g = (n + NT - 1) / NT;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <typename T>
+cudaError_t launch_pairwise_rows(const T* s1, const T* s2, const T* s3, const T* E1, const T* q2,
+                                 T* a1, T* a2, T* a3, T* p1, long long n, double t, double kappa,
+                                 int has_kappa, Ctrl* ctrl, cudaStream_t st) {
+  pairwise_rows_kernel<T><<<pairwise_blocks(n), NT, 0, st>>>(
+      s1, s2, s3, E1, q2, a1, a2, a3, p1, n, (T)t, (T)kappa, has_kappa, ctrl);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pairwise_cols(const T* y1, const T* y2, const T* y3, const T* E2, const T* q1,
+                                 T* b1, T* b2, T* b3, T* p2, double* part, long long n, double t,
+                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st) {
+  pairwise_cols_kernel<T><<<pairwise_blocks(n), NT, 0, st>>>(
+      y1, y2, y3, E2, q1, b1, b2, b3, p2, part, n, (T)t, (T)kappa, has_kappa, ctrl);
+  return cudaGetLastError();
+}
+
+#define JKO_PW_INST(T)                                                                        \
+  template cudaError_t launch_pairwise_rows<T>(const T*, const T*, const T*, const T*,       \
+                                               const T*, T*, T*, T*, T*, long long, double,   \
+                                               double, int, Ctrl*, cudaStream_t);             \
+  template cudaError_t launch_pairwise_cols<T>(const T*, const T*, const T*, const T*,       \
+                                               const T*, T*, T*, T*, T*, double*, long long,  \
+                                               double, double, int, Ctrl*, cudaStream_t);
+JKO_PW_INST(float)
+JKO_PW_INST(double)
+#undef JKO_PW_INST
 
 template <typename T>
 cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,

@@ -226,6 +226,51 @@ cudaError_t begin_species(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
+// One iteration of the pairwise attraction of two densities (Sec. 5.3, 3
+// couplings, attraction.cu): s_m = xi b_m for m = 1, 2, 3 (the first filter
+// pass takes the stop decision on the partials of the previous column
+// half-step), the row prox; y_m = xi a_m (xi is symmetric), the column prox
+// with the residual partials, p_2 and the pair counter.
+template <typename T>
+cudaError_t enqueue_pair_pairwise(jko_handle* h, cudaStream_t st) {
+  const int nb = h->nparts_pw;
+  const long long N = h->N;
+  const T* q1 = (const T*)h->q;
+  T* p1 = (T*)h->p;
+  const double t = h->prm.tau * h->pair_alpha;
+  void* bs[3] = {h->b, h->b2, h->b3};
+  void* as[3] = {h->a, h->a2, h->a3};
+  void* ss[3] = {h->s1, h->s2, h->s3};
+  cudaError_t e;
+#define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  for (int m = 0; m < 3; ++m) {
+    JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, bs[m], h->t1, nullptr, h->part,
+                            m == 0 ? 1 : 0, nb, st));
+    JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, ss[m], nullptr, h->part, 0, nb, st));
+  }
+  JKO_TRY(jko::launch_pairwise_rows<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->s3,
+                                       (const T*)h->E, q1 + N, (T*)h->a, (T*)h->a2, (T*)h->a3,
+                                       p1, N, t, h->kappa_s, h->has_kappa, h->ctrl, st));
+  for (int m = 0; m < 3; ++m) {
+    JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, as[m], h->t1, nullptr, h->part, 0, nb, st));
+    JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, ss[m], nullptr, h->part, 0, nb, st));
+  }
+#undef JKO_TRY
+  return jko::launch_pairwise_cols<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->s3,
+                                      (const T*)h->E2, q1, (T*)h->b, (T*)h->b2, (T*)h->b3,
+                                      p1 + N, h->part, N, t, h->kappa_s, h->has_kappa, h->ctrl,
+                                      st);
+}
+
+// Start of a pairwise-attraction step: b_m = 1 (Prop. prop-implementation-generic).
+template <typename T>
+cudaError_t begin_pairwise(jko_handle* h, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (void* b : {h->b, h->b2, h->b3})
+    if (e == cudaSuccess) e = jko::launch_fill<T>((T*)b, T(1), h->N, st);
+  return e;
+}
+
 // One iteration with the heat-kernel Gibbs kernel (Sec. 4.1, heat.cu):
 // Y = xi~ a, b = q / Y with the residual partials, s = xi~ b (its first kernel
 // takes the stop decision), then a = Prox(s) / s.  xi~ is symmetric, so the
@@ -251,6 +296,7 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 // kernels one pair launches
 long long pair_kernels(const jko_handle* h) {
   if (h->heat_L) return 2LL * (h->heat.D + 1) + 2;
+  if (h->pair_alpha > 0) return 14;
   return h->attract || h->species == 2 ? 9 : 4;
 }
 
@@ -262,6 +308,8 @@ cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
 cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
   if (h->heat_L)
     return h->fp64 ? enqueue_pair_heat<double>(h, st) : enqueue_pair_heat<float>(h, st);
+  if (h->pair_alpha > 0)
+    return h->fp64 ? enqueue_pair_pairwise<double>(h, st) : enqueue_pair_pairwise<float>(h, st);
   if (h->species == 2)
     return h->fp64 ? enqueue_pair_species<double>(h, st) : enqueue_pair_species<float>(h, st);
   if (h->attract)
@@ -423,7 +471,8 @@ void free_handle(jko_handle* h) {
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
-                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1]};
+                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->a3, h->b3,
+                  h->s3};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -484,6 +533,10 @@ jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_ene
       return set_err(nullptr, JKO_ERR_UNSUPPORTED,
                      "the heat kernel serves one density without attraction");
   }
+  if (!(en->pair_alpha >= 0) || !std::isfinite(en->pair_alpha))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "pair_alpha must be finite and >= 0");
+  if (en->pair_alpha > 0 && en->species != 2)
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "pair_alpha couples two species (species = 2)");
   if (en->species < 0 || en->species > 2)
     return set_err(nullptr, JKO_ERR_INVALID_ARG, "species must be 0, 1 or 2");
   if (en->species == 2) {
@@ -528,7 +581,9 @@ template <typename T>
 jko_status build_energy(jko_handle* h, const jko_energy* en) {
   const int N = h->N;
   // the attraction's prox takes h with sigma / (1 + tau) (Eq. prox-psi-attraction)
-  const double sigma = h->prm.tau / h->prm.gamma / (en->target ? 1.0 + h->prm.tau : 1.0);
+  // and the pairwise attraction's h_i with sigma / (1 + tau alpha)
+  const double sigma = h->prm.tau / h->prm.gamma / (en->target ? 1.0 + h->prm.tau : 1.0) /
+                       (1.0 + h->prm.tau * en->pair_alpha);
   h->m = en->m;
   h->ek = en->m_field ? jko::EK_POWER
           : en->m == 0.0 ? jko::EK_CROWD : (en->m == 1.0 ? jko::EK_ENTROPY : jko::EK_POWER);
@@ -614,6 +669,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   if (h->tc) {
     jko_status s2 = jko::tc_begin_step(h->tc, st) == cudaSuccess ? JKO_OK : JKO_ERR_CUDA;
     if (s2 != JKO_OK) return set_err(h, s2, "tensor-core step set-up failed");
+  } else if (h->pair_alpha > 0) {
+    CK(h, begin_pairwise<T>(h, st));
   } else if (h->species == 2) {
     CK(h, begin_species<T>(h, st));
   } else if (h->attract) {
@@ -798,6 +855,18 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       e = cudaMemset(*pp, 0, bytes);
       if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
     }
+    h->pair_alpha = energy->species == 2 ? energy->pair_alpha : 0.0;
+    if (h->pair_alpha > 0) {
+      void* pw[] = {&h->a3, &h->b3, &h->s3};
+      for (void* vp : pw) {
+        void** pp = (void**)vp;
+        e = cudaMalloc(pp, bytes);
+        if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(image)"));
+        e = cudaMemset(*pp, 0, bytes);
+        if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(image)"));
+      }
+      h->nparts_pw = jko::pairwise_blocks(h->N);
+    }
     if (h->attract) {
       std::vector<double> r(energy->target, energy->target + h->N);
       e = h->fp64 ? upload<double>(&h->tgt, r) : upload<float>(&h->tgt, r);
@@ -824,6 +893,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
                       jko::tc_partials(grid->nx, grid->ny));
     if (h->heat_L) np = std::max(np, jko::heat_blocks(grid->nx, grid->ny));
+    if (h->pair_alpha > 0) np = std::max(np, h->nparts_pw);
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
     h->part_cap = np;
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(partials)"));

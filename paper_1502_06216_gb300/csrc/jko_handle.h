@@ -44,6 +44,11 @@ struct jko_handle {
   void* E2 = nullptr;           // e^{-sigma w2} of the second species
   long long ns = 0;             // elements of a state image: N, or 2 N for two species
   int heat_L = 0;               // > 0: the heat-kernel Gibbs kernel (heat.cu)
+  double pair_alpha = 0;        // > 0 (two species): pairwise attraction, 3 couplings
+  void* a3 = nullptr;           // scalings and kernel image of the third coupling
+  void* b3 = nullptr;
+  void* s3 = nullptr;
+  int nparts_pw = 0;            // residual partials of the pairwise column half-step
   jko::HeatPlan heat;
   jko::HeatBuffers hb;
   void *a2 = nullptr, *b2 = nullptr, *tgt = nullptr, *s1 = nullptr, *s2 = nullptr;

@@ -75,6 +75,20 @@ cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* 
                                 T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
                                 cudaStream_t st);
 
+// Pairwise attraction of two densities (attraction.cu; Sec. 5.3, 3 couplings):
+// the row half-step (psi_1) and the column half-step (psi_2, with the residual
+// partials of the stop rule, p_2 and the pair counter).  E1, E2 = e^{-sigma' w_m}
+// with sigma' = sigma / (1 + t), t = tau alpha.
+int pairwise_blocks(long long n);
+template <typename T>
+cudaError_t launch_pairwise_rows(const T* s1, const T* s2, const T* s3, const T* E1, const T* q2,
+                                 T* a1, T* a2, T* a3, T* p1, long long n, double t, double kappa,
+                                 int has_kappa, Ctrl* ctrl, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pairwise_cols(const T* y1, const T* y2, const T* y3, const T* E2, const T* q1,
+                                 T* b1, T* b2, T* b3, T* p2, double* part, long long n, double t,
+                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st);
+
 // Heat-kernel Gibbs kernel (heat.cu): xi~ = (Id - (gamma/L) Delta_M)^{-L} as
 // the Chebyshev expansion of lambda^{-L} on the spectrum interval [1, lmax].
 constexpr int kMaxHeatDegree = 1500;

@@ -65,7 +65,7 @@ class jko_energy(ctypes.Structure):
                 ("alpha", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("m_field", ctypes.c_void_p), ("binary", ctypes.c_int),
                 ("target", ctypes.c_void_p), ("species", ctypes.c_int),
-                ("w2", ctypes.c_void_p)]
+                ("w2", ctypes.c_void_p), ("pair_alpha", ctypes.c_double)]
 
 
 class jko_step_info(ctypes.Structure):
@@ -197,13 +197,15 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                w=None, kappa: float = math.inf, kappa_field=None, m: float = 0.0,
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
                tile: int = 0, m_field=None, binary: bool = False, target=None,
-               species: int = 1, w2=None, heat_L: int = 0) -> Handle:
+               species: int = 1, w2=None, heat_L: int = 0,
+               pair_alpha: float = 0.0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
     ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
     density r of the Wasserstein attraction (Sec. 5.2); ``species = 2`` with
     ``w2``: two densities coupled through the congestion of their sum (Sec. 5.3),
-    whose state images hold [p_1, p_2]; ``heat_L > 0``: the heat-kernel Gibbs
+    or with ``pair_alpha > 0`` through the pairwise attraction pair_alpha
+    W(p_1, p_2), whose state images hold [p_1, p_2]; ``heat_L > 0``: the heat-kernel Gibbs
     kernel (Id - (gamma/L) Delta)^{-L} of the domain outside ``mask`` (Sec. 4.1)."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly, int(heat_L))
@@ -218,7 +220,7 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                    mk.ctypes.data if mk is not None else None,
                    keep[3].ctypes.data if keep[3] is not None else None, int(bool(binary)),
                    keep[4].ctypes.data if keep[4] is not None else None, int(species),
-                   keep[5].ctypes.data if keep[5] is not None else None)
+                   keep[5].ctypes.data if keep[5] is not None else None, float(pair_alpha))
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)
     _check(lib().jko_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), st,
@@ -387,7 +389,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       binary=bool(getattr(pb, "binary", False)),
                       target=getattr(pb, "target", None),
                       species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None),
-                      heat_L=int(getattr(pb, "heat_L", 0)))
+                      heat_L=int(getattr(pb, "heat_L", 0)),
+                      pair_alpha=float(getattr(pb, "pair_alpha", 0.0)))
 
 
 class Batch:
