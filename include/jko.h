@@ -364,6 +364,20 @@ const char* jko_status_string(int status);
 /* Library description: precisions compiled in, device, version. */
 const char* jko_build_info(void);
 
+/* Host-only diagnostic (no device call): the expansion a heat-kernel handle
+ * (jko_grid.heat_L = L > 0, Sec. 4.1, Eq. heat-kernel) applies.  xi~ =
+ * (Id - (gamma/L) Delta)^{-L} is evaluated as p(A), p the Chebyshev series
+ * sum_k coef[k] T_k((lambda - centre) / half-width) of lambda^{-L} on the
+ * spectrum interval [1, lmax] of A = Id - (gamma/L) Delta, lmax = 1 + 4 (gamma/L)
+ * (1/hx^2 + 1/hy^2), truncated for `precision` (JKO_FP64: dropped
+ * coefficients below ~1e-15; JKO_FP32: ~1e-10).  Writes the degree D to
+ * *degree, min(D + 1, cap) coefficients to coef (may be NULL when cap = 0) and,
+ * if interval is not NULL, (1, lmax) to interval[0..1].  JKO_ERR_INVALID_ARG
+ * for sizes, lengths, gamma or L out of range (as jko_create);
+ * JKO_ERR_UNSUPPORTED when D would exceed 1500. */
+jko_status jko_heat_plan(int nx, int ny, double lx, double ly, double gamma, int L,
+                         int precision, int* degree, double* coef, int cap, double* interval);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1141,6 +1141,25 @@ const char* jko_status_string(int s) {
   }
 }
 
+jko_status jko_heat_plan(int nx, int ny, double lx, double ly, double gamma, int L,
+                         int precision, int* degree, double* coef, int cap, double* interval) {
+  if (nx < 1 || ny < 1 || !(lx > 0) || !(ly > 0) || !std::isfinite(lx) || !std::isfinite(ly) ||
+      !(gamma > 0) || !std::isfinite(gamma) || L < 1 || L > 1000 || !degree || cap < 0 ||
+      (cap > 0 && !coef))
+    return set_err(nullptr, JKO_ERR_INVALID_ARG, "jko_heat_plan: argument out of range");
+  if (precision != JKO_FP32 && precision != JKO_FP64)
+    return set_err(nullptr, JKO_ERR_UNSUPPORTED, "the heat kernel runs on JKO_FP32 / JKO_FP64 only");
+  const jko::HeatPlan hp = jko::heat_plan(nx, ny, lx, ly, gamma, L, precision == JKO_FP64);
+  *degree = hp.D;
+  if (interval) {
+    interval[0] = hp.theta - hp.delta;
+    interval[1] = hp.theta + hp.delta;
+  }
+  if (hp.D < 0) return set_err(nullptr, JKO_ERR_UNSUPPORTED, "expansion degree above 1500");
+  for (int k = 0; k < cap && k <= hp.D; ++k) coef[k] = hp.coef[k];
+  return JKO_OK;
+}
+
 const char* jko_build_info(void) {
   return "libjko: sm_103a; precisions FP64 FP32 (CUDA cores), TF32 BF16 BF16X3 (tcgen05)";
 }

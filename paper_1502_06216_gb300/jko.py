@@ -123,6 +123,11 @@ EXPORTS = {
     "jko_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "jko_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "jko_build_info": (ctypes.c_char_p, []),
+    "jko_heat_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -372,6 +377,20 @@ def jko_last_error(h: Optional[Handle] = None) -> str:
 
 def jko_build_info() -> str:
     return lib().jko_build_info().decode()
+
+
+def jko_heat_plan(nx: int, ny: int, gamma: float, L: int = 10, lx: float = 1.0,
+                  ly: float = 1.0, precision: int = Precision.FP64) -> dict:
+    """jko_heat_plan (host only): the degree, Chebyshev coefficients and
+    spectrum interval of the heat kernel's expansion."""
+    deg = ctypes.c_int()
+    iv = (ctypes.c_double * 2)()
+    _check(lib().jko_heat_plan(nx, ny, lx, ly, gamma, L, int(precision), ctypes.byref(deg),
+                               None, 0, iv))
+    coef = (ctypes.c_double * (deg.value + 1))()
+    _check(lib().jko_heat_plan(nx, ny, lx, ly, gamma, L, int(precision), ctypes.byref(deg),
+                               coef, deg.value + 1, iv))
+    return {"degree": deg.value, "coef": np.array(coef[:]), "interval": (iv[0], iv[1])}
 
 
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
