@@ -370,7 +370,8 @@ const char* jko_build_info(void);
  * sum_k coef[k] T_k((lambda - centre) / half-width) of lambda^{-L} on the
  * spectrum interval [1, lmax] of A = Id - (gamma/L) Delta, lmax = 1 + 4 (gamma/L)
  * (1/hx^2 + 1/hy^2), truncated for `precision` (JKO_FP64: dropped
- * coefficients below ~1e-15; JKO_FP32: ~1e-10).  Writes the degree D to
+ * coefficients below ~1e-15 or their rounding floor: the series within ~1e-14
+ * of lambda^{-L}; JKO_FP32: ~1e-10).  Writes the degree D to
  * *degree, min(D + 1, cap) coefficients to coef (may be NULL when cap = 0) and,
  * if interval is not NULL, (1, lmax) to interval[0..1].  JKO_ERR_INVALID_ARG
  * for sizes, lengths, gamma or L out of range (as jko_create);

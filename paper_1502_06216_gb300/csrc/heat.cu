@@ -9,9 +9,10 @@
 // 4 c/hy^2 (Gershgorin), so A^{-L} = f(A) for f(lambda) = lambda^{-L} is
 // replaced by its Chebyshev expansion p of degree D on that interval, with
 // ||p(A) - A^{-L}||_2 <= max |p - f| on [1, lmax] (the sum of the dropped
-// coefficients).  p(A) v is evaluated by Clenshaw's recurrence: one fused
-// 5-point stencil kernel per degree, D + 1 launches for the whole operator
-// (against L separate solves).  p(A) stays symmetric, as xi~ is.
+// coefficients).  p(A) v is evaluated by Clenshaw's recurrence, two degrees
+// per fused 5-point stencil kernel (the first on the tile and a one-cell halo
+// in shared memory): 1 + ceil(D / 2) launches for the whole operator, against
+// L separate solves.  p(A) stays symmetric, as xi~ is.
 // The b-update (with the residual partials of the stop rule) and the prox
 // (with the pair counter) are elementwise kernels around the two xi~
 // applications of a pair; every kernel passes the stop gate first.
@@ -31,6 +32,7 @@ struct HeatGeom {
   int nx, ny;
   double cx, cy;          // c / hx^2, c / hy^2
   const uint8_t* mask;    // 1 = obstacle, or NULL
+  double two_over_delta;  // 2 / delta (Clenshaw recurrence)
 };
 
 __device__ __forceinline__ bool is_free(const HeatGeom& g, int i) {
@@ -57,6 +59,13 @@ __device__ __forceinline__ T apply_A(const HeatGeom& g, const T* v, int x, int y
 // costs digits that the L separate solves keep; the stencil work is a small
 // share of a launch at the grid sizes of this operator.
 
+// The operator's output is clamped at 0: xi~ is positive, and the expansion's
+// error is normwise (~1e-15 of the largest entry in FP64), so where the true
+// kernel tail lies below it the sum can come out slightly negative; 0 there
+// is the same underflow the Gaussian kernel meets far from its support (the
+// b-update and the prox treat it so).  NaN passes through.
+__device__ __forceinline__ double close_value(double r) { return r < 0.0 ? 0.0 : r; }
+
 // First Clenshaw step: b_D = c_D v, b_{D+1} = 0 (v is 0 on the mask).
 template <typename T>
 __global__ void __launch_bounds__(HBX * HBY) heat_cl_init(const T* v, double* b1, double* b2,
@@ -76,7 +85,7 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_init(const T* v, double* b1
 // s = 2 inside the recurrence (O = double), s = 1 for the closing step (O = T).
 // out may alias b2 (each thread reads its own b2 entry before writing it); b1
 // is read at the 5-point stencil and is not written.
-template <typename T, typename O>
+template <typename T, typename O, bool CLOSE>
 __global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const double* b1,
                                                           const double* b2, O* out, HeatGeom g,
                                                           double ck, double s_over_delta,
@@ -91,7 +100,58 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const doub
     return;
   }
   const double Ab = apply_A<double>(g, b1, xx, yy);
-  out[i] = (O)(ck * (double)v[i] + s_over_delta * (Ab - theta * b1[i]) - b2[i]);
+  const double r = ck * (double)v[i] + s_over_delta * (Ab - theta * b1[i]) - b2[i];
+  out[i] = (O)(CLOSE ? close_value(r) : r);
+}
+
+// Two Clenshaw steps in one launch: b_k on the block's tile plus a one-cell
+// halo (shared memory), then b_{k-1} on the tile from it.  Reads b_{k+1} (at a
+// two-cell halo) and b_{k+2}; writes b_k (o1) and b_{k-1} (o2), buffers that no
+// block of this launch reads.  The second step is the closing one (s2 = 1 /
+// delta, O = T, o2 = the operator's output) when k - 1 = 0.
+template <typename T, typename O, bool CLOSE>
+__global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const double* b1,
+                                                           const double* b2, double* o1, O* o2,
+                                                           HeatGeom g, double ck, double ck1,
+                                                           double s2, double theta, Ctrl* ctrl) {
+  constexpr int RX = HBX + 2, RY = HBY + 2;
+  __shared__ double sb[RY][RX];
+  __shared__ int s_it;
+  if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
+  const int x0 = blockIdx.x * HBX, y0 = blockIdx.y * HBY;
+  const int tid = threadIdx.y * HBX + threadIdx.x;
+  for (int idx = tid; idx < RX * RY; idx += HBX * HBY) {
+    const int ry = idx / RX, rx = idx - ry * RX;
+    const int x = x0 + rx - 1, y = y0 + ry - 1;
+    double val = 0.0;
+    if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
+      const int i = y * g.nx + x;
+      if (is_free(g, i)) {
+        const double Ab = apply_A<double>(g, b1, x, y);
+        val = ck * (double)v[i] + g.two_over_delta * (Ab - theta * b1[i]) - b2[i];
+      }
+    }
+    sb[ry][rx] = val;
+  }
+  __syncthreads();
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int i = y * g.nx + x;
+  const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+  const double c = sb[ty][tx];
+  o1[i] = c;
+  if (!is_free(g, i)) {
+    o2[i] = O(0);
+    return;
+  }
+  // A b_k at (x, y) from the tile: the neighbour tests of apply_A
+  double acc = c;
+  if (x > 0 && is_free(g, i - 1)) acc += g.cx * (c - sb[ty][tx - 1]);
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc += g.cx * (c - sb[ty][tx + 1]);
+  if (y > 0 && is_free(g, i - g.nx)) acc += g.cy * (c - sb[ty - 1][tx]);
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc += g.cy * (c - sb[ty + 1][tx]);
+  const double r = ck1 * (double)v[i] + s2 * (acc - theta * c) - b1[i];
+  o2[i] = (O)(CLOSE ? close_value(r) : r);
 }
 
 // b = q / Y (0 where q = 0 or Y is not a normal number), with the residual
@@ -153,7 +213,8 @@ int heat_blocks(int nx, int ny) {
 // Chebyshev coefficients of f(lambda) = lambda^{-L} on [1, lmax], by
 // interpolation at M Chebyshev points (compensated sums: the noise floor of
 // the coefficients stays far below the FP64 target), and the degree D after
-// which the next 8 coefficients sum below eps/2 (they decay geometrically:
+// which the next 8 coefficients sum below eps/2, or each lie at their
+// rounding floor (they decay geometrically:
 // f is analytic on a Bernstein ellipse around the interval, its only pole
 // at lambda = 0).  Degree above max_degree: D = -1.
 HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bool fp64) {
@@ -169,6 +230,7 @@ HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bo
   // FP32 handles run the recurrence in FP64 too: truncate well below their rounding
   const double eps = fp64 ? 1e-15 : 1e-10;
   constexpr int M = 4096, kWin = 8;
+  constexpr double kCoefFloor = 1.5e-16;
   const double pi = 3.14159265358979323846;
   std::vector<double> f(M), ang(M);
   for (int j = 0; j < M; ++j) {
@@ -198,9 +260,14 @@ HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bo
     cf.push_back(coef(k));
     const int D = k - kWin;
     if (D >= 1) {
-      double win = 0.0;
-      for (int j = D + 1; j <= k; ++j) win += std::fabs(cf[j]);
-      if (win <= 0.5 * eps) {
+      double win = 0.0, wmax = 0.0;
+      for (int j = D + 1; j <= k; ++j) {
+        win += std::fabs(cf[j]);
+        wmax = std::max(wmax, std::fabs(cf[j]));
+      }
+      // the coefficients carry a rounding floor of ~1e-16 (f <= 1 on the
+      // interval): a window whose every entry is at that floor has ended the series
+      if (win <= 0.5 * eps || wmax <= kCoefFloor) {
         hp.D = D;
         cf.resize(D + 1);
         hp.coef = cf;
@@ -211,29 +278,55 @@ HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bo
   return hp;
 }
 
-// out_x = p(A) in with the Clenshaw recurrence of the expansion: D + 1 launches.
+// out_x = p(A) in with the Clenshaw recurrence of the expansion: the first
+// step b_D = c_D v, then the D remaining steps (k = D-1 .. 0, the last the
+// closing one) two per launch, one single step first when D is odd:
+// 1 + ceil(D / 2) launches.
 template <typename T>
 cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T* out_x,
                        int nx, int ny, const uint8_t* mask, Ctrl* ctrl, const double* part,
                        int nparts, int decide, cudaStream_t st) {
-  HeatGeom g{nx, ny, hp.cx, hp.cy, mask};
-  const dim3 grid = heat_grid(nx, ny), block(HBX, HBY);
-  double* d[2] = {(double*)B.d[0], (double*)B.d[1]};
-  const int D = hp.D;
-  heat_cl_init<T><<<grid, block, 0, st>>>(in, d[0], d[1], g, hp.coef[D], ctrl, part, nparts,
-                                          decide);
-  // b_{k+1} in d[cur], b_{k+2} in d[cur ^ 1]; b_k overwrites b_{k+2}
-  int cur = 0;
   const double inv_delta = hp.delta > 0 ? 1.0 / hp.delta : 0.0;   // delta = 0: p(A) = c_0 Id
-  for (int k = D - 1; k >= 1; --k) {
-    heat_cl_step<T, double><<<grid, block, 0, st>>>(in, d[cur], d[cur ^ 1], d[cur ^ 1], g,
-                                                    hp.coef[k], 2.0 * inv_delta, hp.theta, ctrl);
-    cur ^= 1;
+  HeatGeom g{nx, ny, hp.cx, hp.cy, mask, 2.0 * inv_delta};
+  const dim3 grid = heat_grid(nx, ny), block(HBX, HBY);
+  double* d[4] = {(double*)B.d[0], (double*)B.d[1], (double*)B.d[2], (double*)B.d[3]};
+  const int D = hp.D;
+  // b_{k+1} in d[r1], b_{k+2} in d[r2]; d[f1], d[f2] free
+  int r1 = 0, r2 = 1, f1 = 2, f2 = 3;
+  heat_cl_init<T><<<grid, block, 0, st>>>(in, d[r1], d[r2], g, hp.coef[D], ctrl, part, nparts,
+                                          decide);
+  int k = D - 1;
+  if (D % 2 == 1) {   // one single step so that the rest pairs up
+    if (k == 0) {
+      heat_cl_step<T, T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], out_x, g, hp.coef[0],
+                                                 inv_delta, hp.theta, ctrl);
+      return cudaGetLastError();
+    }
+    heat_cl_step<T, double, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[r2], g, hp.coef[k],
+                                                    2.0 * inv_delta, hp.theta, ctrl);
+    std::swap(r1, r2);
+    --k;
   }
-  heat_cl_step<T, T><<<grid, block, 0, st>>>(in, d[cur], d[cur ^ 1], out_x, g, hp.coef[0],
-                                             inv_delta, hp.theta, ctrl);
+  for (; k >= 1; k -= 2) {
+    if (k == 1) {   // steps 1 and the closing 0
+      heat_cl_step2<T, T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], out_x, g, hp.coef[1],
+                                                  hp.coef[0], inv_delta, hp.theta, ctrl);
+      break;
+    }
+    heat_cl_step2<T, double, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], d[f2], g,
+                                                     hp.coef[k], hp.coef[k - 1],
+                                                     2.0 * inv_delta, hp.theta, ctrl);
+    // b_{k-1} (f2) and b_k (f1) are the next step's b_{k'+1}, b_{k'+2}
+    const int o1 = r1, o2 = r2;
+    r1 = f2;
+    r2 = f1;
+    f1 = o1;
+    f2 = o2;
+  }
   return cudaGetLastError();
 }
+
+int heat_launches(const HeatPlan& hp) { return 1 + (hp.D + 1) / 2; }
 
 template <typename T>
 cudaError_t heat_bupdate_launch(const T* Y, T* b, const T* q, int nx, int ny, Ctrl* ctrl,

@@ -295,7 +295,7 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 
 // kernels one pair launches
 long long pair_kernels(const jko_handle* h) {
-  if (h->heat_L) return 2LL * (h->heat.D + 1) + 2;
+  if (h->heat_L) return 2LL * jko::heat_launches(h->heat) + 2;
   if (h->pair_alpha > 0) return 14;
   return h->attract || h->species == 2 ? 9 : 4;
 }
@@ -471,8 +471,8 @@ void free_handle(jko_handle* h) {
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
-                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->a3, h->b3,
-                  h->s3};
+                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
+                  h->hb.d[3], h->a3, h->b3, h->s3};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -822,7 +822,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   h->es = h->fp64 ? 8 : 4;
   h->stream = (cudaStream_t)stream;
   h->heat_L = grid->heat_L;
-  // a heat-kernel pair is 2 (D + 1) + 2 launches: short chunks keep the
+  // a heat-kernel pair is 2 (1 + ceil(D / 2)) + 2 launches: short chunks keep the
   // graph small and the overshoot past the stop a pair or two
   h->chunk_iters = params->check_every > 0 ? params->check_every : (h->heat_L ? 2 : 16);
   cudaGetDevice(&h->device);
@@ -880,7 +880,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       return fail(set_err(h, JKO_ERR_UNSUPPORTED,
                           "the heat kernel's expansion needs a degree above 1500 "
                           "(gamma / h^2 too large for this grid)"));
-    void** hbufs[] = {&h->hb.d[0], &h->hb.d[1]};
+    void** hbufs[] = {&h->hb.d[0], &h->hb.d[1], &h->hb.d[2], &h->hb.d[3]};
     const size_t bytes64 = sizeof(double) * (size_t)h->N;   // FP64 Clenshaw iterates
     for (void** pp : hbufs) {
       e = cudaMalloc(pp, bytes64);

@@ -100,10 +100,11 @@ struct HeatPlan {
   std::vector<double> coef;     // Chebyshev coefficients c_0 .. c_D
 };
 struct HeatBuffers {
-  void* d[2] = {nullptr, nullptr};   // the two Clenshaw iterates (FP64, N each)
+  void* d[4] = {nullptr, nullptr, nullptr, nullptr};   // Clenshaw iterates (FP64, N each)
 };
 HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bool fp64);
 int heat_blocks(int nx, int ny);   // blocks of heat_bupdate (= residual partials)
+int heat_launches(const HeatPlan& hp);   // kernel launches of one heat_apply
 // out_x = xi~ in (the first init takes the stop decision when decide = 1)
 template <typename T>
 cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T* out_x,

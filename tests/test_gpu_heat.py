@@ -127,18 +127,21 @@ def test_rejections():
 
 @pytest.mark.parametrize("nx,ny", [(1, 64), (64, 1), (5, 4)])
 def test_degenerate_grids_match_oracle(nx, ny):
-    """One-cell-wide and tiny grids, congestion active: Delta_M has neighbours
-    along one axis only (the Gershgorin interval still bounds the spectrum) or
-    a few cells (the 5 x 4 case runs its whole pair budget on both sides)."""
+    """One-cell-wide and tiny grids, congestion active (a plateau pressed
+    against the boundary by w = 3t): Delta_M has neighbours along one axis only
+    (the Gershgorin interval still bounds the spectrum) or a few cells (the
+    5 x 4 case runs its whole pair budget on both sides).  sigma (max w - min w)
+    = 30 e-folds: within what the expansion's normwise accuracy resolves."""
     n = nx * ny
     t = (np.arange(n) + 0.5) / n
-    q0 = np.exp(-((t - 0.3) ** 2) / 0.01)
+    q0 = (t < 0.3).astype(np.float64)
     q0 /= q0.sum()
-    pb = inputs.Problem(nx=nx, ny=ny, gamma=1e-4, tau=0.02, q0=q0, w=t.copy(),
+    pb = inputs.Problem(nx=nx, ny=ny, gamma=1e-3, tau=0.01, q0=q0, w=3.0 * t,
                         kappa=float(q0.max()), heat_L=10, n_steps=2, tol=1e-11,
                         max_iter=3000)
     ref = oheat.problem_flow(pb)
     traj, infos = gpu_flow(pb, "FP64", 2)
     errs = [rel_l1(traj[k], ref.traj[k + 1]) for k in range(2)]
     print(nx, ny, "rel L1", errs, [i["iters"] for i in infos], ref.iters)
-    assert max(errs) <= 5e-8
+    assert max(errs) <= 1e-10
+    assert np.all(traj >= 0)
