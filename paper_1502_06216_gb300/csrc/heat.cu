@@ -26,7 +26,7 @@ namespace jko {
 
 namespace {
 
-constexpr int HBX = 32, HBY = 8;
+constexpr int HBX = 16, HBY = 8;   // small tiles: the work is FP64-bound per SM, so more blocks spread it
 
 struct HeatGeom {
   int nx, ny;
