@@ -141,6 +141,34 @@ cudaError_t simt_pass_on(jko_handle* h, bool along_y, int epi, const void* in, v
   return jko::simt_pass<T>(epi, h->ek, A, jko::prox_args<T>(h), st);
 }
 
+// One batched EPI_STORE filter pass over n images of the grid (n <= 3): along
+// y or x, in[m] -> out[m], one launch (blockIdx.z = m); the same arithmetic per
+// block as n separate passes.
+template <typename T>
+cudaError_t simt_pass_multi(jko_handle* h, bool along_y, int n, void* const* in, void* const* out,
+                            int decide, int nparts, cudaStream_t st) {
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  PassArgs<T> A{};
+  A.ctrl = h->ctrl;
+  A.part = h->part;
+  A.nparts = nparts;
+  A.decide = decide;
+  A.latency = h->simt_latency;
+  A.nz = n;
+  for (int m = 0; m < n; ++m) {
+    A.in_z[m] = (const T*)in[m];
+    A.out_z[m] = (T*)out[m];
+  }
+  A.in = A.in_z[0];
+  A.out = A.out_z[0];
+  A.p = (T*)h->p;
+  A.taps = (const T*)(along_y ? h->taps_y : h->taps_x);
+  A.n_i = along_y ? ny : nx;
+  A.n_j = along_y ? nx : ny;
+  A.r = along_y ? h->ry : h->rx;
+  return jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, jko::prox_args<T>(h), st);
+}
+
 // One iteration of the Wasserstein attraction (Sec. 5.2, attraction.cu): the
 // b-updates of both couplings with their residual partials (the next pass
 // adds both sets for the stop rule), xi b_1 and xi b_2, then the joint prox.
@@ -148,15 +176,16 @@ template <typename T>
 cudaError_t enqueue_pair_attraction(jko_handle* h, cudaStream_t st) {
   const int nb = h->nparts_simt;
   cudaError_t e;
+  void* as[2] = {h->a, h->a2};
+  void* bs[2] = {h->b, h->b2};
+  void* ts[2] = {h->t1, h->t2};
+  void* ss[2] = {h->s1, h->s2};
 #define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, true, 2, as, ts, 0, nb, st));
   JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a2, h->t1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b2, h->tgt, h->part + nb, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 1, 2 * nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b2, h->t1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s2, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t2, h->b2, h->tgt, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, true, 2, bs, ts, 1, 2 * nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, ss, 0, nb, st));
 #undef JKO_TRY
   return jko::launch_attraction_prox<T>(h->ek, (const T*)h->s1, (const T*)h->s2, (T*)h->a,
                                         (T*)h->a2, (T*)h->p, h->N, h->prm.tau,
@@ -191,15 +220,16 @@ cudaError_t enqueue_pair_species(jko_handle* h, cudaStream_t st) {
   const int nb = h->nparts_simt;
   const T* q2 = (const T*)h->q + h->N;
   cudaError_t e;
+  void* as[2] = {h->a, h->a2};
+  void* bs[2] = {h->b, h->b2};
+  void* ts[2] = {h->t1, h->t2};
+  void* ss[2] = {h->s1, h->s2};
 #define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a, h->t1, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, true, 2, as, ts, 0, nb, st));
   JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->a2, h->t1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b2, q2, h->part + nb, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b, h->t1, nullptr, h->part, 1, 2 * nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, h->b2, h->t1, nullptr, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, h->s2, nullptr, h->part, 0, nb, st));
+  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t2, h->b2, q2, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, true, 2, bs, ts, 1, 2 * nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, ss, 0, nb, st));
 #undef JKO_TRY
   return jko::launch_species_prox<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->E,
                                      (const T*)h->E2, (T*)h->a, (T*)h->a2, (T*)h->p, h->N,
@@ -242,19 +272,15 @@ cudaError_t enqueue_pair_pairwise(jko_handle* h, cudaStream_t st) {
   void* as[3] = {h->a, h->a2, h->a3};
   void* ss[3] = {h->s1, h->s2, h->s3};
   cudaError_t e;
+  void* ts[3] = {h->t1, h->t2, h->t3};
 #define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
-  for (int m = 0; m < 3; ++m) {
-    JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, bs[m], h->t1, nullptr, h->part,
-                            m == 0 ? 1 : 0, nb, st));
-    JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, ss[m], nullptr, h->part, 0, nb, st));
-  }
+  JKO_TRY(simt_pass_multi<T>(h, true, 3, bs, ts, 1, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 3, ts, ss, 0, nb, st));
   JKO_TRY(jko::launch_pairwise_rows<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->s3,
                                        (const T*)h->E, q1 + N, (T*)h->a, (T*)h->a2, (T*)h->a3,
                                        p1, N, t, h->kappa_s, h->has_kappa, h->ctrl, st));
-  for (int m = 0; m < 3; ++m) {
-    JKO_TRY(simt_pass_on<T>(h, true, jko::EPI_STORE, as[m], h->t1, nullptr, h->part, 0, nb, st));
-    JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_STORE, h->t1, ss[m], nullptr, h->part, 0, nb, st));
-  }
+  JKO_TRY(simt_pass_multi<T>(h, true, 3, as, ts, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 3, ts, ss, 0, nb, st));
 #undef JKO_TRY
   return jko::launch_pairwise_cols<T>((const T*)h->s1, (const T*)h->s2, (const T*)h->s3,
                                       (const T*)h->E2, q1, (T*)h->b, (T*)h->b2, (T*)h->b3,
@@ -296,8 +322,8 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 // kernels one pair launches
 long long pair_kernels(const jko_handle* h) {
   if (h->heat_L) return 2LL * jko::heat_launches(h->heat) + 2;
-  if (h->pair_alpha > 0) return 14;
-  return h->attract || h->species == 2 ? 9 : 4;
+  if (h->pair_alpha > 0) return 6;
+  return h->attract || h->species == 2 ? 6 : 4;
 }
 
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
@@ -472,7 +498,7 @@ void free_handle(jko_handle* h) {
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
                   h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
-                  h->hb.d[3], h->a3, h->b3, h->s3};
+                  h->hb.d[3], h->a3, h->b3, h->s3, h->t2, h->t3};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -848,7 +874,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   h->nparts_simt = jko::simt_pass_blocks(grid->nx, grid->ny);  // the b-update pass runs along x
   h->attract = energy->target ? 1 : 0;
   if (h->attract || h->species == 2) {
-    void** more[] = {&h->a2, &h->b2, &h->s1, &h->s2};
+    void** more[] = {&h->a2, &h->b2, &h->s1, &h->s2, &h->t2};
     for (void** pp : more) {
       e = cudaMalloc(pp, bytes);
       if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(image)"));
@@ -857,7 +883,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     }
     h->pair_alpha = energy->species == 2 ? energy->pair_alpha : 0.0;
     if (h->pair_alpha > 0) {
-      void* pw[] = {&h->a3, &h->b3, &h->s3};
+      void* pw[] = {&h->a3, &h->b3, &h->s3, &h->t3};
       for (void* vp : pw) {
         void** pp = (void**)vp;
         e = cudaMalloc(pp, bytes);

@@ -45,6 +45,8 @@ struct jko_handle {
   long long ns = 0;             // elements of a state image: N, or 2 N for two species
   int heat_L = 0;               // > 0: the heat-kernel Gibbs kernel (heat.cu)
   double pair_alpha = 0;        // > 0 (two species): pairwise attraction, 3 couplings
+  void* t2 = nullptr;           // transposed intermediates of batched filter passes
+  void* t3 = nullptr;
   void* a3 = nullptr;           // scalings and kernel image of the third coupling
   void* b3 = nullptr;
   void* s3 = nullptr;

@@ -48,6 +48,15 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   for (int t = tid; t < ntap; t += BJ * BI) s_k[t] = A.taps[t];
   __syncthreads();
 
+  // the image of this block: one per launch, or blockIdx.z of a batched launch
+  const T* in_img = A.in;
+  T* out_img = A.out;
+  if (EPI == EPI_STORE && A.nz > 1) {
+    const int z = blockIdx.z;
+    in_img = z == 0 ? A.in_z[0] : (z == 1 ? A.in_z[1] : A.in_z[2]);
+    out_img = z == 0 ? A.out_z[0] : (z == 1 ? A.out_z[1] : A.out_z[2]);
+  }
+
   const int j = blockIdx.x * BJ + threadIdx.x;
   const int i0 = (blockIdx.y * BI + threadIdx.y) * RB;
   const bool active = (j < A.n_j) && (i0 < A.n_i);
@@ -68,7 +77,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     for (int rr = threadIdx.y; rr < rows; rr += BI) {
       const int ii = blk_lo - r + rr;
       s_in[rr * BJ + threadIdx.x] = (jc < A.n_j && ii >= 0 && ii < n_i)
-                                        ? __ldg(A.in + (size_t)ii * A.n_j + jc) : T(0);
+                                        ? __ldg(in_img + (size_t)ii * A.n_j + jc) : T(0);
     }
     __syncthreads();
     if (active) {
@@ -103,7 +112,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     if (t_lo < 0) t_lo = 0;
     int t_hi = n_i - 1 - i0 + r;
     if (t_hi > 2 * r) t_hi = 2 * r;
-    const T* col = A.in + j;
+    const T* col = in_img + j;
     const size_t ld = (size_t)A.n_j;
     T win[2 * RB];
     int base = i0 - r + t_lo;
@@ -139,7 +148,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     if (EPI == EPI_STORE) {
 #pragma unroll
       for (int o = 0; o < RB; ++o)
-        if (o < nout) A.out[rowoff + i0 + o] = acc[o];
+        if (o < nout) out_img[rowoff + i0 + o] = acc[o];
     } else if (EPI == EPI_B) {
       const bool have_prev = s_it > 0;
 #pragma unroll
@@ -205,7 +214,8 @@ cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t s
     if (e != cudaSuccess) return e;
   }
   dim3 block(BJ, BI);
-  dim3 grid((A.n_j + BJ - 1) / BJ, (A.n_i + BI * RB - 1) / (BI * RB));
+  dim3 grid((A.n_j + BJ - 1) / BJ, (A.n_i + BI * RB - 1) / (BI * RB),
+            (EPI == EPI_STORE && A.nz > 1) ? (unsigned)A.nz : 1u);
   kern<<<grid, block, smem, st>>>(A, P);
   return cudaGetLastError();
 }
