@@ -27,3 +27,25 @@ def test_batched_sizes_and_types():
     assert {p.nx for p in pbs} <= {64, 128, 256, 512}
     assert all((p.m == 0) == (i % 2 == 0) for i, p in enumerate(pbs))
     assert all(5e-4 <= p.gamma <= 4e-3 for p in pbs)
+
+
+def test_heat_crowd_recipe_is_feasible():
+    """The two-room recipe of the heat kernel: q0 a density off the wall and at
+    most kappa, the wall a band with a door, L = 10."""
+    for n in (48, 100):
+        pb = inputs.heat_crowd_problem(n)
+        wall = pb.mask.astype(bool)
+        assert abs(pb.q0.sum() - 1.0) <= 1e-12 and np.all(pb.q0 >= 0)
+        assert not np.any(pb.q0[wall]) and pb.q0.max() <= pb.kappa
+        assert pb.heat_L == 10 and 0.02 < wall.mean() < 0.1
+        door = wall.reshape(n, n)[:, n // 2]
+        assert not door[n // 2] and door[0] and door[-1]
+
+
+def test_pairwise_recipe_masses_and_bound():
+    pb = inputs.pairwise_attraction_problem(64)
+    N = pb.N
+    assert pb.species == 2 and pb.pair_alpha == 1.0 and pb.q0.size == 2 * N
+    assert abs(pb.q0[:N].sum() - 0.5) <= 1e-12 and abs(pb.q0[N:].sum() - 0.5) <= 1e-12
+    assert pb.q0.max() <= pb.kappa * (1 + 1e-12)
+    assert not np.any((pb.q0[:N] > 0) & (pb.q0[N:] > 0))        # disjoint disks
