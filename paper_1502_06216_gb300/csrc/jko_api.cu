@@ -141,12 +141,14 @@ cudaError_t simt_pass_on(jko_handle* h, bool along_y, int epi, const void* in, v
   return jko::simt_pass<T>(epi, h->ek, A, jko::prox_args<T>(h), st);
 }
 
-// One batched EPI_STORE filter pass over n images of the grid (n <= 3): along
-// y or x, in[m] -> out[m], one launch (blockIdx.z = m); the same arithmetic per
-// block as n separate passes.
+// One batched filter pass over n images of the grid (n <= 3): along y or x,
+// in[m] -> out[m], one launch (blockIdx.z = m); the same arithmetic per block as
+// n separate passes.  EPI_STORE, or EPI_B against q[m] with the partials of
+// image m at part + m * (blocks per image).
 template <typename T>
 cudaError_t simt_pass_multi(jko_handle* h, bool along_y, int n, void* const* in, void* const* out,
-                            int decide, int nparts, cudaStream_t st) {
+                            int decide, int nparts, cudaStream_t st, int epi = jko::EPI_STORE,
+                            const void* const* q = nullptr) {
   const int nx = h->grid.nx, ny = h->grid.ny;
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
@@ -158,15 +160,17 @@ cudaError_t simt_pass_multi(jko_handle* h, bool along_y, int n, void* const* in,
   for (int m = 0; m < n; ++m) {
     A.in_z[m] = (const T*)in[m];
     A.out_z[m] = (T*)out[m];
+    A.q_z[m] = q ? (const T*)q[m] : nullptr;
   }
   A.in = A.in_z[0];
   A.out = A.out_z[0];
+  A.q = A.q_z[0];
   A.p = (T*)h->p;
   A.taps = (const T*)(along_y ? h->taps_y : h->taps_x);
   A.n_i = along_y ? ny : nx;
   A.n_j = along_y ? nx : ny;
   A.r = along_y ? h->ry : h->rx;
-  return jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, jko::prox_args<T>(h), st);
+  return jko::simt_pass<T>(epi, h->ek, A, jko::prox_args<T>(h), st);
 }
 
 // One iteration of the Wasserstein attraction (Sec. 5.2, attraction.cu): the
@@ -181,9 +185,9 @@ cudaError_t enqueue_pair_attraction(jko_handle* h, cudaStream_t st) {
   void* ts[2] = {h->t1, h->t2};
   void* ss[2] = {h->s1, h->s2};
 #define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  const void* qs[2] = {h->q, h->tgt};
   JKO_TRY(simt_pass_multi<T>(h, true, 2, as, ts, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t2, h->b2, h->tgt, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, bs, 0, nb, st, jko::EPI_B, qs));
   JKO_TRY(simt_pass_multi<T>(h, true, 2, bs, ts, 1, 2 * nb, st));
   JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, ss, 0, nb, st));
 #undef JKO_TRY
@@ -225,9 +229,9 @@ cudaError_t enqueue_pair_species(jko_handle* h, cudaStream_t st) {
   void* ts[2] = {h->t1, h->t2};
   void* ss[2] = {h->s1, h->s2};
 #define JKO_TRY(x) do { e = (x); if (e != cudaSuccess) return e; } while (0)
+  const void* qs[2] = {h->q, q2};
   JKO_TRY(simt_pass_multi<T>(h, true, 2, as, ts, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t1, h->b, h->q, h->part, 0, nb, st));
-  JKO_TRY(simt_pass_on<T>(h, false, jko::EPI_B, h->t2, h->b2, q2, h->part + nb, 0, nb, st));
+  JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, bs, 0, nb, st, jko::EPI_B, qs));
   JKO_TRY(simt_pass_multi<T>(h, true, 2, bs, ts, 1, 2 * nb, st));
   JKO_TRY(simt_pass_multi<T>(h, false, 2, ts, ss, 0, nb, st));
 #undef JKO_TRY
@@ -323,7 +327,7 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 long long pair_kernels(const jko_handle* h) {
   if (h->heat_L) return 2LL * jko::heat_launches(h->heat) + 2;
   if (h->pair_alpha > 0) return 6;
-  return h->attract || h->species == 2 ? 6 : 4;
+  return h->attract || h->species == 2 ? 5 : 4;
 }
 
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {

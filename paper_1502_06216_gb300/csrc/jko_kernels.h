@@ -29,11 +29,13 @@ struct PassArgs {
   int latency;   // 1: small images take the 4-output, shared-memory-staged variant
                  // (a handle alone); 0: always 16 outputs per thread (flows of a
                  // batch, where other flows fill the GPU)
-  // nz > 1 (EPI_STORE): one launch filters nz images of the same shape,
-  // in_z[z] -> out_z[z] at blockIdx.z (in and out are then unused)
+  // nz > 1 (EPI_STORE, EPI_B): one launch filters nz images of the same
+  // shape, in_z[z] -> out_z[z] (EPI_B: against q_z[z], partials of image z at
+  // part + z * blocks per image) at blockIdx.z; in, out and q are then unused
   int nz = 1;
   const T* in_z[3] = {nullptr, nullptr, nullptr};
   T* out_z[3] = {nullptr, nullptr, nullptr};
+  const T* q_z[3] = {nullptr, nullptr, nullptr};
 };
 
 int simt_tap_padding();

@@ -51,10 +51,12 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   // the image of this block: one per launch, or blockIdx.z of a batched launch
   const T* in_img = A.in;
   T* out_img = A.out;
-  if (EPI == EPI_STORE && A.nz > 1) {
+  const T* q_img = A.q;
+  if (EPI != EPI_A && A.nz > 1) {
     const int z = blockIdx.z;
     in_img = z == 0 ? A.in_z[0] : (z == 1 ? A.in_z[1] : A.in_z[2]);
     out_img = z == 0 ? A.out_z[0] : (z == 1 ? A.out_z[1] : A.out_z[2]);
+    q_img = z == 0 ? A.q_z[0] : (z == 1 ? A.q_z[1] : A.q_z[2]);
   }
 
   const int j = blockIdx.x * BJ + threadIdx.x;
@@ -156,11 +158,11 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
         if (o < nout) {
           const size_t idx = rowoff + i0 + o;
           const T Y = acc[o];
-          const T qv = A.q[idx];
-          if (have_prev) res_t += abs_residual<T>(A.out[idx], Y, qv);
+          const T qv = q_img[idx];
+          if (have_prev) res_t += abs_residual<T>(out_img[idx], Y, qv);
           const T bn = b_update<T>(qv, Y);
           bad |= !dev_finite(bn);
-          A.out[idx] = bn;
+          out_img[idx] = bn;
         }
       }
     } else {  // EPI_A
@@ -183,7 +185,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   bad = warp_or(bad);
   if (EPI == EPI_B) {
     const double res = block_sum((double)res_t, s_red);
-    if (tid == 0) A.part[blockIdx.y * gridDim.x + blockIdx.x] = res;
+    if (tid == 0) A.part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = res;
   }
   if ((threadIdx.x & 31) == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
   if (EPI == EPI_A && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) ctrl->it = s_it + 1;
@@ -215,7 +217,7 @@ cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t s
   }
   dim3 block(BJ, BI);
   dim3 grid((A.n_j + BJ - 1) / BJ, (A.n_i + BI * RB - 1) / (BI * RB),
-            (EPI == EPI_STORE && A.nz > 1) ? (unsigned)A.nz : 1u);
+            (EPI != EPI_A && A.nz > 1) ? (unsigned)A.nz : 1u);
   kern<<<grid, block, smem, st>>>(A, P);
   return cudaGetLastError();
 }
