@@ -88,3 +88,61 @@ def test_flow_keeps_each_mass_and_the_attraction_pulls():
         cd[alpha] = float(np.linalg.norm(c1 - c2))
     print("centroid distance", cd)
     assert cd[4.0] < cd[0.0] - 0.01
+
+
+def test_step_is_the_minimiser_on_four_cells():
+    """The whole step, independent of the scaling algorithm and of the prox
+    formulas: on a 4-cell grid, minimise KL(pi_1|xi) + KL(pi_2|xi) + tau alpha
+    KL(pi_3|xi) + sigma (<w_1, pi_1 1> + <w_2, pi_2^T 1>) over the three
+    couplings (48 unknowns, in log space) subject to pi_1^T 1 = q_1, pi_2 1 =
+    q_2, pi_1 1 = pi_3 1, pi_2^T 1 = pi_3^T 1 (one redundant mass row dropped)
+    and both densities <= kappa (SLSQP with exact gradients), and compare the
+    marginals with the reduced loop's."""
+    from scipy.optimize import minimize
+    n, gamma, tau, alpha, kappa = 4, 0.05, 0.5, 2.0, 0.3
+    xi = gibbs.SeparableXi(n, 1, gamma)
+    K = np.column_stack([xi(np.eye(n)[:, j]) for j in range(n)])
+    q1 = np.array([0.25, 0.15, 0.07, 0.03])
+    q2 = np.array([0.03, 0.07, 0.15, 0.25])
+    w1 = np.array([1.0, 0.5, 0.0, 0.2])
+    w2 = np.array([0.3, 0.0, 0.6, 1.0])
+    sigma, t = tau / gamma, tau * alpha
+    r = P.step(q1, q2, xi, sigma, tau, alpha, w1, w2, kappa, tol=1e-14, max_iter=200000)
+
+    lam = np.concatenate([np.ones(16), np.ones(16), np.full(16, t)])
+    Kr = np.tile(K.ravel(), 3)
+    lK = np.log(Kr)
+    lin = np.zeros(48)
+    lin[:16] = sigma * np.repeat(w1, n)        # <w_1, pi_1 1>: pi_1[i, j] weighs w_1[i]
+    lin[16:32] = sigma * np.tile(w2, n)        # <w_2, pi_2^T 1>: pi_2[i, j] weighs w_2[j]
+    eye, one = np.eye(n), np.ones(n)
+
+    def block(m, v):
+        return np.concatenate([v if b == m else np.zeros(16) for b in range(3)])
+
+    rows = lambda m: np.array([block(m, np.kron(eye[i], one)) for i in range(n)])
+    cols = lambda m: np.array([block(m, np.kron(one, eye[j])) for j in range(n)])
+    A_eq = np.vstack([cols(0), rows(1), rows(0) - rows(2), (cols(1) - cols(2))[:-1]])
+    b_eq = np.concatenate([q1, q2, np.zeros(n), np.zeros(n - 1)])
+    A_in = np.vstack([rows(0), cols(1)])
+
+    def obj(y):
+        x = np.exp(y)
+        return float(np.sum(lam * (x * (y - lK) - x + Kr)) + lin @ x)
+
+    def grad(y):
+        x = np.exp(y)
+        return x * (lam * (y - lK) + lin)
+
+    cons = [{"type": "eq", "fun": lambda y: A_eq @ np.exp(y) - b_eq,
+             "jac": lambda y: A_eq * np.exp(y)},
+            {"type": "ineq", "fun": lambda y: kappa - A_in @ np.exp(y),
+             "jac": lambda y: -A_in * np.exp(y)}]
+    sol = minimize(obj, np.log(np.full(48, 0.5 / 16)), jac=grad, method="SLSQP",
+                   constraints=cons, options={"ftol": 1e-16, "maxiter": 20000})
+    x = np.exp(sol.x)
+    p1, p2 = A_in[:n] @ x, A_in[n:] @ x
+    print(sol.message, "p1", p1, r.p1, "p2", p2, r.p2)
+    assert np.abs(A_eq @ x - b_eq).max() <= 1e-12
+    assert np.abs(p1 - r.p1).max() <= 1e-9 and np.abs(p2 - r.p2).max() <= 1e-9
+    assert r.p1.max() >= kappa * (1 - 1e-9) and r.p2.max() >= kappa * (1 - 1e-9)
