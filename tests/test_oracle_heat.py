@@ -11,9 +11,10 @@ from paper_1502_06216_gb300 import inputs
 
 
 def test_laplacian_structure():
-    pb = inputs.heat_crowd_problem(24)
+    pb = inputs.heat_crowd_problem(40)            # the wall band holds a column of cells
     D = heat.laplacian(pb.nx, pb.ny, mask=pb.mask).toarray()
     free = ~pb.mask.astype(bool)
+    assert 0 < np.count_nonzero(~free) < pb.N
     assert np.allclose(D, D.T)
     assert np.allclose(D.sum(axis=1), 0.0)                 # Neumann: constants in the kernel
     assert np.all(D[~free] == 0) and np.all(D[:, ~free] == 0)

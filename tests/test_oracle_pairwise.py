@@ -99,7 +99,8 @@ def test_step_is_the_minimiser_on_four_cells():
     and both densities <= kappa (SLSQP with exact gradients), and compare the
     marginals with the reduced loop's."""
     from scipy.optimize import minimize
-    n, gamma, tau, alpha, kappa = 4, 0.05, 0.5, 2.0, 0.3
+    # tau alpha != 1: the geometric mean's two weights differ
+    n, gamma, tau, alpha, kappa = 4, 0.05, 0.5, 3.0, 0.25
     xi = gibbs.SeparableXi(n, 1, gamma)
     K = np.column_stack([xi(np.eye(n)[:, j]) for j in range(n)])
     q1 = np.array([0.25, 0.15, 0.07, 0.03])
