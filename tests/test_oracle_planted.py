@@ -7,13 +7,21 @@ import numpy as np
 import pytest
 
 from oracle import attraction as A
+from oracle import gibbs as G
 from oracle import heat as H
 from oracle import pairwise as P
+from oracle import prox as X
 from oracle import summation as S
+from oracle.energy import Energy
 from tests import test_oracle_attraction as t_attr
+from tests import test_oracle_gibbs as t_gibbs
 from tests import test_oracle_heat as t_heat
 from tests import test_oracle_pairwise as t_pair
+from tests import test_oracle_prox as t_prox
+from tests import test_oracle_step as t_step
 from tests import test_oracle_summation as t_sum
+
+MIRROR_POTENTIAL = ("potential", dict(gamma=0.05, tau=0.5))
 
 
 def test_pins_pass_unplanted():
@@ -23,6 +31,49 @@ def test_pins_pass_unplanted():
     t_heat.test_many_steps_approach_the_continuous_heat_kernel()
     t_sum.test_prox_is_the_joint_minimiser()
     t_attr.test_prox_is_the_weighted_kl_minimiser()
+    t_gibbs.test_kernel_width_matches_gaussian_integral()
+    t_prox.test_prox_minimises_1d_objective(0, 0.7, True)
+    t_step.test_dense_coupling_dykstra_equals_two_vector_loop(2)
+    t_step.test_step_matches_mirror_descent_8x8(*MIRROR_POTENTIAL)
+
+
+def test_gibbs_kernel_with_2_gamma_fails(monkeypatch):
+    """e^{-|x-y|^2 / (2 gamma)} in place of e^{-|x-y|^2 / gamma} (Sec. 2.1)."""
+    orig = G.kernel_1d
+    monkeypatch.setattr(G, "kernel_1d", lambda n, gamma, *a, **k: orig(n, 2.0 * gamma, *a, **k))
+    with pytest.raises(AssertionError):
+        t_gibbs.test_kernel_width_matches_gaussian_integral()
+
+
+def test_prox_with_the_potential_sign_flipped_fails(monkeypatch):
+    orig = X.prox
+
+    def prox(s, sigma, energy, *a, **k):
+        flipped = Energy(w=-np.asarray(energy.w), kappa=energy.kappa, m=energy.m,
+                         alpha=energy.alpha, mask=energy.mask)
+        return orig(s, sigma, flipped, *a, **k)
+
+    monkeypatch.setattr(X, "prox", prox)
+    with pytest.raises(AssertionError):
+        t_prox.test_prox_minimises_1d_objective(0, 0.7, True)
+
+
+def test_step_a_update_without_the_division_fails(monkeypatch):
+    """a = Prox(s) in place of a = Prox(s) / s in the 2-vector loop."""
+    monkeypatch.setattr(X, "ratio", lambda s, sigma, energy, *a, **k: X.prox(s, sigma, energy))
+    with pytest.raises(AssertionError):
+        t_step.test_dense_coupling_dykstra_equals_two_vector_loop(2)
+
+
+def test_prox_with_half_sigma_fails(monkeypatch):
+    """sigma / 2 in every proximal map: the scaling forms stay consistent with
+    each other, so only the mirror-descent solve (no proximal maps) sees it."""
+    orig = X.prox
+    monkeypatch.setattr(X, "prox", lambda s, sigma, energy, *a, **k: orig(s, 0.5 * sigma, energy,
+                                                                         *a, **k))
+    t_step.test_dense_coupling_dykstra_equals_two_vector_loop(2)     # blind to it
+    with pytest.raises(AssertionError):
+        t_step.test_step_matches_mirror_descent_8x8(*MIRROR_POTENTIAL)
 
 
 def test_pairwise_swapped_geometric_weights_fail(monkeypatch):
