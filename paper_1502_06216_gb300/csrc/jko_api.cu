@@ -514,98 +514,110 @@ void free_handle(jko_handle* h) {
 }
 
 jko_status validate_create(const jko_grid* g, const jko_params* p, const jko_energy* en) {
-  if (!g || !p || !en) return set_err(nullptr, JKO_ERR_INVALID_ARG, "NULL grid, params or energy");
-  if (g->nx < 1 || g->ny < 1) return set_err(nullptr, JKO_ERR_INVALID_ARG, "nx, ny must be >= 1");
+  const char* msg = "";
+  const jko_status st = jko::check_create_args(g, p, en, &msg);
+  return st == JKO_OK ? JKO_OK : set_err(nullptr, st, msg);
+}
+
+}  // namespace
+
+namespace jko {
+// The argument checks of jko_create, shared with jko_step_noalloc: no
+// allocation, no device call; *msg receives a static description.
+jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_energy* en,
+                             const char** msg) {
+  if (!g || !p || !en) return (*msg = "NULL grid, params or energy", JKO_ERR_INVALID_ARG);
+  if (g->nx < 1 || g->ny < 1) return (*msg = "nx, ny must be >= 1", JKO_ERR_INVALID_ARG);
   if ((long long)g->nx * g->ny > (1LL << 30))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "grid larger than 2^30 cells");
+    return (*msg = "grid larger than 2^30 cells", JKO_ERR_INVALID_ARG);
   if (!(g->lx > 0) || !(g->ly > 0) || !std::isfinite(g->lx) || !std::isfinite(g->ly))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "lx, ly must be finite and > 0");
+    return (*msg = "lx, ly must be finite and > 0", JKO_ERR_INVALID_ARG);
   if (!(p->gamma > 0) || !std::isfinite(p->gamma))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "gamma must be finite and > 0");
+    return (*msg = "gamma must be finite and > 0", JKO_ERR_INVALID_ARG);
   if (!(p->tau > 0) || !std::isfinite(p->tau))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "tau must be finite and > 0");
-  if (!(p->tol >= 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "tol must be >= 0");
-  if (p->max_iter < 1) return set_err(nullptr, JKO_ERR_INVALID_ARG, "max_iter must be >= 1");
-  if (p->check_every < 0) return set_err(nullptr, JKO_ERR_INVALID_ARG, "check_every must be >= 0");
+    return (*msg = "tau must be finite and > 0", JKO_ERR_INVALID_ARG);
+  if (!(p->tol >= 0)) return (*msg = "tol must be >= 0", JKO_ERR_INVALID_ARG);
+  if (p->max_iter < 1) return (*msg = "max_iter must be >= 1", JKO_ERR_INVALID_ARG);
+  if (p->check_every < 0) return (*msg = "check_every must be >= 0", JKO_ERR_INVALID_ARG);
   if (p->precision < JKO_FP64 || p->precision > JKO_BF16X3)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "unknown precision");
+    return (*msg = "unknown precision", JKO_ERR_INVALID_ARG);
   if (p->loop < 0 || p->loop > 3)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "loop must be 0 (automatic), 1, 2 or 3");
+    return (*msg = "loop must be 0 (automatic), 1, 2 or 3", JKO_ERR_INVALID_ARG);
   if (p->tile != 0 && p->tile != 64 && p->tile != 128)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "tile must be 0 (automatic), 64 or 128");
+    return (*msg = "tile must be 0 (automatic), 64 or 128", JKO_ERR_INVALID_ARG);
   if (p->absorb < 0 || p->absorb > 2)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "absorb must be 0 (automatic), 1 or 2");
-  if (!(en->kappa > 0)) return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa must be > 0 (INFINITY = none)");
+    return (*msg = "absorb must be 0 (automatic), 1 or 2", JKO_ERR_INVALID_ARG);
+  if (!(en->kappa > 0)) return (*msg = "kappa must be > 0 (INFINITY = none)", JKO_ERR_INVALID_ARG);
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "m must be 0 or >= 1");
+    return (*msg = "m must be 0 or >= 1", JKO_ERR_INVALID_ARG);
   if (en->target) {
     if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
-      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
-                     "the Wasserstein attraction runs on JKO_FP32 / JKO_FP64 only");
+      return (*msg = "the Wasserstein attraction runs on JKO_FP32 / JKO_FP64 only", JKO_ERR_UNSUPPORTED);
     double tot = 0.0;
     for (long long i = 0; i < (long long)g->nx * g->ny; ++i) {
       const double v = en->target[i];
       if (!(v >= 0) || !std::isfinite(v))
-        return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must be finite and >= 0");
+        return (*msg = "target must be finite and >= 0", JKO_ERR_INVALID_ARG);
       if (en->mask && en->mask[i] && v != 0)
-        return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must vanish on the mask");
+        return (*msg = "target must vanish on the mask", JKO_ERR_INVALID_ARG);
       tot += v;
     }
     if (std::fabs(tot - 1.0) > 1e-3)
-      return set_err(nullptr, JKO_ERR_INVALID_ARG, "target must sum to 1");
+      return (*msg = "target must sum to 1", JKO_ERR_INVALID_ARG);
   }
   if (g->heat_L < 0 || g->heat_L > 1000)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "heat_L must be 0 (Gaussian) or in [1, 1000]");
+    return (*msg = "heat_L must be 0 (Gaussian) or in [1, 1000]", JKO_ERR_INVALID_ARG);
   if (g->heat_L > 0) {
     if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
-      return set_err(nullptr, JKO_ERR_UNSUPPORTED, "the heat kernel runs on JKO_FP32 / JKO_FP64 only");
+      return (*msg = "the heat kernel runs on JKO_FP32 / JKO_FP64 only", JKO_ERR_UNSUPPORTED);
     if (en->target || en->species == 2)
-      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
-                     "the heat kernel serves one density without attraction");
+      return (*msg = "the heat kernel serves one density without attraction", JKO_ERR_UNSUPPORTED);
   }
   if (!(en->pair_alpha >= 0) || !std::isfinite(en->pair_alpha))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "pair_alpha must be finite and >= 0");
+    return (*msg = "pair_alpha must be finite and >= 0", JKO_ERR_INVALID_ARG);
   if (en->pair_alpha > 0 && en->species != 2)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "pair_alpha couples two species (species = 2)");
+    return (*msg = "pair_alpha couples two species (species = 2)", JKO_ERR_INVALID_ARG);
   if (en->species < 0 || en->species > 2)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "species must be 0, 1 or 2");
+    return (*msg = "species must be 0, 1 or 2", JKO_ERR_INVALID_ARG);
   if (en->species == 2) {
     if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
-      return set_err(nullptr, JKO_ERR_UNSUPPORTED, "two species run on JKO_FP32 / JKO_FP64 only");
+      return (*msg = "two species run on JKO_FP32 / JKO_FP64 only", JKO_ERR_UNSUPPORTED);
     if (en->m != 0.0 || en->m_field || en->binary || en->target || en->kappa_field || en->mask)
-      return set_err(nullptr, JKO_ERR_UNSUPPORTED,
-                     "two species take a scalar congestion bound and potentials only");
+      return (*msg = "two species take a scalar congestion bound and potentials only", JKO_ERR_UNSUPPORTED);
     if (en->w2)
       for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
-        if (!std::isfinite(en->w2[i])) return set_err(nullptr, JKO_ERR_INVALID_ARG, "w2 must be finite");
+        if (!std::isfinite(en->w2[i])) return (*msg = "w2 must be finite", JKO_ERR_INVALID_ARG);
   }
   if (en->binary != 0 && en->binary != 1)
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary must be 0 or 1");
+    return (*msg = "binary must be 0 or 1", JKO_ERR_INVALID_ARG);
   if (en->binary && (en->m != 0.0 || en->m_field))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion takes no entropy term (m = 0)");
+    return (*msg = "binary congestion takes no entropy term (m = 0)", JKO_ERR_INVALID_ARG);
   if (en->binary && !en->kappa_field && !std::isfinite(en->kappa))
-    return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion needs a finite kappa");
+    return (*msg = "binary congestion needs a finite kappa", JKO_ERR_INVALID_ARG);
   if (en->binary && en->kappa_field)
     for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
       if (!std::isfinite(en->kappa_field[i]))
-        return set_err(nullptr, JKO_ERR_INVALID_ARG, "binary congestion needs a finite kappa");
+        return (*msg = "binary congestion needs a finite kappa", JKO_ERR_INVALID_ARG);
   if (en->m_field)
     for (long long i = 0; i < (long long)g->nx * g->ny; ++i)
       if (!(en->m_field[i] >= 1.0) || !std::isfinite(en->m_field[i]))
-        return set_err(nullptr, JKO_ERR_INVALID_ARG, "m_field entries must be finite and >= 1");
+        return (*msg = "m_field entries must be finite and >= 1", JKO_ERR_INVALID_ARG);
   const long long N = (long long)g->nx * g->ny;
   for (long long i = 0; i < N; ++i) {
     if (en->w && !std::isfinite(en->w[i]))
-      return set_err(nullptr, JKO_ERR_INVALID_ARG, "w must be finite");
+      return (*msg = "w must be finite", JKO_ERR_INVALID_ARG);
     if (en->kappa_field && !(en->kappa_field[i] > 0))
-      return set_err(nullptr, JKO_ERR_INVALID_ARG, "kappa_field must be > 0");
+      return (*msg = "kappa_field must be > 0", JKO_ERR_INVALID_ARG);
     if (en->alpha && (!(en->alpha[i] > 0) || !std::isfinite(en->alpha[i])))
-      return set_err(nullptr, JKO_ERR_INVALID_ARG, "alpha must be finite and > 0");
+      return (*msg = "alpha must be finite and > 0", JKO_ERR_INVALID_ARG);
     if (en->mask && en->mask[i] > 1)
-      return set_err(nullptr, JKO_ERR_INVALID_ARG, "mask entries must be 0 or 1");
+      return (*msg = "mask entries must be 0 or 1", JKO_ERR_INVALID_ARG);
   }
   return JKO_OK;
 }
+}  // namespace jko
+
+namespace {
 
 template <typename T>
 jko_status build_energy(jko_handle* h, const jko_energy* en) {
@@ -1381,7 +1393,7 @@ jko_status tune_batch(jko_batch* b) {
     jko_handle* h = b->h[f];
     if (c == 0) return own[f];
     if (c == 1) return (int)CAND_PP64;
-    if (c == 2) return h->prec == JKO_BF16X3 ? (int)CAND_PP64 : (int)CAND_PP128;
+    if (c == 2) return h->prec != JKO_TF32 ? (int)CAND_PP64 : (int)CAND_PP128;
     return jko::tc_loop_supported(h->tc) ? (int)CAND_LOOP : (int)CAND_PP64;
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -112,5 +112,10 @@ jko_status step_internal(jko_handle* h, const void* q_in, void* p_out, jko_step_
                          bool validate);
 // Records an error message on the handle and returns the status.
 jko_status handle_error(jko_handle* h, jko_status st, const std::string& msg);
+// Argument checks of jko_create (sizes, parameters, energy fields): JKO_OK, or
+// the error status with *msg set to a static description.  Allocates nothing
+// and makes no device call, so jko_step_noalloc runs the same checks.
+jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_energy* en,
+                             const char** msg);
 
 }  // namespace jko

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "jko.h"
+#include "jko_handle.h"
 #include "jko_kernels.h"
 
 namespace {
@@ -133,8 +134,11 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
                                        void* stream, jko_step_info* info) {
   if (!grid || !prm || !en || !q_dev || !p_out_dev)
     return fail(JKO_ERR_INVALID_ARG, "NULL argument");
-  if (grid->nx < 1 || grid->ny < 1)
-    return fail(JKO_ERR_INVALID_ARG, "jko_step_noalloc: nx, ny must be >= 1");
+  // every argument check of jko_create (parameters finite and in range, energy
+  // fields, species and pair_alpha consistent), then the limits of this form
+  const char* msg = "";
+  const jko_status chk = jko::check_create_args(grid, prm, en, &msg);
+  if (chk != JKO_OK) return fail(chk, msg);
   if (grid->nx > kMaxSide || grid->ny > kMaxSide)
     return fail(JKO_ERR_UNSUPPORTED,
                 "jko_step_noalloc: grid exceeds the fixed scratch (nx, ny must be <= 256)");
@@ -150,19 +154,10 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: two species are not available");
   if (grid->heat_L != 0)
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the heat kernel is not available");
-  if (!(grid->lx > 0) || !(grid->ly > 0) || !(prm->gamma > 0) || !(prm->tau > 0) ||
-      !(prm->tol >= 0) || prm->max_iter < 1 || prm->check_every < 0 || !(en->kappa > 0) ||
-      !(en->m == 0.0 || en->m >= 1.0))
-    return fail(JKO_ERR_INVALID_ARG, "jko_step_noalloc: invalid parameters");
   if (jko::simt_tap_padding() != kTapPad)
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: tap padding mismatch");
   const int nx = grid->nx, ny = grid->ny;
   const long long N = (long long)nx * ny;
-  for (long long i = 0; i < N; ++i) {
-    if ((en->w && !std::isfinite(en->w[i])) || (en->kappa_field && !(en->kappa_field[i] > 0)) ||
-        (en->alpha && !(en->alpha[i] > 0)) || (en->mask && en->mask[i] > 1))
-      return fail(JKO_ERR_INVALID_ARG, "jko_step_noalloc: invalid energy field");
-  }
 
   unsigned char* base = nullptr;
   NA_CK(scratch_base(&base));

@@ -58,3 +58,41 @@ def test_create_rejects_bad_arguments_on_host(libjko):
         jko.jko_create(0, 8, gamma=1e-2, tau=0.1, stream=0)
     with pytest.raises(jko.JKOError):
         jko.jko_create(8, 8, gamma=1e-2, tau=0.1, m=0.5, stream=0)
+
+
+def test_noalloc_step_runs_the_create_checks_on_host(libjko):
+    """jko_step_noalloc rejects what jko_create rejects before touching the
+    device (its checks are jko_create's): pair_alpha without a second species,
+    an unknown species count, non-finite gamma, tau, lengths or exponent.  The
+    device pointers are placeholders that are never dereferenced."""
+    import math
+    from paper_1502_06216_gb300 import jko
+    L = jko.lib()
+    dummy = ctypes.c_void_p(16)
+
+    def status(grid_kw=None, params_kw=None, energy_kw=None):
+        g = jko.jko_grid(8, 8, 1.0, 1.0, 0)
+        p = jko.jko_params(1e-2, 0.1, 1e-6, 10, 0, int(jko.Precision.FP32), 1, 0, 0, 0)
+        e = jko.jko_energy(None, math.inf, None, 0.0, None, None, None, 0, None, 1, None, 0.0)
+        for obj, kw in ((g, grid_kw), (p, params_kw), (e, energy_kw)):
+            for k, v in (kw or {}).items():
+                setattr(obj, k, v)
+        info = jko.jko_step_info()
+        return L.jko_step_noalloc(ctypes.byref(g), ctypes.byref(p), ctypes.byref(e), dummy, dummy,
+                                  None, ctypes.byref(info))
+
+    bad = [dict(energy_kw=dict(pair_alpha=0.5)),                 # needs species = 2
+           dict(energy_kw=dict(species=3)),
+           dict(energy_kw=dict(species=-1)),
+           dict(params_kw=dict(gamma=math.inf)),
+           dict(params_kw=dict(tau=math.inf)),
+           dict(params_kw=dict(gamma=-1.0)),
+           dict(grid_kw=dict(lx=math.inf)),
+           dict(energy_kw=dict(m=math.inf)),
+           dict(energy_kw=dict(m=0.5)),
+           dict(energy_kw=dict(pair_alpha=math.nan, species=2))]
+    for case in bad:
+        assert status(**case) == jko.Status.INVALID_ARG, case
+    # limits of the fixed scratch: reported as unsupported, still on the host
+    assert status(grid_kw=dict(nx=257)) == jko.Status.UNSUPPORTED
+    assert status(params_kw=dict(precision=int(jko.Precision.BF16))) == jko.Status.UNSUPPORTED
