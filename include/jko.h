@@ -68,8 +68,10 @@ typedef enum jko_precision {
   JKO_FP64 = 0,    /* CUDA cores, double throughout */
   JKO_FP32 = 1,    /* CUDA cores, float throughout */
   JKO_TF32 = 2,    /* tensor cores (tcgen05 kind::tf32), fp32 accumulation */
-  JKO_BF16 = 3,    /* tensor cores (tcgen05 kind::f16, bf16 operands), fp32 accumulation */
-  JKO_BF16X3 = 4   /* tensor cores, three bf16 products hi*hi + hi*lo + lo*hi */
+  JKO_BF16 = 3,    /* tensor cores (tcgen05 kind::f16), fp32 accumulation: the Gibbs
+                      factor in bf16, each scaling image as a bf16 pair hi + lo (two
+                      products K * hi + K * lo, ~16 significant bits in the images) */
+  JKO_BF16X3 = 4   /* tensor cores, the factor also as a pair: K_hi * (hi + lo) + K_lo * hi */
 } jko_precision;
 
 /* Uniform grid on [0,lx] x [0,ly] (Sec. 2, numerical grids of Sec. 4). */
@@ -103,7 +105,7 @@ typedef struct jko_params {
                        kernel per pass, 3 = as 1, and in a batch the flow joins the
                        grouped launch of its precision (jko_batch_create) */
   int tile;         /* tensor-core precisions: output tile width of the per-pass kernels,
-                       64 or 128 (128: not JKO_BF16X3), or 0 = automatic.  With loop = 0
+                       64 or 128 (128: JKO_TF32 only), or 0 = automatic.  With loop = 0
                        and tile = 0 on grids of 256^2 cells or more, jko_create times the
                        loop kernel and the per-pass kernels at both widths on 16 pairs and
                        keeps the fastest; the choice is cached per grid, lengths, gamma,
@@ -371,7 +373,8 @@ const char* jko_build_info(void);
  * spectrum interval [1, lmax] of A = Id - (gamma/L) Delta, lmax = 1 + 4 (gamma/L)
  * (1/hx^2 + 1/hy^2), truncated for `precision` (JKO_FP64: dropped
  * coefficients below ~1e-15 or their rounding floor: the series within ~1e-14
- * of lambda^{-L}; JKO_FP32: ~1e-10).  Writes the degree D to
+ * of lambda^{-L}; JKO_FP32 handles truncate alike, since their recurrence
+ * also runs in FP64).  Writes the degree D to
  * *degree, min(D + 1, cap) coefficients to coef (may be NULL when cap = 0) and,
  * if interval is not NULL, (1, lmax) to interval[0..1].  JKO_ERR_INVALID_ARG
  * for sizes, lengths, gamma or L out of range (as jko_create);

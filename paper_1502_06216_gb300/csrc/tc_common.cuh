@@ -32,9 +32,22 @@ constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier polls
 
 enum : int { MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_TF32 = 2 };
 
-// Bytes of one pipeline stage.
+// Operand forms.  TF32: one tf32 x tf32 product.  BF16: the Gibbs factor in
+// bf16, every image operand (a, b and the intermediate) as a pair x = hi + lo
+// of bf16, so one product K_hi . (x_hi + x_lo); a single bf16 image rounds
+// the smooth scalings the same way over whole regions and costs up to 4e-3
+// of relative L1 in one pair, the pair ~2e-5.  BF16X3: also the factor as a
+// pair, K_hi . (x_hi + x_lo) + K_lo . x_hi.  The image pair sits in one
+// shared-memory block of 2 BN rows (hi rows, then lo rows), so K_hi . [x_hi;
+// x_lo] is one MMA of width 2 BN whose accumulator halves are added in the
+// epilogue.
+__host__ __device__ constexpr bool img_split(int mode) { return mode != MODE_TF32; }
+__host__ __device__ constexpr bool fac_split(int mode) { return mode == MODE_BF16X3; }
+
+// Bytes of one pipeline stage: factor hi, image hi, image lo, factor lo.
 __host__ __device__ constexpr uint32_t stage_bytes(int mode, int bn) {
-  return (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)(BM + bn) * (uint32_t)KB_BYTES;
+  return ((fac_split(mode) ? 2u : 1u) * (uint32_t)BM + (img_split(mode) ? 2u : 1u) * (uint32_t)bn) *
+         (uint32_t)KB_BYTES;
 }
 // Epilogue tiles kept beside the stages: b-update pass -> q (fp32) and the old
 // b (operand type, hi [+ lo]); prox pass -> e^{-sigma w} (fp32) and the staged
@@ -42,7 +55,7 @@ __host__ __device__ constexpr uint32_t stage_bytes(int mode, int bn) {
 __host__ __device__ constexpr uint32_t epi_bytes(int mode, int epi, int bn) {
   return epi == 0 ? 0u
          : epi == 1 ? (uint32_t)bn * BM * 4u +
-                          (mode == MODE_BF16X3 ? 2u : 1u) * (uint32_t)bn * BM *
+                          (img_split(mode) ? 2u : 1u) * (uint32_t)bn * BM *
                               (mode == MODE_TF32 ? 4u : 2u)
                     : 2u * (uint32_t)bn * BM * 4u;
 }
@@ -142,6 +155,20 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t b
         : "memory");
   }
 }
+// The MMAs of one 16-byte-aligned K-step kk (0..3) of a stage: a_hi / a_lo
+// are the factor halves, b the image block (hi rows then lo rows when split);
+// accum = 0 starts the accumulator.  Accumulator columns: [0, BN) the hi
+// product (plus K_lo . x_hi), [BN, 2 BN) the lo product.
+template <int MODE, int BN>
+__device__ __forceinline__ void umma_kstep(uint32_t tmem_d, uint64_t a_hi, uint64_t a_lo,
+                                           uint64_t b, int kk, uint32_t accum);
+template <int MODE>
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N);
+// TMEM columns of a BN-wide tile's accumulator (a power of two >= 32).
+__host__ __device__ constexpr uint32_t acc_cols(int mode, int bn) {
+  return (img_split(mode) ? 2u : 1u) * (uint32_t)bn < 32u ? 32u
+                                                           : (img_split(mode) ? 2u : 1u) * (uint32_t)bn;
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -238,6 +265,40 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+template <int MODE, int BN>
+__device__ __forceinline__ void umma_kstep(uint32_t tmem_d, uint64_t a_hi, uint64_t a_lo,
+                                           uint64_t b, int kk, uint32_t accum) {
+  const uint64_t adv = (uint64_t)(kk * 2);   // +32 bytes of K in 16-byte units
+  if constexpr (!img_split(MODE)) {
+    umma<MODE>(tmem_d, a_hi + adv, b + adv, make_idesc<MODE>(BM, BN), accum);
+  } else {
+    umma<MODE>(tmem_d, a_hi + adv, b + adv, make_idesc<MODE>(BM, 2 * BN), accum);
+    if constexpr (fac_split(MODE)) umma<MODE>(tmem_d, a_lo + adv, b + adv, make_idesc<MODE>(BM, BN), 1u);
+  }
+}
+
+// 16 accumulator columns c0 .. c0+15 of this warp's 32 TMEM lanes as floats:
+// the hi and lo products added (split images) or the single product.
+template <int MODE, int BN>
+__device__ __forceinline__ void tmem_tile16(uint32_t taddr_lane, int c0, float (&v)[16]) {
+  uint32_t r0[16];
+  tmem_ld16_issue(taddr_lane + (uint32_t)c0, r0);
+  if constexpr (img_split(MODE)) {
+    uint32_t r1[16];
+    tmem_ld16_issue(taddr_lane + (uint32_t)(BN + c0), r1);
+    tmem_wait_ld();
+    reg_fence16(r0);
+    reg_fence16(r1);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+  } else {
+    tmem_wait_ld();
+    reg_fence16(r0);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r0[j]);
+  }
+}
+
 template <int MODE> struct OpT;
 template <> struct OpT<MODE_BF16> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
 template <> struct OpT<MODE_BF16X3> { using T = __nv_bfloat16; static constexpr int kElems = 64; };
@@ -249,12 +310,23 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// The value an image element takes once stored as operand (tf32, or the
+// bf16 pair hi + lo), as the kernels read it back.
+template <int MODE>
+__device__ __forceinline__ float op_value(float v) {
+  if constexpr (MODE == MODE_TF32) {
+    return tf32_round(v);
+  } else {
+    const float h = __bfloat162float(__float2bfloat16_rn(v));
+    return h + __bfloat162float(__float2bfloat16_rn(v - h));
+  }
+}
+
 // Operand value of one image element (hi [+ lo]) as float.
 template <int MODE, typename T>
 __device__ __forceinline__ float op_load(const T* hi, const T* lo, size_t i) {
   if constexpr (MODE == MODE_TF32) return hi[i];
-  else if constexpr (MODE == MODE_BF16X3) return __bfloat162float(hi[i]) + __bfloat162float(lo[i]);
-  else return __bfloat162float(hi[i]);
+  else return __bfloat162float(hi[i]) + __bfloat162float(lo[i]);
 }
 template <int MODE, typename T>
 __device__ __forceinline__ void op_store(T* hi, T* lo, size_t i, float v) {
@@ -263,7 +335,7 @@ __device__ __forceinline__ void op_store(T* hi, T* lo, size_t i, float v) {
   } else {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[i] = h;
-    if constexpr (MODE == MODE_BF16X3) lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
@@ -324,7 +396,7 @@ __device__ __forceinline__ void load_op16(const T* hi, const T* lo, size_t off, 
           o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
         }
       }
-      if constexpr (MODE == MODE_BF16X3) {
+      if constexpr (img_split(MODE)) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const uint4 t = reinterpret_cast<const uint4*>(lo + off)[q];
@@ -342,6 +414,59 @@ __device__ __forceinline__ void load_op16(const T* hi, const T* lo, size_t off, 
     for (int j = 0; j < 16; ++j) o[j] = j < cnt ? op_load<MODE>(hi, lo, off + j) : 0.0f;
   }
 }
+// load_op16 through L2 only (ld.global.cg): for an image this CTA rewrites
+// with TMA stores between its reads, where an L1 copy from the previous read
+// would be stale.
+template <int MODE, typename T>
+__device__ __forceinline__ void load_op16_cg(const T* hi, const T* lo, size_t off, int cnt,
+                                             float (&o)[16]) {
+  if (cnt == 16) {
+    if constexpr (MODE == MODE_TF32) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = __ldcg(reinterpret_cast<const float4*>(hi + off) + q);
+        o[4 * q] = t.x; o[4 * q + 1] = t.y; o[4 * q + 2] = t.z; o[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint4 t = __ldcg(reinterpret_cast<const uint4*>(hi + off) + q);
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(w[k]);
+          o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint4 t = __ldcg(reinterpret_cast<const uint4*>(lo + off) + q);
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = unpack_bf16x2(w[k]);
+          o[8 * q + 2 * k] += f.x; o[8 * q + 2 * k + 1] += f.y;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float x = 0.0f;
+      if (j < cnt) {
+        if constexpr (MODE == MODE_TF32) {
+          x = __ldcg(hi + off + j);
+        } else {
+          const unsigned short h = __ldcg(reinterpret_cast<const unsigned short*>(hi + off + j));
+          const unsigned short l = __ldcg(reinterpret_cast<const unsigned short*>(lo + off + j));
+          x = __uint_as_float((uint32_t)h << 16) + __uint_as_float((uint32_t)l << 16);
+        }
+      }
+      o[j] = x;
+    }
+  }
+}
+
 // Writes 16 values of local row r, columns 16c .. 16c+15, into the staging
 // tile in the layout of a 128-byte-swizzled TMA box of 128 rows: column block
 // cb holds 128 bytes per row; the 16-byte chunk k of row r sits at k ^ (r & 7).
@@ -378,7 +503,7 @@ __device__ __forceinline__ void stage16(unsigned char* st_hi, unsigned char* st_
       u.x = pack_bf16x2(h[0], h[1]); u.y = pack_bf16x2(h[2], h[3]);
       u.z = pack_bf16x2(h[4], h[5]); u.w = pack_bf16x2(h[6], h[7]);
       *reinterpret_cast<uint4*>(row_hi + (((k0 + q) ^ (r & 7)) << 4)) = u;
-      if constexpr (MODE == MODE_BF16X3) {
+      if constexpr (img_split(MODE)) {
         uint4 w;
         w.x = pack_bf16x2(l[0], l[1]); w.y = pack_bf16x2(l[2], l[3]);
         w.z = pack_bf16x2(l[4], l[5]); w.w = pack_bf16x2(l[6], l[7]);
@@ -427,7 +552,7 @@ __device__ __forceinline__ void smem_ld_op16(const unsigned char* hi, const unsi
         const float2 f = unpack_bf16x2(w[k]);
         o[8 * q + 2 * k] = f.x; o[8 * q + 2 * k + 1] = f.y;
       }
-      if constexpr (MODE == MODE_BF16X3) {
+      if constexpr (img_split(MODE)) {
         const uint4 u = *reinterpret_cast<const uint4*>(lo + off);
         const uint32_t z[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll

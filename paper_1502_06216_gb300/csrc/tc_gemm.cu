@@ -21,9 +21,11 @@
 // factor is a normal number in the operand precision (entries beyond it are
 // stored as exact zeros), so the skipped tiles contribute exactly zero.
 //
-// Precision modes: BF16 (one bf16 x bf16 product), BF16X3 (hi*hi + hi*lo +
-// lo*hi with x = hi + lo split into two bf16), TF32 (kind::tf32, operands
-// rounded to tf32).  Accumulation is FP32 in TMEM throughout.
+// Precision modes (see img_split / fac_split in tc_common.cuh): TF32
+// (kind::tf32, operands rounded to tf32), BF16 (bf16 factor times the image
+// as a bf16 pair hi + lo: one MMA of width 2 BN), BF16X3 (that plus the
+// factor's lo part times the image's hi part).  Accumulation is FP32 in TMEM
+// throughout.
 #include "tc_common.cuh"
 
 namespace jko {
@@ -56,20 +58,19 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;                  // elements per K-block
   constexpr int UK = (MODE == MODE_TF32) ? 8 : 16;      // K per MMA
-  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;  // hi (+ lo) operand tiles
+  constexpr int NSPLIT = img_split(MODE) ? 2 : 1;        // image hi (+ lo) tiles
   constexpr uint32_t A_BYTES = BM * KB_BYTES;
   constexpr uint32_t B_BYTES = BN * KB_BYTES;
-  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  constexpr uint32_t STAGE_BYTES = stage_bytes(MODE, BN);
+  constexpr uint32_t ALO_OFF = A_BYTES + NSPLIT * B_BYTES;  // factor lo (BF16X3)
   constexpr int STAGES = num_stages(MODE, EPI, BN);
   constexpr uint32_t EPI_BYTES = epi_bytes(MODE, EPI, BN);
   // the prox pass loads e^{-sigma w} only for the congestion/potential kind
   constexpr uint32_t EPI_LOAD =
       (EPI == EPI_A && EK != EK_CROWD) ? 0u : epi_load_bytes(MODE, EPI, BN);
   constexpr uint32_t F32_TILE = (uint32_t)BN * BM * 4u;   // one fp32 epilogue tile
-  static_assert(STAGE_BYTES == stage_bytes(MODE, BN), "stage size");
   static_assert(STAGES >= 2, "at least two stages");
-  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
-  constexpr uint32_t IDESC = make_idesc<MODE>(BM, BN);
+  constexpr uint32_t TMEM_COLS = acc_cols(MODE, BN);
 
   Ctrl* ctrl = args.ctrl;
   __shared__ int s_it;
@@ -156,10 +157,8 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       const int kx = kb.x + i * KE;
       tma_load_2d(st, &mapA_hi, &full_bar[s], kx, m0);
       tma_load_2d(st + A_BYTES, &mapB_hi, &full_bar[s], kx, n0);
-      if constexpr (NSPLIT == 2) {
-        tma_load_2d(st + A_BYTES + B_BYTES, &mapA_lo, &full_bar[s], kx, m0);
-        tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapB_lo, &full_bar[s], kx, n0);
-      }
+      if constexpr (NSPLIT == 2) tma_load_2d(st + A_BYTES + B_BYTES, &mapB_lo, &full_bar[s], kx, n0);
+      if constexpr (fac_split(MODE)) tma_load_2d(st + ALO_OFF, &mapA_lo, &full_bar[s], kx, m0);
     }
     if (!ok) atomicOr(&s_fault, 1);
   } else if (warp == 1 && lane == 0) {
@@ -171,19 +170,11 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
       tc_fence_after();
       const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
       const uint64_t a_hi = sdesc_sw128(sa);
-      const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+      const uint64_t a_lo = sdesc_sw128(sa + ALO_OFF);
+      const uint64_t b = sdesc_sw128(sa + A_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < KB_BYTES / 32; ++kk) {   // 32 bytes of K per MMA
-        const uint64_t adv = (uint64_t)(kk * 2);      // +32 bytes in 16-byte units
-        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-        umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
-        if constexpr (NSPLIT == 2) {
-          const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
-          const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
-          umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
-          umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
-        }
-      }
+      for (int kk = 0; kk < KB_BYTES / 32; ++kk)   // 32 bytes of K per MMA
+        umma_kstep<MODE, BN>(tmem_base, a_hi, a_lo, b, kk, (i > 0 || kk > 0) ? 1u : 0u);
       umma_commit(&empty_bar[s]);   // frees the stage once these MMAs have read it
     }
     umma_commit(accum_bar);          // accumulator complete
@@ -224,20 +215,26 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
     // unrolled so that their shared-memory loads and arithmetic overlap
     constexpr int NCH = BN / 16 / NWG;   // chunks per thread
     static_assert(NCH >= 1 && NCH * 16 * NWG == BN, "column groups cover the tile");
+    static_assert(NCH == 1 || !img_split(MODE), "split images: one chunk per thread");
     uint32_t racc[NCH][16];
+    float vsum[16];
+    if constexpr (img_split(MODE)) {
+      tmem_tile16<MODE, BN>(tmem_base + ((uint32_t)(quad * 32) << 16), grp * 16, vsum);
+    } else {
 #pragma unroll
-    for (int cc = 0; cc < NCH; ++cc)
-      tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)((grp * NCH + cc) * 16),
-                      racc[cc]);
-    tmem_wait_ld();
+      for (int cc = 0; cc < NCH; ++cc)
+        tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)((grp * NCH + cc) * 16),
+                        racc[cc]);
+      tmem_wait_ld();
 #pragma unroll
-    for (int cc = 0; cc < NCH; ++cc) reg_fence16(racc[cc]);
+      for (int cc = 0; cc < NCH; ++cc) reg_fence16(racc[cc]);
+    }
 #pragma unroll
     for (int cc = 0; cc < NCH; ++cc) {
       const int c = grp * NCH + cc;
       float v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[cc][j]);
+      for (int j = 0; j < 16; ++j) v[j] = img_split(MODE) ? vsum[j] : __uint_as_float(racc[cc][j]);
       const int nb = n0 + c * 16;
       int cnt = args.N - nb;
       cnt = !row_ok || cnt < 0 ? 0 : (cnt > 16 ? 16 : cnt);
@@ -393,9 +390,10 @@ cudaError_t set_attrs_bn() {
 }
 
 // 128-wide tiles exist for the forms whose epilogue tiles leave room for at
-// least two pipeline stages (not BF16X3).
+// least two pipeline stages: TF32 (the image pairs of BF16 / BF16X3 double
+// the image blocks and the old-b tile).
 template <int MODE>
-constexpr bool has_bn128() { return MODE != MODE_BF16X3; }
+constexpr bool has_bn128() { return !img_split(MODE); }
 
 template <int MODE>
 cudaError_t set_attrs() {
@@ -534,7 +532,7 @@ int absorbed_energy(TcPlan* P, const std::vector<double>& bx, const std::vector<
 void pass_flops_of(TcPlan* P) {
   const TcConfig& c = P->cfg;
   const int KE = P->mode == MODE_TF32 ? 32 : 64;
-  const double mult = P->mode == MODE_BF16X3 ? 3.0 : 1.0;
+  const double mult = P->mode == MODE_BF16X3 ? 3.0 : (P->mode == MODE_BF16 ? 2.0 : 1.0);
   for (int pass = 0; pass < 4; ++pass) {
     const int axis = (pass & 1) == 0 ? 0 : 1;
     const int side = P->absorbed ? (pass >> 1) : 0;
@@ -555,7 +553,8 @@ int create_typed(TcPlan* P, std::string* msg) {
   const int align = 16 / (int)sizeof(T);
   P->px = round_up(nx, align);
   P->py = round_up(ny, align);
-  const int nsplit = P->mode == MODE_BF16X3 ? 2 : 1;
+  const int nsplit = img_split(P->mode) ? 2 : 1;        // image hi (+ lo)
+  const int ksplit = fac_split(P->mode) ? 2 : 1;        // factor hi (+ lo)
   const int KE = P->mode == MODE_TF32 ? 32 : 64;
   P->absorbed = c.absorb && c.w_host ? 1 : 0;
   std::vector<double> beta[2];
@@ -572,7 +571,7 @@ int create_typed(TcPlan* P, std::string* msg) {
         *msg = "absorbed Gibbs factor overflows FP32 (potential too steep for gamma)";
         return 1;
       }
-      for (int sp = 0; sp < nsplit; ++sp) {
+      for (int sp = 0; sp < ksplit; ++sp) {
         const auto& src = sp == 0 ? hi : lo;
         if (cudaMalloc(&P->k[axis][side][sp], src.size() * sizeof(T)) != cudaSuccess ||
             cudaMemcpy(P->k[axis][side][sp], src.data(), src.size() * sizeof(T),
@@ -605,22 +604,23 @@ int create_typed(TcPlan* P, std::string* msg) {
   auto pick = [](int M, int N) { return ((M + BM - 1) / BM) * ((N + 127) / 128) >= 152 ? 128 : 64; };
   P->bn_x = pick(nx, ny);  // pass over x: M = nx, N = ny
   P->bn_y = pick(ny, nx);  // pass over y: M = ny, N = nx
-  if (P->mode == MODE_BF16X3) P->bn_x = P->bn_y = 64;
+  if (img_split(P->mode)) P->bn_x = P->bn_y = 64;
   // tensor maps (hi and lo; lo maps alias hi when unused; b side aliases a side)
   const int m = P->mode;
   for (int sp = 0; sp < 2; ++sp) {
     const int si = sp < nsplit ? sp : 0;
+    const int ki = sp < ksplit ? sp : 0;
     bool ok = true;
     for (int axis = 0; axis < 2 && ok; ++axis)
       for (int side = 0; side < 2 && ok; ++side) {
         const int sd = P->absorbed ? side : 0;
         const int n = axis == 0 ? nx : ny;
-        ok = make_map(&P->mK[axis][side][sp], P->k[axis][sd][si], m, n, n,
+        ok = make_map(&P->mK[axis][side][sp], P->k[axis][sd][ki], m, n, n,
                       axis == 0 ? P->px : P->py, BM);
       }
     // image operand loads: boxes of 64 rows (64-wide tiles) and, where the
     // mode has them, 128 rows (128-wide tiles)
-    const int wide = m == MODE_BF16X3 ? 64 : 128;
+    const int wide = img_split(m) ? 64 : 128;
     ok = ok && make_map(&P->lA[sp], P->img_a[si], m, ny, nx, P->px, 64) &&
          make_map(&P->lB[sp], P->img_b[si], m, ny, nx, P->px, 64) &&
          make_map(&P->lT[sp], P->img_t[si], m, nx, ny, P->py, 64) &&
@@ -741,7 +741,7 @@ double tc_pass_flops(const TcPlan* P, int which) { return P->flops[which & 3]; }
 int tc_tile(const TcPlan* P) { return P->bn_x == P->bn_y ? P->bn_x : 0; }
 
 int tc_set_tile(TcPlan* P, int bn) {
-  if (bn != 64 && !(bn == 128 && P->mode != MODE_BF16X3)) return 1;
+  if (bn != 64 && !(bn == 128 && !img_split(P->mode))) return 1;
   P->bn_x = P->bn_y = bn;
   pass_flops_of(P);
   return 0;

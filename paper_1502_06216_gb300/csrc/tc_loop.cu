@@ -53,21 +53,22 @@ constexpr uint32_t kGoSpinLimit = 1u << 27;
 constexpr int RES_KB = 8;
 constexpr int RES_STAGES = 4;
 
-// output staging tile (operand type, hi [+ lo]) and epilogue region: q | old b
-// in the b-update pass, e^{-sigma w} | p in the prox pass (two fp32 tiles); in
-// resident mode q | old b (operand type) and p is staged in the idle image
-// stages instead
-__host__ __device__ constexpr uint32_t loop_staging_bytes(int mode) {
-  return (mode == MODE_BF16 ? 1u : 2u) * (uint32_t)LBN * BM * 2u;
+// output staging tile (operand type: hi + lo, or one tf32 tile of the same
+// bytes) and epilogue region: q | old b in the b-update pass, e^{-sigma w} | p
+// in the prox pass (two fp32 tiles).  In resident mode the factor band leaves
+// no room for the epilogue tiles: the epilogue reads q, old b and
+// e^{-sigma w} from global memory, and p is staged in the idle image stages.
+__host__ __device__ constexpr uint32_t loop_staging_bytes(int) {
+  return 2u * (uint32_t)LBN * BM * 2u;
 }
 __host__ __device__ constexpr uint32_t loop_epi_bytes(bool res) {
-  return res ? (uint32_t)LBN * BM * 4u + (uint32_t)LBN * BM * 2u : 2u * LBN * BM * 4u;
+  return res ? 0u : 2u * LBN * BM * 4u;
 }
 __host__ __device__ constexpr uint32_t loop_res_bytes(bool res) {
   return res ? (uint32_t)RES_KB * BM * KB_BYTES : 0u;
 }
 __host__ __device__ constexpr uint32_t loop_stage_bytes(int mode, bool res) {
-  return res ? (uint32_t)LBN * KB_BYTES : stage_bytes(mode, LBN);
+  return res ? (img_split(mode) ? 2u : 1u) * (uint32_t)LBN * KB_BYTES : stage_bytes(mode, LBN);
 }
 __host__ __device__ constexpr int loop_stages(int mode, bool res) {
   return res ? RES_STAGES
@@ -98,6 +99,12 @@ struct LoopArgs {
   double* part;      // residual partial of each tile of the b-update pass
   int nparts;
   int pairs;         // pairs this launch may run
+  // resident mode: the epilogue's global reads (q and e^{-sigma w} as
+  // [ny][nx] fp32, b as the operand pair [ny][pitch_b])
+  const float* q;
+  const void* b_hi;
+  const void* b_lo;
+  int pitch_b;
 };
 
 // Tensor maps of the four passes: factor (A), image (B) and output of each
@@ -137,26 +144,32 @@ __global__ void __launch_bounds__(NTL, 1)
 tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ LoopArgs args) {
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;
-  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
+  constexpr int NSPLIT = img_split(MODE) ? 2 : 1;         // image hi (+ lo) blocks
   constexpr uint32_t A_BYTES = BM * KB_BYTES;
   constexpr uint32_t B_BYTES = LBN * KB_BYTES;
-  constexpr uint32_t STAGE_BYTES = RES ? B_BYTES : NSPLIT * (A_BYTES + B_BYTES);
+  constexpr uint32_t STAGE_BYTES = loop_stage_bytes(MODE, RES);
   constexpr int STAGES = loop_stages(MODE, RES);
-  constexpr uint32_t B_OFF = RES ? 0u : A_BYTES;          // image half within a stage
-  static_assert(STAGE_BYTES == loop_stage_bytes(MODE, RES), "stage size");
+  constexpr uint32_t B_OFF = RES ? 0u : A_BYTES;          // image blocks within a stage
+  constexpr uint32_t ALO_OFF = A_BYTES + NSPLIT * B_BYTES; // factor lo (BF16X3)
   static_assert(STAGES >= 2, "at least two stages");
   static_assert(!RES || MODE == MODE_BF16, "resident factors: BF16 only");
   constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
   constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
-  constexpr uint32_t TMEM_COLS = LBN;
-  constexpr uint32_t IDESC = make_idesc<MODE>(BM, LBN);
+  constexpr uint32_t TMEM_COLS = acc_cols(MODE, LBN);
   constexpr int CB = LBN * (int)sizeof(T) / 128;   // 128-byte column blocks of an operand tile
   constexpr uint32_t OUT_BLOCK = BM * 128;
   static_assert((uint32_t)NSPLIT * CB * OUT_BLOCK <= STG_BYTES, "staging tile");
   static_assert((uint32_t)NSPLIT * CB * OUT_BLOCK <= F32_TILE, "old b fits its tile");
   constexpr uint32_t EPI_B_LOAD = F32_TILE + (uint32_t)NSPLIT * CB * OUT_BLOCK;
   constexpr uint32_t EPI_A_LOAD = F32_TILE;
-  constexpr bool EPI3 = EK == EK_CROWD;   // the prox pass loads e^{-sigma w} tiles
+  // epilogue tiles moved by the producer: q and the old b for the b-update
+  // pass, e^{-sigma w} for the prox pass of the congestion/potential kind.  In
+  // resident mode the factor band leaves no room for a region of their own:
+  // the q or e^{-sigma w} tile goes into the output staging region, idle while
+  // the MMAs run, and the old b stays in the registers of the thread that
+  // computed it (every pair gives a thread the same cells of its one tile)
+  constexpr bool EPI1 = true;
+  constexpr bool EPI3 = EK == EK_CROWD;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -164,7 +177,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   unsigned char* stages = smem + loop_res_bytes(RES);        // operand stages
   unsigned char* st_hi = stages + STAGES * STAGE_BYTES;      // output staging
   unsigned char* st_lo = st_hi + CB * OUT_BLOCK;
-  unsigned char* epi_f = st_hi + STG_BYTES;                  // q or e^{-sigma w}
+  unsigned char* epi_f = RES ? st_hi : st_hi + STG_BYTES;    // q or e^{-sigma w}
   unsigned char* epi_g = epi_f + F32_TILE;                   // old b (or p)
   unsigned char* p_st = RES ? stages : epi_g;                // staged p of the prox pass
   static_assert(!RES || STAGES * STAGE_BYTES >= F32_TILE, "p fits the image stages");
@@ -250,7 +263,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
       for (int q = 0; q < nq && ok; ++q) {
         const int p = q & 3;
         const LoopPass& PS = args.pass[p];
-        const bool epi_pass = p == 1 || (p == 3 && EPI3);
+        const bool epi_pass = (p == 1 && EPI1) || (p == 3 && EPI3);
         int pre = 0;              // K-blocks of the first tile whose A half is in flight
         bool epi_pending = false; // epilogue tiles of the first tile issued before the barrier
         for (int t = blockIdx.x; t < PS.ntiles && ok; t += G) {
@@ -259,16 +272,20 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           const int m0 = mt * BM, n0 = (t - mt * PS.tiles_n) * LBN;
           const int4 kb = PS.kbt[mt];
           if (epi_pass) {
-            if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
+            // resident mode: the staging region is free once the stores of
+            // the previous pass have read it (one arrival before every grid
+            // barrier, the q-th before barrier q)
+            if (RES) ok = mbar_wait(epi_free_bar, (uint32_t)(q - 1) & 1);
+            else if (ec > 0) ok = mbar_wait(epi_free_bar, (ec - 1) & 1);
             if (!ok) break;
             if (p == 1) {
-              mbar_arrive_expect_tx(epi_full_bar, EPI_B_LOAD);
+              mbar_arrive_expect_tx(epi_full_bar, RES ? F32_TILE : EPI_B_LOAD);
 #pragma unroll
               for (int cb = 0; cb < LBN / 32; ++cb)
                 tma_load_2d(epi_f + cb * (BM * 128), &maps.Q, epi_full_bar, n0 + cb * 32, m0);
               constexpr int KEO = 128 / (int)sizeof(T);
 #pragma unroll
-              for (int cb = 0; cb < CB; ++cb) {
+              for (int cb = 0; cb < (RES ? 0 : CB); ++cb) {
                 tma_load_2d(epi_g + cb * OUT_BLOCK, &maps.O[1][0], epi_full_bar, n0 + cb * KEO, m0);
                 if constexpr (NSPLIT == 2)
                   tma_load_2d(epi_g + (CB + cb) * OUT_BLOCK, &maps.O[1][1], epi_full_bar,
@@ -292,11 +309,11 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
               if (!ok) break;
               unsigned char* st = stages + s * STAGE_BYTES;
-              mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
+              mbar_arrive_expect_tx(&full_bar[s], (fac_split(MODE) ? 2u : 1u) * A_BYTES);
               const int kx = kb.x + i * KE;
               tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
-              if constexpr (NSPLIT == 2)
-                tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
+              if constexpr (fac_split(MODE))
+                tma_load_2d(st + ALO_OFF, &maps.K[p][1], &full_bar[s], kx, m0);
             }
             if (!ok) break;
             ok = wait_go(&s_go, q);
@@ -326,15 +343,15 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             } else if (!(first && i < pre)) {
               if (k >= (uint32_t)STAGES) ok = mbar_wait(&empty_bar[s], ((k / STAGES) - 1) & 1);
               if (!ok) break;
-              mbar_arrive_expect_tx(&full_bar[s], NSPLIT * A_BYTES);
+              mbar_arrive_expect_tx(&full_bar[s], (fac_split(MODE) ? 2u : 1u) * A_BYTES);
               tma_load_2d(st, &maps.K[p][0], &full_bar[s], kx, m0);
-              if constexpr (NSPLIT == 2)
-                tma_load_2d(st + A_BYTES + B_BYTES, &maps.K[p][1], &full_bar[s], kx, m0);
+              if constexpr (fac_split(MODE))
+                tma_load_2d(st + ALO_OFF, &maps.K[p][1], &full_bar[s], kx, m0);
             }
             mbar_arrive_expect_tx(&full_bar[s], NSPLIT * B_BYTES);
             tma_load_2d(st + B_OFF, &maps.B[p][0], &full_bar[s], kx, n0);
             if constexpr (NSPLIT == 2)
-              tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.B[p][1], &full_bar[s], kx, n0);
+              tma_load_2d(st + B_OFF + B_BYTES, &maps.B[p][1], &full_bar[s], kx, n0);
           }
           kc += kb.y;
         }
@@ -372,19 +389,11 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             tc_fence_after();
             const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
             const uint64_t a_hi = sdesc_sw128(RES ? smem_u32(res_a + i * A_BYTES) : sa);
-            const uint64_t b_hi = sdesc_sw128(sa + B_OFF);
+            const uint64_t a_lo = sdesc_sw128(sa + ALO_OFF);
+            const uint64_t b = sdesc_sw128(sa + B_OFF);
 #pragma unroll
-            for (int kk = 0; kk < KB_BYTES / 32; ++kk) {
-              const uint64_t adv = (uint64_t)(kk * 2);
-              const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-              umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
-              if constexpr (NSPLIT == 2) {
-                const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
-                const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
-                umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
-                umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
-              }
-            }
+            for (int kk = 0; kk < KB_BYTES / 32; ++kk)
+              umma_kstep<MODE, LBN>(tmem_base, a_hi, a_lo, b, kk, (i > 0 || kk > 0) ? 1u : 0u);
             umma_commit(&empty_bar[s]);
           }
           umma_commit(accum_bar);
@@ -409,6 +418,10 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
     bool free_pending = false;   // epi_free owed once the last stores have read smem
     int dec_stop = 0;            // stop rule of this pair, taken during pass 2
     unsigned flag_prev = 0;      // flag slot of the previous barrier (thread 0)
+    // resident mode: this thread's cells of b (operand value hi + lo) from the
+    // last b-update pass, the old b of the next residual
+    float bprev[16];
+    bool bprev_ok = false;
     for (int q = 0; q < nq; ++q) {
       const int p = q & 3;
       const int pair = q >> 2;
@@ -470,7 +483,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         }
       }
       const bool have_prev = p == 1 && (s_it0 + pair) > 0;
-      const bool epi_pass = p == 1 || (p == 3 && EPI3);
+      const bool epi_pass = (p == 1 && EPI1) || (p == 3 && EPI3);
       bool first = true;
       for (int t = blockIdx.x; t < PS.ntiles; t += G) {
         const int mt = t / PS.tiles_n;
@@ -485,34 +498,41 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           free_pending = false;
           named_bar_sync(EPI_BAR, NEPI);
         }
-        bool have = mbar_wait(accum_bar, tc & 1);
-        if (have && epi_pass) have = mbar_wait(epi_full_bar, ec & 1);
-        if (!have && lane == 0) atomicOr(&s_fault, 1);
-        __syncwarp();
-        tc_fence_after();
-        uint32_t racc[16];
-        tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(grp * 16), racc);
-        tmem_wait_ld();
-        reg_fence16(racc);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tmem_free_bar);
         const int c = grp;                      // 16-column chunk of the tile
         const int m = m0 + rl;
         const int nb = n0 + c * 16;
         int cnt = PS.N - nb;
         cnt = (m >= PS.M || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
+        float qv[16], bo[16], ev[16];
+        if constexpr (RES) {
+          // the first b-update pass of a launch that continues a step: the
+          // old b from global memory (this CTA's own tile, read past L1)
+          if (p == 1 && have_prev && !bprev_ok)
+            load_op16_cg<MODE>((const T*)args.b_hi, (const T*)args.b_lo,
+                               cnt ? (size_t)m * args.pitch_b + nb : 0, cnt, bprev);
+        }
+        bool have = mbar_wait(accum_bar, tc & 1);
+        if (have && epi_pass) have = mbar_wait(epi_full_bar, ec & 1);
+        if (!have && lane == 0) atomicOr(&s_fault, 1);
+        __syncwarp();
+        tc_fence_after();
         float v[16], o[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[j]);
+        tmem_tile16<MODE, LBN>(tmem_base + ((uint32_t)(quad * 32) << 16), grp * 16, v);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tmem_free_bar);
         float res_f = 0.0f;
         if (p == 0 || p == 2) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) o[j] = v[j];
         } else if (p == 1) {
-          float qv[16], bo[16];
           smem_ld_f32x16(epi_f, rl, c, qv);
-          if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
+          if constexpr (RES) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) bo[j] = bprev[j];
+          } else {
+            if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (j < cnt) {
@@ -525,7 +545,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           }
         } else {
           const int irow = m * PS.N + nb;
-          float ev[16], pv[16];
+          float pv[16];
           if (EK == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
           if (crowd_plain) {
             const bool hk = P.has_kappa != 0;
@@ -556,6 +576,16 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           }
           smem_st_f32x16(p_st, rl, c, pv);
         }
+        if constexpr (RES) {
+          // every thread has read the q / e^{-sigma w} tile in the staging
+          // region before any writes its output there
+          if (epi_pass) named_bar_sync(EPI_BAR, NEPI);
+          if (p == 1) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) bprev[j] = op_value<MODE>(o[j]);
+            bprev_ok = true;
+          }
+        }
         stage16<MODE>(st_hi, st_lo, rl, c, o);
         fence_proxy_async_smem();
         double res = 0.0;
@@ -578,7 +608,9 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           }
           bulk_commit();
         }
-        free_pending = epi_pass;
+        // resident mode: every pass's stores free the staging region that
+        // the producer refills before the next barrier
+        free_pending = RES ? true : epi_pass;
         first = false;
         ++tc;
         if (epi_pass) ++ec;
@@ -675,17 +707,16 @@ template <int MODE, int EK>
 __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant__ BatchArgs args) {
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;
-  constexpr int NSPLIT = (MODE == MODE_BF16X3) ? 2 : 1;
+  constexpr int NSPLIT = img_split(MODE) ? 2 : 1;         // image hi (+ lo) blocks
   constexpr uint32_t A_BYTES = BM * KB_BYTES;
   constexpr uint32_t B_BYTES = LBN * KB_BYTES;
-  constexpr uint32_t STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
+  constexpr uint32_t STAGE_BYTES = loop_stage_bytes(MODE, false);
+  constexpr uint32_t ALO_OFF = A_BYTES + NSPLIT * B_BYTES; // factor lo (BF16X3)
   constexpr int STAGES = loop_stages(MODE, false);
-  static_assert(STAGE_BYTES == loop_stage_bytes(MODE, false), "stage size");
   static_assert(STAGES >= 2, "at least two stages");
   constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
   constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
-  constexpr uint32_t TMEM_COLS = LBN;
-  constexpr uint32_t IDESC = make_idesc<MODE>(BM, LBN);
+  constexpr uint32_t TMEM_COLS = acc_cols(MODE, LBN);
   constexpr int CB = LBN * (int)sizeof(T) / 128;
   constexpr uint32_t OUT_BLOCK = BM * 128;
   constexpr uint32_t EPI_B_LOAD = F32_TILE + (uint32_t)NSPLIT * CB * OUT_BLOCK;
@@ -813,10 +844,10 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
               mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
               tma_load_2d(st, &mp->K[p][0], &full_bar[s], kx, m0);
               tma_load_2d(st + A_BYTES, &mp->B[p][0], &full_bar[s], kx, n0);
-              if constexpr (NSPLIT == 2) {
-                tma_load_2d(st + A_BYTES + B_BYTES, &mp->K[p][1], &full_bar[s], kx, m0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mp->B[p][1], &full_bar[s], kx, n0);
-              }
+              if constexpr (NSPLIT == 2)
+                tma_load_2d(st + A_BYTES + B_BYTES, &mp->B[p][1], &full_bar[s], kx, n0);
+              if constexpr (fac_split(MODE))
+                tma_load_2d(st + ALO_OFF, &mp->K[p][1], &full_bar[s], kx, m0);
             }
             kc += kb.y;
           } else if (it.w & 1) {
@@ -876,19 +907,11 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
             tc_fence_after();
             const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
             const uint64_t a_hi = sdesc_sw128(sa);
-            const uint64_t b_hi = sdesc_sw128(sa + A_BYTES);
+            const uint64_t a_lo = sdesc_sw128(sa + ALO_OFF);
+            const uint64_t b = sdesc_sw128(sa + A_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < KB_BYTES / 32; ++kk) {
-              const uint64_t adv = (uint64_t)(kk * 2);
-              const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
-              umma<MODE>(tmem_base, a_hi + adv, b_hi + adv, IDESC, acc);
-              if constexpr (NSPLIT == 2) {
-                const uint64_t a_lo = sdesc_sw128(sa + A_BYTES + B_BYTES);
-                const uint64_t b_lo = sdesc_sw128(sa + 2 * A_BYTES + B_BYTES);
-                umma<MODE>(tmem_base, a_hi + adv, b_lo + adv, IDESC, 1u);
-                umma<MODE>(tmem_base, a_lo + adv, b_hi + adv, IDESC, 1u);
-              }
-            }
+            for (int kk = 0; kk < KB_BYTES / 32; ++kk)
+              umma_kstep<MODE, LBN>(tmem_base, a_hi, a_lo, b, kk, (i > 0 || kk > 0) ? 1u : 0u);
             umma_commit(&empty_bar[s]);
           }
           umma_commit(accum_bar);
@@ -1019,10 +1042,8 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
         if (!have && lane == 0) atomicOr(&s_fault, 1);
         __syncwarp();
         tc_fence_after();
-        uint32_t racc[16];
-        tmem_ld16_issue(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(grp * 16), racc);
-        tmem_wait_ld();
-        reg_fence16(racc);
+        float v[16], o[16];
+        tmem_tile16<MODE, LBN>(tmem_base + ((uint32_t)(quad * 32) << 16), grp * 16, v);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tmem_free_bar);
@@ -1031,9 +1052,6 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
         const int nb = n0 + c * 16;
         int cnt = PN - nb;
         cnt = (m >= PM || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
-        float v[16], o[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(racc[j]);
         float res_f = 0.0f;
         int bad = 0;
         if (p == 0 || p == 2) {
@@ -1238,7 +1256,7 @@ int tc_loop_setup(TcPlan* P, std::string* msg) {
   static_assert(LBN == 64, "the plan's 64-row image maps serve the loop kernel");
   // executed flops of one pair with 64-wide tiles
   const int KE = P->mode == MODE_TF32 ? 32 : 64;
-  const double mult = P->mode == MODE_BF16X3 ? 3.0 : 1.0;
+  const double mult = P->mode == MODE_BF16X3 ? 3.0 : (P->mode == MODE_BF16 ? 2.0 : 1.0);
   double f = 0.0;
   for (int w = 0; w < 4; ++w) {
     const LoopPass L = loop_pass(P, w);
@@ -1295,6 +1313,10 @@ cudaError_t tc_enqueue_loop(TcPlan* P, int pairs, cudaStream_t st) {
   args.part = c.part;
   args.nparts = args.pass[1].ntiles;
   args.pairs = pairs;
+  args.q = c.q;
+  args.b_hi = P->img_b[0];
+  args.b_lo = P->img_b[1];
+  args.pitch_b = P->px;
   switch (P->mode) {
     case MODE_TF32: return dispatch_loop<MODE_TF32, false>(c.ek, maps, args, P->loop_grid, st);
     case MODE_BF16X3: return dispatch_loop<MODE_BF16X3, false>(c.ek, maps, args, P->loop_grid, st);

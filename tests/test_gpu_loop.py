@@ -64,7 +64,7 @@ def test_loop_ragged_grids(prec, nx, ny):
     t, _ = flow(pb, prec, 1, loop=1, tol=0.0, max_iter=1, renormalize=False)
     err = rel_l1(t[0], ref.traj[1])
     print(prec, nx, ny, "loop blur rel L1", err)
-    assert err <= {"BF16": 1e-2, "TF32": 2e-3, "BF16X3": 2e-5}[prec]
+    assert err <= {"BF16": 1e-3, "TF32": 1e-3, "BF16X3": 2e-5}[prec]
 
 
 @pytest.mark.parametrize("prec", ["BF16X3", "TF32"])
@@ -166,14 +166,18 @@ def test_handle_info_and_autotuner():
         return i
     loop = info(loop=1)
     assert loop["loop"] and loop["resident"] and loop["pairs_per_launch"] == pb.max_iter + 1
-    pp = info(loop=2, tile=128)
+    pp = info(loop=2, tile=64)
     assert not pp["loop"] and pp["pairs_per_launch"] == 16
     a1, a2 = info(), info()
     print("loop", loop, "per-pass", pp, "auto", a1)
     assert a1 == a2
     assert a1["graph"]
-    with pytest.raises(jko.JKOError):
-        jko.create_from_problem(pb, precision=jko.Precision.BF16X3, tile=128)
+    # 128-wide tiles: TF32 only (the BF16 image pairs leave no room for them)
+    for prec in (jko.Precision.BF16X3, jko.Precision.BF16):
+        with pytest.raises(jko.JKOError):
+            jko.create_from_problem(pb, precision=prec, tile=128)
+    h = jko.create_from_problem(pb, precision=jko.Precision.TF32, loop=2, tile=128)
+    jko.jko_destroy(h)
 
 
 def _delta_problem():

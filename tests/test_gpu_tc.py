@@ -2,7 +2,8 @@
 
 Bars (relative L1 per step): 1e-3 for every tensor-core form, the target of
 the precision form; the tighter expected levels are asserted where the
-arithmetic gives them (BF16x3 carries ~16 significant bits, TF32 11)."""
+arithmetic gives them (the BF16 images and BF16x3 carry ~16 significant bits;
+TF32 11 bits, measured 3e-4 on the blur in an emulation of its roundings)."""
 import math
 
 import numpy as np
@@ -14,7 +15,7 @@ from tests.gpu_util import need_gpu, rel_l1
 
 pytestmark = pytest.mark.gpu
 
-BARS = {"BF16": 1e-2, "TF32": 2e-3, "BF16X3": 2e-5}   # one pair of the blur
+BARS = {"BF16": 1e-3, "TF32": 1e-3, "BF16X3": 2e-5}    # one pair of the blur
 FLOW_BARS = {"BF16": 1e-3, "TF32": 1e-3, "BF16X3": 1e-5}
 
 
