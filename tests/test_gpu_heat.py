@@ -32,10 +32,11 @@ def gpu_flow(pb, prec, n_steps, **kw):
 # far tail, many orders below that, by the largest entries of a: there an
 # absolute error of 1e-15 is a large relative one, in either solver (the LU
 # oracle's triangular solves keep more of it).  Measured ~1.5e-8 in rel L1 of
-# p with equal pair counts.  FP32: the same plus single-precision rounding of
-# the scalings.
+# p with equal pair counts.  FP32: the same expansion (truncated where FP64's
+# is) plus single-precision rounding of the scalings, 3e-8 around an exact
+# kernel in an emulation of those roundings; the bar is the plain-FP32 one.
 @pytest.mark.parametrize("prec,nx,ny,bar", [("FP64", 48, 48, 5e-8), ("FP64", 40, 56, 5e-8),
-                                            ("FP32", 64, 64, 2e-4)])
+                                            ("FP32", 64, 64, 1e-5), ("FP32", 40, 56, 1e-5)])
 def test_heat_crowd_flow_matches_oracle(prec, nx, ny, bar):
     tol = 1e-11 if prec == "FP64" else 1e-6
     pb = inputs.heat_crowd_problem(nx, ny=ny, n_steps=3, tol=tol, max_iter=4000)
