@@ -45,7 +45,7 @@ FP64_TFLOPS_NOMINAL = 1.25
 
 # DRAM bytes (read + write) per launch of the persistent loop kernel (200
 # pairs) and of each per-pass kernel, BF16 form at 1024^2, from one ncu
-# capture (profiles/tc_loop_bf16_crowd1024_full.md).  They hold for the kernel sources whose hash is given;
+# capture of this bench.  They hold for the kernel sources whose hash is given;
 # any change to those sources turns the roofline's traffic back to null until
 # the counters are taken again.
 KERNEL_SOURCES = ("tc_gemm.cu", "tc_gemm.h", "tc_loop.cu", "tc_common.cuh", "jko_internal.cuh")
@@ -177,6 +177,15 @@ def aggregate_over_ranks(total_s, iters, ws, dev=None):
     return float(t.item()), float(it_t.item())
 
 
+def bench_config(n):
+    """The `config` object of both arms (the same workload, named the same way)."""
+    return {"workload": f"crowd motion {n}x{n} on [0,1]^2, gamma=2e-4, tau=0.02, "
+                        "kappa=1.2 max q0, w=|x-(0.9,0.5)|^2, q0 = disk r=0.2 at (0.25,0.5), "
+                        "<=200 pairs/step, tol 1e-6",
+            "l2": "GPU arm: L2 flushed (256 MB write) between timed steps; reference arm: "
+                  "host cores"}
+
+
 def workload(n):
     from paper_1502_06216_gb300 import inputs
     pb = inputs.config_problem(2, n=n)
@@ -215,6 +224,58 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+FLT_MIN_NORMAL = 1.1754943508222875e-38
+
+
+def band_nnz(n, length, gamma):
+    """Non-zero entries of the 1-D Gibbs factor K[i][j] = exp(-(i-j)^2 h^2 /
+    gamma) in the operand precisions (FP32 / TF32 / BF16 share the exponent
+    range): entries below the smallest normal number are exact zeros.
+    Returns (r, nnz), r the band radius."""
+    h = length / n
+    r = 0
+    while r + 1 < n and math.exp(-((r + 1) * h) ** 2 / gamma) >= FLT_MIN_NORMAL:
+        r += 1
+    nnz = sum(min(i, r) + min(n - 1 - i, r) + 1 for i in range(n))
+    return r, nnz
+
+
+def algorithmic_flops_per_pair(pb):
+    """The method's own work per (odd, even) pair: xi^T a and xi b, each two
+    band-limited 1-D contractions, one multiply-add per non-zero factor entry
+    and output line: 2 (2 nnz_x ny + 2 nnz_y nx) flops."""
+    rx, nnz_x = band_nnz(pb.nx, pb.lx, pb.gamma)
+    ry, nnz_y = band_nnz(pb.ny, pb.ly, pb.gamma)
+    return 2.0 * (2.0 * nnz_x * pb.ny + 2.0 * nnz_y * pb.nx), rx, ry
+
+
+def subsample_problem(n_steps=30):
+    """The headline workload's recipe at 256^2 (the precision workload's error
+    runs): the oracle can run its 30 steps in tens of seconds."""
+    from paper_1502_06216_gb300 import inputs
+    return inputs.config_problem(2, n=256, n_steps=n_steps)
+
+
+def cpu_baseline_leg(pb, q_start, budget_s, sub_steps):
+    """The oracle as it stands, on the host cores: (1) its scaling loop on a
+    bounded number of iterations of one step of the headline workload from
+    the warmed-up state (the baseline rate); (2) its flow on the 256^2
+    subsample of the same recipe, whose per-step densities the GPU forms are
+    then measured against.  Returns (cpu_baseline dict, subsample trajectory)."""
+    from oracle import jko as ojko
+    rate, k_it, secs = oracle_iteration_rate(pb, q_start, budget_s=budget_s)
+    sub = subsample_problem(sub_steps)
+    t0 = time.perf_counter()
+    ref = ojko.problem_flow(sub)
+    sub_s = time.perf_counter() - t0
+    cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+           "sample": f"{k_it} FP64 scaling-loop iterations of one {pb.nx}^2 JKO step from the "
+                     f"warmed-up state ({secs:.1f} s, NumPy/BLAS, separable xi)",
+           "subsample_256": {"iters_per_s": sum(ref.iters) / sub_s, "seconds": sub_s,
+                             "steps": sub_steps, "pairs": int(sum(ref.iters))}}
+    return cpu, ref
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -236,9 +297,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"crowd motion {args.n}x{args.n}, gamma=2e-4, tau=0.02, "
-                               "kappa=1.2 max q0, <=200 pairs/step",
-                   "l2": "n/a (host)"},
+        "config": bench_config(args.n),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                          "sample": f"{iters} FP64 scaling-loop iterations over {args.steps} "
                                    f"samples of one {args.n}^2 JKO step (NumPy/BLAS, separable xi)"},
@@ -252,6 +311,24 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------------------
 
+def shard(n_flows, rank, ws):
+    """The flows of one rank: every ws-th flow from index `rank`, so the ranks
+    share the batch without any data exchange."""
+    return list(range(rank, n_flows, ws))
+
+
+def sharded_batch_job(pbs, run_share, dev=None):
+    """Runs this rank's share of the independent flows `pbs` with
+    run_share(list of problems) -> (seconds, pairs, results) and returns
+    (indices of the share, results, whole-job seconds = the slowest rank's,
+    whole-job pairs = all ranks' pairs)."""
+    ws, rank, _ = dist_env()
+    idx = shard(len(pbs), rank, ws)
+    secs, pairs, results = run_share([pbs[i] for i in idx])
+    secs_all, pairs_all = aggregate_over_ranks(secs, pairs, ws, dev)
+    return idx, results, secs_all, pairs_all
+
+
 def run_batched(args, jko, dev, barrier):
     """256 independent crowd / porous flows of sizes {64,128,256,512}^2, 10 JKO
     steps each, advanced together by one batch (graphs with a branch per flow).
@@ -260,26 +337,32 @@ def run_batched(args, jko, dev, barrier):
     import torch
     from paper_1502_06216_gb300 import inputs
     ws, rank, _ = dist_env()
-    pbs = inputs.batched_problems(256)[rank::ws]
+    pbs_all = inputs.batched_problems(256)
     out = {"workload": "256 flows (crowd even / porous odd), n in {64,128,256,512}, "
                        "gamma U[5e-4,4e-3], 10 JKO steps, <=200 pairs, tol 1e-6",
-           "flows_per_rank": len(pbs), "scaling": "weak" if ws == 1 else "strong"}
-    for form, loop in (("BF16X3", 0), ("BF16X3", 3), ("BF16X3", 2), ("FP32", 0)):
-        b = jko.jko_batch_create(pbs, precision=jko.Precision[form], loop=loop)
-        p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
-        jko.jko_batch_flow(b, p0s, 1, want_final=False)        # warm-up
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, table = jko.jko_batch_flow(b, p0s, 10, want_final=False)
-        e1.record()
-        barrier()
-        secs, iters = aggregate_over_ranks(e0.elapsed_time(e1) / 1e3,
-                                           sum(i["iters"] for row in table for i in row), ws, dev)
+           "flows_per_rank": len(shard(len(pbs_all), rank, ws)),
+           "scaling": "weak" if ws == 1 else "strong"}
+    for form, loop in (("BF16", 0), ("BF16", 3), ("BF16X3", 0), ("FP32", 0)):
+        state = {}
+
+        def run_share(pbs):
+            b = jko.jko_batch_create(pbs, precision=jko.Precision[form], loop=loop)
+            p0s = [torch.tensor(pb.q0, dtype=torch.float32, device=dev) for pb in pbs]
+            jko.jko_batch_flow(b, p0s, 1, want_final=False)        # warm-up
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, table = jko.jko_batch_flow(b, p0s, 10, want_final=False)
+            e1.record()
+            barrier()
+            state["info"] = jko.jko_batch_info(b)
+            jko.jko_batch_destroy(b)
+            return e0.elapsed_time(e1) / 1e3, sum(i["iters"] for row in table for i in row), None
+
+        _, _, secs, iters = sharded_batch_job(pbs_all, run_share, dev)
         key = form if loop == 0 else f"{form}_" + ("grouped" if loop == 3 else "per_pass_kernels")
         out[key] = {"iters_per_s": iters / secs, "flow_steps_per_s": 256 * 10 / secs,
-                    "seconds": secs, "pairs": iters, "kernels": jko.jko_batch_info(b)}
-        jko.jko_batch_destroy(b)
+                    "seconds": secs, "pairs": iters, "kernels": state["info"]}
     return out
 
 
@@ -658,14 +741,41 @@ def run_ours(args):
         dict.fromkeys((args.precision, "FP32")))
     runs = {f: run_form(f, args.steps if f == args.precision or args.precision == "auto"
                         else min(args.steps, 3)) for f in forms_to_run}
-    # accuracy of each form: one step from the FP32 form's congested state,
-    # compared with the FP32 form's step (FP32 matches the FP64 oracle to ~1e-7)
-    q_ref = runs["FP32"]["q_start"]
-    outs = {}
-    for f in forms_to_run:
-        outs[f], _ = jko.jko_step(runs[f]["h"], q_ref.to(runs[f]["h"].dtype))
-    ref = outs["FP32"].double()
-    errs = {f: float((outs[f].double() - ref).abs().sum() / ref.abs().sum()) for f in forms_to_run}
+
+    # cpu baseline (rank 0, N = 1): the oracle timed on the host, which also
+    # gives the per-step densities of the 256^2 subsample of this recipe
+    cpu, sub_ref = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu, sub_ref = cpu_baseline_leg(pb, runs["FP32"]["q_start"].double().cpu().numpy(),
+                                        args.cpu_budget, args.sub_steps)
+    # accuracy of each form: per-step relative L1 against the FP64 oracle on
+    # the 256^2 subsample (all steps of the flow); without the oracle leg, one
+    # step from the FP32 form's congested 1024^2 state against the FP32 form
+    accuracy = {}
+    if sub_ref is not None:
+        sub = subsample_problem(args.sub_steps)
+        for f in forms_to_run:
+            hs = jko.create_from_problem(sub, precision=jko.Precision[f])
+            _, traj, sinfos = jko.jko_flow(hs, torch.tensor(sub.q0, dtype=hs.dtype, device=dev),
+                                           sub.n_steps)
+            tr = traj.double().cpu().numpy()
+            errs_t = [float(np.abs(tr[t] - sub_ref.traj[t + 1]).sum() /
+                            np.abs(sub_ref.traj[t + 1]).sum()) for t in range(sub.n_steps)]
+            accuracy[f] = {"max": max(errs_t), "per_step": errs_t,
+                           "pairs": [i["iters"] for i in sinfos]}
+            jko.jko_destroy(hs)
+        errs = {f: accuracy[f]["max"] for f in forms_to_run}
+        err_rule = (f"max per-step rel L1 vs the FP64 oracle over {args.sub_steps} steps of the "
+                    f"256^2 subsample of this recipe")
+    else:
+        q_ref = runs["FP32"]["q_start"]
+        outs = {}
+        for f in forms_to_run:
+            outs[f], _ = jko.jko_step(runs[f]["h"], q_ref.to(runs[f]["h"].dtype))
+        ref = outs["FP32"].double()
+        errs = {f: float((outs[f].double() - ref).abs().sum() / ref.abs().sum())
+                for f in forms_to_run}
+        err_rule = "rel L1 of one step vs the FP32 form (oracle leg skipped)"
     if args.precision == "auto":
         ok = [f for f in TC_FORMS if errs[f] < ERR_BAR]
         head = max(ok, key=lambda f: runs[f]["iters"] / runs[f]["total_s"]) if ok else "FP32"
@@ -709,6 +819,7 @@ def run_ours(args):
 
     peaks, peak_src = load_peaks()
     clocks = R["clocks"]
+    alg_pair, rx, ry = algorithmic_flops_per_pair(pb)
     if prec in (jko.Precision.FP32, jko.Precision.FP64):
         clock_mhz = clocks.get("sm_max_mhz") or 2070.0
         if prec == jko.Precision.FP32:
@@ -720,13 +831,15 @@ def run_ours(args):
             peak_note = "FP64 nominal"
         bound = "alu"
     else:
-        bf16 = _peak_value(peaks, "bf16_tflops_sustained", "bf16_tflops")
+        # the kernel is timed alone (one launch = one step's pairs): burst peak
+        bf16 = _peak_value(peaks, "bf16_tflops")
         src = peak_src
         if bf16 is None:
-            bf16, src = PEAKS_FALLBACK["bf16_tflops_sustained"], "fallback"
+            bf16, src = PEAKS_FALLBACK["bf16_tflops"], "fallback"
         ratio = {jko.Precision.BF16: 1.0, jko.Precision.BF16X3: 1.0, jko.Precision.TF32: 0.5}[prec]
         peak = bf16 * ratio
-        peak_note = f"bf16 dense, sustained, of {src} x {ratio} for {prec.name}"
+        peak_note = (f"bf16 dense burst, {src} (MEASURED_PEAKS.json bf16_tflops) x {ratio} "
+                     f"for {prec.name}")
         bound = "tensor"
     names = ["pass_x_xi_a", "pass_y_xi_a+b_update+residual", "pass_x_xi_b", "pass_y_xi_b+prox"]
     dense_flops = 8.0 * args.n ** 3
@@ -736,34 +849,34 @@ def run_ours(args):
         kname = f"tc_loop_kernel ({LOOP_PAIRS} pairs per launch)"
         traffic = profiled_traffic(head, args.n, "loop")
         pair_ms = k_ms / LOOP_PAIRS
+        alg_launch = alg_pair * LOOP_PAIRS
     else:
         k_ms, k_fl = ms4[kern], fl4[kern]
         kname = names[kern]
         traffic = profiled_traffic(head, args.n, kern)
         pair_ms = sum(ms4)
-    achieved = k_fl / (k_ms / 1e3) / 1e12
+        alg_launch = alg_pair / 4.0       # one pass of the four
+    achieved = alg_launch / (k_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                "kernel": kname, "kernel_ms": k_ms, "flops_per_launch": k_fl,
-                "flops_note": ("executed tensor-core flops of the band of K-tiles the passes visit"
-                               if bound == "tensor" else
-                               "2(2r+1) flops per output of the band-limited filter"),
+                "kernel": kname, "kernel_ms": k_ms,
+                "flops_per_launch": alg_launch,
+                "flops_note": (f"algorithmic: 2 flops per non-zero of the band-limited 1-D factors "
+                               f"(radius r_x={rx}, r_y={ry}: entries below the smallest normal FP32 "
+                               f"number are exact zeros) per output line, 4 contractions per pair"),
                 "peak_source": peak_note,
+                "executed_flops_per_launch": k_fl,
+                "executed_tflops": k_fl / (k_ms / 1e3) / 1e12,
+                "executed_note": ("tensor-core flops issued: whole 128x64 tiles over the K-blocks "
+                                  "of the band, both products of the BF16 image pair"
+                                  if bound == "tensor" else "same as algorithmic"),
                 "per_pass_kernels": {"passes_ms": ms4, "passes_flops": fl4},
                 "us_per_pair": pair_ms * 1e3,
-                "dense_equiv_tflops_per_pair": dense_flops / (pair_ms / 1e3) / 1e12}
+                "dense_equiv_tflops": dense_flops / (pair_ms / 1e3) / 1e12,
+                "dense_equiv_note": "8 n^3 flops per pair (dense separable GEMMs) over the pair time"}
 
-    # cpu baseline: the oracle on a bounded sample (rank 0, N = 1 only)
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, k_it, secs = oracle_iteration_rate(pb, R["q_start"].double().cpu().numpy(),
-                                                 budget_s=args.cpu_budget)
-        cpu = {"value": rate, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-               "sample": f"{k_it} FP64 scaling-loop iterations of one {args.n}^2 JKO step "
-                         f"from the warmed-up state ({secs:.1f} s, NumPy/BLAS, separable xi)"}
-
-    batched = run_batched(args, jko, dev, barrier) if args.batched else None
+    batched = run_batched(args, jko, dev, barrier) if not args.no_batched else None
     pk, _ = load_peaks()
     peak_bf16_for_porous = (_peak_value(pk, "bf16_tflops_sustained", "bf16_tflops")
                             or PEAKS_FALLBACK["bf16_tflops_sustained"])
@@ -778,11 +891,12 @@ def run_ours(args):
         species = run_species(args, jko, dev, barrier)
         heat = run_heat(args, jko, dev, barrier)
         pairwise = run_pairwise(args, jko, dev, barrier)
-    diff = run_differentiation(args, jko, dev, barrier) if args.diff else None
+    diff = (run_differentiation(args, jko, dev, barrier)
+            if not args.no_diff and rank == 0 and ws == 1 else None)
 
     forms = {f: {"iters_per_s": runs[f]["iters"] / runs[f]["total_s"],
                  "steps_timed": len(runs[f]["infos"]),
-                 "rel_l1_vs_fp32_form": errs[f]} for f in forms_to_run}
+                 "rel_l1": errs[f], "rel_l1_rule": err_rule} for f in forms_to_run}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -792,19 +906,21 @@ def run_ours(args):
             "dtype": {"FP64": "f64", "FP32": "f32", "TF32": "tf32", "BF16": "bf16",
                       "BF16X3": "bf16x3"}[prec.name],
             "data": "synthetic",
-            "config": {"workload": f"crowd motion {args.n}x{args.n}, gamma=2e-4, tau=0.02, "
-                                   "kappa=1.2 max q0, w=|x-(0.9,0.5)|^2, <=200 pairs/step, tol 1e-6",
-                       "precision": prec.name, "parallelism": f"replicas{ws}",
-                       "l2": "flushed (256 MB write) between timed steps",
-                       "steps_timed": f"JKO steps {args.warmup + 1}..{args.warmup + args.steps}",
-                       "headline_rule": "fastest tensor-core form with rel L1 < 1e-3 vs the "
-                                        "FP32 form" if args.precision == "auto" else "fixed"},
+            "config": bench_config(args.n),
+            "run": {"precision": prec.name, "parallelism": f"replicas{ws}",
+                    "steps_timed": f"JKO steps {args.warmup + 1}..{args.warmup + args.steps}",
+                    "headline_rule": ("fastest tensor-core form with " + err_rule + " < 1e-3"
+                                      if args.precision == "auto" else "fixed")},
             "jko_steps_per_s": steps_per_s,
             "iters_per_step": [i["iters"] for i in infos],
             "forms": forms,
             "wall_s": R["t_wall"],
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "accuracy_vs_oracle": ({"workload": "the same recipe at 256^2 (gamma=2e-4, kappa=1.2 "
+                                                "max q0, <=200 pairs, tol 1e-6), " +
+                                                f"{args.sub_steps} JKO steps",
+                                    "forms": accuracy} if accuracy else None),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * h.np_dtype().itemsize,
                     "d2h_bytes_per_step": N * h.np_dtype().itemsize},
             "gpu_launches": R["launches"],
@@ -851,11 +967,13 @@ def main():
     ap.add_argument("--no-porous", action="store_true",
                     help="skip the legs beside the headline (porous, varying exponents, "
                          "binary congestion, Wasserstein attraction, two species)")
-    ap.add_argument("--diff", action="store_true",
-                    help="also time 200 Adam steps of potential recovery at 256^2 "
+    ap.add_argument("--no-diff", action="store_true",
+                    help="skip the 200 Adam steps of potential recovery at 256^2 "
                          "(forward flow + implicit adjoint)")
-    ap.add_argument("--batched", action="store_true",
-                    help="also time the 256-flow batched workload (adds a 'batched' key)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-flow batched workload (the 'batched' key)")
+    ap.add_argument("--sub-steps", type=int, default=30,
+                    help="JKO steps of the 256^2 subsample checked against the oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

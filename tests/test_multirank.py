@@ -63,3 +63,62 @@ def test_one_rank_is_the_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate_over_ranks(2.5, 7, 1) == (2.5, 7.0)
+
+
+def _batch_worker(rank, world, port, out):
+    """One rank of the bench's sharded batch, with the oracle as the flow
+    runner on tiny problems (the GPU batch's role)."""
+    import sys
+    import time
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from oracle import jko as ojko
+    from paper_1502_06216_gb300 import inputs
+    pbs = inputs.batched_problems(6, sizes=(12, 16))
+
+    def run_share(share):
+        t0 = time.perf_counter()
+        flows = [ojko.problem_flow(pb, n_steps=2) for pb in share]
+        secs = time.perf_counter() - t0 + 1.0 + rank      # rank 1 is the slower one
+        return secs, sum(sum(f.iters) for f in flows), [f.traj[-1] for f in flows]
+
+    idx, finals, secs_all, pairs_all = bench.sharded_batch_job(pbs, run_share)
+    out.put((rank, idx, finals, secs_all, pairs_all))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_batch_covers_every_flow_once():
+    """bench.run_batched's sharding on two gloo ranks: the shares are disjoint
+    and cover the batch, every flow's result equals the same flow run alone,
+    and the whole-job figures are all pairs over the slowest rank's time."""
+    import sys
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import jko as ojko
+    from paper_1502_06216_gb300 import inputs
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batch_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((out.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    pbs = inputs.batched_problems(6, sizes=(12, 16))
+    alone = [ojko.problem_flow(pb, n_steps=2) for pb in pbs]
+    seen = []
+    for rank, idx, finals, secs_all, pairs_all in res:
+        assert idx == list(range(rank, 6, 2))
+        seen += idx
+        for i, fin in zip(idx, finals):
+            assert np.array_equal(fin, alone[i].traj[-1])
+        assert pairs_all == float(sum(sum(f.iters) for f in alone))
+        assert secs_all >= 2.0                               # rank 1's time is the max
+    assert sorted(seen) == list(range(6))
+    assert res[0][3] == res[1][3] and res[0][4] == res[1][4]  # every rank sees the same totals
