@@ -111,6 +111,19 @@ typedef struct jko_params {
                        keeps the fastest; the choice is cached per grid, lengths, gamma,
                        precision and energy kind for the process, so handles created
                        alike run the same kernels (jko_handle_info reports them) */
+  int stall;        /* > 0: a step also stops when its L1 residual has set no new minimum
+                       for `stall` pairs in a row (the iterates have reached the rounding
+                       floor of their arithmetic; a slowly converging step keeps setting
+                       minima); the step reports JKO_NOT_CONVERGED unless `finish` takes
+                       over.  0 = off (the stopping rule of Sec. 3.4 alone), >= 0 */
+  int finish;       /* tensor-core precisions, 1: a step the stall rule stops continues
+                       from its current scalings a, b on the JKO_FP32 CUDA-core form, within
+                       the same max_iter budget and under the same rules, so it reaches tol
+                       where the tensor-core operands cannot (the step's minimiser is unique,
+                       Eq. def-jko-operator).  Needs stall > 0 and scalings without log-domain
+                       absorption (absorb = 2, or automatic on a potential that does not turn
+                       it on), else JKO_ERR_UNSUPPORTED; single handles only (jko_batch_create:
+                       JKO_ERR_UNSUPPORTED).  0 = off */
 } jko_params;
 
 /* Energy f; every pointer is HOST memory of N = nx*ny entries, or NULL. */
@@ -161,6 +174,8 @@ typedef struct jko_step_info {
   double max_p_over_kappa;   /* max_i p_i / kappa_i (0 without congestion) */
   float ms;                  /* device time of the step in milliseconds */
   int kernels;               /* kernels this library enqueued for the step */
+  int iters_finish;          /* of `iters`, the pairs run on the FP32 CUDA-core form after
+                                the tensor-core pairs stalled (jko_params.finish) */
 } jko_step_info;
 
 typedef struct jko_handle jko_handle;

@@ -394,6 +394,23 @@ cudaError_t launch_chunk(jko_handle* h, cudaStream_t st) {
   return jko::tc_enqueue_loop(h->tc, h->chunk_iters, st);
 }
 
+// The FP32 CUDA-core chunk that finishes a stalled tensor-core step: the four
+// filter passes of check_every pairs on the handle's float images, captured once.
+jko_status capture_finish_chunk(jko_handle* h) {
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i)
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_pass_simt<float>(h, k, h->cap);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_err(h, e, "capture of the finish chunk"); }
+  CK(h, e2);
+  e = cudaGraphInstantiate(&h->chunk_fin, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, e);
+  return JKO_OK;
+}
+
 // ---- tile-shape autotuner (tensor-core handles) ----
 // A candidate is how the scaling loop runs: the persistent loop kernel, or the
 // per-pass kernels with 64- or 128-wide output tiles.
@@ -498,6 +515,7 @@ void free_handle(jko_handle* h) {
   DeviceGuard dg(h->device);
   if (h->tc) jko::tc_destroy(h->tc);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
+  if (h->chunk_fin) cudaGraphExecDestroy(h->chunk_fin);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
@@ -547,6 +565,14 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
     return (*msg = "tile must be 0 (automatic), 64 or 128", JKO_ERR_INVALID_ARG);
   if (p->absorb < 0 || p->absorb > 2)
     return (*msg = "absorb must be 0 (automatic), 1 or 2", JKO_ERR_INVALID_ARG);
+  if (p->stall < 0) return (*msg = "stall must be >= 0", JKO_ERR_INVALID_ARG);
+  if (p->finish != 0 && p->finish != 1) return (*msg = "finish must be 0 or 1", JKO_ERR_INVALID_ARG);
+  if (p->finish && (p->precision == JKO_FP32 || p->precision == JKO_FP64))
+    return (*msg = "finish continues a tensor-core step on the FP32 form: tensor-core precisions only",
+            JKO_ERR_INVALID_ARG);
+  if (p->finish && p->stall < 1)
+    return (*msg = "finish takes over where the stall rule stops a step: it needs stall > 0",
+            JKO_ERR_INVALID_ARG);
   if (!(en->kappa > 0)) return (*msg = "kappa must be > 0 (INFINITY = none)", JKO_ERR_INVALID_ARG);
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return (*msg = "m must be 0 or >= 1", JKO_ERR_INVALID_ARG);
@@ -724,35 +750,64 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   // chunks: launch the expected number at once, then poll with one in flight
   const int C = h->chunk_iters;
   const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
-  int launched = 0, polled = 0;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
-  auto launch = [&]() -> cudaError_t {
-    h->kernels += h->use_loop ? 1LL : pair_kernels(h) * C;
-    cudaError_t e = launch_chunk(h, st);
-    if (e != cudaSuccess) return e;
-    const int slot = launched & 1;
-    e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, 16, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    e = cudaEventRecord(h->ev_poll[slot], st);
-    ++launched;
-    return e;
+  // runs chunks until the step reports a stop; `fin`: the FP32 finish chunks.
+  // Returns the stop state read back (h->poll slot) through *done.
+  auto run_chunks = [&](bool fin, int ahead, int* done) -> jko_status {
+    int launched = 0, polled = 0;
+    auto launch = [&]() -> cudaError_t {
+      h->kernels += fin ? 4LL * C : (h->use_loop ? 1LL : pair_kernels(h) * C);
+      cudaError_t e = fin ? cudaGraphLaunch(h->chunk_fin, st) : launch_chunk(h, st);
+      if (e != cudaSuccess) return e;
+      const int slot = launched & 1;
+      e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, 16, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+      e = cudaEventRecord(h->ev_poll[slot], st);
+      ++launched;
+      return e;
+    };
+    if (ahead < 1) ahead = 1;
+    if (ahead > max_chunks) ahead = max_chunks;
+    for (int i = 0; i < ahead; ++i) CK(h, launch());
+    bool stopped = false;
+    while (!stopped) {
+      // keep one chunk in flight while waiting for the oldest poll we need
+      if (launched - polled < 2 && launched < max_chunks) CK(h, launch());
+      // wait for the newest-but-one launched chunk's poll (or the newest if only one)
+      const int target = launched - 1 - ((launched - polled) >= 2 ? 1 : 0);
+      const int slot = target & 1;
+      CK(h, cudaEventSynchronize(h->ev_poll[slot]));
+      polled = target + 1;
+      *done = h->poll[slot].done;
+      stopped = *done != jko::RUNNING;
+      if (!stopped && launched >= max_chunks && polled >= launched)
+        return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
+    }
+    return JKO_OK;
   };
-  int ahead = h->last_iters / C;  // chunks surely needed, from the previous step
-  if (ahead < 1) ahead = 1;
-  if (ahead > max_chunks) ahead = max_chunks;
-  for (int i = 0; i < ahead; ++i) CK(h, launch());
-  bool stopped = false;
-  while (!stopped) {
-    // keep one chunk in flight while waiting for the oldest poll we need
-    if (launched - polled < 2 && launched < max_chunks) CK(h, launch());
-    // wait for the newest-but-one launched chunk's poll (or the newest if only one)
-    const int target = launched - 1 - ((launched - polled) >= 2 ? 1 : 0);
-    const int slot = target & 1;
-    CK(h, cudaEventSynchronize(h->ev_poll[slot]));
-    polled = target + 1;
-    stopped = h->poll[slot].done != jko::RUNNING;
-    if (!stopped && launched >= max_chunks && polled >= launched)
-      return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
+  int done = jko::RUNNING;
+  jko_status sr = run_chunks(false, h->last_iters / C, &done);  // chunks surely needed
+  if (sr != JKO_OK) return sr;
+  int fin_pairs = -1;
+  if (done == jko::STALLED && h->prm.finish && h->tc) {
+    // the tensor-core operands have reached their rounding floor: continue the
+    // same step on the FP32 CUDA-core form from the current scalings
+    if (!h->chunk_fin) {
+      jko_status sc = capture_finish_chunk(h);
+      if (sc != JKO_OK) return sc;
+    }
+    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const int it_tc = h->poll[0].it;
+    CK(h, jko::tc_export_scalings(h->tc, (float*)h->a, (float*)h->b, st));
+    CK(h, jko::launch_resume(h->ctrl, st));
+    h->kernels += 3;
+    sr = run_chunks(true, h->last_fin / C, &done);
+    if (sr != JKO_OK) return sr;
+    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    fin_pairs = h->poll[0].it - it_tc;
+    h->last_fin = fin_pairs;
   }
 
   CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part, h->part_cap, st));
@@ -765,8 +820,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   // nonfinite bit 1: NaN/Inf met by an epilogue; bit 2: a bounded device wait gave up
   if (c.nonfinite & 2) st_out = JKO_ERR_TIMEOUT;
   else if (c.done == jko::NONFINITE || c.nonfinite) st_out = JKO_ERR_NUMERIC;
-  else if (c.done == jko::MAX_ITER) st_out = JKO_NOT_CONVERGED;
-  h->last_iters = c.it;
+  else if (c.done == jko::MAX_ITER || c.done == jko::STALLED) st_out = JKO_NOT_CONVERGED;
+  h->last_iters = fin_pairs >= 0 ? c.it - fin_pairs : c.it;
   if (info) {
     info->iters = c.it;
     info->status = st_out;
@@ -780,10 +835,13 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
     info->kernels = (int)h->kernels;
+    info->iters_finish = fin_pairs > 0 ? fin_pairs : 0;
   }
   if (st_out == JKO_ERR_TIMEOUT) set_err(h, st_out, "a bounded device-side wait gave up");
   else if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");
-  else if (st_out == JKO_NOT_CONVERGED) set_err(h, st_out, "max_iter reached before tol");
+  else if (st_out == JKO_NOT_CONVERGED)
+    set_err(h, st_out, c.done == jko::STALLED ? "the residual stalled above tol (stall rule)"
+                                              : "max_iter reached before tol");
   return st_out;
 }
 
@@ -950,6 +1008,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   std::memset(h->poll, 0, 2 * sizeof(Ctrl));
   h->ctrl_init->tol = params->tol;
   h->ctrl_init->max_iter = params->max_iter;
+  h->ctrl_init->stall = params->stall;
   for (auto& ev : h->ev_poll) {
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaEventCreate"));
@@ -996,6 +1055,14 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       else if (params->tile != 0 && jko::tc_set_tile(h->tc, params->tile) != 0)
         s = set_err(h, JKO_ERR_UNSUPPORTED, "tile width not available for this precision");
       h->use_loop = params->loop != 2 && ok;
+    }
+    if (s == JKO_OK && params->finish) {
+      // the FP32 CUDA-core form that finishes a stalled step: its taps
+      if (jko::tc_absorbed(h->tc))
+        s = set_err(h, JKO_ERR_UNSUPPORTED,
+                    "finish needs scalings without log-domain absorption (absorb = 2)");
+      else
+        s = setup_simt<float>(h);
     }
   }
   if (s == JKO_OK && h->tc && params->loop == 0 && params->tile == 0 &&
@@ -1513,6 +1580,9 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
   for (int f = 0; f < n_flows; ++f) {
     if (params[f].check_every != params[0].check_every)
       return fail(batch_err(b, JKO_ERR_INVALID_ARG, "all flows must share check_every"));
+    if (params[f].finish)
+      return fail(batch_err(b, JKO_ERR_UNSUPPORTED,
+                            "finish (the FP32 continuation of a stalled step) is for single handles"));
     if (energies[f].target)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
     if (energies[f].species == 2)
@@ -1682,7 +1752,7 @@ jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
       jko_status sf = JKO_OK;
       if (c.nonfinite & 2) sf = JKO_ERR_TIMEOUT;
       else if (c.done == jko::NONFINITE || c.nonfinite) sf = JKO_ERR_NUMERIC;
-      else if (c.done == jko::MAX_ITER) sf = JKO_NOT_CONVERGED;
+      else if (c.done == jko::MAX_ITER || c.done == jko::STALLED) sf = JKO_NOT_CONVERGED;
       worst = worse(worst, sf);
       max_it = std::max(max_it, c.it);
       if (infos) {

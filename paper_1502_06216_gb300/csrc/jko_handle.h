@@ -72,6 +72,10 @@ struct jko_handle {
   cudaGraphExec_t chunk = nullptr;
   int chunk_iters = 16;
   int last_iters = 0;
+  // a tensor-core step that stalled continues on the FP32 CUDA-core form
+  // (jko_params.finish): its chunk of pairs, and the pairs it took last
+  cudaGraphExec_t chunk_fin = nullptr;
+  int last_fin = 0;
 
   jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
   long long kernels = 0;       // kernels enqueued by the running step

@@ -9,7 +9,9 @@
 namespace jko {
 
 // Stop states written into Ctrl::done.
-enum : int { RUNNING = 0, CONVERGED = 1, MAX_ITER = 2, NONFINITE = 3 };
+// STALLED: the residual set no new minimum over `stall` pairs in a row (the
+// iterates have reached the rounding floor of their arithmetic).
+enum : int { RUNNING = 0, CONVERGED = 1, MAX_ITER = 2, NONFINITE = 3, STALLED = 4 };
 
 // Control block in device memory, one per handle.  Kernels of the scaling loop
 // read `done` when they start and return at once when it is set, so a fixed
@@ -39,7 +41,38 @@ struct Ctrl {
   // grid barrier of the persistent loop kernel (all 0 at the start of a step)
   unsigned long long bar_cnt;     // arrivals, G per barrier
   unsigned int bar_flag[4];       // [b % 3]: some CTA met NaN/Inf or gave up a wait before barrier b
+  // stall rule: pairs without a new minimum of the residual before the step
+  // stops (0 = off); the smallest residual so far and the pairs since, kept
+  // twice by pair parity (the decision of pair k reads slot k & 1 and writes
+  // the other), so that every block of a deciding kernel reads the state the
+  // previous decision left while one block writes the next
+  int stall;
+  int since[2];
+  int stall_spare;
+  double best[2];
 };
+
+// The stall rule for the decision after pair `it` (>= 1) with residual
+// `total`: true when the residual has set no new minimum for ctrl->stall
+// pairs.  `write`: this thread records the new state.
+__device__ __forceinline__ bool stall_rule(Ctrl* ctrl, int it, double total, bool write) {
+  const int n = *(volatile int*)&ctrl->stall;
+  if (n <= 0 || it < 1) return false;
+  const int rd = it & 1;
+  double best = it == 1 ? INFINITY : __ldcg(&ctrl->best[rd]);
+  int since = it == 1 ? 0 : *(volatile int*)&ctrl->since[rd];
+  if (total < best) {
+    best = total;
+    since = 0;
+  } else {
+    ++since;
+  }
+  if (write) {
+    ctrl->best[rd ^ 1] = best;
+    ctrl->since[rd ^ 1] = since;
+  }
+  return since >= n;
+}
 
 // ---- stop protocol of the scaling loop ----
 // The b-update pass writes one residual partial per block (plain stores, one
@@ -82,6 +115,7 @@ __device__ __forceinline__ bool stop_gate(Ctrl* ctrl, const double* part, int np
   if (it > 0 && !isfinite(total)) d = NONFINITE;
   else if (it > 0 && total <= ctrl->tol) d = CONVERGED;
   else if (it >= ctrl->max_iter) d = MAX_ITER;
+  else if (stall_rule(ctrl, it, total, first)) d = STALLED;
   if (first) {
     if (it > 0) ctrl->res_last = total;
     if (d != RUNNING) ctrl->done = d;

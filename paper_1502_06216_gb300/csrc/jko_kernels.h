@@ -126,6 +126,9 @@ cudaError_t heat_prox_launch(int ek, const T* s, T* a, T* p, int nx, int ny, con
 
 // Batched flows: copy the stop state of n control blocks into a contiguous
 // array (done flags only, or whole blocks).
+// A stopped step runs on: done = RUNNING, the stall counters restart (the
+// pair counter, the budget and the smallest residual carry over).
+cudaError_t launch_resume(Ctrl* ctrl, cudaStream_t st);
 cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st);
 cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_t st);
 

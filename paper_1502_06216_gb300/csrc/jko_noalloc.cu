@@ -222,6 +222,7 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
   std::memset(&init, 0, sizeof init);
   init.tol = prm->tol;
   init.max_iter = prm->max_iter;
+  init.stall = prm->stall;
   Ctrl host;
   NA_CK(cudaMemcpyAsync(ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   NA_CK(jko::launch_validate<float>((const float*)q_dev, N, P, ctrl, st));
@@ -279,7 +280,7 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
   NA_CK(cudaStreamSynchronize(st));
   jko_status out = JKO_OK;
   if (host.done == jko::NONFINITE || host.nonfinite) out = JKO_ERR_NUMERIC;
-  else if (host.done == jko::MAX_ITER) out = JKO_NOT_CONVERGED;
+  else if (host.done == jko::MAX_ITER || host.done == jko::STALLED) out = JKO_NOT_CONVERGED;
   if (info) {
     info->iters = host.it;
     info->status = out;

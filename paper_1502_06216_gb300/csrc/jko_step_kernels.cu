@@ -167,6 +167,19 @@ __global__ void gather_ctrl_kernel(Ctrl* const* ctrls, Ctrl* out, int n) {
 }
 }  // namespace
 
+namespace {
+__global__ void resume_kernel(Ctrl* ctrl) {
+  ctrl->done = RUNNING;
+  ctrl->since[0] = 0;
+  ctrl->since[1] = 0;
+}
+}  // namespace
+
+cudaError_t launch_resume(Ctrl* ctrl, cudaStream_t st) {
+  resume_kernel<<<1, 1, 0, st>>>(ctrl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_done(Ctrl* const* ctrls, int* done, int n, cudaStream_t st) {
   gather_done_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctrls, done, n);
   return cudaGetLastError();

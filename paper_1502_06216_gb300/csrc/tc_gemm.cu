@@ -326,6 +326,20 @@ tc_pass_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constan
   if (EPI == EPI_A && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0) ctrl->it = s_it + 1;
 }
 
+// The plan's scaling images (operand type, [ny][pitch]) as fp32 [ny][nx]:
+// the operand value hi (+ lo) the passes multiply with.
+template <typename T>
+__global__ void export_op_kernel(const T* hi, const T* lo, int pitch, float* dst, int nx, int ny) {
+  const long long n = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / nx, x = i - y * nx;
+    const long long k = y * pitch + x;
+    if constexpr (sizeof(T) == 4) dst[i] = hi[k];
+    else dst[i] = __bfloat162float(hi[k]) + __bfloat162float(lo[k]);
+  }
+}
+
 // a = 1 in operand precision (cold start), padded columns included.
 template <typename T>
 __global__ void fill_op_kernel(T* hi, T* lo, long long n, float v) {
@@ -680,6 +694,20 @@ cudaError_t tc_begin_step(TcPlan* P, cudaStream_t st) {
   else
     fill_op_kernel<__nv_bfloat16><<<152 * 4, 256, 0, st>>>(
         (__nv_bfloat16*)P->img_a[0], (__nv_bfloat16*)P->img_a[1], n, 1.0f);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_export_scalings(const TcPlan* P, float* a, float* b, cudaStream_t st) {
+  const int nx = P->cfg.nx, ny = P->cfg.ny;
+  if (P->mode == MODE_TF32) {
+    export_op_kernel<float><<<152 * 4, 256, 0, st>>>((const float*)P->img_a[0], nullptr, P->px, a, nx, ny);
+    export_op_kernel<float><<<152 * 4, 256, 0, st>>>((const float*)P->img_b[0], nullptr, P->px, b, nx, ny);
+  } else {
+    export_op_kernel<__nv_bfloat16><<<152 * 4, 256, 0, st>>>(
+        (const __nv_bfloat16*)P->img_a[0], (const __nv_bfloat16*)P->img_a[1], P->px, a, nx, ny);
+    export_op_kernel<__nv_bfloat16><<<152 * 4, 256, 0, st>>>(
+        (const __nv_bfloat16*)P->img_b[0], (const __nv_bfloat16*)P->img_b[1], P->px, b, nx, ny);
+  }
   return cudaGetLastError();
 }
 

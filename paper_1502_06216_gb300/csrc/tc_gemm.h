@@ -42,6 +42,10 @@ int tc_absorbed(const TcPlan* plan);
 int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);
 // Per-step reset of the scaling operands (a = 1).
 cudaError_t tc_begin_step(TcPlan* plan, cudaStream_t st);
+// The current scalings a, b as fp32 [ny][nx] images (the operand values the
+// passes multiply with), for a step that continues on the CUDA-core form.
+// Not for absorbed plans (their scalings carry the factor e^{beta}).
+cudaError_t tc_export_scalings(const TcPlan* plan, float* a, float* b, cudaStream_t st);
 // Pass `which` (0..3) of one (odd, even) pair, same numbering as the SIMT form.
 cudaError_t tc_enqueue_pass(TcPlan* plan, int which, cudaStream_t st);
 // Multiply-add flops (x2) of the tiles pass `which` executes.

@@ -475,6 +475,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           if (it > 0 && !isfinite(v)) d = NONFINITE;
           else if (it > 0 && v <= s_tol) d = CONVERGED;
           else if (it >= s_maxit) d = MAX_ITER;
+          else if (stall_rule(ctrl, it, v, lane == 0 && blockIdx.x == 0)) d = STALLED;
           if (lane == 0 && blockIdx.x == 0) {
             if (it > 0) ctrl->res_last = v;
             if (d != RUNNING) ctrl->done = d;
@@ -998,6 +999,7 @@ __global__ void __launch_bounds__(NTB, 1) tc_batch_kernel(const __grid_constant_
             else if (it > 0 && !isfinite(v)) d = NONFINITE;
             else if (it > 0 && v <= c->tol) d = CONVERGED;
             else if (it >= c->max_iter) d = MAX_ITER;
+            else if (stall_rule(c, it, v, lane == 0)) d = STALLED;
             if (lane == 0) {
               if (it > 0) c->res_last = v;
               if (d != RUNNING) {

@@ -56,7 +56,9 @@ class jko_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("renormalize", ctypes.c_int),
                 ("absorb", ctypes.c_int),
                 ("loop", ctypes.c_int),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int),
+                ("stall", ctypes.c_int),
+                ("finish", ctypes.c_int)]
 
 
 class jko_energy(ctypes.Structure):
@@ -72,7 +74,7 @@ class jko_step_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
                 ("residual_l1", ctypes.c_double), ("mass", ctypes.c_double),
                 ("max_p_over_kappa", ctypes.c_double), ("ms", ctypes.c_float),
-                ("kernels", ctypes.c_int)]
+                ("kernels", ctypes.c_int), ("iters_finish", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -203,7 +205,7 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
                tile: int = 0, m_field=None, binary: bool = False, target=None,
                species: int = 1, w2=None, heat_L: int = 0,
-               pair_alpha: float = 0.0) -> Handle:
+               pair_alpha: float = 0.0, stall: int = 0, finish: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
     ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
@@ -211,11 +213,14 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
     ``w2``: two densities coupled through the congestion of their sum (Sec. 5.3),
     or with ``pair_alpha > 0`` through the pairwise attraction pair_alpha
     W(p_1, p_2), whose state images hold [p_1, p_2]; ``heat_L > 0``: the heat-kernel Gibbs
-    kernel (Id - (gamma/L) Delta)^{-L} of the domain outside ``mask`` (Sec. 4.1)."""
+    kernel (Id - (gamma/L) Delta)^{-L} of the domain outside ``mask`` (Sec. 4.1);
+    ``stall > 0``: a step also stops when its residual sets no new minimum for
+    that many pairs; ``finish = 1`` (tensor-core precisions): such a step goes
+    on from its scalings on the FP32 CUDA-core form until tol."""
     N = nx * ny
     g = jko_grid(nx, ny, lx, ly, int(heat_L))
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
-                   int(absorb), int(loop), int(tile))
+                   int(absorb), int(loop), int(tile), int(stall), int(finish))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N),
             _host_f64(m_field, N), _host_f64(target, N), _host_f64(w2, N)]
     mk = None if mask is None else np.ascontiguousarray(np.asarray(mask, np.uint8).reshape(N))
@@ -396,7 +401,7 @@ def jko_heat_plan(nx: int, ny: int, gamma: float, L: int = 10, lx: float = 1.0,
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
                         max_iter: Optional[int] = None, check_every: int = 0,
                         renormalize: bool = True, stream=None, absorb: int = 0,
-                        loop: int = 0, tile: int = 0) -> Handle:
+                        loop: int = 0, tile: int = 0, stall: int = 0, finish: int = 0) -> Handle:
     """jko_create from an ``inputs.Problem``."""
     return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
                       tol=pb.tol if tol is None else tol,
@@ -409,7 +414,8 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       target=getattr(pb, "target", None),
                       species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None),
                       heat_L=int(getattr(pb, "heat_L", 0)),
-                      pair_alpha=float(getattr(pb, "pair_alpha", 0.0)))
+                      pair_alpha=float(getattr(pb, "pair_alpha", 0.0)), stall=stall,
+                      finish=finish)
 
 
 class Batch:
@@ -450,7 +456,7 @@ def _energy_struct(pb, keep):
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,
                      check_every: int = 0, renormalize: bool = True, stream=None,
-                     loop: int = 0, tile: int = 0) -> Batch:
+                     loop: int = 0, tile: int = 0, stall: int = 0) -> Batch:
     """jko_batch_create for a list of ``inputs.Problem``; ``precision`` and
     ``loop`` may be one value or one per flow (loop = 3: grouped launch)."""
     n = len(problems)
@@ -464,7 +470,8 @@ def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None
         G[f] = jko_grid(pb.nx, pb.ny, pb.lx, pb.ly, int(getattr(pb, "heat_L", 0)))
         P[f] = jko_params(pb.gamma, pb.tau, pb.tol if tol is None else tol,
                           pb.max_iter if max_iter is None else max_iter, check_every,
-                          int(precs[f]), int(bool(renormalize)), 0, int(loops[f]), int(tile))
+                          int(precs[f]), int(bool(renormalize)), 0, int(loops[f]), int(tile),
+                          int(stall), 0)
         E[f] = _energy_struct(pb, keep)
     out = ctypes.c_void_p()
     st = _current_stream() if stream is None else ctypes.c_void_p(stream)

@@ -90,7 +90,11 @@ def test_noalloc_step_runs_the_create_checks_on_host(libjko):
            dict(grid_kw=dict(lx=math.inf)),
            dict(energy_kw=dict(m=math.inf)),
            dict(energy_kw=dict(m=0.5)),
-           dict(energy_kw=dict(pair_alpha=math.nan, species=2))]
+           dict(energy_kw=dict(pair_alpha=math.nan, species=2)),
+           dict(params_kw=dict(stall=-1)),
+           dict(params_kw=dict(finish=2, stall=4)),
+           dict(params_kw=dict(finish=1, stall=4)),                # FP32: no tensor-core pairs
+           dict(params_kw=dict(finish=1, stall=0, precision=int(jko.Precision.BF16)))]
     for case in bad:
         assert status(**case) == jko.Status.INVALID_ARG, case
     # limits of the fixed scratch: reported as unsupported, still on the host
