@@ -591,16 +591,23 @@ def run_heat(args, jko, dev, barrier, steps=4):
     return out
 
 
+FINISH_VARIANTS = (("BF16", 2), ("BF16", 4), ("TF32", 2), ("BF16X3", 2))
+
+
 def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
     """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
     accuracy of one step against the FP32 form from the same state, and the
     roofline of the kernel that runs (loop kernel: executed tensor flops over
-    100 pairs)."""
+    100 pairs).  The tensor-core forms also run with the stall rule and the
+    FP32 finish (jko_params.stall = W, finish = 1: "<form>+finish<W>"), which
+    take every step to tol."""
     import torch
     out = {"workload": workload}
     outs, qs = {}, None
-    for form in ALL_FORMS:
-        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+    runs = [(f, f, {}) for f in ALL_FORMS] + [
+        (f"{f}+finish{w}", f, {"stall": w, "finish": 1}) for f, w in FINISH_VARIANTS]
+    for name, form, kw in runs:
+        h = jko.create_from_problem(pb, precision=jko.Precision[form], **kw)
         q = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
         p = torch.empty_like(q)
         for _ in range(warmup):
@@ -619,15 +626,19 @@ def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
         e1.record()
         barrier()
         secs = e0.elapsed_time(e1) / 1e3
-        outs[form], _ = jko.jko_step(h, qs.to(h.dtype))
+        outs[name], info1 = jko.jko_step(h, qs.to(h.dtype))
         entry = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
                  "pairs_per_step": iters / steps, "kernels": jko.jko_handle_info(h)}
-        entry["roofline"] = form_roofline(jko, h, form, peak_bf16)
-        out[form] = entry
+        if kw:
+            entry["fp32_pairs_of_the_check_step"] = info1["iters_finish"]
+            entry["status_of_the_check_step"] = int(info1["status"])
+        else:
+            entry["roofline"] = form_roofline(jko, h, form, peak_bf16)
+        out[name] = entry
         jko.jko_destroy(h)
     ref = outs["FP32"].double()
-    for form in ALL_FORMS:
-        out[form]["rel_l1_vs_fp32_form"] = float((outs[form].double() - ref).abs().sum() /
+    for name, _, _ in runs:
+        out[name]["rel_l1_vs_fp32_form"] = float((outs[name].double() - ref).abs().sum() /
                                                  ref.abs().sum())
     return out
 

@@ -395,12 +395,15 @@ cudaError_t launch_chunk(jko_handle* h, cudaStream_t st) {
 }
 
 // The FP32 CUDA-core chunk that finishes a stalled tensor-core step: the four
-// filter passes of check_every pairs on the handle's float images, captured once.
+// filter passes of kFinishChunk pairs on the handle's float images, captured
+// once.  From the stalled scalings the FP32 form needs one or two pairs, so the
+// chunk is short: its passes after the stop are launches that return at once.
+constexpr int kFinishChunk = 2;
 jko_status capture_finish_chunk(jko_handle* h) {
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i)
+  for (int i = 0; i < kFinishChunk && e == cudaSuccess; ++i)
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = enqueue_pass_simt<float>(h, k, h->cap);
   cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
   if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_err(h, e, "capture of the finish chunk"); }
@@ -748,12 +751,13 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   }
 
   // chunks: launch the expected number at once, then poll with one in flight
-  const int C = h->chunk_iters;
-  const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
   // runs chunks until the step reports a stop; `fin`: the FP32 finish chunks.
   // Returns the stop state read back (h->poll slot) through *done.
-  auto run_chunks = [&](bool fin, int ahead, int* done) -> jko_status {
+  auto run_chunks = [&](bool fin, int ahead_pairs, int* done, int* it) -> jko_status {
+    const int C = fin ? kFinishChunk : h->chunk_iters;
+    const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
+    int ahead = ahead_pairs / C;
     int launched = 0, polled = 0;
     auto launch = [&]() -> cudaError_t {
       h->kernels += fin ? 4LL * C : (h->use_loop ? 1LL : pair_kernels(h) * C);
@@ -779,35 +783,31 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
       CK(h, cudaEventSynchronize(h->ev_poll[slot]));
       polled = target + 1;
       *done = h->poll[slot].done;
+      *it = h->poll[slot].it;
       stopped = *done != jko::RUNNING;
       if (!stopped && launched >= max_chunks && polled >= launched)
         return set_err(h, JKO_ERR_TIMEOUT, "scaling loop did not report a stop within its budget");
     }
     return JKO_OK;
   };
-  int done = jko::RUNNING;
-  jko_status sr = run_chunks(false, h->last_iters / C, &done);  // chunks surely needed
+  int done = jko::RUNNING, it_tc = 0, it_end = 0;
+  jko_status sr = run_chunks(false, h->last_iters, &done, &it_tc);  // chunks surely needed
   if (sr != JKO_OK) return sr;
-  int fin_pairs = -1;
+  bool finished = false;
   if (done == jko::STALLED && h->prm.finish && h->tc) {
     // the tensor-core operands have reached their rounding floor: continue the
-    // same step on the FP32 CUDA-core form from the current scalings
+    // same step on the FP32 CUDA-core form from the current scalings (the
+    // stopped step's pair counter came back with its stop state)
     if (!h->chunk_fin) {
       jko_status sc = capture_finish_chunk(h);
       if (sc != JKO_OK) return sc;
     }
-    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaStreamSynchronize(st));
-    const int it_tc = h->poll[0].it;
     CK(h, jko::tc_export_scalings(h->tc, (float*)h->a, (float*)h->b, st));
     CK(h, jko::launch_resume(h->ctrl, st));
     h->kernels += 3;
-    sr = run_chunks(true, h->last_fin / C, &done);
+    sr = run_chunks(true, h->last_fin, &done, &it_end);
     if (sr != JKO_OK) return sr;
-    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaStreamSynchronize(st));
-    fin_pairs = h->poll[0].it - it_tc;
-    h->last_fin = fin_pairs;
+    finished = true;
   }
 
   CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part, h->part_cap, st));
@@ -821,7 +821,9 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   if (c.nonfinite & 2) st_out = JKO_ERR_TIMEOUT;
   else if (c.done == jko::NONFINITE || c.nonfinite) st_out = JKO_ERR_NUMERIC;
   else if (c.done == jko::MAX_ITER || c.done == jko::STALLED) st_out = JKO_NOT_CONVERGED;
-  h->last_iters = fin_pairs >= 0 ? c.it - fin_pairs : c.it;
+  const int fin_pairs = finished ? c.it - it_tc : 0;
+  if (finished) h->last_fin = fin_pairs;
+  h->last_iters = c.it - fin_pairs;
   if (info) {
     info->iters = c.it;
     info->status = st_out;
@@ -835,7 +837,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     info->ms = ms;
     info->kernels = (int)h->kernels;
-    info->iters_finish = fin_pairs > 0 ? fin_pairs : 0;
+    info->iters_finish = fin_pairs;
   }
   if (st_out == JKO_ERR_TIMEOUT) set_err(h, st_out, "a bounded device-side wait gave up");
   else if (st_out == JKO_ERR_NUMERIC) set_err(h, st_out, "NaN or Inf in the scaling iterates");

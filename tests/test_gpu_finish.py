@@ -93,3 +93,22 @@ def test_batch_flows_take_the_stall_rule():
         assert table[0][f]["iters"] == infos[0]["iters"] < pb.max_iter
         assert np.array_equal(finals[f].double().cpu().numpy(), t[0])
     jko.jko_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec,stall", [("BF16", 2), ("TF32", 2)])
+def test_finish_on_the_porous_workload_512(prec, stall):
+    """The non-linear diffusion workload at its size (512^2, 15 % obstacles,
+    gamma = 5e-4, tau = 5e-3), 5 steps with the FP32 finish: every step meets
+    tol and stays within the plain-FP32 bar of the oracle."""
+    from paper_1502_06216_gb300 import jko
+    pb = inputs.config_problem(1, n_steps=5)
+    assert pb.nx == 512
+    ref = ojko.problem_flow(pb)
+    traj, infos = flow(pb, prec, 5, stall=stall, finish=1)
+    errs = [rel_l1(traj[t], ref.traj[t + 1]) for t in range(5)]
+    print(prec, stall, "porous 512 per-step rel L1", " ".join(f"{e:.1e}" for e in errs),
+          "pairs", [i["iters"] for i in infos], "of which FP32", [i["iters_finish"] for i in infos],
+          "oracle", ref.iters)
+    for i in infos:
+        assert i["status"] == jko.Status.OK
+    assert max(errs) <= 1e-5
