@@ -594,6 +594,46 @@ def run_heat(args, jko, dev, barrier, steps=4):
 FINISH_VARIANTS = (("BF16", 2), ("BF16", 4), ("TF32", 2), ("BF16X3", 2))
 
 
+def run_fft(args, jko, dev, barrier, steps=4):
+    """The Gaussian by FFT convolution (jko_grid.fft = 1) beside the band-limited
+    filter and the tensor-core form: the porous recipe at 512^2 (gamma = 5e-4,
+    band radius 104 cells) and the same with a wider kernel (gamma = 4e-3,
+    radius 295: the filter's work grows with the radius, the transform's does
+    not).  Per form: pairs/s and JKO steps/s of one `steps`-step flow after a
+    1-step warm-up, and the last step against the FP64 band filter."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    out = {}
+    for gamma in (5e-4, 4e-3):
+        pb = inputs.config_problem(1, gamma=gamma, n_steps=steps)
+        leg = {"workload": f"porous medium m=2, {pb.nx}x{pb.ny}, gamma={gamma}, tau={pb.tau}, "
+                           f"15% obstacles, <={pb.max_iter} pairs/step, tol {pb.tol}"}
+        finals = {}
+        for name, prec, kw in (("FP64", "FP64", {}), ("FP32", "FP32", {}),
+                               ("FP32_fft", "FP32", {"fft": 1}), ("FP64_fft", "FP64", {"fft": 1}),
+                               ("BF16X3+finish2", "BF16X3", {"stall": 2, "finish": 1})):
+            h = jko.create_from_problem(pb, precision=jko.Precision[prec], **kw)
+            p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+            jko.jko_flow(h, p0, 1)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pf, _, infos = jko.jko_flow(h, p0, steps)
+            e1.record()
+            barrier()
+            secs = e0.elapsed_time(e1) / 1e3
+            iters = sum(i["iters"] for i in infos)
+            finals[name] = pf.double()
+            leg[name] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                         "pairs_per_step": iters / steps}
+            jko.jko_destroy(h)
+        for name in finals:
+            leg[name]["rel_l1_vs_fp64_filter"] = float((finals[name] - finals["FP64"]).abs().sum() /
+                                                       finals["FP64"].abs().sum())
+        out[f"gamma={gamma}"] = leg
+    return out
+
+
 def run_diffusion(jko, dev, barrier, peak_bf16, pb, workload, steps, warmup):
     """Per form: pairs/s and JKO steps/s over `steps` steps after `warmup`,
     accuracy of one step against the FP32 form from the same state, and the
@@ -894,7 +934,7 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = binary = attraction = species = heat = pairwise = None
+    genent = binary = attraction = species = heat = pairwise = fft = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
         binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
@@ -902,6 +942,7 @@ def run_ours(args):
         species = run_species(args, jko, dev, barrier)
         heat = run_heat(args, jko, dev, barrier)
         pairwise = run_pairwise(args, jko, dev, barrier)
+        fft = run_fft(args, jko, dev, barrier)
     diff = (run_differentiation(args, jko, dev, barrier)
             if not args.no_diff and rank == 0 and ws == 1 else None)
 
@@ -953,6 +994,8 @@ def run_ours(args):
             line["heat_kernel"] = heat
         if pairwise is not None:
             line["pairwise_attraction"] = pairwise
+        if fft is not None:
+            line["fft_gaussian"] = fft
         if diff is not None:
             line["differentiation"] = diff
         print(json.dumps(line), flush=True)

@@ -84,6 +84,19 @@ typedef struct jko_grid {
    * JKO_FP64 single-density handles only (JKO_ERR_UNSUPPORTED otherwise; not
    * batched, no adjoint, no fixed-scratch step). */
   int heat_L;
+  /* Application of the Gaussian (heat_L = 0): 0 = the band-limited separable
+   * filter (CUDA cores) or tensor-core GEMMs; 1 = the same restricted Gaussian
+   * by FFT convolution along each axis, O(N log N): each line zero-padded to a
+   * power of two L >= n + r (r the band radius of the filter), transformed,
+   * multiplied by the real spectrum of the kernel's circulant embedding and
+   * transformed back.  Accurate normwise (each output within ~eps log2 L of its
+   * line's largest entry), where the filter is accurate entry by entry.
+   * The potential spreads the scalings over e^{tau/gamma (max w - min w)}, so
+   * that range must stay <= 8 (FP32) / 24 (FP64) (measured errors 5.5e-6 /
+   * 9.3e-11 there).  JKO_FP32 / JKO_FP64 single-density handles (no target,
+   * second species or heat kernel), L <= 4096 (FP32) / 2048 (FP64), else
+   * JKO_ERR_UNSUPPORTED; no adjoint, no fixed-scratch step. */
+  int fft;
 } jko_grid;
 
 typedef struct jko_params {

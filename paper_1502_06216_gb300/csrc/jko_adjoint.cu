@@ -336,6 +336,9 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the Wasserstein attraction");
   if (h->species == 2) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for two species");
   if (h->heat_L) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the heat kernel");
+  if (h->fft)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "no adjoint for the FFT application of the Gaussian");
   const size_t es = h->es, N = (size_t)h->N;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);

@@ -44,6 +44,9 @@ struct jko_handle {
   void* E2 = nullptr;           // e^{-sigma w2} of the second species
   long long ns = 0;             // elements of a state image: N, or 2 N for two species
   int heat_L = 0;               // > 0: the heat-kernel Gibbs kernel (heat.cu)
+  int fft = 0;                  // 1: the Gaussian applied by FFT convolution (fft_filter.cu)
+  void *fft_khat_x = nullptr, *fft_tw_x = nullptr, *fft_khat_y = nullptr, *fft_tw_y = nullptr;
+  int fft_Lx = 0, fft_lgx = 0, fft_Ly = 0, fft_lgy = 0;
   double pair_alpha = 0;        // > 0 (two species): pairwise attraction, 3 couplings
   void* t2 = nullptr;           // transposed intermediates of batched filter passes
   void* t3 = nullptr;

@@ -38,6 +38,28 @@ struct PassArgs {
   const T* q_z[3] = {nullptr, nullptr, nullptr};
 };
 
+// FFT form of the pass (fft_filter.cu): the same out[j][i'] and epilogues by
+// convolution through a transform of length L (a power of two >= n_i + r).
+// khat: the real spectrum of the circulant embedding of the taps, with 1/L
+// (L entries); tw: e^{-2 pi i j / L}, j < L/2, interleaved re, im.
+template <typename T>
+struct FftArgs {
+  int L = 0, log2L = 0;
+  const T* khat = nullptr;
+  const T* tw = nullptr;
+};
+// Longest transform per element type (the block's 4 lines and twiddles in
+// shared memory).
+template <typename T> constexpr int fft_max_length() { return sizeof(T) == 4 ? 4096 : 2048; }
+template <typename T>
+cudaError_t fft_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,
+                     const FftArgs<T>& F, cudaStream_t st);
+// Blocks of an FFT pass over an [n_i][n_j] input (= its residual partials).
+int fft_pass_blocks(int n_j);
+// Host tables of one axis (n cells, band radius r): false if L > max_len.
+bool fft_axis_tables(int n, int r, double length, double gamma, int max_len, int* L, int* log2L,
+                     std::vector<double>* khat, std::vector<double>* tw);
+
 int simt_tap_padding();
 // Blocks of a filter pass over an [n_i][n_j] input (= residual partials of the
 // b-update pass).

@@ -152,6 +152,8 @@ extern "C" jko_status jko_step_noalloc(const jko_grid* grid, const jko_params* p
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the Wasserstein attraction is not available");
   if (en->species == 2)
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: two species are not available");
+  if (grid->fft != 0)
+    return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the FFT application is not available");
   if (grid->heat_L != 0)
     return fail(JKO_ERR_UNSUPPORTED, "jko_step_noalloc: the heat kernel is not available");
   if (jko::simt_tap_padding() != kTapPad)

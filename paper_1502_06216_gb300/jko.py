@@ -47,7 +47,8 @@ class JKOError(RuntimeError):
 
 class jko_grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("heat_L", ctypes.c_int)]
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("heat_L", ctypes.c_int),
+                ("fft", ctypes.c_int)]
 
 
 class jko_params(ctypes.Structure):
@@ -205,7 +206,8 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
                alpha=None, mask=None, stream=None, absorb: int = 0, loop: int = 0,
                tile: int = 0, m_field=None, binary: bool = False, target=None,
                species: int = 1, w2=None, heat_L: int = 0,
-               pair_alpha: float = 0.0, stall: int = 0, finish: int = 0) -> Handle:
+               pair_alpha: float = 0.0, stall: int = 0, finish: int = 0,
+               fft: int = 0) -> Handle:
     """jko_create: grid, step parameters and energy (host arrays, copied);
     ``m_field``: per-cell exponents of the paper's generalised entropies;
     ``binary``: the non-convex congestion iota_{{0,kappa}}; ``target``: the
@@ -216,9 +218,10 @@ def jko_create(nx: int, ny: int, gamma: float, tau: float, *, lx: float = 1.0, l
     kernel (Id - (gamma/L) Delta)^{-L} of the domain outside ``mask`` (Sec. 4.1);
     ``stall > 0``: a step also stops when its residual sets no new minimum for
     that many pairs; ``finish = 1`` (tensor-core precisions): such a step goes
-    on from its scalings on the FP32 CUDA-core form until tol."""
+    on from its scalings on the FP32 CUDA-core form until tol; ``fft = 1``:
+    the Gaussian applied by FFT convolution along each axis."""
     N = nx * ny
-    g = jko_grid(nx, ny, lx, ly, int(heat_L))
+    g = jko_grid(nx, ny, lx, ly, int(heat_L), int(fft))
     p = jko_params(gamma, tau, tol, max_iter, check_every, int(precision), int(bool(renormalize)),
                    int(absorb), int(loop), int(tile), int(stall), int(finish))
     keep = [_host_f64(w, N), _host_f64(kappa_field, N), _host_f64(alpha, N),
@@ -401,7 +404,8 @@ def jko_heat_plan(nx: int, ny: int, gamma: float, L: int = 10, lx: float = 1.0,
 def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float] = None,
                         max_iter: Optional[int] = None, check_every: int = 0,
                         renormalize: bool = True, stream=None, absorb: int = 0,
-                        loop: int = 0, tile: int = 0, stall: int = 0, finish: int = 0) -> Handle:
+                        loop: int = 0, tile: int = 0, stall: int = 0, finish: int = 0,
+                        fft: int = 0) -> Handle:
     """jko_create from an ``inputs.Problem``."""
     return jko_create(pb.nx, pb.ny, pb.gamma, pb.tau, lx=pb.lx, ly=pb.ly,
                       tol=pb.tol if tol is None else tol,
@@ -415,7 +419,7 @@ def create_from_problem(pb, precision: int = Precision.FP32, tol: Optional[float
                       species=int(getattr(pb, "species", 1)), w2=getattr(pb, "w2", None),
                       heat_L=int(getattr(pb, "heat_L", 0)),
                       pair_alpha=float(getattr(pb, "pair_alpha", 0.0)), stall=stall,
-                      finish=finish)
+                      finish=finish, fft=fft)
 
 
 class Batch:
