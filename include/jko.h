@@ -110,7 +110,19 @@ typedef struct jko_params {
   int precision;    /* a jko_precision value */
   int renormalize;  /* 1: divide each output p by its FP64 sum; 0: leave as computed */
   int absorb;       /* tensor-core precisions: separable log-domain absorption of the
-                       potential (see jko_create); 0 = automatic, 1 = on, 2 = off */
+                       potential (see jko_create); 0 = automatic, 1 = on, 2 = off;
+                       3 = the log-domain form (JKO_TF32, congestion / potential energy of
+                       one density, single handles, one kernel per pass): every scaling
+                       image is held as a TF32 mantissa and a base-2 exponent per row and
+                       group of 32 cells, the Gibbs factor with one per row and K-block of
+                       32 cells; each pass accumulates every K-block of its band apart and
+                       adds them with exact power-of-two scalings, so the scalings keep a
+                       range beyond FP32 whatever the shape of the potential.  The band
+                       ends where the Gaussian, against the largest growth of e^{-sigma w}
+                       over the distance, falls below e^{-50}; JKO_ERR_UNSUPPORTED where
+                       that band exceeds 16 K-blocks per 128 rows, or where sigma times the
+                       largest step of w between neighbouring cells exceeds 70/32 e-folds
+                       (a group could not hold its image's range) */
   int loop;         /* tensor-core precisions: 0 = automatic (one persistent kernel per
                        step, with the stop rule taken in the kernel, where the device
                        and the grid allow it, else one kernel per pass), 1 = persistent

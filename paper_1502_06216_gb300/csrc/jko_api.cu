@@ -581,8 +581,19 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
     return (*msg = "loop must be 0 (automatic), 1, 2 or 3", JKO_ERR_INVALID_ARG);
   if (p->tile != 0 && p->tile != 64 && p->tile != 128)
     return (*msg = "tile must be 0 (automatic), 64 or 128", JKO_ERR_INVALID_ARG);
-  if (p->absorb < 0 || p->absorb > 2)
-    return (*msg = "absorb must be 0 (automatic), 1 or 2", JKO_ERR_INVALID_ARG);
+  if (p->absorb < 0 || p->absorb > 3)
+    return (*msg = "absorb must be 0 (automatic), 1, 2 or 3", JKO_ERR_INVALID_ARG);
+  if (p->absorb == 3) {
+    if (p->precision != JKO_TF32)
+      return (*msg = "the log-domain form (absorb = 3) runs on JKO_TF32", JKO_ERR_UNSUPPORTED);
+    if (en->m != 0.0 || en->m_field || en->binary || en->target || en->species == 2 ||
+        g->heat_L || g->fft)
+      return (*msg = "the log-domain form serves the congestion / potential energy of one "
+                     "density on the Gaussian kernel", JKO_ERR_UNSUPPORTED);
+    if (p->loop == 1 || p->loop == 3 || (p->tile != 0 && p->tile != 64) || p->finish)
+      return (*msg = "the log-domain form runs its own per-pass kernels (loop 0 or 2, tile 0 "
+                     "or 64, no finish)", JKO_ERR_UNSUPPORTED);
+  }
   if (p->stall < 0) return (*msg = "stall must be >= 0", JKO_ERR_INVALID_ARG);
   if (p->finish != 0 && p->finish != 1) return (*msg = "finish must be 0 or 1", JKO_ERR_INVALID_ARG);
   if (p->finish && (p->precision == JKO_FP32 || p->precision == JKO_FP64))
@@ -1097,7 +1108,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     cfg.w_host = energy->w;
     cfg.sigma = params->tau / params->gamma;
     cfg.absorb = 0;
-    if (energy->w && params->absorb != 2) {
+    if (energy->w && params->absorb != 2 && params->absorb != 3) {
       double lo = INFINITY, hi = -INFINITY;
       for (int i = 0; i < h->N; ++i) { lo = std::min(lo, energy->w[i]); hi = std::max(hi, energy->w[i]); }
       cfg.absorb = params->absorb == 1 || cfg.sigma * (hi - lo) > 120.0 ? 1 : 0;
@@ -1115,6 +1126,14 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
         s = set_err(h, JKO_ERR_UNSUPPORTED, "tile width not available for this precision");
       h->use_loop = params->loop != 2 && ok;
     }
+    if (s == JKO_OK && params->absorb == 3) {
+      // the log-domain form: exponent images and its own per-pass kernels
+      std::string lmsg;
+      const int rc = jko::tc_log_setup(h->tc, energy->w, params->tau / params->gamma, &lmsg);
+      if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, lmsg);
+      else if (rc != 0) s = set_err(h, JKO_ERR_CUDA, lmsg);
+      h->use_loop = 0;
+    }
     if (s == JKO_OK && params->finish) {
       // the FP32 CUDA-core form that finishes a stalled step: its taps
       if (jko::tc_absorbed(h->tc))
@@ -1124,7 +1143,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
         s = setup_simt<float>(h);
     }
   }
-  if (s == JKO_OK && h->tc && params->loop == 0 && params->tile == 0 &&
+  if (s == JKO_OK && h->tc && !jko::tc_logdomain(h->tc) && params->loop == 0 && params->tile == 0 &&
       (long long)grid->nx * grid->ny >= 256LL * 256LL) {
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(cuda_err(h, e, "set-up"));
@@ -1642,6 +1661,8 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
     if (params[f].finish)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED,
                             "finish (the FP32 continuation of a stalled step) is for single handles"));
+    if (params[f].absorb == 3)
+      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the log-domain form is for single handles"));
     if (energies[f].target)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
     if (energies[f].species == 2)

@@ -661,6 +661,23 @@ struct TcPlan {
   int loop_grid = 0;
   int loop_res = 0;            // the loop kernel keeps each CTA's factor band resident
   double loop_flops_pair = 0.0;
+  // log-domain form (tc_log.cu, TF32): exponent per row and 32-cell group of
+  // the images a, b ([ny][gx]) and T ([nx][gy]); -sigma w log2(e) as a
+  // mantissa in [1, 2) and an integer exponent; per axis the factor scaled by
+  // a power of two per row and K-block, those exponents [n][gk] and its band
+  int logd = 0;
+  int gx = 0, gy = 0;
+  int* sh_a = nullptr;
+  int* sh_b = nullptr;
+  int* sh_t = nullptr;
+  float* lwm = nullptr;
+  int* lwe = nullptr;
+  void* k_log[2] = {nullptr, nullptr};
+  int* sk[2] = {nullptr, nullptr};
+  int gk[2] = {0, 0};
+  int4* kbt_log[2] = {nullptr, nullptr};
+  CUtensorMap mKl[2];          // the scaled factors as A operands
+  CUtensorMap l32[3];          // a, b, T loads in 32-row boxes
 };
 
 }  // namespace jko

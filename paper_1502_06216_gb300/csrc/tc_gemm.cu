@@ -687,7 +687,16 @@ int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg) {
   return 0;
 }
 
+cudaError_t tc_log_begin_step(TcPlan* P, cudaStream_t st);
+cudaError_t tc_log_enqueue_pass(TcPlan* P, int which, cudaStream_t st);
+
+int tc_logdomain(const TcPlan* P) { return P ? P->logd : 0; }
+
 cudaError_t tc_begin_step(TcPlan* P, cudaStream_t st) {
+  if (P->logd) {
+    cudaError_t e = tc_log_begin_step(P, st);
+    if (e != cudaSuccess) return e;
+  }
   const long long n = (long long)P->cfg.ny * P->px;
   if (P->mode == MODE_TF32)
     fill_op_kernel<float><<<152 * 4, 256, 0, st>>>((float*)P->img_a[0], nullptr, n, 1.0f);
@@ -712,6 +721,7 @@ cudaError_t tc_export_scalings(const TcPlan* P, float* a, float* b, cudaStream_t
 }
 
 cudaError_t tc_enqueue_pass(TcPlan* P, int which, cudaStream_t st) {
+  if (P->logd) return tc_log_enqueue_pass(P, which, st);
   const TcConfig& c = P->cfg;
   const bool over_x = (which & 1) == 0;
   const int half = which >> 1;
@@ -778,14 +788,17 @@ int tc_set_tile(TcPlan* P, int bn) {
 int tc_absorbed(const TcPlan* P) { return P ? P->absorbed : 0; }
 
 int tc_partials(int nx, int ny) {
-  // upper bound over the tile widths: 64-column tiles give the most blocks
-  return ((nx + 63) / 64) * ((ny + BM - 1) / BM);
+  // upper bound over the tile widths: the log-domain form's 32-column tiles
+  // give the most blocks
+  return ((nx + 31) / 32) * ((ny + BM - 1) / BM);
 }
 
 void tc_destroy(TcPlan* P) {
   if (!P) return;
   void* bufs[] = {P->img_a[0], P->img_a[1], P->img_b[0], P->img_b[1], P->img_t[0],
-                  P->img_t[1], P->E_abs, P->sw_abs};
+                  P->img_t[1], P->E_abs, P->sw_abs, P->sh_a, P->sh_b, P->sh_t, P->lwm,
+                  P->lwe, P->k_log[0], P->k_log[1], P->sk[0], P->sk[1], P->kbt_log[0],
+                  P->kbt_log[1]};
   for (void* b : bufs) if (b) cudaFree(b);
   for (int axis = 0; axis < 2; ++axis)
     for (int side = 0; side < 2; ++side) {

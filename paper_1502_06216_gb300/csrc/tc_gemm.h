@@ -40,6 +40,12 @@ int tc_absorbed(const TcPlan* plan);
 
 // 0 = ok, 1 = unsupported configuration (message set), 2 = CUDA error.
 int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);
+// Log-domain form (tc_log.cu): every image carries base-2 exponents per row and
+// group of 32 cells, the factor one per row and K-block; TF32 plans without
+// separable absorption, per-pass kernels, the congestion/potential energy.
+// 0 = ok, 1 = unsupported (message set), 2 = CUDA error.
+int tc_log_setup(TcPlan* plan, const double* w_host, double sigma, std::string* msg);
+int tc_logdomain(const TcPlan* plan);
 // Per-step reset of the scaling operands (a = 1).
 cudaError_t tc_begin_step(TcPlan* plan, cudaStream_t st);
 // The current scalings a, b as fp32 [ny][nx] images (the operand values the

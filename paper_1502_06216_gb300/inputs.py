@@ -136,6 +136,22 @@ def crowd_problem(n: int, gamma: float, tau: float = 0.02,
                    max_iter=max_iter, tol=tol, name=name)
 
 
+def cone_crowd_problem(n: int, gamma: float = 1e-3, tau: float = 0.5, ny: Optional[int] = None,
+                       kappa_factor: float = 1.5, n_steps: int = 3, tol: float = 1e-6,
+                       max_iter: int = 2000, name: str = "") -> Problem:
+    """Crowd motion toward an exit at (0.9, 0.5) under the cone potential
+    w = |x - (0.9, 0.5)| (the distance, not its square): not a sum of a
+    function of x and one of y, so the potential's range that a separable
+    log-scale cannot remove grows with sigma = tau / gamma (about 110 e-folds
+    at sigma = 500).  q0: the uniform disk of radius 0.2 at (0.25, 0.5)."""
+    pb = crowd_problem(n, gamma=gamma, tau=tau, ny=ny, kappa_factor=kappa_factor,
+                       n_steps=n_steps, max_iter=max_iter, tol=tol,
+                       name=name or f"cone-crowd-{n}")
+    X, Y = _mesh(pb.nx, pb.ny, pb.lx, pb.ly)
+    pb.w = np.sqrt((X - 0.9) ** 2 + (Y - 0.5) ** 2).ravel()
+    return pb
+
+
 def _smooth_field(rng, X, Y, n_bumps=8):
     acc = np.zeros_like(X)
     for _ in range(n_bumps):

@@ -140,6 +140,22 @@ def test_log_domain_where_potential_underflows():
     assert np.abs(r.p - p).sum() <= 1e-12
 
 
+def test_log_domain_equals_scaling_form_on_the_cone():
+    """The cone potential w = |x - (0.9, 0.5)| at sigma = 500 (the recipe of the
+    log-domain tensor-core form): the scalings span e^{500}, inside FP64's
+    range, so the FP64 scaling loop and the log-sum-exp step agree."""
+    pb = inputs.cone_crowd_problem(40, n_steps=1)
+    en = Energy(w=pb.w, kappa=pb.kappa)
+    sigma = pb.tau / pb.gamma
+    r = jko.step(pb.q0, gibbs.SeparableXi(40, 40, pb.gamma), sigma, en, tol=1e-12,
+                 max_iter=20000)
+    p, it, res, la, lb = logdomain.step(pb.q0, logdomain.LogXi(40, 40, pb.gamma), sigma, en,
+                                        tol=1e-12, max_iter=20000)
+    assert la.min() < -300.0
+    assert it == r.iters
+    assert np.abs(r.p - p).sum() <= 1e-11
+
+
 def test_cold_start_does_not_change_the_fixed_point():
     """The step's minimiser is unique (Eq. def-jko-operator), so a converged
     step from a = e^{beta} equals the one from a = 1."""
