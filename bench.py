@@ -558,9 +558,10 @@ def run_heat(args, jko, dev, barrier, steps=4):
     """Crowd motion through a door with the heat-kernel Gibbs kernel (Sec. 4.1,
     Eq. heat-kernel, L = 10): 100^2, two rooms, q0 a disk, kappa = 1.2 max q0,
     gamma = 5e-4, tau = 0.02, <= 300 pairs, tol 1e-6, CUDA-core forms.  Pairs/s
-    of one `steps`-step flow after a 1-step warm-up, the mean time per launch
-    (2 L (K + 1) + 2 launches a pair: the solves are launch-bound at this
-    size), and the last step of FP32 against FP64."""
+    of one `steps`-step flow after a 1-step warm-up, for the persistent form
+    (one cooperative launch per step) and the kernels per Clenshaw phase
+    (2 (1 + ceil(D / 2)) + 2 launches a pair, with their mean time per launch),
+    and the last step of FP32 against FP64."""
     import torch
     from paper_1502_06216_gb300 import inputs
     pb = inputs.heat_crowd_problem(100, n_steps=steps, tol=1e-6, max_iter=300)
@@ -568,8 +569,9 @@ def run_heat(args, jko, dev, barrier, steps=4):
                        f"gamma={pb.gamma}, tau={pb.tau}, kappa=1.2 max q0, <={pb.max_iter} "
                        f"pairs/step, tol {pb.tol}"}
     finals = {}
-    for form in ("FP32", "FP64"):
-        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+
+    def timed(form, loop):
+        h = jko.create_from_problem(pb, precision=jko.Precision[form], loop=loop)
         p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
         jko.jko_flow(h, p0, 1)
         barrier()
@@ -580,12 +582,17 @@ def run_heat(args, jko, dev, barrier, steps=4):
         barrier()
         secs = e0.elapsed_time(e1) / 1e3
         iters = sum(i["iters"] for i in infos)
-        finals[form] = pf.double()
         launches = sum(i["kernels"] for i in infos)
-        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
-                     "pairs_per_step": iters / steps, "launches": launches,
-                     "us_per_launch": 1e6 * secs / launches}
+        info = jko.jko_handle_info(h)
         jko.jko_destroy(h)
+        return pf.double(), {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                             "pairs_per_step": iters / steps, "launches": launches,
+                             "us_per_launch": 1e6 * secs / launches, "persistent": info["loop"]}
+
+    for form in ("FP32", "FP64"):
+        finals[form], out[form] = timed(form, 0)
+        pf2, out[form]["per_phase_kernels"] = timed(form, 2)
+        out[form]["same_bits_as_per_phase"] = bool(torch.equal(pf2, finals[form]))
     out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
                                                finals["FP64"].abs().sum())
     return out

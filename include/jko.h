@@ -128,7 +128,11 @@ typedef struct jko_params {
                        and the grid allow it, else one kernel per pass), 1 = persistent
                        kernel required (JKO_ERR_UNSUPPORTED if it cannot run), 2 = one
                        kernel per pass, 3 = as 1, and in a batch the flow joins the
-                       grouped launch of its precision (jko_batch_create) */
+                       grouped launch of its precision (jko_batch_create).  Heat-kernel
+                       handles (jko_grid.heat_L > 0): 0 or 1 = one persistent cooperative
+                       kernel per step where the device has cooperative launches (1:
+                       JKO_ERR_UNSUPPORTED where not), 2 = kernels per Clenshaw phase;
+                       both give the same bits.  Other CUDA-core handles ignore it */
   int tile;         /* tensor-core precisions: output tile width of the per-pass kernels,
                        64 or 128 (128: JKO_TF32 only), or 0 = automatic.  With loop = 0
                        and tile = 0 on grids of 256^2 cells or more, jko_create times the

@@ -16,6 +16,7 @@
 // The b-update (with the residual partials of the stop rule) and the prox
 // (with the pair counter) are elementwise kernels around the two xi~
 // applications of a pair; every kernel passes the stop gate first.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -39,17 +40,28 @@ __device__ __forceinline__ bool is_free(const HeatGeom& g, int i) {
   return g.mask == nullptr || g.mask[i] == 0;
 }
 
+// The per-cell arithmetic of the recurrence, written with explicit roundings
+// so that every kernel below (per phase or persistent) performs the same
+// operations whatever the compiler contracts.
+// acc + c (vi - vj): one neighbour's term of A v
+__device__ __forceinline__ double nb_term(double acc, double c, double vi, double vj) {
+  return __fma_rn(c, __dsub_rn(vi, vj), acc);
+}
+// one Clenshaw step's value ck v + s (A b1 - theta b1) - b2
+__device__ __forceinline__ double cl_value(double ck, double v, double s, double Ab, double theta,
+                                          double b1, double b2) {
+  return __dsub_rn(__fma_rn(ck, v, __dmul_rn(s, __fma_rn(-theta, b1, Ab))), b2);
+}
+
 // (A v)_i = v_i + sum over free neighbours j of c_dir (v_i - v_j)
-template <typename T>
-__device__ __forceinline__ T apply_A(const HeatGeom& g, const T* v, int x, int y) {
+__device__ __forceinline__ double apply_A(const HeatGeom& g, const double* v, int x, int y) {
   const int i = y * g.nx + x;
-  const T vi = v[i];
-  T acc = vi;
-  const T cx = (T)g.cx, cy = (T)g.cy;
-  if (x > 0 && is_free(g, i - 1)) acc += cx * (vi - v[i - 1]);
-  if (x + 1 < g.nx && is_free(g, i + 1)) acc += cx * (vi - v[i + 1]);
-  if (y > 0 && is_free(g, i - g.nx)) acc += cy * (vi - v[i - g.nx]);
-  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc += cy * (vi - v[i + g.nx]);
+  const double vi = v[i];
+  double acc = vi;
+  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, vi, v[i - 1]);
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, vi, v[i + 1]);
+  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, vi, v[i - g.nx]);
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, vi, v[i + g.nx]);
   return acc;
 }
 
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_init(const T* v, double* b1
   const int xx = blockIdx.x * HBX + threadIdx.x, yy = blockIdx.y * HBY + threadIdx.y;
   if (xx >= g.nx || yy >= g.ny) return;
   const int i = yy * g.nx + xx;
-  b1[i] = is_free(g, i) ? cD * (double)v[i] : 0.0;
+  b1[i] = is_free(g, i) ? __dmul_rn(cD, (double)v[i]) : 0.0;
   b2[i] = 0.0;
 }
 
@@ -99,8 +111,8 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const doub
     out[i] = O(0);
     return;
   }
-  const double Ab = apply_A<double>(g, b1, xx, yy);
-  const double r = ck * (double)v[i] + s_over_delta * (Ab - theta * b1[i]) - b2[i];
+  const double Ab = apply_A(g, b1, xx, yy);
+  const double r = cl_value(ck, (double)v[i], s_over_delta, Ab, theta, b1[i], b2[i]);
   out[i] = (O)(CLOSE ? close_value(r) : r);
 }
 
@@ -127,8 +139,8 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const dou
     if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
       const int i = y * g.nx + x;
       if (is_free(g, i)) {
-        const double Ab = apply_A<double>(g, b1, x, y);
-        val = ck * (double)v[i] + g.two_over_delta * (Ab - theta * b1[i]) - b2[i];
+        const double Ab = apply_A(g, b1, x, y);
+        val = cl_value(ck, (double)v[i], g.two_over_delta, Ab, theta, b1[i], b2[i]);
       }
     }
     sb[ry][rx] = val;
@@ -146,11 +158,11 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const dou
   }
   // A b_k at (x, y) from the tile: the neighbour tests of apply_A
   double acc = c;
-  if (x > 0 && is_free(g, i - 1)) acc += g.cx * (c - sb[ty][tx - 1]);
-  if (x + 1 < g.nx && is_free(g, i + 1)) acc += g.cx * (c - sb[ty][tx + 1]);
-  if (y > 0 && is_free(g, i - g.nx)) acc += g.cy * (c - sb[ty - 1][tx]);
-  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc += g.cy * (c - sb[ty + 1][tx]);
-  const double r = ck1 * (double)v[i] + s2 * (acc - theta * c) - b1[i];
+  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, c, sb[ty][tx - 1]);
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, c, sb[ty][tx + 1]);
+  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, c, sb[ty - 1][tx]);
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, c, sb[ty + 1][tx]);
+  const double r = cl_value(ck1, (double)v[i], s2, acc, theta, c, b1[i]);
   o2[i] = (O)(CLOSE ? close_value(r) : r);
 }
 
@@ -202,6 +214,346 @@ __global__ void __launch_bounds__(HBX * HBY) heat_prox(const T* s, T* a, T* p, H
 }
 
 dim3 heat_grid(int nx, int ny) { return dim3((nx + HBX - 1) / HBX, (ny + HBY - 1) / HBY); }
+
+// ------------------------------------------------------------ persistent form
+// One cooperative launch runs up to `pairs` pairs: the Clenshaw phases of the
+// two applications of xi~, the b-update and the prox, with a grid barrier
+// (jko_internal.cuh) where the kernels above end one launch and start the next.
+// Block b takes the 16x8 tiles b, b + G, ... of the grid (the same tiles in
+// every phase), with the arithmetic of heat_cl_step / heat_cl_step2 per tile:
+//   * the first Clenshaw iterates b_D = c_D v, b_{D+1} = 0 are formed on the
+//     fly from v where the kernels above store them (the same values);
+//   * the closing step ends in the b-update (first application: b = q / Y
+//     and the residual partial of the tile, as heat_bupdate) or the prox
+//     (second application: a, p, as heat_prox);
+//   * the stop rule (Sec. 3.4) adds the tiles' residual partials in the order
+//     of stop_gate, in every block after the barrier that ends the b-update;
+//     when it fires the second application and the prox are skipped, as the
+//     kernels above return at their stop gate.
+// So the two forms give the same bits and the same pair counts.  Reads of what
+// other blocks wrote in an earlier phase are ordinary loads: the barrier's
+// acquire, followed by the block barrier, orders them after those writes.
+template <typename T>
+struct HeatLoopArgs {
+  HeatGeom g;
+  const double* coef;      // c_0 .. c_D
+  int D;
+  double theta, inv_delta;
+  double* d[4];            // Clenshaw iterates (FP64)
+  const T* q;
+  T* a;
+  T* b;
+  T* p;
+  ProxArgs<T> P;
+  Ctrl* ctrl;
+  double* part;            // residual partial of each tile (heat_bupdate's blocks)
+  int ntiles, tiles_x;
+  int pairs;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld_plain(const T* p) { return *p; }
+
+// A v at (x, y) where v is stored as c * v[j] (the first iterate b_D = c_D v):
+// the neighbour terms of apply_A on those values.
+template <typename T>
+__device__ __forceinline__ double scaled(const T* v, int j, double c) {
+  return __dmul_rn(c, (double)ld_plain(v + j));
+}
+template <typename T>
+__device__ __forceinline__ double apply_A_scaled(const HeatGeom& g, const T* v, double c, int x,
+                                                 int y) {
+  const int i = y * g.nx + x;
+  const double vi = scaled(v, i, c);
+  double acc = vi;
+  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, vi, scaled(v, i - 1, c));
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, vi, scaled(v, i + 1, c));
+  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, vi, scaled(v, i - g.nx, c));
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, vi, scaled(v, i + g.nx, c));
+  return acc;
+}
+// A tile and its two-cell halo in shared memory: v, b_{k+1}, b_{k+2}, and
+// whether each cell is in the grid and off the mask.
+constexpr int HEX = HBX + 4, HEY = HBY + 4;
+struct HeatStage {
+  double v[HEY][HEX];
+  double b1[HEY][HEX];
+  double b2[HEY][HEX];
+  unsigned char fr[HEY][HEX];
+};
+
+// The closing step's output r at cell i of the grid, into the b-update (app 0)
+// or the prox (app 1).
+template <typename T, int EK>
+__device__ __forceinline__ void heat_close_cell(const HeatLoopArgs<T>& A, int app, int i, double r,
+                                                bool have_prev, T& res, int& bad) {
+  const T y = (T)close_value(r);
+  if (app == 0) {
+    const T qi = __ldg(A.q + i);
+    if (have_prev) res = abs_residual<T>(ld_plain(A.b + i), y, qi);
+    const T bn = b_update<T>(qi, y);
+    bad |= !dev_finite(bn);
+    A.b[i] = bn;
+  } else {
+    const T ai = prox_ratio<T, EK>(A.P, i, y);
+    bad |= !dev_finite(ai);
+    A.a[i] = ai;
+    A.p[i] = ai * y;
+  }
+}
+
+// One Clenshaw phase on one tile: steps k and (when TWO) k - 1.  b1 = b_{k+1},
+// b2 = b_{k+2} (VIRT: b_{k+1} = c1v v, b_{k+2} = 0, not stored); writes b_k to
+// o1 and b_{k-1} to o2, or closes (CLOSE: the last step is step 0) into the
+// epilogue.  ONE_STORE: a single step that also stores b_{k+1} = c1v v to o2
+// (the first step of an odd degree, whose successors read it).
+template <typename T, int EK, bool TWO, bool VIRT, bool CLOSE>
+__device__ __forceinline__ void heat_tile_phase(const HeatLoopArgs<T>& A, int app, int t,
+                                                const T* v, const double* b1, const double* b2,
+                                                double* o1, double* o2, double c1v, double ck,
+                                                double ck1, bool have_prev, double (*sb)[HBX + 2],
+                                                HeatStage* stg, double* s_red, int& bad) {
+  constexpr int RX = HBX + 2, RY = HBY + 2;
+  const HeatGeom& g = A.g;
+  const int tyt = t / A.tiles_x;
+  const int x0 = (t - tyt * A.tiles_x) * HBX, y0 = tyt * HBY;
+  const int tid = threadIdx.y * HBX + threadIdx.x;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+  const bool in = x < g.nx && y < g.ny;
+  const int i = y * g.nx + x;
+  T res = T(0);
+  if (TWO) {
+    // v, b_{k+1}, b_{k+2} and the free flags (in the grid and off the mask) on
+    // the tile and a two-cell halo, staged with independent loads
+    HeatStage& S = *stg;
+    for (int idx = tid; idx < HEX * HEY; idx += HBX * HBY) {
+      const int ey = idx / HEX, ex = idx - ey * HEX;
+      const int xx = x0 + ex - 2, yy = y0 + ey - 2;
+      double vv = 0.0, bb1 = 0.0, bb2 = 0.0;
+      unsigned char f = 0;
+      if (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) {
+        const int j = yy * g.nx + xx;
+        vv = (double)ld_plain(v + j);
+        if (!VIRT) {
+          bb1 = ld_plain(b1 + j);
+          bb2 = ld_plain(b2 + j);
+        }
+        f = g.mask == nullptr || g.mask[j] == 0;
+      }
+      S.v[ey][ex] = vv;
+      S.b1[ey][ex] = VIRT ? __dmul_rn(c1v, vv) : bb1;
+      S.b2[ey][ex] = bb2;
+      S.fr[ey][ex] = f;
+    }
+    __syncthreads();
+    // b_k on the tile and a one-cell halo (heat_cl_step2's first step)
+    for (int idx = tid; idx < RX * RY; idx += HBX * HBY) {
+      const int ry = idx / RX, rx = idx - ry * RX;
+      const int ey = ry + 1, ex = rx + 1;
+      double val = 0.0;
+      if (S.fr[ey][ex]) {
+        const double bc = S.b1[ey][ex];
+        double Ab = bc;
+        if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, S.b1[ey][ex - 1]);
+        if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, S.b1[ey][ex + 1]);
+        if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, S.b1[ey - 1][ex]);
+        if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, S.b1[ey + 1][ex]);
+        val = cl_value(ck, S.v[ey][ex], g.two_over_delta, Ab, A.theta, bc, S.b2[ey][ex]);
+      }
+      sb[ry][rx] = val;
+    }
+    __syncthreads();
+    if (in) {
+      const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+      const int ex = threadIdx.x + 2, ey = threadIdx.y + 2;
+      const double c = sb[ty][tx];
+      if (!CLOSE) o1[i] = c;
+      if (!S.fr[ey][ex]) {
+        if (CLOSE) heat_close_cell<T, EK>(A, app, i, 0.0, have_prev, res, bad);
+        else o2[i] = 0.0;
+      } else {
+        double acc = c;
+        if (S.fr[ey][ex - 1]) acc = nb_term(acc, g.cx, c, sb[ty][tx - 1]);
+        if (S.fr[ey][ex + 1]) acc = nb_term(acc, g.cx, c, sb[ty][tx + 1]);
+        if (S.fr[ey - 1][ex]) acc = nb_term(acc, g.cy, c, sb[ty - 1][tx]);
+        if (S.fr[ey + 1][ex]) acc = nb_term(acc, g.cy, c, sb[ty + 1][tx]);
+        const double s2 = CLOSE ? A.inv_delta : g.two_over_delta;
+        const double r = cl_value(ck1, S.v[ey][ex], s2, acc, A.theta, c, S.b1[ey][ex]);
+        if (CLOSE) heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
+        else o2[i] = r;
+      }
+    }
+    __syncthreads();   // the staging and sb are reused by the next tile
+  } else if (in) {
+    // one step (heat_cl_step): from the virtual first iterates
+    if (!is_free(g, i)) {
+      if (CLOSE) heat_close_cell<T, EK>(A, app, i, 0.0, have_prev, res, bad);
+      else {
+        o1[i] = 0.0;
+        o2[i] = 0.0;
+      }
+    } else {
+      const double vi = (double)ld_plain(v + i);
+      const double Ab = apply_A_scaled<T>(g, v, c1v, x, y);
+      const double s = CLOSE ? A.inv_delta : g.two_over_delta;
+      const double r = cl_value(ck, vi, s, Ab, A.theta, __dmul_rn(c1v, vi), 0.0);
+      if (CLOSE) heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
+      else {
+        o1[i] = r;
+        o2[i] = __dmul_rn(c1v, vi);
+      }
+    }
+  }
+  if (CLOSE && app == 0) {
+    // the tile's residual partial, as heat_bupdate's block
+    const double tot = block_sum((double)res, s_red);
+    if (tid == 0) A.part[t] = tot;
+  }
+}
+
+template <typename T, int EK>
+__global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A) {
+  __shared__ double sb[HBY + 2][HBX + 2];
+  __shared__ HeatStage stg;
+  __shared__ double s_red[33];
+  __shared__ int s_stop, s_fault, s_it0, s_maxit;
+  __shared__ unsigned s_base;
+  __shared__ double s_tol;
+  const int tid = threadIdx.y * HBX + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  const unsigned G = gridDim.x;
+  Ctrl* ctrl = A.ctrl;
+  if (tid == 0) {
+    const int done = *(volatile int*)&ctrl->done;
+    const int nonfinite = *(volatile int*)&ctrl->nonfinite;
+    s_stop = (done != RUNNING || nonfinite) ? 1 : 0;
+    if (done == RUNNING && nonfinite && blockIdx.x == 0) ctrl->done = NONFINITE;
+    s_it0 = ctrl->it;
+    s_maxit = ctrl->max_iter;
+    s_tol = ctrl->tol;
+    s_base = ctrl->bar_base;
+    s_fault = 0;
+  }
+  __syncthreads();
+  if (s_stop) return;
+  unsigned nbar = 0;
+  int bad = 0;
+  int pairs_done = 0;
+  // grid barrier of every thread of the block; false: the loop stops here
+  // The flag slot of barrier b is final once b is complete; thread 0 loads it
+  // then and acts on it at barrier b + 1 (the load stays off the path to the
+  // next phase), so every block stops at the same barrier.
+  unsigned flag_prev = 0;
+  auto barrier = [&]() -> bool {
+    bad = __syncthreads_or(bad);
+    if (tid == 0) {
+      if (bad) atomicOr(&ctrl->nonfinite, 1);
+      const unsigned b = s_base + (++nbar);
+      const bool ok = grid_barrier(ctrl, G, b, bad != 0 || s_fault != 0);
+      if (!ok) {
+        s_fault = 1;
+        atomicOr(&ctrl->nonfinite, 2);
+      }
+      const int stop = flag_prev != 0 || !ok;
+      if (stop && blockIdx.x == 0) ctrl->done = NONFINITE;
+      s_stop = stop;
+      flag_prev = *(volatile unsigned*)&ctrl->bar_flag[b % 3];
+      if (blockIdx.x == 0) ctrl->bar_flag[(b + 2) % 3] = 0u;
+    }
+    bad = 0;
+    __syncthreads();
+    return s_stop == 0;
+  };
+  const int D = A.D;
+  bool run = true;
+  for (int pair = 0; pair < A.pairs && run; ++pair) {
+    const int it = s_it0 + pair;
+    for (int app = 0; app < 2 && run; ++app) {
+      if (app == 1) {
+        // stop rule from the b-update's partials, in stop_gate's order
+        if (wid == 0) {
+          double v = 0.0;
+          for (int i = lane; i < A.ntiles; i += 32) v += ld_plain(A.part + i);
+          v = warp_sum(v);
+          const bool first = lane == 0 && blockIdx.x == 0;
+          int d = RUNNING;
+          if (it > 0 && !isfinite(v)) d = NONFINITE;
+          else if (it > 0 && v <= s_tol) d = CONVERGED;
+          else if (it >= s_maxit) d = MAX_ITER;
+          else if (stall_rule(ctrl, it, v, first)) d = STALLED;
+          if (first) {
+            if (it > 0) ctrl->res_last = v;
+            if (d != RUNNING) ctrl->done = d;
+          }
+          if (lane == 0) s_stop = d != RUNNING;
+        }
+        __syncthreads();
+        if (s_stop) { run = false; break; }
+      }
+      const T* v = app == 0 ? A.a : A.b;
+      const bool have_prev = app == 0 && it > 0;
+      const double cD = __ldg(A.coef + D);
+      int r1 = 0, r2 = 1, f1 = 2, f2 = 3;
+      int k = D - 1;
+      bool virt = true;
+      if (D % 2 == 1) {
+        // one single step first: b_{D-1} to d[0], b_D = c_D v to d[1] (or
+        // the closing step when D = 1)
+        for (int t = blockIdx.x; t < A.ntiles; t += G) {
+          if (k == 0)
+            heat_tile_phase<T, EK, false, true, true>(A, app, t, v, nullptr, nullptr, nullptr,
+                                                      nullptr, cD, __ldg(A.coef + (0)), 0.0, have_prev,
+                                                      sb, &stg, s_red, bad);
+          else
+            heat_tile_phase<T, EK, false, true, false>(A, app, t, v, nullptr, nullptr, A.d[0],
+                                                       A.d[1], cD, __ldg(A.coef + (k)), 0.0, have_prev,
+                                                       sb, &stg, s_red, bad);
+        }
+        if (!barrier()) { run = false; break; }
+        if (k == 0) continue;
+        virt = false;
+        r1 = 0; r2 = 1; f1 = 2; f2 = 3;
+        --k;
+      }
+      for (; k >= 1 && run; k -= 2) {
+        const bool close = k == 1;
+        for (int t = blockIdx.x; t < A.ntiles; t += G) {
+          if (virt) {
+            if (close)
+              heat_tile_phase<T, EK, true, true, true>(A, app, t, v, nullptr, nullptr, nullptr,
+                                                       nullptr, cD, __ldg(A.coef + (1)), __ldg(A.coef + (0)),
+                                                       have_prev, sb, &stg, s_red, bad);
+            else
+              heat_tile_phase<T, EK, true, true, false>(A, app, t, v, nullptr, nullptr, A.d[f1],
+                                                        A.d[f2], cD, __ldg(A.coef + (k)), __ldg(A.coef + (k - 1)),
+                                                        have_prev, sb, &stg, s_red, bad);
+          } else {
+            if (close)
+              heat_tile_phase<T, EK, true, false, true>(A, app, t, v, A.d[r1], A.d[r2], nullptr,
+                                                        nullptr, 0.0, __ldg(A.coef + (1)), __ldg(A.coef + (0)),
+                                                        have_prev, sb, &stg, s_red, bad);
+            else
+              heat_tile_phase<T, EK, true, false, false>(A, app, t, v, A.d[r1], A.d[r2], A.d[f1],
+                                                         A.d[f2], 0.0, __ldg(A.coef + (k)), __ldg(A.coef + (k - 1)),
+                                                         have_prev, sb, &stg, s_red, bad);
+          }
+        }
+        if (!barrier()) { run = false; break; }
+        virt = false;
+        const int o1 = r1, o2 = r2;
+        r1 = f2;
+        r2 = f1;
+        f1 = o1;
+        f2 = o2;
+      }
+    }
+    if (run) pairs_done = pair + 1;
+  }
+  if (tid == 0 && blockIdx.x == 0) {
+    ctrl->it = s_it0 + pairs_done;
+    ctrl->bar_base = s_base + nbar;   // every block crossed the same barriers
+  }
+}
 
 }  // namespace
 
@@ -332,6 +684,72 @@ cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T*
 
 int heat_launches(const HeatPlan& hp) { return 1 + (hp.D + 1) / 2; }
 
+namespace {
+template <typename T>
+void* heat_loop_fn(int ek) {
+  if (ek == EK_CROWD) return (void*)heat_loop_kernel<T, EK_CROWD>;
+  if (ek == EK_ENTROPY) return (void*)heat_loop_kernel<T, EK_ENTROPY>;
+  return (void*)heat_loop_kernel<T, EK_POWER>;
+}
+}  // namespace
+
+// Blocks of the persistent form: one per 16x8 tile, at most 4 per SM and as
+// many as can be co-resident (a cooperative launch); 0 where the device has
+// no cooperative launch.
+int heat_loop_grid(int nx, int ny, bool fp64, int ek) {
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop || sms <= 0) return 0;
+  void* fn = fp64 ? heat_loop_fn<double>(ek) : heat_loop_fn<float>(ek);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HBX * HBY, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const long long cap = (long long)std::min(per_sm, 4) * sms;
+  const long long tiles = heat_blocks(nx, ny);
+  return (int)std::min(cap, tiles);
+}
+
+template <typename T>
+cudaError_t heat_loop_launch(const HeatPlan& hp, const HeatBuffers& B, int ek, const T* q, T* a,
+                             T* b, T* p, int nx, int ny, const uint8_t* mask, const ProxArgs<T>& P,
+                             Ctrl* ctrl, double* part, int G, int pairs, cudaStream_t st) {
+  HeatLoopArgs<T> A{};
+  const double inv_delta = hp.delta > 0 ? 1.0 / hp.delta : 0.0;
+  A.g = HeatGeom{nx, ny, hp.cx, hp.cy, mask, 2.0 * inv_delta};
+  A.coef = (const double*)B.coef;
+  A.D = hp.D;
+  A.theta = hp.theta;
+  A.inv_delta = inv_delta;
+  for (int i = 0; i < 4; ++i) A.d[i] = (double*)B.d[i];
+  A.q = q;
+  A.a = a;
+  A.b = b;
+  A.p = p;
+  A.P = P;
+  A.ctrl = ctrl;
+  A.part = part;
+  const dim3 tg = heat_grid(nx, ny);
+  A.tiles_x = (int)tg.x;
+  A.ntiles = (int)(tg.x * tg.y);
+  A.pairs = pairs;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(HBX, HBY);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (ek == EK_CROWD) return cudaLaunchKernelEx(&cfg, heat_loop_kernel<T, EK_CROWD>, A);
+  if (ek == EK_ENTROPY) return cudaLaunchKernelEx(&cfg, heat_loop_kernel<T, EK_ENTROPY>, A);
+  return cudaLaunchKernelEx(&cfg, heat_loop_kernel<T, EK_POWER>, A);
+}
+
 template <typename T>
 cudaError_t heat_bupdate_launch(const T* Y, T* b, const T* q, int nx, int ny, Ctrl* ctrl,
                                 double* part, cudaStream_t st) {
@@ -358,7 +776,11 @@ cudaError_t heat_prox_launch(int ek, const T* s, T* a, T* p, int nx, int ny, con
   template cudaError_t heat_bupdate_launch<T>(const T*, T*, const T*, int, int, Ctrl*,        \
                                               double*, cudaStream_t);                         \
   template cudaError_t heat_prox_launch<T>(int, const T*, T*, T*, int, int,                   \
-                                           const ProxArgs<T>&, Ctrl*, cudaStream_t);
+                                           const ProxArgs<T>&, Ctrl*, cudaStream_t);           \
+  template cudaError_t heat_loop_launch<T>(const HeatPlan&, const HeatBuffers&, int, const T*, \
+                                           T*, T*, T*, int, int, const uint8_t*,               \
+                                           const ProxArgs<T>&, Ctrl*, double*, int, int,       \
+                                           cudaStream_t);
 JKO_HEAT_INST(float)
 JKO_HEAT_INST(double)
 #undef JKO_HEAT_INST

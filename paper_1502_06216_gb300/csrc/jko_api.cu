@@ -374,11 +374,28 @@ double pass_flops(const jko_handle* h, int which) {
   return 2.0 * (2.0 * r + 1.0) * (double)h->N;
 }
 
+// `pairs` pairs as one persistent launch: the tensor-core loop kernel, or the
+// heat kernel's persistent form.
+cudaError_t enqueue_loop(jko_handle* h, int pairs, cudaStream_t st) {
+  if (h->tc) return jko::tc_enqueue_loop(h->tc, pairs, st);
+  const int nx = h->grid.nx, ny = h->grid.ny;
+  const uint8_t* mask = (const uint8_t*)h->mask;
+  if (h->fp64)
+    return jko::heat_loop_launch<double>(h->heat, h->hb, h->ek, (const double*)h->q, (double*)h->a,
+                                         (double*)h->b, (double*)h->p, nx, ny, mask,
+                                         jko::prox_args<double>(h), h->ctrl, h->part, h->heat_G,
+                                         pairs, st);
+  return jko::heat_loop_launch<float>(h->heat, h->hb, h->ek, (const float*)h->q, (float*)h->a,
+                                      (float*)h->b, (float*)h->p, nx, ny, mask,
+                                      jko::prox_args<float>(h), h->ctrl, h->part, h->heat_G, pairs,
+                                      st);
+}
+
 jko_status capture_chunk(jko_handle* h) {
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  if (h->use_loop) e = jko::tc_enqueue_loop(h->tc, h->chunk_iters, h->cap);
+  if (h->use_loop) e = enqueue_loop(h, h->chunk_iters, h->cap);
   else
     for (int i = 0; i < h->chunk_iters && e == cudaSuccess; ++i) e = enqueue_pair(h, h->cap);
   cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
@@ -405,7 +422,7 @@ jko_status capture_chunk(jko_handle* h) {
 // One chunk of check_every pairs on stream st.
 cudaError_t launch_chunk(jko_handle* h, cudaStream_t st) {
   if (h->chunk) return cudaGraphLaunch(h->chunk, st);
-  return jko::tc_enqueue_loop(h->tc, h->chunk_iters, st);
+  return enqueue_loop(h, h->chunk_iters, st);
 }
 
 // The FP32 CUDA-core chunk that finishes a stalled tensor-core step: the four
@@ -538,7 +555,7 @@ void free_handle(jko_handle* h) {
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
                   h->fft_khat_x, h->fft_tw_x, h->fft_khat_y, h->fft_tw_y,
                   h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
-                  h->hb.d[3], h->a3, h->b3, h->s3, h->t2, h->t3};
+                  h->hb.d[3], h->hb.coef, h->a3, h->b3, h->s3, h->t2, h->t3};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -1058,6 +1075,11 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
       e = cudaMemset(*pp, 0, bytes64);
       if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMemset(heat scratch)"));
     }
+    const size_t cbytes = sizeof(double) * h->heat.coef.size();
+    e = cudaMalloc(&h->hb.coef, cbytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->hb.coef, h->heat.coef.data(), cbytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_err(h, e, "upload of the heat kernel's coefficients"));
   }
   {
     int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
@@ -1089,6 +1111,15 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaStreamCreate"));
 
   s = h->fp64 ? build_energy<double>(h, energy) : build_energy<float>(h, energy);
+  if (s == JKO_OK && h->heat_L && params->loop != 2) {
+    // the heat kernel: one persistent cooperative kernel per step where the
+    // device allows it (loop 0 or 1), else the kernels per Clenshaw phase (loop 2)
+    h->heat_G = jko::heat_loop_grid(grid->nx, grid->ny, h->fp64, h->ek);
+    if (h->heat_G <= 0 && (params->loop == 1 || params->loop == 3))
+      s = set_err(h, JKO_ERR_UNSUPPORTED,
+                  "the persistent heat-kernel loop cannot run here (no cooperative launch)");
+    h->use_loop = h->heat_G > 0;
+  }
   if (s != JKO_OK) return fail(s);
   if (h->prec == JKO_FP64 || h->prec == JKO_FP32) {
     // the heat kernel needs no Gaussian taps
@@ -1273,16 +1304,16 @@ jko_status jko_profile_loop(jko_handle* h, int pairs, int reps, float* ms, doubl
   c0.tol = -1.0;
   c0.max_iter = 0x7fffffff;
   CK(h, cudaMemcpy(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice));
-  cudaError_t e = jko::tc_enqueue_loop(h->tc, pairs, st);   // warm-up
+  cudaError_t e = enqueue_loop(h, pairs, st);   // warm-up
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, st);
-  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = jko::tc_enqueue_loop(h->tc, pairs, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_loop(h, pairs, st);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
   if (e == cudaSuccess) e = cudaEventSynchronize(h->ev1);
   CK(h, e);
   float t = 0.f;
   CK(h, cudaEventElapsedTime(&t, h->ev0, h->ev1));
   ms[0] = t / reps;
-  if (flops) flops[0] = jko::tc_loop_flops(h->tc, pairs);
+  if (flops) flops[0] = h->tc ? jko::tc_loop_flops(h->tc, pairs) : 0.0;
   CK(h, cudaMemcpy(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
   const int nf = h->poll[0].nonfinite;
   CK(h, cudaMemcpy(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice));

@@ -66,7 +66,8 @@ struct jko_handle {
   double* part = nullptr;      // residual partials of the b-update pass (one per block)
   int nparts_simt = 0;
   int part_cap = 0;       // entries of part (residual and mass partials)
-  int use_loop = 0;       // tensor-core handle runs chunks as one persistent kernel
+  int use_loop = 0;       // chunks run as one persistent kernel (tensor cores or heat kernel)
+  int heat_G = 0;         // blocks of the heat kernel's persistent form
   Ctrl* ctrl_init = nullptr;   // pinned initial value
   Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
   cudaEvent_t ev_poll[2] = {nullptr, nullptr};

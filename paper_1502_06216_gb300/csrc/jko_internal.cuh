@@ -74,6 +74,33 @@ __device__ __forceinline__ bool stall_rule(Ctrl* ctrl, int it, double total, boo
   return since >= n;
 }
 
+// ---- grid-wide barrier of the persistent kernels (tc_loop.cu, heat.cu) ----
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+constexpr unsigned kGridSpinLimit = 1u << 24;   // polls of one barrier before giving up
+
+// Grid-wide barrier number b (1, 2, ... within the step) of the G
+// co-resident blocks, called by one thread per block after the block's
+// writes: one release-add on a 64-bit arrival counter in Ctrl that never
+// resets within a step (barrier b is complete at G b arrivals) and a bounded
+// acquire poll.  `flag`: this block met NaN/Inf or gave up a wait; it is
+// recorded in slot b % 3, final for every block once barrier b is complete.
+// False if the poll gave up.
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned G, unsigned b, bool flag) {
+  if (flag) atomicOr(&ctrl->bar_flag[b % 3], 1u);
+  red_release_add_u64(&ctrl->bar_cnt, 1ull);
+  const unsigned long long target = (unsigned long long)G * b;
+  for (unsigned i = 0; i < kGridSpinLimit; ++i)
+    if (ld_acquire_gpu_u64(&ctrl->bar_cnt) >= target) return true;
+  return false;
+}
+
 // ---- stop protocol of the scaling loop ----
 // The b-update pass writes one residual partial per block (plain stores, one
 // slot each).  The pass that follows it (along x of xi b) reduces the partials

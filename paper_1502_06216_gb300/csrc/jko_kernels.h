@@ -130,6 +130,7 @@ struct HeatPlan {
 };
 struct HeatBuffers {
   void* d[4] = {nullptr, nullptr, nullptr, nullptr};   // Clenshaw iterates (FP64, N each)
+  void* coef = nullptr;                                // c_0 .. c_D (FP64) for the persistent form
 };
 HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bool fp64);
 int heat_blocks(int nx, int ny);   // blocks of heat_bupdate (= residual partials)
@@ -145,6 +146,14 @@ cudaError_t heat_bupdate_launch(const T* Y, T* b, const T* q, int nx, int ny, Ct
 template <typename T>
 cudaError_t heat_prox_launch(int ek, const T* s, T* a, T* p, int nx, int ny, const ProxArgs<T>& P,
                              Ctrl* ctrl, cudaStream_t st);
+// Persistent form: one cooperative launch of G blocks (heat_loop_grid; 0 =
+// unavailable) runs up to `pairs` pairs with the stop rule inside, with the
+// arithmetic and the pair counts of the kernels above.
+int heat_loop_grid(int nx, int ny, bool fp64, int ek);
+template <typename T>
+cudaError_t heat_loop_launch(const HeatPlan& hp, const HeatBuffers& B, int ek, const T* q, T* a,
+                             T* b, T* p, int nx, int ny, const uint8_t* mask, const ProxArgs<T>& P,
+                             Ctrl* ctrl, double* part, int G, int pairs, cudaStream_t st);
 
 // Batched flows: copy the stop state of n control blocks into a contiguous
 // array (done flags only, or whole blocks).

@@ -44,7 +44,6 @@ constexpr int WARP_PROD = 16;
 constexpr int WARP_MMA = 17;
 constexpr int EPI_BAR = 1;                   // named barrier of the epilogue warps
 constexpr uint32_t LOOP_SMEM_BUDGET = 224 * 1024;
-constexpr uint32_t kGridSpinLimit = 1u << 24;
 constexpr uint32_t kGoSpinLimit = 1u << 27;
 
 // Resident-factor mode (BF16, one tile per CTA, the same 1-D factor in every
@@ -115,18 +114,6 @@ struct LoopMaps {
   CUtensorMap O[4][2];
   CUtensorMap Q, E, P;
 };
-
-// Grid-wide barrier number b (1, 2, ... within the step) of the G
-// co-resident CTAs, called by one thread per CTA after the CTA's writes.
-// `flag`: this CTA met NaN/Inf or gave up a wait.  False if the poll gave up.
-__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned G, unsigned b, bool flag) {
-  if (flag) atomicOr(&ctrl->bar_flag[b % 3], 1u);
-  red_release_add_u64(&ctrl->bar_cnt, 1ull);
-  const unsigned long long target = (unsigned long long)G * b;
-  for (uint32_t i = 0; i < kGridSpinLimit; ++i)
-    if (ld_acquire_gpu_u64(&ctrl->bar_cnt) >= target) return true;
-  return false;
-}
 
 // Bounded wait until the epilogue leader has published the barrier of pass q.
 __device__ __forceinline__ bool wait_go(const int* s_go, int q) {

@@ -53,6 +53,34 @@ def test_heat_crowd_flow_matches_oracle(prec, nx, ny, bar):
     assert np.all(traj[-1] <= pb.kappa * (1 + 1e-4))
 
 
+@pytest.mark.parametrize("prec,nx,ny,steps,max_iter", [
+    ("FP32", 64, 64, 3, 300),     # degree 36, 32 tiles
+    ("FP64", 40, 56, 3, 4000),    # degree 28, ragged tiles
+    ("FP32", 50, 50, 3, 300),     # degree 29 (odd: one single Clenshaw step first)
+    ("FP64", 30, 20, 3, 4000),    # degree 17
+    ("FP32", 320, 256, 1, 12),    # degree 152, 640 tiles: blocks take several
+])
+def test_persistent_form_equals_the_kernels_per_phase(prec, nx, ny, steps, max_iter):
+    """The heat kernel's persistent form (one cooperative launch per step,
+    loop = 1) against the kernels per Clenshaw phase (loop = 2): the same
+    arithmetic per cell and the same stop rule, so the same bits and the same
+    pair counts."""
+    from paper_1502_06216_gb300 import jko
+    tol = 1e-11 if prec == "FP64" else 1e-6
+    pb = inputs.heat_crowd_problem(nx, ny=ny, n_steps=steps, tol=tol, max_iter=max_iter)
+    t_ref, i_ref = gpu_flow(pb, prec, steps, loop=2)
+    t_loop, i_loop = gpu_flow(pb, prec, steps, loop=1)
+    print(prec, nx, ny, "pairs", [i["iters"] for i in i_ref], [i["iters"] for i in i_loop])
+    assert [i["iters"] for i in i_ref] == [i["iters"] for i in i_loop]
+    assert [int(i["status"]) for i in i_ref] == [int(i["status"]) for i in i_loop]
+    assert np.array_equal(t_ref, t_loop)
+    need_gpu()
+    for loop, want in ((2, False), (1, True), (0, True)):
+        h = jko.create_from_problem(pb, precision=jko.Precision[prec], loop=loop)
+        assert jko.jko_handle_info(h)["loop"] is want
+        jko.jko_destroy(h)
+
+
 def test_first_pair_applies_the_heat_kernel():
     """One pair from a = 1: xi~ 1 = 1 on the domain, so b = q and the prox
     returns p = e^{-sigma w} xi~ q where the bound is inactive: p / e^{-sigma w}
