@@ -24,7 +24,7 @@ constexpr int NT = 256;
 template <typename T, int EK>
 __global__ void __launch_bounds__(NT) attraction_prox_kernel(const T* s1, const T* s2, T* a1, T* a2,
                                                              T* p, long long n, T tau,
-                                                             ProxArgs<T> P, Ctrl* ctrl) {
+                                                             ProxArgs<T> P, Ctrl* ctrl, int rnd) {
   __shared__ int s_it;
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
   const T w1 = T(1) / (T(1) + tau), w2 = tau / (T(1) + tau);
@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(NT) attraction_prox_kernel(const T* s1, const 
     const T r1 = x1 > T(0) ? pm / x1 : T(0);
     const T r2 = x2 > T(0) ? pm / x2 : T(0);
     bad |= !dev_finite(r1) || !dev_finite(r2) || !dev_finite(pm);
-    a1[i] = r1;
-    a2[i] = r2;
+    a1[i] = op_round<T>(r1, rnd);
+    a2[i] = op_round<T>(r2, rnd);
     p[i] = pm;
   }
   bad = warp_or(bad);
@@ -58,7 +58,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) species_prox_kernel(const T* s1, const T* s2, const T* E1,
                                                           const T* E2, T* a1, T* a2, T* p,
                                                           long long n, T kappa, int has_kappa,
-                                                          Ctrl* ctrl) {
+                                                          Ctrl* ctrl, int rnd) {
   __shared__ int s_it;
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
   int bad = 0;
@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(NT) species_prox_kernel(const T* s1, const T* 
     const T t1 = s1[i] * e1, t2 = s2[i] * e2;
     const T t = t1 + t2;
     const T f = (has_kappa && t > kappa) ? kappa / t : T(1);
-    a1[i] = e1 * f;
-    a2[i] = e2 * f;
+    a1[i] = op_round<T>(e1 * f, rnd);
+    a2[i] = op_round<T>(e2 * f, rnd);
     p[i] = t1 * f;
     p[n + i] = t2 * f;
     bad |= !dev_finite(t1 * f) || !dev_finite(t2 * f);
@@ -104,7 +104,7 @@ template <typename T>
 __global__ void __launch_bounds__(NT) pairwise_rows_kernel(const T* s1, const T* s2, const T* s3,
                                                            const T* E1, const T* q2, T* a1, T* a2,
                                                            T* a3, T* p1, long long n, T t, T kappa,
-                                                           int has_kappa, Ctrl* ctrl) {
+                                                           int has_kappa, Ctrl* ctrl, int rnd) {
   __shared__ int s_it;
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
   int bad = 0;
@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(NT) pairwise_rows_kernel(const T* s1, const T*
     const T r1 = safe_ratio<T>(pm, x1), r3 = safe_ratio<T>(pm, x3);
     const T r2 = b_update<T>(q2[i], s2[i]);
     bad |= !dev_finite(r1) || !dev_finite(r2) || !dev_finite(r3) || !dev_finite(pm);
-    a1[i] = r1;
-    a2[i] = r2;
-    a3[i] = r3;
+    a1[i] = op_round<T>(r1, rnd);
+    a2[i] = op_round<T>(r2, rnd);
+    a3[i] = op_round<T>(r3, rnd);
     p1[i] = pm;
   }
   bad = warp_or(bad);
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NT) pairwise_cols_kernel(const T* y1, const T*
                                                            const T* E2, const T* q1, T* b1, T* b2,
                                                            T* b3, T* p2, double* part, long long n,
                                                            T t, T kappa, int has_kappa,
-                                                           Ctrl* ctrl) {
+                                                           Ctrl* ctrl, int rnd) {
   __shared__ int s_it;
   __shared__ double s_red[33];
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(NT) pairwise_cols_kernel(const T* y1, const T*
     const T r1 = b_update<T>(qq, v1);
     const T r2 = safe_ratio<T>(pm, v2), r3 = safe_ratio<T>(pm, v3);
     bad |= !dev_finite(r1) || !dev_finite(r2) || !dev_finite(r3);
-    b1[i] = r1;
-    b2[i] = r2;
-    b3[i] = r3;
+    b1[i] = op_round<T>(r1, rnd);
+    b2[i] = op_round<T>(r2, rnd);
+    b3[i] = op_round<T>(r3, rnd);
   }
   const double tot = block_sum(res, s_red);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
@@ -175,28 +175,29 @@ int pairwise_blocks(long long n) {
 template <typename T>
 cudaError_t launch_pairwise_rows(const T* s1, const T* s2, const T* s3, const T* E1, const T* q2,
                                  T* a1, T* a2, T* a3, T* p1, long long n, double t, double kappa,
-                                 int has_kappa, Ctrl* ctrl, cudaStream_t st) {
+                                 int has_kappa, Ctrl* ctrl, cudaStream_t st, int rnd) {
   pairwise_rows_kernel<T><<<pairwise_blocks(n), NT, 0, st>>>(
-      s1, s2, s3, E1, q2, a1, a2, a3, p1, n, (T)t, (T)kappa, has_kappa, ctrl);
+      s1, s2, s3, E1, q2, a1, a2, a3, p1, n, (T)t, (T)kappa, has_kappa, ctrl, rnd);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_pairwise_cols(const T* y1, const T* y2, const T* y3, const T* E2, const T* q1,
                                  T* b1, T* b2, T* b3, T* p2, double* part, long long n, double t,
-                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st) {
+                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st,
+                                 int rnd) {
   pairwise_cols_kernel<T><<<pairwise_blocks(n), NT, 0, st>>>(
-      y1, y2, y3, E2, q1, b1, b2, b3, p2, part, n, (T)t, (T)kappa, has_kappa, ctrl);
+      y1, y2, y3, E2, q1, b1, b2, b3, p2, part, n, (T)t, (T)kappa, has_kappa, ctrl, rnd);
   return cudaGetLastError();
 }
 
 #define JKO_PW_INST(T)                                                                        \
   template cudaError_t launch_pairwise_rows<T>(const T*, const T*, const T*, const T*,       \
                                                const T*, T*, T*, T*, T*, long long, double,   \
-                                               double, int, Ctrl*, cudaStream_t);             \
+                                               double, int, Ctrl*, cudaStream_t, int);        \
   template cudaError_t launch_pairwise_cols<T>(const T*, const T*, const T*, const T*,       \
                                                const T*, T*, T*, T*, T*, double*, long long,  \
-                                               double, double, int, Ctrl*, cudaStream_t);
+                                               double, double, int, Ctrl*, cudaStream_t, int);
 JKO_PW_INST(float)
 JKO_PW_INST(double)
 #undef JKO_PW_INST
@@ -204,44 +205,44 @@ JKO_PW_INST(double)
 template <typename T>
 cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,
                                 T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
-                                cudaStream_t st) {
+                                cudaStream_t st, int rnd) {
   long long g = (n + NT - 1) / NT;
   if (g > 152 * 8) g = 152 * 8;
   if (g < 1) g = 1;
   species_prox_kernel<T><<<(int)g, NT, 0, st>>>(s1, s2, E1, E2, a1, a2, p, n, (T)kappa,
-                                                has_kappa, ctrl);
+                                                has_kappa, ctrl, rnd);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_species_prox<float>(const float*, const float*, const float*,
                                                const float*, float*, float*, float*, long long,
-                                               double, int, Ctrl*, cudaStream_t);
+                                               double, int, Ctrl*, cudaStream_t, int);
 template cudaError_t launch_species_prox<double>(const double*, const double*, const double*,
                                                 const double*, double*, double*, double*,
-                                                long long, double, int, Ctrl*, cudaStream_t);
+                                                long long, double, int, Ctrl*, cudaStream_t, int);
 
 template <typename T>
 cudaError_t launch_attraction_prox(int ek, const T* s1, const T* s2, T* a1, T* a2, T* p,
                                    long long n, double tau, const ProxArgs<T>& P, Ctrl* ctrl,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int rnd) {
   long long g = (n + NT - 1) / NT;
   if (g > 152 * 8) g = 152 * 8;
   if (g < 1) g = 1;
   const int grid = (int)g;
   if (ek == EK_CROWD)
-    attraction_prox_kernel<T, EK_CROWD><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl);
+    attraction_prox_kernel<T, EK_CROWD><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl, rnd);
   else if (ek == EK_ENTROPY)
-    attraction_prox_kernel<T, EK_ENTROPY><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl);
+    attraction_prox_kernel<T, EK_ENTROPY><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl, rnd);
   else
-    attraction_prox_kernel<T, EK_POWER><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl);
+    attraction_prox_kernel<T, EK_POWER><<<grid, NT, 0, st>>>(s1, s2, a1, a2, p, n, (T)tau, P, ctrl, rnd);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_attraction_prox<float>(int, const float*, const float*, float*, float*,
                                                    float*, long long, double,
-                                                   const ProxArgs<float>&, Ctrl*, cudaStream_t);
+                                                   const ProxArgs<float>&, Ctrl*, cudaStream_t, int);
 template cudaError_t launch_attraction_prox<double>(int, const double*, const double*, double*,
                                                     double*, double*, long long, double,
-                                                    const ProxArgs<double>&, Ctrl*, cudaStream_t);
+                                                    const ProxArgs<double>&, Ctrl*, cudaStream_t, int);
 
 }  // namespace jko

@@ -315,6 +315,98 @@ cudaError_t begin_pairwise(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
+// ---- the steps with several couplings on the TF32 tensor cores (tc_multi.cu) ----
+// The same iterations as above with each filter pair replaced by the
+// tensor-core passes over x then y (xi is separable and symmetric, so the
+// order changes the rounding only) and the scalings that feed them rounded to
+// tf32 by the joint prox kernels.  xi b_m goes to the prox as fp32.
+
+// xi applied to nz images: in -> out, through the intermediates ts; the
+// second pass's epilogue `epi` (EPI_B against q, or TC_EPI_RAW); the first
+// pass takes the stop decision on `nparts` partials when decide = 1.
+cudaError_t tc_xi_multi(jko_handle* h, int nz, void* const* in, void* const* out, int epi,
+                        const void* const* q, int decide, int nparts, cudaStream_t st) {
+  void* ts[3] = {h->t1, h->t2, h->t3};
+  cudaError_t e = jko::tc_multi_pass(h->tc, 0, nz, (const float* const*)in, (float* const*)ts,
+                                     jko::EPI_STORE, nullptr, h->part, nparts, decide, st);
+  if (e != cudaSuccess) return e;
+  return jko::tc_multi_pass(h->tc, 1, nz, (const float* const*)ts, (float* const*)out, epi,
+                            (const float* const*)q, h->part, 0, 0, st);
+}
+
+cudaError_t enqueue_pair_attraction_tc(jko_handle* h, cudaStream_t st) {
+  const int nb = jko::tc_multi_tiles(h->grid.nx, h->grid.ny, 1);
+  void* as[2] = {h->a, h->a2};
+  void* bs[2] = {h->b, h->b2};
+  void* ss[2] = {h->s1, h->s2};
+  const void* qs[2] = {h->q, h->tgt};
+  cudaError_t e = tc_xi_multi(h, 2, as, bs, jko::EPI_B, qs, 0, 0, st);
+  if (e == cudaSuccess) e = tc_xi_multi(h, 2, bs, ss, jko::TC_EPI_RAW, nullptr, 1, 2 * nb, st);
+  if (e != cudaSuccess) return e;
+  return jko::launch_attraction_prox<float>(h->ek, (const float*)h->s1, (const float*)h->s2,
+                                            (float*)h->a, (float*)h->a2, (float*)h->p, h->N,
+                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, 1);
+}
+
+cudaError_t enqueue_pair_species_tc(jko_handle* h, cudaStream_t st) {
+  const int nb = jko::tc_multi_tiles(h->grid.nx, h->grid.ny, 1);
+  void* as[2] = {h->a, h->a2};
+  void* bs[2] = {h->b, h->b2};
+  void* ss[2] = {h->s1, h->s2};
+  const void* qs[2] = {h->q, (const float*)h->q + h->N};
+  cudaError_t e = tc_xi_multi(h, 2, as, bs, jko::EPI_B, qs, 0, 0, st);
+  if (e == cudaSuccess) e = tc_xi_multi(h, 2, bs, ss, jko::TC_EPI_RAW, nullptr, 1, 2 * nb, st);
+  if (e != cudaSuccess) return e;
+  return jko::launch_species_prox<float>((const float*)h->s1, (const float*)h->s2,
+                                         (const float*)h->E, (const float*)h->E2, (float*)h->a,
+                                         (float*)h->a2, (float*)h->p, h->N, h->kappa_s,
+                                         h->has_kappa, h->ctrl, st, 1);
+}
+
+cudaError_t enqueue_pair_pairwise_tc(jko_handle* h, cudaStream_t st) {
+  const long long N = h->N;
+  const float* q1 = (const float*)h->q;
+  float* p1 = (float*)h->p;
+  const double t = h->prm.tau * h->pair_alpha;
+  void* bs[3] = {h->b, h->b2, h->b3};
+  void* as[3] = {h->a, h->a2, h->a3};
+  void* ss[3] = {h->s1, h->s2, h->s3};
+  cudaError_t e = tc_xi_multi(h, 3, bs, ss, jko::TC_EPI_RAW, nullptr, 1, h->nparts_pw, st);
+  if (e == cudaSuccess)
+    e = jko::launch_pairwise_rows<float>((const float*)h->s1, (const float*)h->s2,
+                                         (const float*)h->s3, (const float*)h->E, q1 + N,
+                                         (float*)h->a, (float*)h->a2, (float*)h->a3, p1, N, t,
+                                         h->kappa_s, h->has_kappa, h->ctrl, st, 1);
+  if (e == cudaSuccess) e = tc_xi_multi(h, 3, as, ss, jko::TC_EPI_RAW, nullptr, 0, 0, st);
+  if (e != cudaSuccess) return e;
+  return jko::launch_pairwise_cols<float>((const float*)h->s1, (const float*)h->s2,
+                                          (const float*)h->s3, (const float*)h->E2, q1,
+                                          (float*)h->b, (float*)h->b2, (float*)h->b3, p1 + N,
+                                          h->part, N, t, h->kappa_s, h->has_kappa, h->ctrl, st, 1);
+}
+
+// Start of an attraction or two-species step on the tensor cores: b_m = 1,
+// s_1 = s_2 = xi 1, then the first joint prox.
+cudaError_t begin_multi_tc(jko_handle* h, cudaStream_t st) {
+  const long long N = h->N;
+  cudaError_t e = jko::launch_fill<float>((float*)h->b, 1.0f, N, st);
+  if (e == cudaSuccess) e = jko::launch_fill<float>((float*)h->b2, 1.0f, N, st);
+  void* bs[1] = {h->b};
+  void* ss[1] = {h->s1};
+  if (e == cudaSuccess) e = tc_xi_multi(h, 1, bs, ss, jko::TC_EPI_RAW, nullptr, 0, 0, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->s2, h->s1, sizeof(float) * (size_t)N, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  if (h->species == 2)
+    return jko::launch_species_prox<float>((const float*)h->s1, (const float*)h->s2,
+                                           (const float*)h->E, (const float*)h->E2, (float*)h->a,
+                                           (float*)h->a2, (float*)h->p, N, h->kappa_s,
+                                           h->has_kappa, h->ctrl, st, 1);
+  return jko::launch_attraction_prox<float>(h->ek, (const float*)h->s1, (const float*)h->s2,
+                                            (float*)h->a, (float*)h->a2, (float*)h->p, N,
+                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, 1);
+}
+
 // One iteration with the heat-kernel Gibbs kernel (Sec. 4.1, heat.cu):
 // Y = xi~ a, b = q / Y with the residual partials, s = xi~ b (its first kernel
 // takes the stop decision), then a = Prox(s) / s.  xi~ is symmetric, so the
@@ -352,6 +444,10 @@ cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
 cudaError_t enqueue_pair(jko_handle* h, cudaStream_t st) {
   if (h->heat_L)
     return h->fp64 ? enqueue_pair_heat<double>(h, st) : enqueue_pair_heat<float>(h, st);
+  if (h->tc_multi) {
+    if (h->pair_alpha > 0) return enqueue_pair_pairwise_tc(h, st);
+    return h->species == 2 ? enqueue_pair_species_tc(h, st) : enqueue_pair_attraction_tc(h, st);
+  }
   if (h->pair_alpha > 0)
     return h->fp64 ? enqueue_pair_pairwise<double>(h, st) : enqueue_pair_pairwise<float>(h, st);
   if (h->species == 2)
@@ -622,9 +718,23 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
   if (!(en->kappa > 0)) return (*msg = "kappa must be > 0 (INFINITY = none)", JKO_ERR_INVALID_ARG);
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return (*msg = "m must be 0 or >= 1", JKO_ERR_INVALID_ARG);
+  if (en->target || en->species == 2) {
+    // several couplings: the CUDA-core forms, or the TF32 tensor-core passes
+    // (tc_multi.cu) on grids whose rows are whole 16-byte units
+    if (p->precision != JKO_FP32 && p->precision != JKO_FP64 && p->precision != JKO_TF32)
+      return (*msg = "the steps with several couplings run on JKO_FP32 / JKO_FP64 / JKO_TF32",
+              JKO_ERR_UNSUPPORTED);
+    if (p->precision == JKO_TF32) {
+      if (g->nx % 4 != 0 || g->ny % 4 != 0)
+        return (*msg = "several couplings on JKO_TF32 need nx and ny multiples of 4",
+                JKO_ERR_UNSUPPORTED);
+      if (p->absorb == 1 || p->absorb == 3 || p->loop == 1 || p->loop == 3 || p->finish ||
+          (p->tile != 0 && p->tile != 64))
+        return (*msg = "several couplings on JKO_TF32 run their own passes: absorb 0 or 2, loop 0 "
+                       "or 2, tile 0 or 64, no finish", JKO_ERR_UNSUPPORTED);
+    }
+  }
   if (en->target) {
-    if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
-      return (*msg = "the Wasserstein attraction runs on JKO_FP32 / JKO_FP64 only", JKO_ERR_UNSUPPORTED);
     double tot = 0.0;
     for (long long i = 0; i < (long long)g->nx * g->ny; ++i) {
       const double v = en->target[i];
@@ -677,8 +787,6 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
   if (en->species < 0 || en->species > 2)
     return (*msg = "species must be 0, 1 or 2", JKO_ERR_INVALID_ARG);
   if (en->species == 2) {
-    if (p->precision != JKO_FP32 && p->precision != JKO_FP64)
-      return (*msg = "two species run on JKO_FP32 / JKO_FP64 only", JKO_ERR_UNSUPPORTED);
     if (en->m != 0.0 || en->m_field || en->binary || en->target || en->kappa_field || en->mask)
       return (*msg = "two species take a scalar congestion bound and potentials only", JKO_ERR_UNSUPPORTED);
     if (en->w2)
@@ -820,7 +928,10 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   CK(h, cudaEventRecord(h->ev0, st));
   if ((const void*)q_in != h->q)
     CK(h, cudaMemcpyAsync(h->q, q_in, h->ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  if (h->tc) {
+  if (h->tc_multi) {
+    if (h->pair_alpha > 0) CK(h, begin_pairwise<float>(h, st));
+    else CK(h, begin_multi_tc(h, st));
+  } else if (h->tc) {
     jko_status s2 = jko::tc_begin_step(h->tc, st) == cudaSuccess ? JKO_OK : JKO_ERR_CUDA;
     if (s2 != JKO_OK) return set_err(h, s2, "tensor-core step set-up failed");
   } else if (h->pair_alpha > 0) {
@@ -1085,6 +1196,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     int np = std::max((h->attract || h->species == 2 ? 2 : 1) * h->nparts_simt,
                       jko::tc_partials(grid->nx, grid->ny));
     if (h->heat_L) np = std::max(np, jko::heat_blocks(grid->nx, grid->ny));
+    if (h->attract || h->species == 2)   // the tensor-core passes' b-update partials
+      np = std::max(np, 3 * jko::tc_multi_tiles(grid->nx, grid->ny, 1));
     if (h->pair_alpha > 0) np = std::max(np, h->nparts_pw);
     e = cudaMalloc((void**)&h->part, sizeof(double) * np);
     h->part_cap = np;
@@ -1139,7 +1252,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     cfg.w_host = energy->w;
     cfg.sigma = params->tau / params->gamma;
     cfg.absorb = 0;
-    if (energy->w && params->absorb != 2 && params->absorb != 3) {
+    const bool multi = h->attract || h->species == 2;   // several couplings: tc_multi.cu
+    if (energy->w && params->absorb != 2 && params->absorb != 3 && !multi) {
       double lo = INFINITY, hi = -INFINITY;
       for (int i = 0; i < h->N; ++i) { lo = std::min(lo, energy->w[i]); hi = std::max(hi, energy->w[i]); }
       cfg.absorb = params->absorb == 1 || cfg.sigma * (hi - lo) > 120.0 ? 1 : 0;
@@ -1148,7 +1262,10 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     int rc = jko::tc_create(cfg, &h->tc, &msg);
     if (rc == 1) s = set_err(h, JKO_ERR_UNSUPPORTED, msg);
     else if (rc != 0) s = set_err(h, JKO_ERR_CUDA, msg);
-    if (s == JKO_OK) {
+    if (s == JKO_OK && multi) {
+      h->tc_multi = 1;
+      h->use_loop = 0;
+    } else if (s == JKO_OK) {
       const int ok = jko::tc_loop_supported(h->tc);
       if ((params->loop == 1 || params->loop == 3) && !ok)
         s = set_err(h, JKO_ERR_UNSUPPORTED,
@@ -1174,7 +1291,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
         s = setup_simt<float>(h);
     }
   }
-  if (s == JKO_OK && h->tc && !jko::tc_logdomain(h->tc) && params->loop == 0 && params->tile == 0 &&
+  if (s == JKO_OK && h->tc && !h->tc_multi && !jko::tc_logdomain(h->tc) && params->loop == 0 &&
+      params->tile == 0 &&
       (long long)grid->nx * grid->ny >= 256LL * 256LL) {
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(cuda_err(h, e, "set-up"));
@@ -1251,6 +1369,9 @@ jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops)
   if (reps < 1 || !ms) return set_err(h, JKO_ERR_INVALID_ARG, "reps < 1 or NULL ms");
   if (h->heat_L)
     return set_err(h, JKO_ERR_UNSUPPORTED, "a heat-kernel handle has no separable passes to time");
+  if (h->attract || h->species == 2)
+    return set_err(h, JKO_ERR_UNSUPPORTED,
+                   "the passes of a handle with several couplings are timed through its steps");
   DeviceGuard dg(h->device);
   cudaStream_t st = h->stream;
   // A running control block that never stops: it = 1 (residuals computed),

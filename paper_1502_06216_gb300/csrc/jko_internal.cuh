@@ -74,6 +74,18 @@ __device__ __forceinline__ bool stall_rule(Ctrl* ctrl, int it, double total, boo
   return since >= n;
 }
 
+// A scaling stored as the operand of the TF32 tensor-core passes (rnd = 1):
+// rounded to tf32 (nearest, ties away), as the tensor-core epilogues store it.
+template <typename T>
+__device__ __forceinline__ T op_round(T x, int) { return x; }
+template <>
+__device__ __forceinline__ float op_round<float>(float x, int rnd) {
+  if (!rnd) return x;
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---- grid-wide barrier of the persistent kernels (tc_loop.cu, heat.cu) ----
 __device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
   unsigned long long v;

@@ -95,15 +95,17 @@ cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, c
 template <typename T>
 cudaError_t launch_attraction_prox(int ek, const T* s1, const T* s2, T* a1, T* a2, T* p,
                                    long long n, double tau, const ProxArgs<T>& P, Ctrl* ctrl,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int rnd = 0);
 
 // Two species (attraction.cu): p = [p_1, p_2] = a~_m min(1, kappa/(a~_1 + a~_2)),
 // a~_m = s_m E_m (E_m = e^{-sigma w_m}, NULL = 1); a_m = E_m min(...).
 template <typename T>
 cudaError_t launch_species_prox(const T* s1, const T* s2, const T* E1, const T* E2, T* a1, T* a2,
                                 T* p, long long n, double kappa, int has_kappa, Ctrl* ctrl,
-                                cudaStream_t st);
+                                cudaStream_t st, int rnd = 0);
 
+// (rnd = 1: the scalings a_m, b_m written by these kernels are rounded to tf32,
+// the operands of the tensor-core passes of tc_multi.cu.)
 // Pairwise attraction of two densities (attraction.cu; Sec. 5.3, 3 couplings):
 // the row half-step (psi_1) and the column half-step (psi_2, with the residual
 // partials of the stop rule, p_2 and the pair counter).  E1, E2 = e^{-sigma' w_m}
@@ -112,11 +114,12 @@ int pairwise_blocks(long long n);
 template <typename T>
 cudaError_t launch_pairwise_rows(const T* s1, const T* s2, const T* s3, const T* E1, const T* q2,
                                  T* a1, T* a2, T* a3, T* p1, long long n, double t, double kappa,
-                                 int has_kappa, Ctrl* ctrl, cudaStream_t st);
+                                 int has_kappa, Ctrl* ctrl, cudaStream_t st, int rnd = 0);
 template <typename T>
 cudaError_t launch_pairwise_cols(const T* y1, const T* y2, const T* y3, const T* E2, const T* q1,
                                  T* b1, T* b2, T* b3, T* p2, double* part, long long n, double t,
-                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st);
+                                 double kappa, int has_kappa, Ctrl* ctrl, cudaStream_t st,
+                                 int rnd = 0);
 
 // Heat-kernel Gibbs kernel (heat.cu): xi~ = (Id - (gamma/L) Delta_M)^{-L} as
 // the Chebyshev expansion of lambda^{-L} on the spectrum interval [1, lmax].

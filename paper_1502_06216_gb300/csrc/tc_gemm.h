@@ -46,6 +46,17 @@ int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);
 // 0 = ok, 1 = unsupported (message set), 2 = CUDA error.
 int tc_log_setup(TcPlan* plan, const double* w_host, double sigma, std::string* msg);
 int tc_logdomain(const TcPlan* plan);
+// Passes of the steps with several couplings on a TF32 plan (tc_multi.cu): one
+// launch applies the pass over `axis` (0: x, in [ny][nx] -> out [nx][ny]; 1: y,
+// in [nx][ny] -> out [ny][nx]) to nz <= 3 fp32 images (nx, ny multiples of 4).
+// epi: EPI_STORE (out rounded to tf32), EPI_B (b = q / D rounded, residual
+// partials of image z at part + z * tiles), TC_EPI_RAW (out as fp32).  The
+// pass takes the stop decision on `nparts` partials when decide = 1.
+constexpr int TC_EPI_RAW = 3;
+int tc_multi_tiles(int nx, int ny, int axis);
+cudaError_t tc_multi_pass(TcPlan* plan, int axis, int nz, const float* const* in, float* const* out,
+                          int epi, const float* const* q, double* part, int nparts, int decide,
+                          cudaStream_t st);
 // Per-step reset of the scaling operands (a = 1).
 cudaError_t tc_begin_step(TcPlan* plan, cudaStream_t st);
 // The current scalings a, b as fp32 [ny][nx] images (the operand values the

@@ -31,7 +31,9 @@ def gpu_flow(pb, prec, n_steps, **kw):
 # at gamma = 8e-3, within FP32; at 2e-3 it underflows (next test).
 @pytest.mark.parametrize("prec,nx,ny,alpha,gamma,bar", [("FP64", 32, 32, 1.0, 2e-3, 1e-11),
                                                         ("FP64", 40, 48, 2.0, 2e-3, 1e-11),
-                                                        ("FP32", 64, 64, 1.0, 8e-3, 1e-5)])
+                                                        ("FP32", 64, 64, 1.0, 8e-3, 1e-5),
+                                                        ("TF32", 64, 64, 1.0, 8e-3, 1e-3),
+                                                        ("TF32", 40, 48, 2.0, 8e-3, 1e-3)])
 def test_pairwise_flow_matches_oracle(prec, nx, ny, alpha, gamma, bar):
     tol = 1e-11 if prec == "FP64" else 1e-6
     pb = inputs.pairwise_attraction_problem(nx, ny=ny, alpha=alpha, gamma=gamma, n_steps=3,
@@ -42,7 +44,9 @@ def test_pairwise_flow_matches_oracle(prec, nx, ny, alpha, gamma, bar):
     iters = [i["iters"] for i in infos]
     print(prec, nx, ny, "rel L1", " ".join(f"{e:.2e}" for e in errs), "iters", iters, iters_o)
     assert max(errs) <= bar
-    assert all(i["status"] == 0 for i in infos)
+    # the TF32 passes may stop at their rounding floor above tol (the budget)
+    ok = (0, 5) if prec == "TF32" else (0,)
+    assert all(i["status"] in ok for i in infos)
     if prec == "FP64":
         assert iters == iters_o
     N = pb.N
