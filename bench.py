@@ -448,21 +448,16 @@ def run_binary(args, jko, dev, barrier, peak_bf16, steps=5):
     return out
 
 
-def run_attraction(args, jko, dev, barrier, steps=5):
-    """Wasserstein attraction with congestion (Sec. 5.2, 2 couplings per step):
-    256^2, disk q0 toward a disk target r, kappa = max q0, gamma = 5e-3, tau =
-    0.3, <= 2000 pairs, tol 1e-6, on the FP32 CUDA-core form.  Pairs/s of one
-    `steps`-step flow after a 1-step warm-up, the roofline of its slowest
-    filter pass, and the last step against the FP64 form."""
+def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
+    """Pairs/s of one `steps`-step flow after a 1-step warm-up on the FP32 and
+    FP64 CUDA-core forms and the TF32 tensor-core passes (stall rule W = 4:
+    its rounding floor lies above tol), and the last step of FP32 and TF32
+    against the FP64 form."""
     import torch
-    from paper_1502_06216_gb300 import inputs
-    pb = inputs.attraction_problem(256, gamma=5e-3, tau=0.3, n_steps=steps, tol=1e-6,
-                                   max_iter=2000)
-    out = {"workload": f"Wasserstein attraction with congestion, {pb.nx}x{pb.ny}, gamma={pb.gamma}, "
-                       f"tau={pb.tau}, kappa=max q0, <={pb.max_iter} pairs/step, tol {pb.tol}"}
-    finals = {}
-    for form in ("FP32", "FP64"):
-        h = jko.create_from_problem(pb, precision=jko.Precision[form])
+    out, finals = {}, {}
+    for form in ("FP32", "FP64", "TF32"):
+        kw = {"stall": 4} if form == "TF32" else {}
+        h = jko.create_from_problem(pb, precision=jko.Precision[form], **kw)
         p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
         jko.jko_flow(h, p0, 1)
         barrier()
@@ -475,12 +470,29 @@ def run_attraction(args, jko, dev, barrier, steps=5):
         iters = sum(i["iters"] for i in infos)
         finals[form] = pf.double()
         out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
-                     "pairs_per_step": iters / steps, "kernels_per_pair": 5}
-        if form == "FP32":
+                     "pairs_per_step": iters / steps, "kernels_per_pair": kernels_per_pair}
+        if form == "FP32" and roofline:
             out[form]["roofline"] = form_roofline(jko, h, form, None)
         jko.jko_destroy(h)
-    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
-                                               finals["FP64"].abs().sum())
+    for form in ("FP32", "TF32"):
+        out[form]["rel_l1_vs_fp64_form"] = float((finals[form] - finals["FP64"]).abs().sum() /
+                                                 finals["FP64"].abs().sum())
+    out["TF32"]["note"] = ("Gibbs-kernel passes of all couplings on the tensor cores (one "
+                           "launch per pass), joint prox on the CUDA cores")
+    return out
+
+
+def run_attraction(args, jko, dev, barrier, steps=5):
+    """Wasserstein attraction with congestion (Sec. 5.2, 2 couplings per step):
+    256^2, disk q0 toward a disk target r, kappa = max q0, gamma = 5e-3, tau =
+    0.3, <= 2000 pairs, tol 1e-6 (coupled_leg; the roofline of the FP32 form's
+    slowest filter pass)."""
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.attraction_problem(256, gamma=5e-3, tau=0.3, n_steps=steps, tol=1e-6,
+                                   max_iter=2000)
+    out = {"workload": f"Wasserstein attraction with congestion, {pb.nx}x{pb.ny}, gamma={pb.gamma}, "
+                       f"tau={pb.tau}, kappa=max q0, <={pb.max_iter} pairs/step, tol {pb.tol}"}
+    out.update(coupled_leg(jko, dev, barrier, pb, steps, 5, roofline=True))
     return out
 
 
@@ -488,33 +500,13 @@ def run_species(args, jko, dev, barrier, steps=5):
     """Two crowds coupled through the congestion of their sum (Sec. 5.3,
     summation couplings, 2 couplings per step): 256^2, two rectangles heading
     for each other, kappa = max(q_1 + q_2), gamma = 2e-3, tau = 0.05, <= 2000
-    pairs, tol 1e-6, CUDA-core forms.  Pairs/s of one `steps`-step flow after a
-    1-step warm-up, and the last step of FP32 against FP64."""
-    import torch
+    pairs, tol 1e-6 (coupled_leg)."""
     from paper_1502_06216_gb300 import inputs
     pb = inputs.two_species_problem(256, gamma=2e-3, tau=0.05, n_steps=steps, tol=1e-6,
                                     max_iter=2000)
     out = {"workload": f"two species, congestion on the sum, {pb.nx}x{pb.ny}, gamma={pb.gamma}, "
                        f"tau={pb.tau}, kappa=max(q1+q2), <={pb.max_iter} pairs/step, tol {pb.tol}"}
-    finals = {}
-    for form in ("FP32", "FP64"):
-        h = jko.create_from_problem(pb, precision=jko.Precision[form])
-        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
-        jko.jko_flow(h, p0, 1)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        pf, _, infos = jko.jko_flow(h, p0, steps)
-        e1.record()
-        barrier()
-        secs = e0.elapsed_time(e1) / 1e3
-        iters = sum(i["iters"] for i in infos)
-        finals[form] = pf.double()
-        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
-                     "pairs_per_step": iters / steps, "kernels_per_pair": 5}
-        jko.jko_destroy(h)
-    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
-                                               finals["FP64"].abs().sum())
+    out.update(coupled_leg(jko, dev, barrier, pb, steps, 5))
     return out
 
 
@@ -523,34 +515,14 @@ def run_pairwise(args, jko, dev, barrier, steps=4):
     (Sec. 5.3, 3 couplings per step): 256^2, two disks drawn into themselves
     and toward each other, alpha = 1, kappa = max q_1, gamma = 8e-3 (the kernel
     between the densities stays in FP32 range), tau = 0.05, <= 2000 pairs, tol
-    1e-6, CUDA-core forms.  Pairs/s of one `steps`-step flow
-    after a 1-step warm-up, and the last step of FP32 against FP64."""
-    import torch
+    1e-6 (coupled_leg)."""
     from paper_1502_06216_gb300 import inputs
     pb = inputs.pairwise_attraction_problem(256, gamma=8e-3, n_steps=steps, tol=1e-6,
                                             max_iter=2000)
     out = {"workload": f"pairwise attraction of two densities, {pb.nx}x{pb.ny}, alpha="
                        f"{pb.pair_alpha}, gamma={pb.gamma}, tau={pb.tau}, kappa=max q1, "
                        f"<={pb.max_iter} pairs/step, tol {pb.tol}"}
-    finals = {}
-    for form in ("FP32", "FP64"):
-        h = jko.create_from_problem(pb, precision=jko.Precision[form])
-        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
-        jko.jko_flow(h, p0, 1)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        pf, _, infos = jko.jko_flow(h, p0, steps)
-        e1.record()
-        barrier()
-        secs = e0.elapsed_time(e1) / 1e3
-        iters = sum(i["iters"] for i in infos)
-        finals[form] = pf.double()
-        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
-                     "pairs_per_step": iters / steps, "kernels_per_pair": 6}
-        jko.jko_destroy(h)
-    out["FP32"]["rel_l1_vs_fp64_form"] = float((finals["FP32"] - finals["FP64"]).abs().sum() /
-                                               finals["FP64"].abs().sum())
+    out.update(coupled_leg(jko, dev, barrier, pb, steps, 6))
     return out
 
 

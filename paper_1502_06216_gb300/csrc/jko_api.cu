@@ -1369,9 +1369,9 @@ jko_status jko_profile_passes(jko_handle* h, int reps, float* ms, double* flops)
   if (reps < 1 || !ms) return set_err(h, JKO_ERR_INVALID_ARG, "reps < 1 or NULL ms");
   if (h->heat_L)
     return set_err(h, JKO_ERR_UNSUPPORTED, "a heat-kernel handle has no separable passes to time");
-  if (h->attract || h->species == 2)
+  if (h->tc_multi)
     return set_err(h, JKO_ERR_UNSUPPORTED,
-                   "the passes of a handle with several couplings are timed through its steps");
+                   "the tensor-core passes of several couplings are timed through the steps");
   DeviceGuard dg(h->device);
   cudaStream_t st = h->stream;
   // A running control block that never stops: it = 1 (residuals computed),
