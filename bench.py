@@ -482,6 +482,44 @@ def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
     return out
 
 
+def run_logdomain(args, jko, dev, barrier, steps=2):
+    """The log-domain tensor-core form (absorb = 3, TF32) on a potential whose
+    range a separable scale cannot remove: the cone w = |x - (0.9, 0.5)| at
+    sigma = 500 (515 e-folds), 256^2, gamma = 1e-3, tau = 0.5, kappa = 1.5 max
+    q0, <= 2000 pairs, tol 1e-6 (stall rule W = 4 on TF32).  Pairs/s of a
+    `steps`-step flow after a 1-step warm-up on the log-domain form and on the
+    FP64 CUDA-core form (whose range holds the cone's), and the per-step rel L1
+    of the former against the latter."""
+    import torch
+    from paper_1502_06216_gb300 import inputs
+    pb = inputs.cone_crowd_problem(256, n_steps=steps)
+    out = {"workload": f"crowd toward an exit under the cone potential, {pb.nx}x{pb.ny}, "
+                       f"gamma={pb.gamma}, tau={pb.tau} (sigma {pb.tau / pb.gamma:g}), kappa=1.5 max "
+                       f"q0, <={pb.max_iter} pairs/step, tol {pb.tol}"}
+    trajs = {}
+    for form, kw in (("TF32_log_domain", {"precision": jko.Precision.TF32, "absorb": 3, "stall": 4}),
+                     ("FP64", {"precision": jko.Precision.FP64})):
+        h = jko.create_from_problem(pb, **kw)
+        p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
+        jko.jko_flow(h, p0, 1)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, traj, infos = jko.jko_flow(h, p0, steps)
+        e1.record()
+        barrier()
+        secs = e0.elapsed_time(e1) / 1e3
+        iters = sum(i["iters"] for i in infos)
+        trajs[form] = traj.double()
+        out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
+                     "pairs_per_step": iters / steps}
+        jko.jko_destroy(h)
+    a, b = trajs["TF32_log_domain"], trajs["FP64"]
+    out["TF32_log_domain"]["rel_l1_vs_fp64_form"] = [
+        float((a[t] - b[t]).abs().sum() / b[t].abs().sum()) for t in range(steps)]
+    return out
+
+
 def run_attraction(args, jko, dev, barrier, steps=5):
     """Wasserstein attraction with congestion (Sec. 5.2, 2 couplings per step):
     256^2, disk q0 toward a disk target r, kappa = max q0, gamma = 5e-3, tau =
@@ -913,7 +951,7 @@ def run_ours(args):
     porous = None
     if not args.no_porous and rank == 0 and ws == 1:
         porous = run_porous(args, jko, dev, barrier, peak_bf16_for_porous)
-    genent = binary = attraction = species = heat = pairwise = fft = None
+    genent = binary = attraction = species = heat = pairwise = fft = logdomain = None
     if not args.no_porous and rank == 0 and ws == 1:
         genent = run_varying_exponents(args, jko, dev, barrier, peak_bf16_for_porous)
         binary = run_binary(args, jko, dev, barrier, peak_bf16_for_porous)
@@ -921,6 +959,7 @@ def run_ours(args):
         species = run_species(args, jko, dev, barrier)
         heat = run_heat(args, jko, dev, barrier)
         pairwise = run_pairwise(args, jko, dev, barrier)
+        logdomain = run_logdomain(args, jko, dev, barrier)
         fft = run_fft(args, jko, dev, barrier)
     diff = (run_differentiation(args, jko, dev, barrier)
             if not args.no_diff and rank == 0 and ws == 1 else None)
@@ -973,6 +1012,8 @@ def run_ours(args):
             line["heat_kernel"] = heat
         if pairwise is not None:
             line["pairwise_attraction"] = pairwise
+        if logdomain is not None:
+            line["log_domain_form"] = logdomain
         if fft is not None:
             line["fft_gaussian"] = fft
         if diff is not None:
