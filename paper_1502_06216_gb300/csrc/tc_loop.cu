@@ -38,6 +38,7 @@ namespace jko {
 namespace {
 
 constexpr int LBN = 64;                      // output tile width of every pass
+constexpr int EK_CROWD_PLAIN = 3;            // EK_CROWD, scalar kappa, no mask or binary
 constexpr int NEPI = 512;                    // epilogue threads: 16 warps, 4 per TMEM quadrant
 constexpr int NTL = NEPI + 64;               // + producer warp + MMA warp
 constexpr int WARP_PROD = 16;
@@ -129,6 +130,10 @@ __device__ __forceinline__ bool wait_go(const int* s_go, int q) {
 template <int MODE, int EK, bool RES>
 __global__ void __launch_bounds__(NTL, 1)
 tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ LoopArgs args) {
+  // EK_CROWD_PLAIN: the congestion/potential kind with a scalar bound and no
+  // mask or binary constraint, compiled without the per-cell field checks
+  constexpr bool PLAIN = EK == EK_CROWD_PLAIN;
+  constexpr int EKP = PLAIN ? EK_CROWD : EK;
   using T = typename OpT<MODE>::T;
   constexpr int KE = OpT<MODE>::kElems;
   constexpr int NSPLIT = img_split(MODE) ? 2 : 1;         // image hi (+ lo) blocks
@@ -142,7 +147,11 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   static_assert(!RES || MODE == MODE_BF16, "resident factors: BF16 only");
   constexpr uint32_t STG_BYTES = loop_staging_bytes(MODE);
   constexpr uint32_t F32_TILE = (uint32_t)LBN * BM * 4u;
-  constexpr uint32_t TMEM_COLS = acc_cols(MODE, LBN);
+  // resident mode keeps each thread's cells of the last b (operand value) in
+  // TMEM columns BPREV_COL .. +63 beside the accumulator, for the next residual
+  constexpr uint32_t BPREV_COL = 128;
+  static_assert(!RES || acc_cols(MODE, LBN) <= BPREV_COL, "accumulator below the old b");
+  constexpr uint32_t TMEM_COLS = RES ? 256u : acc_cols(MODE, LBN);
   constexpr int CB = LBN * (int)sizeof(T) / 128;   // 128-byte column blocks of an operand tile
   constexpr uint32_t OUT_BLOCK = BM * 128;
   static_assert((uint32_t)NSPLIT * CB * OUT_BLOCK <= STG_BYTES, "staging tile");
@@ -156,7 +165,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
   // the MMAs run, and the old b stays in the registers of the thread that
   // computed it (every pair gives a thread the same cells of its one tile)
   constexpr bool EPI1 = true;
-  constexpr bool EPI3 = EK == EK_CROWD;
+  constexpr bool EPI3 = EKP == EK_CROWD;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -398,16 +407,15 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
     const ProxArgs<float> P = args.P;
     // congestion/potential cells with a scalar bound and no mask: the common
     // case, evaluated without the per-cell field checks
-    const bool crowd_plain =
-        EK == EK_CROWD && P.mask == nullptr && P.kappa == nullptr && P.binary == 0;
+    constexpr bool crowd_plain = PLAIN;
     uint32_t tc = 0, ec = 0;
     int bad = 0;
     bool free_pending = false;   // epi_free owed once the last stores have read smem
     int dec_stop = 0;            // stop rule of this pair, taken during pass 2
     unsigned flag_prev = 0;      // flag slot of the previous barrier (thread 0)
-    // resident mode: this thread's cells of b (operand value hi + lo) from the
-    // last b-update pass, the old b of the next residual
-    float bprev[16];
+    // resident mode: whether this thread's cells of b (operand value hi + lo)
+    // from the last b-update pass are in TMEM (BPREV_COL), the old b of the
+    // next residual: registers would spill at this kernel's register cap
     bool bprev_ok = false;
     for (int q = 0; q < nq; ++q) {
       const int p = q & 3;
@@ -494,10 +502,19 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         float qv[16], bo[16], ev[16];
         if constexpr (RES) {
           // the first b-update pass of a launch that continues a step: the
-          // old b from global memory (this CTA's own tile, read past L1)
-          if (p == 1 && have_prev && !bprev_ok)
+          // old b from global memory (this CTA's own tile, read past L1) into
+          // the TMEM columns where the b-update passes keep it
+          if (p == 1 && have_prev && !bprev_ok) {
             load_op16_cg<MODE>((const T*)args.b_hi, (const T*)args.b_lo,
-                               cnt ? (size_t)m * args.pitch_b + nb : 0, cnt, bprev);
+                               cnt ? (size_t)m * args.pitch_b + nb : 0, cnt, bo);
+            uint32_t rb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) rb[j] = __float_as_uint(bo[j]);
+            tmem_st16(tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL + (uint32_t)(grp * 16),
+                      rb);
+            tmem_wait_st();
+            bprev_ok = true;
+          }
         }
         bool have = mbar_wait(accum_bar, tc & 1);
         if (have && epi_pass) have = mbar_wait(epi_full_bar, ec & 1);
@@ -514,45 +531,87 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
 #pragma unroll
           for (int j = 0; j < 16; ++j) o[j] = v[j];
         } else if (p == 1) {
-          smem_ld_f32x16(epi_f, rl, c, qv);
           if constexpr (RES) {
+            // the old b from TMEM; q four columns at a time from the staging
+            // region (the layout of smem_ld_f32x16), to stay within the
+            // register cap of this kernel's 18 warps
+            const unsigned char* qrow = epi_f + (c >> 1) * (BM * 128) + rl * 128;
+            const int k0 = (c & 1) * 4;
+            const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL +
+                                (uint32_t)(grp * 16);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) bo[j] = bprev[j];
+            for (int q4 = 0; q4 < 4; ++q4) {
+              uint32_t rb[4] = {0u, 0u, 0u, 0u};
+              if (have_prev) {
+                tmem_ld4_issue(tb + (uint32_t)(4 * q4), rb);
+                tmem_wait_ld();
+                reg_fence4(rb);
+              }
+              const float4 t = *reinterpret_cast<const float4*>(qrow + (((k0 + q4) ^ (rl & 7)) << 4));
+              const float qq[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int j = 4 * q4 + u;
+                if (j < cnt) {
+                  if (have_prev) res_f += abs_residual<float>(__uint_as_float(rb[u]), v[j], qq[u]);
+                  o[j] = b_update<float>(qq[u], v[j]);
+                  bad |= !isfinite(o[j]);
+                } else {
+                  o[j] = 0.0f;
+                }
+              }
+            }
           } else {
+            smem_ld_f32x16(epi_f, rl, c, qv);
             if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
-          }
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (j < cnt) {
-              if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
-              o[j] = b_update<float>(qv[j], v[j]);
-              bad |= !isfinite(o[j]);
-            } else {
-              o[j] = 0.0f;
+            for (int j = 0; j < 16; ++j) {
+              if (j < cnt) {
+                if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
+                o[j] = b_update<float>(qv[j], v[j]);
+                bad |= !isfinite(o[j]);
+              } else {
+                o[j] = 0.0f;
+              }
             }
           }
         } else {
           const int irow = m * PS.N + nb;
           float pv[16];
-          if (EK == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
           if (crowd_plain) {
+            // e^{-sigma w} in, p out, four columns at a time (the layout of
+            // smem_ld_f32x16 / smem_st_f32x16), to stay within the register
+            // cap of this kernel's 18 warps
             const bool hk = P.has_kappa != 0;
             const float kap = P.kappa_s;
+            const int k0 = (c & 1) * 4;
+            const unsigned char* erow = epi_f + (c >> 1) * (BM * 128) + rl * 128;
+            unsigned char* prow = p_st + (c >> 1) * (BM * 128) + rl * 128;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float a = ev[j];
-              if (hk && a * v[j] > kap) a = ratio_div<float>(kap, v[j]);
-              if (j >= cnt) a = 0.0f;
-              bad |= !isfinite(a);
-              o[j] = a;
-              pv[j] = a * v[j];
+            for (int q4 = 0; q4 < 4; ++q4) {
+              const int off = ((k0 + q4) ^ (rl & 7)) << 4;
+              const float4 t = *reinterpret_cast<const float4*>(erow + off);
+              const float ee[4] = {t.x, t.y, t.z, t.w};
+              float pp[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int j = 4 * q4 + u;
+                float a = ee[u];
+                if (hk && a * v[j] > kap) a = ratio_div<float>(kap, v[j]);
+                if (j >= cnt) a = 0.0f;
+                bad |= !isfinite(a);
+                o[j] = a;
+                pp[u] = a * v[j];
+              }
+              *reinterpret_cast<float4*>(prow + off) = make_float4(pp[0], pp[1], pp[2], pp[3]);
             }
           } else {
+            if (EKP == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               if (j < cnt) {
-                const float a = prox_ratio_e<float, EK>(P, irow + j, v[j],
-                                                         EK == EK_CROWD ? ev[j] : 0.0f);
+                const float a = prox_ratio_e<float, EKP>(P, irow + j, v[j],
+                                                         EKP == EK_CROWD ? ev[j] : 0.0f);
                 bad |= !isfinite(a);
                 o[j] = a;
                 pv[j] = a * v[j];
@@ -561,16 +620,20 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
                 pv[j] = 0.0f;
               }
             }
+            smem_st_f32x16(p_st, rl, c, pv);
           }
-          smem_st_f32x16(p_st, rl, c, pv);
         }
         if constexpr (RES) {
           // every thread has read the q / e^{-sigma w} tile in the staging
           // region before any writes its output there
           if (epi_pass) named_bar_sync(EPI_BAR, NEPI);
           if (p == 1) {
+            uint32_t rb[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) bprev[j] = op_value<MODE>(o[j]);
+            for (int j = 0; j < 16; ++j) rb[j] = __float_as_uint(op_value<MODE>(o[j]));
+            tmem_st16(tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL + (uint32_t)(grp * 16),
+                      rb);
+            tmem_wait_st();
             bprev_ok = true;
           }
         }
@@ -1169,6 +1232,9 @@ cudaError_t launch_loop(const LoopMaps& maps, const LoopArgs& args, int grid, cu
 template <int MODE, bool RES>
 cudaError_t dispatch_loop(int ek, const LoopMaps& maps, const LoopArgs& args, int grid,
                           cudaStream_t st) {
+  const ProxArgs<float>& P = args.P;
+  if (ek == EK_CROWD && P.mask == nullptr && P.kappa == nullptr && P.binary == 0)
+    return launch_loop<MODE, EK_CROWD_PLAIN, RES>(maps, args, grid, st);
   if (ek == EK_CROWD) return launch_loop<MODE, EK_CROWD, RES>(maps, args, grid, st);
   if (ek == EK_ENTROPY) return launch_loop<MODE, EK_ENTROPY, RES>(maps, args, grid, st);
   return launch_loop<MODE, EK_POWER, RES>(maps, args, grid, st);
@@ -1178,6 +1244,7 @@ template <int MODE, int EK, bool RES>
 int blocks_per_sm() {
   int nb = 0;
   if (set_loop_attr<MODE, EK, RES>() != cudaSuccess) return 0;
+  if (EK == EK_CROWD && set_loop_attr<MODE, EK_CROWD_PLAIN, RES>() != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tc_loop_kernel<MODE, EK, RES>, NTL,
                                                     loop_smem_bytes(MODE, RES)) != cudaSuccess)
     return 0;
