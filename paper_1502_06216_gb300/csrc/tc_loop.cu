@@ -522,7 +522,11 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         __syncwarp();
         tc_fence_after();
         float v[16], o[16];
+        // resident mode: the old b of the residual from TMEM
+        const bool ld_old = RES && p == 1 && have_prev;
+        const uint32_t t_old = tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL + (uint32_t)(grp * 16);
         tmem_tile16<MODE, LBN>(tmem_base + ((uint32_t)(quad * 32) << 16), grp * 16, v);
+        if (ld_old) tmem_wait_st();   // this thread's store of it, one pair ago
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tmem_free_bar);
@@ -537,15 +541,13 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             // register cap of this kernel's 18 warps
             const unsigned char* qrow = epi_f + (c >> 1) * (BM * 128) + rl * 128;
             const int k0 = (c & 1) * 4;
-            const uint32_t tb = tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL +
-                                (uint32_t)(grp * 16);
+            uint32_t rb[8];
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) {
-              uint32_t rb[4] = {0u, 0u, 0u, 0u};
-              if (have_prev) {
-                tmem_ld4_issue(tb + (uint32_t)(4 * q4), rb);
+              if (ld_old && (q4 & 1) == 0) {   // the old b, eight columns at a time
+                tmem_ld8_issue(t_old + (uint32_t)(4 * q4), rb);
                 tmem_wait_ld();
-                reg_fence4(rb);
+                reg_fence8(rb);
               }
               const float4 t = *reinterpret_cast<const float4*>(qrow + (((k0 + q4) ^ (rl & 7)) << 4));
               const float qq[4] = {t.x, t.y, t.z, t.w};
@@ -553,7 +555,8 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               for (int u = 0; u < 4; ++u) {
                 const int j = 4 * q4 + u;
                 if (j < cnt) {
-                  if (have_prev) res_f += abs_residual<float>(__uint_as_float(rb[u]), v[j], qq[u]);
+                  if (have_prev)
+                    res_f += abs_residual<float>(__uint_as_float(rb[4 * (q4 & 1) + u]), v[j], qq[u]);
                   o[j] = b_update<float>(qq[u], v[j]);
                   bad |= !isfinite(o[j]);
                 } else {
@@ -628,13 +631,12 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           // region before any writes its output there
           if (epi_pass) named_bar_sync(EPI_BAR, NEPI);
           if (p == 1) {
-            uint32_t rb[16];
+            uint32_t rs[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) rb[j] = __float_as_uint(op_value<MODE>(o[j]));
+            for (int j = 0; j < 16; ++j) rs[j] = __float_as_uint(op_value<MODE>(o[j]));
             tmem_st16(tmem_base + ((uint32_t)(quad * 32) << 16) + BPREV_COL + (uint32_t)(grp * 16),
-                      rb);
-            tmem_wait_st();
-            bprev_ok = true;
+                      rs);
+            bprev_ok = true;   // (waited for before the next load and before the end)
           }
         }
         stage16<MODE>(st_hi, st_lo, rl, c, o);
@@ -669,6 +671,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
       if (p == 3 && q == nq - 1) pairs_done = pair + 1;
     }
     if (threadIdx.x == 0) bulk_wait_all();
+    if (RES) tmem_wait_st();   // the old b's stores, before the columns are freed
     bad = warp_or(bad);
     if (lane == 0 && bad) atomicOr(&ctrl->nonfinite, 1);
   }
