@@ -196,6 +196,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+// All bulk groups but the most recent one complete (their writes done).
+__device__ __forceinline__ void bulk_wait_all_but_last() {
+  asm volatile("cp.async.bulk.wait_group 1;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_wait_read_all() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }

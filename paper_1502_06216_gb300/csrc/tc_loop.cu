@@ -424,7 +424,15 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
       if (q > 0) {
         // ---- grid barrier: the previous pass is complete everywhere ----
         if (threadIdx.x == 0) {
-          bulk_wait_all();                 // this CTA's output tiles are in global memory
+          if (p == 0) {
+            // after the prox pass: its a tiles are in global memory; the p
+            // tiles (their own, last, bulk group) are read by no pass and
+            // need only have left the stages, which the next loads refill
+            bulk_wait_read_all();
+            bulk_wait_all_but_last();
+          } else {
+            bulk_wait_all();               // this CTA's output tiles are in global memory
+          }
           fence_proxy_async_global();
           if (free_pending) mbar_arrive(epi_free_bar);
           if (s_fault & 3) atomicOr(&ctrl->nonfinite, 2);
@@ -655,6 +663,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
             if constexpr (NSPLIT == 2) tma_store_2d(&maps.O[p][1], st_lo + cb * OUT_BLOCK, n0 + cb * KEo, m0);
           }
           if (p == 3) {
+            bulk_commit();                 // the a tiles, then the p tiles as their own group
 #pragma unroll
             for (int cb = 0; cb < LBN / 32; ++cb)
               tma_store_2d(&maps.P, p_st + cb * (BM * 128), n0 + cb * 32, m0);
