@@ -507,7 +507,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         const int nb = n0 + c * 16;
         int cnt = PS.N - nb;
         cnt = (m >= PS.M || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
-        float qv[16], bo[16], ev[16];
+        float qv[16], bo[16];
         if constexpr (RES) {
           // the first b-update pass of a launch that continues a step: the
           // old b from global memory (this CTA's own tile, read past L1) into
@@ -588,7 +588,6 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
           }
         } else {
           const int irow = m * PS.N + nb;
-          float pv[16];
           if (crowd_plain) {
             // e^{-sigma w} in, p out, four columns at a time (the layout of
             // smem_ld_f32x16 / smem_st_f32x16), to stay within the register
@@ -617,21 +616,34 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               *reinterpret_cast<float4*>(prow + off) = make_float4(pp[0], pp[1], pp[2], pp[3]);
             }
           } else {
-            if (EKP == EK_CROWD) smem_ld_f32x16(epi_f, rl, c, ev);
+            // the general prox, four columns at a time as above
+            const int k0 = (c & 1) * 4;
+            const unsigned char* erow = epi_f + (c >> 1) * (BM * 128) + rl * 128;
+            unsigned char* prow = p_st + (c >> 1) * (BM * 128) + rl * 128;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (j < cnt) {
-                const float a = prox_ratio_e<float, EKP>(P, irow + j, v[j],
-                                                         EKP == EK_CROWD ? ev[j] : 0.0f);
-                bad |= !isfinite(a);
-                o[j] = a;
-                pv[j] = a * v[j];
-              } else {
-                o[j] = 0.0f;
-                pv[j] = 0.0f;
+            for (int q4 = 0; q4 < 4; ++q4) {
+              const int off = ((k0 + q4) ^ (rl & 7)) << 4;
+              float ee[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+              if (EKP == EK_CROWD) {
+                const float4 t = *reinterpret_cast<const float4*>(erow + off);
+                ee[0] = t.x; ee[1] = t.y; ee[2] = t.z; ee[3] = t.w;
               }
+              float pp[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int j = 4 * q4 + u;
+                if (j < cnt) {
+                  const float a = prox_ratio_e<float, EKP>(P, irow + j, v[j], ee[u]);
+                  bad |= !isfinite(a);
+                  o[j] = a;
+                  pp[u] = a * v[j];
+                } else {
+                  o[j] = 0.0f;
+                  pp[u] = 0.0f;
+                }
+              }
+              *reinterpret_cast<float4*>(prow + off) = make_float4(pp[0], pp[1], pp[2], pp[3]);
             }
-            smem_st_f32x16(p_st, rl, c, pv);
           }
         }
         if constexpr (RES) {
