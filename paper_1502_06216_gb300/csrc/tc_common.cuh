@@ -595,6 +595,38 @@ __device__ __forceinline__ void smem_ld_op16(const unsigned char* hi, const unsi
   }
 }
 
+// Four fp32 values (columns 16c + 4g .. + 3) of row r in a swizzled fp32 tile
+// (the layout of smem_ld_f32x16 / smem_st_f32x16).
+__device__ __forceinline__ float4 smem_ld_f32x4(const unsigned char* reg, int r, int c, int g) {
+  const unsigned char* row = reg + (c >> 1) * (BM * 128) + r * 128;
+  return *reinterpret_cast<const float4*>(row + ((((c & 1) * 4 + g) ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ void smem_st_f32x4(unsigned char* reg, int r, int c, int g, float4 v) {
+  unsigned char* row = reg + (c >> 1) * (BM * 128) + r * 128;
+  *reinterpret_cast<float4*>(row + ((((c & 1) * 4 + g) ^ (r & 7)) << 4)) = v;
+}
+// Four operand values (hi [+ lo]) of row r, columns 16c + 4g .., from swizzled
+// tiles (the layout of smem_ld_op16).
+template <int MODE>
+__device__ __forceinline__ void smem_ld_op4(const unsigned char* hi, const unsigned char* lo, int r,
+                                            int c, int g, float (&o)[4]) {
+  if constexpr (MODE == MODE_TF32) {
+    const float4 t = smem_ld_f32x4(hi, r, c, g);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  } else {
+    const int cb = c >> 2, unit = (c & 3) * 2 + (g >> 1);
+    const size_t off = cb * (BM * 128) + r * 128 + ((unit ^ (r & 7)) << 4) + (g & 1) * 8;
+    const uint2 t = *reinterpret_cast<const uint2*>(hi + off);
+    const float2 f0 = unpack_bf16x2(t.x), f1 = unpack_bf16x2(t.y);
+    o[0] = f0.x; o[1] = f0.y; o[2] = f1.x; o[3] = f1.y;
+    if constexpr (img_split(MODE)) {
+      const uint2 u = *reinterpret_cast<const uint2*>(lo + off);
+      const float2 h0 = unpack_bf16x2(u.x), h1 = unpack_bf16x2(u.y);
+      o[0] += h0.x; o[1] += h0.y; o[2] += h1.x; o[3] += h1.y;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

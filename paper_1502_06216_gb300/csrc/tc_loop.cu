@@ -507,7 +507,7 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
         const int nb = n0 + c * 16;
         int cnt = PS.N - nb;
         cnt = (m >= PS.M || cnt < 0) ? 0 : (cnt > 16 ? 16 : cnt);
-        float qv[16], bo[16];
+        float bo[16];
         if constexpr (RES) {
           // the first b-update pass of a launch that continues a step: the
           // old b from global memory (this CTA's own tile, read past L1) into
@@ -573,16 +573,23 @@ tc_loop_kernel(const __grid_constant__ LoopMaps maps, const __grid_constant__ Lo
               }
             }
           } else {
-            smem_ld_f32x16(epi_f, rl, c, qv);
-            if (have_prev) smem_ld_op16<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, bo);
+            // q and the old b four columns at a time
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (j < cnt) {
-                if (have_prev) res_f += abs_residual<float>(bo[j], v[j], qv[j]);
-                o[j] = b_update<float>(qv[j], v[j]);
-                bad |= !isfinite(o[j]);
-              } else {
-                o[j] = 0.0f;
+            for (int g4 = 0; g4 < 4; ++g4) {
+              const float4 t = smem_ld_f32x4(epi_f, rl, c, g4);
+              const float qq[4] = {t.x, t.y, t.z, t.w};
+              float bb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+              if (have_prev) smem_ld_op4<MODE>(epi_g, epi_g + CB * OUT_BLOCK, rl, c, g4, bb);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int j = 4 * g4 + u;
+                if (j < cnt) {
+                  if (have_prev) res_f += abs_residual<float>(bb[u], v[j], qq[u]);
+                  o[j] = b_update<float>(qq[u], v[j]);
+                  bad |= !isfinite(o[j]);
+                } else {
+                  o[j] = 0.0f;
+                }
               }
             }
           }
