@@ -220,7 +220,10 @@ dim3 heat_grid(int nx, int ny) { return dim3((nx + HBX - 1) / HBX, (ny + HBY - 1
 // two applications of xi~, the b-update and the prox, with a grid barrier
 // (jko_internal.cuh) where the kernels above end one launch and start the next.
 // Block b takes the 16x8 tiles b, b + G, ... of the grid (the same tiles in
-// every phase), with the arithmetic of heat_cl_step / heat_cl_step2 per tile:
+// every phase), with the arithmetic of heat_cl_step / heat_cl_step2 per cell;
+// a phase runs two or four Clenshaw steps between two grid barriers (four
+// while every tile has a block of its own), on the tile and a halo one cell
+// narrower per step (recomputed by neighbours):
 //   * the first Clenshaw iterates b_D = c_D v, b_{D+1} = 0 are formed on the
 //     fly from v where the kernels above store them (the same values);
 //   * the closing step ends in the b-update (first application: b = q / Y
@@ -249,6 +252,7 @@ struct HeatLoopArgs {
   double* part;            // residual partial of each tile (heat_bupdate's blocks)
   int ntiles, tiles_x;
   int pairs;
+  int steps;               // Clenshaw steps per phase between grid barriers
 };
 
 template <typename T>
@@ -256,32 +260,6 @@ __device__ __forceinline__ T ld_plain(const T* p) { return *p; }
 
 // A v at (x, y) where v is stored as c * v[j] (the first iterate b_D = c_D v):
 // the neighbour terms of apply_A on those values.
-template <typename T>
-__device__ __forceinline__ double scaled(const T* v, int j, double c) {
-  return __dmul_rn(c, (double)ld_plain(v + j));
-}
-template <typename T>
-__device__ __forceinline__ double apply_A_scaled(const HeatGeom& g, const T* v, double c, int x,
-                                                 int y) {
-  const int i = y * g.nx + x;
-  const double vi = scaled(v, i, c);
-  double acc = vi;
-  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, vi, scaled(v, i - 1, c));
-  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, vi, scaled(v, i + 1, c));
-  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, vi, scaled(v, i - g.nx, c));
-  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, vi, scaled(v, i + g.nx, c));
-  return acc;
-}
-// A tile and its two-cell halo in shared memory: v, b_{k+1}, b_{k+2}, and
-// whether each cell is in the grid and off the mask.
-constexpr int HEX = HBX + 4, HEY = HBY + 4;
-struct HeatStage {
-  double v[HEY][HEX];
-  double b1[HEY][HEX];
-  double b2[HEY][HEX];
-  unsigned char fr[HEY][HEX];
-};
-
 // The closing step's output r at cell i of the grid, into the b-update (app 0)
 // or the prox (app 1).
 template <typename T, int EK>
@@ -302,119 +280,121 @@ __device__ __forceinline__ void heat_close_cell(const HeatLoopArgs<T>& A, int ap
   }
 }
 
-// One Clenshaw phase on one tile: steps k and (when TWO) k - 1.  b1 = b_{k+1},
-// b2 = b_{k+2} (VIRT: b_{k+1} = c1v v, b_{k+2} = 0, not stored); writes b_k to
-// o1 and b_{k-1} to o2, or closes (CLOSE: the last step is step 0) into the
-// epilogue.  ONE_STORE: a single step that also stores b_{k+1} = c1v v to o2
-// (the first step of an odd degree, whose successors read it).
-template <typename T, int EK, bool TWO, bool VIRT, bool CLOSE>
-__device__ __forceinline__ void heat_tile_phase(const HeatLoopArgs<T>& A, int app, int t,
-                                                const T* v, const double* b1, const double* b2,
-                                                double* o1, double* o2, double c1v, double ck,
-                                                double ck1, bool have_prev, double (*sb)[HBX + 2],
-                                                HeatStage* stg, double* s_red, int& bad) {
-  constexpr int RX = HBX + 2, RY = HBY + 2;
+// Up to H Clenshaw steps of one phase on one tile: v, b_{k+1}, b_{k+2} and
+// the free flags staged on the tile and an H-cell halo; step s (index
+// k - s) on the tile and an (ns - 1 - s)-cell halo, in place over b_{k+2}'s
+// array (a cell reads b_{k+2} only at itself), with the arithmetic of the
+// kernels per phase cell by cell.  VIRT: the first iterates b_{k+1} = c1v v
+// and b_{k+2} = 0 formed here.  The phase writes its newest iterate to o_new
+// and the one before to o_prev on the tile, or, when its last step is step 0,
+// closes into the epilogue.
+constexpr int HMAX = 4;                      // Clenshaw steps per grid barrier
+constexpr int HSX = HBX + 2 * HMAX, HSY = HBY + 2 * HMAX;
+struct HeatStageH {
+  double v[HSY][HSX];
+  double b1[HSY][HSX];
+  double b2[HSY][HSX];
+  unsigned char fr[HSY][HSX];
+};
+
+template <typename T, int EK>
+__device__ __forceinline__ void heat_tile_steps(const HeatLoopArgs<T>& A, int app, int t, const T* v,
+                                                const double* b1, const double* b2, double* o_new,
+                                                double* o_prev, bool virt, double c1v, int k,
+                                                int ns, bool have_prev, HeatStageH& S, double* s_red,
+                                                int& bad) {
+  constexpr int H = HMAX;
   const HeatGeom& g = A.g;
   const int tyt = t / A.tiles_x;
   const int x0 = (t - tyt * A.tiles_x) * HBX, y0 = tyt * HBY;
   const int tid = threadIdx.y * HBX + threadIdx.x;
-  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-  const bool in = x < g.nx && y < g.ny;
-  const int i = y * g.nx + x;
+  // stage the tile and an ns-cell halo (at offset H - ns in the arrays)
+  const int sx = HBX + 2 * ns, sy = HBY + 2 * ns;
+  for (int idx = tid; idx < sx * sy; idx += HBX * HBY) {
+    const int ey = H - ns + idx / sx, ex = H - ns + idx % sx;
+    const int xx = x0 + ex - H, yy = y0 + ey - H;
+    double vv = 0.0, bb1 = 0.0, bb2 = 0.0;
+    unsigned char f = 0;
+    if (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) {
+      const int j = yy * g.nx + xx;
+      vv = (double)ld_plain(v + j);
+      if (!virt) {
+        bb1 = ld_plain(b1 + j);
+        bb2 = ld_plain(b2 + j);
+      }
+      f = g.mask == nullptr || g.mask[j] == 0;
+    }
+    S.v[ey][ex] = vv;
+    S.b1[ey][ex] = virt ? __dmul_rn(c1v, vv) : bb1;
+    S.b2[ey][ex] = bb2;
+    S.fr[ey][ex] = f;
+  }
+  __syncthreads();
+  double (*cur1)[HSX] = S.b1;
+  double (*cur2)[HSX] = S.b2;
   T res = T(0);
-  if (TWO) {
-    // v, b_{k+1}, b_{k+2} and the free flags (in the grid and off the mask) on
-    // the tile and a two-cell halo, staged with independent loads
-    HeatStage& S = *stg;
-    for (int idx = tid; idx < HEX * HEY; idx += HBX * HBY) {
-      const int ey = idx / HEX, ex = idx - ey * HEX;
-      const int xx = x0 + ex - 2, yy = y0 + ey - 2;
-      double vv = 0.0, bb1 = 0.0, bb2 = 0.0;
-      unsigned char f = 0;
-      if (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) {
-        const int j = yy * g.nx + xx;
-        vv = (double)ld_plain(v + j);
-        if (!VIRT) {
-          bb1 = ld_plain(b1 + j);
-          bb2 = ld_plain(b2 + j);
+  for (int st = 0; st < ns; ++st) {
+    const int kk = k - st;
+    const double ck = __ldg(A.coef + kk);
+    const double sc = kk == 0 ? A.inv_delta : g.two_over_delta;
+    if (st < ns - 1) {
+      // b_kk on the tile and an (ns - 1 - st)-cell halo, into cur2's array
+      const int h = ns - 1 - st;
+      const int rx = HBX + 2 * h, ry = HBY + 2 * h;
+      for (int idx = tid; idx < rx * ry; idx += HBX * HBY) {
+        const int yy = idx / rx, xx = idx - yy * rx;
+        const int ey = H - h + yy, ex = H - h + xx;
+        double val = 0.0;
+        if (S.fr[ey][ex]) {
+          const double bc = cur1[ey][ex];
+          double Ab = bc;
+          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex - 1]);
+          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex + 1]);
+          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey - 1][ex]);
+          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey + 1][ex]);
+          val = cl_value(ck, S.v[ey][ex], sc, Ab, A.theta, bc, cur2[ey][ex]);
         }
-        f = g.mask == nullptr || g.mask[j] == 0;
+        cur2[ey][ex] = val;
       }
-      S.v[ey][ex] = vv;
-      S.b1[ey][ex] = VIRT ? __dmul_rn(c1v, vv) : bb1;
-      S.b2[ey][ex] = bb2;
-      S.fr[ey][ex] = f;
-    }
-    __syncthreads();
-    // b_k on the tile and a one-cell halo (heat_cl_step2's first step)
-    for (int idx = tid; idx < RX * RY; idx += HBX * HBY) {
-      const int ry = idx / RX, rx = idx - ry * RX;
-      const int ey = ry + 1, ex = rx + 1;
-      double val = 0.0;
-      if (S.fr[ey][ex]) {
-        const double bc = S.b1[ey][ex];
-        double Ab = bc;
-        if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, S.b1[ey][ex - 1]);
-        if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, S.b1[ey][ex + 1]);
-        if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, S.b1[ey - 1][ex]);
-        if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, S.b1[ey + 1][ex]);
-        val = cl_value(ck, S.v[ey][ex], g.two_over_delta, Ab, A.theta, bc, S.b2[ey][ex]);
-      }
-      sb[ry][rx] = val;
-    }
-    __syncthreads();
-    if (in) {
-      const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-      const int ex = threadIdx.x + 2, ey = threadIdx.y + 2;
-      const double c = sb[ty][tx];
-      if (!CLOSE) o1[i] = c;
-      if (!S.fr[ey][ex]) {
-        if (CLOSE) heat_close_cell<T, EK>(A, app, i, 0.0, have_prev, res, bad);
-        else o2[i] = 0.0;
-      } else {
-        double acc = c;
-        if (S.fr[ey][ex - 1]) acc = nb_term(acc, g.cx, c, sb[ty][tx - 1]);
-        if (S.fr[ey][ex + 1]) acc = nb_term(acc, g.cx, c, sb[ty][tx + 1]);
-        if (S.fr[ey - 1][ex]) acc = nb_term(acc, g.cy, c, sb[ty - 1][tx]);
-        if (S.fr[ey + 1][ex]) acc = nb_term(acc, g.cy, c, sb[ty + 1][tx]);
-        const double s2 = CLOSE ? A.inv_delta : g.two_over_delta;
-        const double r = cl_value(ck1, S.v[ey][ex], s2, acc, A.theta, c, S.b1[ey][ex]);
-        if (CLOSE) heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
-        else o2[i] = r;
-      }
-    }
-    __syncthreads();   // the staging and sb are reused by the next tile
-  } else if (in) {
-    // one step (heat_cl_step): from the virtual first iterates
-    if (!is_free(g, i)) {
-      if (CLOSE) heat_close_cell<T, EK>(A, app, i, 0.0, have_prev, res, bad);
-      else {
-        o1[i] = 0.0;
-        o2[i] = 0.0;
-      }
+      __syncthreads();
+      double (*tmp)[HSX] = cur2;
+      cur2 = cur1;
+      cur1 = tmp;
     } else {
-      const double vi = (double)ld_plain(v + i);
-      const double Ab = apply_A_scaled<T>(g, v, c1v, x, y);
-      const double s = CLOSE ? A.inv_delta : g.two_over_delta;
-      const double r = cl_value(ck, vi, s, Ab, A.theta, __dmul_rn(c1v, vi), 0.0);
-      if (CLOSE) heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
-      else {
-        o1[i] = r;
-        o2[i] = __dmul_rn(c1v, vi);
+      // the last step, on the tile: written out, or closed into the epilogue
+      const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+      if (x < g.nx && y < g.ny) {
+        const int i = y * g.nx + x;
+        const int ey = H + threadIdx.y, ex = H + threadIdx.x;
+        double r = 0.0;
+        if (S.fr[ey][ex]) {
+          const double bc = cur1[ey][ex];
+          double Ab = bc;
+          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex - 1]);
+          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex + 1]);
+          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey - 1][ex]);
+          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey + 1][ex]);
+          r = cl_value(ck, S.v[ey][ex], sc, Ab, A.theta, bc, cur2[ey][ex]);
+        }
+        if (kk == 0) {
+          heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
+        } else {
+          o_new[i] = r;
+          o_prev[i] = S.fr[ey][ex] ? cur1[ey][ex] : 0.0;
+        }
       }
     }
   }
-  if (CLOSE && app == 0) {
-    // the tile's residual partial, as heat_bupdate's block
+  if (k - ns + 1 == 0 && app == 0) {
     const double tot = block_sum((double)res, s_red);
     if (tid == 0) A.part[t] = tot;
   }
+  __syncthreads();   // the staging is reused by the next tile
 }
 
 template <typename T, int EK>
 __global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A) {
-  __shared__ double sb[HBY + 2][HBX + 2];
-  __shared__ HeatStage stg;
+  __shared__ HeatStageH stg;
   __shared__ double s_red[33];
   __shared__ int s_stop, s_fault, s_it0, s_maxit;
   __shared__ unsigned s_base;
@@ -493,56 +473,25 @@ __global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A)
       const T* v = app == 0 ? A.a : A.b;
       const bool have_prev = app == 0 && it > 0;
       const double cD = __ldg(A.coef + D);
+      // phases of up to HMAX steps from the first iterates (b_D = c_D v,
+      // b_{D+1} = 0), the first one taking D mod HMAX steps; buffers: read
+      // the newest / previous iterates from d[r1] / d[r2], write d[f1] / d[f2]
       int r1 = 0, r2 = 1, f1 = 2, f2 = 3;
+      const int hm = A.steps;   // Clenshaw steps per phase (<= HMAX)
       int k = D - 1;
+      int ns = D % hm == 0 ? hm : D % hm;
       bool virt = true;
-      if (D % 2 == 1) {
-        // one single step first: b_{D-1} to d[0], b_D = c_D v to d[1] (or
-        // the closing step when D = 1)
-        for (int t = blockIdx.x; t < A.ntiles; t += G) {
-          if (k == 0)
-            heat_tile_phase<T, EK, false, true, true>(A, app, t, v, nullptr, nullptr, nullptr,
-                                                      nullptr, cD, __ldg(A.coef + (0)), 0.0, have_prev,
-                                                      sb, &stg, s_red, bad);
-          else
-            heat_tile_phase<T, EK, false, true, false>(A, app, t, v, nullptr, nullptr, A.d[0],
-                                                       A.d[1], cD, __ldg(A.coef + (k)), 0.0, have_prev,
-                                                       sb, &stg, s_red, bad);
-        }
+      while (k >= 0) {
+        for (int t = blockIdx.x; t < A.ntiles; t += G)
+          heat_tile_steps<T, EK>(A, app, t, v, virt ? nullptr : A.d[r1], virt ? nullptr : A.d[r2],
+                                 A.d[f1], A.d[f2], virt, cD, k, ns, have_prev, stg, s_red, bad);
         if (!barrier()) { run = false; break; }
-        if (k == 0) continue;
-        virt = false;
-        r1 = 0; r2 = 1; f1 = 2; f2 = 3;
-        --k;
-      }
-      for (; k >= 1 && run; k -= 2) {
-        const bool close = k == 1;
-        for (int t = blockIdx.x; t < A.ntiles; t += G) {
-          if (virt) {
-            if (close)
-              heat_tile_phase<T, EK, true, true, true>(A, app, t, v, nullptr, nullptr, nullptr,
-                                                       nullptr, cD, __ldg(A.coef + (1)), __ldg(A.coef + (0)),
-                                                       have_prev, sb, &stg, s_red, bad);
-            else
-              heat_tile_phase<T, EK, true, true, false>(A, app, t, v, nullptr, nullptr, A.d[f1],
-                                                        A.d[f2], cD, __ldg(A.coef + (k)), __ldg(A.coef + (k - 1)),
-                                                        have_prev, sb, &stg, s_red, bad);
-          } else {
-            if (close)
-              heat_tile_phase<T, EK, true, false, true>(A, app, t, v, A.d[r1], A.d[r2], nullptr,
-                                                        nullptr, 0.0, __ldg(A.coef + (1)), __ldg(A.coef + (0)),
-                                                        have_prev, sb, &stg, s_red, bad);
-            else
-              heat_tile_phase<T, EK, true, false, false>(A, app, t, v, A.d[r1], A.d[r2], A.d[f1],
-                                                         A.d[f2], 0.0, __ldg(A.coef + (k)), __ldg(A.coef + (k - 1)),
-                                                         have_prev, sb, &stg, s_red, bad);
-          }
-        }
-        if (!barrier()) { run = false; break; }
+        k -= ns;
+        ns = hm;
         virt = false;
         const int o1 = r1, o2 = r2;
-        r1 = f2;
-        r2 = f1;
+        r1 = f1;
+        r2 = f2;
         f1 = o1;
         f2 = o2;
       }
@@ -735,6 +684,10 @@ cudaError_t heat_loop_launch(const HeatPlan& hp, const HeatBuffers& B, int ek, c
   A.tiles_x = (int)tg.x;
   A.ntiles = (int)(tg.x * tg.y);
   A.pairs = pairs;
+  // four steps per barrier while every tile has its own block (the barriers
+  // dominate), two where blocks take several tiles (the recomputed halo's
+  // FP64 work would)
+  A.steps = A.ntiles <= G ? HMAX : 2;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3(HBX, HBY);
