@@ -40,9 +40,26 @@ __device__ __forceinline__ bool is_free(const HeatGeom& g, int i) {
   return g.mask == nullptr || g.mask[i] == 0;
 }
 
-// The per-cell arithmetic of the recurrence, written with explicit roundings
-// so that every kernel below (per phase or persistent) performs the same
-// operations whatever the compiler contracts.
+// ---- the per-cell arithmetic of the recurrence ----
+// Written with explicit roundings, so that every kernel below (per phase or
+// persistent) performs the same operations whatever the compiler contracts.
+// The iterates W are FP64 for both precisions: a high-degree recurrence
+// cancels large intermediate terms in the far field, where the kernel's tail
+// is many orders below its peak, so single precision there costs digits (the
+// flows' error grew 16-fold with FP32 iterates).  Double-float iterates (two
+// floats, ~48 significant bits, on the FP32 pipe) were measured slower than
+// FP64 on GB300 (100^2: 4.8k against 5.3k pairs/s): the stencil is bound by
+// the latency of its dependent chains, which double-float arithmetic
+// lengthens, not by the FP64 pipe's throughput.
+template <typename T> struct HeatIter { using W = double; };
+
+// constants and inputs as iterates
+template <typename W> __device__ __forceinline__ W wc(double d) { return d; }
+__device__ __forceinline__ double wv(double v) { return v; }
+template <typename W> __device__ __forceinline__ W wzero() { return 0.0; }
+// c v (the first iterate b_D = c_D v)
+__device__ __forceinline__ double wscale(double c, double v) { return __dmul_rn(c, v); }
+
 // acc + c (vi - vj): one neighbour's term of A v
 __device__ __forceinline__ double nb_term(double acc, double c, double vi, double vj) {
   return __fma_rn(c, __dsub_rn(vi, vj), acc);
@@ -53,94 +70,107 @@ __device__ __forceinline__ double cl_value(double ck, double v, double s, double
   return __dsub_rn(__fma_rn(ck, v, __dmul_rn(s, __fma_rn(-theta, b1, Ab))), b2);
 }
 
+// The operator's output is clamped at 0: xi~ is positive, and the expansion's
+// error is normwise (~1e-15 of the largest entry), so where the true kernel
+// tail lies below it the sum can come out slightly negative; 0 there is the
+// same underflow the Gaussian kernel meets far from its support (the b-update
+// and the prox treat it so).  NaN passes through.
+template <typename T> __device__ __forceinline__ T close_out(double r) {
+  return (T)(r < 0.0 ? 0.0 : r);
+}
+
 // (A v)_i = v_i + sum over free neighbours j of c_dir (v_i - v_j)
-__device__ __forceinline__ double apply_A(const HeatGeom& g, const double* v, int x, int y) {
+template <typename W>
+__device__ __forceinline__ W apply_A(const HeatGeom& g, const W* v, int x, int y, W cx, W cy) {
   const int i = y * g.nx + x;
-  const double vi = v[i];
-  double acc = vi;
-  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, vi, v[i - 1]);
-  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, vi, v[i + 1]);
-  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, vi, v[i - g.nx]);
-  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, vi, v[i + g.nx]);
+  const W vi = v[i];
+  W acc = vi;
+  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, cx, vi, v[i - 1]);
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, cx, vi, v[i + 1]);
+  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, cy, vi, v[i - g.nx]);
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, cy, vi, v[i + g.nx]);
   return acc;
 }
 
-// The Clenshaw iterates are FP64 for both precisions: a high-degree
-// recurrence cancels large intermediate terms in the far field, where the
-// kernel's tail is many orders below its peak, and single precision there
-// costs digits that the L separate solves keep; the stencil work is a small
-// share of a launch at the grid sizes of this operator.
-
-// The operator's output is clamped at 0: xi~ is positive, and the expansion's
-// error is normwise (~1e-15 of the largest entry in FP64), so where the true
-// kernel tail lies below it the sum can come out slightly negative; 0 there
-// is the same underflow the Gaussian kernel meets far from its support (the
-// b-update and the prox treat it so).  NaN passes through.
-__device__ __forceinline__ double close_value(double r) { return r < 0.0 ? 0.0 : r; }
-
 // First Clenshaw step: b_D = c_D v, b_{D+1} = 0 (v is 0 on the mask).
 template <typename T>
-__global__ void __launch_bounds__(HBX * HBY) heat_cl_init(const T* v, double* b1, double* b2,
+__global__ void __launch_bounds__(HBX * HBY) heat_cl_init(const T* v, void* b1_, void* b2_,
                                                           HeatGeom g, double cD, Ctrl* ctrl,
                                                           const double* part, int nparts,
                                                           int decide) {
+  using W = typename HeatIter<T>::W;
+  W* b1 = (W*)b1_;
+  W* b2 = (W*)b2_;
   __shared__ int s_it;
   if (stop_gate(ctrl, part, nparts, decide != 0, &s_it)) return;
   const int xx = blockIdx.x * HBX + threadIdx.x, yy = blockIdx.y * HBY + threadIdx.y;
   if (xx >= g.nx || yy >= g.ny) return;
   const int i = yy * g.nx + xx;
-  b1[i] = is_free(g, i) ? __dmul_rn(cD, (double)v[i]) : 0.0;
-  b2[i] = 0.0;
+  b1[i] = is_free(g, i) ? wscale(wc<W>(cD), wv(v[i])) : wzero<W>();
+  b2[i] = wzero<W>();
 }
 
-// One Clenshaw step out = c_k v + s (B b1) - b2 with B = (A - theta Id) / delta:
-// s = 2 inside the recurrence (O = double), s = 1 for the closing step (O = T).
-// out may alias b2 (each thread reads its own b2 entry before writing it); b1
-// is read at the 5-point stencil and is not written.
-template <typename T, typename O, bool CLOSE>
-__global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const double* b1,
-                                                          const double* b2, O* out, HeatGeom g,
-                                                          double ck, double s_over_delta,
-                                                          double theta, Ctrl* ctrl) {
+// One Clenshaw step c_k v + s (B b1) - b2 with B = (A - theta Id) / delta:
+// s = 2 inside the recurrence (iterate out), s = 1 for the closing step
+// (CLOSE: T out, the operator's output).  out may alias b2 (each thread reads
+// its own b2 entry before writing it); b1 is read at the 5-point stencil and
+// is not written.
+template <typename T, bool CLOSE>
+__global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const void* b1_,
+                                                          const void* b2_, void* out_, HeatGeom g,
+                                                          double ck_, double s_over_delta,
+                                                          double theta_, Ctrl* ctrl) {
+  using W = typename HeatIter<T>::W;
+  const W* b1 = (const W*)b1_;
+  const W* b2 = (const W*)b2_;
   __shared__ int s_it;
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
   const int xx = blockIdx.x * HBX + threadIdx.x, yy = blockIdx.y * HBY + threadIdx.y;
   if (xx >= g.nx || yy >= g.ny) return;
   const int i = yy * g.nx + xx;
   if (!is_free(g, i)) {
-    out[i] = O(0);
+    if (CLOSE) ((T*)out_)[i] = T(0);
+    else ((W*)out_)[i] = wzero<W>();
     return;
   }
-  const double Ab = apply_A(g, b1, xx, yy);
-  const double r = cl_value(ck, (double)v[i], s_over_delta, Ab, theta, b1[i], b2[i]);
-  out[i] = (O)(CLOSE ? close_value(r) : r);
+  const W cx = wc<W>(g.cx), cy = wc<W>(g.cy);
+  const W Ab = apply_A<W>(g, b1, xx, yy, cx, cy);
+  const W r = cl_value(wc<W>(ck_), wv(v[i]), wc<W>(s_over_delta), Ab, wc<W>(theta_), b1[i], b2[i]);
+  if (CLOSE) ((T*)out_)[i] = close_out<T>(r);
+  else ((W*)out_)[i] = r;
 }
 
 // Two Clenshaw steps in one launch: b_k on the block's tile plus a one-cell
 // halo (shared memory), then b_{k-1} on the tile from it.  Reads b_{k+1} (at a
 // two-cell halo) and b_{k+2}; writes b_k (o1) and b_{k-1} (o2), buffers that no
 // block of this launch reads.  The second step is the closing one (s2 = 1 /
-// delta, O = T, o2 = the operator's output) when k - 1 = 0.
-template <typename T, typename O, bool CLOSE>
-__global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const double* b1,
-                                                           const double* b2, double* o1, O* o2,
-                                                           HeatGeom g, double ck, double ck1,
-                                                           double s2, double theta, Ctrl* ctrl) {
+// delta, CLOSE: o2 = the operator's output, of type T) when k - 1 = 0.
+template <typename T, bool CLOSE>
+__global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const void* b1_,
+                                                           const void* b2_, void* o1_, void* o2_,
+                                                           HeatGeom g, double ck_, double ck1_,
+                                                           double s2_, double theta_, Ctrl* ctrl) {
+  using W = typename HeatIter<T>::W;
+  const W* b1 = (const W*)b1_;
+  const W* b2 = (const W*)b2_;
+  W* o1 = (W*)o1_;
   constexpr int RX = HBX + 2, RY = HBY + 2;
-  __shared__ double sb[RY][RX];
+  __shared__ W sb[RY][RX];
   __shared__ int s_it;
   if (stop_gate(ctrl, nullptr, 0, false, &s_it)) return;
+  const W cx = wc<W>(g.cx), cy = wc<W>(g.cy), theta = wc<W>(theta_);
+  const W two = wc<W>(g.two_over_delta), ck = wc<W>(ck_);
   const int x0 = blockIdx.x * HBX, y0 = blockIdx.y * HBY;
   const int tid = threadIdx.y * HBX + threadIdx.x;
   for (int idx = tid; idx < RX * RY; idx += HBX * HBY) {
     const int ry = idx / RX, rx = idx - ry * RX;
     const int x = x0 + rx - 1, y = y0 + ry - 1;
-    double val = 0.0;
+    W val = wzero<W>();
     if (x >= 0 && x < g.nx && y >= 0 && y < g.ny) {
       const int i = y * g.nx + x;
       if (is_free(g, i)) {
-        const double Ab = apply_A(g, b1, x, y);
-        val = cl_value(ck, (double)v[i], g.two_over_delta, Ab, theta, b1[i], b2[i]);
+        const W Ab = apply_A<W>(g, b1, x, y, cx, cy);
+        val = cl_value(ck, wv(v[i]), two, Ab, theta, b1[i], b2[i]);
       }
     }
     sb[ry][rx] = val;
@@ -150,20 +180,22 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const dou
   if (x >= g.nx || y >= g.ny) return;
   const int i = y * g.nx + x;
   const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;
-  const double c = sb[ty][tx];
+  const W c = sb[ty][tx];
   o1[i] = c;
   if (!is_free(g, i)) {
-    o2[i] = O(0);
+    if (CLOSE) ((T*)o2_)[i] = T(0);
+    else ((W*)o2_)[i] = wzero<W>();
     return;
   }
   // A b_k at (x, y) from the tile: the neighbour tests of apply_A
-  double acc = c;
-  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, g.cx, c, sb[ty][tx - 1]);
-  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, g.cx, c, sb[ty][tx + 1]);
-  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, g.cy, c, sb[ty - 1][tx]);
-  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, g.cy, c, sb[ty + 1][tx]);
-  const double r = cl_value(ck1, (double)v[i], s2, acc, theta, c, b1[i]);
-  o2[i] = (O)(CLOSE ? close_value(r) : r);
+  W acc = c;
+  if (x > 0 && is_free(g, i - 1)) acc = nb_term(acc, cx, c, sb[ty][tx - 1]);
+  if (x + 1 < g.nx && is_free(g, i + 1)) acc = nb_term(acc, cx, c, sb[ty][tx + 1]);
+  if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, cy, c, sb[ty - 1][tx]);
+  if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, cy, c, sb[ty + 1][tx]);
+  const W r = cl_value(wc<W>(ck1_), wv(v[i]), wc<W>(s2_), acc, theta, c, b1[i]);
+  if (CLOSE) ((T*)o2_)[i] = close_out<T>(r);
+  else ((W*)o2_)[i] = r;
 }
 
 // b = q / Y (0 where q = 0 or Y is not a normal number), with the residual
@@ -242,7 +274,7 @@ struct HeatLoopArgs {
   const double* coef;      // c_0 .. c_D
   int D;
   double theta, inv_delta;
-  double* d[4];            // Clenshaw iterates (FP64)
+  void* d[4];              // Clenshaw iterates (HeatIter<T>::W, 8 bytes per cell)
   const T* q;
   T* a;
   T* b;
@@ -263,9 +295,8 @@ __device__ __forceinline__ T ld_plain(const T* p) { return *p; }
 // The closing step's output r at cell i of the grid, into the b-update (app 0)
 // or the prox (app 1).
 template <typename T, int EK>
-__device__ __forceinline__ void heat_close_cell(const HeatLoopArgs<T>& A, int app, int i, double r,
+__device__ __forceinline__ void heat_close_cell(const HeatLoopArgs<T>& A, int app, int i, T y,
                                                 bool have_prev, T& res, int& bad) {
-  const T y = (T)close_value(r);
   if (app == 0) {
     const T qi = __ldg(A.q + i);
     if (have_prev) res = abs_residual<T>(ld_plain(A.b + i), y, qi);
@@ -289,19 +320,23 @@ __device__ __forceinline__ void heat_close_cell(const HeatLoopArgs<T>& A, int ap
 // and the one before to o_prev on the tile, or, when its last step is step 0,
 // closes into the epilogue.
 constexpr int HMAX = 4;                      // Clenshaw steps per grid barrier
+constexpr int HLT = HBX * HBY * 4;           // threads of a persistent block: four per tile
+                                             // cell in the halo phases (the work is latency
+                                             // bound; 2 or 8 per cell measured slower)
 constexpr int HSX = HBX + 2 * HMAX, HSY = HBY + 2 * HMAX;
+template <typename W>
 struct HeatStageH {
-  double v[HSY][HSX];
-  double b1[HSY][HSX];
-  double b2[HSY][HSX];
+  W v[HSY][HSX];
+  W b1[HSY][HSX];
+  W b2[HSY][HSX];
   unsigned char fr[HSY][HSX];
 };
 
-template <typename T, int EK>
+template <typename T, int EK, typename W>
 __device__ __forceinline__ void heat_tile_steps(const HeatLoopArgs<T>& A, int app, int t, const T* v,
-                                                const double* b1, const double* b2, double* o_new,
-                                                double* o_prev, bool virt, double c1v, int k,
-                                                int ns, bool have_prev, HeatStageH& S, double* s_red,
+                                                const W* b1, const W* b2, W* o_new, W* o_prev,
+                                                bool virt, W c1v, int k, int ns, bool have_prev,
+                                                HeatStageH<W>& S, W cx, W cy, W theta, double* s_red,
                                                 int& bad) {
   constexpr int H = HMAX;
   const HeatGeom& g = A.g;
@@ -310,14 +345,14 @@ __device__ __forceinline__ void heat_tile_steps(const HeatLoopArgs<T>& A, int ap
   const int tid = threadIdx.y * HBX + threadIdx.x;
   // stage the tile and an ns-cell halo (at offset H - ns in the arrays)
   const int sx = HBX + 2 * ns, sy = HBY + 2 * ns;
-  for (int idx = tid; idx < sx * sy; idx += HBX * HBY) {
+  for (int idx = tid; idx < sx * sy; idx += HLT) {
     const int ey = H - ns + idx / sx, ex = H - ns + idx % sx;
     const int xx = x0 + ex - H, yy = y0 + ey - H;
-    double vv = 0.0, bb1 = 0.0, bb2 = 0.0;
+    W vv = wzero<W>(), bb1 = wzero<W>(), bb2 = wzero<W>();
     unsigned char f = 0;
     if (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) {
       const int j = yy * g.nx + xx;
-      vv = (double)ld_plain(v + j);
+      vv = wv(ld_plain(v + j));
       if (!virt) {
         bb1 = ld_plain(b1 + j);
         bb2 = ld_plain(b2 + j);
@@ -325,62 +360,62 @@ __device__ __forceinline__ void heat_tile_steps(const HeatLoopArgs<T>& A, int ap
       f = g.mask == nullptr || g.mask[j] == 0;
     }
     S.v[ey][ex] = vv;
-    S.b1[ey][ex] = virt ? __dmul_rn(c1v, vv) : bb1;
+    S.b1[ey][ex] = virt ? wscale(c1v, vv) : bb1;
     S.b2[ey][ex] = bb2;
     S.fr[ey][ex] = f;
   }
   __syncthreads();
-  double (*cur1)[HSX] = S.b1;
-  double (*cur2)[HSX] = S.b2;
+  W (*cur1)[HSX] = S.b1;
+  W (*cur2)[HSX] = S.b2;
   T res = T(0);
   for (int st = 0; st < ns; ++st) {
     const int kk = k - st;
-    const double ck = __ldg(A.coef + kk);
-    const double sc = kk == 0 ? A.inv_delta : g.two_over_delta;
+    const W ck = wc<W>(__ldg(A.coef + kk));
+    const W sc = wc<W>(kk == 0 ? A.inv_delta : g.two_over_delta);
     if (st < ns - 1) {
       // b_kk on the tile and an (ns - 1 - st)-cell halo, into cur2's array
       const int h = ns - 1 - st;
       const int rx = HBX + 2 * h, ry = HBY + 2 * h;
-      for (int idx = tid; idx < rx * ry; idx += HBX * HBY) {
+      for (int idx = tid; idx < rx * ry; idx += HLT) {
         const int yy = idx / rx, xx = idx - yy * rx;
         const int ey = H - h + yy, ex = H - h + xx;
-        double val = 0.0;
+        W val = wzero<W>();
         if (S.fr[ey][ex]) {
-          const double bc = cur1[ey][ex];
-          double Ab = bc;
-          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex - 1]);
-          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex + 1]);
-          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey - 1][ex]);
-          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey + 1][ex]);
-          val = cl_value(ck, S.v[ey][ex], sc, Ab, A.theta, bc, cur2[ey][ex]);
+          const W bc = cur1[ey][ex];
+          W Ab = bc;
+          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, cx, bc, cur1[ey][ex - 1]);
+          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, cx, bc, cur1[ey][ex + 1]);
+          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, cy, bc, cur1[ey - 1][ex]);
+          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, cy, bc, cur1[ey + 1][ex]);
+          val = cl_value(ck, S.v[ey][ex], sc, Ab, theta, bc, cur2[ey][ex]);
         }
         cur2[ey][ex] = val;
       }
       __syncthreads();
-      double (*tmp)[HSX] = cur2;
+      W (*tmp)[HSX] = cur2;
       cur2 = cur1;
       cur1 = tmp;
     } else {
       // the last step, on the tile: written out, or closed into the epilogue
       const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-      if (x < g.nx && y < g.ny) {
+      if (threadIdx.y < HBY && x < g.nx && y < g.ny) {
         const int i = y * g.nx + x;
         const int ey = H + threadIdx.y, ex = H + threadIdx.x;
-        double r = 0.0;
+        W r = wzero<W>();
         if (S.fr[ey][ex]) {
-          const double bc = cur1[ey][ex];
-          double Ab = bc;
-          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex - 1]);
-          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, g.cx, bc, cur1[ey][ex + 1]);
-          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey - 1][ex]);
-          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, g.cy, bc, cur1[ey + 1][ex]);
-          r = cl_value(ck, S.v[ey][ex], sc, Ab, A.theta, bc, cur2[ey][ex]);
+          const W bc = cur1[ey][ex];
+          W Ab = bc;
+          if (S.fr[ey][ex - 1]) Ab = nb_term(Ab, cx, bc, cur1[ey][ex - 1]);
+          if (S.fr[ey][ex + 1]) Ab = nb_term(Ab, cx, bc, cur1[ey][ex + 1]);
+          if (S.fr[ey - 1][ex]) Ab = nb_term(Ab, cy, bc, cur1[ey - 1][ex]);
+          if (S.fr[ey + 1][ex]) Ab = nb_term(Ab, cy, bc, cur1[ey + 1][ex]);
+          r = cl_value(ck, S.v[ey][ex], sc, Ab, theta, bc, cur2[ey][ex]);
         }
         if (kk == 0) {
-          heat_close_cell<T, EK>(A, app, i, r, have_prev, res, bad);
+          heat_close_cell<T, EK>(A, app, i, close_out<T>(r), have_prev, res, bad);
         } else {
           o_new[i] = r;
-          o_prev[i] = S.fr[ey][ex] ? cur1[ey][ex] : 0.0;
+          o_prev[i] = S.fr[ey][ex] ? cur1[ey][ex] : wzero<W>();
         }
       }
     }
@@ -393,8 +428,9 @@ __device__ __forceinline__ void heat_tile_steps(const HeatLoopArgs<T>& A, int ap
 }
 
 template <typename T, int EK>
-__global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A) {
-  __shared__ HeatStageH stg;
+__global__ void __launch_bounds__(HLT) heat_loop_kernel(HeatLoopArgs<T> A) {
+  using W = typename HeatIter<T>::W;
+  __shared__ HeatStageH<W> stg;
   __shared__ double s_red[33];
   __shared__ int s_stop, s_fault, s_it0, s_maxit;
   __shared__ unsigned s_base;
@@ -472,7 +508,9 @@ __global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A)
       }
       const T* v = app == 0 ? A.a : A.b;
       const bool have_prev = app == 0 && it > 0;
-      const double cD = __ldg(A.coef + D);
+      const W cD = wc<W>(__ldg(A.coef + D));
+      const W cx = wc<W>(A.g.cx), cy = wc<W>(A.g.cy), theta = wc<W>(A.theta);
+      W* dd[4] = {(W*)A.d[0], (W*)A.d[1], (W*)A.d[2], (W*)A.d[3]};
       // phases of up to HMAX steps from the first iterates (b_D = c_D v,
       // b_{D+1} = 0), the first one taking D mod HMAX steps; buffers: read
       // the newest / previous iterates from d[r1] / d[r2], write d[f1] / d[f2]
@@ -483,8 +521,9 @@ __global__ void __launch_bounds__(HBX * HBY) heat_loop_kernel(HeatLoopArgs<T> A)
       bool virt = true;
       while (k >= 0) {
         for (int t = blockIdx.x; t < A.ntiles; t += G)
-          heat_tile_steps<T, EK>(A, app, t, v, virt ? nullptr : A.d[r1], virt ? nullptr : A.d[r2],
-                                 A.d[f1], A.d[f2], virt, cD, k, ns, have_prev, stg, s_red, bad);
+          heat_tile_steps<T, EK, W>(A, app, t, v, virt ? nullptr : dd[r1], virt ? nullptr : dd[r2],
+                                    dd[f1], dd[f2], virt, cD, k, ns, have_prev, stg, cx, cy, theta,
+                                    s_red, bad);
         if (!barrier()) { run = false; break; }
         k -= ns;
         ns = hm;
@@ -594,7 +633,7 @@ cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T*
   const double inv_delta = hp.delta > 0 ? 1.0 / hp.delta : 0.0;   // delta = 0: p(A) = c_0 Id
   HeatGeom g{nx, ny, hp.cx, hp.cy, mask, 2.0 * inv_delta};
   const dim3 grid = heat_grid(nx, ny), block(HBX, HBY);
-  double* d[4] = {(double*)B.d[0], (double*)B.d[1], (double*)B.d[2], (double*)B.d[3]};
+  void* d[4] = {B.d[0], B.d[1], B.d[2], B.d[3]};   // iterates (8 bytes per cell)
   const int D = hp.D;
   // b_{k+1} in d[r1], b_{k+2} in d[r2]; d[f1], d[f2] free
   int r1 = 0, r2 = 1, f1 = 2, f2 = 3;
@@ -603,24 +642,24 @@ cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T*
   int k = D - 1;
   if (D % 2 == 1) {   // one single step so that the rest pairs up
     if (k == 0) {
-      heat_cl_step<T, T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], out_x, g, hp.coef[0],
-                                                 inv_delta, hp.theta, ctrl);
+      heat_cl_step<T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], out_x, g, hp.coef[0],
+                                                    inv_delta, hp.theta, ctrl);
       return cudaGetLastError();
     }
-    heat_cl_step<T, double, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[r2], g, hp.coef[k],
-                                                    2.0 * inv_delta, hp.theta, ctrl);
+    heat_cl_step<T, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[r2], g, hp.coef[k],
+                                                   2.0 * inv_delta, hp.theta, ctrl);
     std::swap(r1, r2);
     --k;
   }
   for (; k >= 1; k -= 2) {
     if (k == 1) {   // steps 1 and the closing 0
-      heat_cl_step2<T, T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], out_x, g, hp.coef[1],
-                                                  hp.coef[0], inv_delta, hp.theta, ctrl);
+      heat_cl_step2<T, true><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], out_x, g, hp.coef[1],
+                                                     hp.coef[0], inv_delta, hp.theta, ctrl);
       break;
     }
-    heat_cl_step2<T, double, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], d[f2], g,
-                                                     hp.coef[k], hp.coef[k - 1],
-                                                     2.0 * inv_delta, hp.theta, ctrl);
+    heat_cl_step2<T, false><<<grid, block, 0, st>>>(in, d[r1], d[r2], d[f1], d[f2], g,
+                                                    hp.coef[k], hp.coef[k - 1],
+                                                    2.0 * inv_delta, hp.theta, ctrl);
     // b_{k-1} (f2) and b_k (f1) are the next step's b_{k'+1}, b_{k'+2}
     const int o1 = r1, o2 = r2;
     r1 = f2;
@@ -652,7 +691,7 @@ int heat_loop_grid(int nx, int ny, bool fp64, int ek) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (!coop || sms <= 0) return 0;
   void* fn = fp64 ? heat_loop_fn<double>(ek) : heat_loop_fn<float>(ek);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HBX * HBY, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, HLT, 0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -672,7 +711,7 @@ cudaError_t heat_loop_launch(const HeatPlan& hp, const HeatBuffers& B, int ek, c
   A.D = hp.D;
   A.theta = hp.theta;
   A.inv_delta = inv_delta;
-  for (int i = 0; i < 4; ++i) A.d[i] = (double*)B.d[i];
+  for (int i = 0; i < 4; ++i) A.d[i] = B.d[i];
   A.q = q;
   A.a = a;
   A.b = b;
@@ -690,7 +729,7 @@ cudaError_t heat_loop_launch(const HeatPlan& hp, const HeatBuffers& B, int ek, c
   A.steps = A.ntiles <= G ? HMAX : 2;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3(HBX, HBY);
+  cfg.blockDim = dim3(HBX, HLT / HBX);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
