@@ -104,7 +104,7 @@ typedef struct jko_params {
   double tau;       /* JKO step size tau > 0 (Eq. def-jko-operator) */
   double tol;       /* L1 marginal residual tolerance >= 0 (Sec. 3.4) */
   int max_iter;     /* maximum (odd, even) pairs per step, >= 1 */
-  int check_every;  /* iterations between host polls of the stop flag (0 = default 16);
+  int check_every;  /* iterations between host polls of the stop flag (0 = default 4);
                        handles on the persistent loop kernel run a step's whole budget
                        in one launch that stops itself, and ignore it */
   int precision;    /* a jko_precision value */

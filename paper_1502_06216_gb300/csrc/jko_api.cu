@@ -944,21 +944,45 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     CK(h, jko::launch_fill<T>((T*)h->a, T(1), N, st));   // cold start a = 1 (Sec. 3.4)
   }
 
-  // chunks: launch the expected number at once, then poll with one in flight
+  // chunks: launch the number the last step needed at once, the last one with
+  // the finalisation behind it, and wait once; only a step that runs longer
+  // than that polls on, with one chunk in flight
   h->kernels = (validate ? 1 : 0) + 1 + (h->tc ? 0 : 1) + (p_out ? 2 : 1);
+  // the finalisation: the FP64 mass and max p / kappa of the step's p, and p
+  // written out (renormalised)
+  auto finalize = [&]() -> cudaError_t {
+    cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part,
+                                                    h->part_cap, st);
+    if (e == cudaSuccess && p_out)
+      e = jko::launch_finalize_write<T>((const T*)h->p, p_out, h->ns, h->prm.renormalize,
+                                        h->ctrl, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
+    return e;
+  };
   // runs chunks until the step reports a stop; `fin`: the FP32 finish chunks.
-  // Returns the stop state read back (h->poll slot) through *done.
-  auto run_chunks = [&](bool fin, int ahead_pairs, int* done, int* it) -> jko_status {
+  // Returns the stop state read back (h->poll slot) through *done and *it, and
+  // through *final_slot the poll slot holding the whole control block after
+  // the finalisation when the step stopped within the chunks launched first
+  // (-1 otherwise: the caller finalises).
+  auto run_chunks = [&](bool fin, int ahead_pairs, int* done, int* it,
+                        int* final_slot) -> jko_status {
     const int C = fin ? kFinishChunk : h->chunk_iters;
     const int max_chunks = (h->prm.max_iter + 1 + C - 1) / C + 2;
-    int ahead = ahead_pairs / C;
+    // the stop is decided in the pair after the last one completed
+    int ahead = (ahead_pairs + 1 + C - 1) / C;
     int launched = 0, polled = 0;
-    auto launch = [&]() -> cudaError_t {
+    *final_slot = -1;
+    auto launch = [&](bool with_final) -> cudaError_t {
       h->kernels += fin ? 4LL * C : (h->use_loop ? 1LL : pair_kernels(h) * C);
       cudaError_t e = fin ? cudaGraphLaunch(h->chunk_fin, st) : launch_chunk(h, st);
       if (e != cudaSuccess) return e;
+      if (with_final) {
+        e = finalize();
+        if (e != cudaSuccess) return e;
+      }
       const int slot = launched & 1;
-      e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, 16, cudaMemcpyDeviceToHost, st);
+      e = cudaMemcpyAsync(&h->poll[slot], h->ctrl, with_final ? sizeof(Ctrl) : 16,
+                          cudaMemcpyDeviceToHost, st);
       if (e != cudaSuccess) return e;
       e = cudaEventRecord(h->ev_poll[slot], st);
       ++launched;
@@ -966,11 +990,22 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     };
     if (ahead < 1) ahead = 1;
     if (ahead > max_chunks) ahead = max_chunks;
-    for (int i = 0; i < ahead; ++i) CK(h, launch());
+    for (int i = 0; i < ahead; ++i) CK(h, launch(!fin && i == ahead - 1));
+    {
+      const int slot = (launched - 1) & 1;
+      CK(h, cudaEventSynchronize(h->ev_poll[slot]));
+      polled = launched;
+      *done = h->poll[slot].done;
+      *it = h->poll[slot].it;
+      if (*done != jko::RUNNING) {
+        if (!fin) *final_slot = slot;
+        return JKO_OK;
+      }
+    }
     bool stopped = false;
     while (!stopped) {
       // keep one chunk in flight while waiting for the oldest poll we need
-      if (launched - polled < 2 && launched < max_chunks) CK(h, launch());
+      if (launched - polled < 2 && launched < max_chunks) CK(h, launch(false));
       // wait for the newest-but-one launched chunk's poll (or the newest if only one)
       const int target = launched - 1 - ((launched - polled) >= 2 ? 1 : 0);
       const int slot = target & 1;
@@ -984,8 +1019,8 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     }
     return JKO_OK;
   };
-  int done = jko::RUNNING, it_tc = 0, it_end = 0;
-  jko_status sr = run_chunks(false, h->last_iters, &done, &it_tc);  // chunks surely needed
+  int done = jko::RUNNING, it_tc = 0, it_end = 0, final_slot = -1, fin_slot = -1;
+  jko_status sr = run_chunks(false, h->last_iters, &done, &it_tc, &final_slot);
   if (sr != JKO_OK) return sr;
   bool finished = false;
   if (done == jko::STALLED && h->prm.finish && h->tc) {
@@ -999,17 +1034,19 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     CK(h, jko::tc_export_scalings(h->tc, (float*)h->a, (float*)h->b, st));
     CK(h, jko::launch_resume(h->ctrl, st));
     h->kernels += 3;
-    sr = run_chunks(true, h->last_fin, &done, &it_end);
+    sr = run_chunks(true, h->last_fin, &done, &it_end, &fin_slot);
     if (sr != JKO_OK) return sr;
     finished = true;
+    final_slot = -1;   // the finalisation launched with the first chunks is stale
   }
 
-  CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part, h->part_cap, st));
-  if (p_out) CK(h, jko::launch_finalize_write<T>((const T*)h->p, p_out, h->ns, h->prm.renormalize, h->ctrl, st));
-  CK(h, cudaEventRecord(h->ev1, st));
-  CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-  CK(h, cudaStreamSynchronize(st));
-  const Ctrl& c = h->poll[0];
+  if (final_slot < 0) {
+    CK(h, finalize());
+    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    final_slot = 0;
+  }
+  const Ctrl& c = h->poll[final_slot];
   jko_status st_out = JKO_OK;
   // nonfinite bit 1: NaN/Inf met by an epilogue; bit 2: a bounded device wait gave up
   if (c.nonfinite & 2) st_out = JKO_ERR_TIMEOUT;
@@ -1118,9 +1155,10 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   h->es = h->fp64 ? 8 : 4;
   h->stream = (cudaStream_t)stream;
   h->heat_L = grid->heat_L;
-  // a heat-kernel pair is 2 (1 + ceil(D / 2)) + 2 launches: short chunks keep the
-  // graph small and the overshoot past the stop a pair or two
-  h->chunk_iters = params->check_every > 0 ? params->check_every : (h->heat_L ? 2 : 16);
+  // pairs per chunk: every pass after the stop is a launch that returns at once
+  // (~1.5 us), so chunks stay short (a heat-kernel pair is 2 (1 + ceil(D / 2)) + 2
+  // launches); the driver launches as many as the last step needed at once
+  h->chunk_iters = params->check_every > 0 ? params->check_every : (h->heat_L ? 2 : 4);
   cudaGetDevice(&h->device);
 
   auto fail = [&](jko_status st) {

@@ -167,7 +167,7 @@ def test_handle_info_and_autotuner():
     loop = info(loop=1)
     assert loop["loop"] and loop["resident"] and loop["pairs_per_launch"] == pb.max_iter + 1
     pp = info(loop=2, tile=64)
-    assert not pp["loop"] and pp["pairs_per_launch"] == 16
+    assert not pp["loop"] and pp["pairs_per_launch"] == 4
     a1, a2 = info(), info()
     print("loop", loop, "per-pass", pp, "auto", a1)
     assert a1 == a2
