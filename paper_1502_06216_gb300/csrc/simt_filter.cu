@@ -18,6 +18,8 @@
 // where 16 would leave the grid under two blocks per SM (small images: more
 // threads, each tap sum in the same order, so the same bits).  The taps are
 // the 2r+1 values k(d), d = -r..r, held in shared memory (broadcast reads).
+// The outputs of a block are transposed through shared memory before the
+// epilogue, which then runs along the output rows with coalesced accesses.
 #include "jko_internal.cuh"
 #include "jko_kernels.h"
 
@@ -28,6 +30,19 @@ namespace {
 constexpr int RB_MAX = 16;  // outputs per thread along the filtered axis (or 4)
 constexpr int BJ = 32;   // threads along the contiguous axis
 constexpr int BI = 4;    // thread rows per block
+
+// One element global -> shared by cp.async (L1-allocating); ok = false writes 0
+// and reads nothing.
+template <typename T>
+__device__ __forceinline__ void cp_async_zfill(T* dst, const T* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = ok ? (int)sizeof(T) : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
+               ::"r"(d), "l"(src), "n"((int)sizeof(T)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 // TILE (small images): the block first stages its input rows [i_lo - r, i_lo + BI RB + r)
 // of its 32 columns in shared memory (coalesced, zeros outside the image), so
@@ -76,11 +91,15 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     const int blk_lo = blockIdx.y * BI * RB;
     const int rows = BI * RB + 2 * r + RB;
     const int jc = blockIdx.x * BJ + threadIdx.x;
+    // asynchronous copies, all in flight at once (a load-then-store loop
+    // waits one L2 round trip per row); rows outside the image are zero-filled
     for (int rr = threadIdx.y; rr < rows; rr += BI) {
       const int ii = blk_lo - r + rr;
-      s_in[rr * BJ + threadIdx.x] = (jc < A.n_j && ii >= 0 && ii < n_i)
-                                        ? __ldg(in_img + (size_t)ii * A.n_j + jc) : T(0);
+      const bool ok = jc < A.n_j && ii >= 0 && ii < n_i;
+      cp_async_zfill(s_in + rr * BJ + threadIdx.x,
+                     ok ? in_img + (size_t)ii * A.n_j + jc : in_img, ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (active) {
       // the register window of the untiled pass, refilled from shared memory:
@@ -141,41 +160,41 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     }
   }
 
-  // ---- epilogue: out is [n_j][n_i], this thread owns out[j][i0 .. i0+RB) ----
+  // ---- epilogue: out is [n_j][n_i].  The block's outputs out[jb, jb + BJ)
+  // [ib, ib + W) pass through shared memory and are read back along i, so
+  // that a warp reads and writes whole row segments (W >= 32: 128 bytes; W = 16:
+  // two of 64) instead of one element in each of 32 rows ----
+  constexpr int W = BI * RB;
+  __shared__ T s_o[BJ][W + 1];   // +1: conflict-free column writes
+#pragma unroll
+  for (int o = 0; o < RB; ++o) s_o[threadIdx.x][threadIdx.y * RB + o] = acc[o];
+  __syncthreads();
+  const int jb = blockIdx.x * BJ;
+  const int ib = blockIdx.y * W;
   T res_t = T(0);  // this thread's residual terms, in the working precision
   int bad = 0;
-  if (active) {
-    const size_t rowoff = (size_t)j * A.n_i;
-    const int nout = (A.n_i - i0) < RB ? (A.n_i - i0) : RB;
-    if (EPI == EPI_STORE) {
+  const bool have_prev = s_it > 0;
 #pragma unroll
-      for (int o = 0; o < RB; ++o)
-        if (o < nout) out_img[rowoff + i0 + o] = acc[o];
-    } else if (EPI == EPI_B) {
-      const bool have_prev = s_it > 0;
-#pragma unroll
-      for (int o = 0; o < RB; ++o) {
-        if (o < nout) {
-          const size_t idx = rowoff + i0 + o;
-          const T Y = acc[o];
-          const T qv = q_img[idx];
-          if (have_prev) res_t += abs_residual<T>(out_img[idx], Y, qv);
-          const T bn = b_update<T>(qv, Y);
-          bad |= !dev_finite(bn);
-          out_img[idx] = bn;
-        }
-      }
-    } else {  // EPI_A
-#pragma unroll
-      for (int o = 0; o < RB; ++o) {
-        if (o < nout) {
-          const size_t idx = rowoff + i0 + o;
-          const T s = acc[o];
-          const T a = prox_ratio<T, EK>(P, (int)idx, s);
-          bad |= !dev_finite(a);
-          A.out[idx] = a;
-          A.p[idx] = a * s;
-        }
+  for (int k = 0; k < RB; ++k) {
+    const int e = tid + k * BJ * BI;
+    const int jl = e / W;
+    const int il = e % W;
+    if (jb + jl < A.n_j && ib + il < A.n_i) {
+      const size_t idx = (size_t)(jb + jl) * A.n_i + (ib + il);
+      const T v = s_o[jl][il];
+      if (EPI == EPI_STORE) {
+        out_img[idx] = v;
+      } else if (EPI == EPI_B) {
+        const T qv = q_img[idx];
+        if (have_prev) res_t += abs_residual<T>(out_img[idx], v, qv);
+        const T bn = b_update<T>(qv, v);
+        bad |= !dev_finite(bn);
+        out_img[idx] = bn;
+      } else {  // EPI_A
+        const T a = prox_ratio<T, EK>(P, (int)idx, v);
+        bad |= !dev_finite(a);
+        A.out[idx] = a;
+        A.p[idx] = a * v;
       }
     }
   }
