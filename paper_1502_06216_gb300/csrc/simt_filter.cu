@@ -40,14 +40,90 @@ __device__ __forceinline__ void cp_async_zfill(T* dst, const T* src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;"
                ::"r"(d), "l"(src), "n"((int)sizeof(T)), "r"(n) : "memory");
 }
+// Four consecutive taps from a 16-byte aligned shared address.
+__device__ __forceinline__ void ld_shared4(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld_shared4(const double* p, double* o) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+// 16 bytes global -> shared (L2 only); the bytes past nbytes (0..16) are zeroed.
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, int nbytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+               ::"r"(d), "l"(src), "r"(nbytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// TILE (small images): the block first stages its input rows [i_lo - r, i_lo + BI RB + r)
+// One step of the sliding window: acc[o] += k[t0 + dd] x(t0 + o + dd) for
+// dd < RB, the rows of the window being lo[0 .. RB) then hi[0 .. RB).
+template <typename T, int RB>
+__device__ __forceinline__ void tap_step(T (&acc)[RB], const T (&lo)[RB], const T (&hi)[RB],
+                                         const T* taps) {
+  T kk[RB];
+#pragma unroll
+  for (int v = 0; v < RB; v += 4) ld_shared4(taps + v, kk + v);
+#pragma unroll
+  for (int dd = 0; dd < RB; ++dd) {
+#pragma unroll
+    for (int o = 0; o < RB; ++o)
+      acc[o] = fma(kk[dd], (o + dd < RB) ? lo[o + dd] : hi[o + dd - RB], acc[o]);
+  }
+}
+
+// The tap loop of the untiled pass: rows base + t of the column col (row
+// stride ld), three rotating windows (see the kernel); CHECK: rows outside
+// [0, n_i) read as 0, else all rows read lie inside.
+template <typename T, int RB, bool CHECK>
+__device__ __forceinline__ void global_taps(T (&acc)[RB], const T* col, int ld, int base,
+                                            int n_i, int t_lo, int t_hi, const T* s_k) {
+  auto row = [&](int t) -> T {
+    const int ii = base + t;
+    return (!CHECK || (ii >= 0 && ii < n_i)) ? __ldg(col + (size_t)ii * ld) : T(0);
+  };
+  T wa[RB], wb[RB], wc[RB];
+#pragma unroll
+  for (int u = 0; u < RB; ++u) wa[u] = row(t_lo + u);
+#pragma unroll
+  for (int u = 0; u < RB; ++u) wb[u] = row(t_lo + RB + u);
+  for (int t0 = t_lo;;) {
+    if (t0 > t_hi) break;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) wc[u] = row(t0 + 2 * RB + u);
+    tap_step<T, RB>(acc, wa, wb, s_k + t0);
+    t0 += RB;
+    if (t0 > t_hi) break;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) wa[u] = row(t0 + 2 * RB + u);
+    tap_step<T, RB>(acc, wb, wc, s_k + t0);
+    t0 += RB;
+    if (t0 > t_hi) break;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) wb[u] = row(t0 + 2 * RB + u);
+    tap_step<T, RB>(acc, wc, wa, s_k + t0);
+    t0 += RB;
+  }
+}
+
+// Staged input rows of the tiled pass: the block's BI RB output rows, the
+// 2r rows of the taps' reach and 2 RB more that the last window prefetch reads.
+template <int RB>
+__host__ __device__ constexpr int tile_rows(int r) { return BI * RB + 2 * r + 2 * RB; }
+// Shared-memory slots of the taps (2r + 1 + RB, zero-padded), rounded up to
+// four so that the staged rows behind them start 16-byte aligned.
+template <int RB>
+__host__ __device__ constexpr int tap_slots(int r) { return (2 * r + 1 + RB + 3) & ~3; }
+
+// TILE: the block first stages its input rows [i_lo - r, i_lo + BI RB + r + 2 RB)
 // of its 32 columns in shared memory (coalesced, zeros outside the image), so
-// the tap loop reads shared memory instead of a chain of dependent global
-// loads; the same terms are added in the same order either way.
+// the tap loop reads shared memory with no bounds checks instead of guarded
+// global loads; the same terms are added in the same order either way.
 template <typename T, int EPI, int EK, int RB, bool TILE>
 __global__ void __launch_bounds__(BJ * BI)
 filter_pass(PassArgs<T> A, ProxArgs<T> P) {
@@ -82,82 +158,94 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
 #pragma unroll
   for (int o = 0; o < RB; ++o) acc[o] = T(0);
 
+  // Both forms: acc[o] = sum_t k[t] in[i0 + o + t - r][j] over t in
+  // [t_lo, t_hi], rows outside [0, n_i) read as 0.  t_lo is rounded down to a
+  // multiple of 4 so that the taps of a step load four at a time; the terms
+  // added that way multiply zeros (rows above the image) and leave every sum
+  // unchanged.  Three register windows of RB rows rotate, (a, b) -> (b, c) ->
+  // (c, a): a step reads two and loads the rows of the step after next into
+  // the third, so the window slides without register moves and its loads
+  // are in flight during a step's multiply-adds.
   if constexpr (TILE) {
-    // rows [blk_lo - r, blk_lo + BI RB + r + RB) of columns [blockIdx.x BJ, +BJ)
-    // (RB rows beyond the last used one: the window's last refill reads them)
-    T* s_in = s_k + ntap;
+    // rows [blk_lo - r, blk_lo - r + tile_rows) of columns [blockIdx.x BJ, +BJ)
+    T* s_in = s_k + tap_slots<RB>(A.r);
     const int r = A.r;
     const int n_i = A.n_i;
     const int blk_lo = blockIdx.y * BI * RB;
-    const int rows = BI * RB + 2 * r + RB;
-    const int jc = blockIdx.x * BJ + threadIdx.x;
-    // asynchronous copies, all in flight at once (a load-then-store loop
-    // waits one L2 round trip per row); rows outside the image are zero-filled
-    for (int rr = threadIdx.y; rr < rows; rr += BI) {
-      const int ii = blk_lo - r + rr;
-      const bool ok = jc < A.n_j && ii >= 0 && ii < n_i;
-      cp_async_zfill(s_in + rr * BJ + threadIdx.x,
-                     ok ? in_img + (size_t)ii * A.n_j + jc : in_img, ok);
+    const int rows = tile_rows<RB>(r);
+    const int c0 = blockIdx.x * BJ;
+    // asynchronous copies, all in flight at once, zero-filled outside the
+    // image: 16 bytes each where the rows are 16-byte aligned, else one element
+    constexpr int EPC = 16 / (int)sizeof(T);   // elements per 16-byte chunk
+    constexpr int CPR = BJ / EPC;              // chunks per staged row
+    if (A.n_j % EPC == 0 && (reinterpret_cast<uintptr_t>(in_img) & 15) == 0) {
+      for (int q = tid; q < rows * CPR; q += BJ * BI) {
+        const int rr = q / CPR;
+        const int jc = c0 + (q % CPR) * EPC;
+        const int ii = blk_lo - r + rr;
+        int nb = 0;
+        if (ii >= 0 && ii < n_i && jc < A.n_j)
+          nb = (A.n_j - jc < EPC ? A.n_j - jc : EPC) * (int)sizeof(T);
+        cp_async16_zfill(s_in + rr * BJ + (jc - c0),
+                         nb ? in_img + (size_t)ii * A.n_j + jc : in_img, nb);
+      }
+    } else {
+      const int jc = c0 + threadIdx.x;
+      for (int rr = threadIdx.y; rr < rows; rr += BI) {
+        const int ii = blk_lo - r + rr;
+        const bool ok = jc < A.n_j && ii >= 0 && ii < n_i;
+        cp_async_zfill(s_in + rr * BJ + threadIdx.x,
+                       ok ? in_img + (size_t)ii * A.n_j + jc : in_img, ok);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
     if (active) {
-      // the register window of the untiled pass, refilled from shared memory:
       // input row ii sits at row ii - (blk_lo - r) of s_in
       int t_lo = r - i0 - (RB - 1);
       if (t_lo < 0) t_lo = 0;
+      t_lo &= ~3;
       int t_hi = n_i - 1 - i0 + r;
       if (t_hi > 2 * r) t_hi = 2 * r;
       const T* col = s_in + (i0 - blk_lo) * BJ + threadIdx.x;   // row of t = 0
-      T win[2 * RB];
+      T wa[RB], wb[RB], wc[RB];
 #pragma unroll
-      for (int u = 0; u < RB; ++u) win[u] = col[(t_lo + u) * BJ];
-      for (int t0 = t_lo; t0 <= t_hi; t0 += RB) {
+      for (int u = 0; u < RB; ++u) wa[u] = col[(t_lo + u) * BJ];
 #pragma unroll
-        for (int u = 0; u < RB; ++u) win[RB + u] = col[(t0 + RB + u) * BJ];
+      for (int u = 0; u < RB; ++u) wb[u] = col[(t_lo + RB + u) * BJ];
+      for (int t0 = t_lo;;) {
+        if (t0 > t_hi) break;
 #pragma unroll
-        for (int dd = 0; dd < RB; ++dd) {
-          const T k = s_k[t0 + dd];
+        for (int u = 0; u < RB; ++u) wc[u] = col[(t0 + 2 * RB + u) * BJ];
+        tap_step<T, RB>(acc, wa, wb, s_k + t0);
+        t0 += RB;
+        if (t0 > t_hi) break;
 #pragma unroll
-          for (int o = 0; o < RB; ++o) acc[o] = fma(k, win[o + dd], acc[o]);
-        }
+        for (int u = 0; u < RB; ++u) wa[u] = col[(t0 + 2 * RB + u) * BJ];
+        tap_step<T, RB>(acc, wb, wc, s_k + t0);
+        t0 += RB;
+        if (t0 > t_hi) break;
 #pragma unroll
-        for (int u = 0; u < RB; ++u) win[u] = win[RB + u];
+        for (int u = 0; u < RB; ++u) wb[u] = col[(t0 + 2 * RB + u) * BJ];
+        tap_step<T, RB>(acc, wc, wa, s_k + t0);
+        t0 += RB;
       }
     }
   } else if (active) {
-    // acc[o] = sum_{t=0}^{2r} k[t] in[i0 + o + t - r][j]; rows outside [0, n_i) are 0.
     const int r = A.r;
     const int n_i = A.n_i;
     int t_lo = r - i0 - (RB - 1);
     if (t_lo < 0) t_lo = 0;
+    t_lo &= ~3;
     int t_hi = n_i - 1 - i0 + r;
     if (t_hi > 2 * r) t_hi = 2 * r;
     const T* col = in_img + j;
-    const size_t ld = (size_t)A.n_j;
-    T win[2 * RB];
-    int base = i0 - r + t_lo;
-#pragma unroll
-    for (int u = 0; u < RB; ++u) {
-      const int ii = base + u;
-      win[u] = (ii >= 0 && ii < n_i) ? __ldg(col + (size_t)ii * ld) : T(0);
-    }
-    for (int t0 = t_lo; t0 <= t_hi; t0 += RB) {
-      base = i0 - r + t0;
-#pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        const int ii = base + RB + u;
-        win[RB + u] = (ii >= 0 && ii < n_i) ? __ldg(col + (size_t)ii * ld) : T(0);
-      }
-#pragma unroll
-      for (int dd = 0; dd < RB; ++dd) {
-        const T k = s_k[t0 + dd];
-#pragma unroll
-        for (int o = 0; o < RB; ++o) acc[o] = fma(k, win[o + dd], acc[o]);
-      }
-#pragma unroll
-      for (int u = 0; u < RB; ++u) win[u] = win[RB + u];
-    }
+    // rows i0 - r + t for t in [t_lo, t_hi + 3 RB) are read (the last
+    // prefetch included); where all lie inside the image no load is guarded
+    if (i0 - r + t_lo >= 0 && i0 - r + t_hi + 3 * RB <= n_i)
+      global_taps<T, RB, false>(acc, col, A.n_j, i0 - r, n_i, t_lo, t_hi, s_k);
+    else
+      global_taps<T, RB, true>(acc, col, A.n_j, i0 - r, n_i, t_lo, t_hi, s_k);
   }
 
   // ---- epilogue: out is [n_j][n_i].  The block's outputs out[jb, jb + BJ)
@@ -174,6 +262,27 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   T res_t = T(0);  // this thread's residual terms, in the working precision
   int bad = 0;
   const bool have_prev = s_it > 0;
+  // The global reads of all RB elements (q and the old b; e^{-sigma w} of the
+  // crowd prox) are issued before the first write: a write could alias a
+  // later read, so in one loop they would wait one L2 round trip each.
+  T ld0[RB], ld1[RB];
+#pragma unroll
+  for (int k = 0; k < RB; ++k) {
+    const int e = tid + k * BJ * BI;
+    const int jl = e / W;
+    const int il = e % W;
+    ld0[k] = T(0);
+    ld1[k] = T(0);
+    if (jb + jl < A.n_j && ib + il < A.n_i) {
+      const size_t idx = (size_t)(jb + jl) * A.n_i + (ib + il);
+      if (EPI == EPI_B) {
+        ld0[k] = q_img[idx];
+        if (have_prev) ld1[k] = out_img[idx];
+      } else if (EPI == EPI_A && EK == EK_CROWD) {
+        ld0[k] = P.E[idx];
+      }
+    }
+  }
 #pragma unroll
   for (int k = 0; k < RB; ++k) {
     const int e = tid + k * BJ * BI;
@@ -185,13 +294,14 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
       if (EPI == EPI_STORE) {
         out_img[idx] = v;
       } else if (EPI == EPI_B) {
-        const T qv = q_img[idx];
-        if (have_prev) res_t += abs_residual<T>(out_img[idx], v, qv);
+        const T qv = ld0[k];
+        if (have_prev) res_t += abs_residual<T>(ld1[k], v, qv);
         const T bn = b_update<T>(qv, v);
         bad |= !dev_finite(bn);
         out_img[idx] = bn;
       } else {  // EPI_A
-        const T a = prox_ratio<T, EK>(P, (int)idx, v);
+        const T a = EK == EK_CROWD ? prox_ratio_e<T, EK>(P, (int)idx, v, ld0[k])
+                                   : prox_ratio<T, EK>(P, (int)idx, v);
         bad |= !dev_finite(a);
         A.out[idx] = a;
         A.p[idx] = a * v;
@@ -220,7 +330,7 @@ int rb_for(int n_i, int n_j) {
 // Shared memory of the tiled pass: taps + the staged rows.
 template <typename T, int RB>
 size_t tile_smem(int r) {
-  return sizeof(T) * ((size_t)(2 * r + 1 + RB) + (size_t)(BI * RB + 2 * r + RB) * BJ);
+  return sizeof(T) * ((size_t)tap_slots<RB>(r) + (size_t)tile_rows<RB>(r) * BJ);
 }
 
 template <typename T, int EPI, int EK, int RB, bool TILE>
@@ -241,18 +351,22 @@ cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t s
   return cudaGetLastError();
 }
 
-// Small images (the 4-output variant) stage their rows in shared memory; on
-// large ones the untiled pass keeps more blocks resident and wins (1024^2
-// FP32: 5.4k against 5.0k pairs/s tiled, measured).  Flows of a batch keep the
-// 16-output form: there the other flows fill the GPU, and the extra blocks
-// and staged halos cost throughput (256-flow FP32 batch: 17.6k against 6.2k
-// flow-steps/s, measured).
+// A handle alone stages its rows in shared memory: the 4-output form up to
+// 160 KB a block, the 16-output form up to 72 KB (three or four blocks per
+// SM; 1024^2 FP32, r = 147: 51 KB, plain pass 16.4 us against 23.3 untiled,
+// measured), else the untiled 16-output form (FP64 at 1024^2).  Flows of a
+// batch keep the untiled 16-output form: there the other flows fill the GPU,
+// and the extra blocks and staged halos cost throughput (256-flow FP32 batch:
+// 17.6k against 6.2k flow-steps/s with the 4-output tiles, measured).
 template <typename T, int EPI, int EK>
 cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
   constexpr size_t kTileMax = 160 * 1024;
   if (A.latency && rb_for(A.n_i, A.n_j) == 4)
     return tile_smem<T, 4>(A.r) <= kTileMax ? launch_rb<T, EPI, EK, 4, true>(A, P, st)
                                             : launch_rb<T, EPI, EK, 4, false>(A, P, st);
+  constexpr size_t kTile16Max = 72 * 1024;
+  if (A.latency && tile_smem<T, 16>(A.r) <= kTile16Max)
+    return launch_rb<T, EPI, EK, 16, true>(A, P, st);
   return launch_rb<T, EPI, EK, 16, false>(A, P, st);
 }
 
