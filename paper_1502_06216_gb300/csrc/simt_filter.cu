@@ -87,27 +87,15 @@ __device__ __forceinline__ void global_taps(T (&acc)[RB], const T* col, int ld, 
     const int ii = base + t;
     return (!CHECK || (ii >= 0 && ii < n_i)) ? __ldg(col + (size_t)ii * ld) : T(0);
   };
-  T wa[RB], wb[RB], wc[RB];
+  T wa[RB], wb[RB];
 #pragma unroll
   for (int u = 0; u < RB; ++u) wa[u] = row(t_lo + u);
+  for (int t0 = t_lo; t0 <= t_hi; t0 += RB) {
 #pragma unroll
-  for (int u = 0; u < RB; ++u) wb[u] = row(t_lo + RB + u);
-  for (int t0 = t_lo;;) {
-    if (t0 > t_hi) break;
-#pragma unroll
-    for (int u = 0; u < RB; ++u) wc[u] = row(t0 + 2 * RB + u);
+    for (int u = 0; u < RB; ++u) wb[u] = row(t0 + RB + u);
     tap_step<T, RB>(acc, wa, wb, s_k + t0);
-    t0 += RB;
-    if (t0 > t_hi) break;
 #pragma unroll
-    for (int u = 0; u < RB; ++u) wa[u] = row(t0 + 2 * RB + u);
-    tap_step<T, RB>(acc, wb, wc, s_k + t0);
-    t0 += RB;
-    if (t0 > t_hi) break;
-#pragma unroll
-    for (int u = 0; u < RB; ++u) wb[u] = row(t0 + 2 * RB + u);
-    tap_step<T, RB>(acc, wc, wa, s_k + t0);
-    t0 += RB;
+    for (int u = 0; u < RB; ++u) wa[u] = wb[u];
   }
 }
 
@@ -252,10 +240,15 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   // [ib, ib + W) pass through shared memory and are read back along i, so
   // that a warp reads and writes whole row segments (W >= 32: 128 bytes; W = 16:
   // two of 64) instead of one element in each of 32 rows ----
+  // The buffer, [BJ][W + 1] (+1: conflict-free column writes), sits behind
+  // the taps; in the tiled form it reuses the staged rows, whose last reads
+  // the first barrier waits for (one less static buffer: four 1024^2 FP32
+  // blocks per SM instead of three).
   constexpr int W = BI * RB;
-  __shared__ T s_o[BJ][W + 1];   // +1: conflict-free column writes
+  T* s_o = s_k + tap_slots<RB>(A.r);
+  if constexpr (TILE) __syncthreads();
 #pragma unroll
-  for (int o = 0; o < RB; ++o) s_o[threadIdx.x][threadIdx.y * RB + o] = acc[o];
+  for (int o = 0; o < RB; ++o) s_o[threadIdx.x * (W + 1) + threadIdx.y * RB + o] = acc[o];
   __syncthreads();
   const int jb = blockIdx.x * BJ;
   const int ib = blockIdx.y * W;
@@ -290,7 +283,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     const int il = e % W;
     if (jb + jl < A.n_j && ib + il < A.n_i) {
       const size_t idx = (size_t)(jb + jl) * A.n_i + (ib + il);
-      const T v = s_o[jl][il];
+      const T v = s_o[jl * (W + 1) + il];
       if (EPI == EPI_STORE) {
         out_img[idx] = v;
       } else if (EPI == EPI_B) {
@@ -335,7 +328,8 @@ size_t tile_smem(int r) {
 
 template <typename T, int EPI, int EK, int RB, bool TILE>
 cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
-  const size_t smem = TILE ? tile_smem<T, RB>(A.r) : sizeof(T) * (size_t)(2 * A.r + 1 + RB);
+  const size_t smem = TILE ? tile_smem<T, RB>(A.r)
+                           : sizeof(T) * (size_t)(tap_slots<RB>(A.r) + BJ * (BI * RB + 1));
   auto kern = filter_pass<T, EPI, EK, RB, TILE>;
   // opt in well below 48 KB: the kernel's static shared memory (stop gate,
   // reductions) counts against the same default limit
