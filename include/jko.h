@@ -240,7 +240,14 @@ jko_status jko_step(jko_handle* h, const void* q_dev, void* p_out_dev, jko_step_
 /* n_steps steps of the flow from p0 (Eq. smooth-jko).  traj_dev (may be NULL)
  * receives p_1 .. p_n as n_steps consecutive images; p_final_dev (may be NULL)
  * receives p_n.  infos (may be NULL) receives n_steps reports.  Only p0 is
- * validated.  Returns the worst status over the steps. */
+ * validated.  Returns the worst status over the steps.  The steps after the
+ * first are enqueued together and the host waits once: their chunks of pairs
+ * run as a loop on the device (a CUDA graph with a conditional WHILE node that
+ * ends when the step stops, or after the chunk budget of max_iter pairs), with
+ * the same kernels, hence the same results, as jko_step.  Handles whose steps
+ * need a host decision (jko_params.finish on a tensor-core form) run every
+ * step with host-driven chunks.  The first call allocates pinned reports and
+ * events for n_steps; a later longer flow allocates again. */
 jko_status jko_flow(jko_handle* h, const void* p0_dev, int n_steps, void* traj_dev,
                     void* p_final_dev, jko_step_info* infos);
 

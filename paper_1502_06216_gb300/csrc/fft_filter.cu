@@ -148,10 +148,13 @@ fft_pass_kernel(PassArgs<T> A, ProxArgs<T> P, FftArgs<T> F) {
         bad |= !dev_finite(bn);
         A.out[idx] = bn;
       } else {
-        const T a = prox_ratio<T, EK>(P, (int)idx, acc);
+        // xi b >= 0 for b >= 0: an output below 0 is the transform's rounding
+        // (of the line's largest entry) and is taken as 0, so that p >= 0
+        const T sv = acc < T(0) ? T(0) : acc;
+        const T a = prox_ratio<T, EK>(P, (int)idx, sv);
         bad |= !dev_finite(a);
         A.out[idx] = a;
-        A.p[idx] = a * acc;
+        A.p[idx] = a * sv;
       }
     }
   }

@@ -646,6 +646,10 @@ void free_handle(jko_handle* h) {
   if (h->tc) jko::tc_destroy(h->tc);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   if (h->chunk_fin) cudaGraphExecDestroy(h->chunk_fin);
+  if (h->step_loop) cudaGraphExecDestroy(h->step_loop);
+  for (cudaEvent_t ev : h->flow_ev) cudaEventDestroy(ev);
+  if (h->flow_ctrl) cudaFreeHost(h->flow_ctrl);
+  if (h->flow_ctrl_dev) cudaFree(h->flow_ctrl_dev);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
@@ -905,29 +909,17 @@ jko_status setup_simt(jko_handle* h) {
 }
 
 // ---- one step on device buffers of element type T ----
+// The start of a step on stream st: the control block reset, q copied into
+// the handle's image and the scalings' cold start (a = 1, Sec. 3.4) in one
+// launch, or the coupled and tensor-core forms' set-up after it.
 template <typename T>
-jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info, bool validate) {
-  cudaStream_t st = h->stream;
-  const long long N = h->N;
-  ProxArgs<T> P = jko::prox_args<T>(h);
-  CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-  if (validate) {
-    CK(h, jko::launch_validate<T>(q_in, N, P, h->ctrl, st));
-    if (h->species == 2) CK(h, jko::launch_validate<T>(q_in + N, N, P, h->ctrl, st));
-    CK(h, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(h, cudaStreamSynchronize(st));
-    const Ctrl& c = h->poll[0];
-    char buf[256];
-    if (c.q_bad) { snprintf(buf, sizeof buf, "q has %llu non-finite entries", c.q_bad); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
-    if (c.q_neg) { snprintf(buf, sizeof buf, "q has %llu negative entries", c.q_neg); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
-    if (std::fabs(c.q_sum - 1.0) > 1e-3) { snprintf(buf, sizeof buf, "q sums to %.9g, not 1", c.q_sum); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
-    if (c.q_masked) { snprintf(buf, sizeof buf, "q has mass on %llu masked cells", c.q_masked); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
-    if (c.q_over) { snprintf(buf, sizeof buf, "q exceeds kappa on %llu cells", c.q_over); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
-    CK(h, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-  }
-  CK(h, cudaEventRecord(h->ev0, st));
-  if ((const void*)q_in != h->q)
-    CK(h, cudaMemcpyAsync(h->q, q_in, h->ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+jko_status enqueue_step_begin(jko_handle* h, const T* q_in, cudaStream_t st) {
+  const bool plain = !h->tc_multi && !h->tc && !(h->pair_alpha > 0) && h->species != 2 &&
+                     !h->attract;
+  CK(h, jko::launch_step_begin<T>(*h->ctrl_init, h->ctrl,
+                                  (const void*)q_in != h->q ? q_in : nullptr, (T*)h->q, h->ns,
+                                  plain ? (T*)h->a : nullptr, plain ? (long long)h->N : 0, st));
+  if (plain) return JKO_OK;
   if (h->tc_multi) {
     if (h->pair_alpha > 0) CK(h, begin_pairwise<float>(h, st));
     else CK(h, begin_multi_tc(h, st));
@@ -940,8 +932,101 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     CK(h, begin_species<T>(h, st));
   } else if (h->attract) {
     CK(h, begin_attraction<T>(h, st));
-  } else {
-    CK(h, jko::launch_fill<T>((T*)h->a, T(1), N, st));   // cold start a = 1 (Sec. 3.4)
+  }
+  return JKO_OK;
+}
+
+// The status a step's control block reports.
+jko_status step_status(const Ctrl& c) {
+  // nonfinite bit 1: NaN/Inf met by an epilogue; bit 2: a bounded device wait gave up
+  if (c.nonfinite & 2) return JKO_ERR_TIMEOUT;
+  if (c.done == jko::NONFINITE || c.nonfinite) return JKO_ERR_NUMERIC;
+  if (c.done == jko::MAX_ITER || c.done == jko::STALLED) return JKO_NOT_CONVERGED;
+  return JKO_OK;
+}
+
+// The chunk loop of a step as a graph: a WHILE node whose body is one chunk
+// (the pairs of h->chunk, or one launch of the persistent loop kernel) and the
+// loop condition, which ends it when the step has stopped or after the chunk
+// budget of the host-driven loop.  Built once, at the first flow of more than
+// one step; where the runtime refuses it (state -1) flows keep host-driven chunks.
+void build_step_loop(jko_handle* h) {
+  if (h->step_loop_state != 0) return;
+  h->step_loop_state = -1;
+  const int C = h->chunk_iters;
+  const unsigned max_chunks = (unsigned)((h->prm.max_iter + 1 + C - 1) / C + 2);
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) { cudaGetLastError(); return; }
+  cudaGraphConditionalHandle hc{};
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaSuccess;
+      if (h->use_loop) e1 = enqueue_loop(h, C, h->cap);
+      else
+        for (int i = 0; i < C && e1 == cudaSuccess; ++i) e1 = enqueue_pair(h, h->cap);
+      if (e1 == cudaSuccess) e1 = jko::launch_chunk_loop_cond(h->ctrl, hc, max_chunks, h->cap);
+      cudaGraph_t captured = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(h->cap, &captured);
+      e = e1 != cudaSuccess ? e1 : e2;
+    }
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  h->step_loop = ex;
+  h->step_loop_state = 1;
+}
+
+template <typename T>
+jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info, bool validate) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  ProxArgs<T> P = jko::prox_args<T>(h);
+  // The input checks count into the control block and are read back with the
+  // step's result, so that a step waits on the device once: on a failed check
+  // the step has run on q, but its output write was skipped (outputs
+  // untouched) and the status is JKO_ERR_INVALID_ARG.
+  auto q_check = [&](const Ctrl& c) -> jko_status {
+    char buf[256];
+    if (c.q_bad) { snprintf(buf, sizeof buf, "q has %llu non-finite entries", c.q_bad); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_neg) { snprintf(buf, sizeof buf, "q has %llu negative entries", c.q_neg); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (std::fabs(c.q_sum - 1.0) > 1e-3) { snprintf(buf, sizeof buf, "q sums to %.9g, not 1", c.q_sum); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_masked) { snprintf(buf, sizeof buf, "q has mass on %llu masked cells", c.q_masked); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    if (c.q_over) { snprintf(buf, sizeof buf, "q exceeds kappa on %llu cells", c.q_over); return set_err(h, JKO_ERR_INVALID_ARG, buf); }
+    return JKO_OK;
+  };
+  // the checks of an input that also stopped the step with an error
+  auto q_check_after_error = [&](jko_status s) -> jko_status {
+    if (!validate || s == JKO_ERR_CUDA) return s;
+    if (cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return s;
+    const jko_status qs = q_check(h->poll[0]);
+    return qs != JKO_OK ? qs : s;
+  };
+  CK(h, cudaEventRecord(h->ev0, st));
+  {
+    const jko_status sb = enqueue_step_begin<T>(h, q_in, st);   // resets the control block
+    if (sb != JKO_OK) return sb;
+  }
+  if (validate) {
+    CK(h, jko::launch_validate<T>(q_in, N, P, h->ctrl, st));
+    if (h->species == 2) CK(h, jko::launch_validate<T>(q_in + N, N, P, h->ctrl, st));
   }
 
   // chunks: launch the number the last step needed at once, the last one with
@@ -955,7 +1040,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
                                                     h->part_cap, st);
     if (e == cudaSuccess && p_out)
       e = jko::launch_finalize_write<T>((const T*)h->p, p_out, h->ns, h->prm.renormalize,
-                                        h->ctrl, st);
+                                        h->ctrl, st, validate ? 1 : 0);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, st);
     return e;
   };
@@ -1021,7 +1106,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
   };
   int done = jko::RUNNING, it_tc = 0, it_end = 0, final_slot = -1, fin_slot = -1;
   jko_status sr = run_chunks(false, h->last_iters, &done, &it_tc, &final_slot);
-  if (sr != JKO_OK) return sr;
+  if (sr != JKO_OK) return q_check_after_error(sr);
   bool finished = false;
   if (done == jko::STALLED && h->prm.finish && h->tc) {
     // the tensor-core operands have reached their rounding floor: continue the
@@ -1035,7 +1120,7 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     CK(h, jko::launch_resume(h->ctrl, st));
     h->kernels += 3;
     sr = run_chunks(true, h->last_fin, &done, &it_end, &fin_slot);
-    if (sr != JKO_OK) return sr;
+    if (sr != JKO_OK) return q_check_after_error(sr);
     finished = true;
     final_slot = -1;   // the finalisation launched with the first chunks is stale
   }
@@ -1047,6 +1132,10 @@ jko_status step_impl(jko_handle* h, const T* q_in, T* p_out, jko_step_info* info
     final_slot = 0;
   }
   const Ctrl& c = h->poll[final_slot];
+  if (validate) {
+    const jko_status qs = q_check(c);
+    if (qs != JKO_OK) return qs;
+  }
   jko_status st_out = JKO_OK;
   // nonfinite bit 1: NaN/Inf met by an epilogue; bit 2: a bounded device wait gave up
   if (c.nonfinite & 2) st_out = JKO_ERR_TIMEOUT;
@@ -1101,19 +1190,34 @@ template <typename T>
 jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_final,
                      jko_step_info* infos) {
   const long long N = h->ns;   // elements of a state image
+  cudaStream_t st = h->stream;
   const T* q = p0;
   int worst = JKO_OK;
-  for (int t = 0; t < n_steps; ++t) {
-    T* out = traj ? traj + (size_t)t * N : (T*)h->stage_out;
+  // the output image of step t: its row of the trajectory, else a stage
+  // buffer, never the step's own input
+  auto out_for = [&](int t, T** out) -> jko_status {
+    *out = traj ? traj + (size_t)t * N : (T*)h->stage_out;
     if (!traj && !h->stage_out) {
       CK(h, cudaMalloc(&h->stage_out, N * sizeof(T)));
-      out = (T*)h->stage_out;
+      *out = (T*)h->stage_out;
     }
-    // never write the input of this step in place when q lives in stage_out
-    if (!traj && (const void*)q == (const void*)out) {
+    if (!traj && (const void*)q == (const void*)*out) {
       if (!h->stage_in) CK(h, cudaMalloc(&h->stage_in, N * sizeof(T)));
-      out = (T*)h->stage_in;
+      *out = (T*)h->stage_in;
     }
+    return JKO_OK;
+  };
+  // The first step checks p0 and runs with host-driven chunks; the later ones
+  // run their chunks as the device-side loop, all enqueued before one wait,
+  // unless a step needs a host decision (the FP32 finish of a stalled
+  // tensor-core step) or the runtime refused the loop graph.
+  if (n_steps > 1 && !(h->prm.finish && h->tc)) build_step_loop(h);
+  const bool device_loop = n_steps > 1 && h->step_loop_state == 1 && !(h->prm.finish && h->tc);
+  int t = 0;
+  for (; t < (device_loop ? 1 : n_steps); ++t) {
+    T* out = nullptr;
+    jko_status so = out_for(t, &out);
+    if (so != JKO_OK) return so;
     jko_step_info info{};
     jko_status s = step_impl<T>(h, q, out, &info, t == 0);
     if (s == JKO_ERR_INVALID_ARG || s == JKO_ERR_CUDA || s == JKO_ERR_OOM || s == JKO_ERR_TIMEOUT)
@@ -1122,11 +1226,80 @@ jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_fina
     worst = worse(worst, s);
     q = out;
   }
+  if (device_loop && t < n_steps) {
+    if (h->flow_cap < n_steps) {
+      if (h->flow_ctrl) cudaFreeHost(h->flow_ctrl);
+      if (h->flow_ctrl_dev) cudaFree(h->flow_ctrl_dev);
+      h->flow_ctrl = nullptr;
+      h->flow_ctrl_dev = nullptr;
+      h->flow_cap = 0;
+      CK(h, cudaMallocHost((void**)&h->flow_ctrl, sizeof(Ctrl) * (size_t)n_steps));
+      CK(h, cudaMalloc((void**)&h->flow_ctrl_dev, sizeof(Ctrl) * (size_t)n_steps));
+      h->flow_cap = n_steps;
+    }
+    while ((int)h->flow_ev.size() < 2 * n_steps) {
+      cudaEvent_t ev = nullptr;
+      CK(h, cudaEventCreate(&ev));
+      h->flow_ev.push_back(ev);
+    }
+    ProxArgs<T> P = jko::prox_args<T>(h);
+    const int t0 = t;
+    for (; t < n_steps; ++t) {
+      T* out = nullptr;
+      jko_status so = out_for(t, &out);
+      if (so != JKO_OK) return so;
+      // kernels only: the step's start, its chunk loop, the finalisation
+      // (which also records the control block), no copy between them
+      CK(h, cudaEventRecord(h->flow_ev[2 * t], st));
+      jko_status sb = enqueue_step_begin<T>(h, q, st);
+      if (sb != JKO_OK) return sb;
+      CK(h, cudaGraphLaunch(h->step_loop, st));
+      CK(h, jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part,
+                                           h->part_cap, st));
+      CK(h, jko::launch_finalize_write<T>((const T*)h->p, out, h->ns, h->prm.renormalize,
+                                          h->ctrl, st, 0, h->flow_ctrl_dev + t));
+      CK(h, cudaEventRecord(h->flow_ev[2 * t + 1], st));
+      q = out;
+    }
+    CK(h, cudaMemcpyAsync(h->flow_ctrl + t0, h->flow_ctrl_dev + t0,
+                          sizeof(Ctrl) * (size_t)(n_steps - t0), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const long long per_chunk = h->use_loop ? 1 : pair_kernels(h) * h->chunk_iters;
+    for (int k = t0; k < n_steps; ++k) {
+      const Ctrl& c = h->flow_ctrl[k];
+      const jko_status sk = step_status(c);
+      if (sk == JKO_ERR_TIMEOUT) return set_err(h, sk, "a bounded device-side wait gave up");
+      h->last_iters = c.it;
+      if (infos) {
+        jko_step_info& info = infos[k];
+        info = jko_step_info{};
+        info.iters = c.it;
+        info.status = sk;
+        info.residual_l1 = c.res_last;
+        info.mass = c.mass;
+        unsigned long long bits = c.maxpk_bits;
+        double mx;
+        std::memcpy(&mx, &bits, sizeof mx);
+        info.max_p_over_kappa = h->has_kappa ? mx : 0.0;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->flow_ev[2 * k], h->flow_ev[2 * k + 1]);
+        info.ms = ms;
+        // the step's start, the chunks and their loop conditions, the finalisation
+        info.kernels = (int)(1 + (long long)c.chunks * (per_chunk + 1) + 2);
+        info.iters_finish = 0;
+      }
+      if (sk == JKO_ERR_NUMERIC) set_err(h, sk, "NaN or Inf in the scaling iterates");
+      else if (sk == JKO_NOT_CONVERGED)
+        set_err(h, sk, c.done == jko::STALLED ? "the residual stalled above tol (stall rule)"
+                                              : "max_iter reached before tol");
+      worst = worse(worst, sk);
+    }
+  }
   if (p_final && n_steps > 0)
-    CK(h, cudaMemcpyAsync(p_final, q, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(p_final, q, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
   if (p_final && n_steps == 0)
-    CK(h, cudaMemcpyAsync(p_final, p0, N * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
-  CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpyAsync(p_final, p0, N * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  CK(h, cudaStreamSynchronize(st));
   return (jko_status)worst;
 }
 

@@ -81,6 +81,16 @@ struct jko_handle {
   // (jko_params.finish): its chunk of pairs, and the pairs it took last
   cudaGraphExec_t chunk_fin = nullptr;
   int last_fin = 0;
+  // flows: a step's chunks as a graph WHILE node (one chunk, then the loop
+  // condition on the device), so that the steps after the first are enqueued
+  // without a host wait between them; the control block after each of them
+  // (pinned) and two events per step
+  cudaGraphExec_t step_loop = nullptr;
+  int step_loop_state = 0;      // 0 not built, 1 built, -1 not available (host-driven chunks)
+  Ctrl* flow_ctrl = nullptr;       // pinned host copy
+  Ctrl* flow_ctrl_dev = nullptr;   // device: written by each step's last kernel
+  int flow_cap = 0;
+  std::vector<cudaEvent_t> flow_ev;
 
   jko::TcPlan* tc = nullptr;   // tensor-core path state (JKO_TF32/BF16/BF16X3)
   long long kernels = 0;       // kernels enqueued by the running step

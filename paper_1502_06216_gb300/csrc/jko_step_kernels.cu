@@ -18,6 +18,21 @@ __global__ void fill_kernel(T* x, T v, long long n) {
     x[i] = v;
 }
 
+// The start of a step in one launch: the control block reset to its initial
+// value, q copied into the handle's image (q_in NULL: already there) and, for
+// the plain form, the cold start a = 1 (a NULL: the form sets up its own).
+template <typename T>
+__global__ void step_begin_kernel(Ctrl init, Ctrl* ctrl, const T* q_in, T* q, long long nq,
+                                  T* a, long long na) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ctrl = init;
+  const long long n = nq > na ? nq : na;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (q_in && i < nq) q[i] = q_in[i];
+    if (a && i < na) a[i] = T(1);
+  }
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -103,9 +118,19 @@ __global__ void finalize_reduce_kernel(const T* p, long long n, ProxArgs<T> P, C
   }
 }
 
+// True when the input checks of a step (validate_kernel) found q invalid.
+__device__ __forceinline__ bool q_invalid(const Ctrl* ctrl) {
+  return ctrl->q_bad || ctrl->q_neg || fabs(ctrl->q_sum - 1.0) > 1e-3 || ctrl->q_masked ||
+         ctrl->q_over;
+}
+
 template <typename T>
 __global__ void finalize_write_kernel(const T* p, T* out, long long n, int renorm,
-                                      const Ctrl* ctrl) {
+                                      const Ctrl* ctrl, int check, Ctrl* record) {
+  // the step's final control block, for a flow that reads all steps' at its end
+  if (record && blockIdx.x == 0 && threadIdx.x == 0) *record = *ctrl;
+  // a step whose input failed its checks leaves the output untouched
+  if (check && q_invalid(ctrl)) return;
   const double mass = ctrl->mass;
   const bool scale = renorm && mass > 0.0 && isfinite(mass);
   // p / mass as p times the FP64 reciprocal (within one FP64 ulp of the
@@ -126,6 +151,13 @@ int grid_for(long long n) {
 }
 
 }  // namespace
+
+template <typename T>
+cudaError_t launch_step_begin(const Ctrl& init, Ctrl* ctrl, const T* q_in, T* q, long long nq,
+                              T* a, long long na, cudaStream_t st) {
+  step_begin_kernel<T><<<grid_for(nq > na ? nq : na), NT, 0, st>>>(init, ctrl, q_in, q, nq, a, na);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_fill(T* x, T v, long long n, cudaStream_t st) {
@@ -151,8 +183,8 @@ cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P
 
 template <typename T>
 cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
-                                  cudaStream_t st) {
-  finalize_write_kernel<T><<<grid_for(n), NT, 0, st>>>(p, out, n, renorm, ctrl);
+                                  cudaStream_t st, int check, Ctrl* record) {
+  finalize_write_kernel<T><<<grid_for(n), NT, 0, st>>>(p, out, n, renorm, ctrl, check, record);
   return cudaGetLastError();
 }
 
@@ -166,6 +198,21 @@ __global__ void gather_ctrl_kernel(Ctrl* const* ctrls, Ctrl* out, int n) {
     out[i] = *ctrls[i];
 }
 }  // namespace
+
+namespace {
+__global__ void chunk_loop_cond_kernel(Ctrl* ctrl, cudaGraphConditionalHandle hc,
+                                       unsigned max_chunks) {
+  const unsigned n = ctrl->chunks + 1;
+  ctrl->chunks = n;
+  cudaGraphSetConditional(hc, (ctrl->done == RUNNING && n < max_chunks) ? 1u : 0u);
+}
+}  // namespace
+
+cudaError_t launch_chunk_loop_cond(Ctrl* ctrl, cudaGraphConditionalHandle hc,
+                                   unsigned max_chunks, cudaStream_t st) {
+  chunk_loop_cond_kernel<<<1, 1, 0, st>>>(ctrl, hc, max_chunks);
+  return cudaGetLastError();
+}
 
 namespace {
 __global__ void resume_kernel(Ctrl* ctrl) {
@@ -196,7 +243,9 @@ cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_
   template cudaError_t launch_finalize_reduce<T>(const T*, long long, const ProxArgs<T>&, \
                                                  Ctrl*, double*, int, cudaStream_t);    \
   template cudaError_t launch_finalize_write<T>(const T*, T*, long long, int, const Ctrl*, \
-                                                cudaStream_t);
+                                                cudaStream_t, int, Ctrl*);                    \
+  template cudaError_t launch_step_begin<T>(const Ctrl&, Ctrl*, const T*, T*, long long, T*, \
+                                            long long, cudaStream_t);
 JKO_INST(float)
 JKO_INST(double)
 #undef JKO_INST

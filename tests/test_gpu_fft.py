@@ -71,6 +71,17 @@ def test_porous_512_fp32_matches_band_filter_and_oracle():
     e_band = max(rel_l1(t_band[t], ref.traj[t + 1]) for t in range(5))
     print("porous 512 FP32: FFT", e_fft, "band filter", e_band, "pairs", [i["iters"] for i in i_fft])
     assert e_fft <= 1e-5
+    # p >= 0 (the prox pass takes a transform output below 0 as 0): each step's
+    # output passes the input checks of the next jko_step
+    assert np.all(t_fft >= 0)
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    h = jko.create_from_problem(pb, precision=jko.Precision.FP32, fft=1)
+    q = torch.tensor(pb.q0, dtype=torch.float32, device="cuda")
+    for t in range(3):
+        q, info = jko.jko_step(h, q)
+        assert np.array_equal(q.double().cpu().numpy(), t_fft[t])
+    jko.jko_destroy(h)
 
 
 @pytest.mark.parametrize("prec,R,bar", [("FP32", 4.0, 2e-6), ("FP32", 8.0, 1e-5),

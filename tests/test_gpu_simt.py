@@ -144,6 +144,19 @@ def test_invalid_inputs_leave_outputs_untouched():
             jko.jko_step(h, q, out)
         assert e.value.status == jko.Status.INVALID_ARG
         assert torch.all(out == -7.0)
+        # the input checks are read back with the step's result: the step runs,
+        # its output write is skipped, also when the output is the input
+        q_in = q.clone()
+        with pytest.raises(jko.JKOError) as e:
+            jko.jko_step(h, q, q)
+        assert e.value.status == jko.Status.INVALID_ARG
+        assert torch.equal(q, q_in) or (torch.isnan(q_in).any() and
+                                        torch.equal(torch.nan_to_num(q), torch.nan_to_num(q_in)))
+    # a valid step after the rejected ones runs as on a fresh handle
+    p_after, info = jko.jko_step(h, good)
+    h3 = jko.create_from_problem(pb, precision=jko.Precision.FP32)
+    p_fresh, info3 = jko.jko_step(h3, good)
+    assert torch.equal(p_after, p_fresh) and info["iters"] == info3["iters"]
     # obstacle with mass on it
     pb2 = inputs.config_problem(1, n=32)
     h2 = jko.create_from_problem(pb2, precision=jko.Precision.FP32)
