@@ -6,9 +6,12 @@
 //   pass y of xi a ; pass x of xi a fused with  b = q / xi a  and the residual
 //   of the previous pair (stopping rule of Sec. 3.4) ;
 //   pass y of xi b ; pass x of xi b fused with  p = Prox(s), a = p / s.
-// A chunk of `check_every` pairs is captured once as a CUDA graph.  The host
-// launches chunks and polls a 16-byte slice of the device control block, with
-// one chunk always in flight; kernels launched after the stop return at once.
+// A chunk of `check_every` pairs is captured once as a CUDA graph.  A step
+// launches the number of chunks the last step needed with the finalisation
+// behind the last one and waits once; only a longer step polls on, with one
+// chunk in flight; kernels launched after the stop return at once.  In a flow
+// the steps after the first run their chunks as a device-side loop (a graph
+// WHILE node) and are enqueued without a wait between them.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -650,6 +653,7 @@ void free_handle(jko_handle* h) {
   for (cudaEvent_t ev : h->flow_ev) cudaEventDestroy(ev);
   if (h->flow_ctrl) cudaFreeHost(h->flow_ctrl);
   if (h->flow_ctrl_dev) cudaFree(h->flow_ctrl_dev);
+  if (h->chunk_ctr) cudaFree(h->chunk_ctr);
   void* bufs[] = {h->a, h->b, h->t1, h->p, h->q, h->stage_in, h->stage_out, h->taps_x,
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
@@ -916,7 +920,7 @@ template <typename T>
 jko_status enqueue_step_begin(jko_handle* h, const T* q_in, cudaStream_t st) {
   const bool plain = !h->tc_multi && !h->tc && !(h->pair_alpha > 0) && h->species != 2 &&
                      !h->attract;
-  CK(h, jko::launch_step_begin<T>(*h->ctrl_init, h->ctrl,
+  CK(h, jko::launch_step_begin<T>(*h->ctrl_init, h->ctrl, h->chunk_ctr,
                                   (const void*)q_in != h->q ? q_in : nullptr, (T*)h->q, h->ns,
                                   plain ? (T*)h->a : nullptr, plain ? (long long)h->N : 0, st));
   if (plain) return JKO_OK;
@@ -955,6 +959,11 @@ void build_step_loop(jko_handle* h) {
   h->step_loop_state = -1;
   const int C = h->chunk_iters;
   const unsigned max_chunks = (unsigned)((h->prm.max_iter + 1 + C - 1) / C + 2);
+  if (!h->chunk_ctr && cudaMalloc((void**)&h->chunk_ctr, sizeof(unsigned)) != cudaSuccess) {
+    h->chunk_ctr = nullptr;
+    cudaGetLastError();
+    return;
+  }
   cudaGraph_t g = nullptr;
   if (cudaGraphCreate(&g, 0) != cudaSuccess) { cudaGetLastError(); return; }
   cudaGraphConditionalHandle hc{};
@@ -975,7 +984,8 @@ void build_step_loop(jko_handle* h) {
       if (h->use_loop) e1 = enqueue_loop(h, C, h->cap);
       else
         for (int i = 0; i < C && e1 == cudaSuccess; ++i) e1 = enqueue_pair(h, h->cap);
-      if (e1 == cudaSuccess) e1 = jko::launch_chunk_loop_cond(h->ctrl, hc, max_chunks, h->cap);
+      if (e1 == cudaSuccess)
+        e1 = jko::launch_chunk_loop_cond(h->chunk_ctr, h->ctrl, hc, max_chunks, h->cap);
       cudaGraph_t captured = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(h->cap, &captured);
       e = e1 != cudaSuccess ? e1 : e2;
@@ -1284,8 +1294,11 @@ jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_fina
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->flow_ev[2 * k], h->flow_ev[2 * k + 1]);
         info.ms = ms;
-        // the step's start, the chunks and their loop conditions, the finalisation
-        info.kernels = (int)(1 + (long long)c.chunks * (per_chunk + 1) + 2);
+        // the step's start, the chunks (the stop is decided in the pair after
+        // the last one completed) and their loop conditions, the finalisation
+        const long long chunks =
+            h->use_loop ? 1 : (c.it + 1 + h->chunk_iters - 1) / h->chunk_iters;
+        info.kernels = (int)(1 + chunks * (per_chunk + 1) + 2);
         info.iters_finish = 0;
       }
       if (sk == JKO_ERR_NUMERIC) set_err(h, sk, "NaN or Inf in the scaling iterates");

@@ -87,6 +87,7 @@ struct jko_handle {
   // (pinned) and two events per step
   cudaGraphExec_t step_loop = nullptr;
   int step_loop_state = 0;      // 0 not built, 1 built, -1 not available (host-driven chunks)
+  unsigned* chunk_ctr = nullptr;  // device: chunks the loop has run in this step
   Ctrl* flow_ctrl = nullptr;       // pinned host copy
   Ctrl* flow_ctrl_dev = nullptr;   // device: written by each step's last kernel
   int flow_cap = 0;

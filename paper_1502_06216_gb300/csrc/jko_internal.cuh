@@ -24,7 +24,7 @@ struct Ctrl {
   int nonfinite;          // set when an epilogue meets NaN or Inf
   int max_iter;           // copy of the step budget
   unsigned int bar_base;  // grid barriers the persistent loop kernel completed this step
-  unsigned int chunks;     // chunks the device-side chunk loop of a flow step has run
+  unsigned int bar_spare;
   unsigned int arrive_f;  // arrival counter of the finalisation kernel
   unsigned int arrive_v;  // arrival counter of the validation kernel
   double tol;             // L1 residual tolerance

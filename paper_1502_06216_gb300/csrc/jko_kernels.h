@@ -86,11 +86,13 @@ cudaError_t launch_finalize_reduce(const T* p, long long n, const ProxArgs<T>& P
                                    double* part, int part_cap, cudaStream_t st);
 
 // The condition of the device-side chunk loop (a graph WHILE node whose body
-// is one chunk of pairs and then this kernel): counts the chunk in
-// ctrl->chunks and continues while the step runs and fewer than max_chunks
-// chunks have run, so that the loop ends after max_chunks chunks at most.
-cudaError_t launch_chunk_loop_cond(Ctrl* ctrl, cudaGraphConditionalHandle hc,
-                                   unsigned max_chunks, cudaStream_t st);
+// is one chunk of pairs and then this kernel): counts the chunk in *chunks
+// (reset by the step's start) and continues while the step runs and fewer
+// than max_chunks chunks have run, so that the loop ends after max_chunks
+// chunks at most.
+cudaError_t launch_chunk_loop_cond(unsigned* chunks, const Ctrl* ctrl,
+                                   cudaGraphConditionalHandle hc, unsigned max_chunks,
+                                   cudaStream_t st);
 
 // out = renorm ? p / ctrl->mass : p   (out may alias p); check = 1: nothing is
 // written when the step's input checks (launch_validate into the same ctrl)
@@ -100,11 +102,12 @@ template <typename T>
 cudaError_t launch_finalize_write(const T* p, T* out, long long n, int renorm, const Ctrl* ctrl,
                                   cudaStream_t st, int check = 0, Ctrl* record = nullptr);
 
-// The start of a step in one launch: *ctrl = init, q[0..nq) = q_in (q_in may
-// be NULL: nothing copied), a[0..na) = 1 (a may be NULL).
+// The start of a step in one launch: *ctrl = init, *chunks = 0 (chunks may be
+// NULL), q[0..nq) = q_in (q_in may be NULL: nothing copied), a[0..na) = 1 (a
+// may be NULL).
 template <typename T>
-cudaError_t launch_step_begin(const Ctrl& init, Ctrl* ctrl, const T* q_in, T* q, long long nq,
-                              T* a, long long na, cudaStream_t st);
+cudaError_t launch_step_begin(const Ctrl& init, Ctrl* ctrl, unsigned* chunks, const T* q_in,
+                              T* q, long long nq, T* a, long long na, cudaStream_t st);
 
 // Wasserstein attraction (attraction.cu): p = Prox(s1^{1/(1+tau)} s2^{tau/(1+tau)}),
 // a_m = p / s_m, and the pair counter; returns at once once the step has stopped.

@@ -22,9 +22,12 @@ __global__ void fill_kernel(T* x, T v, long long n) {
 // value, q copied into the handle's image (q_in NULL: already there) and, for
 // the plain form, the cold start a = 1 (a NULL: the form sets up its own).
 template <typename T>
-__global__ void step_begin_kernel(Ctrl init, Ctrl* ctrl, const T* q_in, T* q, long long nq,
-                                  T* a, long long na) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *ctrl = init;
+__global__ void step_begin_kernel(Ctrl init, Ctrl* ctrl, unsigned* chunks, const T* q_in, T* q,
+                                  long long nq, T* a, long long na) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *ctrl = init;
+    if (chunks) *chunks = 0;
+  }
   const long long n = nq > na ? nq : na;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -153,9 +156,10 @@ int grid_for(long long n) {
 }  // namespace
 
 template <typename T>
-cudaError_t launch_step_begin(const Ctrl& init, Ctrl* ctrl, const T* q_in, T* q, long long nq,
-                              T* a, long long na, cudaStream_t st) {
-  step_begin_kernel<T><<<grid_for(nq > na ? nq : na), NT, 0, st>>>(init, ctrl, q_in, q, nq, a, na);
+cudaError_t launch_step_begin(const Ctrl& init, Ctrl* ctrl, unsigned* chunks, const T* q_in,
+                              T* q, long long nq, T* a, long long na, cudaStream_t st) {
+  step_begin_kernel<T><<<grid_for(nq > na ? nq : na), NT, 0, st>>>(init, ctrl, chunks, q_in, q,
+                                                                    nq, a, na);
   return cudaGetLastError();
 }
 
@@ -200,17 +204,18 @@ __global__ void gather_ctrl_kernel(Ctrl* const* ctrls, Ctrl* out, int n) {
 }  // namespace
 
 namespace {
-__global__ void chunk_loop_cond_kernel(Ctrl* ctrl, cudaGraphConditionalHandle hc,
-                                       unsigned max_chunks) {
-  const unsigned n = ctrl->chunks + 1;
-  ctrl->chunks = n;
+__global__ void chunk_loop_cond_kernel(unsigned* chunks, const Ctrl* ctrl,
+                                       cudaGraphConditionalHandle hc, unsigned max_chunks) {
+  const unsigned n = *chunks + 1;
+  *chunks = n;
   cudaGraphSetConditional(hc, (ctrl->done == RUNNING && n < max_chunks) ? 1u : 0u);
 }
 }  // namespace
 
-cudaError_t launch_chunk_loop_cond(Ctrl* ctrl, cudaGraphConditionalHandle hc,
-                                   unsigned max_chunks, cudaStream_t st) {
-  chunk_loop_cond_kernel<<<1, 1, 0, st>>>(ctrl, hc, max_chunks);
+cudaError_t launch_chunk_loop_cond(unsigned* chunks, const Ctrl* ctrl,
+                                   cudaGraphConditionalHandle hc, unsigned max_chunks,
+                                   cudaStream_t st) {
+  chunk_loop_cond_kernel<<<1, 1, 0, st>>>(chunks, ctrl, hc, max_chunks);
   return cudaGetLastError();
 }
 
@@ -244,8 +249,8 @@ cudaError_t launch_gather_ctrl(Ctrl* const* ctrls, Ctrl* out, int n, cudaStream_
                                                  Ctrl*, double*, int, cudaStream_t);    \
   template cudaError_t launch_finalize_write<T>(const T*, T*, long long, int, const Ctrl*, \
                                                 cudaStream_t, int, Ctrl*);                    \
-  template cudaError_t launch_step_begin<T>(const Ctrl&, Ctrl*, const T*, T*, long long, T*, \
-                                            long long, cudaStream_t);
+  template cudaError_t launch_step_begin<T>(const Ctrl&, Ctrl*, unsigned*, const T*, T*,     \
+                                            long long, T*, long long, cudaStream_t);
 JKO_INST(float)
 JKO_INST(double)
 #undef JKO_INST
