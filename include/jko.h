@@ -246,8 +246,9 @@ jko_status jko_step(jko_handle* h, const void* q_dev, void* p_out_dev, jko_step_
  * ends when the step stops, or after the chunk budget of max_iter pairs), with
  * the same kernels, hence the same results, as jko_step.  Handles whose steps
  * need a host decision (jko_params.finish on a tensor-core form) run every
- * step with host-driven chunks.  The first call allocates pinned reports and
- * events for n_steps; a later longer flow allocates again. */
+ * step with host-driven chunks.  The first call on a handle (of any length)
+ * builds the loop graph and allocates pinned reports and events for
+ * max(n_steps, 64) steps; a later longer flow allocates again. */
 jko_status jko_flow(jko_handle* h, const void* p0_dev, int n_steps, void* traj_dev,
                     void* p_final_dev, jko_step_info* infos);
 

@@ -1221,7 +1221,27 @@ jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_fina
   // run their chunks as the device-side loop, all enqueued before one wait,
   // unless a step needs a host decision (the FP32 finish of a stalled
   // tensor-core step) or the runtime refused the loop graph.
-  if (n_steps > 1 && !(h->prm.finish && h->tc)) build_step_loop(h);
+  // The loop graph and the per-step reports are set up at the first flow of
+  // any length (a one-step flow does it for the longer flows after it).
+  if (!(h->prm.finish && h->tc)) {
+    build_step_loop(h);
+    if (h->step_loop_state == 1 && h->flow_cap < n_steps) {
+      const int cap = std::max(n_steps, 64);
+      if (h->flow_ctrl) cudaFreeHost(h->flow_ctrl);
+      if (h->flow_ctrl_dev) cudaFree(h->flow_ctrl_dev);
+      h->flow_ctrl = nullptr;
+      h->flow_ctrl_dev = nullptr;
+      h->flow_cap = 0;
+      CK(h, cudaMallocHost((void**)&h->flow_ctrl, sizeof(Ctrl) * (size_t)cap));
+      CK(h, cudaMalloc((void**)&h->flow_ctrl_dev, sizeof(Ctrl) * (size_t)cap));
+      h->flow_cap = cap;
+    }
+    while (h->step_loop_state == 1 && (int)h->flow_ev.size() < 2 * h->flow_cap) {
+      cudaEvent_t ev = nullptr;
+      CK(h, cudaEventCreate(&ev));
+      h->flow_ev.push_back(ev);
+    }
+  }
   const bool device_loop = n_steps > 1 && h->step_loop_state == 1 && !(h->prm.finish && h->tc);
   int t = 0;
   for (; t < (device_loop ? 1 : n_steps); ++t) {
@@ -1237,21 +1257,6 @@ jko_status flow_impl(jko_handle* h, const T* p0, int n_steps, T* traj, T* p_fina
     q = out;
   }
   if (device_loop && t < n_steps) {
-    if (h->flow_cap < n_steps) {
-      if (h->flow_ctrl) cudaFreeHost(h->flow_ctrl);
-      if (h->flow_ctrl_dev) cudaFree(h->flow_ctrl_dev);
-      h->flow_ctrl = nullptr;
-      h->flow_ctrl_dev = nullptr;
-      h->flow_cap = 0;
-      CK(h, cudaMallocHost((void**)&h->flow_ctrl, sizeof(Ctrl) * (size_t)n_steps));
-      CK(h, cudaMalloc((void**)&h->flow_ctrl_dev, sizeof(Ctrl) * (size_t)n_steps));
-      h->flow_cap = n_steps;
-    }
-    while ((int)h->flow_ev.size() < 2 * n_steps) {
-      cudaEvent_t ev = nullptr;
-      CK(h, cudaEventCreate(&ev));
-      h->flow_ev.push_back(ev);
-    }
     ProxArgs<T> P = jko::prox_args<T>(h);
     const int t0 = t;
     for (; t < n_steps; ++t) {
