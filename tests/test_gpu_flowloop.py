@@ -28,6 +28,16 @@ CASES = {
     # FP64, stall rule on
     "crowd_fp64_stall": (lambda: inputs.config_problem(0, n=48, n_steps=4), "FP64",
                          {"stall": 3}),
+    # two species through their sum, CUDA cores; the pairwise step on the TF32
+    # tensor cores (one launch per pass for all couplings)
+    "species_fp32": (lambda: inputs.two_species_problem(48, gamma=2e-3, tau=0.05, n_steps=4,
+                                                        max_iter=2000), "FP32", {}),
+    "pairwise_tf32": (lambda: inputs.pairwise_attraction_problem(64, gamma=2e-3, n_steps=4,
+                                                                 tol=1e-6, max_iter=2000),
+                      "TF32", {"stall": 4}),
+    # the Gaussian by FFT convolution
+    "porous_fp32_fft": (lambda: inputs.config_problem(1, n=96, ny=80, n_steps=4), "FP32",
+                        {"fft": 1}),
 }
 
 
