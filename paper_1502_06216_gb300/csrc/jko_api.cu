@@ -1372,7 +1372,8 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
   if (e != cudaSuccess) return fail(cuda_err(h, e, "cudaMalloc(ctrl)"));
   h->fft = grid->fft;
   // the b-update pass runs along x: one residual partial per block
-  h->nparts_simt = h->fft ? jko::fft_pass_blocks(grid->ny) : jko::simt_pass_blocks(grid->nx, grid->ny);
+  h->nparts_simt = h->fft ? jko::fft_pass_blocks(grid->ny)
+                           : jko::simt_pass_blocks(grid->nx, grid->ny, 1, h->fp64 ? 1 : 0);
   h->attract = energy->target ? 1 : 0;
   if (h->attract || h->species == 2) {
     void** more[] = {&h->a2, &h->b2, &h->s1, &h->s2, &h->t2};

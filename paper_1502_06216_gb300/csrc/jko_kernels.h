@@ -63,7 +63,7 @@ bool fft_axis_tables(int n, int r, double length, double gamma, int max_len, int
 int simt_tap_padding();
 // Blocks of a filter pass over an [n_i][n_j] input (= residual partials of the
 // b-update pass).
-int simt_pass_blocks(int n_i, int n_j, int latency = 1);
+int simt_pass_blocks(int n_i, int n_j, int latency = 1, int fp64 = 0);
 
 template <typename T>
 cudaError_t simt_pass(int epi, int ek, const PassArgs<T>& A, const ProxArgs<T>& P,

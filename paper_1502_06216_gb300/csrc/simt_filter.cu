@@ -29,7 +29,8 @@ namespace {
 
 constexpr int RB_MAX = 16;  // outputs per thread along the filtered axis (or 4)
 constexpr int BJ = 32;   // threads along the contiguous axis
-constexpr int BI = 4;    // thread rows per block
+// thread rows per block (BI): 4, or 8 for the 4-output FP32 form where 8-row
+// blocks still give every SM one (32 output rows then share one staged halo)
 
 // One element global -> shared by cp.async (L1-allocating); ok = false writes 0
 // and reads nothing.
@@ -101,7 +102,7 @@ __device__ __forceinline__ void global_taps(T (&acc)[RB], const T* col, int ld, 
 
 // Staged input rows of the tiled pass: the block's BI RB output rows, the
 // 2r rows of the taps' reach and 2 RB more that the last window prefetch reads.
-template <int RB>
+template <int RB, int BI>
 __host__ __device__ constexpr int tile_rows(int r) { return BI * RB + 2 * r + 2 * RB; }
 // Shared-memory slots of the taps (2r + 1 + RB, zero-padded), rounded up to
 // four so that the staged rows behind them start 16-byte aligned.
@@ -112,7 +113,7 @@ __host__ __device__ constexpr int tap_slots(int r) { return (2 * r + 1 + RB + 3)
 // of its 32 columns in shared memory (coalesced, zeros outside the image), so
 // the tap loop reads shared memory with no bounds checks instead of guarded
 // global loads; the same terms are added in the same order either way.
-template <typename T, int EPI, int EK, int RB, bool TILE>
+template <typename T, int EPI, int EK, int RB, bool TILE, int BI>
 __global__ void __launch_bounds__(BJ * BI)
 filter_pass(PassArgs<T> A, ProxArgs<T> P) {
   Ctrl* ctrl = A.ctrl;
@@ -160,7 +161,7 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
     const int r = A.r;
     const int n_i = A.n_i;
     const int blk_lo = blockIdx.y * BI * RB;
-    const int rows = tile_rows<RB>(r);
+    const int rows = tile_rows<RB, BI>(r);
     const int c0 = blockIdx.x * BJ;
     // asynchronous copies, all in flight at once, zero-filled outside the
     // image: 16 bytes each where the rows are 16-byte aligned, else one element
@@ -316,21 +317,31 @@ filter_pass(PassArgs<T> A, ProxArgs<T> P) {
 // Outputs per thread for an [n_i][n_j] pass: 16 unless that leaves fewer than
 // two blocks per SM.
 int rb_for(int n_i, int n_j) {
-  const int blocks16 = ((n_j + BJ - 1) / BJ) * ((n_i + BI * 16 - 1) / (BI * 16));
+  const int blocks16 = ((n_j + BJ - 1) / BJ) * ((n_i + 4 * 16 - 1) / (4 * 16));
   return blocks16 < 2 * 152 ? 4 : 16;
 }
 
-// Shared memory of the tiled pass: taps + the staged rows.
-template <typename T, int RB>
-size_t tile_smem(int r) {
-  return sizeof(T) * ((size_t)tap_slots<RB>(r) + (size_t)tile_rows<RB>(r) * BJ);
+// Thread rows per block: 8 for the 4-output form of a handle alone in FP32 where
+// that grid still has a block for every SM (512^2: 256 blocks; halves the staged
+// halo per output row: porous 512^2 passes 7.2-8.9 -> 6.7-8.2 us, measured), else
+// 4 (at 256^2 the 8-row grid left SMs idle: 4.1 -> 4.4 us; FP64 at 512^2 215 -> 224).
+int bi_for(int rb, int n_i, int n_j, int latency, bool fp32) {
+  if (rb != 4 || !latency || !fp32) return 4;
+  const int blocks8 = ((n_j + BJ - 1) / BJ) * ((n_i + 8 * 4 - 1) / (8 * 4));
+  return blocks8 >= 152 ? 8 : 4;
 }
 
-template <typename T, int EPI, int EK, int RB, bool TILE>
+// Shared memory of the tiled pass: taps + the staged rows.
+template <typename T, int RB, int BI>
+size_t tile_smem(int r) {
+  return sizeof(T) * ((size_t)tap_slots<RB>(r) + (size_t)tile_rows<RB, BI>(r) * BJ);
+}
+
+template <typename T, int EPI, int EK, int RB, bool TILE, int BI>
 cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
-  const size_t smem = TILE ? tile_smem<T, RB>(A.r)
+  const size_t smem = TILE ? tile_smem<T, RB, BI>(A.r)
                            : sizeof(T) * (size_t)(tap_slots<RB>(A.r) + BJ * (BI * RB + 1));
-  auto kern = filter_pass<T, EPI, EK, RB, TILE>;
+  auto kern = filter_pass<T, EPI, EK, RB, TILE, BI>;
   // opt in well below 48 KB: the kernel's static shared memory (stop gate,
   // reductions) counts against the same default limit
   if (smem > 32 * 1024) {
@@ -352,24 +363,33 @@ cudaError_t launch_rb(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t s
 // batch keep the untiled 16-output form: there the other flows fill the GPU,
 // and the extra blocks and staged halos cost throughput (256-flow FP32 batch:
 // 17.6k against 6.2k flow-steps/s with the 4-output tiles, measured).
+template <typename T, int EPI, int EK, int RB, int BI>
+cudaError_t launch_rb4(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
+  constexpr size_t kTileMax = 160 * 1024;
+  return tile_smem<T, RB, BI>(A.r) <= kTileMax ? launch_rb<T, EPI, EK, RB, true, BI>(A, P, st)
+                                               : launch_rb<T, EPI, EK, RB, false, BI>(A, P, st);
+}
+
 template <typename T, int EPI, int EK>
 cudaError_t launch_one(const PassArgs<T>& A, const ProxArgs<T>& P, cudaStream_t st) {
-  constexpr size_t kTileMax = 160 * 1024;
-  if (A.latency && rb_for(A.n_i, A.n_j) == 4)
-    return tile_smem<T, 4>(A.r) <= kTileMax ? launch_rb<T, EPI, EK, 4, true>(A, P, st)
-                                            : launch_rb<T, EPI, EK, 4, false>(A, P, st);
+  if (A.latency && rb_for(A.n_i, A.n_j) == 4) {
+    if (bi_for(4, A.n_i, A.n_j, A.latency, sizeof(T) == 4) == 8)
+      return launch_rb4<T, EPI, EK, 4, 8>(A, P, st);
+    return launch_rb4<T, EPI, EK, 4, 4>(A, P, st);
+  }
   constexpr size_t kTile16Max = 72 * 1024;
-  if (A.latency && tile_smem<T, 16>(A.r) <= kTile16Max)
-    return launch_rb<T, EPI, EK, 16, true>(A, P, st);
-  return launch_rb<T, EPI, EK, 16, false>(A, P, st);
+  if (A.latency && tile_smem<T, 16, 4>(A.r) <= kTile16Max)
+    return launch_rb<T, EPI, EK, 16, true, 4>(A, P, st);
+  return launch_rb<T, EPI, EK, 16, false, 4>(A, P, st);
 }
 
 }  // namespace
 
 int simt_tap_padding() { return RB_MAX; }
-int simt_pass_blocks(int n_i, int n_j, int latency) {
+int simt_pass_blocks(int n_i, int n_j, int latency, int fp64) {
   const int rb = latency ? rb_for(n_i, n_j) : 16;
-  return ((n_j + BJ - 1) / BJ) * ((n_i + BI * rb - 1) / (BI * rb));
+  const int bi = bi_for(rb, n_i, n_j, latency, fp64 == 0);
+  return ((n_j + BJ - 1) / BJ) * ((n_i + bi * rb - 1) / (bi * rb));
 }
 
 template <typename T>
