@@ -7,14 +7,31 @@ differentiation in float64.  At convergence this equals the implicit
 derivative of each step's fixed point.  The congestion clamp is written as
 where(x < kappa, x, kappa), so a tie takes kappa (no gradient through it).
 
-Only the congestion + potential energy (Eq. dfn-congestion) is covered here,
-with an optional obstacle mask.  TEST INFRASTRUCTURE ONLY.
+``crowd_*`` cover the congestion + potential energy (Eq. dfn-congestion) with
+an optional obstacle mask.  ``energy_*`` cover every convex energy of
+``oracle.energy.Energy`` (potential, congestion bound as a scalar or a field,
+the entropy m = 1, the power form m > 1, the generalised entropies with
+per-cell exponents, obstacles) through the same loop with the pointwise KL
+prox of ``oracle.prox`` written in torch:
+  * closed forms (no entropy term, m = 1: Eq. prox-entropy) are differentiated
+    as they stand;
+  * the implicit roots (m > 1: log psi + beta psi^{m-1} = l, Eq. prox-psi;
+    per-cell exponents: y + c (e^{m1 y} - 1)/m1 = l) are found in NumPy
+    (``oracle.prox``'s Lambert-W forms, detached from the graph) and then
+    passed through one Newton step y = y* - G(y*)/G'(y*) written in torch.
+    At the root G(y*) = 0, so the step leaves the value unchanged to rounding
+    and its derivative with respect to l is 1/G'(y*): the implicit-function
+    derivative of the root.
+The non-convex binary congestion is not differentiable and is refused.
+TEST INFRASTRUCTURE ONLY.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
 
+from . import prox as _prox
+from .energy import Energy
 from .gibbs import kernel_1d
 
 
@@ -35,7 +52,7 @@ def crowd_step_torch(q, w, Kx, Ky, ny, nx, sigma, kappa, mask=None, tol=1e-13, m
         Y = _xi(Kx, Ky, a, ny, nx)
         if k > 1:
             r = torch.abs(b * Y - q).sum()
-            if float(r) <= tol:
+            if float(r.detach()) <= tol:
                 break
         b = torch.where(qpos, q / Y, torch.zeros_like(q))
         s = _xi(Kx, Ky, b, ny, nx)
@@ -72,3 +89,96 @@ def crowd_flow_loss(p0, w, target, nx, ny, gamma, tau, kappa, n_steps, mask=None
         for _ in range(n_steps):
             p = crowd_step_torch(p, wt, Kx, Ky, ny, nx, tau / gamma, kappa, mask, tol=tol)
         return float(((p - torch.tensor(np.asarray(target, np.float64))) ** 2).sum())
+
+
+def _root_newton(y_star: np.ndarray, l, G, dG):
+    """One Newton step from the detached root y*: same value, derivative 1/G'."""
+    y0 = torch.as_tensor(y_star, dtype=l.dtype)
+    return y0 - G(y0, l) / dG(y0)
+
+
+def prox_torch(s, w, sigma: float, energy: Energy):
+    """Prox^{KL}_{sigma f}(s) cell by cell (the maps of ``oracle.prox.prox``),
+    differentiable in s and w (torch float64)."""
+    if energy.binary:
+        raise ValueError("binary congestion (Eq. dfn-congestion-noncvx) has no derivative")
+    N = s.numel()
+    _, kappa, alpha, mask = energy.arrays(N)
+    pos = s > 0
+    l = torch.log(torch.where(pos, s, torch.ones_like(s))) - sigma * w
+    l_np = l.detach().numpy()
+    if energy.m_field is not None:
+        m1 = energy.exponents(N) - 1.0
+        c = sigma * alpha * (m1 + 1.0)
+        y_star = _prox.genent_log_psi(l_np, c, m1)
+        m1t, ct = torch.as_tensor(m1), torch.as_tensor(c)
+        lin = m1t == 0
+        m1s = torch.where(lin, torch.ones_like(m1t), m1t)
+
+        def G(y, lv):       # y + c E(y) - l, E(y) = (e^{m1 y} - 1)/m1 (= y at m1 = 0)
+            return y + ct * torch.where(lin, y, torch.expm1(m1s * y) / m1s) - lv
+
+        def dG(y):
+            return 1.0 + ct * torch.where(lin, torch.ones_like(y), torch.exp(m1s * y))
+
+        psi = torch.exp(_root_newton(y_star, l, G, dG))
+    elif energy.m == 0:
+        psi = torch.exp(l)
+    elif energy.m == 1:
+        psi = torch.exp(l / (1.0 + sigma * torch.as_tensor(alpha)))
+    else:
+        m = float(energy.m)
+        beta = sigma * alpha * m / (m - 1.0)
+        y_star = np.log(_prox.root_lambertw(l_np, beta, m))
+        bt = torch.as_tensor(beta)
+
+        def G(y, lv):       # log psi + beta psi^{m-1} - l with y = log psi
+            return y + bt * torch.exp((m - 1.0) * y) - lv
+
+        def dG(y):
+            return 1.0 + (m - 1.0) * bt * torch.exp((m - 1.0) * y)
+
+        psi = torch.exp(_root_newton(y_star, l, G, dG))
+    kt = torch.as_tensor(kappa)
+    p = torch.where(psi < kt, psi, kt)            # Prop. 4.1: clamp at kappa (tie takes kappa)
+    keep = torch.as_tensor(~mask, dtype=s.dtype)
+    return torch.where(pos, p, torch.zeros_like(p)) * keep
+
+
+def energy_step_torch(q, w, Kx, Ky, ny, nx, sigma, energy: Energy, tol=1e-13,
+                      max_iter=20000, renormalize=True):
+    """One step of the 2-vector loop (Prop. 3.3 reduced) with ``prox_torch``."""
+    a = torch.ones_like(q)
+    b = torch.ones_like(q)
+    p = torch.zeros_like(q)
+    qpos = q > 0
+    for k in range(1, max_iter + 1):
+        Y = _xi(Kx, Ky, a, ny, nx)
+        if k > 1:
+            r = torch.abs(b * Y - q).sum()
+            if float(r.detach()) <= tol:
+                break
+        b = torch.where(qpos, q / Y, torch.zeros_like(q))
+        s = _xi(Kx, Ky, b, ny, nx)
+        p = prox_torch(s, w, sigma, energy)
+        a = p / s
+    if renormalize:
+        p = p / p.sum()
+    return p
+
+
+def energy_flow_loss_grad(p0, w, target, nx, ny, gamma, tau, energy: Energy, n_steps,
+                          tol=1e-13, lx=1.0, ly=1.0):
+    """L = ||p_T - target||^2 and (dL/dp0, dL/dw, p_T) for ``energy`` with its
+    potential replaced by ``w`` (the variable differentiated), FP64."""
+    Kx = torch.tensor(kernel_1d(nx, gamma, lx))
+    Ky = torch.tensor(kernel_1d(ny, gamma, ly))
+    p0t = torch.tensor(np.asarray(p0, np.float64), requires_grad=True)
+    wt = torch.tensor(np.asarray(w, np.float64), requires_grad=True)
+    p = p0t
+    for _ in range(n_steps):
+        p = energy_step_torch(p, wt, Kx, Ky, ny, nx, tau / gamma, energy, tol=tol)
+    tt = torch.tensor(np.asarray(target, np.float64))
+    L = ((p - tt) ** 2).sum()
+    L.backward()
+    return float(L), p0t.grad.numpy().copy(), wt.grad.numpy().copy(), p.detach().numpy().copy()

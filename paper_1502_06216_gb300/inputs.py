@@ -439,3 +439,29 @@ def differentiation_problem(n: int = 256, seed: int = 4000):
     X, Y = _mesh(n, n, 1.0, 1.0)
     w_star = p.w + 0.3 * _smooth_field(rng, X, Y).ravel()
     return p, w_star
+
+
+def energy_gradient_problems(n: int = 12, gamma: float = 0.01, tau: float = 0.05,
+                             seed: int = 31) -> dict:
+    """Flows whose gradient with respect to a potential is checked beyond the
+    crowd energy, each with a random potential w = 0.05 N(0, 1) per cell:
+    porous medium m = 2 with weights, obstacles and congestion at 1.3 max q0;
+    the entropy m = 1 (weights 0.5) on the crowd recipe with its congestion;
+    the generalised entropies with per-cell exponents (vary = "m") and with
+    varying weights (vary = "b").  2 steps each."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    p = porous_problem(n, seed=5, gamma=gamma, tau=tau, n_steps=2, name=f"grad-porous-{n}")
+    p.kappa = float(1.3 * p.q0.max())
+    out["porous_m2"] = p
+    p = crowd_problem(n, gamma=gamma, tau=tau, kappa_factor=1.3, n_steps=2,
+                      name=f"grad-entropy-{n}")
+    p.m, p.alpha = 1.0, np.full(p.N, 0.5)
+    out["entropy_m1"] = p
+    for vary in ("m", "b"):
+        out["genent_" + vary] = varying_exponent_problem(n, seed=9, gamma=gamma, tau=tau,
+                                                         vary=vary, n_steps=2,
+                                                         name=f"grad-genent-{vary}-{n}")
+    for p in out.values():
+        p.w = 0.05 * rng.standard_normal(p.N)
+    return out

@@ -47,3 +47,81 @@ def test_gradient_matches_central_differences(which):
             g_dir = float(gw @ d)
         fd = (f(eps) - f(-eps)) / (2 * eps)
         assert abs(fd - g_dir) <= 1e-5 * max(abs(fd), 1e-12), (fd, g_dir)
+
+
+def energy_cases(n=12):
+    """(problem, oracle Energy) per case of inputs.energy_gradient_problems."""
+    from oracle.energy import Energy
+    return {k: (pb, Energy.from_problem(pb))
+            for k, pb in inputs.energy_gradient_problems(n).items()}
+
+
+def _numpy_loss(pb, energy, p0, w, target, n_steps=2):
+    """The loss through the NumPy oracle's flow (oracle.jko), independent of
+    the torch loop that the gradient is taken through."""
+    import dataclasses
+    from oracle.gibbs import SeparableXi
+    xi = SeparableXi(pb.nx, pb.ny, pb.gamma)
+    fr = ojko.flow(p0, xi, pb.gamma, pb.tau, dataclasses.replace(energy, w=w), n_steps,
+                   tol=1e-13, max_iter=20000)
+    return float(((fr.traj[-1] - target) ** 2).sum()), fr.traj[-1]
+
+
+@pytest.mark.parametrize("case", ["porous_m2", "entropy_m1", "genent_m", "genent_b"])
+def test_energy_forward_equals_numpy_oracle(case):
+    pb, energy = energy_cases()[case]
+    target = np.full(pb.N, 1.0 / pb.N)
+    L, _, _, pT = adjoint.energy_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma,
+                                                pb.tau, energy, 2)
+    Ln, pn = _numpy_loss(pb, energy, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() <= 1e-12
+    assert abs(L - Ln) <= 1e-12 * abs(Ln)
+
+
+@pytest.mark.parametrize("case", ["porous_m2", "entropy_m1", "genent_m", "genent_b"])
+def test_energy_gradient_matches_central_differences(case):
+    """dL/dw and dL/dp0 along random directions against central differences
+    of the NumPy oracle's flow (relative 1e-5)."""
+    pb, energy = energy_cases()[case]
+    target = np.full(pb.N, 1.0 / pb.N)
+    _, gp, gw, _ = adjoint.energy_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma,
+                                                 pb.tau, energy, 2)
+    rng = np.random.default_rng(41)
+    eps = 1e-5
+    for which in ("w", "p0"):
+        d = rng.standard_normal(pb.N)
+        if which == "p0":
+            d = pb.q0 * (d - d @ pb.q0)              # relative to q0: keeps the mass and p0 >= 0
+            f = lambda e: _numpy_loss(pb, energy, pb.q0 + e * d, pb.w, target)[0]  # noqa: E731
+            g_dir = float(gp @ d)
+        else:
+            f = lambda e: _numpy_loss(pb, energy, pb.q0, pb.w + e * d, target)[0]  # noqa: E731
+            g_dir = float(gw @ d)
+        fd = (f(eps) - f(-eps)) / (2 * eps)
+        assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
+
+
+def test_energy_form_equals_crowd_form():
+    """The general form on the crowd energy gives the crowd form's gradient."""
+    from oracle.energy import Energy
+    pb, target = setup()
+    g1 = adjoint.crowd_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma, pb.tau,
+                                      pb.kappa, 2)
+    g2 = adjoint.energy_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma, pb.tau,
+                                       Energy(kappa=pb.kappa), 2)
+    assert abs(g1[0] - g2[0]) <= 1e-14
+    assert np.abs(g1[1] - g2[1]).sum() <= 1e-10 * np.abs(g1[1]).sum()
+    assert np.abs(g1[2] - g2[2]).sum() <= 1e-10 * np.abs(g1[2]).sum()
+
+
+def test_planted_root_derivative_is_caught(monkeypatch):
+    """A wrong derivative of the implicit root (its Newton step divided by
+    1.5 G') leaves the forward unchanged; the finite-difference pin must
+    reject the gradient it gives."""
+    def wrong(y_star, l, G, dG):
+        y0 = torch.as_tensor(y_star, dtype=l.dtype)
+        return y0 - G(y0, l) / (1.5 * dG(y0))
+    monkeypatch.setattr(adjoint, "_root_newton", wrong)
+    with pytest.raises(AssertionError):
+        test_energy_gradient_matches_central_differences("porous_m2")
+    test_energy_forward_equals_numpy_oracle("porous_m2")
