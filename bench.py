@@ -450,13 +450,13 @@ def run_binary(args, jko, dev, barrier, peak_bf16, steps=5):
 
 def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
     """Pairs/s of one `steps`-step flow after a 1-step warm-up on the FP32 and
-    FP64 CUDA-core forms and the TF32 tensor-core passes (stall rule W = 4:
-    its rounding floor lies above tol), and the last step of FP32 and TF32
-    against the FP64 form."""
+    FP64 CUDA-core forms and the TF32 and BF16x3 tensor-core passes (stall rule
+    W = 4: their rounding floors lie near or above tol), and the last step of
+    FP32, TF32 and BF16x3 against the FP64 form."""
     import torch
     out, finals = {}, {}
-    for form in ("FP32", "FP64", "TF32"):
-        kw = {"stall": 4} if form == "TF32" else {}
+    for form in ("FP32", "FP64", "TF32", "BF16X3"):
+        kw = {"stall": 4} if form in ("TF32", "BF16X3") else {}
         h = jko.create_from_problem(pb, precision=jko.Precision[form], **kw)
         p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
         jko.jko_flow(h, p0, 1)
@@ -470,15 +470,19 @@ def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
         iters = sum(i["iters"] for i in infos)
         finals[form] = pf.double()
         out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
-                     "pairs_per_step": iters / steps, "kernels_per_pair": kernels_per_pair}
+                     "pairs_per_step": iters / steps,
+                     # BF16x3: one split launch before each of the pair's two xi applications
+                     "kernels_per_pair": kernels_per_pair + (2 if form == "BF16X3" else 0)}
         if form == "FP32" and roofline:
             out[form]["roofline"] = form_roofline(jko, h, form, None)
         jko.jko_destroy(h)
-    for form in ("FP32", "TF32"):
+    for form in ("FP32", "TF32", "BF16X3"):
         out[form]["rel_l1_vs_fp64_form"] = float((finals[form] - finals["FP64"]).abs().sum() /
                                                  finals["FP64"].abs().sum())
     out["TF32"]["note"] = ("Gibbs-kernel passes of all couplings on the tensor cores (one "
                            "launch per pass), joint prox on the CUDA cores")
+    out["BF16X3"]["note"] = ("as TF32 with bf16 pairs of images and factor (three products); "
+                             "one split launch per application of xi")
     return out
 
 

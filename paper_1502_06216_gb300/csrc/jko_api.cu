@@ -318,11 +318,16 @@ cudaError_t begin_pairwise(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
-// ---- the steps with several couplings on the TF32 tensor cores (tc_multi.cu) ----
+// ---- the steps with several couplings on the TF32 / BF16x3 tensor cores (tc_multi.cu) ----
 // The same iterations as above with each filter pair replaced by the
 // tensor-core passes over x then y (xi is separable and symmetric, so the
-// order changes the rounding only) and the scalings that feed them rounded to
-// tf32 by the joint prox kernels.  xi b_m goes to the prox as fp32.
+// order changes the rounding only).  TF32: the scalings that feed them are
+// rounded to tf32 by the joint prox kernels.  BF16x3: the scalings stay fp32
+// and each application of xi first splits its nz images into bf16 pairs
+// (h->mpair); the intermediates are pairs.  xi b_m goes to the prox as fp32.
+
+// rnd argument of the joint prox kernels for this handle's tensor-core form
+int multi_rnd(const jko_handle* h) { return jko::tc_mode(h->tc) == 2 ? 1 : 0; }
 
 // xi applied to nz images: in -> out, through the intermediates ts; the
 // second pass's epilogue `epi` (EPI_B against q, or TC_EPI_RAW); the first
@@ -330,10 +335,19 @@ cudaError_t begin_pairwise(jko_handle* h, cudaStream_t st) {
 cudaError_t tc_xi_multi(jko_handle* h, int nz, void* const* in, void* const* out, int epi,
                         const void* const* q, int decide, int nparts, cudaStream_t st) {
   void* ts[3] = {h->t1, h->t2, h->t3};
-  cudaError_t e = jko::tc_multi_pass(h->tc, 0, nz, (const float* const*)in, (float* const*)ts,
-                                     jko::EPI_STORE, nullptr, h->part, nparts, decide, st);
+  const void* ops[3] = {in[0], nz > 1 ? in[1] : in[0], nz > 2 ? in[2] : in[0]};
+  if (h->mpair) {
+    // BF16x3: the operand pairs of the first pass, 4 bytes per cell each
+    void* pairs[3];
+    for (int z = 0; z < 3; ++z) pairs[z] = (unsigned char*)h->mpair + (size_t)z * 4 * h->N;
+    cudaError_t e = jko::tc_split_pairs(nz, (const float* const*)in, pairs, h->N, st);
+    if (e != cudaSuccess) return e;
+    for (int z = 0; z < 3; ++z) ops[z] = pairs[z];
+  }
+  cudaError_t e = jko::tc_multi_pass(h->tc, 0, nz, ops, ts, jko::EPI_STORE, nullptr, h->part,
+                                     nparts, decide, st);
   if (e != cudaSuccess) return e;
-  return jko::tc_multi_pass(h->tc, 1, nz, (const float* const*)ts, (float* const*)out, epi,
+  return jko::tc_multi_pass(h->tc, 1, nz, (const void* const*)ts, out, epi,
                             (const float* const*)q, h->part, 0, 0, st);
 }
 
@@ -348,7 +362,7 @@ cudaError_t enqueue_pair_attraction_tc(jko_handle* h, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   return jko::launch_attraction_prox<float>(h->ek, (const float*)h->s1, (const float*)h->s2,
                                             (float*)h->a, (float*)h->a2, (float*)h->p, h->N,
-                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, 1);
+                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, multi_rnd(h));
 }
 
 cudaError_t enqueue_pair_species_tc(jko_handle* h, cudaStream_t st) {
@@ -363,7 +377,7 @@ cudaError_t enqueue_pair_species_tc(jko_handle* h, cudaStream_t st) {
   return jko::launch_species_prox<float>((const float*)h->s1, (const float*)h->s2,
                                          (const float*)h->E, (const float*)h->E2, (float*)h->a,
                                          (float*)h->a2, (float*)h->p, h->N, h->kappa_s,
-                                         h->has_kappa, h->ctrl, st, 1);
+                                         h->has_kappa, h->ctrl, st, multi_rnd(h));
 }
 
 cudaError_t enqueue_pair_pairwise_tc(jko_handle* h, cudaStream_t st) {
@@ -379,13 +393,13 @@ cudaError_t enqueue_pair_pairwise_tc(jko_handle* h, cudaStream_t st) {
     e = jko::launch_pairwise_rows<float>((const float*)h->s1, (const float*)h->s2,
                                          (const float*)h->s3, (const float*)h->E, q1 + N,
                                          (float*)h->a, (float*)h->a2, (float*)h->a3, p1, N, t,
-                                         h->kappa_s, h->has_kappa, h->ctrl, st, 1);
+                                         h->kappa_s, h->has_kappa, h->ctrl, st, multi_rnd(h));
   if (e == cudaSuccess) e = tc_xi_multi(h, 3, as, ss, jko::TC_EPI_RAW, nullptr, 0, 0, st);
   if (e != cudaSuccess) return e;
   return jko::launch_pairwise_cols<float>((const float*)h->s1, (const float*)h->s2,
                                           (const float*)h->s3, (const float*)h->E2, q1,
                                           (float*)h->b, (float*)h->b2, (float*)h->b3, p1 + N,
-                                          h->part, N, t, h->kappa_s, h->has_kappa, h->ctrl, st, 1);
+                                          h->part, N, t, h->kappa_s, h->has_kappa, h->ctrl, st, multi_rnd(h));
 }
 
 // Start of an attraction or two-species step on the tensor cores: b_m = 1,
@@ -404,10 +418,10 @@ cudaError_t begin_multi_tc(jko_handle* h, cudaStream_t st) {
     return jko::launch_species_prox<float>((const float*)h->s1, (const float*)h->s2,
                                            (const float*)h->E, (const float*)h->E2, (float*)h->a,
                                            (float*)h->a2, (float*)h->p, N, h->kappa_s,
-                                           h->has_kappa, h->ctrl, st, 1);
+                                           h->has_kappa, h->ctrl, st, multi_rnd(h));
   return jko::launch_attraction_prox<float>(h->ek, (const float*)h->s1, (const float*)h->s2,
                                             (float*)h->a, (float*)h->a2, (float*)h->p, N,
-                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, 1);
+                                            h->prm.tau, jko::prox_args<float>(h), h->ctrl, st, multi_rnd(h));
 }
 
 // One iteration with the heat-kernel Gibbs kernel (Sec. 4.1, heat.cu):
@@ -435,8 +449,9 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 // kernels one pair launches
 long long pair_kernels(const jko_handle* h) {
   if (h->heat_L) return 2LL * jko::heat_launches(h->heat) + 2;
-  if (h->pair_alpha > 0) return 6;
-  return h->attract || h->species == 2 ? 5 : 4;
+  const long long split = h->mpair ? 2 : 0;   // BF16x3 several couplings: pair splits
+  if (h->pair_alpha > 0) return 6 + split;
+  return h->attract || h->species == 2 ? 5 + split : 4;
 }
 
 cudaError_t enqueue_pass(jko_handle* h, int which, cudaStream_t st) {
@@ -659,7 +674,7 @@ void free_handle(jko_handle* h) {
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
                   h->fft_khat_x, h->fft_tw_x, h->fft_khat_y, h->fft_tw_y,
                   h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
-                  h->hb.d[3], h->hb.coef, h->a3, h->b3, h->s3, h->t2, h->t3};
+                  h->hb.d[3], h->hb.coef, h->a3, h->b3, h->s3, h->t2, h->t3, h->mpair};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);
   if (h->poll) cudaFreeHost(h->poll);
@@ -727,19 +742,22 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return (*msg = "m must be 0 or >= 1", JKO_ERR_INVALID_ARG);
   if (en->target || en->species == 2) {
-    // several couplings: the CUDA-core forms, or the TF32 tensor-core passes
-    // (tc_multi.cu) on grids whose rows are whole 16-byte units
-    if (p->precision != JKO_FP32 && p->precision != JKO_FP64 && p->precision != JKO_TF32)
-      return (*msg = "the steps with several couplings run on JKO_FP32 / JKO_FP64 / JKO_TF32",
-              JKO_ERR_UNSUPPORTED);
-    if (p->precision == JKO_TF32) {
-      if (g->nx % 4 != 0 || g->ny % 4 != 0)
-        return (*msg = "several couplings on JKO_TF32 need nx and ny multiples of 4",
+    // several couplings: the CUDA-core forms, or the TF32 / BF16x3 tensor-core
+    // passes (tc_multi.cu) on grids whose rows are whole 16-byte units
+    if (p->precision == JKO_BF16)
+      return (*msg = "the steps with several couplings run on JKO_FP32 / JKO_FP64 / JKO_TF32 / "
+                     "JKO_BF16X3", JKO_ERR_UNSUPPORTED);
+    if (p->precision == JKO_TF32 || p->precision == JKO_BF16X3) {
+      const int unit = p->precision == JKO_TF32 ? 4 : 8;
+      if (g->nx % unit != 0 || g->ny % unit != 0)
+        return (*msg = p->precision == JKO_TF32
+                           ? "several couplings on JKO_TF32 need nx and ny multiples of 4"
+                           : "several couplings on JKO_BF16X3 need nx and ny multiples of 8",
                 JKO_ERR_UNSUPPORTED);
       if (p->absorb == 1 || p->absorb == 3 || p->loop == 1 || p->loop == 3 || p->finish ||
           (p->tile != 0 && p->tile != 64))
-        return (*msg = "several couplings on JKO_TF32 run their own passes: absorb 0 or 2, loop 0 "
-                       "or 2, tile 0 or 64, no finish", JKO_ERR_UNSUPPORTED);
+        return (*msg = "several couplings on the tensor cores run their own passes: absorb 0 or "
+                       "2, loop 0 or 2, tile 0 or 64, no finish", JKO_ERR_UNSUPPORTED);
     }
   }
   if (en->target) {
@@ -1495,6 +1513,13 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     if (s == JKO_OK && multi) {
       h->tc_multi = 1;
       h->use_loop = 0;
+      if (params->precision == JKO_BF16X3) {
+        // the bf16 pairs of the first pass's images (up to 3, 4 bytes per cell each)
+        const size_t pb = (size_t)3 * 4 * h->N;
+        cudaError_t me = cudaMalloc(&h->mpair, pb);
+        if (me == cudaSuccess) me = cudaMemset(h->mpair, 0, pb);
+        if (me != cudaSuccess) s = cuda_err(h, me, "cudaMalloc(operand pairs)");
+      }
     } else if (s == JKO_OK) {
       const int ok = jko::tc_loop_supported(h->tc);
       if ((params->loop == 1 || params->loop == 3) && !ok)

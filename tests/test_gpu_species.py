@@ -28,7 +28,8 @@ def gpu_flow(pb, prec, n_steps, **kw):
 
 @pytest.mark.parametrize("prec,n,bar", [("FP64", 32, 1e-11), ("FP64", 40, 1e-11),
                                         ("FP32", 64, 1e-5), ("TF32", 64, 1e-3),
-                                        ("TF32", 100, 1e-3)])
+                                        ("TF32", 100, 1e-3), ("BF16X3", 64, 1e-5),
+                                        ("BF16X3", 96, 1e-5)])
 def test_two_species_flow_matches_oracle(prec, n, bar):
     tol = 1e-11 if prec == "FP64" else 1e-6
     pb = inputs.two_species_problem(n, gamma=2e-3, tau=0.05, n_steps=3, tol=tol, max_iter=4000)
