@@ -50,9 +50,9 @@ FP64_TFLOPS_NOMINAL = 1.25
 # the counters are taken again.
 KERNEL_SOURCES = ("tc_gemm.cu", "tc_gemm.h", "tc_loop.cu", "tc_common.cuh", "jko_internal.cuh")
 PROFILED_TRAFFIC = {
-    "src_sha256": "11166548278d53bcec4f0a30d79b12f103d54cd898e83962716c6d0e07d8532b",
+    "src_sha256": "2da7ca7c946cd292569cb5a1f2032d734a78b5ad04de1366bdb5a4d28c1a8454",
     "precision": "BF16", "n": 1024,
-    "loop": 13680640.0 + 1372928.0,     # one 200-pair launch (one step)
+    "loop": 13726208.0 + 1276160.0,     # one 200-pair launch (one step)
     "passes": [None, None, None, None],  # per-pass kernels: not captured for these sources
 }
 LOOP_PAIRS = 200  # pairs per launch of the loop kernel: one step of the workload (<= 200 pairs)
@@ -450,13 +450,13 @@ def run_binary(args, jko, dev, barrier, peak_bf16, steps=5):
 
 def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
     """Pairs/s of one `steps`-step flow after a 1-step warm-up on the FP32 and
-    FP64 CUDA-core forms and the TF32 and BF16x3 tensor-core passes (stall rule
-    W = 4: their rounding floors lie near or above tol), and the last step of
-    FP32, TF32 and BF16x3 against the FP64 form."""
+    FP64 CUDA-core forms and the TF32, BF16 and BF16x3 tensor-core passes
+    (stall rule W = 4: their rounding floors lie near or above tol), and the
+    last step of each against the FP64 form."""
     import torch
     out, finals = {}, {}
-    for form in ("FP32", "FP64", "TF32", "BF16X3"):
-        kw = {"stall": 4} if form in ("TF32", "BF16X3") else {}
+    for form in ("FP32", "FP64", "TF32", "BF16", "BF16X3"):
+        kw = {"stall": 4} if form in ("TF32", "BF16", "BF16X3") else {}
         h = jko.create_from_problem(pb, precision=jko.Precision[form], **kw)
         p0 = torch.tensor(pb.q0, dtype=h.dtype, device=dev)
         jko.jko_flow(h, p0, 1)
@@ -471,18 +471,20 @@ def coupled_leg(jko, dev, barrier, pb, steps, kernels_per_pair, roofline=False):
         finals[form] = pf.double()
         out[form] = {"iters_per_s": iters / secs, "jko_steps_per_s": steps / secs,
                      "pairs_per_step": iters / steps,
-                     # BF16x3: one split launch before each of the pair's two xi applications
-                     "kernels_per_pair": kernels_per_pair + (2 if form == "BF16X3" else 0)}
+                     # bf16 forms: one split launch before each of the pair's two xi applications
+                     "kernels_per_pair": kernels_per_pair + (2 if form.startswith("BF16") else 0)}
         if form == "FP32" and roofline:
             out[form]["roofline"] = form_roofline(jko, h, form, None)
         jko.jko_destroy(h)
-    for form in ("FP32", "TF32", "BF16X3"):
+    for form in ("FP32", "TF32", "BF16", "BF16X3"):
         out[form]["rel_l1_vs_fp64_form"] = float((finals[form] - finals["FP64"]).abs().sum() /
                                                  finals["FP64"].abs().sum())
     out["TF32"]["note"] = ("Gibbs-kernel passes of all couplings on the tensor cores (one "
                            "launch per pass), joint prox on the CUDA cores")
     out["BF16X3"]["note"] = ("as TF32 with bf16 pairs of images and factor (three products); "
                              "one split launch per application of xi")
+    out["BF16"]["note"] = ("as BF16X3 with the factor in bf16 alone (one product of the "
+                           "image pair)")
     return out
 
 

@@ -176,15 +176,18 @@ typedef struct jko_energy {
                                  W_gamma(r, p) toward this target density r (N entries, >= 0,
                                  sum 1, 0 on the mask); the other terms form h of
                                  Eq. prox-psi-attraction.  The step runs the generic diagonal
-                                 scaling with 2 couplings.  JKO_FP32 / JKO_FP64 only; not for
-                                 batches, the adjoint or jko_step_noalloc.  NULL = none */
+                                 scaling with 2 couplings.  JKO_FP32 / JKO_FP64 (CUDA cores),
+                                 or the tensor-core passes of every coupling: JKO_TF32 (nx, ny
+                                 multiples of 4), JKO_BF16 / JKO_BF16X3 (multiples of 8), with
+                                 absorb 0 or 2, loop 0 or 2, tile 0 or 64 and no finish; not
+                                 for batches, the adjoint or jko_step_noalloc.  NULL = none */
   int species;                /* 2: two densities coupled through the congestion of their sum,
                                  f = iota_{[0,kappa]}(p_1 + p_2) + <p_1, w> + <p_2, w2>
                                  (Sec. 5.3, summation couplings): every state image (q, p,
                                  trajectories) holds [p_1, p_2], 2 N entries, of total mass 1;
                                  scalar kappa only (no kappa_field, mask, entropy, binary or
-                                 target); JKO_FP32 / JKO_FP64; not for batches, the adjoint or
-                                 jko_step_noalloc.  0 or 1: one density */
+                                 target); the precisions of `target`; not for batches, the
+                                 adjoint or jko_step_noalloc.  0 or 1: one density */
   const double* w2;           /* potential of the second species (N entries); NULL = 0 */
   double pair_alpha;          /* > 0 with species = 2: the Wasserstein pairwise attraction
                                  f = pair_alpha W_gamma(p_1, p_2) + h_1(p_1) + h_2(p_2),

@@ -318,12 +318,12 @@ cudaError_t begin_pairwise(jko_handle* h, cudaStream_t st) {
   return e;
 }
 
-// ---- the steps with several couplings on the TF32 / BF16x3 tensor cores (tc_multi.cu) ----
+// ---- the steps with several couplings on the tensor cores (tc_multi.cu) ----
 // The same iterations as above with each filter pair replaced by the
 // tensor-core passes over x then y (xi is separable and symmetric, so the
 // order changes the rounding only).  TF32: the scalings that feed them are
-// rounded to tf32 by the joint prox kernels.  BF16x3: the scalings stay fp32
-// and each application of xi first splits its nz images into bf16 pairs
+// rounded to tf32 by the joint prox kernels.  BF16 / BF16x3: the scalings stay
+// fp32 and each application of xi first splits its nz images into bf16 pairs
 // (h->mpair); the intermediates are pairs.  xi b_m goes to the prox as fp32.
 
 // rnd argument of the joint prox kernels for this handle's tensor-core form
@@ -337,7 +337,7 @@ cudaError_t tc_xi_multi(jko_handle* h, int nz, void* const* in, void* const* out
   void* ts[3] = {h->t1, h->t2, h->t3};
   const void* ops[3] = {in[0], nz > 1 ? in[1] : in[0], nz > 2 ? in[2] : in[0]};
   if (h->mpair) {
-    // BF16x3: the operand pairs of the first pass, 4 bytes per cell each
+    // BF16 / BF16x3: the operand pairs of the first pass, 4 bytes per cell each
     void* pairs[3];
     for (int z = 0; z < 3; ++z) pairs[z] = (unsigned char*)h->mpair + (size_t)z * 4 * h->N;
     cudaError_t e = jko::tc_split_pairs(nz, (const float* const*)in, pairs, h->N, st);
@@ -449,7 +449,7 @@ cudaError_t enqueue_pair_heat(jko_handle* h, cudaStream_t st) {
 // kernels one pair launches
 long long pair_kernels(const jko_handle* h) {
   if (h->heat_L) return 2LL * jko::heat_launches(h->heat) + 2;
-  const long long split = h->mpair ? 2 : 0;   // BF16x3 several couplings: pair splits
+  const long long split = h->mpair ? 2 : 0;   // bf16 forms of several couplings: pair splits
   if (h->pair_alpha > 0) return 6 + split;
   return h->attract || h->species == 2 ? 5 + split : 4;
 }
@@ -742,17 +742,15 @@ jko_status check_create_args(const jko_grid* g, const jko_params* p, const jko_e
   if (!(en->m == 0.0 || en->m >= 1.0) || !std::isfinite(en->m))
     return (*msg = "m must be 0 or >= 1", JKO_ERR_INVALID_ARG);
   if (en->target || en->species == 2) {
-    // several couplings: the CUDA-core forms, or the TF32 / BF16x3 tensor-core
-    // passes (tc_multi.cu) on grids whose rows are whole 16-byte units
-    if (p->precision == JKO_BF16)
-      return (*msg = "the steps with several couplings run on JKO_FP32 / JKO_FP64 / JKO_TF32 / "
-                     "JKO_BF16X3", JKO_ERR_UNSUPPORTED);
-    if (p->precision == JKO_TF32 || p->precision == JKO_BF16X3) {
+    // several couplings: the CUDA-core forms, or the tensor-core passes
+    // (tc_multi.cu) on grids whose rows are whole 16-byte units
+    if (p->precision == JKO_TF32 || p->precision == JKO_BF16 || p->precision == JKO_BF16X3) {
       const int unit = p->precision == JKO_TF32 ? 4 : 8;
       if (g->nx % unit != 0 || g->ny % unit != 0)
         return (*msg = p->precision == JKO_TF32
                            ? "several couplings on JKO_TF32 need nx and ny multiples of 4"
-                           : "several couplings on JKO_BF16X3 need nx and ny multiples of 8",
+                           : "several couplings on JKO_BF16 / JKO_BF16X3 need nx and ny "
+                             "multiples of 8",
                 JKO_ERR_UNSUPPORTED);
       if (p->absorb == 1 || p->absorb == 3 || p->loop == 1 || p->loop == 3 || p->finish ||
           (p->tile != 0 && p->tile != 64))
@@ -1513,7 +1511,7 @@ jko_status jko_create(const jko_grid* grid, const jko_params* params, const jko_
     if (s == JKO_OK && multi) {
       h->tc_multi = 1;
       h->use_loop = 0;
-      if (params->precision == JKO_BF16X3) {
+      if (params->precision == JKO_BF16 || params->precision == JKO_BF16X3) {
         // the bf16 pairs of the first pass's images (up to 3, 4 bytes per cell each)
         const size_t pb = (size_t)3 * 4 * h->N;
         cudaError_t me = cudaMalloc(&h->mpair, pb);

@@ -68,8 +68,8 @@ struct jko_handle {
   int part_cap = 0;       // entries of part (residual and mass partials)
   int use_loop = 0;       // chunks run as one persistent kernel (tensor cores or heat kernel)
   int heat_G = 0;         // blocks of the heat kernel's persistent form
-  int tc_multi = 0;       // several couplings on the TF32 / BF16x3 tensor cores (tc_multi.cu)
-  void* mpair = nullptr;  // BF16x3 several couplings: bf16 pairs of the first pass's images
+  int tc_multi = 0;       // several couplings on the tensor cores (tc_multi.cu)
+  void* mpair = nullptr;  // bf16 forms of several couplings: pairs of the first pass's images
   Ctrl* ctrl_init = nullptr;   // pinned initial value
   Ctrl* poll = nullptr;        // pinned, 2 slots for pipelined polls
   cudaEvent_t ev_poll[2] = {nullptr, nullptr};

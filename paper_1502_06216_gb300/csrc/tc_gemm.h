@@ -46,12 +46,12 @@ int tc_create(const TcConfig& cfg, TcPlan** out, std::string* msg);
 // 0 = ok, 1 = unsupported (message set), 2 = CUDA error.
 int tc_log_setup(TcPlan* plan, const double* w_host, double sigma, std::string* msg);
 int tc_logdomain(const TcPlan* plan);
-// Passes of the steps with several couplings on a TF32 or BF16x3 plan
+// Passes of the steps with several couplings on a TF32, BF16 or BF16x3 plan
 // (tc_multi.cu): one launch applies the pass over `axis` (0: x, in [ny][nx] ->
 // out [nx][ny]; 1: y, in [nx][ny] -> out [ny][nx]) to nz <= 3 images (nx, ny
-// multiples of 4 for TF32, of 8 for BF16x3).  Inputs are operand images: fp32
-// (TF32), or one buffer per image with the bf16 pair hi [rows][cols] then lo
-// (BF16x3).  epi: EPI_STORE (out as operand image: rounded to tf32, or the
+// multiples of 4 for TF32, of 8 for the bf16 forms).  Inputs are operand
+// images: fp32 (TF32), or one buffer per image with the bf16 pair
+// hi [rows][cols] then lo (BF16, BF16x3).  epi: EPI_STORE (out as operand image: rounded to tf32, or the
 // pair), EPI_B (b = q / D as fp32, rounded to tf32 in the TF32 form; residual
 // partials of image z at part + z * tiles), TC_EPI_RAW (out as fp32).  The
 // pass takes the stop decision on `nparts` partials when decide = 1.
@@ -61,7 +61,7 @@ cudaError_t tc_multi_pass(TcPlan* plan, int axis, int nz, const void* const* in,
                           int epi, const float* const* q, double* part, int nparts, int decide,
                           cudaStream_t st);
 // fp32 images x_z of n elements -> their bf16 pairs (hi at pairs[z], lo n
-// elements after), the operands of the BF16x3 form's first pass.
+// elements after), the operands of the bf16 forms' first pass.
 cudaError_t tc_split_pairs(int nz, const float* const* x, void* const* pairs, long long n,
                            cudaStream_t st);
 int tc_mode(const TcPlan* plan);   // MODE_BF16 = 0, MODE_BF16X3 = 1, MODE_TF32 = 2

@@ -1,8 +1,9 @@
 // tc_multi.cu -- the Gibbs-kernel passes of the steps with several couplings
 // (Sec. 5.1 generic diagonal scaling: the Wasserstein attraction of Sec. 5.2,
 // the two species and the pairwise attraction of Sec. 5.3) on the tensor
-// cores (TF32, or BF16x3: images and factor as bf16 pairs hi + lo, the
-// products K_hi . (x_hi + x_lo) + K_lo . x_hi as in the single-density form).
+// cores: TF32; BF16 (the factor in bf16, images as bf16 pairs hi + lo, one
+// product K_hi . (x_hi + x_lo)); BF16x3 (the factor as a pair too, plus
+// K_lo . x_hi), the products of the single-density forms.
 //
 // Those steps apply the same separable xi to M = 2 or 3 images per half-step
 // and meet at a joint proximal map (attraction.cu) that couples the images
@@ -15,14 +16,14 @@
 //   EPI_STORE  D as the operand (rounded to tf32, or the bf16 pair): the
 //              intermediate, next pass's operand;
 //   EPI_B      b_z = q_z / D (rounded to tf32 in the TF32 form; fp32 in the
-//              BF16x3 form, split into its pair before the next pass), and the
+//              bf16 forms, split into its pair before the next pass), and the
 //              residual |b_old D - q_z| partial of the tile (part + z * tiles);
 //   EPI_RAW    D as fp32: xi b_z for the joint prox, which reads it at full
 //              precision (the single-density TF32 form's prox reads the
 //              accumulator itself).
 // The joint prox kernels round their scalings to tf32 when they feed the TF32
-// form, as the single-density TF32 epilogue does; the BF16x3 form takes fp32
-// scalings and splits every image of the first pass into its bf16 pair
+// form, as the single-density TF32 epilogue does; the bf16 forms take fp32
+// scalings and split every image of the first pass into its bf16 pair
 // (tc_split_pairs).
 #include "tc_common.cuh"
 
@@ -35,11 +36,12 @@ constexpr int MNT = 128;                 // 4 warps, one per TMEM lane quadrant
 constexpr int MAXZ = 3;
 constexpr int EPI_RAW = TC_EPI_RAW;
 
-// pipeline stages: 24 KB (TF32) or 48 KB (BF16x3: factor and image pairs)
-__host__ __device__ constexpr int multi_stages(int mode) { return mode == MODE_TF32 ? 6 : 4; }
+// pipeline stages: 24 KB (TF32), 32 KB (BF16: image pairs), 48 KB (BF16x3:
+// factor and image pairs)
+__host__ __device__ constexpr int multi_stages(int mode) { return mode == MODE_BF16X3 ? 4 : 6; }
 
 struct MultiMaps {
-  CUtensorMap A[2];       // factor of the pass (hi, lo: BF16x3)
+  CUtensorMap A[2];       // factor of the pass (hi; lo: BF16x3)
   CUtensorMap B[MAXZ][2]; // images (64-row boxes), hi [+ lo]
   CUtensorMap O[MAXZ][2]; // outputs (128-row boxes), hi [+ lo] when operand-typed
 };
@@ -88,10 +90,9 @@ tc_multi_kernel(const __grid_constant__ MultiMaps maps, MultiArgs args) {
   constexpr uint32_t IDESC = make_idesc<MODE_TF32>(BM, MBN);
   constexpr int CB = MBN * 4 / 128;                        // 128-byte column blocks (fp32)
   constexpr uint32_t OUT_BLOCK = BM * 128;
-  // an operand-typed output (EPI_STORE) of the BF16x3 form: hi and lo tiles
+  // an operand-typed output (EPI_STORE) of the bf16 forms: hi and lo tiles
   constexpr bool PAIR_OUT = EPI == EPI_STORE && MODE != MODE_TF32;
   static_assert(CB * OUT_BLOCK <= MSTAGES * STAGE_BYTES, "staging fits the stages");
-  static_assert(MODE == MODE_TF32 || MODE == MODE_BF16X3, "TF32 or BF16x3 operands");
 
   Ctrl* ctrl = args.ctrl;
   __shared__ int s_it;
@@ -152,10 +153,9 @@ tc_multi_kernel(const __grid_constant__ MultiMaps maps, MultiArgs args) {
       const int kx = kb.x + i * KE;
       tma_load_2d(st, &maps.A[0], &full_bar[s], kx, m0);
       tma_load_2d(st + A_BYTES, mapB, &full_bar[s], kx, n0);
-      if constexpr (NSPLIT == 2) {
+      if constexpr (NSPLIT == 2)
         tma_load_2d(st + A_BYTES + B_BYTES, &maps.B[z][1], &full_bar[s], kx, n0);
-        tma_load_2d(st + ALO_OFF, &maps.A[1], &full_bar[s], kx, m0);
-      }
+      if constexpr (fac_split(MODE)) tma_load_2d(st + ALO_OFF, &maps.A[1], &full_bar[s], kx, m0);
     }
     if (!ok) atomicOr(&s_fault, 1);
   } else if (warp == 1 && lane == 0) {
@@ -278,7 +278,10 @@ constexpr size_t multi_smem_bytes(int mode) {
   return (size_t)multi_stages(mode) * stage_bytes(mode, MBN) + 1024 +
          (2 * multi_stages(mode) + 2) * 8 + 16;
 }
-static_assert(multi_smem_bytes(MODE_BF16X3) <= 227 * 1024, "BF16x3 stages fit shared memory");
+static_assert(multi_smem_bytes(MODE_BF16X3) <= 227 * 1024 &&
+                  multi_smem_bytes(MODE_BF16) <= 227 * 1024 &&
+                  multi_smem_bytes(MODE_TF32) <= 227 * 1024,
+              "the stages fit shared memory");
 
 template <int MODE, int EPI>
 cudaError_t launch_multi(const MultiMaps& maps, const MultiArgs& a, int nz, cudaStream_t st) {
@@ -356,17 +359,16 @@ cudaError_t tc_multi_pass(TcPlan* P, int axis, int nz, const void* const* in, vo
                           cudaStream_t st) {
   const TcConfig& c = P->cfg;
   const int mode = P->mode;
-  if ((mode != MODE_TF32 && mode != MODE_BF16X3) || P->absorbed || nz < 1 || nz > MAXZ)
-    return cudaErrorInvalidValue;
+  if (P->absorbed || nz < 1 || nz > MAXZ) return cudaErrorInvalidValue;
   const int row_unit = mode == MODE_TF32 ? 4 : 8;       // 16-byte rows of the operands
   if (c.nx % row_unit != 0 || c.ny % row_unit != 0) return cudaErrorInvalidValue;
   MultiMaps maps;
   MultiArgs a{};
   // axis 0: in [ny][nx] -> out [nx][ny] (M = nx); axis 1: in [nx][ny] -> out [ny][nx].
-  // Operand images (every input; the output of EPI_STORE) in the BF16x3 form:
+  // Operand images (every input; the output of EPI_STORE) in the bf16 forms:
   // the pair as one buffer, hi [rows][pitch] then lo [rows][pitch].
   const int M = axis == 0 ? c.nx : c.ny, N = axis == 0 ? c.ny : c.nx;
-  const bool pair_out = epi == EPI_STORE && mode == MODE_BF16X3;
+  const bool pair_out = epi == EPI_STORE && mode != MODE_TF32;
   maps.A[0] = P->mK[axis][0][0];
   maps.A[1] = mode == MODE_BF16X3 ? P->mK[axis][0][1] : P->mK[axis][0][0];
   const size_t lo_in = (size_t)N * M * 2, lo_out = (size_t)M * N * 2;   // bytes to the lo half
@@ -397,6 +399,7 @@ cudaError_t tc_multi_pass(TcPlan* P, int axis, int nz, const void* const* in, vo
   a.nparts = nparts;
   a.decide = decide;
   if (mode == MODE_BF16X3) return launch_multi_epi<MODE_BF16X3>(maps, a, nz, epi, st);
+  if (mode == MODE_BF16) return launch_multi_epi<MODE_BF16>(maps, a, nz, epi, st);
   return launch_multi_epi<MODE_TF32>(maps, a, nz, epi, st);
 }
 

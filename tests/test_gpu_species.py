@@ -29,7 +29,8 @@ def gpu_flow(pb, prec, n_steps, **kw):
 @pytest.mark.parametrize("prec,n,bar", [("FP64", 32, 1e-11), ("FP64", 40, 1e-11),
                                         ("FP32", 64, 1e-5), ("TF32", 64, 1e-3),
                                         ("TF32", 100, 1e-3), ("BF16X3", 64, 1e-5),
-                                        ("BF16X3", 96, 1e-5)])
+                                        ("BF16X3", 96, 1e-5), ("BF16", 64, 1e-3),
+                                        ("BF16", 96, 1e-3)])
 def test_two_species_flow_matches_oracle(prec, n, bar):
     tol = 1e-11 if prec == "FP64" else 1e-6
     pb = inputs.two_species_problem(n, gamma=2e-3, tau=0.05, n_steps=3, tol=tol, max_iter=4000)
@@ -77,8 +78,6 @@ def test_rejections():
     torch = need_gpu()
     from paper_1502_06216_gb300 import jko
     pb = inputs.two_species_problem(32, n_steps=1)
-    with pytest.raises(jko.JKOError):
-        jko.create_from_problem(pb, precision=jko.Precision.BF16)
     with pytest.raises(jko.JKOError):
         jko.jko_batch_create([pb], precision=jko.Precision.FP32)
     bad = copy.deepcopy(pb)
