@@ -77,7 +77,8 @@ def crowd_flow_loss_grad(p0, w, target, nx, ny, gamma, tau, kappa, n_steps, mask
     tt = torch.tensor(np.asarray(target, np.float64))
     L = ((p - tt) ** 2).sum()
     L.backward()
-    return float(L), p0t.grad.numpy().copy(), wt.grad.numpy().copy(), p.detach().numpy().copy()
+    return (float(L.detach()), p0t.grad.numpy().copy(), wt.grad.numpy().copy(),
+            p.detach().numpy().copy())
 
 
 def crowd_flow_loss(p0, w, target, nx, ny, gamma, tau, kappa, n_steps, mask=None, tol=1e-13):
@@ -181,4 +182,5 @@ def energy_flow_loss_grad(p0, w, target, nx, ny, gamma, tau, energy: Energy, n_s
     tt = torch.tensor(np.asarray(target, np.float64))
     L = ((p - tt) ** 2).sum()
     L.backward()
-    return float(L), p0t.grad.numpy().copy(), wt.grad.numpy().copy(), p.detach().numpy().copy()
+    return (float(L.detach()), p0t.grad.numpy().copy(), wt.grad.numpy().copy(),
+            p.detach().numpy().copy())

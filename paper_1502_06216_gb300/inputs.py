@@ -446,22 +446,26 @@ def energy_gradient_problems(n: int = 12, gamma: float = 0.01, tau: float = 0.05
     """Flows whose gradient with respect to a potential is checked beyond the
     crowd energy, each with a random potential w = 0.05 N(0, 1) per cell:
     porous medium m = 2 with weights, obstacles and congestion at 1.3 max q0;
-    the entropy m = 1 (weights 0.5) on the crowd recipe with its congestion;
+    the entropy m = 1 (weights 0.5) on a white-noise q0 with congestion at
+    1.3 max q0;
     the generalised entropies with per-cell exponents (vary = "m") and with
-    varying weights (vary = "b").  2 steps each."""
+    varying weights (vary = "b", sigma = 0.5).  2 steps each."""
     rng = np.random.default_rng(seed)
     out = {}
     p = porous_problem(n, seed=5, gamma=gamma, tau=tau, n_steps=2, name=f"grad-porous-{n}")
     p.kappa = float(1.3 * p.q0.max())
     out["porous_m2"] = p
-    p = crowd_problem(n, gamma=gamma, tau=tau, kappa_factor=1.3, n_steps=2,
-                      name=f"grad-entropy-{n}")
-    p.m, p.alpha = 1.0, np.full(p.N, 0.5)
+    p = varying_exponent_problem(n, seed=7, gamma=gamma, tau=tau, vary="m", n_steps=2,
+                                 name=f"grad-entropy-{n}")
+    p.m_field, p.m, p.alpha = None, 1.0, np.full(p.N, 0.5)
+    p.kappa = float(1.3 * p.q0.max())
     out["entropy_m1"] = p
     for vary in ("m", "b"):
-        out["genent_" + vary] = varying_exponent_problem(n, seed=9, gamma=gamma, tau=tau,
-                                                         vary=vary, n_steps=2,
-                                                         name=f"grad-genent-{vary}-{n}")
+        # varying weights up to 20 at sigma = 0.5: sigma b m/(m - 1) = 35 (at
+        # sigma = 5 it is 350, and e^{350} overflows the FP32 scalings)
+        out["genent_" + vary] = varying_exponent_problem(
+            n, seed=9, gamma=gamma, tau=tau if vary == "m" else 0.5 * gamma, vary=vary,
+            n_steps=2, name=f"grad-genent-{vary}-{n}")
     for p in out.values():
         p.w = 0.05 * rng.standard_normal(p.N)
     return out

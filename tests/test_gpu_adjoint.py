@@ -123,3 +123,27 @@ def test_potential_recovery_decreases_the_loss():
     print("losses", losses)
     assert losses[-1] < 0.5 * losses[0]
     jko.jko_destroy(h)
+
+
+@pytest.mark.parametrize("case", ["porous_m2", "entropy_m1", "genent_m", "genent_b"])
+@pytest.mark.parametrize("prec,tol,bar", [("FP64", 1e-13, 1e-6), ("FP32", 1e-7, 1e-3)])
+def test_adjoint_matches_oracle_other_energies(case, prec, tol, bar):
+    """The implicit adjoint for the energies beyond the crowd one (porous m = 2
+    with obstacles and congestion, the entropy m = 1 on a full-support start,
+    per-cell exponents, varying weights) against the oracle's FP64 reverse-mode
+    gradient through the unrolled loop (implicit roots differentiated by a
+    Newton step from the root), 16^2, 2 steps: relative L1 of dL/dw and of
+    dL/dp0 on the support of p0."""
+    from oracle import adjoint
+    from oracle.energy import Energy
+    pb = inputs.energy_gradient_problems(16)[case]
+    target = np.full(pb.N, 1.0 / pb.N)
+    Lo, gpo, gwo, _ = adjoint.energy_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma,
+                                                    pb.tau, Energy.from_problem(pb), 2)
+    L, gp, gw, _ = gpu_grad(pb, pb.w, target, 2, prec, tol)
+    ew = np.abs(gw - gwo).sum() / np.abs(gwo).sum()
+    sup = pb.q0 > 0
+    ep = np.abs(gp[sup] - gpo[sup]).sum() / np.abs(gpo[sup]).sum()
+    print(case, prec, "loss", L, Lo, "rel L1 grad_w", ew, "grad_p0 (support)", ep)
+    assert abs(L - Lo) <= 10 * bar * abs(Lo)
+    assert ew <= bar and ep <= bar
