@@ -82,7 +82,7 @@ typedef struct jko_grid {
    * L in [1, 1000] = the heat kernel (Id - (gamma/L) Delta_M)^{-L} of the
    * domain outside the obstacle mask (Sec. 4.1, Eq. heat-kernel), JKO_FP32 /
    * JKO_FP64 single-density handles only (JKO_ERR_UNSUPPORTED otherwise; not
-   * batched, no adjoint, no fixed-scratch step). */
+   * batched, no fixed-scratch step). */
   int heat_L;
   /* Application of the Gaussian (heat_L = 0): 0 = the band-limited separable
    * filter (CUDA cores) or tensor-core GEMMs; 1 = the same restricted Gaussian
@@ -95,7 +95,7 @@ typedef struct jko_grid {
    * that range must stay <= 8 (FP32) / 24 (FP64) (measured errors 5.5e-6 /
    * 9.3e-11 there).  JKO_FP32 / JKO_FP64 single-density handles (no target,
    * second species or heat kernel), L <= 4096 (FP32) / 2048 (FP64), else
-   * JKO_ERR_UNSUPPORTED; no adjoint, no fixed-scratch step. */
+   * JKO_ERR_UNSUPPORTED; no fixed-scratch step. */
   int fft;
 } jko_grid;
 
@@ -333,8 +333,10 @@ jko_status jko_set_potential_device(jko_handle* h, const void* w_dev);
 
 /* jko_flow that also records, for every step t, its input q_t and the final
  * scaling a_t (the tape of jko_flow_backward).  p_final_dev receives p_n;
- * infos (may be NULL) n_steps reports.  JKO_ERR_UNSUPPORTED for tensor-core
- * handles. */
+ * infos (may be NULL) n_steps reports.  Single-density JKO_FP32 / JKO_FP64
+ * handles with the Gaussian (filter or FFT) or the heat kernel; the binary
+ * congestion has no derivative.  JKO_ERR_UNSUPPORTED for tensor-core,
+ * attraction and two-species handles and the binary congestion. */
 jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void* p_final_dev,
                            jko_step_info* infos);
 
@@ -342,7 +344,8 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
  * grad_final_dev = dL/dp_n (device image); grad_p0_dev (may be NULL) receives
  * dL/dp_0, grad_w_dev (may be NULL) dL/dw (device images, the handle's element
  * type).  Each step is differentiated implicitly at its fixed point (a = r(s),
- * s = xi(q / xi a); the paper has no adjoint, this follows from Prop. 3.3's
+ * s = xi(q / xi a), xi the handle's own symmetric Gibbs kernel: the Gaussian
+ * or the heat kernel; the paper has no adjoint, this follows from Prop. 3.3's
  * fixed point by the implicit-function theorem), including the adjoint of the
  * mass renormalisation; the adjoint linear system is solved by the fixed-point
  * iteration of the transposed linearisation (tolerance params.tol relative,

@@ -22,7 +22,11 @@ prox of ``oracle.prox`` written in torch:
     At the root G(y*) = 0, so the step leaves the value unchanged to rounding
     and its derivative with respect to l is 1/G'(y*): the implicit-function
     derivative of the root.
-The non-convex binary congestion is not differentiable and is refused.
+The non-convex binary congestion is not differentiable and is refused.  The
+Gibbs kernel is the separable Gaussian, or any symmetric operator given as a
+dense matrix (``xi_dense``: the heat kernel of ``oracle.heat`` at small sizes,
+Sec. 4.1, Eq. heat-kernel); where xi b vanishes (obstacle cells of the heat
+kernel) the ratio a = p / s is 0.
 TEST INFRASTRUCTURE ONLY.
 """
 from __future__ import annotations
@@ -146,39 +150,60 @@ def prox_torch(s, w, sigma: float, energy: Energy):
     return torch.where(pos, p, torch.zeros_like(p)) * keep
 
 
-def energy_step_torch(q, w, Kx, Ky, ny, nx, sigma, energy: Energy, tol=1e-13,
-                      max_iter=20000, renormalize=True):
-    """One step of the 2-vector loop (Prop. 3.3 reduced) with ``prox_torch``."""
+def energy_step_torch(q, w, xi, sigma, energy: Energy, tol=1e-13, max_iter=20000,
+                      renormalize=True):
+    """One step of the 2-vector loop (Prop. 3.3 reduced) with ``prox_torch``;
+    ``xi`` applies the (symmetric) Gibbs kernel to a torch vector."""
     a = torch.ones_like(q)
     b = torch.ones_like(q)
     p = torch.zeros_like(q)
     qpos = q > 0
     for k in range(1, max_iter + 1):
-        Y = _xi(Kx, Ky, a, ny, nx)
+        Y = xi(a)
         if k > 1:
             r = torch.abs(b * Y - q).sum()
             if float(r.detach()) <= tol:
                 break
-        b = torch.where(qpos, q / Y, torch.zeros_like(q))
-        s = _xi(Kx, Ky, b, ny, nx)
+        b = torch.where(qpos, q / torch.where(qpos, Y, torch.ones_like(Y)), torch.zeros_like(q))
+        s = xi(b)
         p = prox_torch(s, w, sigma, energy)
-        a = p / s
+        spos = s > 0
+        a = torch.where(spos, p / torch.where(spos, s, torch.ones_like(s)), torch.zeros_like(s))
     if renormalize:
         p = p / p.sum()
     return p
 
 
+def heat_dense(pb) -> np.ndarray:
+    """The heat kernel xi~ of a problem (``oracle.heat``, Sec. 4.1) as a dense
+    N x N matrix: its columns are xi~ applied to the unit vectors."""
+    from .heat import problem_xi
+    xi = problem_xi(pb)
+    N = pb.nx * pb.ny
+    return np.column_stack([xi(np.eye(1, N, j).ravel()) for j in range(N)])
+
+
 def energy_flow_loss_grad(p0, w, target, nx, ny, gamma, tau, energy: Energy, n_steps,
-                          tol=1e-13, lx=1.0, ly=1.0):
+                          tol=1e-13, lx=1.0, ly=1.0, xi_dense=None):
     """L = ||p_T - target||^2 and (dL/dp0, dL/dw, p_T) for ``energy`` with its
-    potential replaced by ``w`` (the variable differentiated), FP64."""
-    Kx = torch.tensor(kernel_1d(nx, gamma, lx))
-    Ky = torch.tensor(kernel_1d(ny, gamma, ly))
+    potential replaced by ``w`` (the variable differentiated), FP64; the Gibbs
+    kernel is the separable Gaussian, or ``xi_dense`` (N x N) when given."""
+    if xi_dense is None:
+        Kx = torch.tensor(kernel_1d(nx, gamma, lx))
+        Ky = torch.tensor(kernel_1d(ny, gamma, ly))
+
+        def xi(v):
+            return _xi(Kx, Ky, v, ny, nx)
+    else:
+        Kd = torch.tensor(np.asarray(xi_dense, np.float64))
+
+        def xi(v):
+            return Kd @ v
     p0t = torch.tensor(np.asarray(p0, np.float64), requires_grad=True)
     wt = torch.tensor(np.asarray(w, np.float64), requires_grad=True)
     p = p0t
     for _ in range(n_steps):
-        p = energy_step_torch(p, wt, Kx, Ky, ny, nx, tau / gamma, energy, tol=tol)
+        p = energy_step_torch(p, wt, xi, tau / gamma, energy, tol=tol)
     tt = torch.tensor(np.asarray(target, np.float64))
     L = ((p - tt) ** 2).sum()
     L.backward()

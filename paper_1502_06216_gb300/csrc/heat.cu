@@ -34,6 +34,7 @@ struct HeatGeom {
   double cx, cy;          // c / hx^2, c / hy^2
   const uint8_t* mask;    // 1 = obstacle, or NULL
   double two_over_delta;  // 2 / delta (Clenshaw recurrence)
+  bool linear;            // output not clamped at 0 (signed inputs: the adjoint)
 };
 
 __device__ __forceinline__ bool is_free(const HeatGeom& g, int i) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step(const T* v, const void
   const W cx = wc<W>(g.cx), cy = wc<W>(g.cy);
   const W Ab = apply_A<W>(g, b1, xx, yy, cx, cy);
   const W r = cl_value(wc<W>(ck_), wv(v[i]), wc<W>(s_over_delta), Ab, wc<W>(theta_), b1[i], b2[i]);
-  if (CLOSE) ((T*)out_)[i] = close_out<T>(r);
+  if (CLOSE) ((T*)out_)[i] = g.linear ? (T)r : close_out<T>(r);
   else ((W*)out_)[i] = r;
 }
 
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(HBX * HBY) heat_cl_step2(const T* v, const voi
   if (y > 0 && is_free(g, i - g.nx)) acc = nb_term(acc, cy, c, sb[ty - 1][tx]);
   if (y + 1 < g.ny && is_free(g, i + g.nx)) acc = nb_term(acc, cy, c, sb[ty + 1][tx]);
   const W r = cl_value(wc<W>(ck1_), wv(v[i]), wc<W>(s2_), acc, theta, c, b1[i]);
-  if (CLOSE) ((T*)o2_)[i] = close_out<T>(r);
+  if (CLOSE) ((T*)o2_)[i] = g.linear ? (T)r : close_out<T>(r);
   else ((W*)o2_)[i] = r;
 }
 
@@ -625,13 +626,14 @@ HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bo
 // out_x = p(A) in with the Clenshaw recurrence of the expansion: the first
 // step b_D = c_D v, then the D remaining steps (k = D-1 .. 0, the last the
 // closing one) two per launch, one single step first when D is odd:
-// 1 + ceil(D / 2) launches.
+// 1 + ceil(D / 2) launches.  `linear`: the output is not clamped at 0 (the
+// adjoint applies xi~ to signed vectors).
 template <typename T>
 cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T* out_x,
                        int nx, int ny, const uint8_t* mask, Ctrl* ctrl, const double* part,
-                       int nparts, int decide, cudaStream_t st) {
+                       int nparts, int decide, cudaStream_t st, bool linear) {
   const double inv_delta = hp.delta > 0 ? 1.0 / hp.delta : 0.0;   // delta = 0: p(A) = c_0 Id
-  HeatGeom g{nx, ny, hp.cx, hp.cy, mask, 2.0 * inv_delta};
+  HeatGeom g{nx, ny, hp.cx, hp.cy, mask, 2.0 * inv_delta, linear};
   const dim3 grid = heat_grid(nx, ny), block(HBX, HBY);
   void* d[4] = {B.d[0], B.d[1], B.d[2], B.d[3]};   // iterates (8 bytes per cell)
   const int D = hp.D;
@@ -764,7 +766,7 @@ cudaError_t heat_prox_launch(int ek, const T* s, T* a, T* p, int nx, int ny, con
 #define JKO_HEAT_INST(T)                                                                      \
   template cudaError_t heat_apply<T>(const HeatPlan&, const HeatBuffers&, const T*, T*, int, \
                                      int, const uint8_t*, Ctrl*, const double*, int, int,     \
-                                     cudaStream_t);                                           \
+                                     cudaStream_t, bool);                                     \
   template cudaError_t heat_bupdate_launch<T>(const T*, T*, const T*, int, int, Ctrl*,        \
                                               double*, cudaStream_t);                         \
   template cudaError_t heat_prox_launch<T>(int, const T*, T*, T*, int, int,                   \

@@ -13,7 +13,10 @@
 //   gradients      qbar = qbar0 + xi(R_s (.) lambda) / Y,   wbar += R_w (.) lambda.
 // Steps are walked backwards from a tape of each step's input q_t and final a_t
 // (jko_flow_record); Y, b, s are recomputed from them.  Every xi application
-// is the two CUDA-core filter passes of the forward.
+// is the forward's own: the two CUDA-core filter passes (or their FFT form)
+// of the Gaussian, or the Clenshaw evaluation of the heat kernel xi~, which is
+// symmetric as well (Sec. 4.1, Eq. heat-kernel).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -129,8 +132,22 @@ __global__ void k_final(jko::ProxArgs<T> P, const T* s, const T* lam, const T* q
   }
 }
 
+// The FFT tables of the pass along x (lines of length nx) or along y.
+template <typename T>
+jko::FftArgs<T> fft_tables(const jko_handle* h, bool along_x) {
+  jko::FftArgs<T> F;
+  F.L = along_x ? h->fft_Lx : h->fft_Ly;
+  F.log2L = along_x ? h->fft_lgx : h->fft_lgy;
+  F.khat = (const T*)(along_x ? h->fft_khat_x : h->fft_khat_y);
+  F.tw = (const T*)(along_x ? h->fft_tw_x : h->fft_tw_y);
+  return F;
+}
+
 template <typename T>
 cudaError_t xi_apply(jko_handle* h, const T* in, T* out, cudaStream_t st) {
+  if (h->heat_L)
+    return jko::heat_apply<T>(h->heat, h->hb, in, out, h->grid.nx, h->grid.ny,
+                              (const uint8_t*)h->mask, h->ctrl, h->part, 0, 0, st, true);
   jko::ProxArgs<T> P = jko::prox_args<T>(h);
   PassArgs<T> A{};
   A.ctrl = h->ctrl;
@@ -140,12 +157,14 @@ cudaError_t xi_apply(jko_handle* h, const T* in, T* out, cudaStream_t st) {
   A.out = (T*)h->t1;
   A.taps = (const T*)h->taps_y;
   A.n_i = h->grid.ny; A.n_j = h->grid.nx; A.r = h->ry;
-  cudaError_t e = jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
+  cudaError_t e = h->fft ? jko::fft_pass<T>(jko::EPI_STORE, h->ek, A, P, fft_tables<T>(h, false), st)
+                         : jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
   if (e != cudaSuccess) return e;
   A.in = (const T*)h->t1;
   A.out = out;
   A.taps = (const T*)h->taps_x;
   A.n_i = h->grid.nx; A.n_j = h->grid.ny; A.r = h->rx;
+  if (h->fft) return jko::fft_pass<T>(jko::EPI_STORE, h->ek, A, P, fft_tables<T>(h, true), st);
   return jko::simt_pass<T>(jko::EPI_STORE, h->ek, A, P, st);
 }
 
@@ -272,10 +291,10 @@ __global__ void k_set_potential(const W* w, T* E, T* sw, double sigma, long long
 
 jko_status check_set_potential(jko_handle* h, const void* w) {
   if (!h || !w) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
-  if (h->attract || h->species == 2 || h->heat_L)
+  if (h->attract || h->species == 2)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "the potential of an attraction, two-species or heat-kernel handle is "
-                             "fixed at creation");
+                             "the potential of an attraction or two-species handle is fixed at "
+                             "creation");
   if (h->tc && jko::tc_absorbed(h->tc))
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the potential is absorbed into the Gibbs factors of this handle");
@@ -292,8 +311,18 @@ extern "C" {
 jko_status jko_set_potential(jko_handle* h, const double* w_host) {
   if (jko_status st = check_set_potential(h, w_host)) return st;
   const long long N = h->N;
-  for (long long i = 0; i < N; ++i)
+  double lo = INFINITY, hi = -INFINITY;
+  for (long long i = 0; i < N; ++i) {
     if (!std::isfinite(w_host[i])) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "w must be finite");
+    lo = std::min(lo, w_host[i]);
+    hi = std::max(hi, w_host[i]);
+  }
+  // the FFT application's range rule of jko_create: e^{sigma (max w - min w)}
+  // within e^8 (FP32) / e^24 (FP64)
+  if (h->fft && h->prm.tau / h->prm.gamma * (hi - lo) > (h->fp64 ? 24.0 : 8.0))
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the FFT application needs the potential's scalings within e^8 "
+                             "(FP32) / e^24 (FP64)");
   double* wd = nullptr;
   ACK(cudaMalloc((void**)&wd, sizeof(double) * N));
   cudaError_t e = cudaMemcpyAsync(wd, w_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
@@ -335,10 +364,6 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   if (h->attract)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the Wasserstein attraction");
   if (h->species == 2) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for two species");
-  if (h->heat_L) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the heat kernel");
-  if (h->fft)
-    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "no adjoint for the FFT application of the Gaussian");
   const size_t es = h->es, N = (size_t)h->N;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);

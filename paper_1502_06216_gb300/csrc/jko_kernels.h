@@ -157,11 +157,14 @@ struct HeatBuffers {
 HeatPlan heat_plan(int nx, int ny, double lx, double ly, double gamma, int L, bool fp64);
 int heat_blocks(int nx, int ny);   // blocks of heat_bupdate (= residual partials)
 int heat_launches(const HeatPlan& hp);   // kernel launches of one heat_apply
-// out_x = xi~ in (the first init takes the stop decision when decide = 1)
+// out_x = xi~ in (the first init takes the stop decision when decide = 1);
+// linear = true leaves the output unclamped (signed inputs, the adjoint), else
+// it is clamped at 0 (xi~ is positive; the expansion's normwise error can turn
+// far tails slightly negative)
 template <typename T>
 cudaError_t heat_apply(const HeatPlan& hp, const HeatBuffers& B, const T* in, T* out_x,
                        int nx, int ny, const uint8_t* mask, Ctrl* ctrl, const double* part,
-                       int nparts, int decide, cudaStream_t st);
+                       int nparts, int decide, cudaStream_t st, bool linear = false);
 template <typename T>
 cudaError_t heat_bupdate_launch(const T* Y, T* b, const T* q, int nx, int ny, Ctrl* ctrl,
                                 double* part, cudaStream_t st);

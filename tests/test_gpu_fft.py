@@ -116,8 +116,11 @@ def test_rejections():
         with pytest.raises(jko.JKOError) as e:
             jko.create_from_problem(crowd, precision=prec, fft=1)
         assert e.value.status == jko.Status.UNSUPPORTED
-    h = jko.create_from_problem(pb, precision=jko.Precision.FP32, fft=1)
-    import torch
-    with pytest.raises(jko.JKOError):
-        jko.jko_flow_record(h, torch.tensor(pb.q0, dtype=torch.float32, device="cuda"), 1)
+    # a new potential keeps the range rule of jko_create
+    cp = inputs.crowd_problem(64, gamma=2e-3, tau=0.005)
+    h = jko.create_from_problem(cp, precision=jko.Precision.FP32, fft=1)
+    jko.jko_set_potential(h, cp.w)
+    with pytest.raises(jko.JKOError) as e:
+        jko.jko_set_potential(h, 10.0 * cp.w)
+    assert e.value.status == jko.Status.UNSUPPORTED
     jko.jko_destroy(h)

@@ -125,3 +125,62 @@ def test_planted_root_derivative_is_caught(monkeypatch):
     with pytest.raises(AssertionError):
         test_energy_gradient_matches_central_differences("porous_m2")
     test_energy_forward_equals_numpy_oracle("porous_m2")
+
+
+def _heat_case():
+    """The two-room heat-kernel crowd at 26^2 (the smallest even grid whose
+    wall holds cells), congestion active, 2 steps."""
+    pb = inputs.heat_crowd_problem(26, n_steps=2)
+    assert pb.mask.sum() > 0
+    return pb
+
+
+def _heat_numpy_loss(pb, p0, w, target):
+    import copy
+    from oracle import heat as oheat
+    q = copy.deepcopy(pb)
+    q.q0, q.w = p0, w
+    fr = oheat.problem_flow(q, n_steps=2, tol=1e-13, max_iter=20000)
+    return float(((fr.traj[-1] - target) ** 2).sum()), fr.traj[-1]
+
+
+def test_heat_dense_kernel_is_the_operator():
+    """xi~ as a dense matrix: symmetric, zero on obstacle rows and columns, and
+    its product with a vector equals the sparse-LU application."""
+    from oracle import heat as oheat
+    pb = _heat_case()
+    K = adjoint.heat_dense(pb)
+    assert np.abs(K - K.T).max() <= 1e-14 * np.abs(K).max()
+    m = pb.mask.astype(bool)
+    assert np.all(K[m] == 0) and np.all(K[:, m] == 0)
+    v = np.random.default_rng(3).uniform(size=pb.N)
+    assert np.abs(K @ v - oheat.problem_xi(pb)(v)).max() <= 1e-14 * np.abs(K @ v).max()
+
+
+def test_heat_gradient_matches_central_differences():
+    """The oracle's gradient through the heat-kernel flow: the torch forward =
+    the NumPy heat flow (1e-12), and dL/dw, dL/dp0 = central differences of
+    the NumPy flow (relative 1e-5)."""
+    from oracle.energy import Energy
+    pb = _heat_case()
+    target = np.full(pb.N, 1.0 / pb.N) * (1 - pb.mask)
+    target /= target.sum()
+    K = adjoint.heat_dense(pb)
+    L, gp, gw, pT = adjoint.energy_flow_loss_grad(pb.q0, pb.w, target, pb.nx, pb.ny, pb.gamma,
+                                                  pb.tau, Energy.from_problem(pb), 2, xi_dense=K)
+    Ln, pn = _heat_numpy_loss(pb, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() <= 1e-12
+    assert abs(L - Ln) <= 1e-12 * abs(Ln)
+    rng = np.random.default_rng(43)
+    eps = 1e-5
+    for which in ("w", "p0"):
+        d = rng.standard_normal(pb.N)
+        if which == "p0":
+            d = pb.q0 * (d - d @ pb.q0)
+            f = lambda e: _heat_numpy_loss(pb, pb.q0 + e * d, pb.w, target)[0]  # noqa: E731
+            g_dir = float(gp @ d)
+        else:
+            f = lambda e: _heat_numpy_loss(pb, pb.q0, pb.w + e * d, target)[0]  # noqa: E731
+            g_dir = float(gw @ d)
+        fd = (f(eps) - f(-eps)) / (2 * eps)
+        assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
