@@ -81,8 +81,8 @@ typedef struct jko_grid {
   /* Gibbs kernel: 0 = the separable Gaussian e^{-|x-y|^2/gamma} (Sec. 2.1);
    * L in [1, 1000] = the heat kernel (Id - (gamma/L) Delta_M)^{-L} of the
    * domain outside the obstacle mask (Sec. 4.1, Eq. heat-kernel), JKO_FP32 /
-   * JKO_FP64 single-density handles only (JKO_ERR_UNSUPPORTED otherwise; not
-   * batched, no fixed-scratch step). */
+   * JKO_FP64 single-density handles only (JKO_ERR_UNSUPPORTED otherwise; in a
+   * batch it runs its kernels per Clenshaw phase; no fixed-scratch step). */
   int heat_L;
   /* Application of the Gaussian (heat_L = 0): 0 = the band-limited separable
    * filter (CUDA cores) or tensor-core GEMMs; 1 = the same restricted Gaussian
@@ -180,14 +180,15 @@ typedef struct jko_energy {
                                  or the tensor-core passes of every coupling: JKO_TF32 (nx, ny
                                  multiples of 4), JKO_BF16 / JKO_BF16X3 (multiples of 8), with
                                  absorb 0 or 2, loop 0 or 2, tile 0 or 64 and no finish; not
-                                 for batches, the adjoint or jko_step_noalloc.  NULL = none */
+                                 for the adjoint or jko_step_noalloc.  NULL = none */
   int species;                /* 2: two densities coupled through the congestion of their sum,
                                  f = iota_{[0,kappa]}(p_1 + p_2) + <p_1, w> + <p_2, w2>
                                  (Sec. 5.3, summation couplings): every state image (q, p,
                                  trajectories) holds [p_1, p_2], 2 N entries, of total mass 1;
                                  scalar kappa only (no kappa_field, mask, entropy, binary or
-                                 target); the precisions of `target`; not for batches, the
-                                 adjoint or jko_step_noalloc.  0 or 1: one density */
+                                 target); the precisions of `target`; in a batch the flow's
+                                 images hold 2 N entries too; not for the adjoint or
+                                 jko_step_noalloc.  0 or 1: one density */
   const double* w2;           /* potential of the second species (N entries); NULL = 0 */
   double pair_alpha;          /* > 0 with species = 2: the Wasserstein pairwise attraction
                                  f = pair_alpha W_gamma(p_1, p_2) + h_1(p_1) + h_2(p_2),

@@ -1824,18 +1824,29 @@ void free_batch(jko_batch* b) {
   delete b;
 }
 
+// The start of a flow's step inside the batch graphs: the control block reset
+// and the cold start of its form (as enqueue_step_begin for a handle alone;
+// the step input is already in h->q).
+template <typename T>
+cudaError_t flow_begin_t(jko_handle* h, cudaStream_t s) {
+  if (h->pair_alpha > 0) return begin_pairwise<T>(h, s);
+  if (h->species == 2) return begin_species<T>(h, s);
+  if (h->attract) return begin_attraction<T>(h, s);
+  return jko::launch_fill<T>((T*)h->a, T(1), h->N, s);
+}
+
 cudaError_t flow_prologue(jko_handle* h, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
+  if (h->tc_multi) return h->pair_alpha > 0 ? begin_pairwise<float>(h, s) : begin_multi_tc(h, s);
   if (h->tc) return jko::tc_begin_step(h->tc, s);
-  if (h->fp64) return jko::launch_fill<double>((double*)h->a, 1.0, h->N, s);
-  return jko::launch_fill<float>((float*)h->a, 1.0f, h->N, s);
+  return h->fp64 ? flow_begin_t<double>(h, s) : flow_begin_t<float>(h, s);
 }
 
 cudaError_t flow_chunk(jko_handle* h, int C, bool per_pass, cudaStream_t s, int loop_pairs = 0) {
   // a flow on the loop kernel: one launch runs its whole pair budget and stops
   // itself; later chunks of the step find it stopped and return at once
-  if (h->use_loop && !per_pass)
+  if (h->use_loop && h->tc && !per_pass)
     return jko::tc_enqueue_loop(h->tc, loop_pairs > 0 ? loop_pairs : h->chunk_iters, s);
   for (int i = 0; i < C; ++i) {
     cudaError_t e = enqueue_pair(h, s);
@@ -1847,11 +1858,12 @@ cudaError_t flow_chunk(jko_handle* h, int C, bool per_pass, cudaStream_t s, int 
 template <typename T>
 cudaError_t flow_finalize_t(jko_handle* h, cudaStream_t s) {
   ProxArgs<T> P = jko::prox_args<T>(h);
-  cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->N, P, h->ctrl, h->part,
+  // h->ns: both densities of a two-species flow
+  cudaError_t e = jko::launch_finalize_reduce<T>((const T*)h->p, h->ns, P, h->ctrl, h->part,
                                                  h->part_cap, s);
   if (e != cudaSuccess) return e;
   // the step output becomes the input of the next step
-  return jko::launch_finalize_write<T>((const T*)h->p, (T*)h->q, h->N, h->prm.renormalize,
+  return jko::launch_finalize_write<T>((const T*)h->p, (T*)h->q, h->ns, h->prm.renormalize,
                                        h->ctrl, s);
 }
 
@@ -2029,6 +2041,7 @@ jko_status check_input(jko_handle* h, const T* q, int flow, jko_batch* b) {
   ProxArgs<T> P = jko::prox_args<T>(h);
   BCK(b, cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   BCK(b, jko::launch_validate<T>(q, h->N, P, h->ctrl, st));
+  if (h->species == 2) BCK(b, jko::launch_validate<T>(q + h->N, h->N, P, h->ctrl, st));
   BCK(b, cudaMemcpyAsync(h->poll, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   BCK(b, cudaStreamSynchronize(st));
   const Ctrl& c = h->poll[0];
@@ -2068,12 +2081,6 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
                             "finish (the FP32 continuation of a stalled step) is for single handles"));
     if (params[f].absorb == 3)
       return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the log-domain form is for single handles"));
-    if (energies[f].target)
-      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the Wasserstein attraction is not batched"));
-    if (energies[f].species == 2)
-      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "two species are not batched"));
-    if (grids[f].heat_L)
-      return fail(batch_err(b, JKO_ERR_UNSUPPORTED, "the heat kernel is not batched"));
     jko_handle* h = nullptr;
     jko_status s = jko_create(&grids[f], &params[f], &energies[f], stream, &h);
     if (s != JKO_OK) {
@@ -2081,9 +2088,12 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
       snprintf(buf, sizeof buf, "flow %d: ", f);
       return fail(batch_err(b, s, buf + g_create_err));
     }
-    // other flows fill the GPU: the CUDA-core passes keep their throughput form
+    // other flows fill the GPU: the CUDA-core passes keep their throughput form,
+    // and a heat-kernel flow runs its kernels per Clenshaw phase (its persistent
+    // form is one cooperative launch over every SM)
     h->simt_latency = 0;
     h->nparts_simt = jko::simt_pass_blocks(grids[f].nx, grids[f].ny, 0);
+    if (h->heat_L) h->use_loop = 0;
     b->h.push_back(h);
     b->max_iter = std::max(b->max_iter, params[f].max_iter);
   }
@@ -2115,7 +2125,8 @@ jko_status jko_batch_create(int n_flows, const jko_grid* grids, const jko_params
   // kernels, time the candidates on the batch graph and keep the fastest
   bool tune = true;
   for (int f = 0; f < n_flows; ++f)
-    tune = tune && params[f].loop == 0 && params[f].tile == 0 && b->h[f]->tc;
+    tune = tune && params[f].loop == 0 && params[f].tile == 0 && b->h[f]->tc &&
+           !b->h[f]->tc_multi;
   b->in_group.assign(n_flows, 0);
   if (tune) {
     jko_status st = tune_batch(b);
@@ -2196,7 +2207,7 @@ jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
     if (s != JKO_OK) return s;
   }
   for (int f = 0; f < b->n; ++f)
-    BCK(b, cudaMemcpyAsync(b->h[f]->q, p0_dev[f], b->h[f]->es * (size_t)b->h[f]->N,
+    BCK(b, cudaMemcpyAsync(b->h[f]->q, p0_dev[f], b->h[f]->es * (size_t)b->h[f]->ns,
                            cudaMemcpyDeviceToDevice, st));
   const int n = b->n, C = b->C;
   const int max_chunks = (b->max_iter + 1 + C - 1) / C + 2;
@@ -2259,7 +2270,7 @@ jko_status jko_batch_flow(jko_batch* b, const void* const* p0_dev, int n_steps,
     for (int f = 0; f < n; ++f)
       if (p_final_dev[f])
         BCK(b, cudaMemcpyAsync(p_final_dev[f], n_steps > 0 ? b->h[f]->q : p0_dev[f],
-                               b->h[f]->es * (size_t)b->h[f]->N, cudaMemcpyDeviceToDevice, st));
+                               b->h[f]->es * (size_t)b->h[f]->ns, cudaMemcpyDeviceToDevice, st));
   BCK(b, cudaStreamSynchronize(st));
   return (jko_status)worst;
 }

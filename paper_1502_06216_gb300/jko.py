@@ -448,14 +448,17 @@ def _energy_struct(pb, keep):
     mk = None if pb.mask is None else np.ascontiguousarray(np.asarray(pb.mask, np.uint8).reshape(N))
     mf = _host_f64(getattr(pb, "m_field", None), N)
     tg = _host_f64(getattr(pb, "target", None), N)
-    keep += [w, al, mk, mf, tg]
+    w2 = _host_f64(getattr(pb, "w2", None), N)
+    keep += [w, al, mk, mf, tg, w2]
     return jko_energy(w.ctypes.data if w is not None else None, float(pb.kappa), None, float(pb.m),
                       al.ctypes.data if al is not None else None,
                       mk.ctypes.data if mk is not None else None,
                       mf.ctypes.data if mf is not None else None,
                       int(bool(getattr(pb, "binary", False))),
                       tg.ctypes.data if tg is not None else None,
-                      int(getattr(pb, "species", 1)))
+                      int(getattr(pb, "species", 1)),
+                      w2.ctypes.data if w2 is not None else None,
+                      float(getattr(pb, "pair_alpha", 0.0)))
 
 
 def jko_batch_create(problems, precision=Precision.FP32, tol=None, max_iter=None,

@@ -105,3 +105,37 @@ def test_batch_step_equals_one_step_of_the_flow():
     for f in range(len(pbs)):
         assert torch.equal(qs[f], finals[f]), f
     jko.jko_batch_destroy(b)
+
+
+def test_batch_of_every_kind_equals_single_handles():
+    """Flows of every energy and Gibbs kernel in one batch: the heat-kernel
+    crowd (FP32), the Wasserstein attraction (FP32 and TF32), two species
+    (FP64, 2N state images), the pairwise attraction (BF16x3 tensor cores) and
+    a plain crowd flow, 2 steps; each equals the same flow run alone, bit for
+    bit, with the same pair counts."""
+    torch = need_gpu()
+    from paper_1502_06216_gb300 import jko
+    flows = [(inputs.heat_crowd_problem(40, n_steps=2), "FP32"),
+             (inputs.attraction_problem(48, gamma=5e-3, tau=0.3, n_steps=2), "FP32"),
+             (inputs.attraction_problem(48, gamma=5e-3, tau=0.3, two_rooms=True, n_steps=2), "TF32"),
+             (inputs.two_species_problem(40, gamma=2e-3, tau=0.05, n_steps=2), "FP64"),
+             (inputs.pairwise_attraction_problem(48, gamma=8e-3, n_steps=2), "BF16X3"),
+             (inputs.config_problem(0, n=40, tol=1e-6, n_steps=2), "FP32")]
+    pbs = [pb for pb, _ in flows]
+    P = [jko.Precision[p] for _, p in flows]
+    b = jko.jko_batch_create(pbs, precision=P)
+    dts = [torch.float64 if p == jko.Precision.FP64 else torch.float32 for p in P]
+    p0s = [torch.tensor(pb.q0, dtype=dt, device="cuda") for pb, dt in zip(pbs, dts)]
+    finals, table = jko.jko_batch_flow(b, p0s, 2)
+    torch.cuda.synchronize()
+    for f, pb in enumerate(pbs):
+        h = jko.create_from_problem(pb, precision=P[f])
+        pf, _, infos = jko.jko_flow(h, p0s[f], 2)
+        same = torch.equal(pf, finals[f])
+        print(f, pb.name, P[f].name, "bitwise", same, "rel L1",
+              float((pf.double() - finals[f].double()).abs().sum() / pf.double().abs().sum()),
+              "iters", [i["iters"] for i in infos], [table[t][f]["iters"] for t in range(2)])
+        assert same, f
+        assert [i["iters"] for i in infos] == [table[t][f]["iters"] for t in range(2)]
+        jko.jko_destroy(h)
+    jko.jko_batch_destroy(b)

@@ -138,8 +138,6 @@ def test_rejections():
     for prec in ("BF16", "BF16X3"):
         with pytest.raises(jko.JKOError):
             jko.create_from_problem(pb, precision=jko.Precision[prec])
-    with pytest.raises(jko.JKOError):
-        jko.jko_batch_create([pb], precision=jko.Precision.FP32)
     bad = copy.deepcopy(pb)
     bad.heat_L = 1001
     with pytest.raises(jko.JKOError):

@@ -78,8 +78,6 @@ def test_rejections():
     torch = need_gpu()
     from paper_1502_06216_gb300 import jko
     pb = inputs.two_species_problem(32, n_steps=1)
-    with pytest.raises(jko.JKOError):
-        jko.jko_batch_create([pb], precision=jko.Precision.FP32)
     bad = copy.deepcopy(pb)
     bad.mask = np.zeros(pb.N, np.uint8)
     with pytest.raises(jko.JKOError):
