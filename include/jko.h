@@ -179,8 +179,9 @@ typedef struct jko_energy {
                                  scaling with 2 couplings.  JKO_FP32 / JKO_FP64 (CUDA cores),
                                  or the tensor-core passes of every coupling: JKO_TF32 (nx, ny
                                  multiples of 4), JKO_BF16 / JKO_BF16X3 (multiples of 8), with
-                                 absorb 0 or 2, loop 0 or 2, tile 0 or 64 and no finish; not
-                                 for the adjoint or jko_step_noalloc.  NULL = none */
+                                 absorb 0 or 2, loop 0 or 2, tile 0 or 64 and no finish; the
+                                 adjoint on JKO_FP64 handles with the congestion / potential
+                                 energy; not for jko_step_noalloc.  NULL = none */
   int species;                /* 2: two densities coupled through the congestion of their sum,
                                  f = iota_{[0,kappa]}(p_1 + p_2) + <p_1, w> + <p_2, w2>
                                  (Sec. 5.3, summation couplings): every state image (q, p,
@@ -335,9 +336,11 @@ jko_status jko_set_potential_device(jko_handle* h, const void* w_dev);
 /* jko_flow that also records, for every step t, its input q_t and the final
  * scaling a_t (the tape of jko_flow_backward).  p_final_dev receives p_n;
  * infos (may be NULL) n_steps reports.  Single-density JKO_FP32 / JKO_FP64
- * handles with the Gaussian (filter or FFT) or the heat kernel; the binary
- * congestion has no derivative.  JKO_ERR_UNSUPPORTED for tensor-core,
- * attraction and two-species handles and the binary congestion. */
+ * handles with the Gaussian (filter or FFT) or the heat kernel, and JKO_FP64
+ * handles of the Wasserstein attraction with the congestion / potential
+ * energy (its Jacobian a_m / s_m leaves the FP32 range).  JKO_ERR_UNSUPPORTED
+ * for tensor-core and two-species handles, other attraction handles and the
+ * binary congestion (no derivative). */
 jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void* p_final_dev,
                            jko_step_info* infos);
 

@@ -22,6 +22,8 @@ prox of ``oracle.prox`` written in torch:
     At the root G(y*) = 0, so the step leaves the value unchanged to rounding
     and its derivative with respect to l is 1/G'(y*): the implicit-function
     derivative of the root.
+``attraction_*``: the Wasserstein attraction with congestion (Sec. 5.2)
+through the reduced 2-coupling loop of ``oracle.attraction`` in torch.
 The non-convex binary congestion is not differentiable and is refused.  The
 Gibbs kernel is the separable Gaussian, or any symmetric operator given as a
 dense matrix (``xi_dense``: the heat kernel of ``oracle.heat`` at small sizes,
@@ -206,6 +208,56 @@ def energy_flow_loss_grad(p0, w, target, nx, ny, gamma, tau, energy: Energy, n_s
         p = energy_step_torch(p, wt, xi, tau / gamma, energy, tol=tol)
     tt = torch.tensor(np.asarray(target, np.float64))
     L = ((p - tt) ** 2).sum()
+    L.backward()
+    return (float(L.detach()), p0t.grad.numpy().copy(), wt.grad.numpy().copy(),
+            p.detach().numpy().copy())
+
+
+def attraction_step_torch(q, r, w, xi, tau, sigma, energy: Energy, tol=1e-13, max_iter=20000):
+    """One step of the Wasserstein attraction (Sec. 5.2) by the reduced
+    2-coupling loop of ``oracle.attraction.step``: s_m = xi b_m, p = the prox
+    of sigma h / (1 + tau) at the geometric mean s_1^{1/(1+tau)}
+    s_2^{tau/(1+tau)} (Eq. prox-psi-attraction), a_m = p / s_m, b_m = t_m / xi a_m
+    with (t_1, t_2) = (q, r); stop when sum_m ||b_m xi a_m - t_m||_1 <= tol."""
+    one = torch.ones_like(q)
+    b1, b2 = one, one
+    p = torch.zeros_like(q)
+    for _ in range(max_iter):
+        s1, s2 = xi(b1), xi(b2)
+        pos = (s1 > 0) & (s2 > 0)
+        l1 = torch.log(torch.where(pos, s1, one))
+        l2 = torch.log(torch.where(pos, s2, one))
+        g = torch.where(pos, torch.exp((l1 + tau * l2) / (1.0 + tau)), torch.zeros_like(q))
+        p = prox_torch(g, w, sigma / (1.0 + tau), energy)
+        a1 = torch.where(s1 > 0, p / torch.where(s1 > 0, s1, one), torch.zeros_like(q))
+        a2 = torch.where(s2 > 0, p / torch.where(s2 > 0, s2, one), torch.zeros_like(q))
+        Y1, Y2 = xi(a1), xi(a2)
+        res = torch.abs(b1 * Y1 - q).sum() + torch.abs(b2 * Y2 - r).sum()
+        if float(res.detach()) <= tol:
+            break
+        b1 = torch.where(q > 0, q / torch.where(q > 0, Y1, one), torch.zeros_like(q))
+        b2 = torch.where(r > 0, r / torch.where(r > 0, Y2, one), torch.zeros_like(q))
+    return p
+
+
+def attraction_flow_loss_grad(pb, p0, w, target, n_steps, tol=1e-13):
+    """L = ||p_T - target||^2 of the attraction flow of problem ``pb`` (target
+    density pb.target, energy h of the problem with its potential replaced by
+    ``w``) and (dL/dp0, dL/dw, p_T), FP64, each step renormalised."""
+    Kx = torch.tensor(kernel_1d(pb.nx, pb.gamma, pb.lx))
+    Ky = torch.tensor(kernel_1d(pb.ny, pb.gamma, pb.ly))
+
+    def xi(v):
+        return _xi(Kx, Ky, v, pb.ny, pb.nx)
+    energy = Energy.from_problem(pb)
+    r = torch.tensor(np.asarray(pb.target, np.float64))
+    p0t = torch.tensor(np.asarray(p0, np.float64), requires_grad=True)
+    wt = torch.tensor(np.asarray(w, np.float64), requires_grad=True)
+    p = p0t
+    for _ in range(n_steps):
+        p = attraction_step_torch(p, r, wt, xi, pb.tau, pb.tau / pb.gamma, energy, tol=tol)
+        p = p / p.sum()
+    L = ((p - torch.tensor(np.asarray(target, np.float64))) ** 2).sum()
     L.backward()
     return (float(L.detach()), p0t.grad.numpy().copy(), wt.grad.numpy().copy(),
             p.detach().numpy().copy())

@@ -268,8 +268,164 @@ jko_status backward_t(jko_handle* h, const T* grad_final, T* grad_p0, T* grad_w,
   return JKO_OK;
 }
 
+// ---- the Wasserstein attraction (Sec. 5.2), congestion/potential energy ----
+// The step's fixed point over both couplings: Y_m = xi a_m, b_m = t_m / Y_m
+// (t_1 = q, t_2 = r), s_m = xi b_m, p = min(E g, kappa) with the geometric mean
+// g = s_1^{th1} s_2^{th2} (th1 = 1/(1+tau), th2 = tau/(1+tau), E = e^{-sigma' w},
+// sigma' = sigma/(1+tau): Eq. prox-psi-attraction), a_m = p / s_m.  Per cell,
+// with p unclamped: da_1/ds_1 = (th1 - 1) a_1/s_1, da_1/ds_2 = th2 a_1/s_2,
+// da_2/ds_1 = th1 a_2/s_1, da_2/ds_2 = (th2 - 1) a_2/s_2, da_m/dw = -sigma' a_m;
+// clamped (E g > kappa): a_m = kappa/s_m, da_m/ds_m = -a_m/s_m, no w term.
+// The adjoint solve runs over both channels: u = J^T lambda cell by cell, then
+// lambda_m = abar_m - xi(D_m xi u_m); p = a_1 s_1 gives the direct terms of
+// channel 1 as in the single-coupling step, and q only enters through b_1.
+template <typename T>
+__device__ __forceinline__ bool att_jacobian(const jko::ProxArgs<T>& P, long long i, T s1, T s2,
+                                             T th1, T th2, T (&J)[4], T& a1, T& a2) {
+  J[0] = J[1] = J[2] = J[3] = T(0);
+  a1 = a2 = T(0);
+  if ((P.mask != nullptr && P.mask[i]) || !(s1 > T(0) && s2 > T(0))) return false;
+  const T g = jko::dev_exp<T>(th1 * jko::dev_log<T>(s1) + th2 * jko::dev_log<T>(s2));
+  const T e = P.E[i];
+  if (P.has_kappa) {
+    const T kap = P.kappa ? P.kappa[i] : P.kappa_s;
+    if (e * g > kap) {
+      a1 = kap / s1;
+      a2 = kap / s2;
+      J[0] = -a1 / s1;
+      J[3] = -a2 / s2;
+      return false;
+    }
+  }
+  const T pm = e * g;
+  a1 = pm / s1;
+  a2 = pm / s2;
+  J[0] = (th1 - T(1)) * a1 / s1;   // da_1/ds_1
+  J[1] = th2 * a1 / s2;            // da_1/ds_2
+  J[2] = th1 * a2 / s1;            // da_2/ds_1
+  J[3] = (th2 - T(1)) * a2 / s2;   // da_2/ds_2
+  return true;
+}
+
+// u = J^T lambda
+template <typename T>
+__global__ void k_att_u(jko::ProxArgs<T> P, const T* s1, const T* s2, const T* l1, const T* l2,
+                        T* u1, T* u2, T th1, T th2, long long n) {
+  GS(i, n) {
+    T J[4], a1, a2;
+    att_jacobian<T>(P, i, s1[i], s2[i], th1, th2, J, a1, a2);
+    u1[i] = J[0] * l1[i] + J[2] * l2[i];
+    u2[i] = J[1] * l1[i] + J[3] * l2[i];
+  }
+}
+
+// g = qbar0 + v invY ;  wbar += -sigma' (a_1 lambda_1 + a_2 lambda_2) where unclamped
+template <typename T>
+__global__ void k_att_final(jko::ProxArgs<T> P, const T* s1, const T* s2, const T* l1,
+                            const T* l2, const T* qbar0, const T* v, const T* invY, T* g, T* wbar,
+                            T th1, T th2, T sigma_f, long long n) {
+  GS(i, n) {
+    T J[4], a1, a2;
+    const bool free_ = att_jacobian<T>(P, i, s1[i], s2[i], th1, th2, J, a1, a2);
+    g[i] = qbar0[i] + v[i] * invY[i];
+    if (free_) wbar[i] += -sigma_f * (a1 * l1[i] + a2 * l2[i]);
+  }
+}
+
+template <typename T>
+jko_status backward_attraction(jko_handle* h, const T* grad_final, T* grad_p0, T* grad_w,
+                               int* adj_iters) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  if (!h->adj2) ACK(cudaMalloc(&h->adj2, sizeof(T) * N * 18));
+  if (!h->adj_red) ACK(cudaMalloc((void**)&h->adj_red, sizeof(double) * 4));
+  T* W = (T*)h->adj2;
+  T *Y1 = W, *Y2 = W + N, *b1 = W + 2 * N, *b2 = W + 3 * N, *s1 = W + 4 * N, *s2 = W + 5 * N,
+    *iY1 = W + 6 * N, *iY2 = W + 7 * N, *g = W + 8 * N, *gt = W + 9 * N, *u1 = W + 10 * N,
+    *u2 = W + 11 * N, *v1 = W + 12 * N, *v2 = W + 13 * N, *l1 = W + 14 * N, *l2 = W + 15 * N,
+    *ab1 = W + 16 * N, *ab2 = W + 17 * N;
+  const T th1 = T(1.0 / (1.0 + h->prm.tau)), th2 = T(h->prm.tau / (1.0 + h->prm.tau));
+  const T sigma_f = T(h->prm.tau / h->prm.gamma / (1.0 + h->prm.tau));
+  jko::ProxArgs<T> P = jko::prox_args<T>(h);
+  ACK(cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  ACK(cudaMemcpyAsync(g, grad_final, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  T* wbar = grad_w ? grad_w : v2;   // v2 is rewritten before it is read again
+  if (grad_w) ACK(cudaMemsetAsync(grad_w, 0, sizeof(T) * N, st));
+  const int budget = std::max(16, 10 * h->prm.max_iter);
+  const double tol = std::max(h->prm.tol, h->fp64 ? 1e-15 : 1e-7);
+  const int G = grid_for(N);
+  const T* r = (const T*)h->tgt;
+  for (int t = h->tape_steps - 1; t >= 0; --t) {
+    const T* q = (const T*)h->tape + (size_t)(3 * t) * N;
+    const T* a1 = q + N;
+    const T* a2 = q + 2 * N;
+    const double m = h->tape_mass[t];
+    ACK(xi_apply<T>(h, a1, Y1, st));
+    ACK(xi_apply<T>(h, a2, Y2, st));
+    k_b_invY<T><<<G, NT, 0, st>>>(q, Y1, b1, iY1, N);
+    k_b_invY<T><<<G, NT, 0, st>>>(r, Y2, b2, iY2, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, b1, s1, st));
+    ACK(xi_apply<T>(h, b2, s2, st));
+    // the renormalisation's adjoint and the direct terms of p = a_1 s_1
+    ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+    k_dot3<T><<<G, NT, 0, st>>>(g, a1, s1, h->adj_red, N);
+    k_renorm<T><<<G, NT, 0, st>>>(g, a1, h->adj_red, m, h->prm.renormalize, gt, u1, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, v1, st));                 // v1 = xi(a_1 gt)
+    k_mul<T><<<G, NT, 0, st>>>(b1, iY1, b1, N);      // b1 <- D_1
+    k_mul<T><<<G, NT, 0, st>>>(b2, iY2, b2, N);      // b2 <- D_2
+    k_mul<T><<<G, NT, 0, st>>>(b1, v1, u1, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, ab1, st));                // xi(D_1 v1)
+    k_abar<T><<<G, NT, 0, st>>>(s1, gt, ab1, v1, iY1, ab1, gt, N);   // abar_1; qbar0 in gt
+    ACK(cudaGetLastError());
+    ACK(cudaMemsetAsync(ab2, 0, sizeof(T) * N, st));
+    ACK(cudaMemcpyAsync(l1, ab1, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    ACK(cudaMemsetAsync(l2, 0, sizeof(T) * N, st));
+    int k = 0;
+    bool conv = false;
+    double host_red[4];
+    for (; k < budget && !conv; ++k) {
+      if ((k & 7) == 0) ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+      k_att_u<T><<<G, NT, 0, st>>>(P, s1, s2, l1, l2, u1, u2, th1, th2, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u1, v1, st));
+      ACK(xi_apply<T>(h, u2, v2, st));
+      k_mul<T><<<G, NT, 0, st>>>(b1, v1, u1, N);
+      k_mul<T><<<G, NT, 0, st>>>(b2, v2, u2, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u1, v1, st));
+      ACK(xi_apply<T>(h, u2, v2, st));
+      k_lambda<T><<<G, NT, 0, st>>>(ab1, v1, l1, h->adj_red, h->adj_red + 1, N);
+      k_lambda<T><<<G, NT, 0, st>>>(ab2, v2, l2, h->adj_red, h->adj_red + 1, N);
+      ACK(cudaGetLastError());
+      if ((k & 7) == 7) {
+        ACK(cudaMemcpyAsync(host_red, h->adj_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+        ACK(cudaStreamSynchronize(st));
+        conv = host_red[0] <= tol * host_red[1];
+        if (!std::isfinite(host_red[0]))
+          return jko::handle_error(h, JKO_ERR_NUMERIC, "adjoint iterates are not finite");
+      }
+    }
+    if (adj_iters) adj_iters[t] = k;
+    // gradients of this step: q enters through b_1 only (r is fixed)
+    k_att_u<T><<<G, NT, 0, st>>>(P, s1, s2, l1, l2, u1, u2, th1, th2, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, v1, st));
+    if (!grad_w) ACK(cudaMemsetAsync(v2, 0, sizeof(T) * N, st));
+    k_att_final<T><<<G, NT, 0, st>>>(P, s1, s2, l1, l2, gt, v1, iY1, g, wbar, th1, th2, sigma_f,
+                                     N);
+    ACK(cudaGetLastError());
+  }
+  if (grad_p0) ACK(cudaMemcpyAsync(grad_p0, g, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+  ACK(cudaStreamSynchronize(st));
+  return JKO_OK;
+}
+
 template <typename T>
 jko_status backward_dispatch(jko_handle* h, const void* gf, void* gp, void* gw, int* it) {
+  if (h->attract) return backward_attraction<T>(h, (const T*)gf, (T*)gp, (T*)gw, it);
   switch (h->ek) {
     case jko::EK_CROWD:
       return backward_t<T, jko::EK_CROWD>(h, (const T*)gf, (T*)gp, (T*)gw, it);
@@ -289,12 +445,17 @@ __global__ void k_set_potential(const W* w, T* E, T* sw, double sigma, long long
   }
 }
 
+// sigma of the energy fields: tau / gamma, over (1 + tau) for the attraction's
+// prox of h (Eq. prox-psi-attraction)
+double field_sigma(const jko_handle* h) {
+  return h->prm.tau / h->prm.gamma / (h->attract ? 1.0 + h->prm.tau : 1.0);
+}
+
 jko_status check_set_potential(jko_handle* h, const void* w) {
   if (!h || !w) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
-  if (h->attract || h->species == 2)
+  if (h->species == 2)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "the potential of an attraction or two-species handle is fixed at "
-                             "creation");
+                             "the potentials of a two-species handle are fixed at creation");
   if (h->tc && jko::tc_absorbed(h->tc))
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the potential is absorbed into the Gibbs factors of this handle");
@@ -326,7 +487,7 @@ jko_status jko_set_potential(jko_handle* h, const double* w_host) {
   double* wd = nullptr;
   ACK(cudaMalloc((void**)&wd, sizeof(double) * N));
   cudaError_t e = cudaMemcpyAsync(wd, w_host, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream);
-  const double sigma = h->prm.tau / h->prm.gamma;
+  const double sigma = field_sigma(h);
   if (e == cudaSuccess) {
     if (h->fp64)
       k_set_potential<double, double><<<grid_for(N), NT, 0, h->stream>>>(wd, (double*)h->E, (double*)h->sw, sigma, N);
@@ -343,7 +504,7 @@ jko_status jko_set_potential(jko_handle* h, const double* w_host) {
 jko_status jko_set_potential_device(jko_handle* h, const void* w_dev) {
   if (jko_status st = check_set_potential(h, w_dev)) return st;
   const long long N = h->N;
-  const double sigma = h->prm.tau / h->prm.gamma;
+  const double sigma = field_sigma(h);
   if (h->fp64)
     k_set_potential<double, double><<<grid_for(N), NT, 0, h->stream>>>(
         (const double*)w_dev, (double*)h->E, (double*)h->sw, sigma, N);
@@ -361,15 +522,27 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   if (h->binary)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the binary congestion prox is discontinuous: no adjoint");
-  if (h->attract)
-    return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the Wasserstein attraction");
+  if (h->attract && h->ek != jko::EK_CROWD)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the attraction's adjoint covers the congestion / potential energy");
+  // Its Jacobian a_m / s_m grows like s_m^{-1 - tau/(1+tau)} where the blur
+  // s_m = xi b_m of one coupling is tiny near the other's support, and the
+  // band-limited FP32 factors that would cancel it are exact zeros there: the
+  // FP32 adjoint overflows (measured: gradients off by 1e37), the FP64 one
+  // matches the oracle.
+  if (h->attract && !h->fp64)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
+                             "the attraction's adjoint needs a JKO_FP64 handle (its Jacobian "
+                             "a_m / s_m leaves the FP32 range)");
   if (h->species == 2) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for two species");
   const size_t es = h->es, N = (size_t)h->N;
+  // per step: q_t and the final scaling a_t (and a_2 of the attraction's second coupling)
+  const size_t per = h->attract ? 3 : 2;
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);
     h->tape = nullptr;
     h->tape_cap = 0;
-    ACK(cudaMalloc(&h->tape, es * N * 2 * n_steps));
+    ACK(cudaMalloc(&h->tape, es * N * per * n_steps));
     h->tape_cap = n_steps;
   }
   h->tape_steps = 0;
@@ -378,11 +551,11 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   int worst = JKO_OK;
   const void* q = p0_dev;
   for (int t = 0; t < n_steps; ++t) {
-    char* slot = (char*)h->tape + es * N * 2 * t;
+    char* slot = (char*)h->tape + es * N * per * t;
     if (q != (const void*)slot)  // from step 1 on the previous step wrote its output here
       ACK(cudaMemcpyAsync(slot, q, es * N, cudaMemcpyDeviceToDevice, st));
     jko_step_info info{};
-    void* dst = (t + 1 < n_steps) ? (void*)((char*)h->tape + es * N * 2 * (t + 1)) : p_final_dev;
+    void* dst = (t + 1 < n_steps) ? (void*)((char*)h->tape + es * N * per * (t + 1)) : p_final_dev;
     if (!dst) {
       if (!h->stage_out) ACK(cudaMalloc(&h->stage_out, es * N));
       dst = h->stage_out;
@@ -394,6 +567,8 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
     if (s == JKO_ERR_NUMERIC) worst = JKO_ERR_NUMERIC;
     else if (s == JKO_NOT_CONVERGED && worst == JKO_OK) worst = JKO_NOT_CONVERGED;
     ACK(cudaMemcpyAsync(slot + es * N, h->a, es * N, cudaMemcpyDeviceToDevice, st));
+    if (h->attract)
+      ACK(cudaMemcpyAsync(slot + 2 * es * N, h->a2, es * N, cudaMemcpyDeviceToDevice, st));
     h->tape_mass[t] = info.mass;
     h->tape_steps = t + 1;
     q = dst;

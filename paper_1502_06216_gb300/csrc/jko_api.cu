@@ -673,7 +673,7 @@ void free_handle(jko_handle* h) {
                   h->taps_y, h->E, h->sw, h->c, h->kap, h->m1f, h->mask, h->ctrl, h->part,
                   h->a2, h->b2, h->tgt, h->s1, h->s2, h->E2,
                   h->fft_khat_x, h->fft_tw_x, h->fft_khat_y, h->fft_tw_y,
-                  h->tape, h->adj, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
+                  h->tape, h->adj, h->adj2, h->adj_red, h->hb.d[0], h->hb.d[1], h->hb.d[2],
                   h->hb.d[3], h->hb.coef, h->a3, h->b3, h->s3, h->t2, h->t3, h->mpair};
   for (void* b : bufs) if (b) cudaFree(b);
   if (h->ctrl_init) cudaFreeHost(h->ctrl_init);

@@ -102,7 +102,8 @@ struct jko_handle {
   int tape_cap = 0;             // steps the tape can hold
   void* tape = nullptr;         // per step: q_t and the final a_t (2 N elements)
   std::vector<double> tape_mass;  // sum of the unnormalised output per step
-  void* adj = nullptr;          // adjoint work images (8 N elements)
+  void* adj = nullptr;          // adjoint work images (10 N elements)
+  void* adj2 = nullptr;         // the attraction's adjoint work images (18 N elements)
   double* adj_red = nullptr;    // device reduction slots
 
   std::string err;

@@ -197,3 +197,30 @@ def test_adjoint_fft_gaussian_matches_oracle(prec, tol, bar):
     print("fft", prec, "loss", L, Lo, "rel L1 grad_w", ew, "grad_p0 (support)", ep)
     assert abs(L - Lo) <= 10 * bar * abs(Lo)
     assert ew <= bar and ep <= bar
+
+
+def test_adjoint_attraction_matches_oracle():
+    """The adjoint of the Wasserstein attraction with congestion (Sec. 5.2,
+    two couplings: the adjoint solve runs over both channels through the
+    Jacobian of the joint prox at the geometric mean) against the oracle's FP64
+    reverse-mode gradient through its reduced 2-coupling loop: 32^2, 2 steps,
+    a random potential added to h; FP64 handles (an FP32 handle refuses the
+    recording: the Jacobian a_m / s_m leaves the FP32 range)."""
+    torch = need_gpu()
+    from oracle import adjoint
+    from paper_1502_06216_gb300 import jko
+    prec, tol, bar = "FP64", 1e-13, 1e-6
+    pb = inputs.attraction_problem(32, gamma=5e-3, tau=0.3, n_steps=2)
+    pb.w = 0.05 * np.random.default_rng(53).standard_normal(pb.N)
+    target = np.full(pb.N, 1.0 / pb.N)
+    Lo, gpo, gwo, _ = adjoint.attraction_flow_loss_grad(pb, pb.q0, pb.w, target, 2)
+    L, gp, gw, _ = gpu_grad(pb, pb.w, target, 2, prec, tol)
+    ew, ep = _grad_errors(gp, gw, gpo, gwo, pb.q0 > 0)
+    print("attraction", prec, "loss", L, Lo, "rel L1 grad_w", ew, "grad_p0 (support)", ep)
+    assert abs(L - Lo) <= 10 * bar * abs(Lo)
+    assert ew <= bar and ep <= bar
+    h32 = jko.create_from_problem(pb, precision=jko.Precision.FP32)
+    with pytest.raises(jko.JKOError) as e:
+        jko.jko_flow_record(h32, torch.tensor(pb.q0, dtype=torch.float32, device="cuda"), 1)
+    assert e.value.status == jko.Status.UNSUPPORTED
+    jko.jko_destroy(h32)

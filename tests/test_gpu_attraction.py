@@ -95,7 +95,10 @@ def test_rejections():
     torch = need_gpu()
     from paper_1502_06216_gb300 import jko
     pb = inputs.attraction_problem(32, n_steps=1)
-    h = jko.create_from_problem(pb, precision=jko.Precision.FP64)
+    # the attraction's adjoint covers the congestion / potential energy only
+    ent = copy.deepcopy(pb)
+    ent.m = 1.0
+    h = jko.create_from_problem(ent, precision=jko.Precision.FP64)
     with pytest.raises(jko.JKOError):
         jko.jko_flow_record(h, torch.tensor(pb.q0, dtype=torch.float64, device="cuda"), 1)
     jko.jko_destroy(h)

@@ -184,3 +184,44 @@ def test_heat_gradient_matches_central_differences():
             g_dir = float(gw @ d)
         fd = (f(eps) - f(-eps)) / (2 * eps)
         assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
+
+
+def _attraction_case():
+    pb = inputs.attraction_problem(16, gamma=5e-3, tau=0.3, n_steps=2)
+    rng = np.random.default_rng(53)
+    pb.w = 0.05 * rng.standard_normal(pb.N)
+    return pb
+
+
+def _attraction_numpy_loss(pb, p0, w, target):
+    import copy
+    from oracle import attraction as oatt
+    q = copy.deepcopy(pb)
+    q.q0, q.w = p0, w
+    traj, _ = oatt.problem_flow(q, n_steps=2, tol=1e-13, max_iter=20000)
+    return float(((traj[-1] - target) ** 2).sum()), traj[-1]
+
+
+def test_attraction_gradient_matches_central_differences():
+    """The oracle's gradient through the attraction flow (Sec. 5.2): the torch
+    loop = the NumPy attraction flow (1e-12), and dL/dw, dL/dp0 = central
+    differences of the NumPy flow (relative 1e-5)."""
+    pb = _attraction_case()
+    target = np.full(pb.N, 1.0 / pb.N)
+    L, gp, gw, pT = adjoint.attraction_flow_loss_grad(pb, pb.q0, pb.w, target, 2)
+    Ln, pn = _attraction_numpy_loss(pb, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() <= 1e-12
+    assert abs(L - Ln) <= 1e-12 * abs(Ln)
+    rng = np.random.default_rng(59)
+    eps = 1e-5
+    for which in ("w", "p0"):
+        d = rng.standard_normal(pb.N)
+        if which == "p0":
+            d = pb.q0 * (d - d @ pb.q0)
+            f = lambda e: _attraction_numpy_loss(pb, pb.q0 + e * d, pb.w, target)[0]  # noqa: E731
+            g_dir = float(gp @ d)
+        else:
+            f = lambda e: _attraction_numpy_loss(pb, pb.q0, pb.w + e * d, target)[0]  # noqa: E731
+            g_dir = float(gw @ d)
+        fd = (f(eps) - f(-eps)) / (2 * eps)
+        assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
