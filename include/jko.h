@@ -188,8 +188,10 @@ typedef struct jko_energy {
                                  trajectories) holds [p_1, p_2], 2 N entries, of total mass 1;
                                  scalar kappa only (no kappa_field, mask, entropy, binary or
                                  target); the precisions of `target`; in a batch the flow's
-                                 images hold 2 N entries too; not for the adjoint or
-                                 jko_step_noalloc.  0 or 1: one density */
+                                 images hold 2 N entries too; the adjoint on JKO_FP32 /
+                                 JKO_FP64 handles (dL/dw: the first species' potential, which
+                                 jko_set_potential replaces); not for jko_step_noalloc.  0 or
+                                 1: one density */
   const double* w2;           /* potential of the second species (N entries); NULL = 0 */
   double pair_alpha;          /* > 0 with species = 2: the Wasserstein pairwise attraction
                                  f = pair_alpha W_gamma(p_1, p_2) + h_1(p_1) + h_2(p_2),
@@ -336,11 +338,12 @@ jko_status jko_set_potential_device(jko_handle* h, const void* w_dev);
 /* jko_flow that also records, for every step t, its input q_t and the final
  * scaling a_t (the tape of jko_flow_backward).  p_final_dev receives p_n;
  * infos (may be NULL) n_steps reports.  Single-density JKO_FP32 / JKO_FP64
- * handles with the Gaussian (filter or FFT) or the heat kernel, and JKO_FP64
+ * handles with the Gaussian (filter or FFT) or the heat kernel, JKO_FP32 /
+ * JKO_FP64 two-species handles (tape and p_final of 2 N entries), and JKO_FP64
  * handles of the Wasserstein attraction with the congestion / potential
  * energy (its Jacobian a_m / s_m leaves the FP32 range).  JKO_ERR_UNSUPPORTED
- * for tensor-core and two-species handles, other attraction handles and the
- * binary congestion (no derivative). */
+ * for tensor-core and pairwise-attraction handles, other attraction handles
+ * and the binary congestion (no derivative). */
 jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void* p_final_dev,
                            jko_step_info* infos);
 

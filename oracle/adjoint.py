@@ -23,7 +23,9 @@ prox of ``oracle.prox`` written in torch:
     and its derivative with respect to l is 1/G'(y*): the implicit-function
     derivative of the root.
 ``attraction_*``: the Wasserstein attraction with congestion (Sec. 5.2)
-through the reduced 2-coupling loop of ``oracle.attraction`` in torch.
+through the reduced 2-coupling loop of ``oracle.attraction`` in torch;
+``species_*``: two densities coupled through the congestion of their sum
+(Sec. 5.3) through the loop of ``oracle.summation``.
 The non-convex binary congestion is not differentiable and is refused.  The
 Gibbs kernel is the separable Gaussian, or any symmetric operator given as a
 dense matrix (``xi_dense``: the heat kernel of ``oracle.heat`` at small sizes,
@@ -256,6 +258,53 @@ def attraction_flow_loss_grad(pb, p0, w, target, n_steps, tol=1e-13):
     p = p0t
     for _ in range(n_steps):
         p = attraction_step_torch(p, r, wt, xi, pb.tau, pb.tau / pb.gamma, energy, tol=tol)
+        p = p / p.sum()
+    L = ((p - torch.tensor(np.asarray(target, np.float64))) ** 2).sum()
+    L.backward()
+    return (float(L.detach()), p0t.grad.numpy().copy(), wt.grad.numpy().copy(),
+            p.detach().numpy().copy())
+
+
+def species_flow_loss_grad(pb, p0, w, target, n_steps, tol=1e-13, max_iter=20000):
+    """Two densities coupled through the congestion of their sum (Sec. 5.3,
+    ``oracle.summation``'s reduced 2-coupling loop) in torch: s_m = xi b_m,
+    t = s_1 e^{-sigma w} + s_2 e^{-sigma w2}, p_m = s_m e^{-sigma w_m} min(1,
+    kappa / t), a_m = p_m / s_m, b_m = q_m / xi a_m; stop when sum_m ||b_m xi a_m
+    - q_m||_1 <= tol.  State images [p_1, p_2] (2N), renormalised to total
+    mass 1 each step.  Returns L = ||p_T - target||^2 and (dL/dp0 (2N),
+    dL/dw (the first species' potential), p_T), FP64."""
+    N = pb.nx * pb.ny
+    Kx = torch.tensor(kernel_1d(pb.nx, pb.gamma, pb.lx))
+    Ky = torch.tensor(kernel_1d(pb.ny, pb.gamma, pb.ly))
+
+    def xi(v):
+        return _xi(Kx, Ky, v, pb.ny, pb.nx)
+    sigma, kappa = pb.tau / pb.gamma, float(pb.kappa)
+    w2 = torch.tensor(np.zeros(N) if pb.w2 is None else np.asarray(pb.w2, np.float64))
+    p0t = torch.tensor(np.asarray(p0, np.float64), requires_grad=True)
+    wt = torch.tensor(np.asarray(w, np.float64), requires_grad=True)
+    E1, E2 = torch.exp(-sigma * wt), torch.exp(-sigma * w2)
+    one = torch.ones(N, dtype=torch.float64)
+    zero = torch.zeros(N, dtype=torch.float64)
+    p = p0t
+    for _ in range(n_steps):
+        q1, q2 = p[:N], p[N:]
+        b1, b2 = one, one
+        for _ in range(max_iter):
+            s1, s2 = xi(b1), xi(b2)
+            t1, t2 = s1 * E1, s2 * E2
+            t = t1 + t2
+            f = torch.where(t > kappa, kappa / torch.where(t > kappa, t, one), one)
+            p1, p2 = t1 * f, t2 * f
+            a1 = torch.where(s1 > 0, p1 / torch.where(s1 > 0, s1, one), zero)
+            a2 = torch.where(s2 > 0, p2 / torch.where(s2 > 0, s2, one), zero)
+            Y1, Y2 = xi(a1), xi(a2)
+            res = torch.abs(b1 * Y1 - q1).sum() + torch.abs(b2 * Y2 - q2).sum()
+            if float(res.detach()) <= tol:
+                break
+            b1 = torch.where(q1 > 0, q1 / torch.where(q1 > 0, Y1, one), zero)
+            b2 = torch.where(q2 > 0, q2 / torch.where(q2 > 0, Y2, one), zero)
+        p = torch.cat([p1, p2])
         p = p / p.sum()
     L = ((p - torch.tensor(np.asarray(target, np.float64))) ** 2).sum()
     L.backward()

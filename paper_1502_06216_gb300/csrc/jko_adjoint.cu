@@ -423,9 +423,160 @@ jko_status backward_attraction(jko_handle* h, const T* grad_final, T* grad_p0, T
   return JKO_OK;
 }
 
+// ---- two species coupled through the congestion of their sum (Sec. 5.3) ----
+// Fixed point over both couplings: b_m = q_m / xi a_m, s_m = xi b_m, the joint
+// prox t = s_1 E_1 + s_2 E_2 (E_m = e^{-sigma w_m}), f = min(1, kappa / t),
+// p_m = s_m E_m f, a_m = E_m f.  Unclamped (t <= kappa) a_m = E_m does not
+// depend on s; clamped, da_m/ds_n = -a_m E_n / t, so (J^T lambda)_n =
+// -E_n (a_1 lambda_1 + a_2 lambda_2) / t.  The potential w = w_1 of the first
+// species: da_1/dw = -sigma a_1 (1 - s_1 E_1 / t 1[clamped]), da_2/dw =
+// sigma a_2 s_1 E_1 / t 1[clamped].  Both species carry direct terms (p_m =
+// a_m s_m) and their own q_m.
+template <typename T>
+__device__ __forceinline__ bool sp_clamped(const T* E1, const T* E2, long long i, T s1, T s2,
+                                          T kappa, int has_kappa, T& t, T& a1, T& a2) {
+  const T e1 = E1[i], e2 = E2 ? E2[i] : T(1);
+  t = s1 * e1 + s2 * e2;
+  const bool c = has_kappa && t > kappa;
+  const T f = c ? kappa / t : T(1);
+  a1 = e1 * f;
+  a2 = e2 * f;
+  return c;
+}
+
+template <typename T>
+__global__ void k_sp_u(const T* E1, const T* E2, const T* s1, const T* s2, const T* l1,
+                       const T* l2, T* u1, T* u2, T kappa, int has_kappa, long long n) {
+  GS(i, n) {
+    T t, a1, a2;
+    if (sp_clamped<T>(E1, E2, i, s1[i], s2[i], kappa, has_kappa, t, a1, a2)) {
+      const T c = -(a1 * l1[i] + a2 * l2[i]) / t;
+      u1[i] = E1[i] * c;
+      u2[i] = (E2 ? E2[i] : T(1)) * c;
+    } else {
+      u1[i] = T(0);
+      u2[i] = T(0);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_sp_final(const T* E1, const T* E2, const T* s1, const T* s2, const T* l1,
+                           const T* l2, const T* qb1, const T* qb2, const T* v1, const T* v2,
+                           const T* iY1, const T* iY2, T* g1, T* g2, T* wbar, T sigma, T kappa,
+                           int has_kappa, long long n) {
+  GS(i, n) {
+    T t, a1, a2;
+    const bool c = sp_clamped<T>(E1, E2, i, s1[i], s2[i], kappa, has_kappa, t, a1, a2);
+    g1[i] = qb1[i] + v1[i] * iY1[i];
+    g2[i] = qb2[i] + v2[i] * iY2[i];
+    const T share = c ? s1[i] * E1[i] / t : T(0);   // the first species' part of t
+    wbar[i] += -sigma * a1 * (T(1) - share) * l1[i] + sigma * a2 * share * l2[i];
+  }
+}
+
+template <typename T>
+jko_status backward_species(jko_handle* h, const T* grad_final, T* grad_p0, T* grad_w,
+                            int* adj_iters) {
+  cudaStream_t st = h->stream;
+  const long long N = h->N;
+  if (!h->adj2) ACK(cudaMalloc(&h->adj2, sizeof(T) * N * 20));
+  if (!h->adj_red) ACK(cudaMalloc((void**)&h->adj_red, sizeof(double) * 4));
+  T* W = (T*)h->adj2;
+  T *Y1 = W, *Y2 = W + N, *b1 = W + 2 * N, *b2 = W + 3 * N, *s1 = W + 4 * N, *s2 = W + 5 * N,
+    *iY1 = W + 6 * N, *iY2 = W + 7 * N, *g = W + 8 * N /* 2N */, *gt = W + 10 * N /* 2N */,
+    *u1 = W + 12 * N, *u2 = W + 13 * N, *v1 = W + 14 * N, *v2 = W + 15 * N, *l1 = W + 16 * N,
+    *l2 = W + 17 * N, *ab1 = W + 18 * N, *ab2 = W + 19 * N;
+  T *g1 = g, *g2 = g + N, *gt1 = gt, *gt2 = gt + N;
+  const T sigma = T(h->prm.tau / h->prm.gamma), kappa = T(h->kappa_s);
+  const T* E1 = (const T*)h->E;
+  const T* E2 = (const T*)h->E2;
+  ACK(cudaMemcpyAsync(h->ctrl, h->ctrl_init, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  ACK(cudaMemcpyAsync(g, grad_final, sizeof(T) * 2 * N, cudaMemcpyDeviceToDevice, st));
+  T* wbar = grad_w;
+  if (grad_w) ACK(cudaMemsetAsync(grad_w, 0, sizeof(T) * N, st));
+  const int budget = std::max(16, 10 * h->prm.max_iter);
+  const double tol = std::max(h->prm.tol, h->fp64 ? 1e-15 : 1e-7);
+  const int G = grid_for(N);
+  for (int t = h->tape_steps - 1; t >= 0; --t) {
+    const T* q1 = (const T*)h->tape + (size_t)(4 * t) * N;
+    const T* q2 = q1 + N;
+    const T* a1 = q1 + 2 * N;
+    const T* a2 = q1 + 3 * N;
+    const double m = h->tape_mass[t];
+    ACK(xi_apply<T>(h, a1, Y1, st));
+    ACK(xi_apply<T>(h, a2, Y2, st));
+    k_b_invY<T><<<G, NT, 0, st>>>(q1, Y1, b1, iY1, N);
+    k_b_invY<T><<<G, NT, 0, st>>>(q2, Y2, b2, iY2, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, b1, s1, st));
+    ACK(xi_apply<T>(h, b2, s2, st));
+    // the renormalisation's adjoint over both species, then the direct terms of p_m = a_m s_m
+    ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+    k_dot3<T><<<G, NT, 0, st>>>(g1, a1, s1, h->adj_red, N);
+    k_dot3<T><<<G, NT, 0, st>>>(g2, a2, s2, h->adj_red, N);
+    k_renorm<T><<<G, NT, 0, st>>>(g1, a1, h->adj_red, m, h->prm.renormalize, gt1, u1, N);
+    k_renorm<T><<<G, NT, 0, st>>>(g2, a2, h->adj_red, m, h->prm.renormalize, gt2, u2, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, v1, st));                 // v_m = xi(a_m gt_m)
+    ACK(xi_apply<T>(h, u2, v2, st));
+    k_mul<T><<<G, NT, 0, st>>>(b1, iY1, b1, N);      // b_m <- D_m
+    k_mul<T><<<G, NT, 0, st>>>(b2, iY2, b2, N);
+    k_mul<T><<<G, NT, 0, st>>>(b1, v1, u1, N);
+    k_mul<T><<<G, NT, 0, st>>>(b2, v2, u2, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, ab1, st));
+    ACK(xi_apply<T>(h, u2, ab2, st));
+    k_abar<T><<<G, NT, 0, st>>>(s1, gt1, ab1, v1, iY1, ab1, gt1, N);   // abar_1; qbar0_1 in gt1
+    k_abar<T><<<G, NT, 0, st>>>(s2, gt2, ab2, v2, iY2, ab2, gt2, N);
+    ACK(cudaGetLastError());
+    ACK(cudaMemcpyAsync(l1, ab1, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    ACK(cudaMemcpyAsync(l2, ab2, sizeof(T) * N, cudaMemcpyDeviceToDevice, st));
+    int k = 0;
+    bool conv = false;
+    double host_red[4];
+    for (; k < budget && !conv; ++k) {
+      if ((k & 7) == 0) ACK(cudaMemsetAsync(h->adj_red, 0, sizeof(double) * 4, st));
+      k_sp_u<T><<<G, NT, 0, st>>>(E1, E2, s1, s2, l1, l2, u1, u2, kappa, h->has_kappa, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u1, v1, st));
+      ACK(xi_apply<T>(h, u2, v2, st));
+      k_mul<T><<<G, NT, 0, st>>>(b1, v1, u1, N);
+      k_mul<T><<<G, NT, 0, st>>>(b2, v2, u2, N);
+      ACK(cudaGetLastError());
+      ACK(xi_apply<T>(h, u1, v1, st));
+      ACK(xi_apply<T>(h, u2, v2, st));
+      k_lambda<T><<<G, NT, 0, st>>>(ab1, v1, l1, h->adj_red, h->adj_red + 1, N);
+      k_lambda<T><<<G, NT, 0, st>>>(ab2, v2, l2, h->adj_red, h->adj_red + 1, N);
+      ACK(cudaGetLastError());
+      if ((k & 7) == 7) {
+        ACK(cudaMemcpyAsync(host_red, h->adj_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+        ACK(cudaStreamSynchronize(st));
+        conv = host_red[0] <= tol * host_red[1];
+        if (!std::isfinite(host_red[0]))
+          return jko::handle_error(h, JKO_ERR_NUMERIC, "adjoint iterates are not finite");
+      }
+    }
+    if (adj_iters) adj_iters[t] = k;
+    k_sp_u<T><<<G, NT, 0, st>>>(E1, E2, s1, s2, l1, l2, u1, u2, kappa, h->has_kappa, N);
+    ACK(cudaGetLastError());
+    ACK(xi_apply<T>(h, u1, v1, st));
+    ACK(xi_apply<T>(h, u2, v2, st));
+    T* wacc = wbar;
+    if (!grad_w) wacc = ab2;   // abar_2 is not needed any more: a scratch accumulator
+    k_sp_final<T><<<G, NT, 0, st>>>(E1, E2, s1, s2, l1, l2, gt1, gt2, v1, v2, iY1, iY2, g1, g2,
+                                    wacc, sigma, kappa, h->has_kappa, N);
+    ACK(cudaGetLastError());
+  }
+  if (grad_p0) ACK(cudaMemcpyAsync(grad_p0, g, sizeof(T) * 2 * N, cudaMemcpyDeviceToDevice, st));
+  ACK(cudaStreamSynchronize(st));
+  return JKO_OK;
+}
+
 template <typename T>
 jko_status backward_dispatch(jko_handle* h, const void* gf, void* gp, void* gw, int* it) {
   if (h->attract) return backward_attraction<T>(h, (const T*)gf, (T*)gp, (T*)gw, it);
+  if (h->species == 2) return backward_species<T>(h, (const T*)gf, (T*)gp, (T*)gw, it);
   switch (h->ek) {
     case jko::EK_CROWD:
       return backward_t<T, jko::EK_CROWD>(h, (const T*)gf, (T*)gp, (T*)gw, it);
@@ -453,9 +604,10 @@ double field_sigma(const jko_handle* h) {
 
 jko_status check_set_potential(jko_handle* h, const void* w) {
   if (!h || !w) return jko::handle_error(h, JKO_ERR_INVALID_ARG, "NULL handle or w");
-  if (h->species == 2)
+  if (h->pair_alpha > 0)
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
-                             "the potentials of a two-species handle are fixed at creation");
+                             "the potentials of a pairwise-attraction handle are fixed at "
+                             "creation");
   if (h->tc && jko::tc_absorbed(h->tc))
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the potential is absorbed into the Gibbs factors of this handle");
@@ -534,10 +686,12 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
     return jko::handle_error(h, JKO_ERR_UNSUPPORTED,
                              "the attraction's adjoint needs a JKO_FP64 handle (its Jacobian "
                              "a_m / s_m leaves the FP32 range)");
-  if (h->species == 2) return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for two species");
-  const size_t es = h->es, N = (size_t)h->N;
-  // per step: q_t and the final scaling a_t (and a_2 of the attraction's second coupling)
-  const size_t per = h->attract ? 3 : 2;
+  if (h->pair_alpha > 0)
+    return jko::handle_error(h, JKO_ERR_UNSUPPORTED, "no adjoint for the pairwise attraction");
+  const size_t es = h->es, N = (size_t)h->N, ns = (size_t)h->ns;
+  // per step: q_t (both species: 2 N) and the final scalings a_t (a_2 of the
+  // second coupling or species too)
+  const size_t per = h->species == 2 ? 4 : (h->attract ? 3 : 2);
   if (h->tape_cap < n_steps) {
     if (h->tape) cudaFree(h->tape);
     h->tape = nullptr;
@@ -553,11 +707,11 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
   for (int t = 0; t < n_steps; ++t) {
     char* slot = (char*)h->tape + es * N * per * t;
     if (q != (const void*)slot)  // from step 1 on the previous step wrote its output here
-      ACK(cudaMemcpyAsync(slot, q, es * N, cudaMemcpyDeviceToDevice, st));
+      ACK(cudaMemcpyAsync(slot, q, es * ns, cudaMemcpyDeviceToDevice, st));
     jko_step_info info{};
     void* dst = (t + 1 < n_steps) ? (void*)((char*)h->tape + es * N * per * (t + 1)) : p_final_dev;
     if (!dst) {
-      if (!h->stage_out) ACK(cudaMalloc(&h->stage_out, es * N));
+      if (!h->stage_out) ACK(cudaMalloc(&h->stage_out, es * ns));
       dst = h->stage_out;
     }
     jko_status s = jko::step_internal(h, slot, dst, &info, t == 0);
@@ -566,9 +720,9 @@ jko_status jko_flow_record(jko_handle* h, const void* p0_dev, int n_steps, void*
     if (infos) infos[t] = info;
     if (s == JKO_ERR_NUMERIC) worst = JKO_ERR_NUMERIC;
     else if (s == JKO_NOT_CONVERGED && worst == JKO_OK) worst = JKO_NOT_CONVERGED;
-    ACK(cudaMemcpyAsync(slot + es * N, h->a, es * N, cudaMemcpyDeviceToDevice, st));
-    if (h->attract)
-      ACK(cudaMemcpyAsync(slot + 2 * es * N, h->a2, es * N, cudaMemcpyDeviceToDevice, st));
+    ACK(cudaMemcpyAsync(slot + es * ns, h->a, es * N, cudaMemcpyDeviceToDevice, st));
+    if (h->attract || h->species == 2)
+      ACK(cudaMemcpyAsync(slot + es * (ns + N), h->a2, es * N, cudaMemcpyDeviceToDevice, st));
     h->tape_mass[t] = info.mass;
     h->tape_steps = t + 1;
     q = dst;

@@ -566,7 +566,7 @@ def jko_flow_backward(h: Handle, grad_final, want_p0: bool = True, want_w: bool 
     _check(L.jko_set_stream(h.ptr, _current_stream()), h.ptr)
     _check(L.jko_flow_backward(h.ptr, _dev_image(h, grad_final.contiguous(), "grad"),
                                _dev_image(h, gp, "grad_p0") if gp is not None else None,
-                               _dev_image(h, gw, "grad_w") if gw is not None else None,
+                               _dev_image(h, gw, "grad_w", h.cells) if gw is not None else None,
                                iters), h.ptr)
     return gp, gw, list(iters)
 

@@ -224,3 +224,21 @@ def test_adjoint_attraction_matches_oracle():
         jko.jko_flow_record(h32, torch.tensor(pb.q0, dtype=torch.float32, device="cuda"), 1)
     assert e.value.status == jko.Status.UNSUPPORTED
     jko.jko_destroy(h32)
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("FP64", 1e-13, 1e-6), ("FP32", 1e-7, 1e-3)])
+def test_adjoint_two_species_matches_oracle(prec, tol, bar):
+    """The adjoint of two densities coupled through the congestion of their
+    sum (Sec. 5.3; both species carry direct terms and their own q, the
+    Jacobian of the joint prox acts where the sum is clamped) against the
+    oracle's FP64 reverse-mode gradient: 32^2, 2 steps, congestion active;
+    dL/dw is the first species' potential, dL/dp0 both species."""
+    from oracle import adjoint
+    pb = inputs.two_species_problem(32, gamma=2e-3, tau=0.05, n_steps=2)
+    target = np.full(2 * pb.N, 0.5 / pb.N)
+    Lo, gpo, gwo, _ = adjoint.species_flow_loss_grad(pb, pb.q0, pb.w, target, 2)
+    L, gp, gw, _ = gpu_grad(pb, pb.w, target, 2, prec, tol)
+    ew, ep = _grad_errors(gp, gw, gpo, gwo, pb.q0 > 0)
+    print("species", prec, "loss", L, Lo, "rel L1 grad_w", ew, "grad_p0 (support)", ep)
+    assert abs(L - Lo) <= 10 * bar * abs(Lo)
+    assert ew <= bar and ep <= bar

@@ -82,9 +82,8 @@ def test_rejections():
     bad.mask = np.zeros(pb.N, np.uint8)
     with pytest.raises(jko.JKOError):
         jko.create_from_problem(bad, precision=jko.Precision.FP32)
-    h = jko.create_from_problem(pb, precision=jko.Precision.FP64)
+    # the adjoint of two species runs on the CUDA-core handles, not the tensor-core ones
+    h = jko.create_from_problem(pb, precision=jko.Precision.TF32)
     with pytest.raises(jko.JKOError):
-        jko.jko_flow_record(h, torch.tensor(pb.q0, dtype=torch.float64, device="cuda"), 1)
-    with pytest.raises(jko.JKOError):
-        jko.jko_set_potential(h, np.zeros(pb.N))
+        jko.jko_flow_record(h, torch.tensor(pb.q0, dtype=torch.float32, device="cuda"), 1)
     jko.jko_destroy(h)

@@ -225,3 +225,40 @@ def test_attraction_gradient_matches_central_differences():
             g_dir = float(gw @ d)
         fd = (f(eps) - f(-eps)) / (2 * eps)
         assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
+
+
+def _species_numpy_loss(pb, p0, w, target):
+    import copy
+    from oracle import summation as osum
+    q = copy.deepcopy(pb)
+    q.q0, q.w = p0, w
+    traj, _ = osum.problem_flow(q, n_steps=2, tol=1e-13, max_iter=20000)
+    return float(((traj[-1] - target) ** 2).sum()), traj[-1]
+
+
+def test_species_gradient_matches_central_differences():
+    """The oracle's gradient through the two-species flow (Sec. 5.3): the torch
+    loop = the NumPy flow (1e-12), and dL/dw (first species' potential),
+    dL/dp0 (both species) = central differences of the NumPy flow (1e-5);
+    congestion of the sum active."""
+    pb = inputs.two_species_problem(16, gamma=2e-3, tau=0.05, n_steps=2)
+    target = np.full(2 * pb.N, 0.5 / pb.N)
+    L, gp, gw, pT = adjoint.species_flow_loss_grad(pb, pb.q0, pb.w, target, 2)
+    Ln, pn = _species_numpy_loss(pb, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() <= 1e-12
+    assert abs(L - Ln) <= 1e-12 * abs(Ln)
+    N = pb.N
+    assert (pn[:N] + pn[N:]).max() >= pb.kappa * (1 - 1e-9)    # congestion binds
+    rng = np.random.default_rng(61)
+    eps = 1e-5
+    for which in ("w", "p0"):
+        d = rng.standard_normal(2 * N if which == "p0" else N)
+        if which == "p0":
+            d = pb.q0 * (d - d @ pb.q0)
+            f = lambda e: _species_numpy_loss(pb, pb.q0 + e * d, pb.w, target)[0]  # noqa: E731
+            g_dir = float(gp @ d)
+        else:
+            f = lambda e: _species_numpy_loss(pb, pb.q0, pb.w + e * d, target)[0]  # noqa: E731
+            g_dir = float(gw @ d)
+        fd = (f(eps) - f(-eps)) / (2 * eps)
+        assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
