@@ -10,7 +10,7 @@
 // cell by cell.  Here one launch runs one pass of xi for all M images
 // (blockIdx.z = image):
 //     D_z[m][n] = sum_k K[m][k] X_z[n][k]
-// with the factor K of the pass (K_x or K_y of the TF32 plan, the same band
+// with the factor K of the pass (K_x or K_y of the handle's plan, the same band
 // tables) and the image X_z stored with its contracted axis contiguous, as
 // the single-density passes of tc_gemm.cu.  Epilogues:
 //   EPI_STORE  D as the operand (rounded to tf32, or the bf16 pair): the
