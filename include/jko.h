@@ -93,8 +93,10 @@ typedef struct jko_grid {
    * line's largest entry), where the filter is accurate entry by entry.
    * The potential spreads the scalings over e^{tau/gamma (max w - min w)}, so
    * that range must stay <= 8 (FP32) / 24 (FP64) (measured errors 5.5e-6 /
-   * 9.3e-11 there).  JKO_FP32 / JKO_FP64 single-density handles (no target,
-   * second species or heat kernel), L <= 4096 (FP32) / 2048 (FP64), else
+   * 9.3e-11 there).  JKO_FP32 / JKO_FP64 handles of one density or of two
+   * species (each potential within the rule; no target, pairwise attraction or
+   * heat kernel: the attraction steps' geometric mean of two blurs reads small
+   * entries the transform holds only normwise), L <= 4096 (FP32) / 2048 (FP64), else
    * JKO_ERR_UNSUPPORTED; no fixed-scratch step. */
   int fft;
 } jko_grid;
