@@ -262,3 +262,32 @@ def test_species_gradient_matches_central_differences():
             g_dir = float(gw @ d)
         fd = (f(eps) - f(-eps)) / (2 * eps)
         assert abs(fd - g_dir) <= 1e-5 * abs(fd), (which, fd, g_dir)
+
+
+def test_planted_attraction_sigma_is_caught(monkeypatch):
+    """The attraction's prox takes h with sigma / (1 + tau) (Eq.
+    prox-psi-attraction); a torch loop that used sigma instead must fail the
+    pin against the NumPy attraction flow."""
+    pb = _attraction_case()
+    real = adjoint.prox_torch
+
+    def wrong(s, w, sigma, energy):
+        return real(s, w, sigma * (1.0 + pb.tau), energy)
+    monkeypatch.setattr(adjoint, "prox_torch", wrong)
+    target = np.full(pb.N, 1.0 / pb.N)
+    _, _, _, pT = adjoint.attraction_flow_loss_grad(pb, pb.q0, pb.w, target, 2)
+    _, pn = _attraction_numpy_loss(pb, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() > 1e-6
+
+
+def test_planted_species_clamp_is_caught():
+    """Two species: a congestion bound 1 % above the problem's in the torch
+    loop alone (a clamp at the wrong level) fails the forward pin."""
+    import copy
+    pb = inputs.two_species_problem(16, gamma=2e-3, tau=0.05, n_steps=2)
+    wrong = copy.deepcopy(pb)
+    wrong.kappa = 1.01 * pb.kappa
+    target = np.full(2 * pb.N, 0.5 / pb.N)
+    _, _, _, pT = adjoint.species_flow_loss_grad(wrong, pb.q0, pb.w, target, 2)
+    _, pn = _species_numpy_loss(pb, pb.q0, pb.w, target)
+    assert np.abs(pT - pn).sum() > 1e-6
